@@ -1,0 +1,14 @@
+"""CPU oracle for Powersort (test infrastructure only).
+
+Only the test-suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The library path never does.
+"""
+from .oracle import (  # noqa: F401
+    build,
+    minrun,
+    power,
+    stable_sort,
+    powersort,
+    powersort_vm,
+    OracleResult,
+)

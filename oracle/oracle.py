@@ -1,0 +1,178 @@
+"""ctypes front end of the C oracle in ``powersort_oracle.c``.
+
+TEST INFRASTRUCTURE ONLY: used by the tests, by the smoke check and by the
+CPU-baseline leg of the benchmark; never by the library path.
+
+The C file is compiled with gcc into ``oracle/_build/liboracle.so`` on first
+use (or by :func:`build`).  Every function here only marshals numpy arrays;
+all arithmetic is in the C source, which follows the paper:
+
+* :func:`minrun`       -- Sec. 5, "Algorithm variants" (minimum run length)
+* :func:`power`        -- Sec. 2 Theorem (definition of Power)
+* :func:`stable_sort`  -- the plain definition of the result (stable order)
+* :func:`powersort`    -- Algorithm 1 with Pingpong storage (Sec. 3)
+* :func:`powersort_vm` -- Algorithm 1 with virtual-memory storage (Sec. 4)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "powersort_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_uint64),
+        ("runs", ctypes.c_uint64),
+        ("merges", ctypes.c_uint64),
+        ("merge_cost", ctypes.c_uint64),
+        ("comparisons", ctypes.c_uint64),
+        ("merge_comparisons", ctypes.c_uint64),
+        ("scan_comparisons", ctypes.c_uint64),
+        ("insert_comparisons", ctypes.c_uint64),
+        ("moves", ctypes.c_uint64),
+        ("insert_moves", ctypes.c_uint64),
+        ("peak_pages", ctypes.c_uint64),
+        ("pool_pages", ctypes.c_uint64),
+        ("minrun", ctypes.c_uint32),
+        ("max_stack", ctypes.c_uint32),
+        ("max_power", ctypes.c_uint32),
+        ("page_size", ctypes.c_uint32),
+    ]
+
+
+def compile_source(src: str, so: str) -> str:
+    """gcc a C source of the oracle into a shared object (plain C, -O2)."""
+    os.makedirs(os.path.dirname(so), exist_ok=True)
+    tmp = so + f".{os.getpid()}.tmp"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-Wall", "-o", tmp, src],
+                   check=True)
+    os.replace(tmp, so)
+    return so
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C, -O2, no target-specific flags)."""
+    with _lock:
+        if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+            compile_source(_SRC, _SO)
+    return _SO
+
+
+def open_library(so: str):
+    """ctypes handle of an oracle shared object with its signatures set."""
+    lib = ctypes.CDLL(so)
+    _declare(lib)
+    return lib
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        _lib = open_library(_SO)
+    return _lib
+
+
+def _declare(lib):
+    u32p = ctypes.POINTER(ctypes.c_uint32)
+    u8p = ctypes.POINTER(ctypes.c_uint8)
+    lib.oracle_minrun.restype = ctypes.c_uint32
+    lib.oracle_minrun.argtypes = [ctypes.c_uint64]
+    lib.oracle_power.restype = ctypes.c_uint32
+    lib.oracle_power.argtypes = [ctypes.c_uint64] * 4
+    lib.oracle_stable_sort.restype = ctypes.c_int
+    lib.oracle_stable_sort.argtypes = [u32p, ctypes.c_uint64, u32p, u32p]
+    lib.oracle_powersort.restype = ctypes.c_int
+    lib.oracle_powersort.argtypes = [u32p, u32p, ctypes.c_uint64, u32p, u8p, u32p,
+                                     ctypes.POINTER(_Stats)]
+    lib.oracle_powersort_vm.restype = ctypes.c_int
+    lib.oracle_powersort_vm.argtypes = [u32p, u32p, ctypes.c_uint64, ctypes.c_uint64,
+                                        u32p, u8p, u32p, ctypes.POINTER(_Stats)]
+
+
+def _ptr(a: np.ndarray, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def minrun(n: int, lib=None) -> int:
+    return int((lib or _load()).oracle_minrun(n))
+
+
+def power(n: int, i: int, j: int, k: int, lib=None) -> int:
+    """Power(n, [i,j), [j,k)) from the definition (Sec. 2 Theorem)."""
+    return int((lib or _load()).oracle_power(n, i, j, k))
+
+
+def stable_sort(keys: np.ndarray):
+    """The definition of the result: (sorted keys, stable permutation)."""
+    keys = np.ascontiguousarray(keys, dtype=np.uint32)
+    n = keys.size
+    ko = np.empty(n, np.uint32)
+    po = np.empty(n, np.uint32)
+    if n:
+        rc = _load().oracle_stable_sort(_ptr(keys, ctypes.c_uint32), n,
+                                        _ptr(ko, ctypes.c_uint32), _ptr(po, ctypes.c_uint32))
+        if rc:
+            raise MemoryError("oracle_stable_sort")
+    return ko, po
+
+
+@dataclass
+class OracleResult:
+    keys: np.ndarray
+    perm: np.ndarray
+    run_starts: np.ndarray          # runs + 1 entries, last is n
+    powers: np.ndarray              # runs - 1 entries (uint8)
+    merges: np.ndarray              # (merges, 3) uint32: lo, mid, hi in execution order
+    stats: dict = field(default_factory=dict)
+
+
+def _run(fn_name: str, keys: np.ndarray, page_size: int | None, lib=None):
+    lib = lib or _load()
+    key = np.array(keys, dtype=np.uint32, copy=True)
+    n = key.size
+    perm = np.empty(n, np.uint32)
+    runs = np.empty(n + 2, np.uint32)
+    pw = np.zeros(max(n, 1), np.uint8)
+    mg = np.empty((max(n, 1), 3), np.uint32)
+    st = _Stats()
+    args = [_ptr(key, ctypes.c_uint32), _ptr(perm, ctypes.c_uint32), n]
+    if page_size is not None:
+        args.append(page_size)
+    args += [_ptr(runs, ctypes.c_uint32), _ptr(pw, ctypes.c_uint8), _ptr(mg, ctypes.c_uint32),
+             ctypes.byref(st)]
+    rc = getattr(lib, fn_name)(*args)
+    if rc:
+        raise MemoryError(fn_name)
+    stats = {name: int(getattr(st, name)) for name, _ in _Stats._fields_}
+    r = stats["runs"]
+    return OracleResult(
+        keys=key,
+        perm=perm,
+        run_starts=runs[: r + 1].copy() if n else np.zeros(1, np.uint32),
+        powers=pw[: max(r - 1, 0)].copy(),
+        merges=mg[: stats["merges"]].copy(),
+        stats=stats,
+    )
+
+
+def powersort(keys: np.ndarray, lib=None) -> OracleResult:
+    """Algorithm 1 with Pingpong storage, executed literally on one core."""
+    return _run("oracle_powersort", keys, None, lib)
+
+
+def powersort_vm(keys: np.ndarray, page_size: int, lib=None) -> OracleResult:
+    """Algorithm 1 with virtual-memory (paged) storage, on one core."""
+    return _run("oracle_powersort_vm", keys, int(page_size), lib)

@@ -1,0 +1,287 @@
+"""Pins of the CPU oracle against what the paper and plain mathematics fix.
+
+Each test checks the oracle against something other than its own code:
+hand-worked values from the paper's figures (tests/golden), enumeration of the
+Power definition, closed forms of balanced trees, the O(n) stable-sort
+characterisation, a textbook insertion sort and numpy's stable argsort, a
+brute-force Cartesian tree, and the paper's bounds (Sec. 2 Theorem, Sec. 3,
+Sec. 4, Sec. 6 H5/H6).
+"""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from checks import cartesian_nodes, check_stable_sort, naive_stable_insertion_sort, run_entropy
+from conftest import golden_rows
+from paper_2605_27147_gb300 import inputs
+
+
+# --- Power (Sec. 2 Theorem) -------------------------------------------------
+
+def power_by_enumeration(n, i, j, k):
+    """Smallest p for which some c/2^p lies in ((i+j)/2n, (j+k)/2n], found by
+    trying every c from 0 to 2^p (the interval lies inside (0, 1])."""
+    lo = Fraction(i + j, 2 * n)
+    hi = Fraction(j + k, 2 * n)
+    p = 0
+    while True:
+        for c in range(0, 2 ** p + 1):
+            x = Fraction(c, 2 ** p)
+            if lo < x <= hi:
+                return p
+        p += 1
+
+
+def test_power_worked_example(oracle_mod):
+    for n, i, j, k, p in golden_rows("power_worked_example.txt"):
+        assert oracle_mod.power(int(n), int(i), int(j), int(k)) == int(p)
+
+
+def test_power_exhaustive_small(oracle_mod):
+    for n in range(2, 25):
+        for i in range(0, n):
+            for j in range(i + 1, n):
+                for k in range(j + 1, n + 1):
+                    assert oracle_mod.power(n, i, j, k) == power_by_enumeration(n, i, j, k), (n, i, j, k)
+
+
+def test_power_sampled_large(oracle_mod):
+    rng = np.random.RandomState(11)
+    for _ in range(300):
+        n = int(rng.randint(2, 1 << 20))
+        i, j, k = sorted(rng.choice(n + 1, 3, replace=False).tolist())
+        if j == i or k == j:
+            continue
+        assert oracle_mod.power(n, i, j, k) == power_by_enumeration(n, i, j, k)
+
+
+def test_power_balanced_closed_form(oracle_mod):
+    # n = 2^K split into aligned runs of length 2^m: boundary t has power
+    # (K - m) - v2(t), the depth of the dyadic point t / 2^(K-m).
+    for K in (6, 10, 16, 28, 31):
+        for m in (0, 3, 5):
+            if m >= K:
+                continue
+            n, L = 1 << K, 1 << m
+            R = n // L
+            for t in list(range(1, min(R, 70))) + [R // 2, R - 1, R // 3 or 1]:
+                if not 1 <= t < R:
+                    continue
+                v2 = (t & -t).bit_length() - 1
+                assert oracle_mod.power(n, (t - 1) * L, t * L, (t + 1) * L) == (K - m) - v2
+
+
+def test_power_is_at_most_ceil_log2_n(oracle_mod):
+    # (j+k)/2n - (i+j)/2n = (k-i)/2n >= 1/n, so some multiple of 2^-p lies in
+    # the interval once 2^-p <= 1/n.
+    rng = np.random.RandomState(3)
+    for _ in range(2000):
+        n = int(rng.randint(2, 1 << 31))
+        i = int(rng.randint(0, n - 1))
+        j = i + 1
+        k = j + 1 if j + 1 <= n else n
+        if k <= j:
+            continue
+        assert oracle_mod.power(n, i, j, k) <= math.ceil(math.log2(n))
+
+
+# --- minrun (Sec. 5) --------------------------------------------------------
+
+def test_minrun_golden(oracle_mod):
+    for n, m in golden_rows("minrun_rule.txt"):
+        assert oracle_mod.minrun(int(n)) == int(m)
+
+
+# --- Algorithm 1 on a hand-traced input --------------------------------------
+
+def _trace_fixture():
+    rows = {r[0]: r[1:] for r in golden_rows("alg1_trace_n200.txt") if r[0] != "merge"}
+    merges = [tuple(int(x) for x in r[1:]) for r in golden_rows("alg1_trace_n200.txt") if r[0] == "merge"]
+    return rows, merges
+
+
+def test_alg1_hand_trace(oracle_mod):
+    rows, merges = _trace_fixture()
+    n = int(rows["n"][0])
+    keys = np.zeros(n, np.uint32)
+    for blk in rows["blocks"]:
+        a, b, v = (int(x) for x in blk.split(":"))
+        keys[a:b] = np.arange(v, v + (b - a), dtype=np.uint32)
+    perm_exp = np.concatenate([np.arange(int(b.split(":")[0]), int(b.split(":")[1]))
+                               for b in rows["perm_blocks"]]).astype(np.uint32)
+    for res in (oracle_mod.powersort(keys), oracle_mod.powersort_vm(keys, 16)):
+        assert res.stats["minrun"] == int(rows["minrun"][0])
+        assert res.run_starts.tolist() == [int(x) for x in rows["run_starts"]]
+        assert res.powers.tolist() == [int(x) for x in rows["powers"]]
+        assert [tuple(m) for m in res.merges.tolist()] == merges
+        assert res.stats["merge_cost"] == int(rows["merge_cost"][0])
+        assert res.stats["max_stack"] == int(rows["max_stack"][0])
+        assert np.array_equal(res.perm, perm_exp)
+        assert np.array_equal(res.keys, keys[perm_exp])
+
+
+# --- the result is the unique stable sort ----------------------------------
+
+EDGE_SIZES = [0, 1, 2, 3, 31, 32, 33, 63, 64, 65, 127, 128, 129, 200, 1000, 4097]
+DISTS = ["uniform", "zipf", "runs", "paper", "sorted", "reversed", "equal", "few"]
+
+
+@pytest.mark.parametrize("dist", DISTS)
+def test_stable_sort_definition(oracle_mod, dist):
+    for n in EDGE_SIZES + [30011]:
+        keys = inputs.make(dist, n, 17 + n)
+        ko, po = oracle_mod.stable_sort(keys)
+        check_stable_sort(keys, ko, po)
+        ref = np.argsort(keys, kind="stable").astype(np.uint32)   # library routine
+        assert np.array_equal(po, ref)
+
+
+def test_stable_sort_vs_textbook_insertion(oracle_mod):
+    for seed, n in [(1, 0), (2, 1), (3, 17), (4, 300), (5, 1000), (6, 2000)]:
+        keys = inputs.make("few", n, seed)
+        ko, po = oracle_mod.stable_sort(keys)
+        nk, np_ = naive_stable_insertion_sort(keys)
+        assert np.array_equal(ko, nk) and np.array_equal(po, np_)
+
+
+@pytest.mark.parametrize("dist", DISTS)
+def test_powersort_result_is_stable_sort(oracle_mod, dist):
+    for n in EDGE_SIZES + [1 << 12, (1 << 15) + 123]:
+        keys = inputs.make(dist, n, 1000 + n)
+        ref = np.argsort(keys, kind="stable").astype(np.uint32)
+        r = oracle_mod.powersort(keys)
+        check_stable_sort(keys, r.keys, r.perm)
+        assert np.array_equal(r.perm, ref)
+        v = oracle_mod.powersort_vm(keys, 64)
+        assert np.array_equal(v.perm, ref) and np.array_equal(v.keys, r.keys)
+        # the storage scheme changes nothing but the memory traffic
+        assert v.run_starts.tolist() == r.run_starts.tolist()
+        assert v.powers.tolist() == r.powers.tolist()
+        assert v.merges.tolist() == r.merges.tolist()
+
+
+def test_powersort_vs_textbook_insertion_small(oracle_mod):
+    for seed in range(30):
+        n = 64 + 37 * seed
+        keys = inputs.make("few" if seed % 2 else "uniform", n, seed)
+        r = oracle_mod.powersort(keys)
+        nk, np_ = naive_stable_insertion_sort(keys)
+        assert np.array_equal(r.keys, nk) and np.array_equal(r.perm, np_)
+
+
+# --- runs, the merge tree and the bounds ------------------------------------
+
+def _runs_by_definition(keys, m):
+    """Run starts straight from Sec. 5's rule, by a plain scan (forced runs
+    are sorted before the scan moves on, as ExtractRun does)."""
+    a = [int(x) for x in keys]
+    n = len(a)
+    starts = [0]
+    s = 0
+    while s < n:
+        e = s + 1
+        while e < n and a[e - 1] <= a[e]:
+            e += 1
+        if e - s < m:
+            e = min(s + m, n)
+            a[s:e] = sorted(a[s:e])
+        s = e
+        starts.append(s)
+    return starts
+
+
+@pytest.mark.parametrize("dist", ["uniform", "zipf", "runs", "few", "paper", "equal"])
+def test_runs_match_rule(oracle_mod, dist):
+    for n in (1, 63, 64, 65, 1000, 5003, 20000):
+        keys = inputs.make(dist, n, 5 + n)
+        r = oracle_mod.powersort(keys)
+        assert r.run_starts.tolist() == _runs_by_definition(keys, oracle_mod.minrun(n))
+        lens = np.diff(r.run_starts.astype(np.int64))
+        if n >= 64 and lens.size > 1:
+            assert lens[:-1].min() >= oracle_mod.minrun(n)
+
+
+@pytest.mark.parametrize("dist", ["uniform", "zipf", "runs", "few", "paper", "sorted"])
+def test_merge_tree_is_cartesian_tree_of_powers(oracle_mod, dist):
+    for n in (64, 65, 1000, 30011, 1 << 16):
+        keys = inputs.make(dist, n, 99 + n)
+        r = oracle_mod.powersort(keys)
+        rs, pw = r.run_starts, r.powers
+        assert len(pw) == len(rs) - 2 or len(rs) <= 2
+        # Power recomputed per boundary from its definition
+        for t in range(1, len(rs) - 1):
+            if t % 7 == 0 or n <= 1000:
+                assert pw[t - 1] == power_by_enumeration(n, int(rs[t - 1]), int(rs[t]), int(rs[t + 1]))
+        nodes = cartesian_nodes(rs, pw)
+        got = {int(mid): (int(lo), int(hi)) for lo, mid, hi in r.merges.tolist()}
+        assert got == nodes
+        assert r.stats["merge_cost"] == sum(hi - lo for lo, hi in nodes.values())
+        # two equal powers always have a smaller one between them
+        pl = pw.tolist()
+        last = {}
+        for t, p in enumerate(pl):
+            if p in last:
+                assert min(pl[last[p] + 1: t] or [99]) < p
+            last[p] = t
+
+
+@pytest.mark.parametrize("dist", ["uniform", "zipf", "runs", "few", "paper", "sorted", "reversed"])
+def test_theorem_bounds_and_counts(oracle_mod, dist):
+    for n in (64, 1000, 30011, 1 << 16, 100003):
+        keys = inputs.make(dist, n, 7 * n + 1)
+        r = oracle_mod.powersort(keys)
+        s = r.stats
+        H = run_entropy(r.run_starts)
+        # Sec. 2 Theorem: stack height and merge cost
+        assert s["max_stack"] <= math.ceil(math.log2(n)) + 1
+        assert s["merge_cost"] <= n * (H + 2) + 1e-6
+        # Sec. 2: merges plus run detection take at most M + n - 1 comparisons
+        assert s["merge_comparisons"] + s["scan_comparisons"] <= s["merge_cost"] + n - 1
+        # Sec. 3: Pingpong moves at most M + n
+        assert s["moves"] <= s["merge_cost"] + n
+        # Sec. 4: VM moves at most M + 3n; pages beyond the input are O(log n)
+        P = max(16, 1 << int(round(math.log2(math.sqrt(n / math.log2(n))))))
+        v = oracle_mod.powersort_vm(keys, P)
+        assert v.stats["merge_cost"] == s["merge_cost"]
+        assert v.stats["moves"] <= s["merge_cost"] + 3 * n
+        assert v.stats["pool_pages"] <= math.ceil(math.log2(n)) + 3
+        # H5: the storage scheme leaves the comparisons (almost) unchanged; the
+        # Pingpong last-pop merges run right to left, which may shift a few
+        # (the footnote to H5 in Sec. 6)
+        assert abs(v.stats["merge_comparisons"] - s["merge_comparisons"]) <= 0.02 * s["merge_cost"] + 64
+
+
+def test_closed_form_uniform_2_16(oracle_mod):
+    # n = 2^16 uniform keys: every run is forced to 32 elements (minrun 32), the
+    # 2048 runs form a perfect tree of height 11 and M = 11 * 2^16.
+    n = 1 << 16
+    r = oracle_mod.powersort(inputs.uniform(n, 0))
+    assert np.all(np.diff(r.run_starts.astype(np.int64)) == 32)
+    assert r.stats["runs"] == 2048
+    assert r.stats["merge_cost"] == 11 * n
+    assert r.stats["max_stack"] == 11
+
+
+def test_closed_form_aligned_blocks(oracle_mod):
+    # ascending blocks of 2^m with a descent between blocks: M = n (K - m)
+    for K, m in [(10, 5), (12, 6), (14, 8), (16, 10)]:
+        n, L = 1 << K, 1 << m
+        keys = np.tile(np.arange(L, dtype=np.uint32), n // L)
+        r = oracle_mod.powersort(keys)
+        assert r.stats["runs"] == n // L
+        assert r.stats["merge_cost"] == n * (K - m)
+
+
+def test_sorted_input_single_run(oracle_mod):
+    for n in (1, 64, 1000, 1 << 16):
+        keys = np.arange(n, dtype=np.uint32)
+        r = oracle_mod.powersort(keys)
+        assert r.stats["runs"] == 1 and r.stats["merge_cost"] == 0 and r.stats["moves"] == 0
+
+
+def test_mt19937_standard_output():
+    # The C++ standard fixes the 10000th output of mt19937 with the default
+    # seed 5489 at 4123659995; the generators start from the same recurrence.
+    assert int(inputs.mt_raw(5489, 10000)[-1]) == 4123659995

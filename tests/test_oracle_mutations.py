@@ -1,0 +1,90 @@
+"""Plant plausible mistakes in a copy of the oracle and check a pin catches each.
+
+Every mutation is a one-token edit of ``oracle/powersort_oracle.c`` (a flipped
+tie rule, an off-by-one power, a wrong index, a dropped term, a wrong minrun
+loop); the copy is compiled with gcc into a temporary directory and the pins
+below -- the same kinds of check as in test_oracle.py -- must fail on it.
+The shipped oracle must pass them all.
+"""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import oracle as ocore
+from checks import cartesian_nodes, check_stable_sort
+from conftest import golden_rows
+from paper_2605_27147_gb300 import inputs
+
+SRC = os.path.join(os.path.dirname(ocore.__file__), "powersort_oracle.c")
+
+MUTATIONS = {
+    "merge ties take the right run": ("if (bkey[xa] <= key[xb])", "if (bkey[xa] < key[xb])"),
+    "right-to-left merge ties take the left run": ("if (bkey[xa - 1] > key[xb - 1])", "if (bkey[xa - 1] >= key[xb - 1])"),
+    "insertion sort unstable": ("if (!(key[y - 1] > v)) break;", "if (!(key[y - 1] >= v)) break;"),
+    "power off by one": ("if (hi > lo) return p;", "if (hi > lo) return p + 1;"),
+    "power uses wrong index": ("(((unsigned __int128)(i + j)) << p)", "(((unsigned __int128)(i + k)) << p)"),
+    "minrun loop bound": ("while (l >= 64) l = (l + 1) / 2;", "while (l > 64) l = (l + 1) / 2;"),
+    "minrun rounds down": ("while (l >= 64) l = (l + 1) / 2;", "while (l >= 64) l = l / 2;"),
+    "merge cost drops the left input": ("st->merge_cost += cj - ti;\n            ci = ti;\n            --top;                                     /* Pop */",
+                                        "st->merge_cost += cj - ci;\n            ci = ti;\n            --top;                                     /* Pop */"),
+    "runs strictly increasing": ("if (key[e - 1] > key[e]) break;   /* first descent: run ends here */",
+                                 "if (key[e - 1] >= key[e]) break;   /* first descent: run ends here */"),
+    "forced run one short": ("uint64_t end = s + minrun < n ? s + minrun : n;",
+                             "uint64_t end = s + minrun - 1 < n ? s + minrun - 1 : n;"),
+}
+
+
+def run_pins(lib):
+    """Raise AssertionError if the library fails any pin."""
+    for n, i, j, k, p in golden_rows("power_worked_example.txt"):
+        assert oracle.power(int(n), int(i), int(j), int(k), lib=lib) == int(p)
+    for n, m in golden_rows("minrun_rule.txt"):
+        assert oracle.minrun(int(n), lib=lib) == int(m)
+    # closed form: 2^16 uniform keys -> 2048 runs of 32, M = 11 * 2^16
+    r = oracle.powersort(inputs.uniform(1 << 16, 0), lib=lib)
+    assert r.stats["runs"] == 2048 and r.stats["merge_cost"] == 11 << 16
+    for dist, n in [("few", 5000), ("uniform", 3001), ("runs", 20000), ("zipf", 4099), ("equal", 3000)]:
+        keys = inputs.make(dist, n, n)
+        r = oracle.powersort(keys, lib=lib)
+        check_stable_sort(keys, r.keys, r.perm)
+        assert np.array_equal(r.perm, np.argsort(keys, kind="stable"))
+        # runs from the rule, by a plain scan
+        a = [int(x) for x in keys]
+        m = oracle.minrun(n, lib=lib)
+        starts, s = [0], 0
+        while s < n:
+            e = s + 1
+            while e < n and a[e - 1] <= a[e]:
+                e += 1
+            if e - s < m:
+                e = min(s + m, n)
+                a[s:e] = sorted(a[s:e])
+            s = e
+            starts.append(s)
+        assert r.run_starts.tolist() == starts
+        got = {int(mid): (int(lo), int(hi)) for lo, mid, hi in r.merges.tolist()}
+        nodes = cartesian_nodes(r.run_starts, r.powers)
+        assert got == nodes
+        assert r.stats["merge_cost"] == sum(h - l for l, h in nodes.values())
+
+
+def test_shipped_oracle_passes_pins(oracle_mod):
+    run_pins(None)
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_mutation(name):
+    old, new = MUTATIONS[name]
+    src = open(SRC).read()
+    assert src.count(old) >= 1, f"mutation anchor missing: {old!r}"
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "mut.c")
+        with open(path, "w") as f:
+            f.write(src.replace(old, new))
+        so = ocore.compile_source(path, os.path.join(d, "libmut.so"))
+        lib = ocore.open_library(so)
+        with pytest.raises(AssertionError):
+            run_pins(lib)
