@@ -1,0 +1,156 @@
+/*
+ * powersort.h -- C ABI of the GB300 (sm_103a) Powersort library.
+ *
+ * The library sorts unsigned 32-bit keys stably on the GPU by the method of
+ * "Virtual-Memory Powersort" (Moltmann, Nakajima, Wild):
+ *   - runs are maximal non-decreasing segments, short ones extended to the
+ *     minimum run length and insertion-sorted (Sec. 2 operation ExtractRun;
+ *     Sec. 5 "Algorithm variants" for the minrun rule);
+ *   - every boundary between adjacent runs gets its Power (Sec. 2 Theorem);
+ *   - the runs are merged along the tree that Algorithm 1's stack policy
+ *     builds (merge the stack top while its power is >= the new power), with
+ *     stable merges that take the left run on ties (Algorithm 2);
+ *   - run storage is either Pingpong (Sec. 3: one n-element scratch buffer,
+ *     every merge out of place) or virtual-memory pages (Sec. 4: runs as page
+ *     lists over a small recycled page pool, a final page permutation).
+ * The result is the unique stable sort: sorted keys and, optionally, the
+ * stable permutation perm (perm[r] = input index of the r-th output).
+ *
+ * Conventions for every call below:
+ *   - Pointers named d_* are CUDA device pointers owned by the caller; the
+ *     library reads and writes them only inside the call's stream work.
+ *     Pointers named h_* (and the stats / config structs) are host memory.
+ *   - Keys are uint32_t, sorted in place (the paper's Powersort(input[0, n))
+ *     sorts its input in place, Algorithm 1).  perm is output only.
+ *   - All work is enqueued on the stream given to ps_create.  A call returns
+ *     once its work is enqueued, except when it is given a non-NULL stats
+ *     pointer or it is a ps_get_* call: those synchronise the stream.
+ *   - Errors: a call that returns anything but PS_OK has enqueued nothing
+ *     (argument errors) or has left the outputs unspecified (device errors).
+ *     PS_EINVAL: NULL where a pointer is required, sizes above the limits
+ *     given at create time, offsets not non-decreasing.  PS_ENOMEM: device
+ *     allocation failed.  PS_ECUDA: a CUDA call failed.  PS_ETIMEOUT: a
+ *     device-side wait exceeded its iteration limit (the kernel stopped and
+ *     reported it; the context stays usable).  PS_EINTERNAL: a device-side
+ *     consistency check failed.
+ *   - Nothing falls back to the CPU: without a usable GPU every call that
+ *     needs one returns PS_ECUDA.
+ *   - A context is used by one host thread at a time.
+ */
+#ifndef POWERSORT_H
+#define POWERSORT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PS_API __attribute__((visibility("default")))
+
+typedef enum ps_status {
+    PS_OK = 0,
+    PS_EINVAL = 1,
+    PS_ENOMEM = 2,
+    PS_ECUDA = 3,
+    PS_ETIMEOUT = 4,
+    PS_EINTERNAL = 5
+} ps_status;
+
+/* Run storage (Sec. 1 "Pingpong Powersort" and "Virtual-Memory Powersort"). */
+typedef enum ps_mode {
+    PS_MODE_PINGPONG = 0, /* Sec. 3: scratch of n keys (+ n perm entries)          */
+    PS_MODE_VM = 1        /* Sec. 4: page pool of O(sqrt(n log n)) elements + tables */
+} ps_mode;
+
+typedef struct ps_config {
+    uint32_t mode;       /* ps_mode                                                  */
+    uint32_t want_perm;  /* nonzero: calls may produce the stable permutation        */
+    uint64_t max_n;      /* largest instance, >= 1, < 2^32                           */
+    uint64_t max_total;  /* largest sum of instance sizes per batched call (0: max_n) */
+    uint32_t max_count;  /* most instances per batched call (0: 1)                   */
+    uint32_t page_log2;  /* VM page size P = 2^page_log2 (0: chosen from max_n as
+                            sqrt(n / log2 n) rounded to a power of two, Sec. 4)      */
+    uint32_t tile_log2;  /* on-chip tile capacity 2^tile_log2 in 10..12 (0: 12)      */
+    uint32_t pool_pages; /* VM page-pool size in pages (0: chosen by the library)    */
+    uint32_t reserved[4];
+} ps_config;
+
+/* Per-call statistics (sums over instances for batched calls).  The paper's
+ * merge cost M is the sum of the lengths of all merge inputs (Sec. 2
+ * Definition); the theorem bounds it by n(H + 2). */
+typedef struct ps_stats {
+    uint64_t n;             /* elements sorted                                    */
+    uint64_t runs;          /* runs found by run detection                        */
+    uint64_t merge_cost;    /* M                                                  */
+    uint64_t tiles;         /* subtrees merged on chip (one CTA each)             */
+    uint64_t global_nodes;  /* merges done through HBM                            */
+    uint64_t leaf_moves;    /* elements copied to reach the parity buffer         */
+    uint64_t scratch_bytes; /* device memory owned by the context                 */
+    uint64_t peak_pages;    /* VM mode: most pool pages in use at once (else 0)   */
+    uint32_t max_power;     /* largest boundary power                             */
+    uint32_t rounds;        /* HBM merge rounds executed                          */
+    uint32_t minrun;        /* minrun of the (first) instance                     */
+    uint32_t instances;
+} ps_stats;
+
+typedef struct ps_ctx ps_ctx;
+
+/* Human-readable name of a status code (static storage). */
+PS_API const char* ps_status_str(ps_status s);
+
+/* Create a context on CUDA device `device`, enqueueing on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  Allocates every
+ * device buffer the limits in *cfg can need (Sec. 4 "Pre-allocation of
+ * buffers": all extra memory is taken once, up front).  *out receives the
+ * context; on error it is set to NULL. */
+PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, ps_ctx** out);
+
+/* Powersort(input[0, n)) (Algorithm 1): sort d_keys[0, n) in place, stably.
+ * d_perm: NULL, or n entries receiving the stable permutation (requires
+ * want_perm at create time).  n == 0 and n == 1 are valid.  stats: NULL, or
+ * filled after the stream is synchronised. */
+PS_API ps_status ps_run(ps_ctx* ctx, uint32_t* d_keys, uint32_t* d_perm, uint64_t n,
+                        ps_stats* stats);
+
+/* The same sort for `count` independent instances in one set of launches.
+ * Instance q is d_keys[off[q], off[q+1]) where off = d_offsets (device,
+ * count + 1 entries, non-decreasing, off[0] = 0); perm values are local to
+ * each instance.  Sizes must respect max_n / max_total / max_count. */
+PS_API ps_status ps_run_batched(ps_ctx* ctx, uint32_t* d_keys, uint32_t* d_perm,
+                                const uint64_t* d_offsets, uint32_t count, ps_stats* stats);
+
+/* Wait for the context's stream and report the device-side status of the
+ * last call: PS_OK, or PS_ETIMEOUT / PS_EINTERNAL when a kernel gave up a
+ * bounded wait or failed a consistency check (calls without stats return
+ * after enqueueing, so this is where such errors surface). */
+PS_API ps_status ps_sync(ps_ctx* ctx);
+
+/* Introspection of the last call, for parity checks (synchronises).
+ *   ps_get_runs:   run starts of instance q plus its end (runs + 1 entries),
+ *                  instance-local (ExtractRun, Sec. 2 / Sec. 5).
+ *   ps_get_powers: Power of every boundary between adjacent runs of instance
+ *                  q, left to right (runs - 1 entries, Sec. 2 Theorem).
+ *   ps_get_nodes:  for every boundary, the element range [lo, hi) of the
+ *                  merge that joins its two sides in Algorithm 1 (2 entries
+ *                  per boundary: lo, hi), i.e. the merge tree.
+ * h_out receives at most `cap` entries; *count (may be NULL) receives the
+ * number available.  PS_EINVAL if q is not an instance of the last call. */
+PS_API ps_status ps_get_runs(ps_ctx* ctx, uint32_t q, uint32_t* h_out, uint64_t cap,
+                             uint64_t* count);
+PS_API ps_status ps_get_powers(ps_ctx* ctx, uint32_t q, uint8_t* h_out, uint64_t cap,
+                               uint64_t* count);
+PS_API ps_status ps_get_nodes(ps_ctx* ctx, uint32_t q, uint32_t* h_out, uint64_t cap,
+                              uint64_t* count);
+/* Statistics of one instance of the last call (synchronises). */
+PS_API ps_status ps_get_instance_stats(ps_ctx* ctx, uint32_t q, ps_stats* stats);
+
+/* Release every device buffer of the context.  NULL is a no-op. */
+PS_API void ps_destroy(ps_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POWERSORT_H */

@@ -1,0 +1,221 @@
+"""Thin Python binding of the C ABI in ``include/powersort.h``.
+
+Argument marshalling only: every step of the sort runs in the CUDA kernels
+of ``libpowersort.so``.  Device arrays are torch CUDA tensors (torch supplies
+device memory and streams); they are passed as raw pointers.  There is no CPU
+fallback: if the library or a GPU is missing, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+PS_OK, PS_EINVAL, PS_ENOMEM, PS_ECUDA, PS_ETIMEOUT, PS_EINTERNAL = range(6)
+PS_MODE_PINGPONG, PS_MODE_VM = 0, 1
+
+# every symbol include/powersort.h declares
+EXPORTS = (
+    "ps_status_str", "ps_create", "ps_run", "ps_run_batched", "ps_sync", "ps_get_runs",
+    "ps_get_powers", "ps_get_nodes", "ps_get_instance_stats", "ps_destroy",
+)
+
+
+class ps_config(ctypes.Structure):
+    _fields_ = [
+        ("mode", ctypes.c_uint32),
+        ("want_perm", ctypes.c_uint32),
+        ("max_n", ctypes.c_uint64),
+        ("max_total", ctypes.c_uint64),
+        ("max_count", ctypes.c_uint32),
+        ("page_log2", ctypes.c_uint32),
+        ("tile_log2", ctypes.c_uint32),
+        ("pool_pages", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32 * 4),
+    ]
+
+
+class ps_stats(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_uint64),
+        ("runs", ctypes.c_uint64),
+        ("merge_cost", ctypes.c_uint64),
+        ("tiles", ctypes.c_uint64),
+        ("global_nodes", ctypes.c_uint64),
+        ("leaf_moves", ctypes.c_uint64),
+        ("scratch_bytes", ctypes.c_uint64),
+        ("peak_pages", ctypes.c_uint64),
+        ("max_power", ctypes.c_uint32),
+        ("rounds", ctypes.c_uint32),
+        ("minrun", ctypes.c_uint32),
+        ("instances", ctypes.c_uint32),
+    ]
+
+    def as_dict(self):
+        return {name: int(getattr(self, name)) for name, _ in self._fields_}
+
+
+class PowersortError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {lib().ps_status_str(status).decode()} ({status})")
+        self.status = status
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.SO
+
+
+def lib(build_if_missing: bool = True):
+    """The loaded ``libpowersort.so`` (built in tree when missing)."""
+    global _lib
+    if _lib is None:
+        path = _build.SO
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise FileNotFoundError(f"{path} is missing: run __graft_entry__.build()")
+            _build.build()
+        L = ctypes.CDLL(path)
+        vp = ctypes.c_void_p
+        u32p = ctypes.POINTER(ctypes.c_uint32)
+        u8p = ctypes.POINTER(ctypes.c_uint8)
+        u64p = ctypes.POINTER(ctypes.c_uint64)
+        L.ps_status_str.restype = ctypes.c_char_p
+        L.ps_status_str.argtypes = [ctypes.c_int]
+        L.ps_create.restype = ctypes.c_int
+        L.ps_create.argtypes = [ctypes.POINTER(ps_config), ctypes.c_int, vp, ctypes.POINTER(vp)]
+        L.ps_run.restype = ctypes.c_int
+        L.ps_run.argtypes = [vp, vp, vp, ctypes.c_uint64, ctypes.POINTER(ps_stats)]
+        L.ps_run_batched.restype = ctypes.c_int
+        L.ps_run_batched.argtypes = [vp, vp, vp, vp, ctypes.c_uint32, ctypes.POINTER(ps_stats)]
+        L.ps_sync.restype = ctypes.c_int
+        L.ps_sync.argtypes = [vp]
+        L.ps_get_runs.restype = ctypes.c_int
+        L.ps_get_runs.argtypes = [vp, ctypes.c_uint32, u32p, ctypes.c_uint64, u64p]
+        L.ps_get_powers.restype = ctypes.c_int
+        L.ps_get_powers.argtypes = [vp, ctypes.c_uint32, u8p, ctypes.c_uint64, u64p]
+        L.ps_get_nodes.restype = ctypes.c_int
+        L.ps_get_nodes.argtypes = [vp, ctypes.c_uint32, u32p, ctypes.c_uint64, u64p]
+        L.ps_get_instance_stats.restype = ctypes.c_int
+        L.ps_get_instance_stats.argtypes = [vp, ctypes.c_uint32, ctypes.POINTER(ps_stats)]
+        L.ps_destroy.restype = None
+        L.ps_destroy.argtypes = [vp]
+        _lib = L
+    return _lib
+
+
+def _check(st: int, what: str):
+    if st != PS_OK:
+        raise PowersortError(st, what)
+
+
+def _ptr(t) -> int | None:
+    """Raw device pointer of a torch tensor (None for None)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("device arrays must be CUDA tensors")
+    if not t.is_contiguous():
+        raise ValueError("device arrays must be contiguous")
+    return t.data_ptr()
+
+
+class Context:
+    """One ``ps_ctx``: its stream and every scratch buffer, allocated once."""
+
+    def __init__(self, max_n: int, *, mode: int = PS_MODE_PINGPONG, want_perm: bool = True,
+                 max_total: int = 0, max_count: int = 0, tile_log2: int = 0, page_log2: int = 0,
+                 pool_pages: int = 0, device: int = 0, stream=None):
+        import torch
+
+        self.device = device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        cfg = ps_config(mode=mode, want_perm=1 if want_perm else 0, max_n=max_n, max_total=max_total,
+                        max_count=max_count, page_log2=page_log2, tile_log2=tile_log2,
+                        pool_pages=pool_pages)
+        h = ctypes.c_void_p()
+        _check(lib().ps_create(ctypes.byref(cfg), device, ctypes.c_void_p(self.stream.cuda_stream),
+                               ctypes.byref(h)), "ps_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().ps_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # --- calls -------------------------------------------------------------
+    def run(self, keys, perm=None, *, stats: bool = False):
+        """ps_run: sort ``keys`` (uint32 as torch.int32/uint32 CUDA tensor) in place."""
+        st = ps_stats() if stats else None
+        _check(lib().ps_run(self._h, _ptr(keys), _ptr(perm), keys.numel(),
+                            ctypes.byref(st) if st is not None else None), "ps_run")
+        return st.as_dict() if st is not None else None
+
+    def run_batched(self, keys, offsets, perm=None, *, stats: bool = False):
+        """ps_run_batched: ``offsets`` is a CUDA int64/uint64 tensor of count + 1 entries."""
+        st = ps_stats() if stats else None
+        _check(lib().ps_run_batched(self._h, _ptr(keys), _ptr(perm), _ptr(offsets), offsets.numel() - 1,
+                                    ctypes.byref(st) if st is not None else None), "ps_run_batched")
+        return st.as_dict() if st is not None else None
+
+    def sync(self):
+        _check(lib().ps_sync(self._h), "ps_sync")
+
+    def runs(self, q: int = 0) -> np.ndarray:
+        cnt = ctypes.c_uint64()
+        _check(lib().ps_get_runs(self._h, q, None, 0, ctypes.byref(cnt)), "ps_get_runs")
+        out = np.empty(cnt.value, np.uint32)
+        _check(lib().ps_get_runs(self._h, q, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), out.size,
+                                 None), "ps_get_runs")
+        return out
+
+    def powers(self, q: int = 0) -> np.ndarray:
+        cnt = ctypes.c_uint64()
+        _check(lib().ps_get_powers(self._h, q, None, 0, ctypes.byref(cnt)), "ps_get_powers")
+        out = np.empty(cnt.value, np.uint8)
+        if out.size:
+            _check(lib().ps_get_powers(self._h, q, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                       out.size, None), "ps_get_powers")
+        return out
+
+    def nodes(self, q: int = 0) -> np.ndarray:
+        cnt = ctypes.c_uint64()
+        _check(lib().ps_get_nodes(self._h, q, None, 0, ctypes.byref(cnt)), "ps_get_nodes")
+        out = np.empty(cnt.value, np.uint32)
+        if out.size:
+            _check(lib().ps_get_nodes(self._h, q, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                      out.size, None), "ps_get_nodes")
+        return out.reshape(-1, 2)
+
+    def instance_stats(self, q: int = 0) -> dict:
+        st = ps_stats()
+        _check(lib().ps_get_instance_stats(self._h, q, ctypes.byref(st)), "ps_get_instance_stats")
+        return st.as_dict()
+
+
+def as_u32(t):
+    """View an int32 torch tensor holding uint32 bit patterns (torch has limited uint32 support)."""
+    import torch
+
+    return t.view(torch.int32) if t.dtype != torch.int32 else t

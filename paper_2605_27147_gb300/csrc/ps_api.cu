@@ -1,0 +1,391 @@
+// C ABI of the library (include/powersort.h): argument checks, the context
+// with every device buffer allocated up front, and the launch sequence.
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ps_internal.cuh"
+
+struct ps_ctx {
+    ps_config cfg;
+    int device;
+    cudaStream_t stream;
+    int num_sms;
+    int grid_runs, grid_plan, grid_tiles, grid_merge;
+    unsigned long long max_total;
+    uint32_t max_count;
+    ps::Job base;               // device buffers; per-call fields filled by each run
+    ps::Ctr* h_ctr;             // pinned host copy of the counters
+    ps::Inst* h_inst;           // pinned host copy of one instance record
+    uint32_t last_count;
+    int last_valid;
+    size_t scratch_bytes;
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+constexpr unsigned long long LIMIT_N = 0xffffffffull;  // instance sizes and totals < 2^32
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+template <typename T>
+ps_status dev_alloc(ps_ctx* c, T** p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) return PS_OK;
+    void* q = nullptr;
+    if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return PS_ENOMEM;
+    }
+    c->allocs.push_back(q);
+    c->scratch_bytes += count * sizeof(T);
+    *p = static_cast<T*>(q);
+    return PS_OK;
+}
+
+void free_all(ps_ctx* c)
+{
+    for (void* p : c->allocs) cudaFree(p);
+    c->allocs.clear();
+    if (c->h_ctr) cudaFreeHost(c->h_ctr);
+    if (c->h_inst) cudaFreeHost(c->h_inst);
+    c->h_ctr = nullptr;
+    c->h_inst = nullptr;
+}
+
+ps_status from_device_error(uint32_t e)
+{
+    if (e == ps::DERR_TIMEOUT) return PS_ETIMEOUT;
+    if (e != 0) return PS_EINTERNAL;
+    return PS_OK;
+}
+
+ps_status enqueue(ps_ctx* c, const ps::Job& J)
+{
+    cudaStream_t s = c->stream;
+    if (ps::launch_setup(J, s) != cudaSuccess) return PS_ECUDA;
+    if (ps::launch_runs(J, c->grid_runs, s) != cudaSuccess) return PS_ECUDA;
+    if (ps::launch_plan(J, c->grid_plan, s) != cudaSuccess) return PS_ECUDA;
+    if (ps::launch_tiles(J, c->grid_tiles, s) != cudaSuccess) return PS_ECUDA;
+    if (ps::launch_merge_rounds(J, c->grid_merge, s) != cudaSuccess) return PS_ECUDA;
+    if (ps::launch_finish(J, s) != cudaSuccess) return PS_ECUDA;
+    if (cudaMemcpyAsync(c->h_ctr, J.ctr, sizeof(ps::Ctr), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return PS_ECUDA;
+    return PS_OK;
+}
+
+ps_status sync_and_check(ps_ctx* c)
+{
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return PS_ECUDA;
+    }
+    return from_device_error(c->h_ctr->error);
+}
+
+void fill_stats(const ps_ctx* c, ps_stats* st, uint32_t count)
+{
+    std::memset(st, 0, sizeof(*st));
+    const ps::Ctr* h = c->h_ctr;
+    st->n = h->n_total;
+    st->runs = h->runs_total;
+    st->merge_cost = h->M_total;
+    st->tiles = h->n_tiles;
+    st->global_nodes = h->n_gnodes;
+    st->leaf_moves = h->leaf_moves;
+    st->scratch_bytes = c->scratch_bytes;
+    st->peak_pages = 0;
+    st->max_power = h->max_power;
+    st->rounds = h->rounds;
+    st->instances = count;
+}
+
+ps_status run_common(ps_ctx* c, uint32_t* d_keys, uint32_t* d_perm, const uint64_t* d_offsets,
+                     unsigned long long single_n, uint32_t count, ps_stats* stats)
+{
+    DeviceGuard g(c->device);
+    ps::Job J = c->base;
+    J.keysA = d_keys;
+    J.permA = d_perm;
+    J.want_perm = d_perm ? 1u : 0u;
+    if (!d_perm) J.permB = nullptr;
+    J.offsets = reinterpret_cast<const unsigned long long*>(d_offsets);
+    J.single_n = single_n;
+    J.count = count;
+    c->last_valid = 0;
+    ps_status st = enqueue(c, J);
+    if (st != PS_OK) {
+        cudaGetLastError();
+        return st;
+    }
+    c->last_valid = 1;
+    c->last_count = count;
+    if (stats) {
+        st = sync_and_check(c);
+        if (st != PS_OK) return st;
+        fill_stats(c, stats, count);
+        // minrun of the first instance
+        if (cudaMemcpy(c->h_inst, J.inst, sizeof(ps::Inst), cudaMemcpyDeviceToHost) != cudaSuccess) return PS_ECUDA;
+        stats->minrun = c->h_inst->minrun;
+    }
+    return PS_OK;
+}
+
+ps_status read_inst(ps_ctx* c, uint32_t q, ps::Inst* out)
+{
+    if (!c->last_valid || q >= c->last_count) return PS_EINVAL;
+    ps_status st = sync_and_check(c);
+    if (st != PS_OK) return st;
+    if (cudaMemcpy(c->h_inst, c->base.inst + q, sizeof(ps::Inst), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return PS_ECUDA;
+    *out = *c->h_inst;
+    return PS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+PS_API const char* ps_status_str(ps_status s)
+{
+    switch (s) {
+    case PS_OK: return "PS_OK";
+    case PS_EINVAL: return "PS_EINVAL: invalid argument";
+    case PS_ENOMEM: return "PS_ENOMEM: device allocation failed";
+    case PS_ECUDA: return "PS_ECUDA: CUDA call failed";
+    case PS_ETIMEOUT: return "PS_ETIMEOUT: device-side wait exceeded its limit";
+    case PS_EINTERNAL: return "PS_EINTERNAL: device-side consistency check failed";
+    }
+    return "unknown ps_status";
+}
+
+PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, ps_ctx** out)
+{
+    if (!out) return PS_EINVAL;
+    *out = nullptr;
+    if (!cfg) return PS_EINVAL;
+    if (cfg->mode != PS_MODE_PINGPONG) return PS_EINVAL;
+    if (cfg->max_n == 0 || cfg->max_n > LIMIT_N) return PS_EINVAL;
+    const unsigned long long max_total = cfg->max_total ? cfg->max_total : cfg->max_n;
+    if (max_total < cfg->max_n || max_total > LIMIT_N) return PS_EINVAL;
+    const uint32_t tile_log2 = cfg->tile_log2 ? cfg->tile_log2 : (uint32_t)ps::TILE_MAX_LOG2;
+    if (tile_log2 < 10 || tile_log2 > (uint32_t)ps::TILE_MAX_LOG2) return PS_EINVAL;
+    if (device < 0) return PS_EINVAL;
+
+    ps_ctx* c = new (std::nothrow) ps_ctx();
+    if (!c) return PS_ENOMEM;
+    c->cfg = *cfg;
+    c->device = device;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    c->max_total = max_total;
+    c->max_count = cfg->max_count ? cfg->max_count : 1u;
+
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device >= ndev) {
+        cudaGetLastError();
+        delete c;
+        return PS_ECUDA;
+    }
+    DeviceGuard g(device);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+        delete c;
+        return PS_ECUDA;
+    }
+    c->num_sms = prop.multiProcessorCount;
+    c->grid_runs = c->num_sms * 8;
+    c->grid_plan = c->num_sms * 8;
+    c->grid_tiles = ps::tiles_max_grid(c->num_sms);
+    c->grid_merge = ps::merge_rounds_max_grid(c->num_sms);
+
+    ps::Job& J = c->base;
+    std::memset(&J, 0, sizeof(J));
+    J.tile_cap = 1u << tile_log2;
+    const unsigned long long slot_cap = max_total / 32 + 2ull * c->max_count + 2;
+    const unsigned long long chunk_cap = max_total / ps::RUN_CHUNK + c->max_count + 1;
+    const unsigned long long entry_cap = slot_cap;
+    const unsigned long long split_cap = max_total / ps::MERGE_E + entry_cap + 2;
+    if (chunk_cap > 0xffffffffull || entry_cap > 0xffffffffull || split_cap > 0xffffffffull) {
+        delete c;
+        return PS_EINVAL;
+    }
+    J.slot_cap = slot_cap;
+    J.chunk_cap = (uint32_t)chunk_cap;
+    J.entry_cap = (uint32_t)entry_cap;
+    J.split_cap = (uint32_t)split_cap;
+
+    ps_status st = PS_OK;
+    if (st == PS_OK) st = dev_alloc(c, &J.keysB, max_total);
+    if (st == PS_OK && cfg->want_perm) st = dev_alloc(c, &J.permB, max_total);
+    if (st == PS_OK) st = dev_alloc(c, &J.inst, c->max_count);
+    if (st == PS_OK) st = dev_alloc(c, &J.chunk_status, chunk_cap);
+    if (st == PS_OK) st = dev_alloc(c, &J.chunk_map, chunk_cap * ps::MAP_STATES);
+    if (st == PS_OK) st = dev_alloc(c, &J.chunk_incl, chunk_cap);
+    if (st == PS_OK) st = dev_alloc(c, &J.run_start, slot_cap);
+    if (st == PS_OK) st = dev_alloc(c, &J.kappa, slot_cap);
+    if (st == PS_OK) st = dev_alloc(c, &J.power, slot_cap);
+    if (st == PS_OK) st = dev_alloc(c, &J.na, slot_cap);
+    if (st == PS_OK) st = dev_alloc(c, &J.nb, slot_cap);
+    if (st == PS_OK) st = dev_alloc(c, &J.tiles, entry_cap);
+    if (st == PS_OK) st = dev_alloc(c, &J.gnodes, entry_cap);
+    if (st == PS_OK) st = dev_alloc(c, &J.gsorted, entry_cap);
+    if (st == PS_OK) st = dev_alloc(c, &J.splits, split_cap);
+    if (st == PS_OK) st = dev_alloc(c, &J.ctr, 1);
+    if (st == PS_OK && cudaMallocHost(&c->h_ctr, sizeof(ps::Ctr)) != cudaSuccess) st = PS_ENOMEM;
+    if (st == PS_OK && cudaMallocHost(&c->h_inst, sizeof(ps::Inst)) != cudaSuccess) st = PS_ENOMEM;
+    if (st == PS_OK && (cudaMemset(J.chunk_status, 0, chunk_cap * sizeof(uint32_t)) != cudaSuccess ||
+                        cudaMemset(J.ctr, 0, sizeof(ps::Ctr)) != cudaSuccess))
+        st = PS_ECUDA;
+    if (st == PS_OK && cudaDeviceSynchronize() != cudaSuccess) st = PS_ECUDA;
+    if (st != PS_OK) {
+        cudaGetLastError();
+        free_all(c);
+        delete c;
+        return st;
+    }
+    std::memset(c->h_ctr, 0, sizeof(ps::Ctr));
+    *out = c;
+    return PS_OK;
+}
+
+PS_API ps_status ps_run(ps_ctx* ctx, uint32_t* d_keys, uint32_t* d_perm, uint64_t n, ps_stats* stats)
+{
+    if (!ctx) return PS_EINVAL;
+    if (n > ctx->cfg.max_n) return PS_EINVAL;
+    if (n > 0 && !d_keys) return PS_EINVAL;
+    if (d_perm && !ctx->cfg.want_perm) return PS_EINVAL;
+    return run_common(ctx, d_keys, d_perm, nullptr, n, 1, stats);
+}
+
+PS_API ps_status ps_run_batched(ps_ctx* ctx, uint32_t* d_keys, uint32_t* d_perm, const uint64_t* d_offsets,
+                                uint32_t count, ps_stats* stats)
+{
+    if (!ctx || !d_offsets) return PS_EINVAL;
+    if (count == 0 || count > ctx->max_count) return PS_EINVAL;
+    if (!d_keys) return PS_EINVAL;
+    if (d_perm && !ctx->cfg.want_perm) return PS_EINVAL;
+    // the offsets live on the device; their limits are checked there too, but
+    // the host checks them first so a bad table enqueues nothing
+    std::vector<uint64_t> off(count + 1);
+    {
+        DeviceGuard g(ctx->device);
+        if (cudaMemcpyAsync(off.data(), d_offsets, (count + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                            ctx->stream) != cudaSuccess ||
+            cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return PS_ECUDA;
+        }
+    }
+    if (off[0] != 0) return PS_EINVAL;
+    for (uint32_t i = 0; i < count; ++i) {
+        if (off[i + 1] < off[i]) return PS_EINVAL;
+        if (off[i + 1] - off[i] > ctx->cfg.max_n) return PS_EINVAL;
+    }
+    if (off[count] > ctx->max_total) return PS_EINVAL;
+    return run_common(ctx, d_keys, d_perm, d_offsets, 0, count, stats);
+}
+
+PS_API ps_status ps_sync(ps_ctx* ctx)
+{
+    if (!ctx) return PS_EINVAL;
+    DeviceGuard g(ctx->device);
+    return sync_and_check(ctx);
+}
+
+PS_API ps_status ps_get_runs(ps_ctx* ctx, uint32_t q, uint32_t* h_out, uint64_t cap, uint64_t* count)
+{
+    if (!ctx || (!h_out && cap)) return PS_EINVAL;
+    DeviceGuard g(ctx->device);
+    ps::Inst I;
+    ps_status st = read_inst(ctx, q, &I);
+    if (st != PS_OK) return st;
+    const uint64_t avail = I.n ? (uint64_t)I.runs + 1 : 1;
+    if (count) *count = avail;
+    const uint64_t k = avail < cap ? avail : cap;
+    if (k && cudaMemcpy(h_out, ctx->base.run_start + I.run_base, k * sizeof(uint32_t), cudaMemcpyDeviceToHost) !=
+                 cudaSuccess)
+        return PS_ECUDA;
+    return PS_OK;
+}
+
+PS_API ps_status ps_get_powers(ps_ctx* ctx, uint32_t q, uint8_t* h_out, uint64_t cap, uint64_t* count)
+{
+    if (!ctx || (!h_out && cap)) return PS_EINVAL;
+    DeviceGuard g(ctx->device);
+    ps::Inst I;
+    ps_status st = read_inst(ctx, q, &I);
+    if (st != PS_OK) return st;
+    const uint64_t avail = I.runs >= 2 ? (uint64_t)I.runs - 1 : 0;
+    if (count) *count = avail;
+    const uint64_t k = avail < cap ? avail : cap;
+    if (k && cudaMemcpy(h_out, ctx->base.power + I.run_base + 1, k, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return PS_ECUDA;
+    return PS_OK;
+}
+
+PS_API ps_status ps_get_nodes(ps_ctx* ctx, uint32_t q, uint32_t* h_out, uint64_t cap, uint64_t* count)
+{
+    if (!ctx || (!h_out && cap)) return PS_EINVAL;
+    DeviceGuard g(ctx->device);
+    ps::Inst I;
+    ps_status st = read_inst(ctx, q, &I);
+    if (st != PS_OK) return st;
+    const uint64_t nbound = I.runs >= 2 ? (uint64_t)I.runs - 1 : 0;
+    if (count) *count = 2 * nbound;
+    if (!nbound || !cap) return PS_OK;
+    std::vector<uint32_t> rs(I.runs + 1), na(I.runs), nb(I.runs);
+    if (cudaMemcpy(rs.data(), ctx->base.run_start + I.run_base, rs.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(na.data(), ctx->base.na + I.run_base, na.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(nb.data(), ctx->base.nb + I.run_base, nb.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return PS_ECUDA;
+    for (uint64_t t = 1; t <= nbound && 2 * (t - 1) + 1 < cap; ++t) {
+        h_out[2 * (t - 1)] = rs[na[t]];
+        h_out[2 * (t - 1) + 1] = rs[nb[t]];
+    }
+    return PS_OK;
+}
+
+PS_API ps_status ps_get_instance_stats(ps_ctx* ctx, uint32_t q, ps_stats* stats)
+{
+    if (!ctx || !stats) return PS_EINVAL;
+    DeviceGuard g(ctx->device);
+    ps::Inst I;
+    ps_status st = read_inst(ctx, q, &I);
+    if (st != PS_OK) return st;
+    std::memset(stats, 0, sizeof(*stats));
+    stats->n = I.n;
+    stats->runs = I.runs;
+    stats->merge_cost = I.M;
+    stats->max_power = I.max_power;
+    stats->minrun = I.minrun;
+    stats->instances = 1;
+    stats->scratch_bytes = ctx->scratch_bytes;
+    return PS_OK;
+}
+
+PS_API void ps_destroy(ps_ctx* ctx)
+{
+    if (!ctx) return;
+    {
+        DeviceGuard g(ctx->device);
+        cudaStreamSynchronize(ctx->stream);
+        free_all(ctx);
+    }
+    delete ctx;
+}
+
+}  // extern "C"

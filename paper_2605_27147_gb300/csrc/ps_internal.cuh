@@ -1,0 +1,178 @@
+// Internal declarations shared by the CUDA translation units of the library.
+//
+// Pipeline of one call (single instance = batch of one):
+//   k_setup        per-instance sizes, minrun (Sec. 5), chunk / slot bases
+//   k_runs         run detection with minrun extension (ExtractRun, Sec. 2/5):
+//                  a chunked chain scan with decoupled look-back
+//   k_kappa        fixed-point run midpoints (the quantities Power compares)
+//   k_nodes        Power per boundary (Sec. 2 Theorem) and the element range
+//                  of the merge Algorithm 1 performs at that boundary
+//   k_classify     split the merge tree into on-chip tiles and HBM nodes
+//   k_depth        depth of tiles / HBM nodes (Pingpong buffer parity, Sec. 3)
+//   k_bucket       HBM nodes grouped into rounds by power, chunk prefix sums
+//   k_tiles        runs sorted and merged inside shared memory
+//   k_merge_rounds persistent cooperative kernel: all HBM merge rounds
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/powersort.h"
+
+namespace ps {
+
+constexpr int RUN_CHUNK = 4096;   // elements per run-detection chunk
+constexpr int RUN_HALO = 96;      // descent bits examined past a chunk's end
+constexpr int RUN_WORDS = (RUN_CHUNK + RUN_HALO) / 32 + 1;
+constexpr int RUN_BLOCK = 128;
+constexpr int MAP_STATES = 64;    // entry states of a chunk: minrun (<= 63) + 1
+constexpr int RUN_REC = RUN_CHUNK / 32 + 2;  // run starts one chain can put in a chunk
+constexpr uint32_t STATE_END = 255;
+
+constexpr int MERGE_E = 4096;     // outputs per HBM merge chunk
+constexpr int MERGE_BLOCK = 256;
+constexpr int MERGE_K = MERGE_E / MERGE_BLOCK;
+
+constexpr int TILE_BLOCK = 256;
+constexpr int TILE_MAX_LOG2 = 12;  // tile capacity bound of the shared-memory layout
+
+constexpr int PLAN_BLOCK = 256;
+constexpr int NPOW = 33;           // powers are 1..32 for n < 2^32
+constexpr uint32_t NONE = 0xffffffffu;
+
+// device error codes (mirrors ps_status)
+constexpr uint32_t DERR_TIMEOUT = 4;
+constexpr uint32_t DERR_INTERNAL = 5;
+
+struct Inst {
+    unsigned long long off;       // first element in the concatenated arrays
+    unsigned long long run_base;  // first slot in the run / boundary arrays
+    unsigned long long M;         // merge cost (Sec. 2 Definition)
+    uint32_t n;
+    uint32_t minrun;
+    uint32_t chunk_base;
+    uint32_t nchunks;
+    uint32_t runs;                // R, written by run detection
+    uint32_t max_power;
+};
+
+// A subtree merged on chip: runs [r0, r1) of an instance; t = its root
+// boundary (NONE for a single run).  depth = depth of the subtree root.
+struct TileItem {
+    uint32_t inst, r0, r1, t, depth, pad;
+};
+
+// A merge done through HBM (boundary t of an instance).
+struct GNode {
+    uint32_t inst, t, depth, power;
+};
+
+// HBM merge in round order: output [goff, goff + la + lb), left child
+// [goff, goff + la), right child [goff + la, ...), children in buffer
+// (depth + 1) & 1, output in buffer depth & 1 (0 = caller's arrays).
+struct GSorted {
+    unsigned long long goff;
+    uint32_t la, lb;
+    uint32_t chunk_base;   // first chunk of this node inside its round
+    uint32_t depth;
+};
+
+struct Ctr {
+    uint32_t error;
+    uint32_t err_where;
+    uint32_t chunk_ticket;
+    uint32_t total_chunks;
+    unsigned long long total_slots;
+    uint32_t n_tiles;
+    uint32_t n_gnodes;
+    uint32_t bucket_count[NPOW + 1];
+    uint32_t bucket_start[NPOW + 2];   // GSorted index where round r starts
+    uint32_t bucket_chunk[NPOW + 2];   // chunks of round r: [0, bucket_chunk[r])
+    uint32_t rounds;                   // non-empty rounds
+    uint32_t bar_count;
+    uint32_t bar_gen;
+    uint32_t max_power;
+    unsigned long long leaf_moves;
+    unsigned long long M_total;
+    unsigned long long runs_total;
+    unsigned long long n_total;
+};
+
+struct Job {
+    uint32_t* keysA;            // caller's keys (buffer 0)
+    uint32_t* permA;            // caller's perm or nullptr
+    uint32_t* keysB;            // scratch keys (buffer 1)
+    uint32_t* permB;            // scratch perm or nullptr
+    const unsigned long long* offsets;  // count + 1 entries, or nullptr
+    unsigned long long single_n;        // instance size when offsets == nullptr
+    uint32_t count;
+    uint32_t want_perm;
+    uint32_t tile_cap;          // T: largest merge-tree node merged on chip
+    uint32_t pad0;
+    Inst* inst;
+    uint32_t* chunk_status;
+    uint32_t* chunk_map;        // MAP_STATES per chunk
+    unsigned long long* chunk_incl;
+    uint32_t* run_start;
+    uint32_t* kappa;
+    uint8_t* power;
+    uint32_t* na;
+    uint32_t* nb;
+    TileItem* tiles;
+    GNode* gnodes;
+    GSorted* gsorted;
+    uint32_t* splits;
+    Ctr* ctr;
+    unsigned long long slot_cap;
+    uint32_t chunk_cap;
+    uint32_t entry_cap;         // capacity of tiles / gnodes / gsorted
+    uint32_t split_cap;
+    uint32_t pad1;
+};
+
+// ---------------------------------------------------------------- helpers
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void set_error(Ctr* c, uint32_t code, uint32_t where)
+{
+    if (atomicCAS(&c->error, 0u, code) == 0u) c->err_where = where;
+}
+
+// Upper bound of spin waits in cycles (about two seconds at 2 GHz); a wait
+// that exceeds it records DERR_TIMEOUT and gives up.
+constexpr long long SPIN_LIMIT_CYCLES = 4000000000ll;
+
+// Index of the instance whose [base, base + size) range holds x, for a
+// non-decreasing array of bases (binary search; the last of equal bases).
+template <typename F>
+__device__ __forceinline__ uint32_t find_inst(uint32_t count, unsigned long long x, F base_of)
+{
+    uint32_t lo = 0, hi = count;  // answer in [lo, hi)
+    while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (base_of(mid) <= x) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------- launchers
+cudaError_t launch_setup(const Job& J, cudaStream_t s);
+cudaError_t launch_runs(const Job& J, int grid, cudaStream_t s);
+cudaError_t launch_plan(const Job& J, int grid, cudaStream_t s);
+cudaError_t launch_tiles(const Job& J, int grid, cudaStream_t s);
+cudaError_t launch_merge_rounds(const Job& J, int grid, cudaStream_t s);
+cudaError_t launch_finish(const Job& J, cudaStream_t s);
+int merge_rounds_max_grid(int num_sms);
+int tiles_max_grid(int num_sms);
+
+}  // namespace ps

@@ -1,0 +1,100 @@
+"""GPU path vs the CPU oracle, through the C ABI (bit-exact: keys, stable
+permutation, run starts, powers, merge tree, merge cost)."""
+import numpy as np
+import pytest
+
+from checks import check_stable_sort
+from gpu_util import assert_matches_oracle, gpu_sort, to_dev, to_host
+from paper_2605_27147_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2605_27147_gb300 import binding
+
+    with binding.Context(1 << 24, want_perm=True) as c:
+        yield c
+
+
+def test_config_1_uniform_2_16(ctx, oracle_mod):
+    keys = inputs.uniform(1 << 16, 0)
+    ref = oracle_mod.powersort(keys)
+    k, p, st = gpu_sort(ctx, keys)
+    assert_matches_oracle(ctx, keys, ref, k, p, st)
+    assert st["merge_cost"] == 11 << 16 and st["runs"] == 2048
+
+
+EDGE = [0, 1, 2, 3, 31, 32, 33, 63, 64, 65, 127, 128, 129, 1000, 4095, 4096, 4097, 8191, 8193,
+        12345, 65535, 65537, 100003, 262147]
+DISTS = ["uniform", "zipf", "runs", "paper", "sorted", "reversed", "equal", "few"]
+
+
+@pytest.mark.parametrize("dist", DISTS)
+def test_edge_sizes(ctx, oracle_mod, dist):
+    for n in EDGE:
+        keys = inputs.make(dist, n, 31 + n)
+        ref = oracle_mod.powersort(keys)
+        k, p, st = gpu_sort(ctx, keys)
+        if n == 0:
+            assert k.size == 0
+            continue
+        assert_matches_oracle(ctx, keys, ref, k, p, st)
+
+
+@pytest.mark.parametrize("dist", ["uniform", "zipf", "runs"])
+def test_config_2_full_2_24(ctx, oracle_mod, dist):
+    n = 1 << 24
+    keys = inputs.make(dist, n, 1)
+    ref = oracle_mod.powersort(keys)
+    k, p, st = gpu_sort(ctx, keys)
+    assert_matches_oracle(ctx, keys, ref, k, p, st)
+
+
+def test_keys_only(ctx, oracle_mod):
+    for n in (5000, 1 << 20):
+        keys = inputs.make("few", n, 3)
+        ref = oracle_mod.powersort(keys)
+        k, p, st = gpu_sort(ctx, keys, want_perm=False)
+        assert p is None
+        assert np.array_equal(k, ref.keys)
+        assert st["merge_cost"] == ref.stats["merge_cost"]
+
+
+def test_repeated_calls_same_result(ctx, oracle_mod):
+    keys = inputs.make("paper", 300007, 9)
+    ref = oracle_mod.powersort(keys)
+    for _ in range(3):
+        k, p, st = gpu_sort(ctx, keys)
+        assert np.array_equal(k, ref.keys) and np.array_equal(p, ref.perm)
+
+
+def test_adversarial_run_lengths(ctx, oracle_mod):
+    # long natural runs of varied lengths (unbalanced trees, runs longer than a
+    # tile and than a run-detection chunk, runs just under / over minrun)
+    rng = np.random.RandomState(5)
+    for trial in range(6):
+        lens = rng.choice([1, 5, 31, 32, 33, 100, 4095, 4097, 9000, 70000], size=40)
+        keys = inputs.presort_segments(inputs.uniform(int(lens.sum()), trial), lens)
+        ref = oracle_mod.powersort(keys)
+        k, p, st = gpu_sort(ctx, keys)
+        assert_matches_oracle(ctx, keys, ref, k, p, st)
+
+
+def test_result_is_stable_sort_large(oracle_mod):
+    # full-size property check at 2^26 (the oracle-free characterisation)
+    from paper_2605_27147_gb300 import binding
+
+    n = 1 << 26
+    keys = inputs.make("few", n, 4)
+    with binding.Context(n, want_perm=True) as c:
+        dk = to_dev(keys)
+        dp = torch.empty(n, dtype=torch.int32, device="cuda")
+        st = c.run(dk, dp, stats=True)
+        check_stable_sort(keys, to_host(dk), to_host(dp))
+        assert st["n"] == n
