@@ -1,0 +1,384 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 Powersort hot path.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+Prints ONE JSON line (rank 0).  Workloads (keys are uint32, the stable
+permutation is produced):
+
+  plain_2^24   (default) one step = three single-instance sorts of n = 2^24:
+               uniform, Zipf(1.1) over 2^20 values, presorted Geometric(mean
+               2^10) runs (seed 1)
+  hbm_2^28     one step = one single-instance sort of n = 2^28 uniform (seed 2)
+
+Timing: inputs are resident in HBM before the timed region; before every
+timed sort the input is restored from a pristine copy and L2 is flushed by
+writing a 512 MiB buffer (both untimed); each sort is bracketed by CUDA
+events on the library's stream, and the per-phase kernel times come from
+events the library records between its launches.  ``e2e`` repeats the
+workload through ps_run_host (pinned host arrays; host->device copy of the
+keys, sort, device->host copy of keys and permutation inside the timed
+region).  ``cpu_baseline`` / ``--impl reference`` time the single-threaded CPU
+oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "hot-path elements/s & % HBM roofline, 1xGB300; batched vs plain; p50/p99 ms"
+UNIT = "elements/s"
+WORKLOADS = {
+    "plain_2^24": [("uniform", 1 << 24, 1), ("zipf", 1 << 24, 1), ("runs", 1 << 24, 1)],
+    "hbm_2^28": [("uniform", 1 << 28, 2)],
+}
+FLUSH_BYTES = 512 << 20
+BYTES_PER_MERGED_ELEM = 16   # key + perm entry read, key + perm entry written
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="plain_2^24", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-sample-seconds", type=float, default=20.0)
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def make_inputs(workload):
+    from paper_2605_27147_gb300 import inputs
+
+    return [(d, n, s, inputs.make(d, n, s)) for d, n, s in WORKLOADS[workload]]
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def traffic_from_profile(workload):
+    """dram bytes per launch of k_merge_rounds from the committed ncu summary,
+    if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"merge_rounds_{workload}.txt")
+    src = os.path.join(ROOT, "paper_2605_27147_gb300", "csrc", "ps_merge.cu")
+    try:
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        vals = {}
+        for line in open(path):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+        if vals.get("kernel_source_sha256_16") != digest:
+            return None
+        return float(vals["dram_bytes_per_launch_scaled"])
+    except Exception:
+        return None
+
+
+def cpu_oracle_rate(data, budget_s):
+    """Single-threaded oracle throughput on a bounded sample (elements/s)."""
+    import oracle
+
+    oracle.build()
+    done, spent, used = 0, 0.0, []
+    for d, n, s, keys in data:
+        if spent > budget_s and done:
+            break
+        t0 = time.perf_counter()
+        oracle.powersort(keys)
+        dt = time.perf_counter() - t0
+        spent += dt
+        done += n
+        used.append(f"{d} n={n}")
+    return done / spent, spent, "; ".join(used)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    data = make_inputs(args.workload)
+    if args.workload == "hbm_2^28":
+        # a bounded sample of the 2^28 workload: its first 2^24 keys per step
+        data = [(d, 1 << 24, s, k[: 1 << 24].copy()) for d, n, s, k in data]
+    import oracle
+
+    oracle.build()
+    times, elems = [], 0
+    for i in range(args.warmup + args.steps):
+        d, n, s, keys = data[i % len(data)]
+        t0 = time.perf_counter()
+        oracle.powersort(keys)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+            elems += n
+    total = sum(times)
+    value = elems / total
+    sample = (f"one oracle run (Algorithm 1, Pingpong storage, one thread) per step, cycling "
+              f"{', '.join(f'{d} n={n}' for d, n, s, k in data)}")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "note": "CPU oracle on host cores (bounded sample per step)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    from paper_2605_27147_gb300 import binding
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    data = make_inputs(args.workload)
+    max_n = max(n for _, n, _, _ in data)
+    stream = torch.cuda.current_stream(dev)
+    pristine = [torch.from_numpy(k.view(np.int32)).to(dev) for _, _, _, k in data]
+    work = torch.empty(max_n, dtype=torch.int32, device=dev)
+    perm = torch.empty(max_n, dtype=torch.int32, device=dev)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    ctx = binding.Context(max_n, want_perm=True, flags=binding.PS_FLAG_TIMING, device=local, stream=stream)
+
+    def one_sort(i, timed):
+        n = data[i][1]
+        work[:n].copy_(pristine[i])
+        flush.fill_(i)                      # write 512 MiB: L2 holds nothing of the input
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = ctx.run(work[:n], perm[:n], stats=False)
+        e1.record(stream)
+        if not timed:
+            return None
+        return e0, e1, n
+
+    for _ in range(args.warmup):
+        for i in range(len(data)):
+            one_sort(i, False)
+    ctx.sync()
+    torch.cuda.synchronize(dev)
+
+    launches_per_sort = 10
+    recs, phases = [], []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            for i in range(len(data)):
+                e0, e1, n = one_sort(i, True)
+                ph = ctx.phase_times()        # waits for this sort (events on the same stream)
+                recs.append((e0, e1, n, i))
+                phases.append(ph)
+        torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    ctx.sync()
+    sort_ms = [e0.elapsed_time(e1) for e0, e1, _, _ in recs]
+    total_ms = sum(sort_ms)
+    elems = sum(n for _, _, n, _ in recs)
+    # one stats call per distribution for the algorithmic byte counts
+    hbm = {}
+    for i in range(len(data)):
+        n = data[i][1]
+        work[:n].copy_(pristine[i])
+        st = ctx.run(work[:n], perm[:n], stats=True)
+        hbm[i] = st
+    merge_ms = sum(p["merge_rounds"] for p in phases)
+    merge_bytes = sum(BYTES_PER_MERGED_ELEM * hbm[i]["hbm_merge_elems"] for _, _, _, i in recs)
+    tiles_ms = sum(p["tiles"] for p in phases)
+    tiles_bytes = sum(12 * data[i][1] for _, _, _, i in recs)   # keys read, keys + perm written
+    runs_ms = sum(p["runs"] for p in phases)
+    phase_tot = {k: sum(p[k] for p in phases) for k in binding.PHASES}
+
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms_max = float(t.item())
+    value = elems * world / (total_ms_max / 1000.0)
+
+    # end to end through ps_run_host with pinned host arrays
+    e2e = None
+    if not args.no_e2e:
+        hctx = binding.Context(max_n, want_perm=True, flags=binding.PS_FLAG_HOST_IO, device=local, stream=stream)
+        hk = torch.empty(max_n, dtype=torch.int32, pin_memory=True)
+        hp = torch.empty(max_n, dtype=torch.int32, pin_memory=True)
+        src = [torch.from_numpy(k.view(np.int32)) for _, _, _, k in data]
+        e2e_steps = max(1, min(args.steps, 5))
+        for i in range(len(data)):   # warm-up
+            n = data[i][1]
+            hk[:n].copy_(src[i])
+            hctx.run_host(hk.data_ptr(), n, hp.data_ptr())
+        tsum, esum, bi, bo = 0.0, 0, 0, 0
+        for _ in range(e2e_steps):
+            for i in range(len(data)):
+                n = data[i][1]
+                hk[:n].copy_(src[i])
+                t0 = time.perf_counter()
+                hctx.run_host(hk.data_ptr(), n, hp.data_ptr())
+                tsum += time.perf_counter() - t0
+                esum += n
+                bi += 4 * n
+                bo += 8 * n
+        # the result of the last e2e sort must be the sorted keys
+        last_n = data[-1][1]
+        assert np.all(np.diff(hk[:last_n].numpy().view(np.uint32).astype(np.int64)) >= 0)
+        hctx.close()
+        e2e = {"value": esum * world / tsum, "unit": UNIT, "h2d_bytes_per_step": bi // e2e_steps,
+               "d2h_bytes_per_step": bo // e2e_steps, "steps": e2e_steps,
+               "api": "ps_run_host (pinned host arrays)"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        sample = data if args.workload == "plain_2^24" else [(d, 1 << 24, s, k[: 1 << 24].copy())
+                                                           for d, n, s, k in data]
+        rate, spent, used = cpu_oracle_rate(sample, args.cpu_sample_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{used} ({spent:.1f} s of one host core)"}
+
+    peak, peak_kind = peaks()
+    achieved = merge_bytes / (merge_ms / 1000.0) / 1e9
+    traffic = traffic_from_profile(args.workload)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {
+            "workload": args.workload,
+            "instances": [f"{d} n=2^{int(np.log2(n))} seed {s}" for d, n, s, _ in data],
+            "outputs": "sorted keys + stable permutation (uint32)",
+            "storage": "pingpong",
+            "l2": "flushed before every timed sort (512 MiB write)",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+        },
+        "roofline": {
+            "kernel": "k_merge_rounds (HBM merge rounds)", "bound": "hbm", "achieved": achieved,
+            "peak": peak, "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
+            "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic,
+            "algorithmic_bytes": "16 B per element per HBM merge (key + perm read and written), "
+                                 "summed over the merges of the call",
+        },
+        "kernels": {
+            "phase_ms_per_step": {k: v / args.steps for k, v in phase_tot.items()},
+            "tiles_gbs": tiles_bytes / (tiles_ms / 1000.0) / 1e9 if tiles_ms else None,
+            "runs_gbs": sum(4 * data[i][1] for *_, i in recs) / (runs_ms / 1000.0) / 1e9 if runs_ms else None,
+            "schedule_gbs": (merge_bytes + tiles_bytes + sum(4 * data[i][1] for *_, i in recs))
+                            / (total_ms / 1000.0) / 1e9,
+        },
+        "stats": {data[i][0]: {k: hbm[i][k] for k in ("runs", "merge_cost", "tiles", "global_nodes", "rounds",
+                                                      "hbm_merge_elems", "max_power")} for i in hbm},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clk.summary(),
+        "gpu_launches": launches_per_sort * len(recs),
+    }
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

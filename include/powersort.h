@@ -74,8 +74,13 @@ typedef struct ps_config {
                             sqrt(n / log2 n) rounded to a power of two, Sec. 4)      */
     uint32_t tile_log2;  /* on-chip tile capacity 2^tile_log2 in 10..12 (0: 12)      */
     uint32_t pool_pages; /* VM page-pool size in pages (0: chosen by the library)    */
-    uint32_t reserved[4];
+    uint32_t flags;      /* PS_FLAG_* below                                          */
+    uint32_t reserved[3];
 } ps_config;
+
+/* ps_config.flags */
+#define PS_FLAG_TIMING 1u  /* record CUDA events around every phase (ps_get_phase_times) */
+#define PS_FLAG_HOST_IO 2u /* allocate device arrays for ps_run_host (max_total keys + perm) */
 
 /* Per-call statistics (sums over instances for batched calls).  The paper's
  * merge cost M is the sum of the lengths of all merge inputs (Sec. 2
@@ -93,6 +98,9 @@ typedef struct ps_stats {
     uint32_t rounds;        /* HBM merge rounds executed                          */
     uint32_t minrun;        /* minrun of the (first) instance                     */
     uint32_t instances;
+    uint64_t hbm_merge_elems; /* sum of the sizes of the merges done through HBM  */
+    uint32_t launches;      /* kernels the call launched                          */
+    uint32_t pad;
 } ps_stats;
 
 typedef struct ps_ctx ps_ctx;
@@ -120,6 +128,19 @@ PS_API ps_status ps_run(ps_ctx* ctx, uint32_t* d_keys, uint32_t* d_perm, uint64_
  * each instance.  Sizes must respect max_n / max_total / max_count. */
 PS_API ps_status ps_run_batched(ps_ctx* ctx, uint32_t* d_keys, uint32_t* d_perm,
                                 const uint64_t* d_offsets, uint32_t count, ps_stats* stats);
+
+/* ps_run for host arrays: copies h_keys[0, n) to the device, sorts, and
+ * copies the sorted keys (and, if h_perm is not NULL, the permutation) back;
+ * returns after the copies have finished.  Needs PS_FLAG_HOST_IO at create
+ * time.  Pinned (page-locked) host memory gives full-speed copies. */
+PS_API ps_status ps_run_host(ps_ctx* ctx, uint32_t* h_keys, uint32_t* h_perm, uint64_t n, ps_stats* stats);
+
+/* Durations in milliseconds of the phases of the last call (needs
+ * PS_FLAG_TIMING; synchronises): [0] setup, [1] run detection, [2] powers and
+ * merge schedule, [3] on-chip tiles, [4] HBM merge rounds, [5] statistics.
+ * Measured with CUDA events recorded on the context's stream between the
+ * launches.  h_ms receives min(cap, 6) values; *count (may be NULL) gets 6. */
+PS_API ps_status ps_get_phase_times(ps_ctx* ctx, float* h_ms, uint32_t cap, uint32_t* count);
 
 /* Wait for the context's stream and report the device-side status of the
  * last call: PS_OK, or PS_ETIMEOUT / PS_EINTERNAL when a kernel gave up a

@@ -19,9 +19,12 @@ PS_MODE_PINGPONG, PS_MODE_VM = 0, 1
 
 # every symbol include/powersort.h declares
 EXPORTS = (
-    "ps_status_str", "ps_create", "ps_run", "ps_run_batched", "ps_sync", "ps_get_runs",
-    "ps_get_powers", "ps_get_nodes", "ps_get_instance_stats", "ps_destroy",
+    "ps_status_str", "ps_create", "ps_run", "ps_run_batched", "ps_run_host", "ps_sync",
+    "ps_get_phase_times", "ps_get_runs", "ps_get_powers", "ps_get_nodes", "ps_get_instance_stats",
+    "ps_destroy",
 )
+PS_FLAG_TIMING, PS_FLAG_HOST_IO = 1, 2
+PHASES = ("setup", "runs", "plan", "tiles", "merge_rounds", "finish")
 
 
 class ps_config(ctypes.Structure):
@@ -34,7 +37,8 @@ class ps_config(ctypes.Structure):
         ("page_log2", ctypes.c_uint32),
         ("tile_log2", ctypes.c_uint32),
         ("pool_pages", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint32 * 4),
+        ("flags", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32 * 3),
     ]
 
 
@@ -52,6 +56,9 @@ class ps_stats(ctypes.Structure):
         ("rounds", ctypes.c_uint32),
         ("minrun", ctypes.c_uint32),
         ("instances", ctypes.c_uint32),
+        ("hbm_merge_elems", ctypes.c_uint64),
+        ("launches", ctypes.c_uint32),
+        ("pad", ctypes.c_uint32),
     ]
 
     def as_dict(self):
@@ -93,6 +100,11 @@ def lib(build_if_missing: bool = True):
         L.ps_run.argtypes = [vp, vp, vp, ctypes.c_uint64, ctypes.POINTER(ps_stats)]
         L.ps_run_batched.restype = ctypes.c_int
         L.ps_run_batched.argtypes = [vp, vp, vp, vp, ctypes.c_uint32, ctypes.POINTER(ps_stats)]
+        L.ps_run_host.restype = ctypes.c_int
+        L.ps_run_host.argtypes = [vp, vp, vp, ctypes.c_uint64, ctypes.POINTER(ps_stats)]
+        L.ps_get_phase_times.restype = ctypes.c_int
+        L.ps_get_phase_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_uint32,
+                                         ctypes.POINTER(ctypes.c_uint32)]
         L.ps_sync.restype = ctypes.c_int
         L.ps_sync.argtypes = [vp]
         L.ps_get_runs.restype = ctypes.c_int
@@ -130,14 +142,14 @@ class Context:
 
     def __init__(self, max_n: int, *, mode: int = PS_MODE_PINGPONG, want_perm: bool = True,
                  max_total: int = 0, max_count: int = 0, tile_log2: int = 0, page_log2: int = 0,
-                 pool_pages: int = 0, device: int = 0, stream=None):
+                 pool_pages: int = 0, flags: int = 0, device: int = 0, stream=None):
         import torch
 
         self.device = device
         self.stream = stream if stream is not None else torch.cuda.current_stream(device)
         cfg = ps_config(mode=mode, want_perm=1 if want_perm else 0, max_n=max_n, max_total=max_total,
                         max_count=max_count, page_log2=page_log2, tile_log2=tile_log2,
-                        pool_pages=pool_pages)
+                        pool_pages=pool_pages, flags=flags)
         h = ctypes.c_void_p()
         _check(lib().ps_create(ctypes.byref(cfg), device, ctypes.c_void_p(self.stream.cuda_stream),
                                ctypes.byref(h)), "ps_create")
@@ -178,6 +190,19 @@ class Context:
         _check(lib().ps_run_batched(self._h, _ptr(keys), _ptr(perm), _ptr(offsets), offsets.numel() - 1,
                                     ctypes.byref(st) if st is not None else None), "ps_run_batched")
         return st.as_dict() if st is not None else None
+
+    def run_host(self, keys_ptr: int, n: int, perm_ptr: int | None = None, *, stats: bool = False):
+        """ps_run_host on raw host pointers (e.g. pinned torch tensors' data_ptr())."""
+        st = ps_stats() if stats else None
+        _check(lib().ps_run_host(self._h, keys_ptr, perm_ptr, n, ctypes.byref(st) if st is not None else None),
+               "ps_run_host")
+        return st.as_dict() if st is not None else None
+
+    def phase_times(self) -> dict:
+        """Milliseconds per phase of the last call (needs PS_FLAG_TIMING)."""
+        buf = (ctypes.c_float * len(PHASES))()
+        _check(lib().ps_get_phase_times(self._h, buf, len(PHASES), None), "ps_get_phase_times")
+        return {name: float(buf[i]) for i, name in enumerate(PHASES)}
 
     def sync(self):
         _check(lib().ps_sync(self._h), "ps_sync")

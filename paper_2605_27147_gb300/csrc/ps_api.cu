@@ -22,11 +22,17 @@ struct ps_ctx {
     int last_valid;
     size_t scratch_bytes;
     std::vector<void*> allocs;
+    bool timing;
+    cudaEvent_t ev[7];          // phase boundaries of the last call (PS_FLAG_TIMING)
+    uint32_t* io_keys;          // device arrays of ps_run_host (PS_FLAG_HOST_IO)
+    uint32_t* io_perm;
 };
 
 namespace {
 
 constexpr unsigned long long LIMIT_N = 0xffffffffull;  // instance sizes and totals < 2^32
+constexpr uint32_t LAUNCHES_PER_CALL = 10;  // setup, runs, 5 planning kernels, tiles, rounds, finish
+constexpr uint32_t NPHASES = 6;
 
 struct DeviceGuard {
     int prev = -1;
@@ -59,6 +65,10 @@ ps_status dev_alloc(ps_ctx* c, T** p, size_t count)
 
 void free_all(ps_ctx* c)
 {
+    if (c->timing)
+        for (cudaEvent_t& e : c->ev)
+            if (e) cudaEventDestroy(e);
+    c->timing = false;
     for (void* p : c->allocs) cudaFree(p);
     c->allocs.clear();
     if (c->h_ctr) cudaFreeHost(c->h_ctr);
@@ -77,12 +87,14 @@ ps_status from_device_error(uint32_t e)
 ps_status enqueue(ps_ctx* c, const ps::Job& J)
 {
     cudaStream_t s = c->stream;
-    if (ps::launch_setup(J, s) != cudaSuccess) return PS_ECUDA;
-    if (ps::launch_runs(J, c->grid_runs, s) != cudaSuccess) return PS_ECUDA;
-    if (ps::launch_plan(J, c->grid_plan, s) != cudaSuccess) return PS_ECUDA;
-    if (ps::launch_tiles(J, c->grid_tiles, s) != cudaSuccess) return PS_ECUDA;
-    if (ps::launch_merge_rounds(J, c->grid_merge, s) != cudaSuccess) return PS_ECUDA;
-    if (ps::launch_finish(J, s) != cudaSuccess) return PS_ECUDA;
+    auto mark = [&](int i) { return !c->timing || cudaEventRecord(c->ev[i], s) == cudaSuccess; };
+    if (!mark(0)) return PS_ECUDA;
+    if (ps::launch_setup(J, s) != cudaSuccess || !mark(1)) return PS_ECUDA;
+    if (ps::launch_runs(J, c->grid_runs, s) != cudaSuccess || !mark(2)) return PS_ECUDA;
+    if (ps::launch_plan(J, c->grid_plan, s) != cudaSuccess || !mark(3)) return PS_ECUDA;
+    if (ps::launch_tiles(J, c->grid_tiles, s) != cudaSuccess || !mark(4)) return PS_ECUDA;
+    if (ps::launch_merge_rounds(J, c->grid_merge, s) != cudaSuccess || !mark(5)) return PS_ECUDA;
+    if (ps::launch_finish(J, s) != cudaSuccess || !mark(6)) return PS_ECUDA;
     if (cudaMemcpyAsync(c->h_ctr, J.ctr, sizeof(ps::Ctr), cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return PS_ECUDA;
     return PS_OK;
@@ -112,6 +124,8 @@ void fill_stats(const ps_ctx* c, ps_stats* st, uint32_t count)
     st->max_power = h->max_power;
     st->rounds = h->rounds;
     st->instances = count;
+    st->hbm_merge_elems = h->hbm_elems;
+    st->launches = LAUNCHES_PER_CALL;
 }
 
 ps_status run_common(ps_ctx* c, uint32_t* d_keys, uint32_t* d_perm, const uint64_t* d_offsets,
@@ -245,6 +259,15 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
     if (st == PS_OK) st = dev_alloc(c, &J.gsorted, entry_cap);
     if (st == PS_OK) st = dev_alloc(c, &J.splits, split_cap);
     if (st == PS_OK) st = dev_alloc(c, &J.ctr, 1);
+    if (st == PS_OK && (cfg->flags & PS_FLAG_HOST_IO)) {
+        st = dev_alloc(c, &c->io_keys, max_total);
+        if (st == PS_OK && cfg->want_perm) st = dev_alloc(c, &c->io_perm, max_total);
+    }
+    if (st == PS_OK && (cfg->flags & PS_FLAG_TIMING)) {
+        c->timing = true;
+        for (cudaEvent_t& e : c->ev)
+            if (cudaEventCreate(&e) != cudaSuccess) st = PS_ECUDA;
+    }
     if (st == PS_OK && cudaMallocHost(&c->h_ctr, sizeof(ps::Ctr)) != cudaSuccess) st = PS_ENOMEM;
     if (st == PS_OK && cudaMallocHost(&c->h_inst, sizeof(ps::Inst)) != cudaSuccess) st = PS_ENOMEM;
     if (st == PS_OK && (cudaMemset(J.chunk_status, 0, chunk_cap * sizeof(uint32_t)) != cudaSuccess ||
@@ -297,6 +320,47 @@ PS_API ps_status ps_run_batched(ps_ctx* ctx, uint32_t* d_keys, uint32_t* d_perm,
     }
     if (off[count] > ctx->max_total) return PS_EINVAL;
     return run_common(ctx, d_keys, d_perm, d_offsets, 0, count, stats);
+}
+
+PS_API ps_status ps_run_host(ps_ctx* ctx, uint32_t* h_keys, uint32_t* h_perm, uint64_t n, ps_stats* stats)
+{
+    if (!ctx) return PS_EINVAL;
+    if (!ctx->io_keys) return PS_EINVAL;
+    if (n > ctx->cfg.max_n) return PS_EINVAL;
+    if (n > 0 && !h_keys) return PS_EINVAL;
+    if (h_perm && !ctx->cfg.want_perm) return PS_EINVAL;
+    if (n == 0) {
+        if (stats) std::memset(stats, 0, sizeof(*stats));
+        return PS_OK;
+    }
+    DeviceGuard g(ctx->device);
+    const size_t bytes = n * sizeof(uint32_t);
+    if (cudaMemcpyAsync(ctx->io_keys, h_keys, bytes, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
+        return PS_ECUDA;
+    ps_stats local;
+    ps_status st = run_common(ctx, ctx->io_keys, h_perm ? ctx->io_perm : nullptr, nullptr, n, 1, nullptr);
+    if (st != PS_OK) return st;
+    if (cudaMemcpyAsync(h_keys, ctx->io_keys, bytes, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
+        return PS_ECUDA;
+    if (h_perm && cudaMemcpyAsync(h_perm, ctx->io_perm, bytes, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
+        return PS_ECUDA;
+    st = sync_and_check(ctx);
+    if (st != PS_OK) return st;
+    fill_stats(ctx, &local, 1);
+    if (stats) *stats = local;
+    return PS_OK;
+}
+
+PS_API ps_status ps_get_phase_times(ps_ctx* ctx, float* h_ms, uint32_t cap, uint32_t* count)
+{
+    if (!ctx || (!h_ms && cap)) return PS_EINVAL;
+    if (!ctx->timing || !ctx->last_valid) return PS_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (cudaEventSynchronize(ctx->ev[NPHASES]) != cudaSuccess) return PS_ECUDA;
+    if (count) *count = NPHASES;
+    for (uint32_t i = 0; i < NPHASES && i < cap; ++i)
+        if (cudaEventElapsedTime(&h_ms[i], ctx->ev[i], ctx->ev[i + 1]) != cudaSuccess) return PS_ECUDA;
+    return PS_OK;
 }
 
 PS_API ps_status ps_sync(ps_ctx* ctx)

@@ -96,6 +96,7 @@ struct Ctr {
     unsigned long long M_total;
     unsigned long long runs_total;
     unsigned long long n_total;
+    unsigned long long hbm_elems;      // sum of the sizes of the HBM merges
 };
 
 struct Job {

@@ -296,6 +296,7 @@ __global__ void __launch_bounds__(1024) k_bucket(Job J)
 {
     __shared__ uint32_t cursor[NPOW + 1];
     __shared__ uint32_t warp_sums[32];
+    __shared__ unsigned long long s_hbm;
     Ctr* C = J.ctr;
     if (*(volatile uint32_t*)&C->error) return;
     const uint32_t ng = min(C->n_gnodes, J.entry_cap);
@@ -308,9 +309,11 @@ __global__ void __launch_bounds__(1024) k_bucket(Job J)
             rounds += C->bucket_count[r] ? 1u : 0u;
         }
         C->bucket_start[NPOW] = acc;
+        s_hbm = 0;
         C->rounds = rounds;
     }
     __syncthreads();
+    unsigned long long hbm = 0;
     for (uint32_t e = threadIdx.x; e < ng; e += blockDim.x) {
         const GNode gn = J.gnodes[e];
         const Inst& I = J.inst[gn.inst];
@@ -326,7 +329,9 @@ __global__ void __launch_bounds__(1024) k_bucket(Job J)
         o.chunk_base = (hi - lo + MERGE_E - 1) / MERGE_E;   // chunk count for now
         o.depth = gn.depth;
         J.gsorted[at] = o;
+        hbm += hi - lo;
     }
+    atomicAdd(&s_hbm, hbm);
     __syncthreads();
     // exclusive scan of the chunk counts: each thread owns a contiguous segment
     const uint32_t per = (ng + blockDim.x - 1) / blockDim.x;
@@ -361,6 +366,7 @@ __global__ void __launch_bounds__(1024) k_bucket(Job J)
     }
     __syncthreads();
     if (threadIdx.x == 0) {
+        C->hbm_elems = s_hbm;
         const uint32_t total_chunks = warp_sums[31];
         for (int r = 0; r <= NPOW; ++r) {
             const uint32_t e = C->bucket_start[r];

@@ -95,6 +95,7 @@ __global__ void __launch_bounds__(1024) k_setup(Job J)
         C->M_total = 0;
         C->runs_total = 0;
         C->n_total = 0;
+        C->hbm_elems = 0;
     }
     for (int r = threadIdx.x; r < NPOW + 2; r += blockDim.x) {
         if (r < NPOW + 1) C->bucket_count[r] = 0;
