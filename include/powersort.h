@@ -170,6 +170,29 @@ PS_API ps_status ps_get_instance_stats(ps_ctx* ctx, uint32_t q, ps_stats* stats)
 /* Release every device buffer of the context.  NULL is a no-op. */
 PS_API void ps_destroy(ps_ctx* ctx);
 
+/* ---------------------------------------------------------------------------
+ * Sorting without any device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc -- code that
+ * owns a fixed, pre-sized budget of device memory which a foreign
+ * allocation would overrun, and latency-sensitive loops in which
+ * cudaMalloc / cudaFree would synchronise the device.
+ *
+ * ps_run_noalloc sorts d_keys[0, n) in place, stably, and writes the stable
+ * permutation to d_perm (NULL: keys only) -- the same result as ps_run --
+ * using one CTA on device `device`, enqueued on `cuda_stream` (a
+ * cudaStream_t; NULL = legacy default stream).  It needs no context and
+ * allocates nothing: its scratch is a file-scope static device array of
+ * about 2 MiB that every GPU loading the library holds until the process
+ * exits.  n must be <= PS_NOALLOC_MAX_N, else PS_EINVAL and nothing is
+ * enqueued.  The first call on a device does a one-time set-up (it looks up
+ * the scratch array's device address); make that first call before any
+ * stream capture.  Every call shares the one scratch array: calls whose work
+ * overlaps on the GPU race and must be serialised by the caller.  The call
+ * returns once the kernel is enqueued. */
+#define PS_NOALLOC_MAX_N 262144u
+PS_API ps_status ps_run_noalloc(uint32_t* d_keys, uint32_t* d_perm, uint64_t n, int device,
+                                void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,8 +21,9 @@ PS_MODE_PINGPONG, PS_MODE_VM = 0, 1
 EXPORTS = (
     "ps_status_str", "ps_create", "ps_run", "ps_run_batched", "ps_run_host", "ps_sync",
     "ps_get_phase_times", "ps_get_runs", "ps_get_powers", "ps_get_nodes", "ps_get_instance_stats",
-    "ps_destroy",
+    "ps_destroy", "ps_run_noalloc",
 )
+PS_NOALLOC_MAX_N = 262144
 PS_FLAG_TIMING, PS_FLAG_HOST_IO = 1, 2
 PHASES = ("setup", "runs", "plan", "tiles", "merge_rounds", "finish")
 
@@ -117,6 +118,8 @@ def lib(build_if_missing: bool = True):
         L.ps_get_instance_stats.argtypes = [vp, ctypes.c_uint32, ctypes.POINTER(ps_stats)]
         L.ps_destroy.restype = None
         L.ps_destroy.argtypes = [vp]
+        L.ps_run_noalloc.restype = ctypes.c_int
+        L.ps_run_noalloc.argtypes = [vp, vp, ctypes.c_uint64, ctypes.c_int, vp]
         _lib = L
     return _lib
 
