@@ -29,9 +29,9 @@ constexpr int MAP_STATES = 64;    // entry states of a chunk: minrun (<= 63) + 1
 constexpr int RUN_REC = RUN_CHUNK / 32 + 2;  // run starts one chain can put in a chunk
 constexpr uint32_t STATE_END = 255;
 
-constexpr int MERGE_E = 4096;     // outputs per HBM merge chunk
 constexpr int MERGE_BLOCK = 256;
-constexpr int MERGE_K = MERGE_E / MERGE_BLOCK;
+constexpr int MERGE_K = 9;        // outputs per thread (odd: conflict-free shared-memory strides)
+constexpr int MERGE_E = MERGE_BLOCK * MERGE_K;   // outputs per HBM merge chunk
 
 constexpr int TILE_BLOCK = 256;
 constexpr int TILE_MAX_LOG2 = 12;  // tile capacity bound of the shared-memory layout
@@ -122,7 +122,8 @@ struct Job {
     TileItem* tiles;
     GNode* gnodes;
     GSorted* gsorted;
-    uint32_t* splits;
+    uint32_t* splits;           // per chunk of the current round: left-child elements before it
+    uint32_t* chunk_node;       // per chunk of the current round: its GSorted index
     Ctr* ctr;
     unsigned long long slot_cap;
     uint32_t chunk_cap;
@@ -147,6 +148,86 @@ __device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v)
 __device__ __forceinline__ void set_error(Ctr* c, uint32_t code, uint32_t where)
 {
     if (atomicCAS(&c->error, 0u, code) == 0u) c->err_where = where;
+}
+
+// ---- TMA (1-D bulk copies) and mbarrier helpers (sm_90+ PTX) -------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// one arrival that also announces `bytes` of transaction traffic
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// global -> shared bulk copy; completes `bytes` on the mbarrier.  Both
+// addresses 16-byte aligned, bytes a multiple of 16 (checked by callers).
+__device__ __forceinline__ void tma_load_1d(void* dst_smem, const void* src_gmem, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst_smem)), "l"(src_gmem), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// shared -> global bulk copy in the current bulk group (same alignment rules)
+__device__ __forceinline__ void tma_store_1d(void* dst_gmem, const void* src_smem, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst_gmem),
+                 "r"(smem_addr(src_smem)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit()
+{
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+// the shared-memory sources of every committed bulk store have been read
+__device__ __forceinline__ void bulk_wait_read_all()
+{
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
+// every committed bulk store has completed
+__device__ __forceinline__ void bulk_wait_all()
+{
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_global()
+{
+    asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
 // Upper bound of spin waits in cycles (about two seconds at 2 GHz); a wait

@@ -5,12 +5,21 @@
 //
 // Rounds go from the largest power to the smallest; all merges of one round
 // are disjoint and their children are finished.  Every merge is cut into
-// chunks of MERGE_E outputs.  Phase A finds, for every chunk start, how many
-// of the first d outputs come from the left child (merge-path split: the
-// largest i with A[i-1] <= B[d-i], ties to the left).  Phase B gives each
-// chunk to a CTA, which stages the chunk's two input slices in shared memory,
-// merges them (each thread K outputs, again split by merge path) and writes
-// keys and permutation entries back with coalesced stores.
+// chunks of MERGE_E outputs.
+//
+// Phase A: for every chunk, its merge (GSorted index) and how many of the
+// merge's first d outputs come from the left child (merge-path split: the
+// largest i with A[i-1] <= B[d-i], ties to the left).
+//
+// Phase B: each CTA walks its chunks with a two-stage TMA pipeline.  While
+// chunk i is merged, the 1-D bulk copies (cp.async.bulk) of chunk i+1's two
+// input slices (keys and permutation) are in flight into the other shared-
+// memory stage; elements outside the 16-byte-aligned interior of a slice (at
+// most three at each end) are fetched with ordinary loads into registers and
+// stored into the stage after the merge.  Each thread produces MERGE_K
+// consecutive outputs (merge-path split inside shared memory, then a serial
+// merge); the chunk's output leaves through a bulk store (plus ordinary stores
+// for its unaligned ends).
 //
 // One persistent cooperative launch runs every round; a grid barrier (bounded
 // spin, error flag on timeout) separates the phases.  Cooperative launch
@@ -20,6 +29,9 @@
 namespace ps {
 
 namespace {
+
+constexpr int SLOT = MERGE_E + 16;   // a staged array: up to 3 + 3 + 3 shift slots
+constexpr int EDGE_SLOTS = 8;        // unaligned elements of one slice (<= 7)
 
 __device__ bool grid_barrier(Ctr* C)
 {
@@ -74,17 +86,210 @@ __device__ __forceinline__ uint32_t merge_path(const uint32_t* A, uint32_t la, c
     return lo;
 }
 
+// A contiguous slice of one array: its 16-byte-aligned interior moves by
+// bulk copy, the rest (head / tail, at most 3 elements each, or the whole
+// slice when it has no aligned 16-byte block) by ordinary accesses.
+struct Slice {
+    uint32_t head;    // elements before the aligned interior (or the whole slice)
+    uint32_t nint;    // elements of the aligned interior (multiple of 4)
+    uint32_t len;
+};
+
+__device__ __forceinline__ Slice slice_of(const uint32_t* g, uint32_t len)
+{
+    Slice s;
+    s.len = len;
+    const uint32_t mis = (uint32_t)(((uintptr_t)g >> 2) & 3u);     // elements past a 16-byte boundary
+    const uint32_t head = (4u - mis) & 3u;
+    if (len > head) {
+        s.head = head;
+        s.nint = (len - head) & ~3u;
+    } else {
+        s.head = len;
+        s.nint = 0;
+    }
+    if (s.nint == 0) s.head = len;
+    return s;
+}
+
+// index inside the slice of unaligned element number j (j < EDGE_SLOTS), or NONE
+__device__ __forceinline__ uint32_t edge_index(const Slice& s, uint32_t j)
+{
+    if (j < s.head) return j;
+    const uint32_t i = s.head + s.nint + (j - s.head);
+    return i < s.len ? i : NONE;
+}
+
+// shared-memory slot of a slice start: congruent to its global address mod 16
+__device__ __forceinline__ uint32_t shift_of(const uint32_t* g)
+{
+    return (uint32_t)(((uintptr_t)g >> 2) & 3u);
+}
+
+struct Stage {
+    const uint32_t* gk[2];   // slice starts in global memory: [0] left, [1] right (keys)
+    const uint32_t* gp[2];   // same for the permutation (nullptr: keys only)
+    uint32_t sk[2], sp[2];   // slice starts inside the staged arrays
+    Slice slk[2], slp[2];
+    uint32_t na, nb;
+    uint32_t* ok;            // output chunk start (keys, permutation)
+    uint32_t* op;
+    uint32_t sok, sop;       // output start inside the output staging arrays
+    uint32_t cnt;
+};
+
+struct __align__(16) MergeSmem {
+    uint32_t in_k[2][SLOT];
+    uint32_t in_p[2][SLOT];
+    uint32_t out_k[SLOT];
+    uint32_t out_p[SLOT];
+    uint64_t bar[2];
+    Stage st[2];
+};
+
+// Describe chunk q of the current round (reads the phase-A tables).
+__device__ void describe(const Job& J, uint32_t q, uint32_t c0, uint32_t nch, Stage& S)
+{
+    const uint32_t e = J.chunk_node[q];
+    const GSorted g = J.gsorted[e];
+    const uint32_t total = g.la + g.lb;
+    const uint32_t d0 = (c0 + q - g.chunk_base) * MERGE_E;
+    const uint32_t d1 = min(d0 + (uint32_t)MERGE_E, total);
+    const uint32_t a0 = J.splits[q];
+    const uint32_t a1 = (d1 == total || q + 1 >= nch) ? g.la : J.splits[q + 1];
+    const uint32_t b0 = d0 - a0, b1 = d1 - a1;
+    const bool src_b = ((g.depth + 1) & 1u) != 0, dst_b = (g.depth & 1u) != 0;
+    const uint32_t* ks = (src_b ? J.keysB : J.keysA) + g.goff;
+    const uint32_t* ps = J.want_perm ? (src_b ? J.permB : J.permA) + g.goff : nullptr;
+    S.na = a1 - a0;
+    S.nb = b1 - b0;
+    S.cnt = d1 - d0;
+    S.gk[0] = ks + a0;
+    S.gk[1] = ks + g.la + b0;
+    S.gp[0] = ps ? ps + a0 : nullptr;
+    S.gp[1] = ps ? ps + g.la + b0 : nullptr;
+    S.sk[0] = shift_of(S.gk[0]);
+    S.sk[1] = ((S.sk[0] + S.na + 3u) & ~3u) + shift_of(S.gk[1]);
+    S.slk[0] = slice_of(S.gk[0], S.na);
+    S.slk[1] = slice_of(S.gk[1], S.nb);
+    S.sp[0] = S.sp[1] = 0;
+    if (ps) {
+        S.sp[0] = shift_of(S.gp[0]);
+        S.sp[1] = ((S.sp[0] + S.na + 3u) & ~3u) + shift_of(S.gp[1]);
+        S.slp[0] = slice_of(S.gp[0], S.na);
+        S.slp[1] = slice_of(S.gp[1], S.nb);
+    }
+    S.ok = (dst_b ? J.keysB : J.keysA) + g.goff + d0;
+    S.op = J.want_perm ? (dst_b ? J.permB : J.permA) + g.goff + d0 : nullptr;
+    S.sok = shift_of(S.ok);
+    S.sop = S.op ? shift_of(S.op) : 0u;
+}
+
+__device__ __forceinline__ bool aligned16(const void* p)
+{
+    return (((uintptr_t)p) & 15u) == 0;
+}
+
+// Thread 0: start the bulk copies of a described chunk into stage s.
+__device__ void issue_loads(MergeSmem& sm, int s, Ctr* C)
+{
+    const Stage& S = sm.st[s];
+    uint32_t bytes = 0;
+    const void* src[4];
+    void* dst[4];
+    uint32_t sz[4];
+    int k = 0;
+    for (int side = 0; side < 2; ++side) {
+        const Slice& a = S.slk[side];
+        if (a.nint) {
+            src[k] = S.gk[side] + a.head;
+            dst[k] = &sm.in_k[s][S.sk[side] + a.head];
+            sz[k] = a.nint * 4u;
+            ++k;
+        }
+        if (S.gp[side]) {
+            const Slice& b = S.slp[side];
+            if (b.nint) {
+                src[k] = S.gp[side] + b.head;
+                dst[k] = &sm.in_p[s][S.sp[side] + b.head];
+                sz[k] = b.nint * 4u;
+                ++k;
+            }
+        }
+    }
+    bool ok = true;
+    for (int i = 0; i < k; ++i) {
+        ok = ok && aligned16(src[i]) && aligned16(dst[i]) && (sz[i] & 15u) == 0;
+        bytes += sz[i];
+    }
+    if (!ok) {                       // never expected: report, copy nothing
+        set_error(C, DERR_INTERNAL, 41);
+        k = 0;
+        bytes = 0;
+    }
+    fence_proxy_async_smem();        // generic reads of this stage come before the async writes
+    mbar_arrive_expect_tx(&sm.bar[s], bytes);
+    for (int i = 0; i < k; ++i) tma_load_1d(dst[i], src[i], sz[i], &sm.bar[s]);
+}
+
+// Edge elements of a described chunk: lane l of warp 0 owns slice l / 8
+// (0: left keys, 1: right keys, 2: left perm, 3: right perm), slot l % 8.
+struct EdgeReg {
+    uint32_t val;
+    uint32_t slot;   // destination in the staged array, NONE when idle
+};
+
+__device__ __forceinline__ EdgeReg load_edge(const Stage& S, int lane)
+{
+    EdgeReg r{0u, NONE};
+    const int which = lane >> 3, j = lane & 7;
+    const int side = which & 1;
+    const bool is_perm = which >= 2;
+    if (is_perm && !S.gp[side]) return r;
+    const Slice& sl = is_perm ? S.slp[side] : S.slk[side];
+    const uint32_t i = edge_index(sl, (uint32_t)j);
+    if (i == NONE) return r;
+    r.val = is_perm ? S.gp[side][i] : S.gk[side][i];
+    r.slot = (is_perm ? S.sp[side] : S.sk[side]) + i;
+    return r;
+}
+
+__device__ __forceinline__ void store_edge(MergeSmem& sm, int s, int lane, const EdgeReg& r)
+{
+    if (r.slot == NONE) return;
+    if ((lane >> 3) >= 2) sm.in_p[s][r.slot] = r.val;
+    else sm.in_k[s][r.slot] = r.val;
+}
+
+__device__ bool wait_stage(MergeSmem& sm, int s, uint32_t parity, Ctr* C)
+{
+    if (mbar_try_wait(&sm.bar[s], parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(&sm.bar[s], parity)) {
+        if (clock64() - t0 > SPIN_LIMIT_CYCLES) {
+            set_error(C, DERR_TIMEOUT, 42);
+            return false;
+        }
+    }
+    return true;
+}
+
 }  // namespace
 
 __global__ void __launch_bounds__(MERGE_BLOCK) k_merge_rounds(Job J)
 {
-    __shared__ uint32_t sk[MERGE_E];
-    __shared__ uint32_t sp[MERGE_E];
-    __shared__ GSorted s_node;
-    __shared__ uint32_t s_e;
+    extern __shared__ __align__(16) unsigned char merge_raw[];
+    MergeSmem& sm = *reinterpret_cast<MergeSmem*>(merge_raw);
     Ctr* C = J.ctr;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool perm = J.want_perm != 0;
+    if (tid == 0) {
+        mbar_init(&sm.bar[0], 1);
+        mbar_init(&sm.bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t parity[2] = {0u, 0u};
 
     for (int r = 0; r < NPOW; ++r) {
         if (*(volatile uint32_t*)&C->error) return;
@@ -93,93 +298,130 @@ __global__ void __launch_bounds__(MERGE_BLOCK) k_merge_rounds(Job J)
         const uint32_t c0 = C->bucket_chunk[r], c1 = C->bucket_chunk[r + 1];
         const uint32_t nch = c1 - c0;
 
-        // phase A: merge-path split of every chunk start
+        // phase A: the merge and the merge-path split of every chunk start
         for (uint32_t q = blockIdx.x * blockDim.x + tid; q < nch; q += gridDim.x * blockDim.x) {
             const uint32_t cid = c0 + q;
-            const GSorted g = J.gsorted[node_of_chunk(J.gsorted, e0, e1, cid)];
+            const uint32_t e = node_of_chunk(J.gsorted, e0, e1, cid);
+            const GSorted g = J.gsorted[e];
             const uint32_t d = (cid - g.chunk_base) * MERGE_E;
             const uint32_t* src = ((g.depth + 1) & 1u) ? J.keysB : J.keysA;
             const uint32_t* A = src + g.goff;
             J.splits[q] = merge_path(A, g.la, A + g.la, g.lb, d);
+            J.chunk_node[q] = e;
         }
         if (!grid_barrier(C)) return;
+        if (tid == 0) fence_proxy_async_global();   // earlier generic writes before async reads
 
-        // phase B: one chunk per CTA iteration
-        for (uint32_t q = blockIdx.x; q < nch; q += gridDim.x) {
-            const uint32_t cid = c0 + q;
+        // phase B: this CTA's chunks, two stages deep
+        uint32_t q = blockIdx.x;
+        if (q < nch) {
             if (tid == 0) {
-                s_e = node_of_chunk(J.gsorted, e0, e1, cid);
-                s_node = J.gsorted[s_e];
+                describe(J, q, c0, nch, sm.st[0]);
+                issue_loads(sm, 0, C);
             }
             __syncthreads();
-            const GSorted g = s_node;
-            const uint32_t total = g.la + g.lb;
-            const uint32_t d0 = (cid - g.chunk_base) * MERGE_E;
-            const uint32_t d1 = min(d0 + (uint32_t)MERGE_E, total);
-            const uint32_t a0 = J.splits[q];
-            const uint32_t a1 = d1 == total ? g.la : J.splits[q + 1];
-            const uint32_t b0 = d0 - a0, b1 = d1 - a1;
-            const uint32_t na = a1 - a0, nb = b1 - b0, cnt = na + nb;
-            const bool src_b = ((g.depth + 1) & 1u) != 0;
-            const uint32_t* ksrc = (src_b ? J.keysB : J.keysA) + g.goff;
-            const uint32_t* psrc = perm ? (src_b ? J.permB : J.permA) + g.goff : nullptr;
-            uint32_t* kdst = ((g.depth & 1u) ? J.keysB : J.keysA) + g.goff + d0;
-            uint32_t* pdst = perm ? ((g.depth & 1u) ? J.permB : J.permA) + g.goff + d0 : nullptr;
-
-            // stage: left slice then right slice
-#pragma unroll
-            for (int j = 0; j < MERGE_K; ++j) {
-                const uint32_t i = tid + j * MERGE_BLOCK;
-                if (i < cnt) {
-                    const uint32_t gi = i < na ? a0 + i : g.la + b0 + (i - na);
-                    sk[i] = ksrc[gi];
-                    if (perm) sp[i] = psrc[gi];
+            if (warp == 0) store_edge(sm, 0, lane, load_edge(sm.st[0], lane));
+            // (the __syncthreads at the top of the loop orders these stores)
+        }
+        int s = 0;
+        for (; q < nch; q += gridDim.x, s ^= 1) {
+            const uint32_t qn = q + gridDim.x;
+            __syncthreads();
+            EdgeReg nxt{0u, NONE};
+            if (qn < nch) {                          // prefetch the next chunk
+                if (tid == 0) {
+                    describe(J, qn, c0, nch, sm.st[s ^ 1]);
+                    issue_loads(sm, s ^ 1, C);
                 }
+                __syncwarp();
+                if (warp == 0) nxt = load_edge(sm.st[s ^ 1], lane);
             }
-            __syncthreads();
+            if (!wait_stage(sm, s, parity[s], C)) return;
+            parity[s] ^= 1u;
 
-            // each thread: MERGE_K consecutive outputs
+            const Stage& S = sm.st[s];
+            const uint32_t na = S.na, nb = S.nb, cnt = S.cnt;
+            const uint32_t* Ak = &sm.in_k[s][S.sk[0]];
+            const uint32_t* Bk = &sm.in_k[s][S.sk[1]];
+            const uint32_t* Ap = &sm.in_p[s][S.sp[0]];
+            const uint32_t* Bp = &sm.in_p[s][S.sp[1]];
             uint32_t ok[MERGE_K], op[MERGE_K];
             const uint32_t x0 = tid * MERGE_K;
             if (x0 < cnt) {
                 uint32_t lo = x0 > nb ? x0 - nb : 0u, hi = min(x0, na);
                 while (lo < hi) {
                     const uint32_t mid = (lo + hi) >> 1;
-                    if (sk[mid] <= sk[na + x0 - 1 - mid]) lo = mid + 1; else hi = mid;
+                    if (Ak[mid] <= Bk[x0 - 1 - mid]) lo = mid + 1; else hi = mid;
                 }
-                uint32_t ia = lo, ib = na + (x0 - lo);
-                const uint32_t bend = cnt;
+                uint32_t ia = lo, ib = x0 - lo;
+                uint32_t va = ia < na ? Ak[ia] : 0u, vb = ib < nb ? Bk[ib] : 0u;
 #pragma unroll
                 for (int j = 0; j < MERGE_K; ++j) {
                     if (x0 + j < cnt) {
-                        const bool take_a = ia < na && (ib >= bend || sk[ia] <= sk[ib]);
-                        const uint32_t src = take_a ? ia : ib;
-                        ok[j] = sk[src];
-                        op[j] = perm ? sp[src] : 0u;
-                        if (take_a) ++ia; else ++ib;
+                        const bool take_a = ia < na && (ib >= nb || va <= vb);
+                        if (take_a) {
+                            ok[j] = va;
+                            if (perm) op[j] = Ap[ia];
+                            ++ia;
+                            va = ia < na ? Ak[ia] : 0u;
+                        } else {
+                            ok[j] = vb;
+                            if (perm) op[j] = Bp[ib];
+                            ++ib;
+                            vb = ib < nb ? Bk[ib] : 0u;
+                        }
                     }
                 }
             }
+            if (tid == 0) bulk_wait_read_all();    // the previous chunk's output has left shared memory
             __syncthreads();
             if (x0 < cnt) {
 #pragma unroll
                 for (int j = 0; j < MERGE_K; ++j) {
                     if (x0 + j < cnt) {
-                        sk[x0 + j] = ok[j];
-                        if (perm) sp[x0 + j] = op[j];
+                        sm.out_k[S.sok + x0 + j] = ok[j];
+                        if (perm) sm.out_p[S.sop + x0 + j] = op[j];
                     }
                 }
             }
+            fence_proxy_async_smem();
+            if (warp == 0) store_edge(sm, s ^ 1, lane, nxt);
             __syncthreads();
-#pragma unroll
-            for (int j = 0; j < MERGE_K; ++j) {
-                const uint32_t i = tid + j * MERGE_BLOCK;
-                if (i < cnt) {
-                    kdst[i] = sk[i];
-                    if (perm) pdst[i] = sp[i];
+            // output: aligned interior by bulk store, the ends by ordinary stores
+            const Slice ok_sl = slice_of(S.ok, cnt);
+            const Slice op_sl = perm ? slice_of(S.op, cnt) : Slice{0u, 0u, 0u};
+            if (tid == 0) {
+                bool good = true;
+                if (ok_sl.nint) {
+                    void* g = S.ok + ok_sl.head;
+                    const void* l = &sm.out_k[S.sok + ok_sl.head];
+                    good = good && aligned16(g) && aligned16(l);
+                    if (good) tma_store_1d(g, l, ok_sl.nint * 4u);
+                }
+                if (perm && op_sl.nint) {
+                    void* g = S.op + op_sl.head;
+                    const void* l = &sm.out_p[S.sop + op_sl.head];
+                    const bool g2 = aligned16(g) && aligned16(l);
+                    if (g2) tma_store_1d(g, l, op_sl.nint * 4u);
+                    good = good && g2;
+                }
+                if (!good) set_error(C, DERR_INTERNAL, 43);
+                bulk_commit();
+            }
+            if (warp == 1 && (lane & 15) < EDGE_SLOTS) {   // lanes 0-7: keys, 16-23: permutation
+                const bool is_perm = lane >= 16;
+                if (!is_perm || perm) {
+                    const uint32_t i = edge_index(is_perm ? op_sl : ok_sl, (uint32_t)(lane & 15));
+                    if (i != NONE) {
+                        if (is_perm) S.op[i] = sm.out_p[S.sop + i];
+                        else S.ok[i] = sm.out_k[S.sok + i];
+                    }
                 }
             }
-            __syncthreads();
+        }
+        if (tid == 0) {
+            bulk_wait_all();                        // this round's output is in global memory
+            fence_proxy_async_global();
         }
         if (!grid_barrier(C)) return;
     }
@@ -188,14 +430,16 @@ __global__ void __launch_bounds__(MERGE_BLOCK) k_merge_rounds(Job J)
 int merge_rounds_max_grid(int num_sms)
 {
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_merge_rounds, MERGE_BLOCK, 0);
+    cudaFuncSetAttribute(k_merge_rounds, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MergeSmem));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_merge_rounds, MERGE_BLOCK, sizeof(MergeSmem));
     return num_sms * (per_sm > 0 ? per_sm : 1);
 }
 
 cudaError_t launch_merge_rounds(const Job& J, int grid, cudaStream_t s)
 {
     void* args[] = {(void*)&J};
-    return cudaLaunchCooperativeKernel((const void*)k_merge_rounds, dim3(grid), dim3(MERGE_BLOCK), args, 0, s);
+    return cudaLaunchCooperativeKernel((const void*)k_merge_rounds, dim3(grid), dim3(MERGE_BLOCK), args,
+                                       sizeof(MergeSmem), s);
 }
 
 }  // namespace ps

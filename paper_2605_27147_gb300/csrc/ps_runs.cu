@@ -211,7 +211,25 @@ __global__ void __launch_bounds__(RUN_BLOCK) k_runs(Job J, uint32_t epoch)
         }
         __syncthreads();
 
-        // 2. the chain from every entry state (lane = state; state m = D0)
+        // 2a. can any step from inside this chunk be natural?  Only if two
+        //     consecutive descents (or position 0 and the first descent) lie at
+        //     least minrun apart; otherwise every chain is forced all the way
+        //     and has a closed form (the usual case for unsorted data).
+        bool may_natural = false;
+        for (int w = tid; w < RUN_WORDS && w * 32 < (int)span; w += RUN_BLOCK) {
+            uint32_t word = bits[w];
+            if (w == 0) word |= 1u;                    // position 0 starts a gap too
+            while (word) {
+                const int e = w * 32 + __ffs(word) - 1;
+                word &= word - 1;
+                if ((uint32_t)e >= span) break;
+                if (next_desc(bits, e + 1, KMAX) - e >= (int)m) { may_natural = true; break; }
+            }
+            if (may_natural) break;
+        }
+        const bool walk_all = __syncthreads_or(may_natural) != 0;
+
+        // 2b. the chain from every entry state (lane = state; state m = D0)
         if (tid <= (int)m) {
             uint32_t cnt = 0, exitv = 0;
             int k = 0;
@@ -227,7 +245,13 @@ __global__ void __launch_bounds__(RUN_BLOCK) k_runs(Job J, uint32_t epoch)
                     k = d0;
                 }
             }
-            if (walk) {
+            if (walk && !walk_all) {
+                // forced steps only: starts k, k + m, k + 2m, ... below span
+                cnt = (uint32_t)k < span ? (span - (uint32_t)k + m - 1) / m : 0u;
+                if (E == n) exitv = STATE_END;
+                else exitv = (uint32_t)k + cnt * m - span;   // < m
+                rec[tid][0] = (uint16_t)k;                    // the progression's start
+            } else if (walk) {
                 bool symbolic = false;
                 while ((uint32_t)k < span) {
                     rec[tid][cnt++] = (uint16_t)k;
@@ -335,6 +359,9 @@ __global__ void __launch_bounds__(RUN_BLOCK) k_runs(Job J, uint32_t epoch)
             const unsigned long long cap = (unsigned long long)(n / 32) + 2;
             if ((unsigned long long)prefix + cnt + 1 > cap || cnt > (uint32_t)RUN_REC) {
                 if (tid == 0) set_error(C, DERR_INTERNAL, 13);
+            } else if (!walk_all) {
+                const uint32_t k0 = B + rec[entry][0];
+                for (uint32_t i = tid; i < cnt; i += RUN_BLOCK) rs[i] = k0 + i * m;
             } else {
                 for (uint32_t i = tid; i < cnt; i += RUN_BLOCK) rs[i] = B + rec[entry][i];
             }

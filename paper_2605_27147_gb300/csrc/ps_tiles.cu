@@ -8,10 +8,10 @@
 // up, one power level at a time: at level p every boundary of power p joins
 // the two segments around it (the segments being delimited by the boundaries
 // of smaller power), exactly the merges Algorithm 1 performs inside this
-// subtree, in an order that respects the tree.  Elements carry their input
-// index in the low half of a 64-bit word, so the merges compare (key, index)
-// pairs; the left segment's indices are all smaller than the right one's, so
-// this is the stable merge of Algorithm 2 (ties take the left run).
+// subtree, in an order that respects the tree.  Each merge is the stable merge
+// of Algorithm 2 (ties take the left segment); every element carries its
+// input position inside the tile (16 bits), from which the permutation is
+// written at the end.
 //
 // The finished tile goes to buffer depth & 1 (0 = caller's arrays, 1 = the
 // scratch arrays) with its stable permutation, ready for the HBM rounds.
@@ -26,14 +26,20 @@ namespace {
 constexpr uint32_t FULL = 0xffffffffu;
 constexpr int TILE_MAX = 1 << TILE_MAX_LOG2;
 constexpr int TILE_RUNS = TILE_MAX / 32 + 2;   // runs of a tile (minrun >= 32 when n >= 64)
-constexpr int TILE_K = TILE_MAX / TILE_BLOCK;  // outputs per thread per level
-constexpr unsigned long long PACK_MAX = ~0ull;
+constexpr int TILE_K = 17;                     // outputs per thread per level (odd: conflict-free strides)
+static_assert(TILE_K * TILE_BLOCK >= TILE_MAX, "a level must cover a whole tile");
+
+struct TileSmem {
+    uint32_t key[2][TILE_MAX];
+    uint16_t idx[2][TILE_MAX];   // input position inside the tile (the permutation)
+};
 
 }  // namespace
 
 __global__ void __launch_bounds__(TILE_BLOCK) k_tiles(Job J)
 {
-    extern __shared__ unsigned long long tile_sm[];   // 2 x TILE_MAX packed (key, index)
+    extern __shared__ __align__(16) unsigned char tile_raw[];
+    TileSmem& sm = *reinterpret_cast<TileSmem*>(tile_raw);
     __shared__ uint32_t rs_s[TILE_RUNS + 1];
     __shared__ uint8_t pw_s[TILE_RUNS + 1];
     __shared__ uint32_t seg_lo[TILE_RUNS + 2];
@@ -67,13 +73,12 @@ __global__ void __launch_bounds__(TILE_BLOCK) k_tiles(Job J)
             continue;
         }
 
-        unsigned long long* cur = tile_sm;
-        unsigned long long* nxt = tile_sm + TILE_MAX;
         const uint32_t nr = it.r1 - it.r0;   // runs in the tile (<= TILE_RUNS - 1)
         if (nr + 1 > (uint32_t)TILE_RUNS) {  // cannot happen for minrun >= 32
             if (tid == 0) set_error(J.ctr, DERR_INTERNAL, 50);
             continue;
         }
+        int cur = 0;
         if (tid == 0) s_mask = 0;
         __syncthreads();
         for (uint32_t k = tid; k <= nr; k += TILE_BLOCK) {
@@ -84,33 +89,33 @@ __global__ void __launch_bounds__(TILE_BLOCK) k_tiles(Job J)
                 atomicOr(&s_mask, 1u << (p - 1));
             }
         }
-        for (uint32_t x = tid; x < size; x += TILE_BLOCK)
-            cur[x] = ((unsigned long long)ksrc[x] << 32) | x;
+        for (uint32_t x = tid; x < size; x += TILE_BLOCK) {
+            sm.key[0][x] = ksrc[x];
+            sm.idx[0][x] = (uint16_t)x;
+        }
         __syncthreads();
 
-        // forced runs (length <= 63 whenever unsorted): sort by rank, one warp each
+        // forced runs (length <= 63 whenever unsorted): stable rank sort, one warp each
         for (uint32_t r = warp; r < nr; r += TILE_BLOCK / 32) {
             const uint32_t rlo = rs_s[r], len = rs_s[r + 1] - rlo;
             if (len > 64 || len < 2) continue;
-            const unsigned long long v0 = lane < (int)len ? cur[rlo + lane] : PACK_MAX;
-            const unsigned long long v1 = lane + 32 < (int)len ? cur[rlo + lane + 32] : PACK_MAX;
-            // any descent inside the run?
-            const unsigned long long nx0 = __shfl_down_sync(FULL, v0, 1);
-            const unsigned long long first1 = __shfl_sync(FULL, v1, 0);
-            const unsigned long long nx1 = __shfl_down_sync(FULL, v1, 1);
-            const unsigned long long succ0 = lane == 31 ? first1 : nx0;
-            const bool d0 = (lane + 1 < (int)len) && (v0 >> 32) > (succ0 >> 32);
-            const bool d1 = (lane + 33 < (int)len) && (v1 >> 32) > (nx1 >> 32);
+            const bool ok0 = lane < (int)len, ok1 = lane + 32 < (int)len;
+            const uint32_t k0 = ok0 ? sm.key[0][rlo + lane] : FULL;
+            const uint32_t k1 = ok1 ? sm.key[0][rlo + lane + 32] : FULL;
+            const uint32_t nk0 = __shfl_down_sync(FULL, k0, 1), f1 = __shfl_sync(FULL, k1, 0);
+            const uint32_t nk1 = __shfl_down_sync(FULL, k1, 1);
+            const bool d0 = lane + 1 < (int)len && k0 > (lane == 31 ? f1 : nk0);
+            const bool d1 = lane + 33 < (int)len && k1 > nk1;
             if (!__any_sync(FULL, d0 || d1)) continue;
             uint32_t rk0 = 0, rk1 = 0;
             for (uint32_t j = 0; j < len; ++j) {
-                const unsigned long long y = __shfl_sync(FULL, j < 32 ? v0 : v1, j & 31);
-                rk0 += y < v0;
-                rk1 += y < v1;
+                const uint32_t y = __shfl_sync(FULL, j < 32 ? k0 : k1, j & 31);
+                rk0 += (y < k0) || (y == k0 && j < (uint32_t)lane);
+                rk1 += (y < k1) || (y == k1 && j < (uint32_t)lane + 32);
             }
             __syncwarp();
-            if (lane < (int)len) cur[rlo + rk0] = v0;
-            if (lane + 32 < (int)len) cur[rlo + rk1] = v1;
+            if (ok0) { sm.key[0][rlo + rk0] = k0; sm.idx[0][rlo + rk0] = (uint16_t)(rlo + lane); }
+            if (ok1) { sm.key[0][rlo + rk1] = k1; sm.idx[0][rlo + rk1] = (uint16_t)(rlo + lane + 32); }
             __syncwarp();
         }
         __syncthreads();
@@ -147,6 +152,10 @@ __global__ void __launch_bounds__(TILE_BLOCK) k_tiles(Job J)
             if (eq) seg_mid[before] = rs_s[tid];
             __syncthreads();
 
+            const uint32_t* ck = sm.key[cur];
+            const uint16_t* ci = sm.idx[cur];
+            uint32_t* nk = sm.key[cur ^ 1];
+            uint16_t* ni = sm.idx[cur ^ 1];
             const uint32_t x0 = tid * TILE_K;
             if (x0 < size) {
                 const uint32_t x1 = min(x0 + TILE_K, size);
@@ -160,26 +169,32 @@ __global__ void __launch_bounds__(TILE_BLOCK) k_tiles(Job J)
                     const uint32_t slo = seg_lo[sg], smid = seg_mid[sg], shi = seg_lo[sg + 1];
                     const uint32_t end = min(x1, shi);
                     if (smid == shi) {
-                        for (; x < end; ++x) nxt[x] = cur[x];
+                        for (; x < end; ++x) {
+                            nk[x] = ck[x];
+                            ni[x] = ci[x];
+                        }
                     } else {
+                        // stable merge: keys only, the left segment wins ties
                         const uint32_t la = smid - slo, lb = shi - smid, d = x - slo;
                         uint32_t ilo = d > lb ? d - lb : 0u, ihi = min(d, la);
                         while (ilo < ihi) {
                             const uint32_t m = (ilo + ihi) >> 1;
-                            if (cur[slo + m] < cur[smid + d - 1 - m]) ilo = m + 1; else ihi = m;
+                            if (ck[slo + m] <= ck[smid + d - 1 - m]) ilo = m + 1; else ihi = m;
                         }
                         uint32_t ia = ilo, ib = d - ilo;
-                        unsigned long long va = ia < la ? cur[slo + ia] : PACK_MAX;
-                        unsigned long long vb = ib < lb ? cur[smid + ib] : PACK_MAX;
+                        uint32_t va = ia < la ? ck[slo + ia] : 0u;
+                        uint32_t vb = ib < lb ? ck[smid + ib] : 0u;
                         for (; x < end; ++x) {
-                            if (va < vb) {
-                                nxt[x] = va;
+                            if (ia < la && (ib >= lb || va <= vb)) {
+                                nk[x] = va;
+                                ni[x] = ci[slo + ia];
                                 ++ia;
-                                va = ia < la ? cur[slo + ia] : PACK_MAX;
+                                va = ia < la ? ck[slo + ia] : 0u;
                             } else {
-                                nxt[x] = vb;
+                                nk[x] = vb;
+                                ni[x] = ci[smid + ib];
                                 ++ib;
-                                vb = ib < lb ? cur[smid + ib] : PACK_MAX;
+                                vb = ib < lb ? ck[smid + ib] : 0u;
                             }
                         }
                     }
@@ -187,15 +202,12 @@ __global__ void __launch_bounds__(TILE_BLOCK) k_tiles(Job J)
                 }
             }
             __syncthreads();
-            unsigned long long* t = cur;
-            cur = nxt;
-            nxt = t;
+            cur ^= 1;
         }
 
         for (uint32_t x = tid; x < size; x += TILE_BLOCK) {
-            const unsigned long long v = cur[x];
-            kdst[x] = (uint32_t)(v >> 32);
-            if (pdst) pdst[x] = lo + (uint32_t)v;
+            kdst[x] = sm.key[cur][x];
+            if (pdst) pdst[x] = lo + sm.idx[cur][x];
         }
         if (to_scratch && nr == 1 && tid == 0) atomicAdd(&J.ctr->leaf_moves, (unsigned long long)size);
         __syncthreads();
@@ -205,21 +217,14 @@ __global__ void __launch_bounds__(TILE_BLOCK) k_tiles(Job J)
 int tiles_max_grid(int num_sms)
 {
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tiles, TILE_BLOCK,
-                                                  2 * TILE_MAX * sizeof(unsigned long long));
+    cudaFuncSetAttribute(k_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileSmem));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tiles, TILE_BLOCK, sizeof(TileSmem));
     return num_sms * (per_sm > 0 ? per_sm : 1);
 }
 
 cudaError_t launch_tiles(const Job& J, int grid, cudaStream_t s)
 {
-    const size_t smem = 2 * TILE_MAX * sizeof(unsigned long long);
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    k_tiles<<<grid, TILE_BLOCK, smem, s>>>(J);
+    k_tiles<<<grid, TILE_BLOCK, sizeof(TileSmem), s>>>(J);
     return cudaGetLastError();
 }
 
