@@ -258,6 +258,7 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
     if (st == PS_OK) st = dev_alloc(c, &J.gnodes, entry_cap);
     if (st == PS_OK) st = dev_alloc(c, &J.gsorted, entry_cap);
     if (st == PS_OK) st = dev_alloc(c, &J.splits, split_cap);
+    if (st == PS_OK) st = dev_alloc(c, &J.chunk_node, split_cap);
     if (st == PS_OK) st = dev_alloc(c, &J.ctr, 1);
     if (st == PS_OK && (cfg->flags & PS_FLAG_HOST_IO)) {
         st = dev_alloc(c, &c->io_keys, max_total);
@@ -274,6 +275,11 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
                         cudaMemset(J.ctr, 0, sizeof(ps::Ctr)) != cudaSuccess))
         st = PS_ECUDA;
     if (st == PS_OK && cudaDeviceSynchronize() != cudaSuccess) st = PS_ECUDA;
+    // every table the kernels write must exist (permB only with want_perm)
+    if (st == PS_OK && (!J.keysB || !J.inst || !J.chunk_status || !J.chunk_map || !J.chunk_incl ||
+                        !J.run_start || !J.kappa || !J.power || !J.na || !J.nb || !J.tiles || !J.gnodes ||
+                        !J.gsorted || !J.splits || !J.chunk_node || !J.ctr || (cfg->want_perm && !J.permB)))
+        st = PS_EINTERNAL;
     if (st != PS_OK) {
         cudaGetLastError();
         free_all(c);
