@@ -258,7 +258,7 @@ def main():
     ctx.sync()
     torch.cuda.synchronize(dev)
 
-    launches_per_sort = 10
+    launches_per_sort = 11
     recs, phases = [], []
     if dist:
         dist.barrier()

@@ -31,7 +31,7 @@ struct ps_ctx {
 namespace {
 
 constexpr unsigned long long LIMIT_N = 0xffffffffull;  // instance sizes and totals < 2^32
-constexpr uint32_t LAUNCHES_PER_CALL = 10;  // setup, runs, 5 planning kernels, tiles, rounds, finish
+constexpr uint32_t LAUNCHES_PER_CALL = 11;  // setup, runs, 6 planning kernels, tiles, rounds, finish
 constexpr uint32_t NPHASES = 6;
 
 struct DeviceGuard {
@@ -233,7 +233,10 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
     const unsigned long long chunk_cap = max_total / ps::RUN_CHUNK + c->max_count + 1;
     const unsigned long long entry_cap = slot_cap;
     const unsigned long long split_cap = max_total / ps::MERGE_E + entry_cap + 2;
-    if (chunk_cap > 0xffffffffull || entry_cap > 0xffffffffull || split_cap > 0xffffffffull) {
+    // chunks summed over all rounds: at most 32 rounds of max_total outputs
+    const unsigned long long chunk_node_cap = (unsigned long long)(ps::NPOW - 1) * (max_total / ps::MERGE_E) + entry_cap + 2;
+    if (chunk_cap > 0xffffffffull || entry_cap > 0xffffffffull || split_cap > 0xffffffffull ||
+        chunk_node_cap > 0xffffffffull) {
         delete c;
         return PS_EINVAL;
     }
@@ -241,6 +244,7 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
     J.chunk_cap = (uint32_t)chunk_cap;
     J.entry_cap = (uint32_t)entry_cap;
     J.split_cap = (uint32_t)split_cap;
+    J.chunk_node_cap = (uint32_t)chunk_node_cap;
 
     ps_status st = PS_OK;
     if (st == PS_OK) st = dev_alloc(c, &J.keysB, max_total);
@@ -258,7 +262,7 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
     if (st == PS_OK) st = dev_alloc(c, &J.gnodes, entry_cap);
     if (st == PS_OK) st = dev_alloc(c, &J.gsorted, entry_cap);
     if (st == PS_OK) st = dev_alloc(c, &J.splits, split_cap);
-    if (st == PS_OK) st = dev_alloc(c, &J.chunk_node, split_cap);
+    if (st == PS_OK) st = dev_alloc(c, &J.chunk_node, chunk_node_cap);
     if (st == PS_OK) st = dev_alloc(c, &J.ctr, 1);
     if (st == PS_OK && (cfg->flags & PS_FLAG_HOST_IO)) {
         st = dev_alloc(c, &c->io_keys, max_total);

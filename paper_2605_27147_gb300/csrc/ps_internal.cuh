@@ -123,13 +123,13 @@ struct Job {
     GNode* gnodes;
     GSorted* gsorted;
     uint32_t* splits;           // per chunk of the current round: left-child elements before it
-    uint32_t* chunk_node;       // per chunk of the current round: its GSorted index
+    uint32_t* chunk_node;       // per chunk (ids global across rounds): its GSorted index
     Ctr* ctr;
     unsigned long long slot_cap;
     uint32_t chunk_cap;
     uint32_t entry_cap;         // capacity of tiles / gnodes / gsorted
     uint32_t split_cap;
-    uint32_t pad1;
+    uint32_t chunk_node_cap;
 };
 
 // ---------------------------------------------------------------- helpers

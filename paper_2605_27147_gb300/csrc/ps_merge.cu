@@ -7,19 +7,22 @@
 // are disjoint and their children are finished.  Every merge is cut into
 // chunks of MERGE_E outputs.
 //
-// Phase A: for every chunk, its merge (GSorted index) and how many of the
-// merge's first d outputs come from the left child (merge-path split: the
-// largest i with A[i-1] <= B[d-i], ties to the left).
+// Phase A: for every chunk, how many of its merge's first d outputs come
+// from the left child (merge-path split: the largest i with A[i-1] <= B[d-i],
+// ties to the left).  The chunk -> merge table is built once per call by the
+// planning kernels.
 //
-// Phase B: each CTA walks its chunks with a two-stage TMA pipeline.  While
-// chunk i is merged, the 1-D bulk copies (cp.async.bulk) of chunk i+1's two
-// input slices (keys and permutation) are in flight into the other shared-
-// memory stage; elements outside the 16-byte-aligned interior of a slice (at
-// most three at each end) are fetched with ordinary loads into registers and
-// stored into the stage after the merge.  Each thread produces MERGE_K
-// consecutive outputs (merge-path split inside shared memory, then a serial
-// merge); the chunk's output leaves through a bulk store (plus ordinary stores
-// for its unaligned ends).
+// Phase B is warp specialised.  A producer warp walks the CTA's chunks: it
+// waits until a shared-memory stage is free (an "empty" mbarrier), describes
+// the chunk, starts the 1-D bulk copies (cp.async.bulk, TMA) of the chunk's
+// two input slices (keys and permutation) into the stage, and loads the
+// elements outside the slices' 16-byte-aligned interiors (at most three at
+// each end) with ordinary loads; the stage's "full" mbarrier completes when
+// both have landed.  Eight consumer warps wait on "full", merge (each thread
+// MERGE_K consecutive outputs: merge-path split inside shared memory, then a
+// serial merge), release the stage, and send the chunk's output out through a
+// bulk store (plus ordinary stores for its unaligned ends).  With two stages
+// the producer runs one chunk ahead of the consumers.
 //
 // One persistent cooperative launch runs every round; a grid barrier (bounded
 // spin, error flag on timeout) separates the phases.  Cooperative launch
@@ -62,16 +65,6 @@ __device__ bool grid_barrier(Ctr* C)
     }
     __syncthreads();
     return s_ok != 0;
-}
-
-__device__ __forceinline__ uint32_t node_of_chunk(const GSorted* gs, uint32_t e0, uint32_t e1, uint32_t cid)
-{
-    uint32_t lo = e0, hi = e1;   // last e in [e0, e1) with chunk_base <= cid
-    while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (gs[mid].chunk_base <= cid) lo = mid; else hi = mid;
-    }
-    return lo;
 }
 
 // Number of left-run elements among the first d outputs of the stable merge.
@@ -138,19 +131,24 @@ struct Stage {
     uint32_t cnt;
 };
 
+constexpr int NCONS = MERGE_BLOCK / 32;          // consumer warps
+constexpr int MTHREADS = MERGE_BLOCK + 32;        // + the producer warp
+constexpr int NST = 2;                            // shared-memory stages
+
 struct __align__(16) MergeSmem {
-    uint32_t in_k[2][SLOT];
-    uint32_t in_p[2][SLOT];
+    uint32_t in_k[NST][SLOT];
+    uint32_t in_p[NST][SLOT];
     uint32_t out_k[SLOT];
     uint32_t out_p[SLOT];
-    uint64_t bar[2];
-    Stage st[2];
+    uint64_t full[NST];      // producer -> consumers: the stage holds a chunk
+    uint64_t empty[NST];     // consumers -> producer: the stage may be refilled
+    Stage st[NST];
 };
 
-// Describe chunk q of the current round (reads the phase-A tables).
+// Describe chunk q (round-local index; global chunk id c0 + q) of the current round.
 __device__ void describe(const Job& J, uint32_t q, uint32_t c0, uint32_t nch, Stage& S)
 {
-    const uint32_t e = J.chunk_node[q];
+    const uint32_t e = J.chunk_node[c0 + q];
     const GSorted g = J.gsorted[e];
     const uint32_t total = g.la + g.lb;
     const uint32_t d0 = (c0 + q - g.chunk_base) * MERGE_E;
@@ -190,7 +188,7 @@ __device__ __forceinline__ bool aligned16(const void* p)
     return (((uintptr_t)p) & 15u) == 0;
 }
 
-// Thread 0: start the bulk copies of a described chunk into stage s.
+// Producer lane 0: announce the stage's bytes and start its bulk copies.
 __device__ void issue_loads(MergeSmem& sm, int s, Ctr* C)
 {
     const Stage& S = sm.st[s];
@@ -227,69 +225,71 @@ __device__ void issue_loads(MergeSmem& sm, int s, Ctr* C)
         k = 0;
         bytes = 0;
     }
-    fence_proxy_async_smem();        // generic reads of this stage come before the async writes
-    mbar_arrive_expect_tx(&sm.bar[s], bytes);
-    for (int i = 0; i < k; ++i) tma_load_1d(dst[i], src[i], sz[i], &sm.bar[s]);
+    fence_proxy_async_smem();        // earlier generic accesses of this stage come first
+    mbar_arrive_expect_tx(&sm.full[s], bytes);
+    for (int i = 0; i < k; ++i) tma_load_1d(dst[i], src[i], sz[i], &sm.full[s]);
 }
 
-// Edge elements of a described chunk: lane l of warp 0 owns slice l / 8
-// (0: left keys, 1: right keys, 2: left perm, 3: right perm), slot l % 8.
-struct EdgeReg {
-    uint32_t val;
-    uint32_t slot;   // destination in the staged array, NONE when idle
-};
-
-__device__ __forceinline__ EdgeReg load_edge(const Stage& S, int lane)
+// Producer lane l: the unaligned element l % 8 of slice l / 8 (0: left
+// keys, 1: right keys, 2: left perm, 3: right perm) goes into the stage.
+__device__ __forceinline__ void copy_edge(MergeSmem& sm, int s, int lane)
 {
-    EdgeReg r{0u, NONE};
+    const Stage& S = sm.st[s];
     const int which = lane >> 3, j = lane & 7;
     const int side = which & 1;
     const bool is_perm = which >= 2;
-    if (is_perm && !S.gp[side]) return r;
+    if (is_perm && !S.gp[side]) return;
     const Slice& sl = is_perm ? S.slp[side] : S.slk[side];
     const uint32_t i = edge_index(sl, (uint32_t)j);
-    if (i == NONE) return r;
-    r.val = is_perm ? S.gp[side][i] : S.gk[side][i];
-    r.slot = (is_perm ? S.sp[side] : S.sk[side]) + i;
-    return r;
+    if (i == NONE) return;
+    if (is_perm) sm.in_p[s][S.sp[side] + i] = S.gp[side][i];
+    else sm.in_k[s][S.sk[side] + i] = S.gk[side][i];
 }
 
-__device__ __forceinline__ void store_edge(MergeSmem& sm, int s, int lane, const EdgeReg& r)
+__device__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, Ctr* C, uint32_t where)
 {
-    if (r.slot == NONE) return;
-    if ((lane >> 3) >= 2) sm.in_p[s][r.slot] = r.val;
-    else sm.in_k[s][r.slot] = r.val;
-}
-
-__device__ bool wait_stage(MergeSmem& sm, int s, uint32_t parity, Ctr* C)
-{
-    if (mbar_try_wait(&sm.bar[s], parity)) return true;
+    if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
-    while (!mbar_try_wait(&sm.bar[s], parity)) {
+    while (!mbar_try_wait(bar, parity)) {
         if (clock64() - t0 > SPIN_LIMIT_CYCLES) {
-            set_error(C, DERR_TIMEOUT, 42);
+            set_error(C, DERR_TIMEOUT, where);
             return false;
         }
     }
     return true;
 }
 
+__device__ __forceinline__ void consumers_sync()
+{
+    asm volatile("bar.sync 1, %0;" ::"n"(MERGE_BLOCK) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
 }  // namespace
 
-__global__ void __launch_bounds__(MERGE_BLOCK) k_merge_rounds(Job J)
+__global__ void __launch_bounds__(MTHREADS, 4) k_merge_rounds(Job J)
 {
     extern __shared__ __align__(16) unsigned char merge_raw[];
     MergeSmem& sm = *reinterpret_cast<MergeSmem*>(merge_raw);
     Ctr* C = J.ctr;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool producer = warp == NCONS;
     const bool perm = J.want_perm != 0;
     if (tid == 0) {
-        mbar_init(&sm.bar[0], 1);
-        mbar_init(&sm.bar[1], 1);
+        for (int s = 0; s < NST; ++s) {
+            mbar_init(&sm.full[s], 2);        // expect_tx arrival + edge arrival
+            mbar_init(&sm.empty[s], NCONS);   // one arrival per consumer warp
+        }
         fence_mbar_init();
     }
     __syncthreads();
-    uint32_t parity[2] = {0u, 0u};
+    // stage use counters (identical in every thread: all walk the same chunks)
+    uint32_t fills[NST] = {0u, 0u}, uses[NST] = {0u, 0u};
+    uint32_t slot = 0;                        // next stage, round robin
 
     for (int r = 0; r < NPOW; ++r) {
         if (*(volatile uint32_t*)&C->error) return;
@@ -298,130 +298,135 @@ __global__ void __launch_bounds__(MERGE_BLOCK) k_merge_rounds(Job J)
         const uint32_t c0 = C->bucket_chunk[r], c1 = C->bucket_chunk[r + 1];
         const uint32_t nch = c1 - c0;
 
-        // phase A: the merge and the merge-path split of every chunk start
+        // phase A: the merge-path split of every chunk start
         for (uint32_t q = blockIdx.x * blockDim.x + tid; q < nch; q += gridDim.x * blockDim.x) {
-            const uint32_t cid = c0 + q;
-            const uint32_t e = node_of_chunk(J.gsorted, e0, e1, cid);
-            const GSorted g = J.gsorted[e];
-            const uint32_t d = (cid - g.chunk_base) * MERGE_E;
-            const uint32_t* src = ((g.depth + 1) & 1u) ? J.keysB : J.keysA;
-            const uint32_t* A = src + g.goff;
+            const GSorted g = J.gsorted[J.chunk_node[c0 + q]];
+            const uint32_t d = (c0 + q - g.chunk_base) * MERGE_E;
+            const uint32_t* A = (((g.depth + 1) & 1u) ? J.keysB : J.keysA) + g.goff;
             J.splits[q] = merge_path(A, g.la, A + g.la, g.lb, d);
-            J.chunk_node[q] = e;
         }
         if (!grid_barrier(C)) return;
-        if (tid == 0) fence_proxy_async_global();   // earlier generic writes before async reads
 
-        // phase B: this CTA's chunks, two stages deep
-        uint32_t q = blockIdx.x;
-        if (q < nch) {
-            if (tid == 0) {
-                describe(J, q, c0, nch, sm.st[0]);
-                issue_loads(sm, 0, C);
-            }
-            __syncthreads();
-            if (warp == 0) store_edge(sm, 0, lane, load_edge(sm.st[0], lane));
-            // (the __syncthreads at the top of the loop orders these stores)
-        }
-        int s = 0;
-        for (; q < nch; q += gridDim.x, s ^= 1) {
-            const uint32_t qn = q + gridDim.x;
-            __syncthreads();
-            EdgeReg nxt{0u, NONE};
-            if (qn < nch) {                          // prefetch the next chunk
-                if (tid == 0) {
-                    describe(J, qn, c0, nch, sm.st[s ^ 1]);
-                    issue_loads(sm, s ^ 1, C);
+        if (producer) {
+            if (lane == 0) fence_proxy_async_global();   // earlier generic writes before async reads
+            __syncwarp();
+            uint32_t sl = slot;
+            for (uint32_t q = blockIdx.x; q < nch; q += gridDim.x) {
+                const int s = (int)sl;
+                if (fills[s] > 0 && !mbar_wait_bounded(&sm.empty[s], (fills[s] - 1) & 1u, C, 44)) return;
+                ++fills[s];
+                if (lane == 0) {
+                    describe(J, q, c0, nch, sm.st[s]);
+                    issue_loads(sm, s, C);
                 }
                 __syncwarp();
-                if (warp == 0) nxt = load_edge(sm.st[s ^ 1], lane);
+                copy_edge(sm, s, lane);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sm.full[s]);
+                sl = (sl + 1) % NST;
             }
-            if (!wait_stage(sm, s, parity[s], C)) return;
-            parity[s] ^= 1u;
-
-            const Stage& S = sm.st[s];
-            const uint32_t na = S.na, nb = S.nb, cnt = S.cnt;
-            const uint32_t* Ak = &sm.in_k[s][S.sk[0]];
-            const uint32_t* Bk = &sm.in_k[s][S.sk[1]];
-            const uint32_t* Ap = &sm.in_p[s][S.sp[0]];
-            const uint32_t* Bp = &sm.in_p[s][S.sp[1]];
-            uint32_t ok[MERGE_K], op[MERGE_K];
-            const uint32_t x0 = tid * MERGE_K;
-            if (x0 < cnt) {
-                uint32_t lo = x0 > nb ? x0 - nb : 0u, hi = min(x0, na);
-                while (lo < hi) {
-                    const uint32_t mid = (lo + hi) >> 1;
-                    if (Ak[mid] <= Bk[x0 - 1 - mid]) lo = mid + 1; else hi = mid;
-                }
-                uint32_t ia = lo, ib = x0 - lo;
-                uint32_t va = ia < na ? Ak[ia] : 0u, vb = ib < nb ? Bk[ib] : 0u;
+        } else {
+            uint32_t sl = slot;
+            for (uint32_t q = blockIdx.x; q < nch; q += gridDim.x) {
+                const int s = (int)sl;
+                if (!mbar_wait_bounded(&sm.full[s], uses[s] & 1u, C, 42)) return;
+                ++uses[s];
+                const Stage& S = sm.st[s];
+                const uint32_t na = S.na, nb = S.nb, cnt = S.cnt;
+                uint32_t* const gok = S.ok;
+                uint32_t* const gop = S.op;
+                const uint32_t sok = S.sok, sop = S.sop;
+                const uint32_t* Ak = &sm.in_k[s][S.sk[0]];
+                const uint32_t* Bk = &sm.in_k[s][S.sk[1]];
+                const uint32_t* Ap = &sm.in_p[s][S.sp[0]];
+                const uint32_t* Bp = &sm.in_p[s][S.sp[1]];
+                uint32_t ok[MERGE_K], op[MERGE_K];
+                const uint32_t x0 = tid * MERGE_K;
+                if (x0 < cnt) {
+                    uint32_t lo = x0 > nb ? x0 - nb : 0u, hi = min(x0, na);
+                    while (lo < hi) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if (Ak[mid] <= Bk[x0 - 1 - mid]) lo = mid + 1; else hi = mid;
+                    }
+                    uint32_t ia = lo, ib = x0 - lo;
+                    uint32_t va = ia < na ? Ak[ia] : 0u, vb = ib < nb ? Bk[ib] : 0u;
 #pragma unroll
-                for (int j = 0; j < MERGE_K; ++j) {
-                    if (x0 + j < cnt) {
-                        const bool take_a = ia < na && (ib >= nb || va <= vb);
-                        if (take_a) {
-                            ok[j] = va;
-                            if (perm) op[j] = Ap[ia];
-                            ++ia;
-                            va = ia < na ? Ak[ia] : 0u;
-                        } else {
-                            ok[j] = vb;
-                            if (perm) op[j] = Bp[ib];
-                            ++ib;
-                            vb = ib < nb ? Bk[ib] : 0u;
+                    for (int j = 0; j < MERGE_K; ++j) {
+                        if (x0 + j < cnt) {
+                            const bool take_a = ia < na && (ib >= nb || va <= vb);
+                            if (take_a) {
+                                ok[j] = va;
+                                if (perm) op[j] = Ap[ia];
+                                ++ia;
+                                va = ia < na ? Ak[ia] : 0u;
+                            } else {
+                                ok[j] = vb;
+                                if (perm) op[j] = Bp[ib];
+                                ++ib;
+                                vb = ib < nb ? Bk[ib] : 0u;
+                            }
                         }
                     }
                 }
-            }
-            if (tid == 0) bulk_wait_read_all();    // the previous chunk's output has left shared memory
-            __syncthreads();
-            if (x0 < cnt) {
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sm.empty[s]);   // this warp is done with the stage
+                if (tid == 0) bulk_wait_read_all();         // the previous output has left shared memory
+                consumers_sync();
+                if (x0 < cnt) {
 #pragma unroll
-                for (int j = 0; j < MERGE_K; ++j) {
-                    if (x0 + j < cnt) {
-                        sm.out_k[S.sok + x0 + j] = ok[j];
-                        if (perm) sm.out_p[S.sop + x0 + j] = op[j];
+                    for (int j = 0; j < MERGE_K; ++j) {
+                        if (x0 + j < cnt) {
+                            sm.out_k[sok + x0 + j] = ok[j];
+                            if (perm) sm.out_p[sop + x0 + j] = op[j];
+                        }
                     }
                 }
+                fence_proxy_async_smem();
+                consumers_sync();
+                // output: aligned interior by bulk store, the ends by ordinary stores
+                const Slice ok_sl = slice_of(gok, cnt);
+                const Slice op_sl = perm ? slice_of(gop, cnt) : Slice{0u, 0u, 0u};
+                if (tid == 0) {
+                    bool good = true;
+                    if (ok_sl.nint) {
+                        void* g = gok + ok_sl.head;
+                        const void* l = &sm.out_k[sok + ok_sl.head];
+                        good = good && aligned16(g) && aligned16(l);
+                        if (good) tma_store_1d(g, l, ok_sl.nint * 4u);
+                    }
+                    if (perm && op_sl.nint) {
+                        void* g = gop + op_sl.head;
+                        const void* l = &sm.out_p[sop + op_sl.head];
+                        const bool g2 = aligned16(g) && aligned16(l);
+                        if (g2) tma_store_1d(g, l, op_sl.nint * 4u);
+                        good = good && g2;
+                    }
+                    if (!good) set_error(C, DERR_INTERNAL, 43);
+                    bulk_commit();
+                }
+                if (warp == 1 && (lane & 15) < EDGE_SLOTS) {   // lanes 0-7: keys, 16-23: permutation
+                    const bool is_perm = lane >= 16;
+                    if (!is_perm || perm) {
+                        const uint32_t i = edge_index(is_perm ? op_sl : ok_sl, (uint32_t)(lane & 15));
+                        if (i != NONE) {
+                            if (is_perm) gop[i] = sm.out_p[sop + i];
+                            else gok[i] = sm.out_k[sok + i];
+                        }
+                    }
+                }
+                sl = (sl + 1) % NST;
             }
-            fence_proxy_async_smem();
-            if (warp == 0) store_edge(sm, s ^ 1, lane, nxt);
-            __syncthreads();
-            // output: aligned interior by bulk store, the ends by ordinary stores
-            const Slice ok_sl = slice_of(S.ok, cnt);
-            const Slice op_sl = perm ? slice_of(S.op, cnt) : Slice{0u, 0u, 0u};
             if (tid == 0) {
-                bool good = true;
-                if (ok_sl.nint) {
-                    void* g = S.ok + ok_sl.head;
-                    const void* l = &sm.out_k[S.sok + ok_sl.head];
-                    good = good && aligned16(g) && aligned16(l);
-                    if (good) tma_store_1d(g, l, ok_sl.nint * 4u);
-                }
-                if (perm && op_sl.nint) {
-                    void* g = S.op + op_sl.head;
-                    const void* l = &sm.out_p[S.sop + op_sl.head];
-                    const bool g2 = aligned16(g) && aligned16(l);
-                    if (g2) tma_store_1d(g, l, op_sl.nint * 4u);
-                    good = good && g2;
-                }
-                if (!good) set_error(C, DERR_INTERNAL, 43);
-                bulk_commit();
-            }
-            if (warp == 1 && (lane & 15) < EDGE_SLOTS) {   // lanes 0-7: keys, 16-23: permutation
-                const bool is_perm = lane >= 16;
-                if (!is_perm || perm) {
-                    const uint32_t i = edge_index(is_perm ? op_sl : ok_sl, (uint32_t)(lane & 15));
-                    if (i != NONE) {
-                        if (is_perm) S.op[i] = sm.out_p[S.sop + i];
-                        else S.ok[i] = sm.out_k[S.sok + i];
-                    }
-                }
+                bulk_wait_all();                    // this round's output is in global memory
+                fence_proxy_async_global();
             }
         }
-        if (tid == 0) {
-            bulk_wait_all();                        // this round's output is in global memory
-            fence_proxy_async_global();
+        // both roles advanced the stage pointer by this CTA's chunk count
+        for (uint32_t q = blockIdx.x; q < nch; q += gridDim.x) slot = (slot + 1) % NST;
+        if (producer) {
+            for (int s = 0; s < NST; ++s) uses[s] = fills[s];
+        } else {
+            for (int s = 0; s < NST; ++s) fills[s] = uses[s];
         }
         if (!grid_barrier(C)) return;
     }
@@ -431,14 +436,14 @@ int merge_rounds_max_grid(int num_sms)
 {
     int per_sm = 0;
     cudaFuncSetAttribute(k_merge_rounds, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MergeSmem));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_merge_rounds, MERGE_BLOCK, sizeof(MergeSmem));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_merge_rounds, MTHREADS, sizeof(MergeSmem));
     return num_sms * (per_sm > 0 ? per_sm : 1);
 }
 
 cudaError_t launch_merge_rounds(const Job& J, int grid, cudaStream_t s)
 {
     void* args[] = {(void*)&J};
-    return cudaLaunchCooperativeKernel((const void*)k_merge_rounds, dim3(grid), dim3(MERGE_BLOCK), args,
+    return cudaLaunchCooperativeKernel((const void*)k_merge_rounds, dim3(grid), dim3(MTHREADS), args,
                                        sizeof(MergeSmem), s);
 }
 

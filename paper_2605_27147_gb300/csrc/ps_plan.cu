@@ -375,6 +375,36 @@ __global__ void __launch_bounds__(1024) k_bucket(Job J)
         // per-round chunk counts must fit the split table
         for (int r = 0; r < NPOW; ++r)
             if (C->bucket_chunk[r + 1] - C->bucket_chunk[r] + 1 > J.split_cap) set_error(C, DERR_INTERNAL, 30);
+        if (total_chunks > J.chunk_node_cap) set_error(C, DERR_INTERNAL, 31);
+    }
+}
+
+// Chunk -> merge table for every round (chunk ids are global across rounds):
+// each thread covers 32 consecutive chunks with one binary search and a walk.
+__global__ void __launch_bounds__(PLAN_BLOCK) k_chunk_nodes(Job J)
+{
+    if (*(volatile uint32_t*)&J.ctr->error) return;
+    const Ctr* C = J.ctr;
+    const uint32_t ng = min(C->n_gnodes, J.entry_cap);
+    const uint32_t total = C->bucket_chunk[NPOW];
+    if (ng == 0 || total > J.chunk_node_cap) return;
+    const uint32_t groups = (total + 31) / 32;
+    for (uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x; gi < groups; gi += gridDim.x * blockDim.x) {
+        const uint32_t c0 = gi * 32, c1 = min(c0 + 32, total);
+        uint32_t lo = 0, hi = ng;     // last node with chunk_base <= c0
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (J.gsorted[mid].chunk_base <= c0) lo = mid; else hi = mid;
+        }
+        uint32_t e = lo;
+        uint32_t next = e + 1 < ng ? J.gsorted[e + 1].chunk_base : 0xffffffffu;
+        for (uint32_t c = c0; c < c1; ++c) {
+            while (c >= next) {
+                ++e;
+                next = e + 1 < ng ? J.gsorted[e + 1].chunk_base : 0xffffffffu;
+            }
+            J.chunk_node[c] = e;
+        }
     }
 }
 
@@ -420,6 +450,7 @@ cudaError_t launch_plan(const Job& J, int grid, cudaStream_t s)
     k_classify<<<grid, PLAN_BLOCK, 0, s>>>(J);
     k_depth<<<grid, PLAN_BLOCK, 0, s>>>(J);
     k_bucket<<<1, 1024, 0, s>>>(J);
+    k_chunk_nodes<<<grid, PLAN_BLOCK, 0, s>>>(J);
     return cudaGetLastError();
 }
 

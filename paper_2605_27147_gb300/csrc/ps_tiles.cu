@@ -95,27 +95,55 @@ __global__ void __launch_bounds__(TILE_BLOCK) k_tiles(Job J)
         }
         __syncthreads();
 
-        // forced runs (length <= 63 whenever unsorted): stable rank sort, one warp each
+        // forced runs (length <= 63 whenever unsorted): one warp each, bitonic
+        // network on (key, input position) pairs -- the pairs are distinct, so
+        // the result is the stable order an insertion sort gives
         for (uint32_t r = warp; r < nr; r += TILE_BLOCK / 32) {
             const uint32_t rlo = rs_s[r], len = rs_s[r + 1] - rlo;
             if (len > 64 || len < 2) continue;
             const bool ok0 = lane < (int)len, ok1 = lane + 32 < (int)len;
-            const uint32_t k0 = ok0 ? sm.key[0][rlo + lane] : FULL;
-            const uint32_t k1 = ok1 ? sm.key[0][rlo + lane + 32] : FULL;
+            uint32_t k0 = ok0 ? sm.key[0][rlo + lane] : FULL;
+            uint32_t k1 = ok1 ? sm.key[0][rlo + lane + 32] : FULL;
             const uint32_t nk0 = __shfl_down_sync(FULL, k0, 1), f1 = __shfl_sync(FULL, k1, 0);
             const uint32_t nk1 = __shfl_down_sync(FULL, k1, 1);
             const bool d0 = lane + 1 < (int)len && k0 > (lane == 31 ? f1 : nk0);
             const bool d1 = lane + 33 < (int)len && k1 > nk1;
             if (!__any_sync(FULL, d0 || d1)) continue;
-            uint32_t rk0 = 0, rk1 = 0;
-            for (uint32_t j = 0; j < len; ++j) {
-                const uint32_t y = __shfl_sync(FULL, j < 32 ? k0 : k1, j & 31);
-                rk0 += (y < k0) || (y == k0 && j < (uint32_t)lane);
-                rk1 += (y < k1) || (y == k1 && j < (uint32_t)lane + 32);
+            // padding sorts last: key FULL and a position beyond any tile
+            uint32_t i0 = ok0 ? rlo + lane : 0x10000u + lane;
+            uint32_t i1 = ok1 ? rlo + lane + 32 : 0x10020u + lane;
+            const uint32_t kmax = len > 32 ? 64u : 32u;
+            for (uint32_t k = 2; k <= kmax; k <<= 1) {
+                for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                    if (j == 32) {   // partners in the same lane: slot 0 (i) with slot 1 (i + 32)
+                        const bool swap = (k1 < k0) || (k1 == k0 && i1 < i0);   // ascending (i & 64 == 0)
+                        if (swap) {
+                            const uint32_t tk = k0, ti = i0;
+                            k0 = k1; i0 = i1; k1 = tk; i1 = ti;
+                        }
+                        continue;
+                    }
+                    const uint32_t pk0 = __shfl_xor_sync(FULL, k0, j), pi0 = __shfl_xor_sync(FULL, i0, j);
+                    {
+                        const uint32_t idx = (uint32_t)lane;
+                        const bool asc = (idx & k) == 0;
+                        const bool lower = (idx & j) == 0;
+                        const bool pless = (pk0 < k0) || (pk0 == k0 && pi0 < i0);
+                        // the lower element keeps the min when ascending, the max otherwise
+                        if (pless == (lower == asc)) { k0 = pk0; i0 = pi0; }
+                    }
+                    if (kmax == 64) {
+                        const uint32_t pk1 = __shfl_xor_sync(FULL, k1, j), pi1 = __shfl_xor_sync(FULL, i1, j);
+                        const uint32_t idx = (uint32_t)lane + 32;
+                        const bool asc = (idx & k) == 0;
+                        const bool lower = (idx & j) == 0;
+                        const bool pless = (pk1 < k1) || (pk1 == k1 && pi1 < i1);
+                        if (pless == (lower == asc)) { k1 = pk1; i1 = pi1; }
+                    }
+                }
             }
-            __syncwarp();
-            if (ok0) { sm.key[0][rlo + rk0] = k0; sm.idx[0][rlo + rk0] = (uint16_t)(rlo + lane); }
-            if (ok1) { sm.key[0][rlo + rk1] = k1; sm.idx[0][rlo + rk1] = (uint16_t)(rlo + lane + 32); }
+            if (ok0) { sm.key[0][rlo + lane] = k0; sm.idx[0][rlo + lane] = (uint16_t)i0; }
+            if (ok1) { sm.key[0][rlo + lane + 32] = k1; sm.idx[0][rlo + lane + 32] = (uint16_t)i1; }
             __syncwarp();
         }
         __syncthreads();
