@@ -278,12 +278,14 @@ def main():
     total_ms = sum(sort_ms)
     elems = sum(n for _, _, n, _ in recs)
     # one stats call per distribution for the algorithmic byte counts
-    hbm = {}
+    hbm, rounds = {}, {}
     for i in range(len(data)):
         n = data[i][1]
         work[:n].copy_(pristine[i])
+        flush.fill_(i)
         st = ctx.run(work[:n], perm[:n], stats=True)
         hbm[i] = st
+        rounds[data[i][0]] = [[round(x, 1) for x in rt] for rt in ctx.round_times()]
     merge_ms = sum(p["merge_rounds"] for p in phases)
     merge_bytes = sum(BYTES_PER_MERGED_ELEM * hbm[i]["hbm_merge_elems"] for _, _, _, i in recs)
     tiles_ms = sum(p["tiles"] for p in phases)
@@ -368,6 +370,7 @@ def main():
         },
         "stats": {data[i][0]: {k: hbm[i][k] for k in ("runs", "merge_cost", "tiles", "global_nodes", "rounds",
                                                       "hbm_merge_elems", "max_power")} for i in hbm},
+        "round_us_split_merge_barrier": rounds,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clk.summary(),

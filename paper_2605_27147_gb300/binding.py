@@ -21,7 +21,7 @@ PS_MODE_PINGPONG, PS_MODE_VM = 0, 1
 EXPORTS = (
     "ps_status_str", "ps_create", "ps_run", "ps_run_batched", "ps_run_host", "ps_sync",
     "ps_get_phase_times", "ps_get_runs", "ps_get_powers", "ps_get_nodes", "ps_get_instance_stats",
-    "ps_destroy", "ps_run_noalloc",
+    "ps_destroy", "ps_run_noalloc", "ps_get_round_times",
 )
 PS_NOALLOC_MAX_N = 262144
 PS_FLAG_TIMING, PS_FLAG_HOST_IO = 1, 2
@@ -105,6 +105,9 @@ def lib(build_if_missing: bool = True):
         L.ps_run_host.argtypes = [vp, vp, vp, ctypes.c_uint64, ctypes.POINTER(ps_stats)]
         L.ps_get_phase_times.restype = ctypes.c_int
         L.ps_get_phase_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_uint32,
+                                         ctypes.POINTER(ctypes.c_uint32)]
+        L.ps_get_round_times.restype = ctypes.c_int
+        L.ps_get_round_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_uint32,
                                          ctypes.POINTER(ctypes.c_uint32)]
         L.ps_sync.restype = ctypes.c_int
         L.ps_sync.argtypes = [vp]
@@ -206,6 +209,15 @@ class Context:
         buf = (ctypes.c_float * len(PHASES))()
         _check(lib().ps_get_phase_times(self._h, buf, len(PHASES), None), "ps_get_phase_times")
         return {name: float(buf[i]) for i, name in enumerate(PHASES)}
+
+    def round_times(self) -> list:
+        """[(split_us, merge_us, barrier_us)] per HBM merge round of the last call."""
+        cnt = ctypes.c_uint32()
+        _check(lib().ps_get_round_times(self._h, None, 0, ctypes.byref(cnt)), "ps_get_round_times")
+        buf = (ctypes.c_float * max(1, cnt.value))()
+        _check(lib().ps_get_round_times(self._h, buf, cnt.value, None), "ps_get_round_times")
+        v = [float(buf[i]) for i in range(cnt.value)]
+        return [tuple(v[i:i + 3]) for i in range(0, len(v), 3)]
 
     def sync(self):
         _check(lib().ps_sync(self._h), "ps_sync")

@@ -373,6 +373,26 @@ PS_API ps_status ps_get_phase_times(ps_ctx* ctx, float* h_ms, uint32_t cap, uint
     return PS_OK;
 }
 
+PS_API ps_status ps_get_round_times(ps_ctx* ctx, float* h_us, uint32_t cap, uint32_t* count)
+{
+    if (!ctx || (!h_us && cap)) return PS_EINVAL;
+    if (!ctx->last_valid) return PS_EINVAL;
+    DeviceGuard g(ctx->device);
+    ps_status st = sync_and_check(ctx);
+    if (st != PS_OK) return st;
+    const ps::Ctr* h = ctx->h_ctr;
+    uint32_t k = 0;
+    for (int r = 0; r < ps::NPOW; ++r) {
+        const unsigned long long* t = h->round_ns[r];
+        if (h->bucket_start[r] == h->bucket_start[r + 1] || t[0] == 0 || t[3] < t[0]) continue;
+        const float v[3] = {(float)(t[1] - t[0]) * 1e-3f, (float)(t[2] - t[1]) * 1e-3f, (float)(t[3] - t[2]) * 1e-3f};
+        for (int i = 0; i < 3; ++i, ++k)
+            if (k < cap) h_us[k] = v[i];
+    }
+    if (count) *count = k;
+    return PS_OK;
+}
+
 PS_API ps_status ps_sync(ps_ctx* ctx)
 {
     if (!ctx) return PS_EINVAL;

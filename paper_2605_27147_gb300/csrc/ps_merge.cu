@@ -297,6 +297,8 @@ __global__ void __launch_bounds__(MTHREADS, 4) k_merge_rounds(Job J)
         if (e0 == e1) continue;
         const uint32_t c0 = C->bucket_chunk[r], c1 = C->bucket_chunk[r + 1];
         const uint32_t nch = c1 - c0;
+        const bool stamp = blockIdx.x == 0 && tid == 0;
+        if (stamp) C->round_ns[r][0] = globaltimer_ns();
 
         // phase A: the merge-path split of every chunk start
         for (uint32_t q = blockIdx.x * blockDim.x + tid; q < nch; q += gridDim.x * blockDim.x) {
@@ -306,6 +308,7 @@ __global__ void __launch_bounds__(MTHREADS, 4) k_merge_rounds(Job J)
             J.splits[q] = merge_path(A, g.la, A + g.la, g.lb, d);
         }
         if (!grid_barrier(C)) return;
+        if (stamp) C->round_ns[r][1] = globaltimer_ns();
 
         if (producer) {
             if (lane == 0) fence_proxy_async_global();   // earlier generic writes before async reads
@@ -349,23 +352,19 @@ __global__ void __launch_bounds__(MTHREADS, 4) k_merge_rounds(Job J)
                         if (Ak[mid] <= Bk[x0 - 1 - mid]) lo = mid + 1; else hi = mid;
                     }
                     uint32_t ia = lo, ib = x0 - lo;
-                    uint32_t va = ia < na ? Ak[ia] : 0u, vb = ib < nb ? Bk[ib] : 0u;
+                    uint32_t va = ia < na ? Ak[ia] : 0xffffffffu, vb = ib < nb ? Bk[ib] : 0xffffffffu;
+                    // branch-free serial merge; an exhausted side is read at slot 0
+                    // (a valid address whose value is never used)
 #pragma unroll
                     for (int j = 0; j < MERGE_K; ++j) {
-                        if (x0 + j < cnt) {
-                            const bool take_a = ia < na && (ib >= nb || va <= vb);
-                            if (take_a) {
-                                ok[j] = va;
-                                if (perm) op[j] = Ap[ia];
-                                ++ia;
-                                va = ia < na ? Ak[ia] : 0u;
-                            } else {
-                                ok[j] = vb;
-                                if (perm) op[j] = Bp[ib];
-                                ++ib;
-                                vb = ib < nb ? Bk[ib] : 0u;
-                            }
-                        }
+                        const bool take_a = ia < na && (ib >= nb || va <= vb);
+                        ok[j] = take_a ? va : vb;
+                        if (perm) op[j] = take_a ? Ap[ia < na ? ia : 0u] : Bp[ib < nb ? ib : 0u];
+                        ia += take_a;
+                        ib += !take_a;
+                        const uint32_t nxt = take_a ? Ak[ia < na ? ia : 0u] : Bk[ib < nb ? ib : 0u];
+                        va = take_a ? nxt : va;
+                        vb = take_a ? vb : nxt;
                     }
                 }
                 __syncwarp();
@@ -419,6 +418,7 @@ __global__ void __launch_bounds__(MTHREADS, 4) k_merge_rounds(Job J)
             if (tid == 0) {
                 bulk_wait_all();                    // this round's output is in global memory
                 fence_proxy_async_global();
+                if (stamp) C->round_ns[r][2] = globaltimer_ns();
             }
         }
         // both roles advanced the stage pointer by this CTA's chunk count
@@ -429,6 +429,7 @@ __global__ void __launch_bounds__(MTHREADS, 4) k_merge_rounds(Job J)
             for (int s = 0; s < NST; ++s) fills[s] = uses[s];
         }
         if (!grid_barrier(C)) return;
+        if (stamp) C->round_ns[r][3] = globaltimer_ns();
     }
 }
 

@@ -98,6 +98,8 @@ __global__ void __launch_bounds__(1024) k_setup(Job J)
         C->hbm_elems = 0;
     }
     for (int r = threadIdx.x; r < NPOW + 2; r += blockDim.x) {
+        if (r < NPOW)
+            for (int i = 0; i < 4; ++i) C->round_ns[r][i] = 0;
         if (r < NPOW + 1) C->bucket_count[r] = 0;
         C->bucket_start[r] = 0;
         C->bucket_chunk[r] = 0;

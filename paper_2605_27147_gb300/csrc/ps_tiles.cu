@@ -212,18 +212,18 @@ __global__ void __launch_bounds__(TILE_BLOCK) k_tiles(Job J)
                         uint32_t ia = ilo, ib = d - ilo;
                         uint32_t va = ia < la ? ck[slo + ia] : 0u;
                         uint32_t vb = ib < lb ? ck[smid + ib] : 0u;
+                        // branch-free serial merge; an exhausted side is read at the
+                        // segment start (a valid slot whose value is never used)
                         for (; x < end; ++x) {
-                            if (ia < la && (ib >= lb || va <= vb)) {
-                                nk[x] = va;
-                                ni[x] = ci[slo + ia];
-                                ++ia;
-                                va = ia < la ? ck[slo + ia] : 0u;
-                            } else {
-                                nk[x] = vb;
-                                ni[x] = ci[smid + ib];
-                                ++ib;
-                                vb = ib < lb ? ck[smid + ib] : 0u;
-                            }
+                            const bool take_a = ia < la && (ib >= lb || va <= vb);
+                            const uint32_t src = take_a ? slo + ia : smid + ib;
+                            nk[x] = take_a ? va : vb;
+                            ni[x] = ci[src];
+                            ia += take_a;
+                            ib += !take_a;
+                            const uint32_t nxt = ck[take_a ? (ia < la ? slo + ia : slo) : (ib < lb ? smid + ib : slo)];
+                            va = take_a ? nxt : va;
+                            vb = take_a ? vb : nxt;
                         }
                     }
                     ++sg;
