@@ -143,11 +143,12 @@ PS_API ps_status ps_run_host(ps_ctx* ctx, uint32_t* h_keys, uint32_t* h_perm, ui
 PS_API ps_status ps_get_phase_times(ps_ctx* ctx, float* h_ms, uint32_t cap, uint32_t* count);
 
 /* Timeline of the HBM merge rounds of the last call (synchronises), from
- * globaltimer stamps taken by one CTA: for every round that ran, three values
+ * globaltimer stamps taken by one CTA: for every round that ran, four values
  * in microseconds -- the split phase (merge-path searches and the grid
  * barrier after them), the merge phase (until that CTA's last output was
- * written), and the wait at the round's closing barrier.  h_us receives
- * min(cap, 3 x rounds) values; *count (may be NULL) gets 3 x rounds. */
+ * written), the wait at the round's closing barrier, and the part of the
+ * split phase that CTA spent on its own searches.  h_us receives
+ * min(cap, 4 x rounds) values; *count (may be NULL) gets 4 x rounds. */
 PS_API ps_status ps_get_round_times(ps_ctx* ctx, float* h_us, uint32_t cap, uint32_t* count);
 
 /* Wait for the context's stream and report the device-side status of the

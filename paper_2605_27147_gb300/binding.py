@@ -211,13 +211,13 @@ class Context:
         return {name: float(buf[i]) for i, name in enumerate(PHASES)}
 
     def round_times(self) -> list:
-        """[(split_us, merge_us, barrier_us)] per HBM merge round of the last call."""
+        """[(split_us, merge_us, barrier_us, own_search_us)] per HBM merge round of the last call."""
         cnt = ctypes.c_uint32()
         _check(lib().ps_get_round_times(self._h, None, 0, ctypes.byref(cnt)), "ps_get_round_times")
         buf = (ctypes.c_float * max(1, cnt.value))()
         _check(lib().ps_get_round_times(self._h, buf, cnt.value, None), "ps_get_round_times")
         v = [float(buf[i]) for i in range(cnt.value)]
-        return [tuple(v[i:i + 3]) for i in range(0, len(v), 3)]
+        return [tuple(v[i:i + 4]) for i in range(0, len(v), 4)]
 
     def sync(self):
         _check(lib().ps_sync(self._h), "ps_sync")

@@ -385,8 +385,9 @@ PS_API ps_status ps_get_round_times(ps_ctx* ctx, float* h_us, uint32_t cap, uint
     for (int r = 0; r < ps::NPOW; ++r) {
         const unsigned long long* t = h->round_ns[r];
         if (h->bucket_start[r] == h->bucket_start[r + 1] || t[0] == 0 || t[3] < t[0]) continue;
-        const float v[3] = {(float)(t[1] - t[0]) * 1e-3f, (float)(t[2] - t[1]) * 1e-3f, (float)(t[3] - t[2]) * 1e-3f};
-        for (int i = 0; i < 3; ++i, ++k)
+        const float v[4] = {(float)(t[1] - t[0]) * 1e-3f, (float)(t[2] - t[1]) * 1e-3f,
+                            (float)(t[3] - t[2]) * 1e-3f, (float)(t[4] - t[0]) * 1e-3f};
+        for (int i = 0; i < 4; ++i, ++k)
             if (k < cap) h_us[k] = v[i];
     }
     if (count) *count = k;

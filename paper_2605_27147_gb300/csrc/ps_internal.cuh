@@ -99,8 +99,9 @@ struct Ctr {
     unsigned long long hbm_elems;      // sum of the sizes of the HBM merges
     // globaltimer stamps (ns) taken by CTA 0 of the merge rounds: [round][0] round
     // start, [1] after the split phase's barrier, [2] its last output sent,
-    // [3] after the round's closing barrier (0 for empty rounds)
-    unsigned long long round_ns[NPOW][4];
+    // [3] after the round's closing barrier, [4] its own split searches done
+    // (0 for empty rounds)
+    unsigned long long round_ns[NPOW][5];
 };
 
 __device__ __forceinline__ unsigned long long globaltimer_ns()

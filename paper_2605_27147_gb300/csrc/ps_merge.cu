@@ -51,8 +51,10 @@ __device__ bool grid_barrier(Ctr* C)
             st_release_u32(&C->bar_gen, gen + 1);
         } else {
             const long long t0 = clock64();
+            uint32_t nap = 64;                       // back off: hundreds of CTAs poll one word
             while (ld_acquire_u32(&C->bar_gen) == gen) {
-                __nanosleep(32);
+                __nanosleep(nap);
+                nap = nap < 1024 ? nap * 2 : 1024;
                 if (clock64() - t0 > SPIN_LIMIT_CYCLES) {
                     set_error(C, DERR_TIMEOUT, 40);
                     ok = 0;
@@ -307,6 +309,7 @@ __global__ void __launch_bounds__(MTHREADS, 4) k_merge_rounds(Job J)
             const uint32_t* A = (((g.depth + 1) & 1u) ? J.keysB : J.keysA) + g.goff;
             J.splits[q] = merge_path(A, g.la, A + g.la, g.lb, d);
         }
+        if (stamp) C->round_ns[r][4] = globaltimer_ns();
         if (!grid_barrier(C)) return;
         if (stamp) C->round_ns[r][1] = globaltimer_ns();
 
