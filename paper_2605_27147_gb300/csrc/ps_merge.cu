@@ -50,9 +50,11 @@ __device__ bool grid_barrier(Ctr* C)
             __threadfence();
             st_release_u32(&C->bar_gen, gen + 1);
         } else {
+            // poll with relaxed loads (an acquire per poll would stall the SM's
+            // other warps), back off, and acquire once the generation moved
             const long long t0 = clock64();
-            uint32_t nap = 64;                       // back off: hundreds of CTAs poll one word
-            while (ld_acquire_u32(&C->bar_gen) == gen) {
+            uint32_t nap = 64;
+            while (ld_relaxed_u32(&C->bar_gen) == gen) {
                 __nanosleep(nap);
                 nap = nap < 1024 ? nap * 2 : 1024;
                 if (clock64() - t0 > SPIN_LIMIT_CYCLES) {
@@ -61,6 +63,7 @@ __device__ bool grid_barrier(Ctr* C)
                     break;
                 }
             }
+            fence_acquire_gpu();
         }
         __threadfence();
         s_ok = ok;
