@@ -225,6 +225,7 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
     c->grid_plan = c->num_sms * 8;
     c->grid_tiles = ps::tiles_max_grid(c->num_sms);
     c->grid_merge = ps::merge_rounds_max_grid(c->num_sms);
+    if (c->grid_merge > 1024) c->grid_merge = 1024;   // the grid barrier's group table
 
     ps::Job& J = c->base;
     std::memset(&J, 0, sizeof(J));

@@ -91,6 +91,7 @@ struct Ctr {
     uint32_t rounds;                   // non-empty rounds
     uint32_t bar_count;
     uint32_t bar_gen;
+    uint32_t bar_group[32];            // arrivals per group of 32 CTAs (grids of <= 1024 CTAs)
     uint32_t max_power;
     unsigned long long leaf_moves;
     unsigned long long M_total;

@@ -36,6 +36,10 @@ namespace {
 constexpr int SLOT = MERGE_E + 16;   // a staged array: up to 3 + 3 + 3 shift slots
 constexpr int EDGE_SLOTS = 8;        // unaligned elements of one slice (<= 7)
 
+// Grid barrier in two levels: CTAs arrive at a counter of their group of 32,
+// the last of a group arrives at the global counter, the last group bumps the
+// generation.  Arrivals on 20-odd different words proceed in parallel instead
+// of 600 atomics serialising on one.
 __device__ bool grid_barrier(Ctr* C)
 {
     __syncthreads();
@@ -44,14 +48,20 @@ __device__ bool grid_barrier(Ctr* C)
         uint32_t ok = 1;
         const uint32_t gen = ld_acquire_u32(&C->bar_gen);
         __threadfence();
-        const uint32_t arrived = atomicAdd(&C->bar_count, 1u);
-        if (arrived == gridDim.x - 1) {
+        const uint32_t grp = blockIdx.x >> 5;
+        const uint32_t ngroups = (gridDim.x + 31) >> 5;
+        const uint32_t gsize = min(32u, gridDim.x - (grp << 5));
+        bool last = false;
+        if (atomicAdd(&C->bar_group[grp], 1u) == gsize - 1) {
+            atomicExch(&C->bar_group[grp], 0u);
+            last = atomicAdd(&C->bar_count, 1u) == ngroups - 1;
+        }
+        if (last) {
             atomicExch(&C->bar_count, 0u);
             __threadfence();
             st_release_u32(&C->bar_gen, gen + 1);
         } else {
-            // poll with relaxed loads (an acquire per poll would stall the SM's
-            // other warps), back off, and acquire once the generation moved
+            // poll with relaxed loads, back off, acquire once the generation moved
             const long long t0 = clock64();
             uint32_t nap = 64;
             while (ld_relaxed_u32(&C->bar_gen) == gen) {
@@ -306,7 +316,8 @@ __global__ void __launch_bounds__(MTHREADS, 4) k_merge_rounds(Job J)
         if (stamp) C->round_ns[r][0] = globaltimer_ns();
 
         // phase A: the merge-path split of every chunk start
-        for (uint32_t q = blockIdx.x * blockDim.x + tid; q < nch; q += gridDim.x * blockDim.x) {
+        // chunks interleaved over all CTAs, so every CTA searches and none idles
+        for (uint32_t q = tid * gridDim.x + blockIdx.x; q < nch; q += gridDim.x * blockDim.x) {
             const GSorted g = J.gsorted[J.chunk_node[c0 + q]];
             const uint32_t d = (c0 + q - g.chunk_base) * MERGE_E;
             const uint32_t* A = (((g.depth + 1) & 1u) ? J.keysB : J.keysA) + g.goff;

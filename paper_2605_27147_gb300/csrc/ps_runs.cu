@@ -97,6 +97,7 @@ __global__ void __launch_bounds__(1024) k_setup(Job J)
         C->n_total = 0;
         C->hbm_elems = 0;
     }
+    if (threadIdx.x < 32) C->bar_group[threadIdx.x] = 0;
     for (int r = threadIdx.x; r < NPOW + 2; r += blockDim.x) {
         if (r < NPOW)
             for (int i = 0; i < 5; ++i) C->round_ns[r][i] = 0;
