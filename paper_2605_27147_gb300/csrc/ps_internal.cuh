@@ -92,6 +92,7 @@ struct Ctr {
     uint32_t bar_count;
     uint32_t bar_gen;
     uint32_t bar_group[32];            // arrivals per group of 32 CTAs (grids of <= 1024 CTAs)
+    uint32_t chunk_next[NPOW];         // per round: next chunk to hand out (dynamic scheduling)
     uint32_t max_power;
     unsigned long long leaf_moves;
     unsigned long long M_total;

@@ -144,6 +144,7 @@ struct Stage {
     uint32_t* op;
     uint32_t sok, sop;       // output start inside the output staging arrays
     uint32_t cnt;
+    uint32_t last;           // nonzero: no chunk; the round is over for this CTA
 };
 
 constexpr int NCONS = MERGE_BLOCK / 32;          // consumer warps
@@ -302,9 +303,10 @@ __global__ void __launch_bounds__(MTHREADS, 4) k_merge_rounds(Job J)
         fence_mbar_init();
     }
     __syncthreads();
-    // stage use counters (identical in every thread: all walk the same chunks)
+    // stage use counters: the producer fills stages round robin, the consumers
+    // take them in the same order, so both sides keep identical counts
     uint32_t fills[NST] = {0u, 0u}, uses[NST] = {0u, 0u};
-    uint32_t slot = 0;                        // next stage, round robin
+    uint32_t slot = 0;
 
     for (int r = 0; r < NPOW; ++r) {
         if (*(volatile uint32_t*)&C->error) return;
@@ -315,8 +317,8 @@ __global__ void __launch_bounds__(MTHREADS, 4) k_merge_rounds(Job J)
         const bool stamp = blockIdx.x == 0 && tid == 0;
         if (stamp) C->round_ns[r][0] = globaltimer_ns();
 
-        // phase A: the merge-path split of every chunk start
-        // chunks interleaved over all CTAs, so every CTA searches and none idles
+        // phase A: the merge-path split of every chunk start, chunks interleaved
+        // over all CTAs so every CTA searches and none idles
         for (uint32_t q = tid * gridDim.x + blockIdx.x; q < nch; q += gridDim.x * blockDim.x) {
             const GSorted g = J.gsorted[J.chunk_node[c0 + q]];
             const uint32_t d = (c0 + q - g.chunk_base) * MERGE_E;
@@ -327,15 +329,32 @@ __global__ void __launch_bounds__(MTHREADS, 4) k_merge_rounds(Job J)
         if (!grid_barrier(C)) return;
         if (stamp) C->round_ns[r][1] = globaltimer_ns();
 
+        // phase B: chunks handed out dynamically (one atomic per chunk), the
+        // last stage of the round carries no chunk
         if (producer) {
             if (lane == 0) fence_proxy_async_global();   // earlier generic writes before async reads
             __syncwarp();
-            uint32_t sl = slot;
-            for (uint32_t q = blockIdx.x; q < nch; q += gridDim.x) {
-                const int s = (int)sl;
+            for (;;) {
+                uint32_t q = 0;
+                if (lane == 0) q = atomicAdd(&C->chunk_next[r], 1u);
+                q = __shfl_sync(0xffffffffu, q, 0);
+                const int s = (int)slot;
                 if (fills[s] > 0 && !mbar_wait_bounded(&sm.empty[s], (fills[s] - 1) & 1u, C, 44)) return;
                 ++fills[s];
+                slot = (slot + 1) % NST;
+                if (q >= nch) {                       // close the round for the consumers
+                    if (lane == 0) {
+                        sm.st[s].last = 1;
+                        sm.st[s].cnt = 0;
+                        fence_proxy_async_smem();
+                        mbar_arrive_expect_tx(&sm.full[s], 0);
+                        mbar_arrive(&sm.full[s]);
+                    }
+                    __syncwarp();
+                    break;
+                }
                 if (lane == 0) {
+                    sm.st[s].last = 0;
                     describe(J, q, c0, nch, sm.st[s]);
                     issue_loads(sm, s, C);
                 }
@@ -343,15 +362,19 @@ __global__ void __launch_bounds__(MTHREADS, 4) k_merge_rounds(Job J)
                 copy_edge(sm, s, lane);
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&sm.full[s]);
-                sl = (sl + 1) % NST;
             }
         } else {
-            uint32_t sl = slot;
-            for (uint32_t q = blockIdx.x; q < nch; q += gridDim.x) {
-                const int s = (int)sl;
+            for (;;) {
+                const int s = (int)slot;
                 if (!mbar_wait_bounded(&sm.full[s], uses[s] & 1u, C, 42)) return;
                 ++uses[s];
+                slot = (slot + 1) % NST;
                 const Stage& S = sm.st[s];
+                if (S.last) {
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&sm.empty[s]);
+                    break;
+                }
                 const uint32_t na = S.na, nb = S.nb, cnt = S.cnt;
                 uint32_t* const gok = S.ok;
                 uint32_t* const gop = S.op;
@@ -430,7 +453,6 @@ __global__ void __launch_bounds__(MTHREADS, 4) k_merge_rounds(Job J)
                         }
                     }
                 }
-                sl = (sl + 1) % NST;
             }
             if (tid == 0) {
                 bulk_wait_all();                    // this round's output is in global memory
@@ -438,8 +460,6 @@ __global__ void __launch_bounds__(MTHREADS, 4) k_merge_rounds(Job J)
                 if (stamp) C->round_ns[r][2] = globaltimer_ns();
             }
         }
-        // both roles advanced the stage pointer by this CTA's chunk count
-        for (uint32_t q = blockIdx.x; q < nch; q += gridDim.x) slot = (slot + 1) % NST;
         if (producer) {
             for (int s = 0; s < NST; ++s) uses[s] = fills[s];
         } else {

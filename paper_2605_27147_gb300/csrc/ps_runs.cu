@@ -99,8 +99,10 @@ __global__ void __launch_bounds__(1024) k_setup(Job J)
     }
     if (threadIdx.x < 32) C->bar_group[threadIdx.x] = 0;
     for (int r = threadIdx.x; r < NPOW + 2; r += blockDim.x) {
-        if (r < NPOW)
+        if (r < NPOW) {
             for (int i = 0; i < 5; ++i) C->round_ns[r][i] = 0;
+            C->chunk_next[r] = 0;
+        }
         if (r < NPOW + 1) C->bucket_count[r] = 0;
         C->bucket_start[r] = 0;
         C->bucket_chunk[r] = 0;
