@@ -75,7 +75,9 @@ typedef struct ps_config {
     uint32_t tile_log2;  /* on-chip tile capacity 2^tile_log2 in 10..12 (0: 12)      */
     uint32_t pool_pages; /* VM page-pool size in pages (0: chosen by the library)    */
     uint32_t flags;      /* PS_FLAG_* below                                          */
-    uint32_t reserved[3];
+    uint32_t merge_ctas_per_sm; /* CTAs per SM of the HBM merge kernel (0: the most
+                            that fit; a tuning knob, see paper_2605_27147_gb300/autotune.py) */
+    uint32_t reserved[2];
 } ps_config;
 
 /* ps_config.flags */
@@ -125,9 +127,27 @@ PS_API ps_status ps_run(ps_ctx* ctx, uint32_t* d_keys, uint32_t* d_perm, uint64_
 /* The same sort for `count` independent instances in one set of launches.
  * Instance q is d_keys[off[q], off[q+1]) where off = d_offsets (device,
  * count + 1 entries, non-decreasing, off[0] = 0); perm values are local to
- * each instance.  Sizes must respect max_n / max_total / max_count. */
+ * each instance.  count must be <= max_count; the table itself is checked on
+ * the device (each size <= max_n, off[count] <= max_total): a bad table makes
+ * the call sort nothing, and the next synchronising call (stats, ps_sync)
+ * returns PS_EINVAL.  The call never synchronises unless stats is given, so
+ * it can be captured into a CUDA graph (see ps_graph_create_batched). */
 PS_API ps_status ps_run_batched(ps_ctx* ctx, uint32_t* d_keys, uint32_t* d_perm,
                                 const uint64_t* d_offsets, uint32_t count, ps_stats* stats);
+
+/* A batched sort captured once into a CUDA graph and replayed with one
+ * launch (its arrays are fixed at capture time; refill them between
+ * launches).  ps_graph_create_batched captures ps_run_batched(ctx, d_keys,
+ * d_perm, d_offsets, count) on the context's stream (which must not be
+ * capturing already) and instantiates it; ps_graph_launch enqueues one
+ * replay on the context's stream (asynchronous: use ps_sync, or stats
+ * through ps_get_instance_stats); ps_graph_destroy frees it (NULL: no-op).
+ * Phase timing (PS_FLAG_TIMING) is not recorded inside a graph. */
+typedef struct ps_graph ps_graph;
+PS_API ps_status ps_graph_create_batched(ps_ctx* ctx, uint32_t* d_keys, uint32_t* d_perm,
+                                         const uint64_t* d_offsets, uint32_t count, ps_graph** out);
+PS_API ps_status ps_graph_launch(ps_graph* g);
+PS_API void ps_graph_destroy(ps_graph* g);
 
 /* ps_run for host arrays: copies h_keys[0, n) to the device, sorts, and
  * copies the sorted keys (and, if h_perm is not NULL, the permutation) back;

@@ -21,7 +21,8 @@ PS_MODE_PINGPONG, PS_MODE_VM = 0, 1
 EXPORTS = (
     "ps_status_str", "ps_create", "ps_run", "ps_run_batched", "ps_run_host", "ps_sync",
     "ps_get_phase_times", "ps_get_runs", "ps_get_powers", "ps_get_nodes", "ps_get_instance_stats",
-    "ps_destroy", "ps_run_noalloc", "ps_get_round_times",
+    "ps_destroy", "ps_run_noalloc", "ps_get_round_times", "ps_graph_create_batched",
+    "ps_graph_launch", "ps_graph_destroy",
 )
 PS_NOALLOC_MAX_N = 262144
 PS_FLAG_TIMING, PS_FLAG_HOST_IO = 1, 2
@@ -39,7 +40,8 @@ class ps_config(ctypes.Structure):
         ("tile_log2", ctypes.c_uint32),
         ("pool_pages", ctypes.c_uint32),
         ("flags", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint32 * 3),
+        ("merge_ctas_per_sm", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32 * 2),
     ]
 
 
@@ -111,6 +113,12 @@ def lib(build_if_missing: bool = True):
                                          ctypes.POINTER(ctypes.c_uint32)]
         L.ps_sync.restype = ctypes.c_int
         L.ps_sync.argtypes = [vp]
+        L.ps_graph_create_batched.restype = ctypes.c_int
+        L.ps_graph_create_batched.argtypes = [vp, vp, vp, vp, ctypes.c_uint32, ctypes.POINTER(vp)]
+        L.ps_graph_launch.restype = ctypes.c_int
+        L.ps_graph_launch.argtypes = [vp]
+        L.ps_graph_destroy.restype = None
+        L.ps_graph_destroy.argtypes = [vp]
         L.ps_get_runs.restype = ctypes.c_int
         L.ps_get_runs.argtypes = [vp, ctypes.c_uint32, u32p, ctypes.c_uint64, u64p]
         L.ps_get_powers.restype = ctypes.c_int
@@ -148,14 +156,15 @@ class Context:
 
     def __init__(self, max_n: int, *, mode: int = PS_MODE_PINGPONG, want_perm: bool = True,
                  max_total: int = 0, max_count: int = 0, tile_log2: int = 0, page_log2: int = 0,
-                 pool_pages: int = 0, flags: int = 0, device: int = 0, stream=None):
+                 pool_pages: int = 0, flags: int = 0, merge_ctas_per_sm: int = 0, device: int = 0,
+                 stream=None):
         import torch
 
         self.device = device
         self.stream = stream if stream is not None else torch.cuda.current_stream(device)
         cfg = ps_config(mode=mode, want_perm=1 if want_perm else 0, max_n=max_n, max_total=max_total,
                         max_count=max_count, page_log2=page_log2, tile_log2=tile_log2,
-                        pool_pages=pool_pages, flags=flags)
+                        pool_pages=pool_pages, flags=flags, merge_ctas_per_sm=merge_ctas_per_sm)
         h = ctypes.c_void_p()
         _check(lib().ps_create(ctypes.byref(cfg), device, ctypes.c_void_p(self.stream.cuda_stream),
                                ctypes.byref(h)), "ps_create")
@@ -196,6 +205,13 @@ class Context:
         _check(lib().ps_run_batched(self._h, _ptr(keys), _ptr(perm), _ptr(offsets), offsets.numel() - 1,
                                     ctypes.byref(st) if st is not None else None), "ps_run_batched")
         return st.as_dict() if st is not None else None
+
+    def graph_batched(self, keys, offsets, perm=None) -> "Graph":
+        """Capture ps_run_batched on these arrays into a replayable CUDA graph."""
+        h = ctypes.c_void_p()
+        _check(lib().ps_graph_create_batched(self._h, _ptr(keys), _ptr(perm), _ptr(offsets), offsets.numel() - 1,
+                                             ctypes.byref(h)), "ps_graph_create_batched")
+        return Graph(h, self)
 
     def run_host(self, keys_ptr: int, n: int, perm_ptr: int | None = None, *, stats: bool = False):
         """ps_run_host on raw host pointers (e.g. pinned torch tensors' data_ptr())."""
@@ -252,6 +268,28 @@ class Context:
         st = ps_stats()
         _check(lib().ps_get_instance_stats(self._h, q, ctypes.byref(st)), "ps_get_instance_stats")
         return st.as_dict()
+
+
+class Graph:
+    """A captured batched sort (ps_graph); launch() replays it on the context's stream."""
+
+    def __init__(self, handle, ctx):
+        self._h = handle
+        self.ctx = ctx
+
+    def launch(self):
+        _check(lib().ps_graph_launch(self._h), "ps_graph_launch")
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            lib().ps_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def as_u32(t):

@@ -23,6 +23,7 @@ struct ps_ctx {
     size_t scratch_bytes;
     std::vector<void*> allocs;
     bool timing;
+    bool capturing;             // inside ps_graph_create_batched: no events, no syncs
     cudaEvent_t ev[7];          // phase boundaries of the last call (PS_FLAG_TIMING)
     uint32_t* io_keys;          // device arrays of ps_run_host (PS_FLAG_HOST_IO)
     uint32_t* io_perm;
@@ -79,6 +80,7 @@ void free_all(ps_ctx* c)
 
 ps_status from_device_error(uint32_t e)
 {
+    if (e == ps::DERR_INVAL) return PS_EINVAL;
     if (e == ps::DERR_TIMEOUT) return PS_ETIMEOUT;
     if (e != 0) return PS_EINTERNAL;
     return PS_OK;
@@ -87,7 +89,9 @@ ps_status from_device_error(uint32_t e)
 ps_status enqueue(ps_ctx* c, const ps::Job& J)
 {
     cudaStream_t s = c->stream;
-    auto mark = [&](int i) { return !c->timing || cudaEventRecord(c->ev[i], s) == cudaSuccess; };
+    auto mark = [&](int i) {
+        return !c->timing || c->capturing || cudaEventRecord(c->ev[i], s) == cudaSuccess;
+    };
     if (!mark(0)) return PS_ECUDA;
     if (ps::launch_setup(J, s) != cudaSuccess || !mark(1)) return PS_ECUDA;
     if (ps::launch_runs(J, c->grid_runs, s) != cudaSuccess || !mark(2)) return PS_ECUDA;
@@ -224,12 +228,14 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
     c->grid_runs = c->num_sms * 8;
     c->grid_plan = c->num_sms * 8;
     c->grid_tiles = ps::tiles_max_grid(c->num_sms);
-    c->grid_merge = ps::merge_rounds_max_grid(c->num_sms);
+    c->grid_merge = ps::merge_rounds_grid_for(c->num_sms, (int)cfg->merge_ctas_per_sm);
     if (c->grid_merge > 1024) c->grid_merge = 1024;   // the grid barrier's group table
 
     ps::Job& J = c->base;
     std::memset(&J, 0, sizeof(J));
     J.tile_cap = 1u << tile_log2;
+    J.max_n = cfg->max_n;
+    J.max_total = max_total;
     const unsigned long long slot_cap = max_total / 32 + 2ull * c->max_count + 2;
     const unsigned long long chunk_cap = max_total / ps::RUN_CHUNK + c->max_count + 1;
     const unsigned long long entry_cap = slot_cap;
@@ -312,24 +318,7 @@ PS_API ps_status ps_run_batched(ps_ctx* ctx, uint32_t* d_keys, uint32_t* d_perm,
     if (count == 0 || count > ctx->max_count) return PS_EINVAL;
     if (!d_keys) return PS_EINVAL;
     if (d_perm && !ctx->cfg.want_perm) return PS_EINVAL;
-    // the offsets live on the device; their limits are checked there too, but
-    // the host checks them first so a bad table enqueues nothing
-    std::vector<uint64_t> off(count + 1);
-    {
-        DeviceGuard g(ctx->device);
-        if (cudaMemcpyAsync(off.data(), d_offsets, (count + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost,
-                            ctx->stream) != cudaSuccess ||
-            cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
-            cudaGetLastError();
-            return PS_ECUDA;
-        }
-    }
-    if (off[0] != 0) return PS_EINVAL;
-    for (uint32_t i = 0; i < count; ++i) {
-        if (off[i + 1] < off[i]) return PS_EINVAL;
-        if (off[i + 1] - off[i] > ctx->cfg.max_n) return PS_EINVAL;
-    }
-    if (off[count] > ctx->max_total) return PS_EINVAL;
+    // the offsets table lives on the device and is checked there (k_setup)
     return run_common(ctx, d_keys, d_perm, d_offsets, 0, count, stats);
 }
 
@@ -393,6 +382,80 @@ PS_API ps_status ps_get_round_times(ps_ctx* ctx, float* h_us, uint32_t cap, uint
     }
     if (count) *count = k;
     return PS_OK;
+}
+
+}  // extern "C"
+
+struct ps_graph {
+    ps_ctx* ctx;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    uint32_t count;
+};
+
+extern "C" {
+
+PS_API ps_status ps_graph_create_batched(ps_ctx* ctx, uint32_t* d_keys, uint32_t* d_perm,
+                                         const uint64_t* d_offsets, uint32_t count, ps_graph** out)
+{
+    if (!out) return PS_EINVAL;
+    *out = nullptr;
+    if (!ctx || !d_keys || !d_offsets || count == 0 || count > ctx->max_count) return PS_EINVAL;
+    if (d_perm && !ctx->cfg.want_perm) return PS_EINVAL;
+    if (!ctx->stream) return PS_EINVAL;           // the legacy default stream cannot be captured
+    DeviceGuard g(ctx->device);
+    ps_graph* pg = new (std::nothrow) ps_graph();
+    if (!pg) return PS_ENOMEM;
+    pg->ctx = ctx;
+    pg->count = count;
+    if (cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        delete pg;
+        return PS_ECUDA;
+    }
+    ctx->capturing = true;
+    const ps_status st = run_common(ctx, d_keys, d_perm, d_offsets, 0, count, nullptr);
+    ctx->capturing = false;
+    const cudaError_t e = cudaStreamEndCapture(ctx->stream, &pg->graph);
+    if (st != PS_OK || e != cudaSuccess) {
+        cudaGetLastError();
+        if (e == cudaSuccess && pg->graph) cudaGraphDestroy(pg->graph);
+        delete pg;
+        ctx->last_valid = 0;
+        return st != PS_OK ? st : PS_ECUDA;
+    }
+    if (cudaGraphInstantiate(&pg->exec, pg->graph, 0) != cudaSuccess) {
+        cudaGetLastError();
+        cudaGraphDestroy(pg->graph);
+        delete pg;
+        ctx->last_valid = 0;
+        return PS_ECUDA;
+    }
+    ctx->last_valid = 0;                          // nothing ran yet
+    *out = pg;
+    return PS_OK;
+}
+
+PS_API ps_status ps_graph_launch(ps_graph* g)
+{
+    if (!g) return PS_EINVAL;
+    DeviceGuard dg(g->ctx->device);
+    if (cudaGraphLaunch(g->exec, g->ctx->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return PS_ECUDA;
+    }
+    g->ctx->last_valid = 1;
+    g->ctx->last_count = g->count;
+    return PS_OK;
+}
+
+PS_API void ps_graph_destroy(ps_graph* g)
+{
+    if (!g) return;
+    DeviceGuard dg(g->ctx->device);
+    cudaGraphExecDestroy(g->exec);
+    cudaGraphDestroy(g->graph);
+    delete g;
 }
 
 PS_API ps_status ps_sync(ps_ctx* ctx)

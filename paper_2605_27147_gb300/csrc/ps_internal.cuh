@@ -41,6 +41,7 @@ constexpr int NPOW = 33;           // powers are 1..32 for n < 2^32
 constexpr uint32_t NONE = 0xffffffffu;
 
 // device error codes (mirrors ps_status)
+constexpr uint32_t DERR_INVAL = 1;
 constexpr uint32_t DERR_TIMEOUT = 4;
 constexpr uint32_t DERR_INTERNAL = 5;
 
@@ -80,6 +81,7 @@ struct GSorted {
 struct Ctr {
     uint32_t error;
     uint32_t err_where;
+    uint32_t epoch;                    // bumped by every call (chunk status words carry it)
     uint32_t chunk_ticket;
     uint32_t total_chunks;
     unsigned long long total_slots;
@@ -124,6 +126,8 @@ struct Job {
     uint32_t want_perm;
     uint32_t tile_cap;          // T: largest merge-tree node merged on chip
     uint32_t pad0;
+    unsigned long long max_n;   // limits the offsets table is checked against
+    unsigned long long max_total;
     Inst* inst;
     uint32_t* chunk_status;
     uint32_t* chunk_map;        // MAP_STATES per chunk
@@ -276,6 +280,7 @@ __device__ __forceinline__ uint32_t find_inst(uint32_t count, unsigned long long
 // ---------------------------------------------------------------- launchers
 cudaError_t launch_setup(const Job& J, cudaStream_t s);
 cudaError_t launch_runs(const Job& J, int grid, cudaStream_t s);
+int merge_rounds_grid_for(int num_sms, int ctas_per_sm);
 cudaError_t launch_plan(const Job& J, int grid, cudaStream_t s);
 cudaError_t launch_tiles(const Job& J, int grid, cudaStream_t s);
 cudaError_t launch_merge_rounds(const Job& J, int grid, cudaStream_t s);

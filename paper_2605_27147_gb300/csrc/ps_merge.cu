@@ -470,6 +470,13 @@ __global__ void __launch_bounds__(MTHREADS, 4) k_merge_rounds(Job J)
     }
 }
 
+int merge_rounds_grid_for(int num_sms, int ctas_per_sm)
+{
+    const int mx = merge_rounds_max_grid(num_sms) / num_sms;
+    const int k = (ctas_per_sm > 0 && ctas_per_sm < mx) ? ctas_per_sm : mx;
+    return num_sms * k;
+}
+
 int merge_rounds_max_grid(int num_sms)
 {
     int per_sm = 0;

@@ -80,11 +80,15 @@ __global__ void __launch_bounds__(1024) k_setup(Job J)
     __shared__ unsigned long long carry_slots;
     __shared__ uint32_t carry_chunks;
     Ctr* C = J.ctr;
+    __shared__ uint32_t s_bad;
     if (threadIdx.x == 0) {
         carry_slots = 0;
         carry_chunks = 0;
+        s_bad = 0;
         C->error = 0;
         C->err_where = 0;
+        C->epoch = (C->epoch + 1) & 0x3fffffffu;          // never 0: fresh words read "not ready"
+        if (C->epoch == 0) C->epoch = 1;
         C->chunk_ticket = 0;
         C->n_tiles = 0;
         C->n_gnodes = 0;
@@ -115,7 +119,14 @@ __global__ void __launch_bounds__(1024) k_setup(Job J)
         if (valid) {
             if (J.offsets) {
                 off = J.offsets[i];
-                n64 = J.offsets[i + 1] - off;
+                const unsigned long long end = J.offsets[i + 1];
+                // the table must start at 0, never decrease and respect the limits
+                if ((i == 0 && off != 0) || end < off || end - off > J.max_n || end > J.max_total) {
+                    atomicOr(&s_bad, 1u);
+                    n64 = 0;
+                } else {
+                    n64 = end - off;
+                }
             } else {
                 n64 = J.single_n;
             }
@@ -139,7 +150,7 @@ __global__ void __launch_bounds__(1024) k_setup(Job J)
             I.max_power = 0;
             I.runs = n == 0 ? 0u : (n < 64 ? 1u : 0u);
             J.inst[i] = I;
-            if (n < 64) {            // one run [0, n) (or none)
+            if (n < 64 && I.run_base + 1 < J.slot_cap) {   // one run [0, n) (or none)
                 J.run_start[I.run_base] = 0;
                 if (n) J.run_start[I.run_base + 1] = n;
             }
@@ -154,7 +165,8 @@ __global__ void __launch_bounds__(1024) k_setup(Job J)
     if (threadIdx.x == 0) {
         C->total_chunks = carry_chunks;
         C->total_slots = carry_slots;
-        if (carry_chunks > J.chunk_cap || carry_slots > J.slot_cap) set_error(C, DERR_INTERNAL, 1);
+        if (s_bad) set_error(C, DERR_INVAL, 2);
+        else if (carry_chunks > J.chunk_cap || carry_slots > J.slot_cap) set_error(C, DERR_INTERNAL, 1);
     }
 }
 
@@ -177,7 +189,7 @@ __device__ __forceinline__ int next_desc(const uint32_t* bits, int k0, int kmax)
 
 }  // namespace
 
-__global__ void __launch_bounds__(RUN_BLOCK) k_runs(Job J, uint32_t epoch)
+__global__ void __launch_bounds__(RUN_BLOCK) k_runs(Job J)
 {
     __shared__ uint32_t bits[RUN_WORDS];
     __shared__ uint16_t rec[MAP_STATES][RUN_REC];
@@ -186,6 +198,7 @@ __global__ void __launch_bounds__(RUN_BLOCK) k_runs(Job J, uint32_t epoch)
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     Ctr* C = J.ctr;
+    const uint32_t epoch = C->epoch;
     const uint32_t ST_AGG = epoch * 4u + 1u, ST_INC = epoch * 4u + 2u;
     const int KMAX = RUN_WORDS * 32;
     if (*(volatile uint32_t*)&C->error) return;
@@ -392,11 +405,9 @@ cudaError_t launch_setup(const Job& J, cudaStream_t s)
 
 cudaError_t launch_runs(const Job& J, int grid, cudaStream_t s)
 {
-    // the epoch lets chunk status words from earlier calls read as "not ready"
-    static uint32_t epoch = 0;
-    epoch = (epoch + 1) & 0x3fffffffu;
-    if (epoch == 0) epoch = 1;
-    k_runs<<<grid, RUN_BLOCK, 0, s>>>(J, epoch);
+    // the setup kernel bumps the epoch in device memory, so status words left
+    // by earlier calls (or earlier replays of a captured graph) read as "not ready"
+    k_runs<<<grid, RUN_BLOCK, 0, s>>>(J);
     return cudaGetLastError();
 }
 
