@@ -60,7 +60,8 @@ def test_batched_matches_oracle_per_instance(bctx, oracle_mod):
 
 def test_batched_equals_single_instance_calls(bctx):
     rng = np.random.RandomState(7)
-    sizes = np.floor(2.0 ** (8 + 10 * rng.rand(300))).astype(np.int64)
+    # (the context holds at most 2^22 elements per batched call)
+    sizes = np.floor(2.0 ** (8 + 8 * rng.rand(200))).astype(np.int64)   # about 2.4M elements
     keys, off, parts = _batch(sizes, ["uniform", "runs", "zipf"], 5)
     dk, dp = to_dev(keys), torch.empty(keys.size, dtype=torch.int32, device="cuda")
     bctx.run_batched(dk, _dev_offsets(off), dp)
@@ -90,7 +91,7 @@ def test_batched_bad_offsets_rejected_on_device(bctx):
 
 def test_graph_replays_match(bctx, oracle_mod):
     rng = np.random.RandomState(11)
-    sizes = np.floor(2.0 ** (6 + 12 * rng.rand(200))).astype(np.int64)
+    sizes = np.floor(2.0 ** (6 + 10 * rng.rand(200))).astype(np.int64)   # about 1.9M elements
     keys1, off, parts1 = _batch(sizes, ["uniform", "paper"], 21)
     keys2 = np.concatenate([inputs.make("zipf", int(n), 900 + i) for i, n in enumerate(sizes)])
     dk = to_dev(keys1)
