@@ -71,6 +71,7 @@ def test_batched_equals_single_instance_calls(bctx):
         a, b = int(off[q]), int(off[q + 1])
         sk, sp = to_dev(parts[q]), torch.empty(b - a, dtype=torch.int32, device="cuda")
         bctx.run(sk, sp)
+        bctx.sync()                 # the context works on its own stream
         assert np.array_equal(to_host(sk), gk[a:b]) and np.array_equal(to_host(sp), gp[a:b])
 
 
@@ -100,6 +101,7 @@ def test_graph_replays_match(bctx, oracle_mod):
     g = bctx.graph_batched(dk, doff, dp)
     for keys in (keys1, keys2, keys1):
         dk.copy_(to_dev(keys))
+        torch.cuda.synchronize()    # the refill (default stream) before the replay (context stream)
         g.launch()
         bctx.sync()
         gk, gp = to_host(dk), to_host(dp)
