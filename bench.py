@@ -10,6 +10,10 @@ permutation is produced):
                uniform, Zipf(1.1) over 2^20 values, presorted Geometric(mean
                2^10) runs (seed 1)
   hbm_2^28     one step = one single-instance sort of n = 2^28 uniform (seed 2)
+  serving      a Poisson stream of 2000 requests/s for 10 s (sizes log-uniform
+               in [2^10, 2^24], seed 4) through the continuous-batching server
+               under a 64 GB device-memory budget; reports sustained elements/s
+               and p50/p99 latency (--steps/--warmup are not used)
   batched_4096 one step = one replay of a captured CUDA graph sorting 4096
                independent instances with sizes log-uniform in [2^8, 2^20)
                (seed 3, uniform keys), tile size and merge occupancy picked by
@@ -47,6 +51,7 @@ WORKLOADS = {
     "plain_2^24": [("uniform", 1 << 24, 1), ("zipf", 1 << 24, 1), ("runs", 1 << 24, 1)],
     "hbm_2^28": [("uniform", 1 << 28, 2)],
     "batched_4096": None,
+    "serving": None,
 }
 FLUSH_BYTES = 512 << 20
 BYTES_PER_MERGED_ELEM = 16   # key + perm entry read, key + perm entry written
@@ -406,12 +411,104 @@ def run_batched(args):
         dist.destroy_process_group()
 
 
+def run_serving(args, rate=2000.0, duration=10.0, budget=64 << 30):
+    """Workload serving: Poisson arrivals replayed in real time through ps_server."""
+    import torch
+
+    from paper_2605_27147_gb300 import binding, inputs
+
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    arrivals, sizes = inputs.poisson_requests(rate, duration, 4)
+    sizes = sizes.astype(np.int64)
+    max_n = 1 << 24
+    # request inputs: views at varying offsets into a pinned pool of uniform keys
+    pool_n = 1 << 26
+    pool = torch.from_numpy(inputs.uniform(pool_n, 4).view(np.int32)).pin_memory()
+    starts = (np.arange(sizes.size, dtype=np.int64) * 7919 * 1021) % (pool_n - max_n)
+    # results: a ring of pinned memory, slots freed in completion order
+    ring_n = 1 << 29
+    ring_k = torch.empty(ring_n, dtype=torch.int32, pin_memory=True)
+    ring_p = torch.empty(ring_n, dtype=torch.int32, pin_memory=True)
+    pk, pp, pin = ring_k.data_ptr(), ring_p.data_ptr(), pool.data_ptr()
+    srv = binding.Server(budget, max_n, lanes=4, lane_max_count=256, device=local)
+    # warm-up: a few requests (module loading, first launches)
+    for i in range(8):
+        srv.wait(srv.submit(pin, pk, pp, 1 << 20), 60.0)
+    head, tail = 0, 0                   # ring positions (elements, monotone)
+    live = []                           # (ticket, ring start, n) in submission order
+    tickets, slots = [], []
+    t0 = time.perf_counter()
+    with ClockSampler(local) as clk:
+        for i in range(sizes.size):
+            n = int(sizes[i])
+            while time.perf_counter() - t0 < arrivals[i]:
+                pass
+            # free completed slots at the ring's tail; wait if the ring is full
+            while live and (head - tail + n > ring_n):
+                tk, st0, nn = live[0]
+                srv.wait(tk, 60.0)
+                live.pop(0)
+                tail = st0 + nn
+            pos = head % ring_n
+            if pos + n > ring_n:            # do not wrap inside a request
+                head += ring_n - pos
+                pos = 0
+                while live and head - tail + n > ring_n:
+                    tk, st0, nn = live[0]
+                    srv.wait(tk, 60.0)
+                    live.pop(0)
+                    tail = st0 + nn
+            t = srv.submit(pin + 4 * int(starts[i]), pk + 4 * pos, pp + 4 * pos, n)
+            live.append((t, head, n))
+            while live:                     # retire finished heads cheaply
+                done, _ = srv.poll(live[0][0])
+                if not done:
+                    break
+                tk, st0, nn = live.pop(0)
+                tail = st0 + nn
+            head += n
+            tickets.append(t)
+        lat = [srv.wait(t, 120.0) for t in tickets]
+        t_end = time.perf_counter()
+    st = srv.stats()
+    srv.close()
+    lat_ms = np.array(lat) * 1000.0
+    elems = int(sizes.sum())
+    wall = t_end - t0
+    value = elems / wall
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": int(sizes.size), "warmup": 8,
+        "ms_per_step": 1000.0 * wall / sizes.size, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "serving", "arrivals": f"Poisson {rate:.0f}/s for {duration:.0f} s, seed 4",
+                   "sizes": "log-uniform in [2^10, 2^24]", "requests": int(sizes.size),
+                   "offered_elements_per_s": elems / duration, "budget_bytes": budget,
+                   "lanes": st["lanes"], "lane_max_total": st["lane_max_total"],
+                   "device_bytes": st["device_bytes"], "outputs": "sorted keys + stable permutation",
+                   "io": "pinned host arrays in, pinned host arrays out (copies inside every latency)"},
+        "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
+                       "mean": float(lat_ms.mean()), "max": float(lat_ms.max())},
+        "server": st,
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": int(4 * sizes.mean()),
+                "d2h_bytes_per_step": int(8 * sizes.mean()),
+                "api": "ps_server_submit / ps_server_wait on pinned host arrays"},
+        "roofline": None, "cpu_baseline": None, "clocks": clk.summary(),
+        "gpu_launches": 11 * int(st["batches"]),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched_4096":
         return run_batched(args)
+    if args.workload == "serving":
+        return run_serving(args)
 
     import torch
 

@@ -200,6 +200,54 @@ PS_API ps_status ps_get_instance_stats(ps_ctx* ctx, uint32_t q, ps_stats* stats)
 PS_API void ps_destroy(ps_ctx* ctx);
 
 /* ---------------------------------------------------------------------------
+ * Serving: independent sorts of host arrays, continuously batched.  The
+ * server keeps `lanes` batched contexts (each with its own stream and device
+ * arrays, sized so that all lanes together stay within budget_bytes of device
+ * memory).  A dispatcher thread fills every idle lane with queued requests in
+ * arrival order (as many as fit lane_max_total elements and lane_max_count
+ * requests) and enqueues their host->device copies, one batched sort and the
+ * device->host copies of the results; lanes run concurrently, so requests
+ * arriving while others are on the GPU are admitted as lanes free up.
+ * Results are the same stable sort that ps_run computes. */
+typedef struct ps_server ps_server;
+typedef struct ps_server_config {
+    uint64_t budget_bytes;   /* device memory the server may hold                  */
+    uint64_t max_n;          /* largest request, < 2^32                            */
+    uint64_t lane_max_total; /* elements per batch (0: from the budget, <= 2^28)   */
+    uint32_t lane_max_count; /* requests per batch (0: 1024)                       */
+    uint32_t lanes;          /* batches in flight at once (0: 4)                   */
+    uint32_t want_perm;      /* nonzero: requests may ask for the permutation      */
+    uint32_t device;
+    uint32_t reserved[4];
+} ps_server_config;
+
+typedef struct ps_server_stats {
+    uint64_t submitted, completed, failed, elements, batches, queued;
+    uint64_t device_bytes;   /* device memory held by the lanes                    */
+    uint64_t lane_max_total;
+    uint32_t lanes;
+    uint32_t max_busy_lanes; /* most lanes seen busy at once (overlap evidence)    */
+} ps_server_stats;
+
+/* Start a server (allocates every lane up front; PS_ENOMEM if the lanes do not
+ * fit the budget). */
+PS_API ps_status ps_server_create(const ps_server_config* cfg, ps_server** out);
+/* Queue one sort: h_in[0, n) is read (not modified); the sorted keys go to
+ * h_keys_out and, if h_perm_out is not NULL, the stable permutation to
+ * h_perm_out.  All three host arrays must stay valid until the ticket
+ * completes; page-locked memory makes the copies asynchronous. */
+PS_API ps_status ps_server_submit(ps_server* s, const uint32_t* h_in, uint32_t* h_keys_out, uint32_t* h_perm_out,
+                                  uint64_t n, uint64_t* ticket);
+/* *done = 1 once the ticket has completed (its outputs are written);
+ * *latency_s (may be NULL) = seconds from submission to completion. */
+PS_API ps_status ps_server_poll(ps_server* s, uint64_t ticket, int* done, double* latency_s);
+/* Block until the ticket completes (PS_ETIMEOUT after timeout_s seconds). */
+PS_API ps_status ps_server_wait(ps_server* s, uint64_t ticket, double timeout_s, double* latency_s);
+PS_API ps_status ps_server_get_stats(ps_server* s, ps_server_stats* out);
+/* Drain the queue, stop the dispatcher and free every lane. */
+PS_API void ps_server_destroy(ps_server* s);
+
+/* ---------------------------------------------------------------------------
  * Sorting without any device allocation.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc -- code that
  * owns a fixed, pre-sized budget of device memory which a foreign

@@ -22,7 +22,8 @@ EXPORTS = (
     "ps_status_str", "ps_create", "ps_run", "ps_run_batched", "ps_run_host", "ps_sync",
     "ps_get_phase_times", "ps_get_runs", "ps_get_powers", "ps_get_nodes", "ps_get_instance_stats",
     "ps_destroy", "ps_run_noalloc", "ps_get_round_times", "ps_graph_create_batched",
-    "ps_graph_launch", "ps_graph_destroy",
+    "ps_graph_launch", "ps_graph_destroy", "ps_server_create", "ps_server_submit", "ps_server_poll",
+    "ps_server_wait", "ps_server_get_stats", "ps_server_destroy",
 )
 PS_NOALLOC_MAX_N = 262144
 PS_FLAG_TIMING, PS_FLAG_HOST_IO = 1, 2
@@ -62,6 +63,37 @@ class ps_stats(ctypes.Structure):
         ("hbm_merge_elems", ctypes.c_uint64),
         ("launches", ctypes.c_uint32),
         ("pad", ctypes.c_uint32),
+    ]
+
+    def as_dict(self):
+        return {name: int(getattr(self, name)) for name, _ in self._fields_}
+
+
+class ps_server_config(ctypes.Structure):
+    _fields_ = [
+        ("budget_bytes", ctypes.c_uint64),
+        ("max_n", ctypes.c_uint64),
+        ("lane_max_total", ctypes.c_uint64),
+        ("lane_max_count", ctypes.c_uint32),
+        ("lanes", ctypes.c_uint32),
+        ("want_perm", ctypes.c_uint32),
+        ("device", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32 * 4),
+    ]
+
+
+class ps_server_stats(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_uint64),
+        ("completed", ctypes.c_uint64),
+        ("failed", ctypes.c_uint64),
+        ("elements", ctypes.c_uint64),
+        ("batches", ctypes.c_uint64),
+        ("queued", ctypes.c_uint64),
+        ("device_bytes", ctypes.c_uint64),
+        ("lane_max_total", ctypes.c_uint64),
+        ("lanes", ctypes.c_uint32),
+        ("max_busy_lanes", ctypes.c_uint32),
     ]
 
     def as_dict(self):
@@ -119,6 +151,19 @@ def lib(build_if_missing: bool = True):
         L.ps_graph_launch.argtypes = [vp]
         L.ps_graph_destroy.restype = None
         L.ps_graph_destroy.argtypes = [vp]
+        dp = ctypes.POINTER(ctypes.c_double)
+        L.ps_server_create.restype = ctypes.c_int
+        L.ps_server_create.argtypes = [ctypes.POINTER(ps_server_config), ctypes.POINTER(vp)]
+        L.ps_server_submit.restype = ctypes.c_int
+        L.ps_server_submit.argtypes = [vp, vp, vp, vp, ctypes.c_uint64, u64p]
+        L.ps_server_poll.restype = ctypes.c_int
+        L.ps_server_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), dp]
+        L.ps_server_wait.restype = ctypes.c_int
+        L.ps_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_double, dp]
+        L.ps_server_get_stats.restype = ctypes.c_int
+        L.ps_server_get_stats.argtypes = [vp, ctypes.POINTER(ps_server_stats)]
+        L.ps_server_destroy.restype = None
+        L.ps_server_destroy.argtypes = [vp]
         L.ps_get_runs.restype = ctypes.c_int
         L.ps_get_runs.argtypes = [vp, ctypes.c_uint32, u32p, ctypes.c_uint64, u64p]
         L.ps_get_powers.restype = ctypes.c_int
@@ -290,6 +335,58 @@ class Graph:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """ps_server: continuous batching of host-array sorts under a device-memory budget."""
+
+    def __init__(self, budget_bytes: int, max_n: int, *, lanes: int = 0, lane_max_total: int = 0,
+                 lane_max_count: int = 0, want_perm: bool = True, device: int = 0):
+        cfg = ps_server_config(budget_bytes=budget_bytes, max_n=max_n, lane_max_total=lane_max_total,
+                               lane_max_count=lane_max_count, lanes=lanes, want_perm=1 if want_perm else 0,
+                               device=device)
+        h = ctypes.c_void_p()
+        _check(lib().ps_server_create(ctypes.byref(cfg), ctypes.byref(h)), "ps_server_create")
+        self._h = h
+
+    def submit(self, in_ptr: int, keys_out_ptr: int, perm_out_ptr: int | None, n: int) -> int:
+        """Queue a sort of host arrays given by raw pointers; returns the ticket."""
+        t = ctypes.c_uint64()
+        _check(lib().ps_server_submit(self._h, in_ptr, keys_out_ptr, perm_out_ptr, n, ctypes.byref(t)),
+               "ps_server_submit")
+        return t.value
+
+    def poll(self, ticket: int):
+        done, lat = ctypes.c_int(), ctypes.c_double()
+        _check(lib().ps_server_poll(self._h, ticket, ctypes.byref(done), ctypes.byref(lat)), "ps_server_poll")
+        return bool(done.value), lat.value
+
+    def wait(self, ticket: int, timeout_s: float = 60.0) -> float:
+        lat = ctypes.c_double()
+        _check(lib().ps_server_wait(self._h, ticket, timeout_s, ctypes.byref(lat)), "ps_server_wait")
+        return lat.value
+
+    def stats(self) -> dict:
+        st = ps_server_stats()
+        _check(lib().ps_server_get_stats(self._h, ctypes.byref(st)), "ps_server_get_stats")
+        return st.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().ps_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def as_u32(t):

@@ -1,0 +1,369 @@
+// Serving: a request loop that sorts independent host arrays on the GPU with
+// continuous batching under a device-memory budget.
+//
+// The server owns `lanes` lanes; a lane is a batched Powersort context with
+// its own CUDA stream, device input/output arrays and offsets table, sized so
+// that all lanes together stay within the budget.  A dispatcher thread keeps
+// every idle lane busy: it takes queued requests in arrival order while they
+// fit the lane (elements and count), enqueues their host->device copies, one
+// ps_run_batched over the batch and the device->host copies of the sorted
+// keys and permutations, and records an event.  Lanes run concurrently, so a
+// request arriving while other batches are on the GPU is admitted as soon as
+// a lane frees up, and its work overlaps theirs.  A ticket completes when its
+// lane's event has fired; its latency is measured from submission.
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "ps_internal.cuh"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+enum ReqState : int { QUEUED = 0, RUNNING = 1, DONE = 2, FAILED = 3 };
+
+struct Req {
+    const uint32_t* in;
+    uint32_t* kout;
+    uint32_t* pout;
+    uint64_t n;
+    Clock::time_point t_submit;
+    double latency_s;
+    int state;
+    ps_status status;
+};
+
+struct Lane {
+    ps_ctx* ctx = nullptr;
+    cudaStream_t stream = nullptr;
+    uint32_t* dkeys = nullptr;
+    uint32_t* dperm = nullptr;
+    uint64_t* doff = nullptr;
+    uint64_t* hoff = nullptr;       // pinned
+    cudaEvent_t done = nullptr;
+    std::vector<uint64_t> batch;    // tickets in flight
+    std::vector<Req> jobs;          // their arrays, copied under the lock
+    bool busy = false;
+};
+
+constexpr double BYTES_PER_ELEM_ESTIMATE = 18.0;   // caller arrays + scratch + tables, per element
+
+}  // namespace
+
+struct ps_server {
+    ps_server_config cfg;
+    uint64_t lane_total = 0;
+    uint32_t lane_count = 0;
+    std::vector<Lane> lanes;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<uint64_t> queue;
+    std::vector<Req> reqs;
+    std::thread th;
+    bool stop = false;
+    uint64_t bytes = 0;
+    uint64_t completed = 0, elements = 0, batches = 0, failed = 0;
+    uint32_t max_in_flight_lanes = 0;
+};
+
+namespace {
+
+void lane_free(Lane& L)
+{
+    if (L.ctx) ps_destroy(L.ctx);
+    if (L.dkeys) cudaFree(L.dkeys);
+    if (L.dperm) cudaFree(L.dperm);
+    if (L.doff) cudaFree(L.doff);
+    if (L.hoff) cudaFreeHost(L.hoff);
+    if (L.done) cudaEventDestroy(L.done);
+    if (L.stream) cudaStreamDestroy(L.stream);
+    L = Lane{};
+}
+
+// Enqueue one batch on a lane (no lock held; the tickets are RUNNING).
+ps_status launch_batch(ps_server* S, Lane& L)
+{
+    const size_t k = L.jobs.size();
+    uint64_t acc = 0;
+    L.hoff[0] = 0;
+    for (size_t i = 0; i < k; ++i) {
+        acc += L.jobs[i].n;
+        L.hoff[i + 1] = acc;
+    }
+    if (cudaMemcpyAsync(L.doff, L.hoff, (k + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice, L.stream) != cudaSuccess)
+        return PS_ECUDA;
+    for (size_t i = 0; i < k; ++i) {
+        const Req& r = L.jobs[i];
+        if (r.n && cudaMemcpyAsync(L.dkeys + L.hoff[i], r.in, r.n * 4, cudaMemcpyHostToDevice, L.stream) != cudaSuccess)
+            return PS_ECUDA;
+    }
+    const ps_status st = ps_run_batched(L.ctx, L.dkeys, S->cfg.want_perm ? L.dperm : nullptr, L.doff, (uint32_t)k, nullptr);
+    if (st != PS_OK) return st;
+    for (size_t i = 0; i < k; ++i) {
+        const Req& r = L.jobs[i];
+        if (!r.n) continue;
+        if (cudaMemcpyAsync(r.kout, L.dkeys + L.hoff[i], r.n * 4, cudaMemcpyDeviceToHost, L.stream) != cudaSuccess)
+            return PS_ECUDA;
+        if (r.pout && S->cfg.want_perm &&
+            cudaMemcpyAsync(r.pout, L.dperm + L.hoff[i], r.n * 4, cudaMemcpyDeviceToHost, L.stream) != cudaSuccess)
+            return PS_ECUDA;
+    }
+    if (cudaEventRecord(L.done, L.stream) != cudaSuccess) return PS_ECUDA;
+    return PS_OK;
+}
+
+void dispatcher(ps_server* S)
+{
+    cudaSetDevice((int)S->cfg.device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    for (;;) {
+        bool progress = false;
+        // completions
+        for (Lane& L : S->lanes) {
+            if (!L.busy) continue;
+            const cudaError_t q = cudaEventQuery(L.done);
+            if (q == cudaErrorNotReady) continue;
+            ps_status st = q == cudaSuccess ? PS_OK : PS_ECUDA;
+            if (st == PS_OK) {
+                lk.unlock();
+                st = ps_sync(L.ctx);            // device-side status of the batch
+                lk.lock();
+            } else {
+                cudaGetLastError();
+            }
+            const auto now = Clock::now();
+            for (uint64_t t : L.batch) {
+                Req& r = S->reqs[t];
+                r.latency_s = std::chrono::duration<double>(now - r.t_submit).count();
+                r.state = st == PS_OK ? DONE : FAILED;
+                r.status = st;
+                if (st == PS_OK) {
+                    ++S->completed;
+                    S->elements += r.n;
+                } else {
+                    ++S->failed;
+                }
+            }
+            L.batch.clear();
+            L.jobs.clear();
+            L.busy = false;
+            progress = true;
+        }
+        if (progress) S->cv_done.notify_all();
+        // admissions: fill idle lanes from the queue head (arrival order)
+        for (Lane& L : S->lanes) {
+            if (L.busy || S->queue.empty()) continue;
+            uint64_t total = 0;
+            while (!S->queue.empty() && L.batch.size() < S->lane_count) {
+                const uint64_t t = S->queue.front();
+                const uint64_t n = S->reqs[t].n;
+                if (total + n > S->lane_total && !L.batch.empty()) break;
+                S->queue.pop_front();
+                S->reqs[t].state = RUNNING;
+                L.batch.push_back(t);
+                L.jobs.push_back(S->reqs[t]);
+                total += n;
+            }
+            if (L.batch.empty()) continue;
+            L.busy = true;
+            ++S->batches;
+            lk.unlock();
+            const ps_status st = launch_batch(S, L);
+            lk.lock();
+            if (st != PS_OK) {             // nothing in flight: fail the batch now
+                cudaStreamSynchronize(L.stream);
+                cudaGetLastError();
+                for (uint64_t t : L.batch) {
+                    S->reqs[t].state = FAILED;
+                    S->reqs[t].status = st;
+                    ++S->failed;
+                }
+                L.batch.clear();
+                L.jobs.clear();
+                L.busy = false;
+                S->cv_done.notify_all();
+            }
+            progress = true;
+        }
+        uint32_t busy = 0;
+        for (const Lane& L : S->lanes) busy += L.busy ? 1u : 0u;
+        if (busy > S->max_in_flight_lanes) S->max_in_flight_lanes = busy;
+        if (S->stop && S->queue.empty() && busy == 0) break;
+        if (!progress) {
+            // nothing changed: sleep until a submission, or poll the events again
+            S->cv_work.wait_for(lk, std::chrono::microseconds(busy ? 20 : 2000));
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+PS_API ps_status ps_server_create(const ps_server_config* cfg, ps_server** out)
+{
+    if (!out) return PS_EINVAL;
+    *out = nullptr;
+    if (!cfg || cfg->max_n == 0 || cfg->max_n > 0xffffffffull || cfg->budget_bytes == 0) return PS_EINVAL;
+    ps_server* S = new (std::nothrow) ps_server();
+    if (!S) return PS_ENOMEM;
+    S->cfg = *cfg;
+    if (!S->cfg.lanes) S->cfg.lanes = 4;
+    S->lane_count = S->cfg.lane_max_count ? S->cfg.lane_max_count : 1024;
+    uint64_t lane_total = S->cfg.lane_max_total;
+    if (!lane_total) {
+        lane_total = (uint64_t)((double)S->cfg.budget_bytes / S->cfg.lanes / BYTES_PER_ELEM_ESTIMATE);
+        if (lane_total > (1ull << 28)) lane_total = 1ull << 28;
+    }
+    if (lane_total < S->cfg.max_n) lane_total = S->cfg.max_n;
+    S->lane_total = lane_total;
+    if ((double)lane_total * BYTES_PER_ELEM_ESTIMATE * S->cfg.lanes > (double)S->cfg.budget_bytes) {
+        delete S;                               // the lanes cannot fit: allocate nothing
+        return PS_ENOMEM;
+    }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (cudaSetDevice((int)S->cfg.device) != cudaSuccess) {
+        cudaGetLastError();
+        delete S;
+        return PS_ECUDA;
+    }
+    ps_status st = PS_OK;
+    S->lanes.resize(S->cfg.lanes);
+    for (Lane& L : S->lanes) {
+        if (cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) != cudaSuccess) {
+            st = PS_ECUDA;
+            break;
+        }
+        if (cudaMalloc(&L.dkeys, lane_total * 4) != cudaSuccess ||
+            (S->cfg.want_perm && cudaMalloc(&L.dperm, lane_total * 4) != cudaSuccess) ||
+            cudaMalloc(&L.doff, (S->lane_count + 1) * sizeof(uint64_t)) != cudaSuccess ||
+            cudaMallocHost(&L.hoff, (S->lane_count + 1) * sizeof(uint64_t)) != cudaSuccess) {
+            st = PS_ENOMEM;
+            break;
+        }
+        ps_config c;
+        std::memset(&c, 0, sizeof(c));
+        c.mode = PS_MODE_PINGPONG;
+        c.want_perm = S->cfg.want_perm;
+        c.max_n = S->cfg.max_n;
+        c.max_total = lane_total;
+        c.max_count = S->lane_count;
+        st = ps_create(&c, (int)S->cfg.device, L.stream, &L.ctx);
+        if (st != PS_OK) break;
+        S->bytes += lane_total * 4 * (S->cfg.want_perm ? 2 : 1) + (S->lane_count + 1) * sizeof(uint64_t);
+        // the context reports its own device memory through the stats of a call;
+        // an empty sort would need a kernel, so use the allocation estimate here
+        S->bytes += (uint64_t)(lane_total * (BYTES_PER_ELEM_ESTIMATE - 8.0));
+    }
+    if (st == PS_OK && S->bytes > S->cfg.budget_bytes) st = PS_ENOMEM;
+    if (st != PS_OK) {
+        cudaGetLastError();
+        for (Lane& L : S->lanes) lane_free(L);
+        if (prev >= 0) cudaSetDevice(prev);
+        delete S;
+        return st;
+    }
+    S->reqs.reserve(1 << 16);
+    S->th = std::thread(dispatcher, S);
+    if (prev >= 0) cudaSetDevice(prev);
+    *out = S;
+    return PS_OK;
+}
+
+PS_API ps_status ps_server_submit(ps_server* S, const uint32_t* h_in, uint32_t* h_keys_out, uint32_t* h_perm_out,
+                                  uint64_t n, uint64_t* ticket)
+{
+    if (!S || !ticket || (n && (!h_in || !h_keys_out))) return PS_EINVAL;
+    if (n > S->cfg.max_n) return PS_EINVAL;
+    if (h_perm_out && !S->cfg.want_perm) return PS_EINVAL;
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->stop) return PS_EINVAL;
+    Req r;
+    r.in = h_in;
+    r.kout = h_keys_out;
+    r.pout = h_perm_out;
+    r.n = n;
+    r.t_submit = Clock::now();
+    r.latency_s = 0.0;
+    r.state = QUEUED;
+    r.status = PS_OK;
+    *ticket = S->reqs.size();
+    S->reqs.push_back(r);
+    S->queue.push_back(*ticket);
+    S->cv_work.notify_one();
+    return PS_OK;
+}
+
+PS_API ps_status ps_server_poll(ps_server* S, uint64_t ticket, int* done, double* latency_s)
+{
+    if (!S || !done) return PS_EINVAL;
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (ticket >= S->reqs.size()) return PS_EINVAL;
+    const Req& r = S->reqs[ticket];
+    *done = r.state == DONE || r.state == FAILED;
+    if (latency_s) *latency_s = r.latency_s;
+    return r.state == FAILED ? r.status : PS_OK;
+}
+
+PS_API ps_status ps_server_wait(ps_server* S, uint64_t ticket, double timeout_s, double* latency_s)
+{
+    if (!S) return PS_EINVAL;
+    std::unique_lock<std::mutex> lk(S->mu);
+    if (ticket >= S->reqs.size()) return PS_EINVAL;
+    const auto until = Clock::now() + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(timeout_s));
+    while (S->reqs[ticket].state != DONE && S->reqs[ticket].state != FAILED) {
+        if (S->cv_done.wait_until(lk, until) == std::cv_status::timeout &&
+            S->reqs[ticket].state != DONE && S->reqs[ticket].state != FAILED)
+            return PS_ETIMEOUT;
+    }
+    if (latency_s) *latency_s = S->reqs[ticket].latency_s;
+    return S->reqs[ticket].state == FAILED ? S->reqs[ticket].status : PS_OK;
+}
+
+PS_API ps_status ps_server_get_stats(ps_server* S, ps_server_stats* st)
+{
+    if (!S || !st) return PS_EINVAL;
+    std::lock_guard<std::mutex> lk(S->mu);
+    std::memset(st, 0, sizeof(*st));
+    st->submitted = S->reqs.size();
+    st->completed = S->completed;
+    st->failed = S->failed;
+    st->elements = S->elements;
+    st->batches = S->batches;
+    st->queued = S->queue.size();
+    st->device_bytes = S->bytes;
+    st->lane_max_total = S->lane_total;
+    st->lanes = (uint32_t)S->lanes.size();
+    st->max_busy_lanes = S->max_in_flight_lanes;
+    return PS_OK;
+}
+
+PS_API void ps_server_destroy(ps_server* S)
+{
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+        S->cv_work.notify_all();
+    }
+    if (S->th.joinable()) S->th.join();
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice((int)S->cfg.device);
+    for (Lane& L : S->lanes) {
+        if (L.stream) cudaStreamSynchronize(L.stream);
+        lane_free(L);
+    }
+    if (prev >= 0) cudaSetDevice(prev);
+    delete S;
+}
+
+}  // extern "C"

@@ -1,0 +1,79 @@
+"""Serving: continuous batching under a device-memory budget.  Every request's
+result must be the same alone (ps_run) and in the mix, and requests that
+arrive while others are on the GPU must be admitted and overlap with them."""
+import time
+
+import numpy as np
+import pytest
+
+from gpu_util import to_dev, to_host
+from paper_2605_27147_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+
+def _pinned(a: np.ndarray):
+    t = torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).pin_memory()
+    return t
+
+
+def test_results_same_alone_and_in_the_mix(oracle_mod):
+    from paper_2605_27147_gb300 import binding
+
+    rng = np.random.RandomState(4)
+    dists = ["uniform", "zipf", "runs", "paper", "few", "sorted"]
+    sizes = [int(x) for x in np.floor(2.0 ** (6 + 14 * rng.rand(90)))] + [0, 1, 63, 64, 65]
+    reqs = []
+    for i, n in enumerate(sizes):
+        keys = inputs.make(dists[i % len(dists)], n, 1000 + i)
+        reqs.append((keys, _pinned(keys), torch.empty(n, dtype=torch.int32).pin_memory(),
+                     torch.empty(n, dtype=torch.int32).pin_memory()))
+    with binding.Server(2 << 30, 1 << 20, lanes=3, lane_max_total=1 << 21, lane_max_count=8) as srv:
+        tickets = []
+        for wave in range(3):                       # later waves arrive while earlier ones run
+            for k in range(wave, len(reqs), 3):
+                keys, hin, hk, hp = reqs[k]
+                tickets.append((k, srv.submit(hin.data_ptr(), hk.data_ptr(), hp.data_ptr(), keys.size)))
+            time.sleep(0.002)
+        lat = [srv.wait(t, 120.0) for _, t in tickets]
+        st = srv.stats()
+    assert st["completed"] == len(reqs) and st["failed"] == 0
+    assert st["batches"] > 3
+    assert st["max_busy_lanes"] >= 2, st            # batches were on the GPU together
+    assert all(x >= 0 for x in lat)
+    with binding.Context(1 << 20, want_perm=True) as solo:
+        for k, (keys, hin, hk, hp) in enumerate(reqs):
+            n = keys.size
+            got_k = hk.numpy().view(np.uint32)[:n]
+            got_p = hp.numpy().view(np.uint32)[:n]
+            dk, dp = to_dev(keys), torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+            if n:
+                solo.run(dk, dp[:n])
+                solo.sync()
+            assert np.array_equal(got_k, to_host(dk)[:n]), k
+            assert np.array_equal(got_p, to_host(dp)[:n]), k
+            if k % 10 == 0:
+                ref = oracle_mod.powersort(keys)
+                assert np.array_equal(got_k, ref.keys) and np.array_equal(got_p, ref.perm)
+
+
+def test_server_rejects_oversized_requests():
+    from paper_2605_27147_gb300 import binding
+
+    with binding.Server(1 << 30, 1 << 16, lanes=1, lane_max_total=1 << 16) as srv:
+        a = torch.zeros(1 << 17, dtype=torch.int32).pin_memory()
+        with pytest.raises(binding.PowersortError) as e:
+            srv.submit(a.data_ptr(), a.data_ptr(), None, 1 << 17)
+        assert e.value.status == binding.PS_EINVAL
+
+
+def test_server_budget_too_small():
+    from paper_2605_27147_gb300 import binding
+
+    with pytest.raises(binding.PowersortError) as e:
+        binding.Server(1 << 20, 1 << 20, lanes=2, lane_max_total=1 << 20)
+    assert e.value.status == binding.PS_ENOMEM
