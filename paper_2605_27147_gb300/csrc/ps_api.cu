@@ -1,5 +1,6 @@
 // C ABI of the library (include/powersort.h): argument checks, the context
 // with every device buffer allocated up front, and the launch sequence.
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -12,7 +13,7 @@ struct ps_ctx {
     int device;
     cudaStream_t stream;
     int num_sms;
-    int grid_runs, grid_plan, grid_tiles, grid_merge;
+    int grid_runs, grid_plan, grid_tiles, grid_merge, grid_vm;
     unsigned long long max_total;
     uint32_t max_count;
     ps::Job base;               // device buffers; per-call fields filled by each run
@@ -97,7 +98,11 @@ ps_status enqueue(ps_ctx* c, const ps::Job& J)
     if (ps::launch_runs(J, c->grid_runs, s) != cudaSuccess || !mark(2)) return PS_ECUDA;
     if (ps::launch_plan(J, c->grid_plan, s) != cudaSuccess || !mark(3)) return PS_ECUDA;
     if (ps::launch_tiles(J, c->grid_tiles, s) != cudaSuccess || !mark(4)) return PS_ECUDA;
-    if (ps::launch_merge_rounds(J, c->grid_merge, s) != cudaSuccess || !mark(5)) return PS_ECUDA;
+    if (J.vm) {
+        if (ps::launch_vm(J, c->grid_vm, s) != cudaSuccess || !mark(5)) return PS_ECUDA;
+    } else {
+        if (ps::launch_merge_rounds(J, c->grid_merge, s) != cudaSuccess || !mark(5)) return PS_ECUDA;
+    }
     if (ps::launch_finish(J, s) != cudaSuccess || !mark(6)) return PS_ECUDA;
     if (cudaMemcpyAsync(c->h_ctr, J.ctr, sizeof(ps::Ctr), cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return PS_ECUDA;
@@ -124,7 +129,7 @@ void fill_stats(const ps_ctx* c, ps_stats* st, uint32_t count)
     st->global_nodes = h->n_gnodes;
     st->leaf_moves = h->leaf_moves;
     st->scratch_bytes = c->scratch_bytes;
-    st->peak_pages = 0;
+    st->peak_pages = c->base.vm ? h->vm_in_use_peak : 0;
     st->max_power = h->max_power;
     st->rounds = h->rounds;
     st->instances = count;
@@ -140,7 +145,11 @@ ps_status run_common(ps_ctx* c, uint32_t* d_keys, uint32_t* d_perm, const uint64
     J.keysA = d_keys;
     J.permA = d_perm;
     J.want_perm = d_perm ? 1u : 0u;
-    if (!d_perm) J.permB = nullptr;
+    if (!d_perm) {
+        J.permB = nullptr;
+        J.permA = nullptr;
+    }
+    if (J.vm) J.vm_na = (uint32_t)((single_n + (1ull << J.vm_plog2) - 1) >> J.vm_plog2);
     J.offsets = reinterpret_cast<const unsigned long long*>(d_offsets);
     J.single_n = single_n;
     J.count = count;
@@ -196,7 +205,8 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
     if (!out) return PS_EINVAL;
     *out = nullptr;
     if (!cfg) return PS_EINVAL;
-    if (cfg->mode != PS_MODE_PINGPONG) return PS_EINVAL;
+    if (cfg->mode != PS_MODE_PINGPONG && cfg->mode != PS_MODE_VM) return PS_EINVAL;
+    if (cfg->mode == PS_MODE_VM && cfg->max_count > 1) return PS_EINVAL;   // VM storage: one instance per call
     if (cfg->max_n == 0 || cfg->max_n > LIMIT_N) return PS_EINVAL;
     const unsigned long long max_total = cfg->max_total ? cfg->max_total : cfg->max_n;
     if (max_total < cfg->max_n || max_total > LIMIT_N) return PS_EINVAL;
@@ -229,6 +239,8 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
     c->grid_plan = c->num_sms * 8;
     c->grid_tiles = ps::tiles_max_grid(c->num_sms);
     c->grid_merge = ps::merge_rounds_grid_for(c->num_sms, (int)cfg->merge_ctas_per_sm);
+    c->grid_vm = ps::vm_rounds_max_grid(c->num_sms);
+    if (c->grid_vm > 1024) c->grid_vm = 1024;
     if (c->grid_merge > 1024) c->grid_merge = 1024;   // the grid barrier's group table
 
     ps::Job& J = c->base;
@@ -254,8 +266,41 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
     J.chunk_node_cap = (uint32_t)chunk_node_cap;
 
     ps_status st = PS_OK;
-    if (st == PS_OK) st = dev_alloc(c, &J.keysB, max_total);
-    if (st == PS_OK && cfg->want_perm) st = dev_alloc(c, &J.permB, max_total);
+    const bool vm = cfg->mode == PS_MODE_VM;
+    if (vm) {
+        // page size: sqrt(n / log2 n) rounded to a power of two (Sec. 4), at most
+        // the tile size (so a page meets at most two HBM merges), at least 2^8
+        uint32_t plog2 = cfg->page_log2;
+        if (!plog2) {
+            const double nn = (double)cfg->max_n > 4.0 ? (double)cfg->max_n : 4.0;
+            plog2 = (uint32_t)std::lround(std::log2(std::sqrt(nn / std::log2(nn))));
+        }
+        if (plog2 < 8) plog2 = 8;
+        if (plog2 > tile_log2) plog2 = tile_log2;
+        J.vm = 1;
+        J.vm_plog2 = plog2;
+        J.vm_na_cap = (uint32_t)((cfg->max_n + (1ull << plog2) - 1) >> plog2);
+        J.vm_wave_max = (uint32_t)(2 * c->grid_vm);
+        J.vm_pool = cfg->pool_pages ? cfg->pool_pages : J.vm_wave_max + 64;
+        if (J.vm_pool < 8) J.vm_pool = 8;
+        const size_t P = (size_t)1 << plog2;
+        if (st == PS_OK) st = dev_alloc(c, &J.pool_keys, (size_t)J.vm_pool * P);
+        if (st == PS_OK && cfg->want_perm) st = dev_alloc(c, &J.pool_perm, (size_t)J.vm_pool * P);
+        if (st == PS_OK) st = dev_alloc(c, &J.pt, J.vm_na_cap);
+        if (st == PS_OK) st = dev_alloc(c, &J.pt_new, J.vm_na_cap);
+        if (st == PS_OK) st = dev_alloc(c, &J.page_cnt, J.vm_na_cap);
+        if (st == PS_OK) st = dev_alloc(c, &J.page_nodes, 2ull * J.vm_na_cap);
+        if (st == PS_OK) st = dev_alloc(c, &J.consumed, J.vm_na_cap);
+        if (st == PS_OK) st = dev_alloc(c, &J.touched, J.vm_na_cap);
+        if (st == PS_OK) st = dev_alloc(c, &J.free_stack, (size_t)J.vm_na_cap + J.vm_pool);
+        if (st == PS_OK) st = dev_alloc(c, &J.holder, (size_t)J.vm_na_cap + J.vm_pool);
+        if (st == PS_OK) st = dev_alloc(c, &J.front, entry_cap);
+        if (st == PS_OK) st = dev_alloc(c, &J.wave_front, 2ull * J.vm_wave_max);
+        if (st == PS_OK) st = dev_alloc(c, &J.wave_node, 2ull * J.vm_wave_max);
+    } else {
+        if (st == PS_OK) st = dev_alloc(c, &J.keysB, max_total);
+        if (st == PS_OK && cfg->want_perm) st = dev_alloc(c, &J.permB, max_total);
+    }
     if (st == PS_OK) st = dev_alloc(c, &J.inst, c->max_count);
     if (st == PS_OK) st = dev_alloc(c, &J.chunk_status, chunk_cap);
     if (st == PS_OK) st = dev_alloc(c, &J.chunk_map, chunk_cap * ps::MAP_STATES);
@@ -287,9 +332,10 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
         st = PS_ECUDA;
     if (st == PS_OK && cudaDeviceSynchronize() != cudaSuccess) st = PS_ECUDA;
     // every table the kernels write must exist (permB only with want_perm)
-    if (st == PS_OK && (!J.keysB || !J.inst || !J.chunk_status || !J.chunk_map || !J.chunk_incl ||
+    if (st == PS_OK && ((!vm && !J.keysB) || !J.inst || !J.chunk_status || !J.chunk_map || !J.chunk_incl ||
                         !J.run_start || !J.kappa || !J.power || !J.na || !J.nb || !J.tiles || !J.gnodes ||
-                        !J.gsorted || !J.splits || !J.chunk_node || !J.ctr || (cfg->want_perm && !J.permB)))
+                        !J.gsorted || !J.splits || !J.chunk_node || !J.ctr ||
+                        (!vm && cfg->want_perm && !J.permB) || (vm && (!J.pool_keys || !J.pt || !J.front))))
         st = PS_EINTERNAL;
     if (st != PS_OK) {
         cudaGetLastError();
@@ -315,6 +361,7 @@ PS_API ps_status ps_run_batched(ps_ctx* ctx, uint32_t* d_keys, uint32_t* d_perm,
                                 uint32_t count, ps_stats* stats)
 {
     if (!ctx || !d_offsets) return PS_EINVAL;
+    if (ctx->base.vm) return PS_EINVAL;          // VM storage sorts one instance per call
     if (count == 0 || count > ctx->max_count) return PS_EINVAL;
     if (!d_keys) return PS_EINVAL;
     if (d_perm && !ctx->cfg.want_perm) return PS_EINVAL;
@@ -401,6 +448,7 @@ PS_API ps_status ps_graph_create_batched(ps_ctx* ctx, uint32_t* d_keys, uint32_t
     if (!out) return PS_EINVAL;
     *out = nullptr;
     if (!ctx || !d_keys || !d_offsets || count == 0 || count > ctx->max_count) return PS_EINVAL;
+    if (ctx->base.vm) return PS_EINVAL;          // VM storage sorts one instance per call
     if (d_perm && !ctx->cfg.want_perm) return PS_EINVAL;
     if (!ctx->stream) return PS_EINVAL;           // the legacy default stream cannot be captured
     DeviceGuard g(ctx->device);

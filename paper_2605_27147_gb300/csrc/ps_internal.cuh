@@ -95,6 +95,13 @@ struct Ctr {
     uint32_t bar_gen;
     uint32_t bar_group[32];            // arrivals per group of 32 CTAs (grids of <= 1024 CTAs)
     uint32_t chunk_next[NPOW];         // per round: next chunk to hand out (dynamic scheduling)
+    // virtual-memory storage
+    uint32_t vm_free_top;              // entries on the free-page stack
+    uint32_t vm_touched;               // pages written by the current round
+    uint32_t vm_wave;                  // pages in the current wave
+    uint32_t vm_in_use_peak;           // most physical pages holding data at once
+    uint32_t vm_waves;                 // waves run by the call
+    uint32_t vm_copy_moves;            // page copies made by the final Copy
     uint32_t max_power;
     unsigned long long leaf_moves;
     unsigned long long M_total;
@@ -148,6 +155,26 @@ struct Job {
     uint32_t entry_cap;         // capacity of tiles / gnodes / gsorted
     uint32_t split_cap;
     uint32_t chunk_node_cap;
+    // virtual-memory storage (Sec. 4): pages of P = 2^vm_plog2 elements
+    uint32_t vm;                // nonzero: VM storage instead of Pingpong
+    uint32_t vm_plog2;
+    uint32_t vm_na;             // virtual pages of the instance: ceil(n / P) (set per call)
+    uint32_t vm_na_cap;         // capacity of the page tables
+    uint32_t vm_pool;           // pool pages (physical pages vm_na_cap .. vm_na_cap + pool)
+    uint32_t vm_wave_max;       // output pages per wave
+    uint32_t* pool_keys;        // pool pages, P keys each
+    uint32_t* pool_perm;
+    uint32_t* pt;               // virtual page -> physical page
+    uint32_t* pt_new;           // the page written for it by the current round
+    uint32_t* page_cnt;         // merges of the current round touching the page
+    uint32_t* page_nodes;       // 2 per page: those merges (GSorted index)
+    uint32_t* consumed;         // elements of the page consumed by the current round
+    uint32_t* touched;          // the round's written pages, in order
+    uint32_t* free_stack;       // free physical pages
+    uint32_t* holder;           // physical page -> virtual page it holds (final Copy)
+    unsigned long long* front;  // per merge: (outputs done << 32) | left elements consumed
+    unsigned long long* wave_front;  // 2 per wave page: new fronts of the merges it advanced
+    uint32_t* wave_node;        // 2 per wave page: those merges (NONE: none)
 };
 
 // ---------------------------------------------------------------- helpers
@@ -285,6 +312,8 @@ cudaError_t launch_plan(const Job& J, int grid, cudaStream_t s);
 cudaError_t launch_tiles(const Job& J, int grid, cudaStream_t s);
 cudaError_t launch_merge_rounds(const Job& J, int grid, cudaStream_t s);
 cudaError_t launch_finish(const Job& J, cudaStream_t s);
+cudaError_t launch_vm(const Job& J, int grid, cudaStream_t s);
+int vm_rounds_max_grid(int num_sms);
 int merge_rounds_max_grid(int num_sms);
 int tiles_max_grid(int num_sms);
 

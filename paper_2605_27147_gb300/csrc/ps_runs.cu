@@ -162,6 +162,26 @@ __global__ void __launch_bounds__(1024) k_setup(Job J)
         }
         __syncthreads();
     }
+    if (J.vm) {
+        // virtual-memory storage: every virtual page starts as its own array page,
+        // the free stack holds the pool pages
+        const uint32_t na = J.single_n ? (uint32_t)((J.single_n + (1ull << J.vm_plog2) - 1) >> J.vm_plog2) : 0u;
+        for (uint32_t u = threadIdx.x; u < J.vm_na_cap; u += blockDim.x) {
+            J.pt[u] = u;
+            J.page_cnt[u] = 0;
+            J.consumed[u] = 0;
+        }
+        for (uint32_t i = threadIdx.x; i < J.vm_pool; i += blockDim.x) J.free_stack[i] = J.vm_na_cap + i;
+        if (threadIdx.x == 0) {
+            C->vm_free_top = J.vm_pool;
+            C->vm_touched = 0;
+            C->vm_wave = 0;
+            C->vm_in_use_peak = 0;
+            C->vm_waves = 0;
+            C->vm_copy_moves = 0;
+            if (na > J.vm_na_cap) set_error(C, DERR_INTERNAL, 3);
+        }
+    }
     if (threadIdx.x == 0) {
         C->total_chunks = carry_chunks;
         C->total_slots = carry_slots;

@@ -57,7 +57,8 @@ __global__ void __launch_bounds__(TILE_BLOCK) k_tiles(Job J)
         const uint32_t* rs = J.run_start + I.run_base;
         const uint32_t lo = rs[it.r0], hi = rs[it.r1];
         const uint32_t size = hi - lo;
-        const bool to_scratch = (it.depth & 1u) != 0;
+        // Pingpong: buffer of the subtree root's depth parity; VM storage: in place
+        const bool to_scratch = !J.vm && (it.depth & 1u) != 0;
         uint32_t* kdst = (to_scratch ? J.keysB : J.keysA) + I.off + lo;
         uint32_t* pdst = J.want_perm ? (to_scratch ? J.permB : J.permA) + I.off + lo : nullptr;
         const uint32_t* ksrc = J.keysA + I.off + lo;

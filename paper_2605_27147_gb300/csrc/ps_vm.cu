@@ -1,0 +1,475 @@
+// Virtual-memory storage (Sec. 4): the HBM merges without an n-element
+// scratch buffer.
+//
+// The instance's index range is cut into virtual pages of P = 2^plog2
+// elements.  A page table maps every virtual page to a physical page: one of
+// the caller's array pages (physical id < vm_na_cap) or a page of a small
+// pool (the rest).  The tiles are merged in place, so at first every virtual
+// page is its own array page.  A merge round writes the output of every page
+// its merges touch into a fresh physical page taken from a free-page stack
+// (elements of a touched page that no merge of the round covers are carried
+// over unchanged); an input page goes back to the stack once all of its
+// elements have been consumed (the paper's PopFront freeing an emptied page).
+// Rounds run in waves of at most vm_wave_max output pages, in page order, each
+// wave taking its pages from the stack: a merge consumes exactly as many
+// input elements as it writes, so the pages freed by one wave cover the next
+// one, and the pool needs only about one wave of pages plus a few partly
+// consumed pages -- not n elements.  Merge-path searches are bounded below by
+// each merge's consumed front, so they never read a page that went back to
+// the stack.  Finally Copy (Sec. 4) moves every virtual page to its own array
+// page: a page still holding data that is needed later is first moved to a
+// free page, exactly as the paper describes.
+#include "ps_internal.cuh"
+
+namespace ps {
+
+namespace {
+
+constexpr int VM_BLOCK = 256;
+constexpr int VM_K = 9;
+constexpr int VM_E = VM_BLOCK * VM_K;     // outputs per sub-chunk
+constexpr int COPY_BLOCK = 1024;
+
+__device__ __forceinline__ uint32_t* phys_k(const Job& J, uint32_t p)
+{
+    const size_t P = (size_t)1 << J.vm_plog2;
+    return p < J.vm_na_cap ? J.keysA + (size_t)p * P : J.pool_keys + (size_t)(p - J.vm_na_cap) * P;
+}
+
+__device__ __forceinline__ uint32_t* phys_p(const Job& J, uint32_t p)
+{
+    const size_t P = (size_t)1 << J.vm_plog2;
+    return p < J.vm_na_cap ? J.permA + (size_t)p * P : J.pool_perm + (size_t)(p - J.vm_na_cap) * P;
+}
+
+// key at virtual index v (through the page table)
+__device__ __forceinline__ uint32_t vkey(const Job& J, uint32_t v)
+{
+    return phys_k(J, J.pt[v >> J.vm_plog2])[v & ((1u << J.vm_plog2) - 1)];
+}
+
+__device__ __forceinline__ uint32_t vperm(const Job& J, uint32_t v)
+{
+    return phys_p(J, J.pt[v >> J.vm_plog2])[v & ((1u << J.vm_plog2) - 1)];
+}
+
+__device__ __forceinline__ uint32_t page_size(const Job& J, uint32_t u, uint32_t n)
+{
+    const uint32_t P = 1u << J.vm_plog2;
+    return (u + 1 == J.vm_na) ? n - u * P : P;
+}
+
+__device__ bool vm_barrier(Ctr* C)
+{
+    __syncthreads();
+    __shared__ uint32_t s_ok;
+    if (threadIdx.x == 0) {
+        uint32_t ok = 1;
+        const uint32_t gen = ld_acquire_u32(&C->bar_gen);
+        __threadfence();
+        const uint32_t grp = blockIdx.x >> 5;
+        const uint32_t ngroups = (gridDim.x + 31) >> 5;
+        const uint32_t gsize = min(32u, gridDim.x - (grp << 5));
+        bool last = false;
+        if (atomicAdd(&C->bar_group[grp], 1u) == gsize - 1) {
+            atomicExch(&C->bar_group[grp], 0u);
+            last = atomicAdd(&C->bar_count, 1u) == ngroups - 1;
+        }
+        if (last) {
+            atomicExch(&C->bar_count, 0u);
+            __threadfence();
+            st_release_u32(&C->bar_gen, gen + 1);
+        } else {
+            const long long t0 = clock64();
+            uint32_t nap = 64;
+            while (ld_relaxed_u32(&C->bar_gen) == gen) {
+                __nanosleep(nap);
+                nap = nap < 1024 ? nap * 2 : 1024;
+                if (clock64() - t0 > SPIN_LIMIT_CYCLES) {
+                    set_error(C, DERR_TIMEOUT, 60);
+                    ok = 0;
+                    break;
+                }
+            }
+            fence_acquire_gpu();
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Left-child elements among the first d outputs of merge g, searched only
+// above the consumed front (a_lo left / b_lo right elements are gone).
+__device__ uint32_t vm_split(const Job& J, const GSorted& g, uint32_t d, uint32_t a_lo, uint32_t b_lo)
+{
+    const uint32_t lo = (uint32_t)g.goff, mid = lo + g.la;
+    uint32_t l = max(a_lo, d > g.lb ? d - g.lb : 0u);
+    uint32_t h = min(d - min(d, b_lo), g.la);
+    while (l < h) {
+        const uint32_t m = (l + h) >> 1;
+        if (vkey(J, lo + m) <= vkey(J, mid + d - 1 - m)) l = m + 1; else h = m;
+    }
+    return l;
+}
+
+// Count `cnt` consumed elements of virtual range [v0, v0 + cnt); a page whose
+// every element is consumed goes back to the free stack.
+__device__ void consume(const Job& J, uint32_t v0, uint32_t cnt, uint32_t n)
+{
+    const uint32_t L = J.vm_plog2;
+    while (cnt) {
+        const uint32_t u = v0 >> L;
+        const uint32_t take = min(cnt, ((u + 1) << L) - v0);
+        const uint32_t before = atomicAdd(&J.consumed[u], take);
+        if (before + take == page_size(J, u, n)) {
+            // the caller's last array page may be partial: like the paper's partial
+            // input page it is never declared free (it could not hold a full page)
+            const uint32_t old = J.pt[u];
+            const bool partial_tail = old + 1 == J.vm_na && (n & ((1u << J.vm_plog2) - 1)) != 0;
+            if (!partial_tail) {
+                const uint32_t at = atomicAdd(&J.ctr->vm_free_top, 1u);
+                J.free_stack[at] = old;
+            }
+        }
+        v0 += take;
+        cnt -= take;
+    }
+}
+
+struct VmSmem {
+    uint32_t k[VM_E + 8];
+    uint32_t p[VM_E + 8];
+    uint32_t seg_lo[6], seg_hi[6], seg_node[6];
+    uint32_t nseg;
+    uint32_t a0, a1;
+};
+
+// One output page of the current wave: its merge segments and copy gaps.
+__device__ void vm_page(const Job& J, VmSmem& sm, uint32_t u, uint32_t slot, uint32_t n, bool perm)
+{
+    const int tid = threadIdx.x;
+    const uint32_t L = J.vm_plog2;
+    const uint32_t ps0 = u << L, pe = min(ps0 + (1u << L), n);
+    uint32_t* dk = phys_k(J, J.pt_new[u]);
+    uint32_t* dp = perm ? phys_p(J, J.pt_new[u]) : nullptr;
+    if (tid == 0) {
+        // up to two merges touch the page; order them, fill the gaps with copies
+        uint32_t e[2] = {NONE, NONE};
+        const uint32_t c = min(J.page_cnt[u], 2u);
+        for (uint32_t i = 0; i < c; ++i) e[i] = J.page_nodes[2 * u + i];
+        if (c == 2 && J.gsorted[e[0]].goff > J.gsorted[e[1]].goff) {
+            const uint32_t t = e[0];
+            e[0] = e[1];
+            e[1] = t;
+        }
+        uint32_t cur = ps0, ns = 0;
+        for (uint32_t i = 0; i < c; ++i) {
+            const GSorted g = J.gsorted[e[i]];
+            const uint32_t lo = (uint32_t)g.goff, hi = lo + g.la + g.lb;
+            const uint32_t s0 = max(lo, ps0), s1 = min(hi, pe);
+            if (s0 >= s1) continue;
+            if (s0 > cur) { sm.seg_lo[ns] = cur; sm.seg_hi[ns] = s0; sm.seg_node[ns] = NONE; ++ns; }
+            sm.seg_lo[ns] = s0; sm.seg_hi[ns] = s1; sm.seg_node[ns] = e[i]; ++ns;
+            cur = s1;
+        }
+        if (cur < pe) { sm.seg_lo[ns] = cur; sm.seg_hi[ns] = pe; sm.seg_node[ns] = NONE; ++ns; }
+        sm.nseg = ns;
+    }
+    if (tid == 0) {
+        J.wave_node[2 * slot] = NONE;
+        J.wave_node[2 * slot + 1] = NONE;
+    }
+    __syncthreads();
+    const uint32_t nseg = sm.nseg;
+    uint32_t merge_no = 0;                       // record slot of this page's merge segments
+    for (uint32_t sg = 0; sg < nseg; ++sg) {
+        const uint32_t s0 = sm.seg_lo[sg], s1 = sm.seg_hi[sg], e = sm.seg_node[sg];
+        if (e == NONE) {                         // carried over unchanged (a gap)
+            for (uint32_t v = s0 + tid; v < s1; v += VM_BLOCK) {
+                dk[v - ps0] = vkey(J, v);
+                if (dp) dp[v - ps0] = vperm(J, v);
+            }
+            __syncthreads();
+            if (tid == 0) consume(J, s0, s1 - s0, n);
+            continue;
+        }
+        const GSorted g = J.gsorted[e];
+        const uint32_t lo = (uint32_t)g.goff, mid = lo + g.la;
+        const unsigned long long fr = J.front[e];
+        if (merge_no > 1) set_error(J.ctr, DERR_INTERNAL, 64);
+        const uint32_t a_front = (uint32_t)fr, d_front = (uint32_t)(fr >> 32);
+        for (uint32_t x0 = s0; x0 < s1; x0 += VM_E) {
+            const uint32_t x1 = min(x0 + (uint32_t)VM_E, s1);
+            const uint32_t d0 = x0 - lo, d1 = x1 - lo;
+            if (tid == 0) sm.a0 = vm_split(J, g, d0, a_front, d_front - a_front);
+            if (tid == 32) sm.a1 = d1 == g.la + g.lb ? g.la : vm_split(J, g, d1, a_front, d_front - a_front);
+            __syncthreads();
+            const uint32_t a0 = sm.a0, a1 = sm.a1, b0 = d0 - a0, b1 = d1 - a1;
+            const uint32_t na = a1 - a0, nb = b1 - b0, cnt = na + nb;
+            for (uint32_t i = tid; i < cnt; i += VM_BLOCK) {
+                const uint32_t v = i < na ? lo + a0 + i : mid + b0 + (i - na);
+                sm.k[i] = vkey(J, v);
+                if (perm) sm.p[i] = vperm(J, v);
+            }
+            __syncthreads();
+            uint32_t okv[VM_K], opv[VM_K];
+            const uint32_t t0 = tid * VM_K;
+            if (t0 < cnt) {
+                uint32_t l = t0 > nb ? t0 - nb : 0u, h = min(t0, na);
+                while (l < h) {
+                    const uint32_t m = (l + h) >> 1;
+                    if (sm.k[m] <= sm.k[na + t0 - 1 - m]) l = m + 1; else h = m;
+                }
+                uint32_t ia = l, ib = na + (t0 - l);
+#pragma unroll
+                for (int j = 0; j < VM_K; ++j) {
+                    if (t0 + j < cnt) {
+                        const bool ta = ia < na && (ib >= cnt || sm.k[ia] <= sm.k[ib]);
+                        const uint32_t src = ta ? ia : ib;
+                        okv[j] = sm.k[src];
+                        opv[j] = perm ? sm.p[src] : 0u;
+                        ia += ta;
+                        ib += !ta;
+                    }
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < VM_K; ++j) {
+                if (t0 + j < cnt) {
+                    sm.k[t0 + j] = okv[j];
+                    if (perm) sm.p[t0 + j] = opv[j];
+                }
+            }
+            __syncthreads();
+            for (uint32_t i = tid; i < cnt; i += VM_BLOCK) {
+                dk[x0 - ps0 + i] = sm.k[i];
+                if (dp) dp[x0 - ps0 + i] = sm.p[i];
+            }
+            __syncthreads();
+            if (tid == 0) {
+                consume(J, lo + a0, na, n);
+                consume(J, mid + b0, nb, n);
+                // the merge's new front; applied between waves, so every search
+                // of this wave sees the front as it stood when the wave began
+                if (merge_no < 2) {
+                    J.wave_front[2 * slot + merge_no] = ((unsigned long long)d1 << 32) | a1;
+                    J.wave_node[2 * slot + merge_no] = e;
+                }
+            }
+        }
+        ++merge_no;
+    }
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(VM_BLOCK) k_vm_rounds(Job J)
+{
+    __shared__ VmSmem sm;
+    __shared__ uint32_t warp_sums[VM_BLOCK / 32];
+    Ctr* C = J.ctr;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool perm = J.want_perm != 0;
+    const uint32_t n = J.inst[0].n;
+    const uint32_t L = J.vm_plog2, NA = J.vm_na;
+    const uint32_t nwarps_grid = gridDim.x * (VM_BLOCK / 32);
+    const uint32_t gwarp = blockIdx.x * (VM_BLOCK / 32) + warp;
+
+    for (int r = 0; r < NPOW; ++r) {
+        if (*(volatile uint32_t*)&C->error) return;
+        const uint32_t e0 = C->bucket_start[r], e1 = C->bucket_start[r + 1];
+        if (e0 == e1) continue;
+        // 1. the pages each merge of the round touches (a warp per merge)
+        for (uint32_t e = e0 + gwarp; e < e1; e += nwarps_grid) {
+            const GSorted g = J.gsorted[e];
+            const uint32_t lo = (uint32_t)g.goff, hi = lo + g.la + g.lb;
+            const uint32_t first = lo >> L, last = (hi - 1) >> L;
+            if (lane == 0) J.front[e] = 0ull;
+            for (uint32_t u = first + lane; u <= last; u += 32) {
+                if (u == first || u == last) {
+                    const uint32_t slot = atomicAdd(&J.page_cnt[u], 1u);
+                    if (slot < 2) J.page_nodes[2 * u + slot] = e;
+                    else set_error(C, DERR_INTERNAL, 61);
+                } else {
+                    J.page_cnt[u] = 1;
+                    J.page_nodes[2 * u] = e;
+                }
+            }
+        }
+        if (!vm_barrier(C)) return;
+        // 2. the touched pages, in page order (CTA 0)
+        if (blockIdx.x == 0) {
+            uint32_t carry = 0;
+            for (uint32_t base = 0; base < NA; base += VM_BLOCK) {
+                const uint32_t u = base + tid;
+                const bool t = u < NA && J.page_cnt[u] > 0;
+                const uint32_t bal = __ballot_sync(0xffffffffu, t);
+                if (lane == 0) warp_sums[warp] = __popc(bal);
+                __syncthreads();
+                uint32_t before = carry + __popc(bal & ((1u << lane) - 1u));
+                uint32_t tot = 0;
+                for (int w = 0; w < VM_BLOCK / 32; ++w) {
+                    if (w < warp) before += warp_sums[w];
+                    tot += warp_sums[w];
+                }
+                if (t) J.touched[before] = u;
+                carry += tot;
+                __syncthreads();
+            }
+            if (tid == 0) C->vm_touched = carry;
+        }
+        if (!vm_barrier(C)) return;
+        // 3. waves of output pages
+        const uint32_t ntouched = C->vm_touched;
+        uint32_t prev_k = 0;
+        for (uint32_t pos = 0; pos < ntouched;) {
+            // raise the fronts of the merges the previous wave advanced
+            for (uint32_t j = blockIdx.x * VM_BLOCK + tid; j < 2 * prev_k; j += gridDim.x * VM_BLOCK) {
+                const uint32_t e = J.wave_node[j];
+                if (e != NONE) atomicMax(&J.front[e], J.wave_front[j]);
+            }
+            if (blockIdx.x == 0 && tid == 0) {
+                const uint32_t top = C->vm_free_top;
+                const uint32_t k = min(min(J.vm_wave_max, top), ntouched - pos);
+                if (k == 0) set_error(C, DERR_INTERNAL, 62);      // no free page: cannot progress
+                for (uint32_t j = 0; j < k; ++j) J.pt_new[J.touched[pos + j]] = J.free_stack[top - 1 - j];
+                C->vm_free_top = top - k;
+                C->vm_wave = k;
+                C->vm_waves += 1;
+                const uint32_t extra = J.vm_pool > top - k ? J.vm_pool - (top - k) : 0u;   // pages beyond n/P
+                if (extra > C->vm_in_use_peak) C->vm_in_use_peak = extra;
+            }
+            if (!vm_barrier(C)) return;
+            if (*(volatile uint32_t*)&C->error) return;
+            const uint32_t k = C->vm_wave;
+            for (uint32_t j = blockIdx.x; j < k; j += gridDim.x) vm_page(J, sm, J.touched[pos + j], j, n, perm);
+            if (!vm_barrier(C)) return;
+            pos += k;
+            prev_k = k;
+        }
+        // 4. the written pages become current; reset the per-round tables
+        for (uint32_t j = blockIdx.x * VM_BLOCK + tid; j < ntouched; j += gridDim.x * VM_BLOCK) {
+            const uint32_t u = J.touched[j];
+            J.pt[u] = J.pt_new[u];
+            J.page_cnt[u] = 0;
+            J.consumed[u] = 0;
+        }
+        if (!vm_barrier(C)) return;
+    }
+}
+
+// Copy (Sec. 4): walk the virtual pages in order; a needed page still held
+// elsewhere is first moved out to a free page, then the page is copied home.
+// One CTA; the page copies use all its threads.
+__global__ void __launch_bounds__(COPY_BLOCK) k_vm_copy(Job J)
+{
+    __shared__ uint32_t s_src, s_evict_to, s_skip;
+    Ctr* C = J.ctr;
+    if (*(volatile uint32_t*)&C->error) return;
+    const int tid = threadIdx.x;
+    const bool perm = J.want_perm != 0;
+    const uint32_t n = J.inst[0].n;
+    const uint32_t NA = J.vm_na, NP = J.vm_na_cap + J.vm_pool;
+    // holder[p]: the virtual page whose data physical page p holds (NONE: free)
+    for (uint32_t p = tid; p < NP; p += COPY_BLOCK) J.holder[p] = NONE;
+    __syncthreads();
+    for (uint32_t u = tid; u < NA; u += COPY_BLOCK) J.holder[J.pt[u]] = u;
+    __syncthreads();
+    uint32_t moves = 0;
+    for (uint32_t q = 0; q < NA; ++q) {
+        if (tid == 0) {
+            s_src = J.pt[q];
+            s_skip = s_src == q;
+            s_evict_to = NONE;
+            if (!s_skip) {
+                const uint32_t r = J.holder[q];     // page q holds another virtual page's data (r > q)
+                if (r != NONE) {
+                    // take a free page that is not page q and not a finished page (< q)
+                    uint32_t f = NONE;
+                    for (uint32_t i = C->vm_free_top; i-- > 0;) {
+                        const uint32_t c = J.free_stack[i];
+                        if (c != q && (c >= J.vm_na_cap || c > q) && J.holder[c] == NONE) {
+                            f = c;
+                            J.free_stack[i] = J.free_stack[C->vm_free_top - 1];
+                            C->vm_free_top -= 1;
+                            break;
+                        }
+                    }
+                    if (f == NONE) set_error(C, DERR_INTERNAL, 63);
+                    s_evict_to = f;
+                }
+            }
+        }
+        __syncthreads();
+        if (*(volatile uint32_t*)&C->error) return;
+        if (s_skip) continue;
+        const uint32_t src = s_src, ev = s_evict_to;
+        if (ev != NONE) {                       // move page q's current data out of the way
+            const uint32_t r = J.holder[q];
+            const uint32_t cnt = page_size(J, r, n);
+            uint32_t* fk = phys_k(J, ev);
+            const uint32_t* qk = phys_k(J, q);
+            for (uint32_t i = tid; i < cnt; i += COPY_BLOCK) fk[i] = qk[i];
+            if (perm) {
+                uint32_t* fp = phys_p(J, ev);
+                const uint32_t* qp = phys_p(J, q);
+                for (uint32_t i = tid; i < cnt; i += COPY_BLOCK) fp[i] = qp[i];
+            }
+            __syncthreads();
+            if (tid == 0) {
+                J.pt[r] = ev;
+                J.holder[ev] = r;
+                ++moves;
+            }
+            __syncthreads();
+        }
+        // the data of virtual page q may have just moved (if src == q it is home)
+        const uint32_t from = J.pt[q];
+        const uint32_t cnt = page_size(J, q, n);
+        if (from != q) {
+            uint32_t* qk = phys_k(J, q);
+            const uint32_t* sk = phys_k(J, from);
+            for (uint32_t i = tid; i < cnt; i += COPY_BLOCK) qk[i] = sk[i];
+            if (perm) {
+                uint32_t* qp = phys_p(J, q);
+                const uint32_t* sp = phys_p(J, from);
+                for (uint32_t i = tid; i < cnt; i += COPY_BLOCK) qp[i] = sp[i];
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            if (from != q) {
+                J.holder[from] = NONE;
+                const uint32_t at = C->vm_free_top++;
+                J.free_stack[at] = from;
+                ++moves;
+            }
+            J.pt[q] = q;
+            J.holder[q] = q;
+        }
+        __syncthreads();
+    }
+    if (tid == 0) C->vm_copy_moves = moves;
+}
+
+int vm_rounds_max_grid(int num_sms)
+{
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_vm_rounds, VM_BLOCK, 0);
+    if (per_sm > 4) per_sm = 4;
+    return num_sms * (per_sm > 0 ? per_sm : 1);
+}
+
+cudaError_t launch_vm(const Job& J, int grid, cudaStream_t s)
+{
+    void* args[] = {(void*)&J};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_vm_rounds, dim3(grid), dim3(VM_BLOCK), args, 0, s);
+    if (e != cudaSuccess) return e;
+    k_vm_copy<<<1, COPY_BLOCK, 0, s>>>(J);
+    return cudaGetLastError();
+}
+
+}  // namespace ps

@@ -1,0 +1,66 @@
+"""Virtual-memory storage (Sec. 4) on the GPU: the same stable sort as the
+oracle (keys, permutation, runs, powers, merge tree, merge cost) with a small
+recycled page pool instead of an n-element scratch buffer."""
+import numpy as np
+import pytest
+
+from gpu_util import assert_matches_oracle, gpu_sort
+from paper_2605_27147_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+
+def _vm(max_n, **kw):
+    from paper_2605_27147_gb300 import binding
+
+    return binding.Context(max_n, mode=binding.PS_MODE_VM, want_perm=True, **kw)
+
+
+@pytest.mark.parametrize("dist", ["uniform", "zipf", "runs", "paper", "few", "sorted", "reversed", "equal"])
+def test_vm_matches_oracle(oracle_mod, dist):
+    with _vm(1 << 20, page_log2=8) as ctx:          # small pages: many pages, many waves
+        for n in (1, 63, 64, 1000, 4097, 8193, 65537, 300007, 1 << 20):
+            keys = inputs.make(dist, n, 3 + n)
+            ref = oracle_mod.powersort(keys)
+            k, p, st = gpu_sort(ctx, keys)
+            assert_matches_oracle(ctx, keys, ref, k, p, st)
+
+
+def test_vm_tiny_pool_recycles_pages(oracle_mod):
+    # a pool barely larger than one wave: every wave must reuse freed pages
+    with _vm(1 << 22, page_log2=10, tile_log2=12, pool_pages=64) as ctx:
+        for dist, n in (("uniform", (1 << 22) - 12345), ("runs", 3000001), ("zipf", 1 << 22)):
+            keys = inputs.make(dist, n, 7)
+            ref = oracle_mod.powersort(keys)
+            k, p, st = gpu_sort(ctx, keys)
+            assert_matches_oracle(ctx, keys, ref, k, p, st)
+            assert 0 < st["peak_pages"]
+
+
+def test_vm_uses_far_less_memory_than_pingpong(oracle_mod):
+    from paper_2605_27147_gb300 import binding
+
+    n = 1 << 24
+    keys = inputs.make("uniform", n, 5)
+    with _vm(n) as vm, binding.Context(n, want_perm=True) as pp:
+        kv, pv, sv = gpu_sort(vm, keys)
+        kp, ppm, sp = gpu_sort(pp, keys)
+    assert np.array_equal(kv, kp) and np.array_equal(pv, ppm)
+    assert sv["merge_cost"] == sp["merge_cost"]
+    # Pingpong holds n keys + n permutation entries of scratch; VM holds a pool
+    assert sp["scratch_bytes"] - sv["scratch_bytes"] > 7 * n
+    assert sv["peak_pages"] > 0
+
+
+def test_vm_keys_only(oracle_mod):
+    with _vm(1 << 20, page_log2=9) as ctx:
+        for n in (5000, 654321):
+            keys = inputs.make("few", n, 2)
+            ref = oracle_mod.powersort(keys)
+            k, p, st = gpu_sort(ctx, keys, want_perm=False)
+            assert np.array_equal(k, ref.keys)
+            assert st["merge_cost"] == ref.stats["merge_cost"]
