@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="plain_2^24", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--storage", default="pingpong", choices=["pingpong", "vm"],
+                    help="run storage of the plain workloads: Pingpong (n-element scratch) or VM pages")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample-seconds", type=float, default=20.0)
@@ -532,7 +534,9 @@ def main():
     work = torch.empty(max_n, dtype=torch.int32, device=dev)
     perm = torch.empty(max_n, dtype=torch.int32, device=dev)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
-    ctx = binding.Context(max_n, want_perm=True, flags=binding.PS_FLAG_TIMING, device=local, stream=stream)
+    mode = binding.PS_MODE_VM if args.storage == "vm" else binding.PS_MODE_PINGPONG
+    ctx = binding.Context(max_n, mode=mode, want_perm=True, flags=binding.PS_FLAG_TIMING, device=local,
+                          stream=stream)
 
     def one_sort(i, timed):
         n = data[i][1]
@@ -580,7 +584,8 @@ def main():
         flush.fill_(i)
         st = ctx.run(work[:n], perm[:n], stats=True)
         hbm[i] = st
-        rounds[data[i][0]] = [[round(x, 1) for x in rt] for rt in ctx.round_times()]
+        if args.storage == "pingpong":
+            rounds[data[i][0]] = [[round(x, 1) for x in rt] for rt in ctx.round_times()]
     merge_ms = sum(p["merge_rounds"] for p in phases)
     merge_bytes = sum(BYTES_PER_MERGED_ELEM * hbm[i]["hbm_merge_elems"] for _, _, _, i in recs)
     tiles_ms = sum(p["tiles"] for p in phases)
@@ -597,7 +602,8 @@ def main():
     # end to end through ps_run_host with pinned host arrays
     e2e = None
     if not args.no_e2e:
-        hctx = binding.Context(max_n, want_perm=True, flags=binding.PS_FLAG_HOST_IO, device=local, stream=stream)
+        hctx = binding.Context(max_n, mode=mode, want_perm=True, flags=binding.PS_FLAG_HOST_IO, device=local,
+                               stream=stream)
         hk = torch.empty(max_n, dtype=torch.int32, pin_memory=True)
         hp = torch.empty(max_n, dtype=torch.int32, pin_memory=True)
         src = [torch.from_numpy(k.view(np.int32)) for _, _, _, k in data]
@@ -644,12 +650,15 @@ def main():
             "workload": args.workload,
             "instances": [f"{d} n=2^{int(np.log2(n))} seed {s}" for d, n, s, _ in data],
             "outputs": "sorted keys + stable permutation (uint32)",
-            "storage": "pingpong",
+            "storage": args.storage,
+            "scratch_bytes": hbm[0]["scratch_bytes"],
+            "peak_pool_pages": hbm[0]["peak_pages"],
             "l2": "flushed before every timed sort (512 MiB write)",
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
         },
         "roofline": {
-            "kernel": "k_merge_rounds (HBM merge rounds)", "bound": "hbm", "achieved": achieved,
+            "kernel": "k_merge_rounds (HBM merge rounds)" if args.storage == "pingpong"
+            else "k_vm_rounds + k_vm_copy (paged merge rounds, final Copy)", "bound": "hbm", "achieved": achieved,
             "peak": peak, "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
             "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic,
@@ -664,7 +673,8 @@ def main():
                             / (total_ms / 1000.0) / 1e9,
         },
         "stats": {data[i][0]: {k: hbm[i][k] for k in ("runs", "merge_cost", "tiles", "global_nodes", "rounds",
-                                                      "hbm_merge_elems", "max_power")} for i in hbm},
+                                                      "hbm_merge_elems", "max_power", "scratch_bytes",
+                                                      "peak_pages")} for i in hbm},
         "round_us_split_merge_barrier": rounds,
         "cpu_baseline": cpu,
         "e2e": e2e,
