@@ -28,7 +28,6 @@ namespace {
 constexpr int VM_BLOCK = 256;
 constexpr int VM_K = 9;
 constexpr int VM_E = VM_BLOCK * VM_K;     // outputs per sub-chunk
-constexpr int COPY_BLOCK = 1024;
 
 __device__ __forceinline__ uint32_t* phys_k(const Job& J, uint32_t p)
 {
@@ -361,98 +360,107 @@ __global__ void __launch_bounds__(VM_BLOCK) k_vm_rounds(Job J)
     }
 }
 
-// Copy (Sec. 4): walk the virtual pages in order; a needed page still held
-// elsewhere is first moved out to a free page, then the page is copied home.
-// One CTA; the page copies use all its threads.
-__global__ void __launch_bounds__(COPY_BLOCK) k_vm_copy(Job J)
+// Copy (Sec. 4), in batches of target pages.  The paper walks the virtual
+// pages in order: a target array page that still holds data needed later is
+// first moved out to a free page, then the page's own data is copied in.
+// Here a batch of up to `pool` consecutive targets does the same in two
+// parallel steps: (1) every target of the batch that holds another page's
+// data moves it out to a free page; (2) every target receives its own data.
+// After step 1 no target of the batch holds needed data, so the copies of
+// step 2 never overwrite a source; each copy frees its source, so the number
+// of free pages is the same after every batch.  Counting pages shows that
+// with at most pool - 1 targets per batch the free pages cover every move out.
+__device__ void vm_copy_page(const Job& J, uint32_t dst, uint32_t src, uint32_t cnt, bool perm)
 {
-    __shared__ uint32_t s_src, s_evict_to, s_skip;
+    uint32_t* dk = phys_k(J, dst);
+    const uint32_t* sk = phys_k(J, src);
+    for (uint32_t i = threadIdx.x; i < cnt; i += VM_BLOCK) dk[i] = sk[i];
+    if (perm) {
+        uint32_t* dp = phys_p(J, dst);
+        const uint32_t* sp = phys_p(J, src);
+        for (uint32_t i = threadIdx.x; i < cnt; i += VM_BLOCK) dp[i] = sp[i];
+    }
+}
+
+__global__ void __launch_bounds__(VM_BLOCK) k_vm_copy(Job J)
+{
+    __shared__ uint32_t s_src;
     Ctr* C = J.ctr;
     if (*(volatile uint32_t*)&C->error) return;
     const int tid = threadIdx.x;
     const bool perm = J.want_perm != 0;
     const uint32_t n = J.inst[0].n;
     const uint32_t NA = J.vm_na, NP = J.vm_na_cap + J.vm_pool;
-    // holder[p]: the virtual page whose data physical page p holds (NONE: free)
-    for (uint32_t p = tid; p < NP; p += COPY_BLOCK) J.holder[p] = NONE;
-    __syncthreads();
-    for (uint32_t u = tid; u < NA; u += COPY_BLOCK) J.holder[J.pt[u]] = u;
-    __syncthreads();
-    uint32_t moves = 0;
-    for (uint32_t q = 0; q < NA; ++q) {
-        if (tid == 0) {
-            s_src = J.pt[q];
-            s_skip = s_src == q;
-            s_evict_to = NONE;
-            if (!s_skip) {
-                const uint32_t r = J.holder[q];     // page q holds another virtual page's data (r > q)
-                if (r != NONE) {
-                    // take a free page that is not page q and not a finished page (< q)
-                    uint32_t f = NONE;
-                    for (uint32_t i = C->vm_free_top; i-- > 0;) {
-                        const uint32_t c = J.free_stack[i];
-                        if (c != q && (c >= J.vm_na_cap || c > q) && J.holder[c] == NONE) {
-                            f = c;
-                            J.free_stack[i] = J.free_stack[C->vm_free_top - 1];
-                            C->vm_free_top -= 1;
-                            break;
-                        }
-                    }
-                    if (f == NONE) set_error(C, DERR_INTERNAL, 63);
-                    s_evict_to = f;
+    const uint32_t gtid = blockIdx.x * VM_BLOCK + tid, gstride = gridDim.x * VM_BLOCK;
+    const bool tail_partial = (n & ((1u << J.vm_plog2) - 1)) != 0;
+    // holder[p]: the virtual page whose data physical page p holds (NONE: none)
+    for (uint32_t p = gtid; p < NP; p += gstride) J.holder[p] = NONE;
+    if (!vm_barrier(C)) return;
+    for (uint32_t u = gtid; u < NA; u += gstride) J.holder[J.pt[u]] = u;
+    if (!vm_barrier(C)) return;
+    for (uint32_t q0 = 0; q0 < NA;) {
+        // at most pool - 1 targets: then the free pages always cover the moves out
+        // (one page of slack for the partial last array page, which is never free)
+        const uint32_t B = min(J.vm_pool - 1, NA - q0);
+        const uint32_t q1 = q0 + B;
+        // free pages: hold nothing, are not a target of this or an earlier batch,
+        // and are not the partial last array page
+        if (gtid == 0) {
+            C->vm_free_top = 0;
+            C->vm_wave = 0;
+        }
+        if (!vm_barrier(C)) return;
+        for (uint32_t p = gtid; p < NP; p += gstride) {
+            if (p >= J.vm_na_cap && p - J.vm_na_cap >= J.vm_pool) continue;
+            const bool is_array = p < J.vm_na_cap;
+            if (is_array && (p >= NA || p < q1)) continue;
+            if (is_array && tail_partial && p + 1 == NA) continue;
+            if (J.holder[p] == NONE) J.free_stack[atomicAdd(&C->vm_free_top, 1u)] = p;
+        }
+        if (!vm_barrier(C)) return;
+        // step 1: move needed data out of the batch's targets
+        for (uint32_t q = q0 + blockIdx.x; q < q1; q += gridDim.x) {
+            const uint32_t r = J.holder[q];
+            if (r == NONE || r == q) continue;
+            if (tid == 0) {
+                const uint32_t at = atomicAdd(&C->vm_wave, 1u);
+                s_src = at < C->vm_free_top ? J.free_stack[at] : NONE;
+                if (s_src == NONE) set_error(C, DERR_INTERNAL, 65);
+            }
+            __syncthreads();
+            const uint32_t f = s_src;
+            if (f != NONE) {
+                vm_copy_page(J, f, q, page_size(J, r, n), perm);
+                __syncthreads();
+                if (tid == 0) {
+                    J.pt[r] = f;
+                    J.holder[f] = r;
+                    J.holder[q] = NONE;
+                    atomicAdd(&C->vm_copy_moves, 1u);
                 }
             }
+            __syncthreads();
         }
-        __syncthreads();
+        if (!vm_barrier(C)) return;
         if (*(volatile uint32_t*)&C->error) return;
-        if (s_skip) continue;
-        const uint32_t src = s_src, ev = s_evict_to;
-        if (ev != NONE) {                       // move page q's current data out of the way
-            const uint32_t r = J.holder[q];
-            const uint32_t cnt = page_size(J, r, n);
-            uint32_t* fk = phys_k(J, ev);
-            const uint32_t* qk = phys_k(J, q);
-            for (uint32_t i = tid; i < cnt; i += COPY_BLOCK) fk[i] = qk[i];
-            if (perm) {
-                uint32_t* fp = phys_p(J, ev);
-                const uint32_t* qp = phys_p(J, q);
-                for (uint32_t i = tid; i < cnt; i += COPY_BLOCK) fp[i] = qp[i];
-            }
-            __syncthreads();
-            if (tid == 0) {
-                J.pt[r] = ev;
-                J.holder[ev] = r;
-                ++moves;
+        // step 2: every target receives its own data
+        for (uint32_t q = q0 + blockIdx.x; q < q1; q += gridDim.x) {
+            const uint32_t src = J.pt[q];
+            if (src != q) {
+                vm_copy_page(J, q, src, page_size(J, q, n), perm);
+                __syncthreads();
+                if (tid == 0) {
+                    J.holder[src] = NONE;
+                    J.pt[q] = q;
+                    J.holder[q] = q;
+                    atomicAdd(&C->vm_copy_moves, 1u);
+                }
             }
             __syncthreads();
         }
-        // the data of virtual page q may have just moved (if src == q it is home)
-        const uint32_t from = J.pt[q];
-        const uint32_t cnt = page_size(J, q, n);
-        if (from != q) {
-            uint32_t* qk = phys_k(J, q);
-            const uint32_t* sk = phys_k(J, from);
-            for (uint32_t i = tid; i < cnt; i += COPY_BLOCK) qk[i] = sk[i];
-            if (perm) {
-                uint32_t* qp = phys_p(J, q);
-                const uint32_t* sp = phys_p(J, from);
-                for (uint32_t i = tid; i < cnt; i += COPY_BLOCK) qp[i] = sp[i];
-            }
-        }
-        __syncthreads();
-        if (tid == 0) {
-            if (from != q) {
-                J.holder[from] = NONE;
-                const uint32_t at = C->vm_free_top++;
-                J.free_stack[at] = from;
-                ++moves;
-            }
-            J.pt[q] = q;
-            J.holder[q] = q;
-        }
-        __syncthreads();
+        if (!vm_barrier(C)) return;
+        q0 = q1;
     }
-    if (tid == 0) C->vm_copy_moves = moves;
 }
 
 int vm_rounds_max_grid(int num_sms)
@@ -468,8 +476,7 @@ cudaError_t launch_vm(const Job& J, int grid, cudaStream_t s)
     void* args[] = {(void*)&J};
     cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_vm_rounds, dim3(grid), dim3(VM_BLOCK), args, 0, s);
     if (e != cudaSuccess) return e;
-    k_vm_copy<<<1, COPY_BLOCK, 0, s>>>(J);
-    return cudaGetLastError();
+    return cudaLaunchCooperativeKernel((const void*)k_vm_copy, dim3(grid), dim3(VM_BLOCK), args, 0, s);
 }
 
 }  // namespace ps
