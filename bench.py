@@ -55,6 +55,7 @@ WORKLOADS = {
 }
 FLUSH_BYTES = 512 << 20
 BYTES_PER_MERGED_ELEM = 16   # key + perm entry read, key + perm entry written
+LAUNCHES_PER_BATCH = 12      # one batched Pingpong call: setup, runs, 7 planning kernels, tiles, rounds, finish
 
 
 def parse():
@@ -403,7 +404,7 @@ def run_batched(args):
         "kernels": {"phase_ms_one_call": ph, "stats": {k: st[k] for k in ("runs", "merge_cost", "tiles",
                                                                            "global_nodes", "rounds",
                                                                            "hbm_merge_elems")}},
-        "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(), "gpu_launches": 11 * args.steps,
+        "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(), "gpu_launches": int(st["launches"]) * args.steps,
     }
     graph.close()
     ctx.close()
@@ -497,7 +498,7 @@ def run_serving(args, rate=2000.0, duration=10.0, budget=64 << 30):
                 "d2h_bytes_per_step": int(8 * sizes.mean()),
                 "api": "ps_server_submit / ps_server_wait on pinned host arrays"},
         "roofline": None, "cpu_baseline": None, "clocks": clk.summary(),
-        "gpu_launches": 11 * int(st["batches"]),
+        "gpu_launches": LAUNCHES_PER_BATCH * int(st["batches"]),
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -557,7 +558,6 @@ def main():
     ctx.sync()
     torch.cuda.synchronize(dev)
 
-    launches_per_sort = 11
     recs, phases = [], []
     if dist:
         dist.barrier()
@@ -584,6 +584,7 @@ def main():
         flush.fill_(i)
         st = ctx.run(work[:n], perm[:n], stats=True)
         hbm[i] = st
+        launches_per_sort = int(st["launches"])
         if args.storage == "pingpong":
             rounds[data[i][0]] = [[round(x, 1) for x in rt] for rt in ctx.round_times()]
     merge_ms = sum(p["merge_rounds"] for p in phases)
@@ -675,7 +676,7 @@ def main():
         "stats": {data[i][0]: {k: hbm[i][k] for k in ("runs", "merge_cost", "tiles", "global_nodes", "rounds",
                                                       "hbm_merge_elems", "max_power", "scratch_bytes",
                                                       "peak_pages")} for i in hbm},
-        "round_us_split_merge_barrier": rounds,
+        "round_timeline_us": rounds,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clk.summary(),

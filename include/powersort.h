@@ -75,8 +75,10 @@ typedef struct ps_config {
     uint32_t tile_log2;  /* on-chip tile capacity 2^tile_log2 in 10..12 (0: 12)      */
     uint32_t pool_pages; /* VM page-pool size in pages (0: chosen by the library)    */
     uint32_t flags;      /* PS_FLAG_* below                                          */
-    uint32_t merge_ctas_per_sm; /* CTAs per SM of the HBM merge kernel (0: the most
-                            that fit; a tuning knob, see paper_2605_27147_gb300/autotune.py) */
+    uint32_t merge_ctas_per_sm; /* HBM merge kernel shape, a tuning knob (see
+                            paper_2605_27147_gb300/autotune.py): 4 = four CTAs per SM
+                            with two shared-memory stages each, 1..3 = that many CTAs
+                            per SM with three stages, 0 = chosen per call by size  */
     uint32_t reserved[2];
 } ps_config;
 
@@ -162,13 +164,14 @@ PS_API ps_status ps_run_host(ps_ctx* ctx, uint32_t* h_keys, uint32_t* h_perm, ui
  * launches.  h_ms receives min(cap, 6) values; *count (may be NULL) gets 6. */
 PS_API ps_status ps_get_phase_times(ps_ctx* ctx, float* h_ms, uint32_t cap, uint32_t* count);
 
-/* Timeline of the HBM merge rounds of the last call (synchronises), from
- * globaltimer stamps taken by one CTA: for every round that ran, four values
- * in microseconds -- the split phase (merge-path searches and the grid
- * barrier after them), the merge phase (until that CTA's last output was
- * written), the wait at the round's closing barrier, and the part of the
- * split phase that CTA spent on its own searches.  h_us receives
- * min(cap, 4 x rounds) values; *count (may be NULL) gets 4 x rounds. */
+/* Timeline of the HBM merges of the last Pingpong call (synchronises).  The
+ * merges are grouped in rounds of equal power (children before parents) but
+ * run as a dataflow: a merge starts when its two children are complete, so
+ * rounds overlap.  For every round that ran, four values in microseconds
+ * since the merge kernel started: the first and the last time one of the
+ * round's chunks found its inputs complete, and the first and the last time
+ * one of its chunks sent its output.  h_us receives min(cap, 4 x rounds)
+ * values; *count (may be NULL) gets 4 x rounds (0 for VM storage). */
 PS_API ps_status ps_get_round_times(ps_ctx* ctx, float* h_us, uint32_t cap, uint32_t* count);
 
 /* Wait for the context's stream and report the device-side status of the

@@ -13,7 +13,9 @@ struct ps_ctx {
     int device;
     cudaStream_t stream;
     int num_sms;
-    int grid_runs, grid_plan, grid_tiles, grid_merge, grid_vm;
+    int grid_runs, grid_plan, grid_tiles, grid_vm;
+    int grid_merge2, grid_merge3;   // HBM merge kernel: two-stage and three-stage variants
+    int merge_stages;               // 2 or 3 when fixed by the config, 0: chosen per call
     unsigned long long max_total;
     uint32_t max_count;
     ps::Job base;               // device buffers; per-call fields filled by each run
@@ -33,7 +35,7 @@ struct ps_ctx {
 namespace {
 
 constexpr unsigned long long LIMIT_N = 0xffffffffull;  // instance sizes and totals < 2^32
-constexpr uint32_t LAUNCHES_PER_CALL = 11;  // setup, runs, 6 planning kernels, tiles, rounds, finish
+constexpr uint32_t LAUNCHES_PER_CALL = 12;  // setup, runs, 7 planning kernels, tiles, rounds, finish
 constexpr uint32_t NPHASES = 6;
 
 struct DeviceGuard {
@@ -101,7 +103,12 @@ ps_status enqueue(ps_ctx* c, const ps::Job& J)
     if (J.vm) {
         if (ps::launch_vm(J, c->grid_vm, s) != cudaSuccess || !mark(5)) return PS_ECUDA;
     } else {
-        if (ps::launch_merge_rounds(J, c->grid_merge, s) != cudaSuccess || !mark(5)) return PS_ECUDA;
+        // measured on GB300: three stages win for arrays up to about 2^26
+        // elements, four CTAs of two stages for larger ones
+        const unsigned long long size = J.offsets ? J.max_total : J.single_n;
+        const int stages = c->merge_stages ? c->merge_stages : (size >= (1ull << 26) ? 2 : 3);
+        const int grid = stages == 2 ? c->grid_merge2 : c->grid_merge3;
+        if (ps::launch_merge_rounds(J, grid, stages, s) != cudaSuccess || !mark(5)) return PS_ECUDA;
     }
     if (ps::launch_finish(J, s) != cudaSuccess || !mark(6)) return PS_ECUDA;
     if (cudaMemcpyAsync(c->h_ctr, J.ctr, sizeof(ps::Ctr), cudaMemcpyDeviceToHost, s) != cudaSuccess)
@@ -134,7 +141,7 @@ void fill_stats(const ps_ctx* c, ps_stats* st, uint32_t count)
     st->rounds = h->rounds;
     st->instances = count;
     st->hbm_merge_elems = h->hbm_elems;
-    st->launches = LAUNCHES_PER_CALL;
+    st->launches = LAUNCHES_PER_CALL + (c->base.vm ? 1u : 0u);   // VM: rounds + the final Copy
 }
 
 ps_status run_common(ps_ctx* c, uint32_t* d_keys, uint32_t* d_perm, const uint64_t* d_offsets,
@@ -238,10 +245,14 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
     c->grid_runs = c->num_sms * 8;
     c->grid_plan = c->num_sms * 8;
     c->grid_tiles = ps::tiles_max_grid(c->num_sms);
-    c->grid_merge = ps::merge_rounds_grid_for(c->num_sms, (int)cfg->merge_ctas_per_sm);
+    // merge_ctas_per_sm: 4 selects the two-stage variant (four CTAs per SM), 1-3
+    // the three-stage one with that many CTAs per SM, 0 lets each call choose
+    const int mcs = (int)cfg->merge_ctas_per_sm;
+    c->merge_stages = mcs >= 4 ? 2 : (mcs > 0 ? 3 : 0);
+    c->grid_merge2 = ps::merge_rounds_grid_for(c->num_sms, 0, 2);
+    c->grid_merge3 = ps::merge_rounds_grid_for(c->num_sms, mcs > 0 && mcs < 4 ? mcs : 0, 3);
     c->grid_vm = ps::vm_rounds_max_grid(c->num_sms);
     if (c->grid_vm > 1024) c->grid_vm = 1024;
-    if (c->grid_merge > 1024) c->grid_merge = 1024;   // the grid barrier's group table
 
     ps::Job& J = c->base;
     std::memset(&J, 0, sizeof(J));
@@ -251,10 +262,9 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
     const unsigned long long slot_cap = max_total / 32 + 2ull * c->max_count + 2;
     const unsigned long long chunk_cap = max_total / ps::RUN_CHUNK + c->max_count + 1;
     const unsigned long long entry_cap = slot_cap;
-    const unsigned long long split_cap = max_total / ps::MERGE_E + entry_cap + 2;
     // chunks summed over all rounds: at most 32 rounds of max_total outputs
     const unsigned long long chunk_node_cap = (unsigned long long)(ps::NPOW - 1) * (max_total / ps::MERGE_E) + entry_cap + 2;
-    if (chunk_cap > 0xffffffffull || entry_cap > 0xffffffffull || split_cap > 0xffffffffull ||
+    if (chunk_cap > 0xffffffffull || entry_cap > 0xffffffffull ||
         chunk_node_cap > 0xffffffffull) {
         delete c;
         return PS_EINVAL;
@@ -262,7 +272,6 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
     J.slot_cap = slot_cap;
     J.chunk_cap = (uint32_t)chunk_cap;
     J.entry_cap = (uint32_t)entry_cap;
-    J.split_cap = (uint32_t)split_cap;
     J.chunk_node_cap = (uint32_t)chunk_node_cap;
 
     ps_status st = PS_OK;
@@ -313,7 +322,8 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
     if (st == PS_OK) st = dev_alloc(c, &J.tiles, entry_cap);
     if (st == PS_OK) st = dev_alloc(c, &J.gnodes, entry_cap);
     if (st == PS_OK) st = dev_alloc(c, &J.gsorted, entry_cap);
-    if (st == PS_OK) st = dev_alloc(c, &J.splits, split_cap);
+    if (st == PS_OK) st = dev_alloc(c, &J.dep, entry_cap);
+    J.gidx = J.kappa;
     if (st == PS_OK) st = dev_alloc(c, &J.chunk_node, chunk_node_cap);
     if (st == PS_OK) st = dev_alloc(c, &J.ctr, 1);
     if (st == PS_OK && (cfg->flags & PS_FLAG_HOST_IO)) {
@@ -334,7 +344,7 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
     // every table the kernels write must exist (permB only with want_perm)
     if (st == PS_OK && ((!vm && !J.keysB) || !J.inst || !J.chunk_status || !J.chunk_map || !J.chunk_incl ||
                         !J.run_start || !J.kappa || !J.power || !J.na || !J.nb || !J.tiles || !J.gnodes ||
-                        !J.gsorted || !J.splits || !J.chunk_node || !J.ctr ||
+                        !J.gsorted || !J.dep || !J.chunk_node || !J.ctr ||
                         (!vm && cfg->want_perm && !J.permB) || (vm && (!J.pool_keys || !J.pt || !J.front))))
         st = PS_EINTERNAL;
     if (st != PS_OK) {
@@ -419,13 +429,12 @@ PS_API ps_status ps_get_round_times(ps_ctx* ctx, float* h_us, uint32_t cap, uint
     if (st != PS_OK) return st;
     const ps::Ctr* h = ctx->h_ctr;
     uint32_t k = 0;
+    const unsigned long long t0 = h->merge_t0;
     for (int r = 0; r < ps::NPOW; ++r) {
         const unsigned long long* t = h->round_ns[r];
-        if (h->bucket_start[r] == h->bucket_start[r + 1] || t[0] == 0 || t[3] < t[0]) continue;
-        const float v[4] = {(float)(t[1] - t[0]) * 1e-3f, (float)(t[2] - t[1]) * 1e-3f,
-                            (float)(t[3] - t[2]) * 1e-3f, (float)(t[4] - t[0]) * 1e-3f};
+        if (h->bucket_start[r] == h->bucket_start[r + 1] || t[0] == ~0ull || t[2] == ~0ull) continue;
         for (int i = 0; i < 4; ++i, ++k)
-            if (k < cap) h_us[k] = v[i];
+            if (k < cap) h_us[k] = t[i] > t0 ? (float)(t[i] - t0) * 1e-3f : 0.0f;
     }
     if (count) *count = k;
     return PS_OK;

@@ -9,9 +9,12 @@
 //                  of the merge Algorithm 1 performs at that boundary
 //   k_classify     split the merge tree into on-chip tiles and HBM nodes
 //   k_depth        depth of tiles / HBM nodes (Pingpong buffer parity, Sec. 3)
-//   k_bucket       HBM nodes grouped into rounds by power, chunk prefix sums
+//   k_bucket_scan  round starts (prefix sums of per-round merge / chunk counts)
+//   k_bucket       HBM nodes placed by round, chunk numbers
+//   k_chunk_nodes  chunk -> merge table; parent links and dependency counts
 //   k_tiles        runs sorted and merged inside shared memory
-//   k_merge_rounds persistent cooperative kernel: all HBM merge rounds
+//   k_merge_rounds persistent cooperative kernel: every HBM merge, scheduled
+//                  as a dataflow over the merge tree
 #pragma once
 
 #include <cstdint>
@@ -25,6 +28,8 @@ constexpr int RUN_CHUNK = 4096;   // elements per run-detection chunk
 constexpr int RUN_HALO = 96;      // descent bits examined past a chunk's end
 constexpr int RUN_WORDS = (RUN_CHUNK + RUN_HALO) / 32 + 1;
 constexpr int RUN_BLOCK = 128;
+constexpr int RUN_LOADS = RUN_WORDS * 32 / RUN_BLOCK;   // keys loaded per thread per chunk
+static_assert(RUN_WORDS * 32 % RUN_BLOCK == 0, "the bitmask window is a whole number of block loads");
 constexpr int MAP_STATES = 64;    // entry states of a chunk: minrun (<= 63) + 1
 constexpr int RUN_REC = RUN_CHUNK / 32 + 2;  // run starts one chain can put in a chunk
 constexpr uint32_t STATE_END = 255;
@@ -74,8 +79,10 @@ struct GNode {
 struct GSorted {
     unsigned long long goff;
     uint32_t la, lb;
-    uint32_t chunk_base;   // first chunk of this node inside its round
+    uint32_t chunk_base;   // number of its first chunk (chunks are numbered round by round)
     uint32_t depth;
+    uint32_t parent;       // GSorted index of the parent merge (NONE for an instance's root)
+    uint32_t pad;
 };
 
 struct Ctr {
@@ -87,7 +94,9 @@ struct Ctr {
     unsigned long long total_slots;
     uint32_t n_tiles;
     uint32_t n_gnodes;
-    uint32_t bucket_count[NPOW + 1];
+    uint32_t bucket_count[NPOW + 1];   // HBM merges of round r
+    uint32_t bucket_nchunk[NPOW + 1];  // their chunks (MERGE_E outputs each)
+    unsigned long long bucket_cursor[NPOW + 1];   // (merges << 40) | chunks placed so far
     uint32_t bucket_start[NPOW + 2];   // GSorted index where round r starts
     uint32_t bucket_chunk[NPOW + 2];   // chunks of round r: [0, bucket_chunk[r])
     uint32_t rounds;                   // non-empty rounds
@@ -108,11 +117,11 @@ struct Ctr {
     unsigned long long runs_total;
     unsigned long long n_total;
     unsigned long long hbm_elems;      // sum of the sizes of the HBM merges
-    // globaltimer stamps (ns) taken by CTA 0 of the merge rounds: [round][0] round
-    // start, [1] after the split phase's barrier, [2] its last output sent,
-    // [3] after the round's closing barrier, [4] its own split searches done
-    // (0 for empty rounds)
-    unsigned long long round_ns[NPOW][5];
+    // HBM merge timeline (globaltimer, ns): per round the first and last time a
+    // chunk's inputs were found complete, the first and last time a chunk's
+    // output was sent; merge_t0 = the merge kernel's start
+    unsigned long long round_ns[NPOW][4];
+    unsigned long long merge_t0;
 };
 
 __device__ __forceinline__ unsigned long long globaltimer_ns()
@@ -147,13 +156,14 @@ struct Job {
     TileItem* tiles;
     GNode* gnodes;
     GSorted* gsorted;
-    uint32_t* splits;           // per chunk of the current round: left-child elements before it
+    uint32_t* dep;              // per GSorted entry: chunks of its HBM children not yet written
+    uint32_t* gidx;             // per boundary slot: GSorted index of its HBM merge (kappa's memory,
+                                // reused once the powers are known)
     uint32_t* chunk_node;       // per chunk (ids global across rounds): its GSorted index
     Ctr* ctr;
     unsigned long long slot_cap;
     uint32_t chunk_cap;
     uint32_t entry_cap;         // capacity of tiles / gnodes / gsorted
-    uint32_t split_cap;
     uint32_t chunk_node_cap;
     // virtual-memory storage (Sec. 4): pages of P = 2^vm_plog2 elements
     uint32_t vm;                // nonzero: VM storage instead of Pingpong
@@ -243,6 +253,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
     return ok != 0;
 }
 
+// non-blocking probe of a phase completion
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 // global -> shared bulk copy; completes `bytes` on the mbarrier.  Both
 // addresses 16-byte aligned, bytes a multiple of 16 (checked by callers).
 __device__ __forceinline__ void tma_load_1d(void* dst_smem, const void* src_gmem, uint32_t bytes, uint64_t* bar)
@@ -307,14 +331,14 @@ __device__ __forceinline__ uint32_t find_inst(uint32_t count, unsigned long long
 // ---------------------------------------------------------------- launchers
 cudaError_t launch_setup(const Job& J, cudaStream_t s);
 cudaError_t launch_runs(const Job& J, int grid, cudaStream_t s);
-int merge_rounds_grid_for(int num_sms, int ctas_per_sm);
+int merge_rounds_grid_for(int num_sms, int ctas_per_sm, int stages);
 cudaError_t launch_plan(const Job& J, int grid, cudaStream_t s);
 cudaError_t launch_tiles(const Job& J, int grid, cudaStream_t s);
-cudaError_t launch_merge_rounds(const Job& J, int grid, cudaStream_t s);
+cudaError_t launch_merge_rounds(const Job& J, int grid, int stages, cudaStream_t s);
 cudaError_t launch_finish(const Job& J, cudaStream_t s);
 cudaError_t launch_vm(const Job& J, int grid, cudaStream_t s);
 int vm_rounds_max_grid(int num_sms);
-int merge_rounds_max_grid(int num_sms);
+int merge_rounds_max_grid(int num_sms, int stages);
 int tiles_max_grid(int num_sms);
 
 }  // namespace ps

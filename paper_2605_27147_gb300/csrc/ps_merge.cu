@@ -1,98 +1,82 @@
-// HBM merge rounds: the merges of Algorithm 1 whose inputs exceed the tile
-// size, executed as stable out-of-place merges (Algorithm 2, StandardMerge:
-// ties take the left run) between the caller's arrays and the scratch arrays
+// HBM merges: the merges of Algorithm 1 whose inputs exceed the tile size,
+// executed as stable out-of-place merges (Algorithm 2, StandardMerge: ties
+// take the left run) between the caller's arrays and the scratch arrays
 // (Pingpong storage, Sec. 3).
 //
-// Rounds go from the largest power to the smallest; all merges of one round
-// are disjoint and their children are finished.  Every merge is cut into
-// chunks of MERGE_E outputs.
+// Every merge is cut into chunks of MERGE_E outputs.  Chunks are numbered
+// round by round (rounds go from the largest power to the smallest), so a
+// merge's children always carry smaller chunk numbers than the merge itself.
+// One persistent cooperative launch processes every chunk as a dataflow,
+// without grid-wide barriers: a merge starts as soon as both of its children
+// are complete, while other merges of the previous round may still run.
 //
-// Phase A: for every chunk, how many of its merge's first d outputs come
-// from the left child (merge-path split: the largest i with A[i-1] <= B[d-i],
-// ties to the left).  The chunk -> merge table is built once per call by the
-// planning kernels.
+//   dep[e]  chunks of merge e's HBM children not yet written (set by the
+//           planning kernels; children that are tiles are finished before the
+//           launch).  Whoever writes a chunk decrements its parent's counter
+//           once the chunk has reached global memory.
 //
-// Phase B is warp specialised.  A producer warp walks the CTA's chunks: it
-// waits until a shared-memory stage is free (an "empty" mbarrier), describes
-// the chunk, starts the 1-D bulk copies (cp.async.bulk, TMA) of the chunk's
-// two input slices (keys and permutation) into the stage, and loads the
-// elements outside the slices' 16-byte-aligned interiors (at most three at
-// each end) with ordinary loads; the stage's "full" mbarrier completes when
-// both have landed.  Eight consumer warps wait on "full", merge (each thread
-// MERGE_K consecutive outputs: merge-path split inside shared memory, then a
-// serial merge), release the stage, and send the chunk's output out through a
-// bulk store (plus ordinary stores for its unaligned ends).  With two stages
-// the producer runs one chunk ahead of the consumers.
+// A CTA has three roles.
+//   Search warp: NSEARCH lanes, each holding one chunk.  A lane claims the
+//     next chunk number (one global ticket, so chunks are claimed in order),
+//     waits until the chunk's merge has dep = 0, and finds the merge-path
+//     splits of the chunk's first and last output (how many of the merge's
+//     first d outputs come from the left child: the largest i with
+//     A[i-1] <= B[d-i], ties to the left).  All lanes run one loop in which
+//     each advances its own chunk by one step per iteration (one probe of each
+//     of its two binary searches), so the probes of different chunks overlap.
+//     A prepared chunk goes into the lane's slot of a shared-memory ring.
+//   Producer warp: takes the prepared chunk with the smallest number, waits
+//     for a free shared-memory stage (an "empty" mbarrier), starts the 1-D
+//     bulk copies (cp.async.bulk, TMA) of the chunk's two input slices (keys
+//     and permutation) and loads the elements outside the slices'
+//     16-byte-aligned interiors (at most three at each end) with ordinary
+//     loads; the stage's "full" mbarrier completes when both have landed.
+//   Eight consumer warps: merge a full stage straight into the output
+//     staging arrays (each thread MERGE_K consecutive outputs: merge-path
+//     split inside shared memory, then a branch-free serial merge), release
+//     it, and write the chunk back: the aligned interior by a bulk store, the
+//     ends by ordinary stores.  One chunk later, or as soon as the CTA has
+//     nothing to merge, the store is known to be complete and the parent's
+//     counter drops.
 //
-// One persistent cooperative launch runs every round; a grid barrier (bounded
-// spin, error flag on timeout) separates the phases.  Cooperative launch
-// guarantees that all CTAs are resident, so the barrier cannot starve.
+// Progress: chunks are claimed in increasing order and wait only for smaller
+// chunk numbers, so the smallest unfinished chunk always has its inputs
+// complete; every written chunk is announced (at the latest when its CTA goes
+// idle); cooperative launch keeps every CTA resident.  Every wait is bounded
+// and records DERR_TIMEOUT instead of hanging.
 #include "ps_internal.cuh"
 
 namespace ps {
 
 namespace {
 
+constexpr uint32_t FULL_MASK = 0xffffffffu;
 constexpr int SLOT = MERGE_E + 16;   // a staged array: up to 3 + 3 + 3 shift slots
 constexpr int EDGE_SLOTS = 8;        // unaligned elements of one slice (<= 7)
+constexpr int NCONS = MERGE_BLOCK / 32;          // consumer warps
+constexpr int PRODUCER_WARP = NCONS;
+constexpr int SEARCH_WARP = NCONS + 1;
+constexpr int MTHREADS = MERGE_BLOCK + 64;        // + producer warp + search warp
+// Two variants: NST = 3 shared-memory stages with three CTAs per SM, or
+// NST = 2 stages with four CTAs per SM (more CTAs, fewer bytes in flight each).
+template <int NST>
+constexpr int merge_min_ctas() { return NST == 2 ? 4 : 3; }
+#ifndef PS_MERGE_NSEARCH
+#define PS_MERGE_NSEARCH 16
+#endif
+constexpr int NSEARCH = PS_MERGE_NSEARCH;         // chunks a CTA prepares ahead (<= 32)
+static_assert(NSEARCH >= 1 && NSEARCH <= 32, "one search warp");
 
-// Grid barrier in two levels: CTAs arrive at a counter of their group of 32,
-// the last of a group arrives at the global counter, the last group bumps the
-// generation.  Arrivals on 20-odd different words proceed in parallel instead
-// of 600 atomics serialising on one.
-__device__ bool grid_barrier(Ctr* C)
-{
-    __syncthreads();
-    __shared__ uint32_t s_ok;
-    if (threadIdx.x == 0) {
-        uint32_t ok = 1;
-        const uint32_t gen = ld_acquire_u32(&C->bar_gen);
-        __threadfence();
-        const uint32_t grp = blockIdx.x >> 5;
-        const uint32_t ngroups = (gridDim.x + 31) >> 5;
-        const uint32_t gsize = min(32u, gridDim.x - (grp << 5));
-        bool last = false;
-        if (atomicAdd(&C->bar_group[grp], 1u) == gsize - 1) {
-            atomicExch(&C->bar_group[grp], 0u);
-            last = atomicAdd(&C->bar_count, 1u) == ngroups - 1;
-        }
-        if (last) {
-            atomicExch(&C->bar_count, 0u);
-            __threadfence();
-            st_release_u32(&C->bar_gen, gen + 1);
-        } else {
-            // poll with relaxed loads, back off, acquire once the generation moved
-            const long long t0 = clock64();
-            uint32_t nap = 64;
-            while (ld_relaxed_u32(&C->bar_gen) == gen) {
-                __nanosleep(nap);
-                nap = nap < 1024 ? nap * 2 : 1024;
-                if (clock64() - t0 > SPIN_LIMIT_CYCLES) {
-                    set_error(C, DERR_TIMEOUT, 40);
-                    ok = 0;
-                    break;
-                }
-            }
-            fence_acquire_gpu();
-        }
-        __threadfence();
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
+constexpr uint32_t RS_EMPTY = 0, RS_FULL = 1, RS_END = 2;   // ring slot states
 
-// Number of left-run elements among the first d outputs of the stable merge.
-__device__ __forceinline__ uint32_t merge_path(const uint32_t* A, uint32_t la, const uint32_t* B, uint32_t lb,
-                                               uint32_t d)
-{
-    uint32_t lo = d > lb ? d - lb : 0u, hi = min(d, la);
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (A[mid] <= B[d - 1 - mid]) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
+// A chunk whose inputs are complete and whose splits are known.
+struct Prep {
+    GSorted g;             // its merge
+    uint32_t c;            // chunk number
+    uint32_t a0, a1;       // left-child elements before its first / after its last output
+    uint32_t round;
+    unsigned long long t_ready;   // globaltimer when its inputs were found complete
+};
 
 // A contiguous slice of one array: its 16-byte-aligned interior moves by
 // bulk copy, the rest (head / tail, at most 3 elements each, or the whole
@@ -143,14 +127,23 @@ struct Stage {
     uint32_t* ok;            // output chunk start (keys, permutation)
     uint32_t* op;
     uint32_t sok, sop;       // output start inside the output staging arrays
+    Slice osk, osp;          // the output chunk (keys, permutation) as slices
     uint32_t cnt;
-    uint32_t last;           // nonzero: no chunk; the round is over for this CTA
+    uint32_t parent;         // the merge's parent (GSorted index; NONE for a root)
+    uint32_t round;
+    uint32_t last;           // nonzero: no chunk; the CTA's work is over
+    unsigned long long t_ready;
 };
 
-constexpr int NCONS = MERGE_BLOCK / 32;          // consumer warps
-constexpr int MTHREADS = MERGE_BLOCK + 32;        // + the producer warp
-constexpr int NST = 2;                            // shared-memory stages
+// Per-round timeline kept in shared memory by consumer thread 0 and merged
+// into the counters whenever the round of its chunks changes (a CTA receives
+// its chunks in increasing order).
+struct Timeline {
+    unsigned long long ready_min, ready_max, done_min, done_max;
+    uint32_t round;
+};
 
+template <int NST>
 struct __align__(16) MergeSmem {
     uint32_t in_k[NST][SLOT];
     uint32_t in_p[NST][SLOT];
@@ -159,18 +152,36 @@ struct __align__(16) MergeSmem {
     uint64_t full[NST];      // producer -> consumers: the stage holds a chunk
     uint64_t empty[NST];     // consumers -> producer: the stage may be refilled
     Stage st[NST];
+    Prep ring[NSEARCH];      // search lane l -> producer
+    uint32_t ring_state[NSEARCH];
+    uint32_t round_chunk[NPOW + 1];   // first chunk of every round; [NPOW] = all chunks
+    uint32_t err;
+    uint32_t pend;           // consumer thread 0: parent of the written, unannounced chunk
+    Timeline tl;
 };
 
-// Describe chunk q (round-local index; global chunk id c0 + q) of the current round.
-__device__ void describe(const Job& J, uint32_t q, uint32_t c0, uint32_t nch, Stage& S)
+// 228 KiB of shared memory per SM, 1 KiB of it reserved per CTA
+static_assert(sizeof(MergeSmem<2>) <= 233472 / merge_min_ctas<2>() - 1024, "two stages must fit four CTAs per SM");
+static_assert(sizeof(MergeSmem<3>) <= 233472 / merge_min_ctas<3>() - 1024, "three stages must fit three CTAs per SM");
+
+__device__ __forceinline__ uint32_t ld_vol(const uint32_t* p)
 {
-    const uint32_t e = J.chunk_node[c0 + q];
-    const GSorted g = J.gsorted[e];
+    return *(const volatile uint32_t*)p;
+}
+
+__device__ __forceinline__ void st_vol(uint32_t* p, uint32_t v)
+{
+    *(volatile uint32_t*)p = v;
+}
+
+// Producer lane 0: the stage's addresses for a prepared chunk.
+__device__ void describe(const Job& J, const Prep& p, Stage& S)
+{
+    const GSorted& g = p.g;
     const uint32_t total = g.la + g.lb;
-    const uint32_t d0 = (c0 + q - g.chunk_base) * MERGE_E;
+    const uint32_t d0 = (p.c - g.chunk_base) * MERGE_E;
     const uint32_t d1 = min(d0 + (uint32_t)MERGE_E, total);
-    const uint32_t a0 = J.splits[q];
-    const uint32_t a1 = (d1 == total || q + 1 >= nch) ? g.la : J.splits[q + 1];
+    const uint32_t a0 = p.a0, a1 = p.a1;
     const uint32_t b0 = d0 - a0, b1 = d1 - a1;
     const bool src_b = ((g.depth + 1) & 1u) != 0, dst_b = (g.depth & 1u) != 0;
     const uint32_t* ks = (src_b ? J.keysB : J.keysA) + g.goff;
@@ -197,6 +208,11 @@ __device__ void describe(const Job& J, uint32_t q, uint32_t c0, uint32_t nch, St
     S.op = J.want_perm ? (dst_b ? J.permB : J.permA) + g.goff + d0 : nullptr;
     S.sok = shift_of(S.ok);
     S.sop = S.op ? shift_of(S.op) : 0u;
+    S.osk = slice_of(S.ok, S.cnt);
+    S.osp = S.op ? slice_of(S.op, S.cnt) : Slice{0u, 0u, 0u};
+    S.parent = g.parent;
+    S.round = p.round;
+    S.t_ready = p.t_ready;
 }
 
 __device__ __forceinline__ bool aligned16(const void* p)
@@ -205,7 +221,8 @@ __device__ __forceinline__ bool aligned16(const void* p)
 }
 
 // Producer lane 0: announce the stage's bytes and start its bulk copies.
-__device__ void issue_loads(MergeSmem& sm, int s, Ctr* C)
+template <int NST>
+__device__ void issue_loads(MergeSmem<NST>& sm, int s, Ctr* C)
 {
     const Stage& S = sm.st[s];
     uint32_t bytes = 0;
@@ -248,7 +265,9 @@ __device__ void issue_loads(MergeSmem& sm, int s, Ctr* C)
 
 // Producer lane l: the unaligned element l % 8 of slice l / 8 (0: left
 // keys, 1: right keys, 2: left perm, 3: right perm) goes into the stage.
-__device__ __forceinline__ void copy_edge(MergeSmem& sm, int s, int lane)
+// Loads bypass L1: the data were written by other SMs during this launch.
+template <int NST>
+__device__ __forceinline__ void copy_edge(MergeSmem<NST>& sm, int s, int lane)
 {
     const Stage& S = sm.st[s];
     const int which = lane >> 3, j = lane & 7;
@@ -258,8 +277,8 @@ __device__ __forceinline__ void copy_edge(MergeSmem& sm, int s, int lane)
     const Slice& sl = is_perm ? S.slp[side] : S.slk[side];
     const uint32_t i = edge_index(sl, (uint32_t)j);
     if (i == NONE) return;
-    if (is_perm) sm.in_p[s][S.sp[side] + i] = S.gp[side][i];
-    else sm.in_k[s][S.sk[side] + i] = S.gk[side][i];
+    if (is_perm) sm.in_p[s][S.sp[side] + i] = __ldcg(S.gp[side] + i);
+    else sm.in_k[s][S.sk[side] + i] = __ldcg(S.gk[side] + i);
 }
 
 __device__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, Ctr* C, uint32_t where)
@@ -285,211 +304,422 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
+// every committed bulk store but the most recent group has completed
+__device__ __forceinline__ void bulk_wait_all_but_one()
+{
+    asm volatile("cp.async.bulk.wait_group 1;" ::: "memory");
+}
+
+// The chunk written before has reached global memory (its bulk store
+// completed, its edge stores precede a warp barrier this thread passed):
+// make it visible and count it off the parent's dependencies.
+__device__ __forceinline__ void announce(const Job& J, uint32_t parent)
+{
+    fence_proxy_async_global();
+    __threadfence();
+    atomicSub(&J.dep[parent], 1u);
+}
+
+__device__ void timeline_reset(Timeline& t)
+{
+    t.round = NONE;
+    t.ready_min = t.done_min = ~0ull;
+    t.ready_max = t.done_max = 0;
+}
+
+__device__ void timeline_flush(Timeline& t, Ctr* C)
+{
+    if (t.round == NONE) return;
+    atomicMin(&C->round_ns[t.round][0], t.ready_min);
+    atomicMax(&C->round_ns[t.round][1], t.ready_max);
+    atomicMin(&C->round_ns[t.round][2], t.done_min);
+    atomicMax(&C->round_ns[t.round][3], t.done_max);
+    timeline_reset(t);
+}
+
+__device__ void timeline_note(Timeline& t, Ctr* C, uint32_t r, unsigned long long t_ready, unsigned long long t_done)
+{
+    if (r != t.round) {
+        timeline_flush(t, C);
+        t.round = r;
+    }
+    t.ready_min = min(t.ready_min, t_ready);
+    t.ready_max = max(t.ready_max, t_ready);
+    t.done_min = min(t.done_min, t_done);
+    t.done_max = max(t.done_max, t_done);
+}
+
+// ---------------------------------------------------------------- roles
+
+template <int NST>
+__device__ __noinline__ void search_warp(const Job& J, MergeSmem<NST>& sm, Ctr* C)
+{
+    // Each iteration a lane issues the one global access its state needs and
+    // takes the result at the end of the iteration, so the accesses of all
+    // lanes overlap.
+    enum : uint32_t { S_CLAIM, S_NODE, S_INFO, S_WAIT, S_SEARCH, S_PUB, S_DONE };
+    const int lane = threadIdx.x & 31;
+    const uint32_t total_chunks = sm.round_chunk[NPOW];
+    uint32_t state = lane < NSEARCH ? S_CLAIM : S_DONE;
+    uint32_t c = 0, e = 0, d0 = 0, d1 = 0, round = 0;
+    GSorted g = {};
+    uint32_t lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0;
+    long long t_wait = 0;
+    unsigned long long t_ready = 0;
+    uint32_t gap = 1, next_poll = 0;     // a waiting lane polls every gap iterations (1, 2, 4)
+    for (uint32_t iter = 0;; ++iter) {
+        // ---- issue
+        const uint32_t want = __ballot_sync(FULL_MASK, state == S_CLAIM);
+        const int leader = want ? __ffs(want) - 1 : 0;
+        uint32_t base = 0;
+        if (want && lane == leader) base = atomicAdd(&C->chunk_next[0], (uint32_t)__popc(want));
+        uint32_t e_new = 0;
+        if (state == S_NODE) e_new = __ldcg(J.chunk_node + c);
+        GSorted g_new = {};
+        if (state == S_INFO) g_new = J.gsorted[e];
+        const bool poll = state == S_WAIT && iter >= next_poll;
+        uint32_t depv = 1;
+        if (poll) depv = ld_acquire_u32(&J.dep[e]);
+        const bool s0 = state == S_SEARCH && lo0 < hi0, s1 = state == S_SEARCH && lo1 < hi1;
+        const uint32_t m0 = (lo0 + hi0) >> 1, m1 = (lo1 + hi1) >> 1;
+        uint32_t x0 = 0, y0 = 0, x1 = 0, y1 = 0;
+        const uint32_t* A = (((g.depth + 1) & 1u) ? J.keysB : J.keysA) + g.goff;
+        if (s0) {
+            x0 = __ldcg(A + m0);
+            y0 = __ldcg(A + g.la + (d0 - 1u - m0));
+        }
+        if (s1) {
+            x1 = __ldcg(A + m1);
+            y1 = __ldcg(A + g.la + (d1 - 1u - m1));
+        }
+        const bool pub_free = state == S_PUB && ld_vol(&sm.ring_state[lane]) == RS_EMPTY;
+        // ---- take the results
+        if (want) base = __shfl_sync(FULL_MASK, base, leader);
+        if (state == S_CLAIM) {
+            c = base + (uint32_t)__popc(want & ((1u << lane) - 1u));
+            if (c < total_chunks) {
+                state = S_NODE;
+            } else {
+                state = S_DONE;
+                st_vol(&sm.ring_state[lane], RS_END);
+            }
+        } else if (state == S_NODE) {
+            e = e_new;
+            state = S_INFO;
+        } else if (state == S_INFO) {
+            g = g_new;
+            d0 = (c - g.chunk_base) * MERGE_E;
+            d1 = min(d0 + (uint32_t)MERGE_E, g.la + g.lb);
+            uint32_t lo = 0, hi = NPOW;              // last round starting at or before c
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (sm.round_chunk[mid] <= c) lo = mid; else hi = mid;
+            }
+            round = lo;
+            state = S_WAIT;
+            t_wait = clock64();
+            gap = 1;
+            next_poll = iter + 1;
+        } else if (poll) {
+            if (depv == 0u) {
+                lo0 = d0 > g.lb ? d0 - g.lb : 0u;
+                hi0 = min(d0, g.la);
+                lo1 = d1 > g.lb ? d1 - g.lb : 0u;
+                hi1 = min(d1, g.la);
+                t_ready = globaltimer_ns();
+                state = S_SEARCH;
+            } else if (clock64() - t_wait > SPIN_LIMIT_CYCLES) {
+                set_error(C, DERR_TIMEOUT, 45);
+                state = S_DONE;
+                st_vol(&sm.ring_state[lane], RS_END);
+            } else {
+                next_poll = iter + gap;
+                gap = gap < 4u ? gap * 2u : 4u;
+            }
+        } else if (state == S_SEARCH) {
+            if (s0) {
+                if (x0 <= y0) lo0 = m0 + 1u; else hi0 = m0;
+            }
+            if (s1) {
+                if (x1 <= y1) lo1 = m1 + 1u; else hi1 = m1;
+            }
+            if (lo0 >= hi0 && lo1 >= hi1) {      // splits: lo0, lo1
+                Prep& p = sm.ring[lane];
+                p.g = g;
+                p.c = c;
+                p.a0 = lo0;
+                p.a1 = lo1;
+                p.round = round;
+                p.t_ready = t_ready;
+                __threadfence_block();
+                st_vol(&sm.ring_state[lane], RS_FULL);
+                state = S_PUB;
+            }
+        } else if (pub_free) {
+            state = S_CLAIM;
+        }
+        if (__all_sync(FULL_MASK, state == S_DONE)) break;
+        // lane 0 decides for the warp, which must leave the loop together
+        uint32_t stop = 0;
+        if (lane == 0 && (iter & 63u) == 63u) stop = *(volatile uint32_t*)&C->error;
+        if (__shfl_sync(FULL_MASK, stop, 0)) {
+            if (lane < NSEARCH) st_vol(&sm.ring_state[lane], RS_END);
+            break;
+        }
+        const bool moving = state == S_CLAIM || state == S_NODE || state == S_INFO || state == S_SEARCH;
+        if (!__any_sync(FULL_MASK, moving)) __nanosleep(64);
+    }
+}
+
+template <int NST>
+__device__ __noinline__ void producer_warp(const Job& J, MergeSmem<NST>& sm, Ctr* C)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t k = 0;                      // stages filled so far (stage k % NST)
+    long long t_idle = clock64();
+    for (;;) {
+        // the prepared chunk with the smallest number
+        const uint32_t rs = lane < NSEARCH ? ld_vol(&sm.ring_state[lane]) : RS_END;
+        __threadfence_block();
+        const uint32_t key = rs == RS_FULL ? sm.ring[lane].c : 0xffffffffu;
+        const uint32_t m = __reduce_min_sync(FULL_MASK, key);
+        if (m == 0xffffffffu) {
+            if (__all_sync(FULL_MASK, rs == RS_END)) break;
+            // lane 0 decides for the warp, which must leave the loop together
+            uint32_t stop = 0;
+            if (lane == 0) {
+                if (*(volatile uint32_t*)&C->error) {
+                    stop = 1;
+                } else if (clock64() - t_idle > SPIN_LIMIT_CYCLES) {
+                    set_error(C, DERR_TIMEOUT, 46);
+                    stop = 1;
+                }
+            }
+            if (__shfl_sync(FULL_MASK, stop, 0)) break;
+            __nanosleep(32);
+            continue;
+        }
+        t_idle = clock64();
+        const int src = __ffs(__ballot_sync(FULL_MASK, key == m)) - 1;
+        const int s = (int)(k % NST);
+        if (k >= (uint32_t)NST && !mbar_wait_bounded(&sm.empty[s], ((k / NST) - 1u) & 1u, C, 44)) return;
+        ++k;
+        if (lane == 0) {
+            const Prep p = sm.ring[src];
+            __threadfence_block();
+            st_vol(&sm.ring_state[src], RS_EMPTY);
+            sm.st[s].last = 0;
+            describe(J, p, sm.st[s]);
+            fence_proxy_async_global();   // the inputs were written by other CTAs' bulk stores
+            issue_loads(sm, s, C);
+        }
+        __syncwarp();
+        copy_edge(sm, s, lane);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sm.full[s]);
+    }
+    // close the consumers' loop with a stage that carries no chunk
+    const int s = (int)(k % NST);
+    if (k >= (uint32_t)NST && !mbar_wait_bounded(&sm.empty[s], ((k / NST) - 1u) & 1u, C, 47)) return;
+    if (lane == 0) {
+        sm.st[s].last = 1;
+        sm.st[s].cnt = 0;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&sm.full[s], 0);
+        mbar_arrive(&sm.full[s]);
+    }
+    __syncwarp();
+}
+
+template <int NST>
+__device__ __noinline__ void consumer_warps(const Job& J, MergeSmem<NST>& sm, Ctr* C)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool perm = J.want_perm != 0;
+    uint32_t u = 0;                      // stages taken so far (stage u % NST)
+    if (tid == 0) {
+        sm.pend = NONE;
+        timeline_reset(sm.tl);
+    }
+    for (;;) {
+        const int s = (int)(u % NST);
+        const uint32_t parity = (u / NST) & 1u;
+        if (!mbar_try_wait(&sm.full[s], parity)) {
+            // nothing to merge yet: announce the last chunk before waiting
+            if (tid == 0 && sm.pend != NONE) {
+                bulk_wait_all();
+                announce(J, sm.pend);
+                sm.pend = NONE;
+            }
+            if (!mbar_wait_bounded(&sm.full[s], parity, C, 42)) break;
+        }
+        ++u;
+        const Stage& S = sm.st[s];
+        if (S.last) {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm.empty[s]);
+            break;
+        }
+        const uint32_t na = S.na, nb = S.nb, cnt = S.cnt;
+        const uint32_t sok = S.sok, sop = S.sop;
+        const uint32_t* Ak = &sm.in_k[s][S.sk[0]];
+        const uint32_t* Bk = &sm.in_k[s][S.sk[1]];
+        const uint32_t* Ap = &sm.in_p[s][S.sp[0]];
+        const uint32_t* Bp = &sm.in_p[s][S.sp[1]];
+        if (tid == 0) bulk_wait_read_all();         // the previous output has left the staging arrays
+        consumers_sync();
+        const uint32_t x0 = tid * MERGE_K;
+        if (x0 < cnt) {
+            uint32_t lo = x0 > nb ? x0 - nb : 0u, hi = min(x0, na);
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (Ak[mid] <= Bk[x0 - 1 - mid]) lo = mid + 1; else hi = mid;
+            }
+            uint32_t ia = lo, ib = x0 - lo;
+            uint32_t va = ia < na ? Ak[ia] : 0xffffffffu, vb = ib < nb ? Bk[ib] : 0xffffffffu;
+            uint32_t* outk = &sm.out_k[sok + x0];
+            uint32_t* outp = &sm.out_p[sop + x0];
+            const uint32_t nout = min(cnt - x0, (uint32_t)MERGE_K);
+            // branch-free serial merge straight into the staging arrays; an
+            // exhausted side is read at slot 0 (a valid address whose value is
+            // never used)
+#pragma unroll
+            for (int j = 0; j < MERGE_K; ++j) {
+                const bool take_a = ia < na && (ib >= nb || va <= vb);
+                if ((uint32_t)j < nout) {
+                    outk[j] = take_a ? va : vb;
+                    if (perm) outp[j] = take_a ? Ap[ia < na ? ia : 0u] : Bp[ib < nb ? ib : 0u];
+                }
+                ia += take_a;
+                ib += !take_a;
+                const uint32_t nxt = take_a ? Ak[ia < na ? ia : 0u] : Bk[ib < nb ? ib : 0u];
+                va = take_a ? nxt : va;
+                vb = take_a ? vb : nxt;
+            }
+        }
+        __syncwarp();
+        uint32_t parent = NONE, round = 0;
+        unsigned long long t_ready = 0;
+        uint32_t* gok = nullptr;
+        uint32_t* gop = nullptr;
+        Slice ok_sl = {0u, 0u, 0u}, op_sl = {0u, 0u, 0u};
+        if (warp == 0) {                            // read before warp 0 releases the stage
+            parent = S.parent;
+            round = S.round;
+            t_ready = S.t_ready;
+            gok = S.ok;
+            gop = S.op;
+            ok_sl = S.osk;
+            op_sl = S.osp;
+        }
+        if (lane == 0) mbar_arrive(&sm.empty[s]);   // this warp is done with the stage
+        fence_proxy_async_smem();
+        consumers_sync();
+        if (warp != 0) continue;
+        // warp 0 sends the chunk out: the ends by ordinary stores (lanes 0-7
+        // keys, 16-23 permutation), ordered before thread 0's announcement by
+        // __syncwarp; the aligned interior by bulk store
+        if ((lane & 15) < EDGE_SLOTS) {
+            const bool is_perm = lane >= 16;
+            if (!is_perm || perm) {
+                const uint32_t i = edge_index(is_perm ? op_sl : ok_sl, (uint32_t)(lane & 15));
+                if (i != NONE) {
+                    if (is_perm) gop[i] = sm.out_p[sop + i];
+                    else gok[i] = sm.out_k[sok + i];
+                }
+            }
+        }
+        __syncwarp();
+        if (tid == 0) {
+            bool good = true;
+            if (ok_sl.nint) {
+                void* g = gok + ok_sl.head;
+                const void* l = &sm.out_k[sok + ok_sl.head];
+                good = good && aligned16(g) && aligned16(l);
+                if (good) tma_store_1d(g, l, ok_sl.nint * 4u);
+            }
+            if (perm && op_sl.nint) {
+                void* g = gop + op_sl.head;
+                const void* l = &sm.out_p[sop + op_sl.head];
+                const bool g2 = aligned16(g) && aligned16(l);
+                if (g2) tma_store_1d(g, l, op_sl.nint * 4u);
+                good = good && g2;
+            }
+            if (!good) set_error(C, DERR_INTERNAL, 43);
+            bulk_commit();
+            // the previous chunk's store is complete once at most this one is pending
+            if (sm.pend != NONE) {
+                bulk_wait_all_but_one();
+                announce(J, sm.pend);
+            }
+            sm.pend = parent;
+            timeline_note(sm.tl, C, round, t_ready, globaltimer_ns());
+        }
+    }
+    if (tid == 0) {
+        bulk_wait_all();
+        if (sm.pend != NONE) announce(J, sm.pend);
+        timeline_flush(sm.tl, C);
+    }
+}
+
 }  // namespace
 
-__global__ void __launch_bounds__(MTHREADS, 4) k_merge_rounds(Job J)
+template <int NST>
+__global__ void __launch_bounds__(MTHREADS, merge_min_ctas<NST>()) k_merge_rounds(Job J)
 {
     extern __shared__ __align__(16) unsigned char merge_raw[];
-    MergeSmem& sm = *reinterpret_cast<MergeSmem*>(merge_raw);
+    MergeSmem<NST>& sm = *reinterpret_cast<MergeSmem<NST>*>(merge_raw);
     Ctr* C = J.ctr;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const bool producer = warp == NCONS;
-    const bool perm = J.want_perm != 0;
+    const int tid = threadIdx.x, warp = tid >> 5;
     if (tid == 0) {
         for (int s = 0; s < NST; ++s) {
             mbar_init(&sm.full[s], 2);        // expect_tx arrival + edge arrival
             mbar_init(&sm.empty[s], NCONS);   // one arrival per consumer warp
         }
         fence_mbar_init();
+        sm.err = *(volatile uint32_t*)&C->error;
+        if (blockIdx.x == 0) C->merge_t0 = globaltimer_ns();
     }
+    if (tid < NSEARCH) sm.ring_state[tid] = RS_EMPTY;
+    for (int r = tid; r <= NPOW; r += blockDim.x) sm.round_chunk[r] = C->bucket_chunk[r];
     __syncthreads();
-    // stage use counters: the producer fills stages round robin, the consumers
-    // take them in the same order, so both sides keep identical counts
-    uint32_t fills[NST] = {0u, 0u}, uses[NST] = {0u, 0u};
-    uint32_t slot = 0;
-
-    for (int r = 0; r < NPOW; ++r) {
-        if (*(volatile uint32_t*)&C->error) return;
-        const uint32_t e0 = C->bucket_start[r], e1 = C->bucket_start[r + 1];
-        if (e0 == e1) continue;
-        const uint32_t c0 = C->bucket_chunk[r], c1 = C->bucket_chunk[r + 1];
-        const uint32_t nch = c1 - c0;
-        const bool stamp = blockIdx.x == 0 && tid == 0;
-        if (stamp) C->round_ns[r][0] = globaltimer_ns();
-
-        // phase A: the merge-path split of every chunk start, chunks interleaved
-        // over all CTAs so every CTA searches and none idles
-        for (uint32_t q = tid * gridDim.x + blockIdx.x; q < nch; q += gridDim.x * blockDim.x) {
-            const GSorted g = J.gsorted[J.chunk_node[c0 + q]];
-            const uint32_t d = (c0 + q - g.chunk_base) * MERGE_E;
-            const uint32_t* A = (((g.depth + 1) & 1u) ? J.keysB : J.keysA) + g.goff;
-            J.splits[q] = merge_path(A, g.la, A + g.la, g.lb, d);
-        }
-        if (stamp) C->round_ns[r][4] = globaltimer_ns();
-        if (!grid_barrier(C)) return;
-        if (stamp) C->round_ns[r][1] = globaltimer_ns();
-
-        // phase B: chunks handed out dynamically (one atomic per chunk), the
-        // last stage of the round carries no chunk
-        if (producer) {
-            if (lane == 0) fence_proxy_async_global();   // earlier generic writes before async reads
-            __syncwarp();
-            for (;;) {
-                uint32_t q = 0;
-                if (lane == 0) q = atomicAdd(&C->chunk_next[r], 1u);
-                q = __shfl_sync(0xffffffffu, q, 0);
-                const int s = (int)slot;
-                if (fills[s] > 0 && !mbar_wait_bounded(&sm.empty[s], (fills[s] - 1) & 1u, C, 44)) return;
-                ++fills[s];
-                slot = (slot + 1) % NST;
-                if (q >= nch) {                       // close the round for the consumers
-                    if (lane == 0) {
-                        sm.st[s].last = 1;
-                        sm.st[s].cnt = 0;
-                        fence_proxy_async_smem();
-                        mbar_arrive_expect_tx(&sm.full[s], 0);
-                        mbar_arrive(&sm.full[s]);
-                    }
-                    __syncwarp();
-                    break;
-                }
-                if (lane == 0) {
-                    sm.st[s].last = 0;
-                    describe(J, q, c0, nch, sm.st[s]);
-                    issue_loads(sm, s, C);
-                }
-                __syncwarp();
-                copy_edge(sm, s, lane);
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&sm.full[s]);
-            }
-        } else {
-            for (;;) {
-                const int s = (int)slot;
-                if (!mbar_wait_bounded(&sm.full[s], uses[s] & 1u, C, 42)) return;
-                ++uses[s];
-                slot = (slot + 1) % NST;
-                const Stage& S = sm.st[s];
-                if (S.last) {
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&sm.empty[s]);
-                    break;
-                }
-                const uint32_t na = S.na, nb = S.nb, cnt = S.cnt;
-                uint32_t* const gok = S.ok;
-                uint32_t* const gop = S.op;
-                const uint32_t sok = S.sok, sop = S.sop;
-                const uint32_t* Ak = &sm.in_k[s][S.sk[0]];
-                const uint32_t* Bk = &sm.in_k[s][S.sk[1]];
-                const uint32_t* Ap = &sm.in_p[s][S.sp[0]];
-                const uint32_t* Bp = &sm.in_p[s][S.sp[1]];
-                uint32_t ok[MERGE_K], op[MERGE_K];
-                const uint32_t x0 = tid * MERGE_K;
-                if (x0 < cnt) {
-                    uint32_t lo = x0 > nb ? x0 - nb : 0u, hi = min(x0, na);
-                    while (lo < hi) {
-                        const uint32_t mid = (lo + hi) >> 1;
-                        if (Ak[mid] <= Bk[x0 - 1 - mid]) lo = mid + 1; else hi = mid;
-                    }
-                    uint32_t ia = lo, ib = x0 - lo;
-                    uint32_t va = ia < na ? Ak[ia] : 0xffffffffu, vb = ib < nb ? Bk[ib] : 0xffffffffu;
-                    // branch-free serial merge; an exhausted side is read at slot 0
-                    // (a valid address whose value is never used)
-#pragma unroll
-                    for (int j = 0; j < MERGE_K; ++j) {
-                        const bool take_a = ia < na && (ib >= nb || va <= vb);
-                        ok[j] = take_a ? va : vb;
-                        if (perm) op[j] = take_a ? Ap[ia < na ? ia : 0u] : Bp[ib < nb ? ib : 0u];
-                        ia += take_a;
-                        ib += !take_a;
-                        const uint32_t nxt = take_a ? Ak[ia < na ? ia : 0u] : Bk[ib < nb ? ib : 0u];
-                        va = take_a ? nxt : va;
-                        vb = take_a ? vb : nxt;
-                    }
-                }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&sm.empty[s]);   // this warp is done with the stage
-                if (tid == 0) bulk_wait_read_all();         // the previous output has left shared memory
-                consumers_sync();
-                if (x0 < cnt) {
-#pragma unroll
-                    for (int j = 0; j < MERGE_K; ++j) {
-                        if (x0 + j < cnt) {
-                            sm.out_k[sok + x0 + j] = ok[j];
-                            if (perm) sm.out_p[sop + x0 + j] = op[j];
-                        }
-                    }
-                }
-                fence_proxy_async_smem();
-                consumers_sync();
-                // output: aligned interior by bulk store, the ends by ordinary stores
-                const Slice ok_sl = slice_of(gok, cnt);
-                const Slice op_sl = perm ? slice_of(gop, cnt) : Slice{0u, 0u, 0u};
-                if (tid == 0) {
-                    bool good = true;
-                    if (ok_sl.nint) {
-                        void* g = gok + ok_sl.head;
-                        const void* l = &sm.out_k[sok + ok_sl.head];
-                        good = good && aligned16(g) && aligned16(l);
-                        if (good) tma_store_1d(g, l, ok_sl.nint * 4u);
-                    }
-                    if (perm && op_sl.nint) {
-                        void* g = gop + op_sl.head;
-                        const void* l = &sm.out_p[sop + op_sl.head];
-                        const bool g2 = aligned16(g) && aligned16(l);
-                        if (g2) tma_store_1d(g, l, op_sl.nint * 4u);
-                        good = good && g2;
-                    }
-                    if (!good) set_error(C, DERR_INTERNAL, 43);
-                    bulk_commit();
-                }
-                if (warp == 1 && (lane & 15) < EDGE_SLOTS) {   // lanes 0-7: keys, 16-23: permutation
-                    const bool is_perm = lane >= 16;
-                    if (!is_perm || perm) {
-                        const uint32_t i = edge_index(is_perm ? op_sl : ok_sl, (uint32_t)(lane & 15));
-                        if (i != NONE) {
-                            if (is_perm) gop[i] = sm.out_p[sop + i];
-                            else gok[i] = sm.out_k[sok + i];
-                        }
-                    }
-                }
-            }
-            if (tid == 0) {
-                bulk_wait_all();                    // this round's output is in global memory
-                fence_proxy_async_global();
-                if (stamp) C->round_ns[r][2] = globaltimer_ns();
-            }
-        }
-        if (producer) {
-            for (int s = 0; s < NST; ++s) uses[s] = fills[s];
-        } else {
-            for (int s = 0; s < NST; ++s) fills[s] = uses[s];
-        }
-        if (!grid_barrier(C)) return;
-        if (stamp) C->round_ns[r][3] = globaltimer_ns();
-    }
+    if (sm.err) return;
+    if (warp == SEARCH_WARP) search_warp<NST>(J, sm, C);
+    else if (warp == PRODUCER_WARP) producer_warp<NST>(J, sm, C);
+    else consumer_warps<NST>(J, sm, C);
 }
 
-int merge_rounds_grid_for(int num_sms, int ctas_per_sm)
+template <int NST>
+int max_grid(int num_sms)
 {
-    const int mx = merge_rounds_max_grid(num_sms) / num_sms;
+    int per_sm = 0;
+    const int bytes = (int)sizeof(MergeSmem<NST>);
+    cudaFuncSetAttribute(k_merge_rounds<NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_merge_rounds<NST>, MTHREADS, bytes);
+    return num_sms * (per_sm > 0 ? per_sm : 1);
+}
+
+int merge_rounds_max_grid(int num_sms, int stages)
+{
+    return stages == 2 ? max_grid<2>(num_sms) : max_grid<3>(num_sms);
+}
+
+int merge_rounds_grid_for(int num_sms, int ctas_per_sm, int stages)
+{
+    const int mx = merge_rounds_max_grid(num_sms, stages) / num_sms;
     const int k = (ctas_per_sm > 0 && ctas_per_sm < mx) ? ctas_per_sm : mx;
     return num_sms * k;
 }
 
-int merge_rounds_max_grid(int num_sms)
-{
-    int per_sm = 0;
-    cudaFuncSetAttribute(k_merge_rounds, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MergeSmem));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_merge_rounds, MTHREADS, sizeof(MergeSmem));
-    return num_sms * (per_sm > 0 ? per_sm : 1);
-}
-
-cudaError_t launch_merge_rounds(const Job& J, int grid, cudaStream_t s)
+cudaError_t launch_merge_rounds(const Job& J, int grid, int stages, cudaStream_t s)
 {
     void* args[] = {(void*)&J};
-    return cudaLaunchCooperativeKernel((const void*)k_merge_rounds, dim3(grid), dim3(MTHREADS), args,
-                                       sizeof(MergeSmem), s);
+    if (stages == 2)
+        return cudaLaunchCooperativeKernel((const void*)k_merge_rounds<2>, dim3(grid), dim3(MTHREADS), args,
+                                           sizeof(MergeSmem<2>), s);
+    return cudaLaunchCooperativeKernel((const void*)k_merge_rounds<3>, dim3(grid), dim3(MTHREADS), args,
+                                       sizeof(MergeSmem<3>), s);
 }
 
 }  // namespace ps

@@ -284,103 +284,88 @@ __global__ void __launch_bounds__(PLAN_BLOCK) k_depth(Job J)
             const uint32_t g = e - nt;
             GNode gn = J.gnodes[g];
             const Inst& I = J.inst[gn.inst];
-            J.gnodes[g].depth = depth_of(J.na + I.run_base, J.nb + I.run_base, gn.t, I.runs);
+            const uint32_t* na = J.na + I.run_base;
+            const uint32_t* nb = J.nb + I.run_base;
+            J.gnodes[g].depth = depth_of(na, nb, gn.t, I.runs);
+            const uint32_t size = node_size(J.run_start + I.run_base, na, nb, gn.t);
             atomicAdd(&J.ctr->bucket_count[32 - gn.power], 1u);
+            atomicAdd(&J.ctr->bucket_nchunk[32 - gn.power], (size + MERGE_E - 1) / MERGE_E);
         }
     }
 }
 
-// One CTA: order HBM nodes by round, then number their chunks (MERGE_E
-// outputs each) with one exclusive scan over all rounds.
-__global__ void __launch_bounds__(1024) k_bucket(Job J)
+// One small CTA: where each round starts among the HBM merges and among the
+// chunks (prefix sums of the per-round counts), and the table limits.
+__global__ void __launch_bounds__(32) k_bucket_scan(Job J)
 {
-    __shared__ uint32_t cursor[NPOW + 1];
-    __shared__ uint32_t warp_sums[32];
-    __shared__ unsigned long long s_hbm;
+    Ctr* C = J.ctr;
+    if (*(volatile uint32_t*)&C->error) return;
+    if (threadIdx.x != 0) return;
+    uint32_t acc = 0, chunks = 0, rounds = 0;
+    for (int r = 0; r < NPOW; ++r) {
+        C->bucket_start[r] = acc;
+        C->bucket_chunk[r] = chunks;
+        acc += C->bucket_count[r];
+        chunks += C->bucket_nchunk[r];
+        rounds += C->bucket_count[r] ? 1u : 0u;
+    }
+    C->bucket_start[NPOW] = acc;
+    C->bucket_chunk[NPOW] = chunks;
+    C->rounds = rounds;
+    if (chunks > J.chunk_node_cap) set_error(C, DERR_INTERNAL, 31);
+}
+
+// Every HBM merge takes the next place of its round with one 64-bit atomic
+// that advances the round's merge count and chunk count together, so within
+// a round the chunk bases grow with the merge order (the chunk -> merge
+// table below relies on it).
+__global__ void __launch_bounds__(PLAN_BLOCK) k_bucket(Job J)
+{
     Ctr* C = J.ctr;
     if (*(volatile uint32_t*)&C->error) return;
     const uint32_t ng = min(C->n_gnodes, J.entry_cap);
-    if (threadIdx.x == 0) {
-        uint32_t acc = 0, rounds = 0;
-        for (int r = 0; r < NPOW; ++r) {
-            C->bucket_start[r] = acc;
-            cursor[r] = acc;
-            acc += C->bucket_count[r];
-            rounds += C->bucket_count[r] ? 1u : 0u;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t base = blockIdx.x * blockDim.x; base < ng; base += stride) {
+        const uint32_t e = base + threadIdx.x;
+        unsigned long long size = 0;
+        if (e < ng) {
+            const GNode gn = J.gnodes[e];
+            const Inst& I = J.inst[gn.inst];
+            const uint32_t* rs = J.run_start + I.run_base;
+            const uint32_t lo = rs[J.na[I.run_base + gn.t]];
+            const uint32_t mid = rs[gn.t];
+            const uint32_t hi = rs[J.nb[I.run_base + gn.t]];
+            const uint32_t r = 32 - gn.power;
+            const uint32_t nch = (hi - lo + MERGE_E - 1) / MERGE_E;
+            const unsigned long long old = atomicAdd(&C->bucket_cursor[r], (1ull << 40) | nch);
+            const uint32_t at = C->bucket_start[r] + (uint32_t)(old >> 40);
+            GSorted o;
+            o.goff = I.off + lo;
+            o.la = mid - lo;
+            o.lb = hi - mid;
+            o.chunk_base = C->bucket_chunk[r] + (uint32_t)(old & ((1ull << 40) - 1));
+            o.depth = gn.depth;
+            o.parent = NONE;                  // linked by k_chunk_nodes
+            o.pad = 0;
+            if (at < C->bucket_start[r + 1]) {
+                J.gsorted[at] = o;
+                J.dep[at] = 0;
+                J.gidx[I.run_base + gn.t] = at;
+            } else {
+                set_error(C, DERR_INTERNAL, 32);
+            }
+            size = hi - lo;
         }
-        C->bucket_start[NPOW] = acc;
-        s_hbm = 0;
-        C->rounds = rounds;
-    }
-    __syncthreads();
-    unsigned long long hbm = 0;
-    for (uint32_t e = threadIdx.x; e < ng; e += blockDim.x) {
-        const GNode gn = J.gnodes[e];
-        const Inst& I = J.inst[gn.inst];
-        const uint32_t* rs = J.run_start + I.run_base;
-        const uint32_t lo = rs[J.na[I.run_base + gn.t]];
-        const uint32_t mid = rs[gn.t];
-        const uint32_t hi = rs[J.nb[I.run_base + gn.t]];
-        const uint32_t at = atomicAdd(&cursor[32 - gn.power], 1u);
-        GSorted o;
-        o.goff = I.off + lo;
-        o.la = mid - lo;
-        o.lb = hi - mid;
-        o.chunk_base = (hi - lo + MERGE_E - 1) / MERGE_E;   // chunk count for now
-        o.depth = gn.depth;
-        J.gsorted[at] = o;
-        hbm += hi - lo;
-    }
-    atomicAdd(&s_hbm, hbm);
-    __syncthreads();
-    // exclusive scan of the chunk counts: each thread owns a contiguous segment
-    const uint32_t per = (ng + blockDim.x - 1) / blockDim.x;
-    const uint32_t b0 = min(ng, threadIdx.x * per), b1 = min(ng, b0 + per);
-    uint32_t local = 0;
-    for (uint32_t e = b0; e < b1; ++e) local += J.gsorted[e].chunk_base;
-    // block exclusive scan of `local`
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t x = local;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(FULL, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) warp_sums[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t w = warp_sums[lane];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(FULL, w, o);
-            if (lane >= o) w += y;
-        }
-        warp_sums[lane] = w;
-    }
-    __syncthreads();
-    uint32_t run = (warp ? warp_sums[warp - 1] : 0u) + x - local;
-    for (uint32_t e = b0; e < b1; ++e) {
-        const uint32_t cnt = J.gsorted[e].chunk_base;
-        J.gsorted[e].chunk_base = run;
-        run += cnt;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        C->hbm_elems = s_hbm;
-        const uint32_t total_chunks = warp_sums[31];
-        for (int r = 0; r <= NPOW; ++r) {
-            const uint32_t e = C->bucket_start[r];
-            C->bucket_chunk[r] = e < ng ? J.gsorted[e].chunk_base : total_chunks;
-        }
-        // per-round chunk counts must fit the split table
-        for (int r = 0; r < NPOW; ++r)
-            if (C->bucket_chunk[r + 1] - C->bucket_chunk[r] + 1 > J.split_cap) set_error(C, DERR_INTERNAL, 30);
-        if (total_chunks > J.chunk_node_cap) set_error(C, DERR_INTERNAL, 31);
+        for (int o = 16; o > 0; o >>= 1) size += __shfl_xor_sync(FULL, size, o);
+        if ((threadIdx.x & 31) == 0 && size) atomicAdd(&C->hbm_elems, size);
     }
 }
 
 // Chunk -> merge table for every round (chunk ids are global across rounds):
 // each thread covers 32 consecutive chunks with one binary search and a walk.
+// Then every HBM merge is linked to its parent merge (which is larger, hence
+// an HBM merge too) and adds its chunk count to the parent's dependencies.
 __global__ void __launch_bounds__(PLAN_BLOCK) k_chunk_nodes(Job J)
 {
     if (*(volatile uint32_t*)&J.ctr->error) return;
@@ -388,6 +373,21 @@ __global__ void __launch_bounds__(PLAN_BLOCK) k_chunk_nodes(Job J)
     const uint32_t ng = min(C->n_gnodes, J.entry_cap);
     const uint32_t total = C->bucket_chunk[NPOW];
     if (ng == 0 || total > J.chunk_node_cap) return;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < ng; i += gridDim.x * blockDim.x) {
+        const GNode gn = J.gnodes[i];
+        const Inst& I = J.inst[gn.inst];
+        const uint32_t me = J.gidx[I.run_base + gn.t];
+        const uint32_t p = parent_of(J.power + I.run_base, J.na + I.run_base, J.nb + I.run_base, gn.t, I.runs);
+        if (p == NONE) continue;                 // the instance's root
+        const uint32_t par = J.gidx[I.run_base + p];
+        if (me >= ng || par >= ng) {
+            set_error(J.ctr, DERR_INTERNAL, 33);
+            continue;
+        }
+        J.gsorted[me].parent = par;
+        const GSorted g = J.gsorted[me];
+        atomicAdd(&J.dep[par], (g.la + g.lb + MERGE_E - 1) / MERGE_E);
+    }
     const uint32_t groups = (total + 31) / 32;
     for (uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x; gi < groups; gi += gridDim.x * blockDim.x) {
         const uint32_t c0 = gi * 32, c1 = min(c0 + 32, total);
@@ -449,7 +449,8 @@ cudaError_t launch_plan(const Job& J, int grid, cudaStream_t s)
     k_nodes<<<grid, PLAN_BLOCK, 0, s>>>(J);
     k_classify<<<grid, PLAN_BLOCK, 0, s>>>(J);
     k_depth<<<grid, PLAN_BLOCK, 0, s>>>(J);
-    k_bucket<<<1, 1024, 0, s>>>(J);
+    k_bucket_scan<<<1, 32, 0, s>>>(J);
+    k_bucket<<<grid, PLAN_BLOCK, 0, s>>>(J);
     k_chunk_nodes<<<grid, PLAN_BLOCK, 0, s>>>(J);
     return cudaGetLastError();
 }

@@ -100,14 +100,20 @@ __global__ void __launch_bounds__(1024) k_setup(Job J)
         C->runs_total = 0;
         C->n_total = 0;
         C->hbm_elems = 0;
+        C->merge_t0 = 0;
     }
     if (threadIdx.x < 32) C->bar_group[threadIdx.x] = 0;
     for (int r = threadIdx.x; r < NPOW + 2; r += blockDim.x) {
         if (r < NPOW) {
-            for (int i = 0; i < 5; ++i) C->round_ns[r][i] = 0;
+            C->round_ns[r][0] = C->round_ns[r][2] = ~0ull;   // minima
+            C->round_ns[r][1] = C->round_ns[r][3] = 0;       // maxima
             C->chunk_next[r] = 0;
         }
-        if (r < NPOW + 1) C->bucket_count[r] = 0;
+        if (r < NPOW + 1) {
+            C->bucket_count[r] = 0;
+            C->bucket_nchunk[r] = 0;
+            C->bucket_cursor[r] = 0;
+        }
         C->bucket_start[r] = 0;
         C->bucket_chunk[r] = 0;
     }
@@ -238,14 +244,22 @@ __global__ void __launch_bounds__(RUN_BLOCK) k_runs(Job J)
         const uint32_t rem = n - B;
         const uint32_t* a = J.keysA + I.off;
 
-        // 1. descent bitmask: bit k <-> position B + k (the end n counts as one)
-        for (int w = warp; w < RUN_WORDS; w += RUN_BLOCK / 32) {
-            const unsigned long long P = (unsigned long long)B + (unsigned)(w * 32 + lane);
-            bool d = false;
-            if (P == n) d = true;
-            else if (P < n && P > 0) d = a[P - 1] > a[P];
+        // 1. descent bitmask: bit k <-> position B + k (the end n counts as one).
+        //    Every load of a thread is issued before the first comparison, so a
+        //    CTA keeps its whole window (RUN_LOADS keys per thread) in flight.
+        uint32_t cur[RUN_LOADS], prv[RUN_LOADS];
+#pragma unroll
+        for (int j = 0; j < RUN_LOADS; ++j) {
+            const unsigned long long P = (unsigned long long)B + (unsigned)(j * RUN_BLOCK + tid);
+            cur[j] = P < n ? __ldg(a + P) : 0u;
+            prv[j] = (P > 0 && P < n) ? __ldg(a + P - 1) : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < RUN_LOADS; ++j) {
+            const unsigned long long P = (unsigned long long)B + (unsigned)(j * RUN_BLOCK + tid);
+            const bool d = P == n || (P < n && P > 0 && prv[j] > cur[j]);
             const uint32_t word = __ballot_sync(FULL, d);
-            if (lane == 0) bits[w] = word;
+            if (lane == 0) bits[j * (RUN_BLOCK / 32) + warp] = word;
         }
         __syncthreads();
 
