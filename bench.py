@@ -55,7 +55,7 @@ WORKLOADS = {
 }
 FLUSH_BYTES = 512 << 20
 BYTES_PER_MERGED_ELEM = 16   # key + perm entry read, key + perm entry written
-LAUNCHES_PER_BATCH = 12      # one batched Pingpong call: setup, runs, 7 planning kernels, tiles, rounds, finish
+LAUNCHES_PER_BATCH = 13      # one batched Pingpong call: setup, 2 run detection, 7 planning, tiles, merges, finish
 
 
 def parse():

@@ -35,7 +35,7 @@ struct ps_ctx {
 namespace {
 
 constexpr unsigned long long LIMIT_N = 0xffffffffull;  // instance sizes and totals < 2^32
-constexpr uint32_t LAUNCHES_PER_CALL = 12;  // setup, runs, 7 planning kernels, tiles, rounds, finish
+constexpr uint32_t LAUNCHES_PER_CALL = 13;  // setup, 2 run detection, 7 planning, tiles, merges, finish
 constexpr uint32_t NPHASES = 6;
 
 struct DeviceGuard {
@@ -242,7 +242,7 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
         return PS_ECUDA;
     }
     c->num_sms = prop.multiProcessorCount;
-    c->grid_runs = c->num_sms * 8;
+    c->grid_runs = std::min(c->num_sms * ps::RUN_GRID_PER_SM, ps::RUN_RANGES_MAX);
     c->grid_plan = c->num_sms * 8;
     c->grid_tiles = ps::tiles_max_grid(c->num_sms);
     // merge_ctas_per_sm: 4 selects the two-stage variant (four CTAs per SM), 1-3
@@ -311,9 +311,10 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
         if (st == PS_OK && cfg->want_perm) st = dev_alloc(c, &J.permB, max_total);
     }
     if (st == PS_OK) st = dev_alloc(c, &J.inst, c->max_count);
-    if (st == PS_OK) st = dev_alloc(c, &J.chunk_status, chunk_cap);
     if (st == PS_OK) st = dev_alloc(c, &J.chunk_map, chunk_cap * ps::MAP_STATES);
-    if (st == PS_OK) st = dev_alloc(c, &J.chunk_incl, chunk_cap);
+    if (st == PS_OK) st = dev_alloc(c, &J.chunk_info, chunk_cap);
+    if (st == PS_OK) st = dev_alloc(c, &J.range_agg, (size_t)c->grid_runs * ps::MAP_STATES);
+    if (st == PS_OK) st = dev_alloc(c, &J.range_entry, (size_t)c->grid_runs);
     if (st == PS_OK) st = dev_alloc(c, &J.run_start, slot_cap);
     if (st == PS_OK) st = dev_alloc(c, &J.kappa, slot_cap);
     if (st == PS_OK) st = dev_alloc(c, &J.power, slot_cap);
@@ -337,12 +338,11 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
     }
     if (st == PS_OK && cudaMallocHost(&c->h_ctr, sizeof(ps::Ctr)) != cudaSuccess) st = PS_ENOMEM;
     if (st == PS_OK && cudaMallocHost(&c->h_inst, sizeof(ps::Inst)) != cudaSuccess) st = PS_ENOMEM;
-    if (st == PS_OK && (cudaMemset(J.chunk_status, 0, chunk_cap * sizeof(uint32_t)) != cudaSuccess ||
-                        cudaMemset(J.ctr, 0, sizeof(ps::Ctr)) != cudaSuccess))
+    if (st == PS_OK && cudaMemset(J.ctr, 0, sizeof(ps::Ctr)) != cudaSuccess)
         st = PS_ECUDA;
     if (st == PS_OK && cudaDeviceSynchronize() != cudaSuccess) st = PS_ECUDA;
     // every table the kernels write must exist (permB only with want_perm)
-    if (st == PS_OK && ((!vm && !J.keysB) || !J.inst || !J.chunk_status || !J.chunk_map || !J.chunk_incl ||
+    if (st == PS_OK && ((!vm && !J.keysB) || !J.inst || !J.chunk_map || !J.chunk_info || !J.range_agg || !J.range_entry ||
                         !J.run_start || !J.kappa || !J.power || !J.na || !J.nb || !J.tiles || !J.gnodes ||
                         !J.gsorted || !J.dep || !J.chunk_node || !J.ctr ||
                         (!vm && cfg->want_perm && !J.permB) || (vm && (!J.pool_keys || !J.pt || !J.front))))

@@ -3,7 +3,8 @@
 // Pipeline of one call (single instance = batch of one):
 //   k_setup        per-instance sizes, minrun (Sec. 5), chunk / slot bases
 //   k_runs         run detection with minrun extension (ExtractRun, Sec. 2/5):
-//                  a chunked chain scan with decoupled look-back
+//                  chunk maps of the chain scan, folded per range, scanned
+//   k_runs_emit    run starts of every chunk from its entry state
 //   k_kappa        fixed-point run midpoints (the quantities Power compares)
 //   k_nodes        Power per boundary (Sec. 2 Theorem) and the element range
 //                  of the merge Algorithm 1 performs at that boundary
@@ -33,6 +34,12 @@ static_assert(RUN_WORDS * 32 % RUN_BLOCK == 0, "the bitmask window is a whole nu
 constexpr int MAP_STATES = 64;    // entry states of a chunk: minrun (<= 63) + 1
 constexpr int RUN_REC = RUN_CHUNK / 32 + 2;  // run starts one chain can put in a chunk
 constexpr uint32_t STATE_END = 255;
+constexpr uint32_t CHUNK_FORCED = 1u << 31;   // chunk_info: every step in the chunk is forced
+constexpr uint32_t CHUNK_FIRST = 1u << 30;    // chunk_info: the instance's first chunk
+constexpr uint32_t RANGE_RESET = 1u << 31;    // range map word: the range restarts an instance
+constexpr uint32_t RANGE_COUNT_MASK = 0x7fffffffu;
+constexpr int RUN_GRID_PER_SM = 4;            // run-detection CTAs (chunk ranges) per SM
+constexpr int RUN_RANGES_MAX = 1024;
 
 constexpr int MERGE_BLOCK = 256;
 constexpr int MERGE_K = 9;        // outputs per thread (odd: conflict-free shared-memory strides)
@@ -88,8 +95,7 @@ struct GSorted {
 struct Ctr {
     uint32_t error;
     uint32_t err_where;
-    uint32_t epoch;                    // bumped by every call (chunk status words carry it)
-    uint32_t chunk_ticket;
+    uint32_t runs_done;                // run-detection CTAs finished (the last one scans)
     uint32_t total_chunks;
     unsigned long long total_slots;
     uint32_t n_tiles;
@@ -145,9 +151,10 @@ struct Job {
     unsigned long long max_n;   // limits the offsets table is checked against
     unsigned long long max_total;
     Inst* inst;
-    uint32_t* chunk_status;
-    uint32_t* chunk_map;        // MAP_STATES per chunk
-    unsigned long long* chunk_incl;
+    uint32_t* chunk_map;        // MAP_STATES per chunk: (runs << 8) | exit state, per entry state
+    uint32_t* chunk_info;       // per chunk: CHUNK_FORCED | CHUNK_FIRST | first descent offset
+    uint32_t* range_agg;        // MAP_STATES per run-detection CTA: its range's map
+    unsigned long long* range_entry;   // per run-detection CTA: (runs before << 8) | entry state
     uint32_t* run_start;
     uint32_t* kappa;
     uint8_t* power;

@@ -15,14 +15,22 @@
 // so a chunk has at most minrun + 1 <= 64 entry states.  Each chunk walks the
 // chain from every entry state (one lane per state) over its descent bitmask,
 // which gives a map  entry state -> (exit state of the next chunk, runs
-// started in this chunk).  A decoupled look-back composes the maps of the
-// predecessors (chunks are claimed in order through an atomic ticket, so a
-// predecessor is always resident or finished) to find the real entry state
-// and the number of runs before the chunk; the chunk then writes its run
-// starts.  The descent bitmask reaches RUN_HALO positions past the chunk, so a
-// forced step from inside the chunk (length <= 63) is always decided locally;
-// a natural run that runs past the halo ends at the next chunk's D0, which is
-// one of that chunk's entry states.
+// started in this chunk).  The descent bitmask reaches RUN_HALO positions past
+// the chunk, so a forced step from inside the chunk (length <= 63) is always
+// decided locally; a natural run that runs past the halo ends at the next
+// chunk's D0, which is one of that chunk's entry states.  An instance's first
+// chunk is entered at state 0 whatever came before: its map is constant, and
+// it restarts the run count.
+//
+// The maps are composed by a reduce-then-scan.  k_runs: every CTA owns a
+// contiguous range of chunks, computes their maps and folds them into one
+// 64-entry map for the range; the last CTA to finish walks the ranges' maps
+// in order and records the entry state and run count at every range start.
+// k_runs_emit: every CTA walks its range's chunk maps from that entry,
+// giving each chunk's entry state and the number of runs before it, and
+// writes the chunk's run starts -- in closed form when every step in the
+// chunk is forced (the usual case for unsorted data), otherwise by walking
+// the one chain it actually takes over the chunk's descent bitmask.
 #include "ps_internal.cuh"
 
 namespace ps {
@@ -87,9 +95,7 @@ __global__ void __launch_bounds__(1024) k_setup(Job J)
         s_bad = 0;
         C->error = 0;
         C->err_where = 0;
-        C->epoch = (C->epoch + 1) & 0x3fffffffu;          // never 0: fresh words read "not ready"
-        if (C->epoch == 0) C->epoch = 1;
-        C->chunk_ticket = 0;
+        C->runs_done = 0;
         C->n_tiles = 0;
         C->n_gnodes = 0;
         C->rounds = 0;
@@ -213,219 +219,376 @@ __device__ __forceinline__ int next_desc(const uint32_t* bits, int k0, int kmax)
     return (w << 5) + __ffs(word) - 1;
 }
 
+constexpr int KMAX = RUN_WORDS * 32;
+constexpr int WIN = 32;                      // maps staged in shared memory per batch
+
+// The chunk g of instance qi as seen by both kernels.
+struct ChunkView {
+    uint32_t qi, c, n, m, B, E, span, rem;
+    const uint32_t* a;
+};
+
+// qi: the instance of the previous chunk of the same range (NONE at the
+// range start); chunks of a range are consecutive, so it only moves forward.
+__device__ __forceinline__ ChunkView chunk_view(const Job& J, uint32_t g, uint32_t& qi)
+{
+    ChunkView v;
+    if (qi == NONE) {
+        qi = find_inst(J.count, g, [&](uint32_t i) { return (unsigned long long)J.inst[i].chunk_base; });
+    } else {
+        while (qi + 1 < J.count && J.inst[qi + 1].chunk_base <= g) ++qi;
+    }
+    v.qi = qi;
+    const Inst& I = J.inst[v.qi];
+    v.c = g - I.chunk_base;
+    v.n = I.n;
+    v.m = I.minrun;
+    v.B = v.c * RUN_CHUNK;
+    v.E = min(v.B + (uint32_t)RUN_CHUNK, v.n);
+    v.span = v.E - v.B;
+    v.rem = v.n - v.B;
+    v.a = J.keysA + I.off;
+    return v;
+}
+
+// The chunk's key window [W0, W1), W0 = max(B, 1) - 1 (the key before the
+// chunk, when there is one), W1 = min(B + KMAX, n), staged in shared memory
+// by asynchronous copies (cp.async: no registers held while they fly): the
+// 16-byte-aligned interior 16 bytes at a time, the at most three keys at each
+// end 4 bytes at a time.  Key x sits at slot x - W0 + shift, where shift
+// keeps the slot congruent to the global address modulo 16 bytes.
+constexpr int WIN_SLOTS = KMAX + 8;
+
+struct KeyWindow {
+    uint32_t W0, len, shift;
+};
+
+__device__ __forceinline__ KeyWindow window_of(const ChunkView& v)
+{
+    KeyWindow w;
+    w.W0 = v.B > 0 ? v.B - 1 : 0u;
+    const uint32_t W1 = (uint32_t)min((unsigned long long)v.B + KMAX, (unsigned long long)v.n);
+    w.len = W1 - w.W0;
+    w.shift = (uint32_t)(((uintptr_t)(v.a + w.W0) >> 2) & 3u);
+    return w;
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(smem)), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(smem)), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Start staging the window (one commit group per call).
+__device__ __forceinline__ void stage_keys(const ChunkView& v, const KeyWindow& w, uint32_t* keys)
+{
+    const int tid = threadIdx.x;
+    const uint32_t* g = v.a + w.W0;
+    const uint32_t head = min((4u - w.shift) & 3u, w.len);
+    const uint32_t nvec = (w.len - head) >> 2;
+    for (uint32_t i = tid; i < nvec; i += RUN_BLOCK)
+        cp_async16(&keys[w.shift + head + 4 * i], g + head + 4 * i);
+    const uint32_t tail0 = head + 4 * nvec;
+    for (uint32_t x = tid; x < head; x += RUN_BLOCK) cp_async4(&keys[w.shift + x], g + x);
+    for (uint32_t x = tail0 + tid; x < w.len; x += RUN_BLOCK) cp_async4(&keys[w.shift + x], g + x);
+    cp_async_commit();
+}
+
+// Descent bitmask of the chunk from its staged window: bit k <-> position
+// B + k (the end n counts as one).
+__device__ __forceinline__ void bits_from_keys(const ChunkView& v, const KeyWindow& w, const uint32_t* keys,
+                                               uint32_t* bits)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+#pragma unroll 4
+    for (int j = 0; j < RUN_LOADS; ++j) {
+        const unsigned long long P = (unsigned long long)v.B + (unsigned)(j * RUN_BLOCK + tid);
+        bool d = P == v.n;
+        if (P < v.n && P > 0) {
+            const uint32_t x = (uint32_t)P - w.W0 + w.shift;
+            d = keys[x - 1] > keys[x];
+        }
+        const uint32_t word = __ballot_sync(FULL, d);
+        if (lane == 0) bits[j * (RUN_BLOCK / 32) + warp] = word;
+    }
+}
+
+// Can any step from inside the chunk be natural?  Only if two consecutive
+// descents (or position 0 and the first descent) lie at least minrun apart;
+// otherwise every chain is forced all the way and has a closed form.
+__device__ __forceinline__ bool chunk_may_natural(const ChunkView& v, const uint32_t* bits)
+{
+    const int tid = threadIdx.x;
+    bool may = false;
+    for (int w = tid; w < RUN_WORDS && w * 32 < (int)v.span; w += RUN_BLOCK) {
+        uint32_t word = bits[w];
+        if (w == 0) word |= 1u;                    // position 0 starts a gap too
+        while (word) {
+            const int e = w * 32 + __ffs(word) - 1;
+            word &= word - 1;
+            if ((uint32_t)e >= v.span) break;
+            if (next_desc(bits, e + 1, KMAX) - e >= (int)v.m) { may = true; break; }
+        }
+        if (may) break;
+    }
+    return __syncthreads_or(may) != 0;
+}
+
+// Exit state of a chain that stopped at chunk offset k (or ran past the halo).
+__device__ __forceinline__ uint32_t exit_state(const ChunkView& v, int k, bool symbolic)
+{
+    // the last chunk's chains all end at n; elsewhere the exit is an entry state
+    // of the next chunk (a position past the next chunk's first minrun positions
+    // can only be its D0, even when it is n)
+    if (v.E == v.n) return STATE_END;
+    if (symbolic) return v.m;
+    const uint32_t x = (uint32_t)k - v.span;
+    return x < v.m ? x : v.m;
+}
+
+// Start offset of the chain entered in state s (s < m: offset s; s = m: the
+// first descent), or -1 when no run starts in the chunk from there.
+__device__ __forceinline__ int entry_offset(const ChunkView& v, const uint32_t* bits, uint32_t s)
+{
+    if (s < v.m) return (int)s;
+    const int d0 = next_desc(bits, 0, KMAX);
+    return (d0 >= KMAX || (uint32_t)d0 >= v.span) ? -1 : d0;
+}
+
+// Map entry of state s: (runs started in the chunk << 8) | exit state.
+__device__ uint32_t chain_map(const ChunkView& v, const uint32_t* bits, uint32_t s, bool walk)
+{
+    const int k0 = entry_offset(v, bits, s);
+    if (k0 < 0) return v.E == v.n ? STATE_END : v.m;
+    if (!walk) {
+        // forced steps only: starts k0, k0 + m, k0 + 2m, ... below span
+        const uint32_t cnt = (uint32_t)k0 < v.span ? (v.span - (uint32_t)k0 + v.m - 1) / v.m : 0u;
+        const uint32_t ex = v.E == v.n ? STATE_END : (uint32_t)k0 + cnt * v.m - v.span;   // < m
+        return (cnt << 8) | ex;
+    }
+    uint32_t cnt = 0;
+    int k = k0;
+    bool symbolic = false;
+    while ((uint32_t)k < v.span) {
+        ++cnt;
+        const int d = next_desc(bits, k + 1, KMAX);
+        if (d >= KMAX) { symbolic = true; break; }   // f = d = next chunk's D0
+        k = max(d, (int)min((uint32_t)k + v.m, v.rem));
+    }
+    return (cnt << 8) | exit_state(v, k, symbolic);
+}
+
+// One step of the scan: (runs so far << 8 | state) through map entry word f,
+// where f already includes a restart when the chunk begins an instance.
+__device__ __forceinline__ unsigned long long apply_map(unsigned long long at, const uint32_t* map, bool restart)
+{
+    const uint32_t st = (uint32_t)(at & 0xffu);
+    const uint32_t f = map[st < (uint32_t)MAP_STATES ? st : 0u];
+    const unsigned long long before = restart ? 0ull : (at >> 8);
+    return ((before + ((f & RANGE_COUNT_MASK) >> 8)) << 8) | (f & 0xffu);
+}
+
 }  // namespace
 
+// Pass 1: chunk maps, range maps, and (by the last CTA) the range entries.
 __global__ void __launch_bounds__(RUN_BLOCK) k_runs(Job J)
 {
+    __shared__ __align__(16) uint32_t keys[2][WIN_SLOTS];   // double-buffered key windows
     __shared__ uint32_t bits[RUN_WORDS];
-    __shared__ uint16_t rec[MAP_STATES][RUN_REC];
     __shared__ uint32_t mapv[MAP_STATES];
-    __shared__ uint32_t s_g, s_entry, s_prefix, s_abort;
+    __shared__ uint32_t agg[MAP_STATES];     // (runs << 8 | state) after the range so far, per entry state
+    __shared__ uint32_t s_last, s_reset;
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     Ctr* C = J.ctr;
-    const uint32_t epoch = C->epoch;
-    const uint32_t ST_AGG = epoch * 4u + 1u, ST_INC = epoch * 4u + 2u;
-    const int KMAX = RUN_WORDS * 32;
     if (*(volatile uint32_t*)&C->error) return;
+    const uint32_t T = C->total_chunks, G = gridDim.x;
+    const uint32_t K = (T + G - 1) / G;
+    const uint32_t g0 = min(blockIdx.x * K, T), g1 = min(g0 + K, T);
+    if (tid < MAP_STATES) agg[tid] = (uint32_t)tid;
+    if (tid == 0) s_reset = 0;
+    __syncthreads();
 
-    for (;;) {
-        if (tid == 0) s_g = atomicAdd(&C->chunk_ticket, 1u);
-        __syncthreads();
-        const uint32_t g = s_g;
-        if (g >= C->total_chunks) return;
-        const uint32_t qi = find_inst(J.count, g, [&](uint32_t i) { return (unsigned long long)J.inst[i].chunk_base; });
-        const Inst I = J.inst[qi];
-        const uint32_t c = g - I.chunk_base;
-        const uint32_t n = I.n, m = I.minrun;
-        const uint32_t B = c * RUN_CHUNK;
-        const uint32_t E = min(B + (uint32_t)RUN_CHUNK, n);
-        const uint32_t span = E - B;
-        const uint32_t rem = n - B;
-        const uint32_t* a = J.keysA + I.off;
-
-        // 1. descent bitmask: bit k <-> position B + k (the end n counts as one).
-        //    Every load of a thread is issued before the first comparison, so a
-        //    CTA keeps its whole window (RUN_LOADS keys per thread) in flight.
-        uint32_t cur[RUN_LOADS], prv[RUN_LOADS];
-#pragma unroll
-        for (int j = 0; j < RUN_LOADS; ++j) {
-            const unsigned long long P = (unsigned long long)B + (unsigned)(j * RUN_BLOCK + tid);
-            cur[j] = P < n ? __ldg(a + P) : 0u;
-            prv[j] = (P > 0 && P < n) ? __ldg(a + P - 1) : 0u;
-        }
-#pragma unroll
-        for (int j = 0; j < RUN_LOADS; ++j) {
-            const unsigned long long P = (unsigned long long)B + (unsigned)(j * RUN_BLOCK + tid);
-            const bool d = P == n || (P < n && P > 0 && prv[j] > cur[j]);
-            const uint32_t word = __ballot_sync(FULL, d);
-            if (lane == 0) bits[j * (RUN_BLOCK / 32) + warp] = word;
+    uint32_t qi = NONE;
+    ChunkView vn = {};
+    KeyWindow wn = {};
+    if (g0 < g1) {
+        vn = chunk_view(J, g0, qi);
+        wn = window_of(vn);
+        stage_keys(vn, wn, keys[0]);
+    }
+    for (uint32_t g = g0; g < g1; ++g) {
+        const ChunkView v = vn;
+        const KeyWindow w = wn;
+        const int buf = (int)((g - g0) & 1u);
+        // the next chunk's keys fly while this one is scanned
+        if (g + 1 < g1) {
+            vn = chunk_view(J, g + 1, qi);
+            wn = window_of(vn);
+            stage_keys(vn, wn, keys[buf ^ 1]);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
         __syncthreads();
-
-        // 2a. can any step from inside this chunk be natural?  Only if two
-        //     consecutive descents (or position 0 and the first descent) lie at
-        //     least minrun apart; otherwise every chain is forced all the way
-        //     and has a closed form (the usual case for unsorted data).
-        bool may_natural = false;
-        for (int w = tid; w < RUN_WORDS && w * 32 < (int)span; w += RUN_BLOCK) {
-            uint32_t word = bits[w];
-            if (w == 0) word |= 1u;                    // position 0 starts a gap too
-            while (word) {
-                const int e = w * 32 + __ffs(word) - 1;
-                word &= word - 1;
-                if ((uint32_t)e >= span) break;
-                if (next_desc(bits, e + 1, KMAX) - e >= (int)m) { may_natural = true; break; }
-            }
-            if (may_natural) break;
-        }
-        const bool walk_all = __syncthreads_or(may_natural) != 0;
-
-        // 2b. the chain from every entry state (lane = state; state m = D0)
-        if (tid <= (int)m) {
-            uint32_t cnt = 0, exitv = 0;
-            int k = 0;
-            bool walk = true;
-            if (tid < (int)m) {
-                k = tid;
-            } else {
-                const int d0 = next_desc(bits, 0, KMAX);
-                if (d0 >= KMAX || (uint32_t)d0 >= span) {   // no run starts here
-                    walk = false;
-                    exitv = E == n ? STATE_END : m;
-                } else {
-                    k = d0;
-                }
-            }
-            if (walk && !walk_all) {
-                // forced steps only: starts k, k + m, k + 2m, ... below span
-                cnt = (uint32_t)k < span ? (span - (uint32_t)k + m - 1) / m : 0u;
-                if (E == n) exitv = STATE_END;
-                else exitv = (uint32_t)k + cnt * m - span;   // < m
-                rec[tid][0] = (uint16_t)k;                    // the progression's start
-            } else if (walk) {
-                bool symbolic = false;
-                while ((uint32_t)k < span) {
-                    rec[tid][cnt++] = (uint16_t)k;
-                    const int d = next_desc(bits, k + 1, KMAX);
-                    if (d >= KMAX) { symbolic = true; break; }   // f = d = next chunk's D0
-                    const int forced = (int)min((uint32_t)(k + (int)m), rem);
-                    k = max(d, forced);
-                }
-                // the last chunk's chains all end at n; elsewhere the exit is an
-                // entry state of the next chunk (a position past the next chunk's
-                // first minrun positions can only be its D0, even when it is n)
-                if (E == n) exitv = STATE_END;
-                else if (symbolic) exitv = m;
-                else {
-                    const uint32_t x = (uint32_t)k - span;
-                    exitv = x < m ? x : m;
-                }
-            }
-            mapv[tid] = (cnt << 8) | exitv;
+        bits_from_keys(v, w, keys[buf], bits);
+        __syncthreads();
+        const bool walk = chunk_may_natural(v, bits);
+        if (tid <= (int)v.m) mapv[tid] = chain_map(v, bits, (uint32_t)tid, walk);
+        __syncthreads();
+        // an instance's first chunk is entered at state 0 whatever came before:
+        // its map is constant; states above m never occur and copy state m
+        const bool first = v.c == 0;
+        uint32_t f = 0;
+        if (tid < MAP_STATES) f = first ? mapv[0] : mapv[min((uint32_t)tid, v.m)];
+        if (tid == 0) {
+            const int d0 = next_desc(bits, 0, KMAX);
+            J.chunk_info[g] = (walk ? 0u : CHUNK_FORCED) | (first ? CHUNK_FIRST : 0u) | (uint32_t)min(d0, 0xffff);
+            if (first) s_reset = RANGE_RESET;
         }
         __syncthreads();
-
-        // 3. decoupled look-back over the chunks of this instance (warp 0)
-        if (warp == 0) {
-            uint32_t entry = 0;
-            uint32_t prefix = 0;
-            bool abort = false;
-            if (c > 0) {
-                uint32_t* gmap = J.chunk_map + (size_t)g * MAP_STATES;
-                gmap[lane] = mapv[lane];
-                gmap[lane + 32] = mapv[lane + 32];
-                __threadfence();
-                __syncwarp();
-                if (lane == 0) st_release_u32(&J.chunk_status[g], ST_AGG);
-                // h maps entry states of chunk k + 1 to (state of chunk g, runs in between)
-                uint32_t hs0 = lane, hs1 = lane + 32, hc0 = 0, hc1 = 0;
-                uint32_t k = g - 1;
-                for (;;) {
-                    // every lane acquires the flag itself (bounded wait); the
-                    // branch taken is lane 0's view, so the warp stays uniform
-                    uint32_t sv = ld_acquire_u32(&J.chunk_status[k]);
-                    if (sv != ST_AGG && sv != ST_INC) {
-                        const long long t0 = clock64();
-                        do {
-                            __nanosleep(64);
-                            sv = ld_acquire_u32(&J.chunk_status[k]);
-                            if (clock64() - t0 > SPIN_LIMIT_CYCLES) break;
-                        } while (sv != ST_AGG && sv != ST_INC);
-                    }
-                    if (!__all_sync(FULL, sv == ST_AGG || sv == ST_INC)) {
-                        if (lane == 0) set_error(C, DERR_TIMEOUT, 10);
-                        abort = true;
-                        break;
-                    }
-                    sv = __shfl_sync(FULL, sv, 0);
-                    if (sv == ST_INC) {
-                        unsigned long long inc = 0;
-                        if (lane == 0) inc = J.chunk_incl[k];   // lane 0 acquired ST_INC
-                        inc = __shfl_sync(FULL, inc, 0);
-                        const uint32_t y = (uint32_t)(inc & 0xffu);
-                        const uint32_t cy = (uint32_t)(inc >> 8);
-                        const uint32_t s0 = __shfl_sync(FULL, hs0, y & 31), s1 = __shfl_sync(FULL, hs1, y & 31);
-                        const uint32_t c0 = __shfl_sync(FULL, hc0, y & 31), c1 = __shfl_sync(FULL, hc1, y & 31);
-                        entry = y < 32 ? s0 : s1;
-                        prefix = cy + (y < 32 ? c0 : c1);
-                        if (y > m) { if (lane == 0) set_error(C, DERR_INTERNAL, 11); abort = true; }
-                        break;
-                    }
-                    const uint32_t* kmap = J.chunk_map + (size_t)k * MAP_STATES;
-                    const uint32_t m0 = kmap[lane], m1 = kmap[lane + 32];
-                    const uint32_t y0 = m0 & 0xffu, y1 = m1 & 0xffu;
-                    const uint32_t a0 = __shfl_sync(FULL, hs0, y0 & 31), a1 = __shfl_sync(FULL, hs1, y0 & 31);
-                    const uint32_t b0 = __shfl_sync(FULL, hc0, y0 & 31), b1 = __shfl_sync(FULL, hc1, y0 & 31);
-                    const uint32_t e0 = __shfl_sync(FULL, hs0, y1 & 31), e1 = __shfl_sync(FULL, hs1, y1 & 31);
-                    const uint32_t f0 = __shfl_sync(FULL, hc0, y1 & 31), f1 = __shfl_sync(FULL, hc1, y1 & 31);
-                    hs0 = y0 < 32 ? a0 : a1;
-                    hc0 = (m0 >> 8) + (y0 < 32 ? b0 : b1);
-                    hs1 = y1 < 32 ? e0 : e1;
-                    hc1 = (m1 >> 8) + (y1 < 32 ? f0 : f1);
-                    --k;
-                }
-            }
-            if (!abort) {
-                const uint32_t me = mapv[entry];
-                if (lane == 0) {
-                    J.chunk_incl[g] = ((unsigned long long)(prefix + (me >> 8)) << 8) | (me & 0xffu);
-                    __threadfence();
-                    st_release_u32(&J.chunk_status[g], ST_INC);
-                }
-            }
-            if (lane == 0) {
-                s_entry = entry;
-                s_prefix = prefix;
-                s_abort = abort ? 1u : 0u;
+        if (tid < MAP_STATES) {
+            mapv[tid] = f;
+            J.chunk_map[(size_t)g * MAP_STATES + tid] = f;
+        }
+        __syncthreads();
+        if (tid < MAP_STATES) {
+            // fold the chunk into the range map (a restart discards the runs before it)
+            const uint32_t a = agg[tid], st = a & 0xffu;
+            if (first || st < (uint32_t)MAP_STATES) {
+                const uint32_t fm = mapv[first ? 0u : st];
+                agg[tid] = (((first ? 0u : a >> 8) + (fm >> 8)) << 8) | (fm & 0xffu);
             }
         }
         __syncthreads();
+    }
+    if (tid < MAP_STATES) J.range_agg[(size_t)blockIdx.x * MAP_STATES + tid] = agg[tid] | s_reset;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(&C->runs_done, 1u) == G - 1 ? 1u : 0u;
+    __syncthreads();
+    if (!s_last) return;
 
-        // 4. write this chunk's run starts
-        if (!s_abort) {
-            const uint32_t entry = s_entry, prefix = s_prefix;
-            const uint32_t me = mapv[entry];
-            const uint32_t cnt = me >> 8;
+    // the last CTA: entry (runs before it << 8 | state) of every range, in
+    // order, staging the range maps in the (now free) key windows
+    __threadfence();
+    constexpr uint32_t SCAN_WIN = 2 * WIN_SLOTS / MAP_STATES;   // range maps per batch
+    uint32_t (*win)[MAP_STATES] = reinterpret_cast<uint32_t (*)[MAP_STATES]>(&keys[0][0]);
+    unsigned long long at = 0;                   // range 0 begins chunk 0: state 0, no runs before
+    for (uint32_t r0 = 0; r0 < G; r0 += SCAN_WIN) {
+        const uint32_t nr = min(SCAN_WIN, G - r0);
+        for (uint32_t i = tid; i < nr * MAP_STATES; i += RUN_BLOCK)
+            win[i / MAP_STATES][i % MAP_STATES] = __ldcg(J.range_agg + (size_t)r0 * MAP_STATES + i);
+        __syncthreads();
+        if (tid == 0) {
+            for (uint32_t r = 0; r < nr; ++r) {
+                J.range_entry[r0 + r] = at;
+                at = apply_map(at, win[r], (win[r][0] & RANGE_RESET) != 0);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Pass 2: every CTA walks its range's chunk maps from the range entry and
+// writes the run starts of each chunk.
+__global__ void __launch_bounds__(RUN_BLOCK) k_runs_emit(Job J)
+{
+    __shared__ __align__(16) uint32_t keys[WIN_SLOTS];
+    __shared__ uint32_t bits[RUN_WORDS];
+    __shared__ uint32_t win[WIN][MAP_STATES];
+    __shared__ unsigned long long entry[WIN];    // runs before the chunk << 8 | its entry state
+    __shared__ uint32_t s_cnt;
+
+    const int tid = threadIdx.x;
+    Ctr* C = J.ctr;
+    if (*(volatile uint32_t*)&C->error) return;
+    const uint32_t T = C->total_chunks, G = gridDim.x;
+    const uint32_t K = (T + G - 1) / G;
+    const uint32_t g0 = min(blockIdx.x * K, T), g1 = min(g0 + K, T);
+    unsigned long long at = J.range_entry[blockIdx.x];
+
+    for (uint32_t b0 = g0; b0 < g1; b0 += WIN) {
+        const uint32_t nb = min((uint32_t)WIN, g1 - b0);
+        for (uint32_t i = tid; i < nb * MAP_STATES; i += RUN_BLOCK)
+            win[i / MAP_STATES][i % MAP_STATES] = J.chunk_map[(size_t)b0 * MAP_STATES + i];
+        __syncthreads();
+        if (tid == 0) {
+            for (uint32_t i = 0; i < nb; ++i) {
+                const bool first = (J.chunk_info[b0 + i] & CHUNK_FIRST) != 0;
+                if (first) at = 0;               // an instance starts: state 0, no runs before
+                entry[i] = at;
+                at = apply_map(at, win[i], first);
+            }
+        }
+        __syncthreads();
+        uint32_t qi = NONE;
+        for (uint32_t i = 0; i < nb; ++i) {
+            const uint32_t g = b0 + i;
+            const ChunkView v = chunk_view(J, g, qi);
+            const Inst& I = J.inst[v.qi];
+            const uint32_t info = J.chunk_info[g];
+            const uint32_t st = (uint32_t)(entry[i] & 0xffu);
+            const unsigned long long prefix = entry[i] >> 8;
+            const uint32_t me = win[i][st < (uint32_t)MAP_STATES ? st : 0u];
+            const uint32_t cnt = (me & RANGE_COUNT_MASK) >> 8;
             uint32_t* rs = J.run_start + I.run_base + prefix;
-            const unsigned long long cap = (unsigned long long)(n / 32) + 2;
-            if ((unsigned long long)prefix + cnt + 1 > cap || cnt > (uint32_t)RUN_REC) {
+            const unsigned long long cap = (unsigned long long)(v.n / 32) + 2;
+            if (st > v.m || prefix + cnt + 1 > cap || cnt > (uint32_t)RUN_REC) {
                 if (tid == 0) set_error(C, DERR_INTERNAL, 13);
-            } else if (!walk_all) {
-                const uint32_t k0 = B + rec[entry][0];
-                for (uint32_t i = tid; i < cnt; i += RUN_BLOCK) rs[i] = k0 + i * m;
+            } else if (info & CHUNK_FORCED) {
+                // forced steps only: starts k0, k0 + m, ... (k0: the entry offset or D0)
+                const uint32_t d0 = info & 0xffffu;
+                const uint32_t k0 = st < v.m ? st : d0;
+                for (uint32_t x = tid; x < cnt; x += RUN_BLOCK) rs[x] = v.B + k0 + x * v.m;
             } else {
-                for (uint32_t i = tid; i < cnt; i += RUN_BLOCK) rs[i] = B + rec[entry][i];
+                const KeyWindow w = window_of(v);
+                stage_keys(v, w, keys);
+                cp_async_wait<0>();
+                __syncthreads();
+                bits_from_keys(v, w, keys, bits);
+                __syncthreads();
+                if (tid == 0) {
+                    uint32_t c2 = 0;
+                    int k = entry_offset(v, bits, st);
+                    if (k >= 0) {
+                        while ((uint32_t)k < v.span && c2 < cnt) {
+                            rs[c2++] = v.B + (uint32_t)k;
+                            const int d = next_desc(bits, k + 1, KMAX);
+                            if (d >= KMAX) break;
+                            k = max(d, (int)min((uint32_t)k + v.m, v.rem));
+                        }
+                    }
+                    s_cnt = c2;
+                }
+                __syncthreads();
+                if (tid == 0 && s_cnt != cnt) set_error(C, DERR_INTERNAL, 14);
             }
-            if (c + 1 == I.nchunks && tid == 0) {
-                const uint32_t R = prefix + cnt;
-                if ((me & 0xffu) != STATE_END || (unsigned long long)R + 1 > (unsigned long long)(n / 32) + 2)
+            if (v.c + 1 == I.nchunks && tid == 0) {
+                const unsigned long long R = prefix + cnt;
+                if ((me & 0xffu) != STATE_END || R + 1 > cap) {
                     set_error(C, DERR_INTERNAL, 12);
-                else {
-                    J.run_start[I.run_base + R] = n;
-                    J.inst[qi].runs = R;
+                } else {
+                    J.run_start[I.run_base + R] = v.n;
+                    J.inst[v.qi].runs = (uint32_t)R;
                 }
             }
+            if (!(info & CHUNK_FORCED)) __syncthreads();   // the window is reused by the next walk
         }
         __syncthreads();
     }
@@ -439,9 +602,8 @@ cudaError_t launch_setup(const Job& J, cudaStream_t s)
 
 cudaError_t launch_runs(const Job& J, int grid, cudaStream_t s)
 {
-    // the setup kernel bumps the epoch in device memory, so status words left
-    // by earlier calls (or earlier replays of a captured graph) read as "not ready"
     k_runs<<<grid, RUN_BLOCK, 0, s>>>(J);
+    k_runs_emit<<<grid, RUN_BLOCK, 0, s>>>(J);
     return cudaGetLastError();
 }
 
