@@ -313,6 +313,7 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
     if (st == PS_OK) st = dev_alloc(c, &J.inst, c->max_count);
     if (st == PS_OK) st = dev_alloc(c, &J.chunk_map, chunk_cap * ps::MAP_STATES);
     if (st == PS_OK) st = dev_alloc(c, &J.chunk_info, chunk_cap);
+    if (st == PS_OK) st = dev_alloc(c, &J.chunk_bits, chunk_cap * ps::RUN_WORDS);
     if (st == PS_OK) st = dev_alloc(c, &J.range_agg, (size_t)c->grid_runs * ps::MAP_STATES);
     if (st == PS_OK) st = dev_alloc(c, &J.range_entry, (size_t)c->grid_runs);
     if (st == PS_OK) st = dev_alloc(c, &J.run_start, slot_cap);
@@ -342,7 +343,7 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
         st = PS_ECUDA;
     if (st == PS_OK && cudaDeviceSynchronize() != cudaSuccess) st = PS_ECUDA;
     // every table the kernels write must exist (permB only with want_perm)
-    if (st == PS_OK && ((!vm && !J.keysB) || !J.inst || !J.chunk_map || !J.chunk_info || !J.range_agg || !J.range_entry ||
+    if (st == PS_OK && ((!vm && !J.keysB) || !J.inst || !J.chunk_map || !J.chunk_info || !J.chunk_bits || !J.range_agg || !J.range_entry ||
                         !J.run_start || !J.kappa || !J.power || !J.na || !J.nb || !J.tiles || !J.gnodes ||
                         !J.gsorted || !J.dep || !J.chunk_node || !J.ctr ||
                         (!vm && cfg->want_perm && !J.permB) || (vm && (!J.pool_keys || !J.pt || !J.front))))

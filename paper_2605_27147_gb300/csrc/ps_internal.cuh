@@ -26,9 +26,9 @@
 namespace ps {
 
 constexpr int RUN_CHUNK = 4096;   // elements per run-detection chunk
-constexpr int RUN_HALO = 96;      // descent bits examined past a chunk's end
-constexpr int RUN_WORDS = (RUN_CHUNK + RUN_HALO) / 32 + 1;
-constexpr int RUN_BLOCK = 128;
+constexpr int RUN_HALO = 256;     // descent bits examined past a chunk's end (>= 64)
+constexpr int RUN_WORDS = (RUN_CHUNK + RUN_HALO) / 32;
+constexpr int RUN_BLOCK = 256;
 constexpr int RUN_LOADS = RUN_WORDS * 32 / RUN_BLOCK;   // keys loaded per thread per chunk
 static_assert(RUN_WORDS * 32 % RUN_BLOCK == 0, "the bitmask window is a whole number of block loads");
 constexpr int MAP_STATES = 64;    // entry states of a chunk: minrun (<= 63) + 1
@@ -153,6 +153,7 @@ struct Job {
     Inst* inst;
     uint32_t* chunk_map;        // MAP_STATES per chunk: (runs << 8) | exit state, per entry state
     uint32_t* chunk_info;       // per chunk: CHUNK_FORCED | CHUNK_FIRST | first descent offset
+    uint32_t* chunk_bits;       // RUN_WORDS per chunk: descent bitmask of chunks that need the chain walk
     uint32_t* range_agg;        // MAP_STATES per run-detection CTA: its range's map
     unsigned long long* range_entry;   // per run-detection CTA: (runs before << 8) | entry state
     uint32_t* run_start;

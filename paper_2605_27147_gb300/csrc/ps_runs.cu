@@ -328,23 +328,30 @@ __device__ __forceinline__ void bits_from_keys(const ChunkView& v, const KeyWind
     }
 }
 
-// Can any step from inside the chunk be natural?  Only if two consecutive
-// descents (or position 0 and the first descent) lie at least minrun apart;
-// otherwise every chain is forced all the way and has a closed form.
+// Can any step from inside the chunk be natural?  Only if some descent e
+// (or position 0) inside the chunk is followed by minrun - 1 >= 31 positions
+// without a descent.  Each thread looks for a run of 31 clear bits starting
+// in its word (a 64-bit window over it and the next word); finding none
+// proves every chain forced all the way, with a closed form.  Finding one
+// only selects the exact chain walk.
 __device__ __forceinline__ bool chunk_may_natural(const ChunkView& v, const uint32_t* bits)
 {
     const int tid = threadIdx.x;
     bool may = false;
-    for (int w = tid; w < RUN_WORDS && w * 32 < (int)v.span; w += RUN_BLOCK) {
-        uint32_t word = bits[w];
-        if (w == 0) word |= 1u;                    // position 0 starts a gap too
-        while (word) {
-            const int e = w * 32 + __ffs(word) - 1;
-            word &= word - 1;
-            if ((uint32_t)e >= v.span) break;
-            if (next_desc(bits, e + 1, KMAX) - e >= (int)v.m) { may = true; break; }
-        }
-        if (may) break;
+    for (int w = tid; w < RUN_WORDS && w * 32 <= (int)v.span; w += RUN_BLOCK) {
+        const unsigned long long hi = w + 1 < RUN_WORDS ? bits[w + 1] : 0u;
+        const unsigned long long z = ~((unsigned long long)bits[w] | (hi << 32));
+        unsigned long long r = z & (z >> 1);   // runs of 2 clear bits
+        r &= r >> 2;                           // 4
+        r &= r >> 4;                           // 8
+        r &= r >> 8;                           // 16
+        r &= r >> 15;                          // 31: bit p set <=> bits p .. p + 30 clear
+        // run starts p = e + 1 with 1 <= p <= span (e = 0: the chunk's first position)
+        uint32_t starts = (uint32_t)r;
+        if (w == 0) starts &= ~1u;
+        const uint32_t lo = (uint32_t)w * 32u;
+        if (v.span - lo + 1u < 32u) starts &= (1u << (v.span - lo + 1u)) - 1u;
+        may = may || starts != 0;
     }
     return __syncthreads_or(may) != 0;
 }
@@ -461,6 +468,8 @@ __global__ void __launch_bounds__(RUN_BLOCK) k_runs(Job J)
             J.chunk_info[g] = (walk ? 0u : CHUNK_FORCED) | (first ? CHUNK_FIRST : 0u) | (uint32_t)min(d0, 0xffff);
             if (first) s_reset = RANGE_RESET;
         }
+        if (walk)   // k_runs_emit walks one chain of this chunk over the same bitmask
+            for (int x = tid; x < RUN_WORDS; x += RUN_BLOCK) J.chunk_bits[(size_t)g * RUN_WORDS + x] = bits[x];
         __syncthreads();
         if (tid < MAP_STATES) {
             mapv[tid] = f;
@@ -484,21 +493,55 @@ __global__ void __launch_bounds__(RUN_BLOCK) k_runs(Job J)
     __syncthreads();
     if (!s_last) return;
 
-    // the last CTA: entry (runs before it << 8 | state) of every range, in
-    // order, staging the range maps in the (now free) key windows
+    // The last CTA: the entry (runs before it << 8 | state) of every range,
+    // in order.  Per batch of range maps staged in the (now free) key windows:
+    // every warp folds a group of 32 consecutive ranges into one map (each
+    // lane two entry states), thread 0 walks the group maps, then lane r of
+    // each warp walks its group's ranges from the group's entry.
     __threadfence();
-    constexpr uint32_t SCAN_WIN = 2 * WIN_SLOTS / MAP_STATES;   // range maps per batch
+    constexpr uint32_t GROUP = 32;
+    constexpr uint32_t SCAN_WIN = (2 * WIN_SLOTS / MAP_STATES) / GROUP * GROUP;   // range maps per batch
+    constexpr uint32_t NGROUPS = SCAN_WIN / GROUP;
+    static_assert(NGROUPS <= RUN_BLOCK / 32, "one warp per group");
     uint32_t (*win)[MAP_STATES] = reinterpret_cast<uint32_t (*)[MAP_STATES]>(&keys[0][0]);
+    __shared__ uint32_t gmap[NGROUPS][MAP_STATES];
+    __shared__ unsigned long long gentry[NGROUPS];
+    const int lane = tid & 31, warp = tid >> 5;
     unsigned long long at = 0;                   // range 0 begins chunk 0: state 0, no runs before
     for (uint32_t r0 = 0; r0 < G; r0 += SCAN_WIN) {
         const uint32_t nr = min(SCAN_WIN, G - r0);
         for (uint32_t i = tid; i < nr * MAP_STATES; i += RUN_BLOCK)
             win[i / MAP_STATES][i % MAP_STATES] = __ldcg(J.range_agg + (size_t)r0 * MAP_STATES + i);
         __syncthreads();
+        const uint32_t ng = (nr + GROUP - 1) / GROUP;
+        if ((uint32_t)warp < ng) {
+            const uint32_t q0 = warp * GROUP, q1 = min(q0 + GROUP, nr);
+            bool reset = false;
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t s0 = (uint32_t)lane + 32u * h;
+                unsigned long long a = s0;
+                for (uint32_t q = q0; q < q1; ++q) {
+                    const bool rq = (win[q][0] & RANGE_RESET) != 0;
+                    a = apply_map(a, win[q], rq);
+                    reset = reset || rq;
+                }
+                gmap[warp][s0] = (uint32_t)(a & 0xffu) | (uint32_t)((a >> 8) << 8) | (reset ? RANGE_RESET : 0u);
+            }
+        }
+        __syncthreads();
         if (tid == 0) {
-            for (uint32_t r = 0; r < nr; ++r) {
-                J.range_entry[r0 + r] = at;
-                at = apply_map(at, win[r], (win[r][0] & RANGE_RESET) != 0);
+            for (uint32_t q = 0; q < ng; ++q) {
+                gentry[q] = at;
+                at = apply_map(at, gmap[q], (gmap[q][0] & RANGE_RESET) != 0);
+            }
+        }
+        __syncthreads();
+        if ((uint32_t)warp < ng && lane == 0) {
+            unsigned long long a = gentry[warp];
+            const uint32_t q0 = warp * GROUP, q1 = min(q0 + GROUP, nr);
+            for (uint32_t q = q0; q < q1; ++q) {
+                J.range_entry[r0 + q] = a;
+                a = apply_map(a, win[q], (win[q][0] & RANGE_RESET) != 0);
             }
         }
         __syncthreads();
@@ -509,13 +552,12 @@ __global__ void __launch_bounds__(RUN_BLOCK) k_runs(Job J)
 // writes the run starts of each chunk.
 __global__ void __launch_bounds__(RUN_BLOCK) k_runs_emit(Job J)
 {
-    __shared__ __align__(16) uint32_t keys[WIN_SLOTS];
-    __shared__ uint32_t bits[RUN_WORDS];
+    constexpr int NW = RUN_BLOCK / 32;
+    __shared__ uint32_t bits[NW][RUN_WORDS];     // one descent bitmask per warp
     __shared__ uint32_t win[WIN][MAP_STATES];
     __shared__ unsigned long long entry[WIN];    // runs before the chunk << 8 | its entry state
-    __shared__ uint32_t s_cnt;
 
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     Ctr* C = J.ctr;
     if (*(volatile uint32_t*)&C->error) return;
     const uint32_t T = C->total_chunks, G = gridDim.x;
@@ -537,8 +579,9 @@ __global__ void __launch_bounds__(RUN_BLOCK) k_runs_emit(Job J)
             }
         }
         __syncthreads();
+        // one warp per chunk
         uint32_t qi = NONE;
-        for (uint32_t i = 0; i < nb; ++i) {
+        for (uint32_t i = warp; i < nb; i += NW) {
             const uint32_t g = b0 + i;
             const ChunkView v = chunk_view(J, g, qi);
             const Inst& I = J.inst[v.qi];
@@ -550,36 +593,33 @@ __global__ void __launch_bounds__(RUN_BLOCK) k_runs_emit(Job J)
             uint32_t* rs = J.run_start + I.run_base + prefix;
             const unsigned long long cap = (unsigned long long)(v.n / 32) + 2;
             if (st > v.m || prefix + cnt + 1 > cap || cnt > (uint32_t)RUN_REC) {
-                if (tid == 0) set_error(C, DERR_INTERNAL, 13);
+                if (lane == 0) set_error(C, DERR_INTERNAL, 13);
             } else if (info & CHUNK_FORCED) {
                 // forced steps only: starts k0, k0 + m, ... (k0: the entry offset or D0)
                 const uint32_t d0 = info & 0xffffu;
                 const uint32_t k0 = st < v.m ? st : d0;
-                for (uint32_t x = tid; x < cnt; x += RUN_BLOCK) rs[x] = v.B + k0 + x * v.m;
+                for (uint32_t x = lane; x < cnt; x += 32) rs[x] = v.B + k0 + x * v.m;
             } else {
-                const KeyWindow w = window_of(v);
-                stage_keys(v, w, keys);
-                cp_async_wait<0>();
-                __syncthreads();
-                bits_from_keys(v, w, keys, bits);
-                __syncthreads();
-                if (tid == 0) {
+                // the one chain this chunk takes, over the bitmask pass 1 kept
+                const uint32_t* gb = J.chunk_bits + (size_t)g * RUN_WORDS;
+                for (int x = lane; x < RUN_WORDS; x += 32) bits[warp][x] = gb[x];
+                __syncwarp();
+                if (lane == 0) {
                     uint32_t c2 = 0;
-                    int k = entry_offset(v, bits, st);
+                    int k = entry_offset(v, bits[warp], st);
                     if (k >= 0) {
                         while ((uint32_t)k < v.span && c2 < cnt) {
                             rs[c2++] = v.B + (uint32_t)k;
-                            const int d = next_desc(bits, k + 1, KMAX);
+                            const int d = next_desc(bits[warp], k + 1, KMAX);
                             if (d >= KMAX) break;
                             k = max(d, (int)min((uint32_t)k + v.m, v.rem));
                         }
                     }
-                    s_cnt = c2;
+                    if (c2 != cnt) set_error(C, DERR_INTERNAL, 14);
                 }
-                __syncthreads();
-                if (tid == 0 && s_cnt != cnt) set_error(C, DERR_INTERNAL, 14);
+                __syncwarp();
             }
-            if (v.c + 1 == I.nchunks && tid == 0) {
+            if (v.c + 1 == I.nchunks && lane == 0) {
                 const unsigned long long R = prefix + cnt;
                 if ((me & 0xffu) != STATE_END || R + 1 > cap) {
                     set_error(C, DERR_INTERNAL, 12);
@@ -588,7 +628,6 @@ __global__ void __launch_bounds__(RUN_BLOCK) k_runs_emit(Job J)
                     J.inst[v.qi].runs = (uint32_t)R;
                 }
             }
-            if (!(info & CHUNK_FORCED)) __syncthreads();   // the window is reused by the next walk
         }
         __syncthreads();
     }
