@@ -17,6 +17,17 @@
 // scratch arrays) with its stable permutation, ready for the HBM rounds.
 // A single run longer than T (always a natural, sorted run) is streamed:
 // keys copied when its buffer is the scratch one, perm written.
+//
+// Whatever order its merges run in, a subtree's result is the stable sort of
+// its range: the elements ordered by (key, input position).  A tile made of
+// many short runs (the usual case for unsorted data: forced runs of minrun
+// elements) therefore takes a faster road to the same result: each element
+// becomes one 64-bit word (key << 32 | position), every thread sorts 16
+// consecutive words in registers with a bitonic network, and the sorted
+// blocks are merged pairwise in shared memory (merge path, 16 outputs per
+// thread) up to the whole tile.  The words are distinct, so no tie rule is
+// needed and the order is exactly the stable one.  Tiles of few runs follow
+// the tree level by level as described above.
 #include "ps_internal.cuh"
 
 namespace ps {
@@ -34,12 +45,104 @@ struct TileSmem {
     uint16_t idx[2][TILE_MAX];   // input position inside the tile (the permutation)
 };
 
+constexpr int NET_PER = 16;                          // words per thread in the network road
+constexpr int NET_SLOTS = TILE_MAX + TILE_MAX / NET_PER;   // one spare slot per 16: fewer bank conflicts
+constexpr uint32_t NET_MIN_RUNS = 8;                 // tiles with this many runs take the network road
+static_assert(NET_PER * TILE_BLOCK >= TILE_MAX, "one block of 16 words per thread covers a tile");
+
+struct NetSmem {
+    unsigned long long w[2][NET_SLOTS];
+};
+
+__device__ __forceinline__ uint32_t net_slot(uint32_t x)
+{
+    return x + (x >> 4);
+}
+
+// Bitonic sorting network over N words held in registers (ascending).
+template <int N>
+__device__ __forceinline__ void sort_registers(unsigned long long (&v)[N])
+{
+#pragma unroll
+    for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const unsigned long long a = v[i], b = v[l];
+                    const bool swap = ((i & k) == 0) ? (b < a) : (a < b);
+                    v[i] = swap ? b : a;
+                    v[l] = swap ? a : b;
+                }
+            }
+        }
+    }
+}
+
+// The network road for one tile of `size` elements: sorted (key, position)
+// words end in sm.w[result]; returns result.
+__device__ int tile_network(NetSmem& sm, const uint32_t* ksrc, uint32_t size)
+{
+    const int tid = threadIdx.x;
+    uint32_t P = NET_PER;                       // a power of two >= size
+    while (P < size) P <<= 1;
+    for (uint32_t x = tid; x < P; x += TILE_BLOCK)
+        sm.w[0][net_slot(x)] = x < size ? ((unsigned long long)__ldg(ksrc + x) << 32) | x : ~0ull;
+    __syncthreads();
+    const uint32_t x0 = (uint32_t)tid * NET_PER;
+    if (x0 < P) {
+        unsigned long long v[NET_PER];
+#pragma unroll
+        for (int j = 0; j < NET_PER; ++j) v[j] = sm.w[0][net_slot(x0) + j];
+        sort_registers<NET_PER>(v);
+#pragma unroll
+        for (int j = 0; j < NET_PER; ++j) sm.w[0][net_slot(x0) + j] = v[j];
+    }
+    __syncthreads();
+    int cur = 0;
+    for (uint32_t w = NET_PER; w < P; w <<= 1) {
+        const unsigned long long* src = sm.w[cur];
+        unsigned long long* dst = sm.w[cur ^ 1];
+        if (x0 < P) {
+            const uint32_t blk = x0 & ~(2 * w - 1), d = x0 - blk;
+            const uint32_t A = blk, B = blk + w;
+            uint32_t lo = d > w ? d - w : 0u, hi = min(d, w);
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (src[net_slot(A + mid)] <= src[net_slot(B + d - 1 - mid)]) lo = mid + 1; else hi = mid;
+            }
+            uint32_t ia = lo, ib = d - lo;
+            unsigned long long va = ia < w ? src[net_slot(A + ia)] : 0ull;
+            unsigned long long vb = ib < w ? src[net_slot(B + ib)] : 0ull;
+            unsigned long long* out = dst + net_slot(x0);
+            // branch-free serial merge; an exhausted side is read at its first
+            // slot (a valid address whose value is never used)
+#pragma unroll
+            for (int j = 0; j < NET_PER; ++j) {
+                const bool take_a = ia < w && (ib >= w || va <= vb);
+                out[j] = take_a ? va : vb;
+                ia += take_a;
+                ib += !take_a;
+                const unsigned long long nxt = src[net_slot(take_a ? A + (ia < w ? ia : 0u) : B + (ib < w ? ib : 0u))];
+                va = take_a ? nxt : va;
+                vb = take_a ? vb : nxt;
+            }
+        }
+        __syncthreads();
+        cur ^= 1;
+    }
+    return cur;
+}
+
 }  // namespace
 
 __global__ void __launch_bounds__(TILE_BLOCK) k_tiles(Job J)
 {
     extern __shared__ __align__(16) unsigned char tile_raw[];
     TileSmem& sm = *reinterpret_cast<TileSmem*>(tile_raw);
+    NetSmem& net = *reinterpret_cast<NetSmem*>(tile_raw);
     __shared__ uint32_t rs_s[TILE_RUNS + 1];
     __shared__ uint8_t pw_s[TILE_RUNS + 1];
     __shared__ uint32_t seg_lo[TILE_RUNS + 2];
@@ -77,6 +180,16 @@ __global__ void __launch_bounds__(TILE_BLOCK) k_tiles(Job J)
         const uint32_t nr = it.r1 - it.r0;   // runs in the tile (<= TILE_RUNS - 1)
         if (nr + 1 > (uint32_t)TILE_RUNS) {  // cannot happen for minrun >= 32
             if (tid == 0) set_error(J.ctr, DERR_INTERNAL, 50);
+            continue;
+        }
+        if (nr >= NET_MIN_RUNS) {
+            const int res = tile_network(net, ksrc, size);
+            for (uint32_t x = tid; x < size; x += TILE_BLOCK) {
+                const unsigned long long w = net.w[res][net_slot(x)];
+                kdst[x] = (uint32_t)(w >> 32);
+                if (pdst) pdst[x] = lo + (uint32_t)(w & 0xffffffffu);
+            }
+            __syncthreads();
             continue;
         }
         int cur = 0;
@@ -243,17 +356,19 @@ __global__ void __launch_bounds__(TILE_BLOCK) k_tiles(Job J)
     }
 }
 
+constexpr size_t TILE_SMEM = sizeof(TileSmem) > sizeof(NetSmem) ? sizeof(TileSmem) : sizeof(NetSmem);
+
 int tiles_max_grid(int num_sms)
 {
     int per_sm = 0;
-    cudaFuncSetAttribute(k_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileSmem));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tiles, TILE_BLOCK, sizeof(TileSmem));
+    cudaFuncSetAttribute(k_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TILE_SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tiles, TILE_BLOCK, TILE_SMEM);
     return num_sms * (per_sm > 0 ? per_sm : 1);
 }
 
 cudaError_t launch_tiles(const Job& J, int grid, cudaStream_t s)
 {
-    k_tiles<<<grid, TILE_BLOCK, sizeof(TileSmem), s>>>(J);
+    k_tiles<<<grid, TILE_BLOCK, TILE_SMEM, s>>>(J);
     return cudaGetLastError();
 }
 
