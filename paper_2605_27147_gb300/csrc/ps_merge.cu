@@ -360,13 +360,21 @@ __device__ __noinline__ void search_warp(const Job& J, MergeSmem<NST>& sm, Ctr* 
     enum : uint32_t { S_CLAIM, S_NODE, S_INFO, S_WAIT, S_SEARCH, S_PUB, S_DONE };
     const int lane = threadIdx.x & 31;
     const uint32_t total_chunks = sm.round_chunk[NPOW];
-    uint32_t state = lane < NSEARCH ? S_CLAIM : S_DONE;
+    // Lanes in use: about one round's share of chunks per CTA (at least 2, at
+    // most NSEARCH), so that when a round has few chunks the first claims
+    // still spread it over every CTA instead of filling the first ones.
+    uint32_t rounds = 0;
+    for (int r = 0; r < NPOW; ++r) rounds += sm.round_chunk[r + 1] > sm.round_chunk[r] ? 1u : 0u;
+    const uint32_t share = rounds ? (total_chunks + rounds * gridDim.x - 1) / (rounds * gridDim.x) : 0u;
+    const int lanes = (int)min((uint32_t)NSEARCH, max(2u, share));
+    uint32_t state = lane < lanes ? S_CLAIM : S_DONE;
+    if (lane >= lanes && lane < NSEARCH) st_vol(&sm.ring_state[lane], RS_END);
     uint32_t c = 0, e = 0, d0 = 0, d1 = 0, round = 0;
     GSorted g = {};
     uint32_t lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0;
     long long t_wait = 0;
     unsigned long long t_ready = 0;
-    uint32_t gap = 1, next_poll = 0;     // a waiting lane polls every gap iterations (1, 2, 4)
+    uint32_t gap = 1, next_poll = 0;     // a waiting lane polls every gap iterations (1, then 2)
     for (uint32_t iter = 0;; ++iter) {
         // ---- issue
         const uint32_t want = __ballot_sync(FULL_MASK, state == S_CLAIM);
@@ -434,7 +442,7 @@ __device__ __noinline__ void search_warp(const Job& J, MergeSmem<NST>& sm, Ctr* 
                 st_vol(&sm.ring_state[lane], RS_END);
             } else {
                 next_poll = iter + gap;
-                gap = gap < 4u ? gap * 2u : 4u;
+                gap = 2u;
             }
         } else if (state == S_SEARCH) {
             if (s0) {
@@ -544,7 +552,7 @@ __device__ __noinline__ void consumer_warps(const Job& J, MergeSmem<NST>& sm, Ct
     for (;;) {
         const int s = (int)(u % NST);
         const uint32_t parity = (u / NST) & 1u;
-        if (!mbar_try_wait(&sm.full[s], parity)) {
+        if (!mbar_test_wait(&sm.full[s], parity)) {
             // nothing to merge yet: announce the last chunk before waiting
             if (tid == 0 && sm.pend != NONE) {
                 bulk_wait_all();

@@ -508,8 +508,9 @@ __global__ void __launch_bounds__(RUN_BLOCK) k_runs(Job J)
     __shared__ unsigned long long gentry[NGROUPS];
     const int lane = tid & 31, warp = tid >> 5;
     unsigned long long at = 0;                   // range 0 begins chunk 0: state 0, no runs before
-    for (uint32_t r0 = 0; r0 < G; r0 += SCAN_WIN) {
-        const uint32_t nr = min(SCAN_WIN, G - r0);
+    const uint32_t GR = K ? min(G, (T + K - 1) / K) : 0u;   // ranges that hold chunks
+    for (uint32_t r0 = 0; r0 < GR; r0 += SCAN_WIN) {
+        const uint32_t nr = min(SCAN_WIN, GR - r0);
         for (uint32_t i = tid; i < nr * MAP_STATES; i += RUN_BLOCK)
             win[i / MAP_STATES][i % MAP_STATES] = __ldcg(J.range_agg + (size_t)r0 * MAP_STATES + i);
         __syncthreads();
