@@ -299,22 +299,33 @@ __global__ void __launch_bounds__(VM_BLOCK) k_vm_rounds(Job J)
             }
         }
         if (!vm_barrier(C)) return;
-        // 2. the touched pages, in page order (CTA 0)
+        // 2. the touched pages, in page order (CTA 0; each thread takes
+        //    TOUCH_PER consecutive pages per pass)
         if (blockIdx.x == 0) {
+            constexpr uint32_t TOUCH_PER = 8;
             uint32_t carry = 0;
-            for (uint32_t base = 0; base < NA; base += VM_BLOCK) {
-                const uint32_t u = base + tid;
-                const bool t = u < NA && J.page_cnt[u] > 0;
-                const uint32_t bal = __ballot_sync(0xffffffffu, t);
-                if (lane == 0) warp_sums[warp] = __popc(bal);
+            for (uint32_t base = 0; base < NA; base += VM_BLOCK * TOUCH_PER) {
+                const uint32_t u0 = base + tid * TOUCH_PER;
+                uint32_t flags = 0;
+#pragma unroll
+                for (uint32_t i = 0; i < TOUCH_PER; ++i)
+                    if (u0 + i < NA && J.page_cnt[u0 + i] > 0) flags |= 1u << i;
+                const uint32_t c = __popc(flags);
+                uint32_t x = c;                       // inclusive warp scan of the counts
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= o) x += y;
+                }
+                if (lane == 31) warp_sums[warp] = x;
                 __syncthreads();
-                uint32_t before = carry + __popc(bal & ((1u << lane) - 1u));
-                uint32_t tot = 0;
+                uint32_t before = carry + x - c, tot = 0;
                 for (int w = 0; w < VM_BLOCK / 32; ++w) {
                     if (w < warp) before += warp_sums[w];
                     tot += warp_sums[w];
                 }
-                if (t) J.touched[before] = u;
+                for (uint32_t i = 0; i < TOUCH_PER; ++i)
+                    if (flags & (1u << i)) J.touched[before++] = u0 + i;
                 carry += tot;
                 __syncthreads();
             }
@@ -330,16 +341,23 @@ __global__ void __launch_bounds__(VM_BLOCK) k_vm_rounds(Job J)
                 const uint32_t e = J.wave_node[j];
                 if (e != NONE) atomicMax(&J.front[e], J.wave_front[j]);
             }
-            if (blockIdx.x == 0 && tid == 0) {
-                const uint32_t top = C->vm_free_top;
-                const uint32_t k = min(min(J.vm_wave_max, top), ntouched - pos);
-                if (k == 0) set_error(C, DERR_INTERNAL, 62);      // no free page: cannot progress
-                for (uint32_t j = 0; j < k; ++j) J.pt_new[J.touched[pos + j]] = J.free_stack[top - 1 - j];
-                C->vm_free_top = top - k;
-                C->vm_wave = k;
-                C->vm_waves += 1;
-                const uint32_t extra = J.vm_pool > top - k ? J.vm_pool - (top - k) : 0u;   // pages beyond n/P
-                if (extra > C->vm_in_use_peak) C->vm_in_use_peak = extra;
+            if (blockIdx.x == 0) {
+                // the wave's output pages come off the top of the free stack
+                __shared__ uint32_t s_top, s_k;
+                if (tid == 0) {
+                    const uint32_t top = C->vm_free_top;
+                    const uint32_t k = min(min(J.vm_wave_max, top), ntouched - pos);
+                    if (k == 0) set_error(C, DERR_INTERNAL, 62);      // no free page: cannot progress
+                    C->vm_free_top = top - k;
+                    C->vm_wave = k;
+                    C->vm_waves += 1;
+                    const uint32_t extra = J.vm_pool > top - k ? J.vm_pool - (top - k) : 0u;   // pages beyond n/P
+                    if (extra > C->vm_in_use_peak) C->vm_in_use_peak = extra;
+                    s_top = top;
+                    s_k = k;
+                }
+                __syncthreads();
+                for (uint32_t j = tid; j < s_k; j += VM_BLOCK) J.pt_new[J.touched[pos + j]] = J.free_stack[s_top - 1 - j];
             }
             if (!vm_barrier(C)) return;
             if (*(volatile uint32_t*)&C->error) return;
