@@ -289,7 +289,8 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
         J.vm = 1;
         J.vm_plog2 = plog2;
         J.vm_na_cap = (uint32_t)((cfg->max_n + (1ull << plog2) - 1) >> plog2);
-        J.vm_wave_max = (uint32_t)(2 * c->grid_vm);
+        // a wave: one output page for every page group of every CTA
+        J.vm_wave_max = (uint32_t)c->grid_vm * ps::vm_groups_per_cta(plog2);
         J.vm_pool = cfg->pool_pages ? cfg->pool_pages : J.vm_wave_max + 64;
         if (J.vm_pool < 8) J.vm_pool = 8;
         const size_t P = (size_t)1 << plog2;
@@ -303,9 +304,7 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
         if (st == PS_OK) st = dev_alloc(c, &J.touched, J.vm_na_cap);
         if (st == PS_OK) st = dev_alloc(c, &J.free_stack, (size_t)J.vm_na_cap + J.vm_pool);
         if (st == PS_OK) st = dev_alloc(c, &J.holder, (size_t)J.vm_na_cap + J.vm_pool);
-        if (st == PS_OK) st = dev_alloc(c, &J.front, entry_cap);
-        if (st == PS_OK) st = dev_alloc(c, &J.wave_front, 2ull * J.vm_wave_max);
-        if (st == PS_OK) st = dev_alloc(c, &J.wave_node, 2ull * J.vm_wave_max);
+        if (st == PS_OK) st = dev_alloc(c, &J.vm_split_at, (size_t)J.vm_na_cap + 1);
     } else {
         if (st == PS_OK) st = dev_alloc(c, &J.keysB, max_total);
         if (st == PS_OK && cfg->want_perm) st = dev_alloc(c, &J.permB, max_total);
@@ -346,7 +345,7 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
     if (st == PS_OK && ((!vm && !J.keysB) || !J.inst || !J.chunk_map || !J.chunk_info || !J.chunk_bits || !J.range_agg || !J.range_entry ||
                         !J.run_start || !J.kappa || !J.power || !J.na || !J.nb || !J.tiles || !J.gnodes ||
                         !J.gsorted || !J.dep || !J.chunk_node || !J.ctr ||
-                        (!vm && cfg->want_perm && !J.permB) || (vm && (!J.pool_keys || !J.pt || !J.front))))
+                        (!vm && cfg->want_perm && !J.permB) || (vm && (!J.pool_keys || !J.pt || !J.vm_split_at))))
         st = PS_EINTERNAL;
     if (st != PS_OK) {
         cudaGetLastError();

@@ -190,9 +190,7 @@ struct Job {
     uint32_t* touched;          // the round's written pages, in order
     uint32_t* free_stack;       // free physical pages
     uint32_t* holder;           // physical page -> virtual page it holds (final Copy)
-    unsigned long long* front;  // per merge: (outputs done << 32) | left elements consumed
-    unsigned long long* wave_front;  // 2 per wave page: new fronts of the merges it advanced
-    uint32_t* wave_node;        // 2 per wave page: those merges (NONE: none)
+    uint32_t* vm_split_at;      // per page start inside a merge of the round: its merge-path split
 };
 
 // ---------------------------------------------------------------- helpers
@@ -346,6 +344,7 @@ cudaError_t launch_merge_rounds(const Job& J, int grid, int stages, cudaStream_t
 cudaError_t launch_finish(const Job& J, cudaStream_t s);
 cudaError_t launch_vm(const Job& J, int grid, cudaStream_t s);
 int vm_rounds_max_grid(int num_sms);
+uint32_t vm_groups_per_cta(uint32_t plog2);
 int merge_rounds_max_grid(int num_sms, int stages);
 int tiles_max_grid(int num_sms);
 

@@ -14,11 +14,14 @@
 // wave taking its pages from the stack: a merge consumes exactly as many
 // input elements as it writes, so the pages freed by one wave cover the next
 // one, and the pool needs only about one wave of pages plus a few partly
-// consumed pages -- not n elements.  Merge-path searches are bounded below by
-// each merge's consumed front, so they never read a page that went back to
-// the stack.  Finally Copy (Sec. 4) moves every virtual page to its own array
-// page: a page still holding data that is needed later is first moved to a
-// free page, exactly as the paper describes.
+// consumed pages -- not n elements.  Every merge-path split a page needs (at
+// page boundaries inside a merge) is searched at the start of the round, all
+// pages in parallel, while every input page still holds its data; the waves
+// then only stream.  Finally Copy (Sec. 4) moves every virtual page to its own
+// array page: a page still holding data that is needed later is first moved
+// to a free page, exactly as the paper describes.
+#include <algorithm>
+
 #include "ps_internal.cuh"
 
 namespace ps {
@@ -26,8 +29,38 @@ namespace ps {
 namespace {
 
 constexpr int VM_BLOCK = 256;
-constexpr int VM_K = 9;
-constexpr int VM_E = VM_BLOCK * VM_K;     // outputs per sub-chunk
+constexpr int VM_WARPS = VM_BLOCK / 32;
+constexpr int VM_K = 16;                  // outputs per thread of a merge sub-chunk
+constexpr int VM_SLOTS = VM_BLOCK * VM_K + 8 * VM_WARPS;   // staging words per CTA
+
+// A CTA works on several output pages at once: groups of W warps, W = P / 512
+// clamped to 1..8, each group merging sub-chunks of 512 W = 16 x its threads
+// outputs (at least one page) in its own slice of shared memory, with its own
+// named barrier.
+struct VmGroup {
+    uint32_t g;        // group index inside the CTA
+    uint32_t groups;   // groups per CTA
+    uint32_t nthr;     // threads per group
+    uint32_t tid;      // thread index inside the group
+    uint32_t cap;      // outputs per sub-chunk
+};
+
+__device__ __forceinline__ VmGroup vm_group(uint32_t plog2)
+{
+    VmGroup G;
+    const uint32_t w = plog2 >= 9 ? min(1u << (plog2 - 9), (uint32_t)VM_WARPS) : 1u;
+    G.groups = VM_WARPS / w;
+    G.nthr = 32u * w;
+    G.g = threadIdx.x / G.nthr;
+    G.tid = threadIdx.x % G.nthr;
+    G.cap = G.nthr * VM_K;
+    return G;
+}
+
+__device__ __forceinline__ void group_sync(const VmGroup& G)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(1u + G.g), "r"(G.nthr) : "memory");
+}
 
 __device__ __forceinline__ uint32_t* phys_k(const Job& J, uint32_t p)
 {
@@ -99,13 +132,13 @@ __device__ bool vm_barrier(Ctr* C)
     return s_ok != 0;
 }
 
-// Left-child elements among the first d outputs of merge g, searched only
-// above the consumed front (a_lo left / b_lo right elements are gone).
-__device__ uint32_t vm_split(const Job& J, const GSorted& g, uint32_t d, uint32_t a_lo, uint32_t b_lo)
+// Left-child elements among the first d outputs of merge g (merge path over
+// the page-table-translated keys).
+__device__ uint32_t vm_split(const Job& J, const GSorted& g, uint32_t d)
 {
     const uint32_t lo = (uint32_t)g.goff, mid = lo + g.la;
-    uint32_t l = max(a_lo, d > g.lb ? d - g.lb : 0u);
-    uint32_t h = min(d - min(d, b_lo), g.la);
+    uint32_t l = d > g.lb ? d - g.lb : 0u;
+    uint32_t h = min(d, g.la);
     while (l < h) {
         const uint32_t m = (l + h) >> 1;
         if (vkey(J, lo + m) <= vkey(J, mid + d - 1 - m)) l = m + 1; else h = m;
@@ -138,17 +171,20 @@ __device__ void consume(const Job& J, uint32_t v0, uint32_t cnt, uint32_t n)
 }
 
 struct VmSmem {
-    uint32_t k[VM_E + 8];
-    uint32_t p[VM_E + 8];
-    uint32_t seg_lo[6], seg_hi[6], seg_node[6];
-    uint32_t nseg;
-    uint32_t a0, a1;
+    uint32_t k[VM_SLOTS];
+    uint32_t p[VM_SLOTS];
+    uint32_t seg_lo[VM_WARPS][6], seg_hi[VM_WARPS][6], seg_node[VM_WARPS][6];
+    uint32_t nseg[VM_WARPS];
+    uint32_t a[VM_WARPS][2];
 };
 
-// One output page of the current wave: its merge segments and copy gaps.
-__device__ void vm_page(const Job& J, VmSmem& sm, uint32_t u, uint32_t slot, uint32_t n, bool perm)
+// One output page of the current wave, by one group: its merge segments and
+// copy gaps.
+__device__ void vm_page(const Job& J, VmSmem& sm, const VmGroup& G, uint32_t u, uint32_t n, bool perm)
 {
-    const int tid = threadIdx.x;
+    const uint32_t tid = G.tid, gi = G.g;
+    uint32_t* sk = sm.k + gi * (G.cap + 8);
+    uint32_t* sp = sm.p + gi * (G.cap + 8);
     const uint32_t L = J.vm_plog2;
     const uint32_t ps0 = u << L, pe = min(ps0 + (1u << L), n);
     uint32_t* dk = phys_k(J, J.pt_new[u]);
@@ -169,103 +205,95 @@ __device__ void vm_page(const Job& J, VmSmem& sm, uint32_t u, uint32_t slot, uin
             const uint32_t lo = (uint32_t)g.goff, hi = lo + g.la + g.lb;
             const uint32_t s0 = max(lo, ps0), s1 = min(hi, pe);
             if (s0 >= s1) continue;
-            if (s0 > cur) { sm.seg_lo[ns] = cur; sm.seg_hi[ns] = s0; sm.seg_node[ns] = NONE; ++ns; }
-            sm.seg_lo[ns] = s0; sm.seg_hi[ns] = s1; sm.seg_node[ns] = e[i]; ++ns;
+            if (s0 > cur) { sm.seg_lo[gi][ns] = cur; sm.seg_hi[gi][ns] = s0; sm.seg_node[gi][ns] = NONE; ++ns; }
+            sm.seg_lo[gi][ns] = s0; sm.seg_hi[gi][ns] = s1; sm.seg_node[gi][ns] = e[i]; ++ns;
             cur = s1;
         }
-        if (cur < pe) { sm.seg_lo[ns] = cur; sm.seg_hi[ns] = pe; sm.seg_node[ns] = NONE; ++ns; }
-        sm.nseg = ns;
+        if (cur < pe) { sm.seg_lo[gi][ns] = cur; sm.seg_hi[gi][ns] = pe; sm.seg_node[gi][ns] = NONE; ++ns; }
+        sm.nseg[gi] = ns;
     }
-    if (tid == 0) {
-        J.wave_node[2 * slot] = NONE;
-        J.wave_node[2 * slot + 1] = NONE;
-    }
-    __syncthreads();
-    const uint32_t nseg = sm.nseg;
-    uint32_t merge_no = 0;                       // record slot of this page's merge segments
+    group_sync(G);
+    const uint32_t nseg = sm.nseg[gi];
     for (uint32_t sg = 0; sg < nseg; ++sg) {
-        const uint32_t s0 = sm.seg_lo[sg], s1 = sm.seg_hi[sg], e = sm.seg_node[sg];
+        const uint32_t s0 = sm.seg_lo[gi][sg], s1 = sm.seg_hi[gi][sg], e = sm.seg_node[gi][sg];
         if (e == NONE) {                         // carried over unchanged (a gap)
-            for (uint32_t v = s0 + tid; v < s1; v += VM_BLOCK) {
-                dk[v - ps0] = vkey(J, v);
-                if (dp) dp[v - ps0] = vperm(J, v);
+#pragma unroll 8
+            for (uint32_t v = s0 + tid; v < s1; v += G.nthr) {
+                const uint32_t ph = J.pt[v >> L], off = v & ((1u << L) - 1u);
+                dk[v - ps0] = phys_k(J, ph)[off];
+                if (dp) dp[v - ps0] = phys_p(J, ph)[off];
             }
-            __syncthreads();
+            group_sync(G);
             if (tid == 0) consume(J, s0, s1 - s0, n);
             continue;
         }
         const GSorted g = J.gsorted[e];
         const uint32_t lo = (uint32_t)g.goff, mid = lo + g.la;
-        const unsigned long long fr = J.front[e];
-        if (merge_no > 1) set_error(J.ctr, DERR_INTERNAL, 64);
-        const uint32_t a_front = (uint32_t)fr, d_front = (uint32_t)(fr >> 32);
-        for (uint32_t x0 = s0; x0 < s1; x0 += VM_E) {
-            const uint32_t x1 = min(x0 + (uint32_t)VM_E, s1);
+        for (uint32_t x0 = s0; x0 < s1; x0 += G.cap) {
+            const uint32_t x1 = min(x0 + G.cap, s1);
             const uint32_t d0 = x0 - lo, d1 = x1 - lo;
-            if (tid == 0) sm.a0 = vm_split(J, g, d0, a_front, d_front - a_front);
-            if (tid == 32) sm.a1 = d1 == g.la + g.lb ? g.la : vm_split(J, g, d1, a_front, d_front - a_front);
-            __syncthreads();
-            const uint32_t a0 = sm.a0, a1 = sm.a1, b0 = d0 - a0, b1 = d1 - a1;
-            const uint32_t na = a1 - a0, nb = b1 - b0, cnt = na + nb;
-            for (uint32_t i = tid; i < cnt; i += VM_BLOCK) {
-                const uint32_t v = i < na ? lo + a0 + i : mid + b0 + (i - na);
-                sm.k[i] = vkey(J, v);
-                if (perm) sm.p[i] = vperm(J, v);
+            if (tid < 2) {
+                // the splits at the merge's ends are 0 and la; at a page start
+                // inside the merge the round's search left it in vm_split_at
+                // (a sub-chunk always holds a whole page, so no other boundary
+                // occurs)
+                const uint32_t x = tid == 0 ? x0 : x1, d = x - lo;
+                uint32_t a;
+                if (d == 0) a = 0;
+                else if (d == g.la + g.lb) a = g.la;
+                else if ((x & ((1u << L) - 1u)) == 0) a = J.vm_split_at[x >> L];
+                else { a = 0; set_error(J.ctr, DERR_INTERNAL, 65); }   // a sub-chunk holds a whole page
+                sm.a[gi][tid] = a;
             }
-            __syncthreads();
-            uint32_t okv[VM_K], opv[VM_K];
+            group_sync(G);
+            const uint32_t a0 = sm.a[gi][0], a1 = sm.a[gi][1], b0 = d0 - a0, b1 = d1 - a1;
+            const uint32_t na = a1 - a0, nb = b1 - b0, cnt = na + nb;
+            // the slices' keys (and permutation) through the page table; eight
+            // iterations per thread in flight at once
+#pragma unroll 8
+            for (uint32_t i = tid; i < cnt; i += G.nthr) {
+                const uint32_t v = i < na ? lo + a0 + i : mid + b0 + (i - na);
+                const uint32_t ph = J.pt[v >> L], off = v & ((1u << L) - 1u);
+                sk[i] = phys_k(J, ph)[off];
+                if (perm) sp[i] = phys_p(J, ph)[off];
+            }
+            group_sync(G);
+            // each thread merges VM_K consecutive outputs straight into the
+            // fresh output page (a pool page nobody else reads this wave)
             const uint32_t t0 = tid * VM_K;
             if (t0 < cnt) {
                 uint32_t l = t0 > nb ? t0 - nb : 0u, h = min(t0, na);
                 while (l < h) {
                     const uint32_t m = (l + h) >> 1;
-                    if (sm.k[m] <= sm.k[na + t0 - 1 - m]) l = m + 1; else h = m;
+                    if (sk[m] <= sk[na + t0 - 1 - m]) l = m + 1; else h = m;
                 }
                 uint32_t ia = l, ib = na + (t0 - l);
-#pragma unroll
+                uint32_t* ok = dk + (x0 - ps0) + t0;
+                uint32_t* op = dp ? dp + (x0 - ps0) + t0 : nullptr;
+#pragma unroll 4
                 for (int j = 0; j < VM_K; ++j) {
                     if (t0 + j < cnt) {
-                        const bool ta = ia < na && (ib >= cnt || sm.k[ia] <= sm.k[ib]);
+                        const bool ta = ia < na && (ib >= cnt || sk[ia] <= sk[ib]);
                         const uint32_t src = ta ? ia : ib;
-                        okv[j] = sm.k[src];
-                        opv[j] = perm ? sm.p[src] : 0u;
+                        ok[j] = sk[src];
+                        if (op) op[j] = sp[src];
                         ia += ta;
                         ib += !ta;
                     }
                 }
             }
-            __syncthreads();
-#pragma unroll
-            for (int j = 0; j < VM_K; ++j) {
-                if (t0 + j < cnt) {
-                    sm.k[t0 + j] = okv[j];
-                    if (perm) sm.p[t0 + j] = opv[j];
-                }
-            }
-            __syncthreads();
-            for (uint32_t i = tid; i < cnt; i += VM_BLOCK) {
-                dk[x0 - ps0 + i] = sm.k[i];
-                if (dp) dp[x0 - ps0 + i] = sm.p[i];
-            }
-            __syncthreads();
+            group_sync(G);
             if (tid == 0) {
                 consume(J, lo + a0, na, n);
                 consume(J, mid + b0, nb, n);
-                // the merge's new front; applied between waves, so every search
-                // of this wave sees the front as it stood when the wave began
-                if (merge_no < 2) {
-                    J.wave_front[2 * slot + merge_no] = ((unsigned long long)d1 << 32) | a1;
-                    J.wave_node[2 * slot + merge_no] = e;
-                }
             }
         }
-        ++merge_no;
     }
 }
 
 }  // namespace
 
-__global__ void __launch_bounds__(VM_BLOCK) k_vm_rounds(Job J)
+__global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_rounds(Job J)
 {
     __shared__ VmSmem sm;
     __shared__ uint32_t warp_sums[VM_BLOCK / 32];
@@ -286,7 +314,6 @@ __global__ void __launch_bounds__(VM_BLOCK) k_vm_rounds(Job J)
             const GSorted g = J.gsorted[e];
             const uint32_t lo = (uint32_t)g.goff, hi = lo + g.la + g.lb;
             const uint32_t first = lo >> L, last = (hi - 1) >> L;
-            if (lane == 0) J.front[e] = 0ull;
             for (uint32_t u = first + lane; u <= last; u += 32) {
                 if (u == first || u == last) {
                     const uint32_t slot = atomicAdd(&J.page_cnt[u], 1u);
@@ -296,6 +323,17 @@ __global__ void __launch_bounds__(VM_BLOCK) k_vm_rounds(Job J)
                     J.page_cnt[u] = 1;
                     J.page_nodes[2 * u] = e;
                 }
+            }
+        }
+        if (!vm_barrier(C)) return;
+        // 1b. the merge-path split at every page start that lies inside a merge,
+        //     one thread per page, before any input page can be recycled
+        for (uint32_t u = blockIdx.x * VM_BLOCK + tid; u < NA; u += gridDim.x * VM_BLOCK) {
+            const uint32_t c = min(J.page_cnt[u], 2u), ps0 = u << L;
+            for (uint32_t i = 0; i < c; ++i) {
+                const GSorted g = J.gsorted[J.page_nodes[2 * u + i]];
+                const uint32_t lo = (uint32_t)g.goff;
+                if (lo < ps0 && ps0 < lo + g.la + g.lb) J.vm_split_at[u] = vm_split(J, g, ps0 - lo);
             }
         }
         if (!vm_barrier(C)) return;
@@ -334,13 +372,7 @@ __global__ void __launch_bounds__(VM_BLOCK) k_vm_rounds(Job J)
         if (!vm_barrier(C)) return;
         // 3. waves of output pages
         const uint32_t ntouched = C->vm_touched;
-        uint32_t prev_k = 0;
         for (uint32_t pos = 0; pos < ntouched;) {
-            // raise the fronts of the merges the previous wave advanced
-            for (uint32_t j = blockIdx.x * VM_BLOCK + tid; j < 2 * prev_k; j += gridDim.x * VM_BLOCK) {
-                const uint32_t e = J.wave_node[j];
-                if (e != NONE) atomicMax(&J.front[e], J.wave_front[j]);
-            }
             if (blockIdx.x == 0) {
                 // the wave's output pages come off the top of the free stack
                 __shared__ uint32_t s_top, s_k;
@@ -362,10 +394,11 @@ __global__ void __launch_bounds__(VM_BLOCK) k_vm_rounds(Job J)
             if (!vm_barrier(C)) return;
             if (*(volatile uint32_t*)&C->error) return;
             const uint32_t k = C->vm_wave;
-            for (uint32_t j = blockIdx.x; j < k; j += gridDim.x) vm_page(J, sm, J.touched[pos + j], j, n, perm);
+            const VmGroup G = vm_group(L);
+            for (uint32_t j = blockIdx.x * G.groups + G.g; j < k; j += gridDim.x * G.groups)
+                vm_page(J, sm, G, J.touched[pos + j], n, perm);
             if (!vm_barrier(C)) return;
             pos += k;
-            prev_k = k;
         }
         // 4. the written pages become current; reset the per-round tables
         for (uint32_t j = blockIdx.x * VM_BLOCK + tid; j < ntouched; j += gridDim.x * VM_BLOCK) {
@@ -485,8 +518,14 @@ int vm_rounds_max_grid(int num_sms)
 {
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_vm_rounds, VM_BLOCK, 0);
-    if (per_sm > 4) per_sm = 4;
+    if (per_sm > 6) per_sm = 6;
     return num_sms * (per_sm > 0 ? per_sm : 1);
+}
+
+uint32_t vm_groups_per_cta(uint32_t plog2)
+{
+    const uint32_t w = plog2 >= 9 ? std::min(1u << (plog2 - 9), (uint32_t)VM_WARPS) : 1u;
+    return VM_WARPS / w;
 }
 
 cudaError_t launch_vm(const Job& J, int grid, cudaStream_t s)

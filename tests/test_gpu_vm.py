@@ -51,8 +51,9 @@ def test_vm_uses_far_less_memory_than_pingpong(oracle_mod):
         kp, ppm, sp = gpu_sort(pp, keys)
     assert np.array_equal(kv, kp) and np.array_equal(pv, ppm)
     assert sv["merge_cost"] == sp["merge_cost"]
-    # Pingpong holds n keys + n permutation entries of scratch; VM holds a pool
-    assert sp["scratch_bytes"] - sv["scratch_bytes"] > 7 * n
+    # Pingpong holds n keys + n permutation entries of scratch (8n bytes); VM
+    # holds a pool of about one wave of pages (a few per CTA), tens of MB here
+    assert sp["scratch_bytes"] - sv["scratch_bytes"] > 6 * n
     assert sv["peak_pages"] > 0
 
 
