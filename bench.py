@@ -272,7 +272,7 @@ def run_batched(args):
     """Workload batched_4096: one captured-graph replay per step."""
     import torch
 
-    from paper_2605_27147_gb300 import autotune, binding, inputs
+    from paper_2605_27147_gb300 import autotune, binding, inputs, replicas
 
     keys_np, off_np = inputs.batch(4096, 3)
     sizes = np.diff(off_np.astype(np.int64))
@@ -327,11 +327,8 @@ def run_batched(args):
     if dist:
         dist.barrier()
     total_ms = sum(a.elapsed_time(b) for a, b in recs)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms_max = float(t.item())
-    value = args.steps * total * world / (total_ms_max / 1000.0)
+    total_ms_max = replicas.max_over_ranks(total_ms, dist, dev)
+    value = replicas.job_rate(args.steps * total, world, total_ms_max)
     # result check on a few instances (sorted keys, permutation consistent)
     gk = work.cpu().numpy().view(np.uint32)
     gp = perm.cpu().numpy().view(np.uint32)
@@ -515,7 +512,7 @@ def main():
 
     import torch
 
-    from paper_2605_27147_gb300 import binding
+    from paper_2605_27147_gb300 import binding, replicas
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -594,11 +591,8 @@ def main():
     runs_ms = sum(p["runs"] for p in phases)
     phase_tot = {k: sum(p[k] for p in phases) for k in binding.PHASES}
 
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms_max = float(t.item())
-    value = elems * world / (total_ms_max / 1000.0)
+    total_ms_max = replicas.max_over_ranks(total_ms, dist, dev)
+    value = replicas.job_rate(elems, world, total_ms_max)
 
     # end to end through ps_run_host with pinned host arrays
     e2e = None

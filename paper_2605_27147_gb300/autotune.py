@@ -5,7 +5,8 @@ captures the batched sort into a CUDA graph for every candidate of
 
 * tile_log2          -- on-chip tile capacity 2^10 .. 2^12 (how much of the
                         merge tree is merged in shared memory before the HBM rounds)
-* merge_ctas_per_sm  -- CTAs per SM of the persistent HBM merge kernel
+* merge_ctas_per_sm  -- shape of the persistent HBM merge kernel: 2 or 3 CTAs
+                        per SM with three shared-memory stages, 4 with two
 
 times each graph's replays with CUDA events, and keeps the fastest.  Results
 are cached in memory and in a JSON file (``$PS_AUTOTUNE_CACHE``, default
