@@ -299,7 +299,7 @@ def run_batched(args):
     doff = torch.from_numpy(off_np.astype(np.int64)).to(dev)
     tuned = autotune.tune(work, doff, perm, max_n, stream=stream)
     ctx = binding.Context(max_n, want_perm=True, max_total=total, max_count=count, tile_log2=tuned["tile_log2"],
-                          merge_ctas_per_sm=tuned["merge_ctas_per_sm"], flags=binding.PS_FLAG_TIMING,
+                          merge_shape=tuned["merge_shape"], flags=binding.PS_FLAG_TIMING,
                           device=local, stream=stream)
     graph = ctx.graph_batched(work, doff, perm)
 
@@ -389,7 +389,7 @@ def run_batched(args):
                    "sizes": "log-uniform in [2^8, 2^20), seed 3, uniform keys", "max_instance": max_n,
                    "outputs": "sorted keys + stable permutation (uint32)", "storage": "pingpong",
                    "launch": "one CUDA-graph replay per step (persistent cooperative merge kernel)",
-                   "autotune": {k: tuned[k] for k in ("tile_log2", "merge_ctas_per_sm", "ms", "cached")},
+                   "autotune": {k: tuned[k] for k in ("tile_log2", "merge_shape", "ms", "cached")},
                    "l2": "inputs (2 GiB keys) exceed L2; input restored before every replay (untimed)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "batched_vs_plain_loop": {"batched": value / world, "plain_loop": loop_rate,

@@ -5,8 +5,8 @@ captures the batched sort into a CUDA graph for every candidate of
 
 * tile_log2          -- on-chip tile capacity 2^10 .. 2^12 (how much of the
                         merge tree is merged in shared memory before the HBM rounds)
-* merge_ctas_per_sm  -- shape of the persistent HBM merge kernel: 2 or 3 CTAs
-                        per SM with three shared-memory stages, 4 with two
+* merge_shape        -- shape of the persistent HBM merge kernel: 1 = three
+                        shared-memory stages of 384 consumer threads, 2 = two of 512
 
 times each graph's replays with CUDA events, and keeps the fastest.  Results
 are cached in memory and in a JSON file (``$PS_AUTOTUNE_CACHE``, default
@@ -22,7 +22,7 @@ import os
 import threading
 
 TILE_LOG2 = (10, 11, 12)
-MERGE_CTAS = (2, 3, 4)
+MERGE_SHAPES = (1, 2)
 _lock = threading.Lock()
 _mem: dict = {}
 
@@ -32,9 +32,12 @@ def _cache_path() -> str:
                           os.path.join(os.path.expanduser("~"), ".cache", "paper_2605_27147_gb300", "autotune.json"))
 
 
+CACHE_VERSION = 2   # entries of other versions (other tuning knobs) are not reused
+
+
 def shape_key(gpu: str, count: int, total: int, max_n: int) -> str:
     b = lambda x: int(round(math.log2(max(1, x)) * 2))   # half-octave buckets
-    return f"{gpu}|c{b(count)}|t{b(total)}|m{b(max_n)}"
+    return f"v{CACHE_VERSION}|{gpu}|c{b(count)}|t{b(total)}|m{b(max_n)}"
 
 
 def _load_file() -> dict:
@@ -59,7 +62,7 @@ def _store_file(d: dict) -> None:
 
 def tune(keys, offsets, perm, max_n: int, *, reps: int = 3, stream=None, use_cache: bool = True,
          candidates=None) -> dict:
-    """Best {tile_log2, merge_ctas_per_sm} for sorting this batch, with timings.
+    """Best {tile_log2, merge_shape} for sorting this batch, with timings.
 
     keys / perm: CUDA int32 tensors (keys are restored after tuning);
     offsets: CUDA int64 tensor of count + 1 entries."""
@@ -81,11 +84,11 @@ def tune(keys, offsets, perm, max_n: int, *, reps: int = 3, stream=None, use_cac
                 return dict(disk[key], cached=True)
     stream = stream or torch.cuda.Stream(keys.device)
     pristine = keys.clone()
-    cands = candidates or [(t, c) for t in TILE_LOG2 for c in MERGE_CTAS]
+    cands = candidates or [(t, m) for t in TILE_LOG2 for m in MERGE_SHAPES]
     results = []
-    for tile_log2, ctas in cands:
+    for tile_log2, shape in cands:
         with binding.Context(max_n, want_perm=perm is not None, max_total=total, max_count=count,
-                             tile_log2=tile_log2, merge_ctas_per_sm=ctas, stream=stream) as ctx:
+                             tile_log2=tile_log2, merge_shape=shape, stream=stream) as ctx:
             g = ctx.graph_batched(keys, offsets, perm)
             times = []
             with torch.cuda.stream(stream):
@@ -99,11 +102,11 @@ def tune(keys, offsets, perm, max_n: int, *, reps: int = 3, stream=None, use_cac
                     if i:
                         times.append(e0.elapsed_time(e1))
             g.close()
-        results.append({"tile_log2": tile_log2, "merge_ctas_per_sm": ctas, "ms": min(times)})
+        results.append({"tile_log2": tile_log2, "merge_shape": shape, "ms": min(times)})
     keys.copy_(pristine)
     torch.cuda.synchronize(keys.device)
     best = min(results, key=lambda r: r["ms"])
-    out = {"tile_log2": best["tile_log2"], "merge_ctas_per_sm": best["merge_ctas_per_sm"], "ms": best["ms"],
+    out = {"tile_log2": best["tile_log2"], "merge_shape": best["merge_shape"], "ms": best["ms"],
            "trials": results, "shape": key}
     with _lock:
         _mem[key] = out

@@ -41,9 +41,7 @@ constexpr uint32_t RANGE_COUNT_MASK = 0x7fffffffu;
 constexpr int RUN_GRID_PER_SM = 4;            // run-detection CTAs (chunk ranges) per SM
 constexpr int RUN_RANGES_MAX = 1024;
 
-constexpr int MERGE_BLOCK = 256;
-constexpr int MERGE_K = 9;        // outputs per thread (odd: conflict-free shared-memory strides)
-constexpr int MERGE_E = MERGE_BLOCK * MERGE_K;   // outputs per HBM merge chunk
+constexpr uint32_t MERGE_E_MIN = 384 * 9;   // smallest HBM merge chunk of the kernel's shapes
 
 constexpr int TILE_BLOCK = 256;
 constexpr int TILE_MAX_LOG2 = 12;  // tile capacity bound of the shared-memory layout
@@ -101,7 +99,7 @@ struct Ctr {
     uint32_t n_tiles;
     uint32_t n_gnodes;
     uint32_t bucket_count[NPOW + 1];   // HBM merges of round r
-    uint32_t bucket_nchunk[NPOW + 1];  // their chunks (MERGE_E outputs each)
+    uint32_t bucket_nchunk[NPOW + 1];  // their chunks (merge_e outputs each)
     unsigned long long bucket_cursor[NPOW + 1];   // (merges << 40) | chunks placed so far
     uint32_t bucket_start[NPOW + 2];   // GSorted index where round r starts
     uint32_t bucket_chunk[NPOW + 2];   // chunks of round r: [0, bucket_chunk[r])
@@ -147,7 +145,7 @@ struct Job {
     uint32_t count;
     uint32_t want_perm;
     uint32_t tile_cap;          // T: largest merge-tree node merged on chip
-    uint32_t pad0;
+    uint32_t merge_e;           // outputs per HBM merge chunk (the merge kernel's shape)
     unsigned long long max_n;   // limits the offsets table is checked against
     unsigned long long max_total;
     Inst* inst;
@@ -337,15 +335,15 @@ __device__ __forceinline__ uint32_t find_inst(uint32_t count, unsigned long long
 // ---------------------------------------------------------------- launchers
 cudaError_t launch_setup(const Job& J, cudaStream_t s);
 cudaError_t launch_runs(const Job& J, int grid, cudaStream_t s);
-int merge_rounds_grid_for(int num_sms, int ctas_per_sm, int stages);
+uint32_t merge_chunk(int shape);
 cudaError_t launch_plan(const Job& J, int grid, cudaStream_t s);
 cudaError_t launch_tiles(const Job& J, int grid, cudaStream_t s);
-cudaError_t launch_merge_rounds(const Job& J, int grid, int stages, cudaStream_t s);
+cudaError_t launch_merge_rounds(const Job& J, int grid, int shape, cudaStream_t s);
 cudaError_t launch_finish(const Job& J, cudaStream_t s);
 cudaError_t launch_vm(const Job& J, int grid, cudaStream_t s);
 int vm_rounds_max_grid(int num_sms);
 uint32_t vm_groups_per_cta(uint32_t plog2);
-int merge_rounds_max_grid(int num_sms, int stages);
+int merge_rounds_max_grid(int num_sms, int shape);
 int tiles_max_grid(int num_sms);
 
 }  // namespace ps

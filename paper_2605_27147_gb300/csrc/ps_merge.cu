@@ -3,7 +3,8 @@
 // take the left run) between the caller's arrays and the scratch arrays
 // (Pingpong storage, Sec. 3).
 //
-// Every merge is cut into chunks of MERGE_E outputs.  Chunks are numbered
+// Every merge is cut into chunks of E outputs (E = the kernel shape's consumer
+// threads x MERGE_K).  Chunks are numbered
 // round by round (rounds go from the largest power to the smallest), so a
 // merge's children always carry smaller chunk numbers than the merge itself.
 // One persistent cooperative launch processes every chunk as a dataflow,
@@ -51,21 +52,26 @@ namespace ps {
 namespace {
 
 constexpr uint32_t FULL_MASK = 0xffffffffu;
-constexpr int SLOT = MERGE_E + 16;   // a staged array: up to 3 + 3 + 3 shift slots
 constexpr int EDGE_SLOTS = 8;        // unaligned elements of one slice (<= 7)
-constexpr int NCONS = MERGE_BLOCK / 32;          // consumer warps
-constexpr int PRODUCER_WARP = NCONS;
-constexpr int SEARCH_WARP = NCONS + 1;
-constexpr int MTHREADS = MERGE_BLOCK + 64;        // + producer warp + search warp
-// Two variants: NST = 3 shared-memory stages with three CTAs per SM, or
-// NST = 2 stages with four CTAs per SM (more CTAs, fewer bytes in flight each).
-template <int NST>
-constexpr int merge_min_ctas() { return NST == 2 ? 4 : 3; }
+constexpr int MERGE_K = 9;           // outputs per consumer thread (odd: conflict-free strides)
 #ifndef PS_MERGE_NSEARCH
 #define PS_MERGE_NSEARCH 16
 #endif
 constexpr int NSEARCH = PS_MERGE_NSEARCH;         // chunks a CTA prepares ahead (<= 32)
 static_assert(NSEARCH >= 1 && NSEARCH <= 32, "one search warp");
+
+// The kernel's shape: NST shared-memory stages, BLOCK consumer threads (each
+// MERGE_K outputs of a chunk of E = BLOCK x MERGE_K), one producer warp and
+// one search warp.
+template <int NST, int BLOCK>
+struct Shape {
+    static constexpr int E = BLOCK * MERGE_K;
+    static constexpr int SLOT = E + 16;           // a staged array: up to 3 + 3 + 3 shift slots
+    static constexpr int NCONS = BLOCK / 32;      // consumer warps
+    static constexpr int PRODUCER_WARP = NCONS;
+    static constexpr int SEARCH_WARP = NCONS + 1;
+    static constexpr int MTHREADS = BLOCK + 64;
+};
 
 constexpr uint32_t RS_EMPTY = 0, RS_FULL = 1, RS_END = 2;   // ring slot states
 
@@ -143,8 +149,9 @@ struct Timeline {
     uint32_t round;
 };
 
-template <int NST>
+template <int NST, int BLOCK>
 struct __align__(16) MergeSmem {
+    static constexpr int SLOT = Shape<NST, BLOCK>::SLOT;
     uint32_t in_k[NST][SLOT];
     uint32_t in_p[NST][SLOT];
     uint32_t out_k[SLOT];
@@ -161,8 +168,15 @@ struct __align__(16) MergeSmem {
 };
 
 // 228 KiB of shared memory per SM, 1 KiB of it reserved per CTA
-static_assert(sizeof(MergeSmem<2>) <= 233472 / merge_min_ctas<2>() - 1024, "two stages must fit four CTAs per SM");
-static_assert(sizeof(MergeSmem<3>) <= 233472 / merge_min_ctas<3>() - 1024, "three stages must fit three CTAs per SM");
+// CTAs per SM the stages leave room for (228 KiB of shared memory per SM,
+// 1 KiB of it reserved per CTA), at most 4
+template <int NST, int BLOCK>
+constexpr int merge_min_ctas()
+{
+    return 233472 / (int)(sizeof(MergeSmem<NST, BLOCK>) + 1024) < 4
+               ? 233472 / (int)(sizeof(MergeSmem<NST, BLOCK>) + 1024)
+               : 4;
+}
 
 __device__ __forceinline__ uint32_t ld_vol(const uint32_t* p)
 {
@@ -174,13 +188,14 @@ __device__ __forceinline__ void st_vol(uint32_t* p, uint32_t v)
     *(volatile uint32_t*)p = v;
 }
 
-// Producer lane 0: the stage's addresses for a prepared chunk.
+// Producer lane 0: the stage's addresses for a prepared chunk (chunks of E outputs).
+template <int E>
 __device__ void describe(const Job& J, const Prep& p, Stage& S)
 {
     const GSorted& g = p.g;
     const uint32_t total = g.la + g.lb;
-    const uint32_t d0 = (p.c - g.chunk_base) * MERGE_E;
-    const uint32_t d1 = min(d0 + (uint32_t)MERGE_E, total);
+    const uint32_t d0 = (p.c - g.chunk_base) * E;
+    const uint32_t d1 = min(d0 + (uint32_t)E, total);
     const uint32_t a0 = p.a0, a1 = p.a1;
     const uint32_t b0 = d0 - a0, b1 = d1 - a1;
     const bool src_b = ((g.depth + 1) & 1u) != 0, dst_b = (g.depth & 1u) != 0;
@@ -221,8 +236,8 @@ __device__ __forceinline__ bool aligned16(const void* p)
 }
 
 // Producer lane 0: announce the stage's bytes and start its bulk copies.
-template <int NST>
-__device__ void issue_loads(MergeSmem<NST>& sm, int s, Ctr* C)
+template <int NST, int BLOCK>
+__device__ void issue_loads(MergeSmem<NST, BLOCK>& sm, int s, Ctr* C)
 {
     const Stage& S = sm.st[s];
     uint32_t bytes = 0;
@@ -266,8 +281,8 @@ __device__ void issue_loads(MergeSmem<NST>& sm, int s, Ctr* C)
 // Producer lane l: the unaligned element l % 8 of slice l / 8 (0: left
 // keys, 1: right keys, 2: left perm, 3: right perm) goes into the stage.
 // Loads bypass L1: the data were written by other SMs during this launch.
-template <int NST>
-__device__ __forceinline__ void copy_edge(MergeSmem<NST>& sm, int s, int lane)
+template <int NST, int BLOCK>
+__device__ __forceinline__ void copy_edge(MergeSmem<NST, BLOCK>& sm, int s, int lane)
 {
     const Stage& S = sm.st[s];
     const int which = lane >> 3, j = lane & 7;
@@ -294,9 +309,10 @@ __device__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, Ctr* C, uint32
     return true;
 }
 
+template <int BLOCK>
 __device__ __forceinline__ void consumers_sync()
 {
-    asm volatile("bar.sync 1, %0;" ::"n"(MERGE_BLOCK) : "memory");
+    asm volatile("bar.sync 1, %0;" ::"n"(BLOCK) : "memory");
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar)
@@ -351,8 +367,8 @@ __device__ void timeline_note(Timeline& t, Ctr* C, uint32_t r, unsigned long lon
 
 // ---------------------------------------------------------------- roles
 
-template <int NST>
-__device__ __noinline__ void search_warp(const Job& J, MergeSmem<NST>& sm, Ctr* C)
+template <int NST, int BLOCK>
+__device__ __noinline__ void search_warp(const Job& J, MergeSmem<NST, BLOCK>& sm, Ctr* C)
 {
     // Each iteration a lane issues the one global access its state needs and
     // takes the result at the end of the iteration, so the accesses of all
@@ -416,8 +432,8 @@ __device__ __noinline__ void search_warp(const Job& J, MergeSmem<NST>& sm, Ctr* 
             state = S_INFO;
         } else if (state == S_INFO) {
             g = g_new;
-            d0 = (c - g.chunk_base) * MERGE_E;
-            d1 = min(d0 + (uint32_t)MERGE_E, g.la + g.lb);
+            d0 = (c - g.chunk_base) * Shape<NST, BLOCK>::E;
+            d1 = min(d0 + (uint32_t)Shape<NST, BLOCK>::E, g.la + g.lb);
             uint32_t lo = 0, hi = NPOW;              // last round starting at or before c
             while (hi - lo > 1) {
                 const uint32_t mid = (lo + hi) >> 1;
@@ -479,8 +495,8 @@ __device__ __noinline__ void search_warp(const Job& J, MergeSmem<NST>& sm, Ctr* 
     }
 }
 
-template <int NST>
-__device__ __noinline__ void producer_warp(const Job& J, MergeSmem<NST>& sm, Ctr* C)
+template <int NST, int BLOCK>
+__device__ __noinline__ void producer_warp(const Job& J, MergeSmem<NST, BLOCK>& sm, Ctr* C)
 {
     const int lane = threadIdx.x & 31;
     uint32_t k = 0;                      // stages filled so far (stage k % NST)
@@ -517,12 +533,12 @@ __device__ __noinline__ void producer_warp(const Job& J, MergeSmem<NST>& sm, Ctr
             __threadfence_block();
             st_vol(&sm.ring_state[src], RS_EMPTY);
             sm.st[s].last = 0;
-            describe(J, p, sm.st[s]);
+            describe<Shape<NST, BLOCK>::E>(J, p, sm.st[s]);
             fence_proxy_async_global();   // the inputs were written by other CTAs' bulk stores
-            issue_loads(sm, s, C);
+            issue_loads<NST, BLOCK>(sm, s, C);
         }
         __syncwarp();
-        copy_edge(sm, s, lane);
+        copy_edge<NST, BLOCK>(sm, s, lane);
         __syncwarp();
         if (lane == 0) mbar_arrive(&sm.full[s]);
     }
@@ -539,8 +555,8 @@ __device__ __noinline__ void producer_warp(const Job& J, MergeSmem<NST>& sm, Ctr
     __syncwarp();
 }
 
-template <int NST>
-__device__ __noinline__ void consumer_warps(const Job& J, MergeSmem<NST>& sm, Ctr* C)
+template <int NST, int BLOCK>
+__device__ __noinline__ void consumer_warps(const Job& J, MergeSmem<NST, BLOCK>& sm, Ctr* C)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool perm = J.want_perm != 0;
@@ -575,7 +591,7 @@ __device__ __noinline__ void consumer_warps(const Job& J, MergeSmem<NST>& sm, Ct
         const uint32_t* Ap = &sm.in_p[s][S.sp[0]];
         const uint32_t* Bp = &sm.in_p[s][S.sp[1]];
         if (tid == 0) bulk_wait_read_all();         // the previous output has left the staging arrays
-        consumers_sync();
+        consumers_sync<BLOCK>();
         const uint32_t x0 = tid * MERGE_K;
         if (x0 < cnt) {
             uint32_t lo = x0 > nb ? x0 - nb : 0u, hi = min(x0, na);
@@ -622,7 +638,7 @@ __device__ __noinline__ void consumer_warps(const Job& J, MergeSmem<NST>& sm, Ct
         }
         if (lane == 0) mbar_arrive(&sm.empty[s]);   // this warp is done with the stage
         fence_proxy_async_smem();
-        consumers_sync();
+        consumers_sync<BLOCK>();
         if (warp != 0) continue;
         // warp 0 sends the chunk out: the ends by ordinary stores (lanes 0-7
         // keys, 16-23 permutation), ordered before thread 0's announcement by
@@ -673,17 +689,17 @@ __device__ __noinline__ void consumer_warps(const Job& J, MergeSmem<NST>& sm, Ct
 
 }  // namespace
 
-template <int NST>
-__global__ void __launch_bounds__(MTHREADS, merge_min_ctas<NST>()) k_merge_rounds(Job J)
+template <int NST, int BLOCK>
+__global__ void __launch_bounds__(Shape<NST, BLOCK>::MTHREADS, merge_min_ctas<NST, BLOCK>()) k_merge_rounds(Job J)
 {
     extern __shared__ __align__(16) unsigned char merge_raw[];
-    MergeSmem<NST>& sm = *reinterpret_cast<MergeSmem<NST>*>(merge_raw);
+    MergeSmem<NST, BLOCK>& sm = *reinterpret_cast<MergeSmem<NST, BLOCK>*>(merge_raw);
     Ctr* C = J.ctr;
     const int tid = threadIdx.x, warp = tid >> 5;
     if (tid == 0) {
         for (int s = 0; s < NST; ++s) {
             mbar_init(&sm.full[s], 2);        // expect_tx arrival + edge arrival
-            mbar_init(&sm.empty[s], NCONS);   // one arrival per consumer warp
+            mbar_init(&sm.empty[s], Shape<NST, BLOCK>::NCONS);   // one arrival per consumer warp
         }
         fence_mbar_init();
         sm.err = *(volatile uint32_t*)&C->error;
@@ -693,41 +709,42 @@ __global__ void __launch_bounds__(MTHREADS, merge_min_ctas<NST>()) k_merge_round
     for (int r = tid; r <= NPOW; r += blockDim.x) sm.round_chunk[r] = C->bucket_chunk[r];
     __syncthreads();
     if (sm.err) return;
-    if (warp == SEARCH_WARP) search_warp<NST>(J, sm, C);
-    else if (warp == PRODUCER_WARP) producer_warp<NST>(J, sm, C);
-    else consumer_warps<NST>(J, sm, C);
+    if (warp == Shape<NST, BLOCK>::SEARCH_WARP) search_warp<NST, BLOCK>(J, sm, C);
+    else if (warp == Shape<NST, BLOCK>::PRODUCER_WARP) producer_warp<NST, BLOCK>(J, sm, C);
+    else consumer_warps<NST, BLOCK>(J, sm, C);
 }
 
-template <int NST>
+// The two shapes: 1 = three stages of 384 consumer threads (measured best up
+// to about 2^26 elements), 2 = two stages of 512 consumer threads (larger).
+template <int NST, int BLOCK>
 int max_grid(int num_sms)
 {
     int per_sm = 0;
-    const int bytes = (int)sizeof(MergeSmem<NST>);
-    cudaFuncSetAttribute(k_merge_rounds<NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_merge_rounds<NST>, MTHREADS, bytes);
+    const int bytes = (int)sizeof(MergeSmem<NST, BLOCK>);
+    cudaFuncSetAttribute(k_merge_rounds<NST, BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_merge_rounds<NST, BLOCK>, Shape<NST, BLOCK>::MTHREADS,
+                                                  bytes);
     return num_sms * (per_sm > 0 ? per_sm : 1);
 }
 
-int merge_rounds_max_grid(int num_sms, int stages)
+int merge_rounds_max_grid(int num_sms, int shape)
 {
-    return stages == 2 ? max_grid<2>(num_sms) : max_grid<3>(num_sms);
+    return shape == 2 ? max_grid<2, 512>(num_sms) : max_grid<3, 384>(num_sms);
 }
 
-int merge_rounds_grid_for(int num_sms, int ctas_per_sm, int stages)
+uint32_t merge_chunk(int shape)
 {
-    const int mx = merge_rounds_max_grid(num_sms, stages) / num_sms;
-    const int k = (ctas_per_sm > 0 && ctas_per_sm < mx) ? ctas_per_sm : mx;
-    return num_sms * k;
+    return shape == 2 ? (uint32_t)Shape<2, 512>::E : (uint32_t)Shape<3, 384>::E;
 }
 
-cudaError_t launch_merge_rounds(const Job& J, int grid, int stages, cudaStream_t s)
+cudaError_t launch_merge_rounds(const Job& J, int grid, int shape, cudaStream_t s)
 {
     void* args[] = {(void*)&J};
-    if (stages == 2)
-        return cudaLaunchCooperativeKernel((const void*)k_merge_rounds<2>, dim3(grid), dim3(MTHREADS), args,
-                                           sizeof(MergeSmem<2>), s);
-    return cudaLaunchCooperativeKernel((const void*)k_merge_rounds<3>, dim3(grid), dim3(MTHREADS), args,
-                                       sizeof(MergeSmem<3>), s);
+    if (shape == 2)
+        return cudaLaunchCooperativeKernel((const void*)k_merge_rounds<2, 512>, dim3(grid),
+                                           dim3(Shape<2, 512>::MTHREADS), args, sizeof(MergeSmem<2, 512>), s);
+    return cudaLaunchCooperativeKernel((const void*)k_merge_rounds<3, 384>, dim3(grid),
+                                       dim3(Shape<3, 384>::MTHREADS), args, sizeof(MergeSmem<3, 384>), s);
 }
 
 }  // namespace ps

@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(PLAN_BLOCK) k_depth(Job J)
             J.gnodes[g].depth = depth_of(na, nb, gn.t, I.runs);
             const uint32_t size = node_size(J.run_start + I.run_base, na, nb, gn.t);
             atomicAdd(&J.ctr->bucket_count[32 - gn.power], 1u);
-            atomicAdd(&J.ctr->bucket_nchunk[32 - gn.power], (size + MERGE_E - 1) / MERGE_E);
+            atomicAdd(&J.ctr->bucket_nchunk[32 - gn.power], (size + J.merge_e - 1) / J.merge_e);
         }
     }
 }
@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(PLAN_BLOCK) k_bucket(Job J)
             const uint32_t mid = rs[gn.t];
             const uint32_t hi = rs[J.nb[I.run_base + gn.t]];
             const uint32_t r = 32 - gn.power;
-            const uint32_t nch = (hi - lo + MERGE_E - 1) / MERGE_E;
+            const uint32_t nch = (hi - lo + J.merge_e - 1) / J.merge_e;
             const unsigned long long old = atomicAdd(&C->bucket_cursor[r], (1ull << 40) | nch);
             const uint32_t at = C->bucket_start[r] + (uint32_t)(old >> 40);
             GSorted o;
@@ -386,7 +386,7 @@ __global__ void __launch_bounds__(PLAN_BLOCK) k_chunk_nodes(Job J)
         }
         J.gsorted[me].parent = par;
         const GSorted g = J.gsorted[me];
-        atomicAdd(&J.dep[par], (g.la + g.lb + MERGE_E - 1) / MERGE_E);
+        atomicAdd(&J.dep[par], (g.la + g.lb + J.merge_e - 1) / J.merge_e);
     }
     const uint32_t groups = (total + 31) / 32;
     for (uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x; gi < groups; gi += gridDim.x * blockDim.x) {
