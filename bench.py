@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample-seconds", type=float, default=20.0)
+    ap.add_argument("--lane-total", type=int, default=1 << 25,
+                    help="serving: most elements one batch of a lane may hold")
     return ap.parse_args()
 
 
@@ -299,7 +301,7 @@ def run_batched(args):
     doff = torch.from_numpy(off_np.astype(np.int64)).to(dev)
     tuned = autotune.tune(work, doff, perm, max_n, stream=stream)
     ctx = binding.Context(max_n, want_perm=True, max_total=total, max_count=count, tile_log2=tuned["tile_log2"],
-                          merge_shape=tuned["merge_shape"], flags=binding.PS_FLAG_TIMING,
+                          flags=binding.PS_FLAG_TIMING,
                           device=local, stream=stream)
     graph = ctx.graph_batched(work, doff, perm)
 
@@ -389,7 +391,7 @@ def run_batched(args):
                    "sizes": "log-uniform in [2^8, 2^20), seed 3, uniform keys", "max_instance": max_n,
                    "outputs": "sorted keys + stable permutation (uint32)", "storage": "pingpong",
                    "launch": "one CUDA-graph replay per step (persistent cooperative merge kernel)",
-                   "autotune": {k: tuned[k] for k in ("tile_log2", "merge_shape", "ms", "cached")},
+                   "autotune": {k: tuned[k] for k in ("tile_log2", "ms", "cached")},
                    "l2": "inputs (2 GiB keys) exceed L2; input restored before every replay (untimed)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "batched_vs_plain_loop": {"batched": value / world, "plain_loop": loop_rate,
@@ -412,6 +414,9 @@ def run_batched(args):
 
 
 def run_serving(args, rate=2000.0, duration=10.0, budget=64 << 30):
+    # Elements per batch are capped so that a burst cannot build one long
+    # batch (latency grows with the batch; the offered load is far below
+    # capacity, so smaller batches cost no throughput).
     """Workload serving: Poisson arrivals replayed in real time through ps_server."""
     import torch
 
@@ -432,7 +437,8 @@ def run_serving(args, rate=2000.0, duration=10.0, budget=64 << 30):
     ring_k = torch.empty(ring_n, dtype=torch.int32, pin_memory=True)
     ring_p = torch.empty(ring_n, dtype=torch.int32, pin_memory=True)
     pk, pp, pin = ring_k.data_ptr(), ring_p.data_ptr(), pool.data_ptr()
-    srv = binding.Server(budget, max_n, lanes=4, lane_max_count=256, device=local)
+    lane_total = args.lane_total
+    srv = binding.Server(budget, max_n, lanes=4, lane_max_total=lane_total, lane_max_count=256, device=local)
     # warm-up: a few requests (module loading, first launches)
     for i in range(8):
         srv.wait(srv.submit(pin, pk, pp, 1 << 20), 60.0)

@@ -75,11 +75,7 @@ typedef struct ps_config {
     uint32_t tile_log2;  /* on-chip tile capacity 2^tile_log2 in 10..12 (0: 12)      */
     uint32_t pool_pages; /* VM page-pool size in pages (0: chosen by the library)    */
     uint32_t flags;      /* PS_FLAG_* below                                          */
-    uint32_t merge_shape; /* HBM merge kernel shape, a tuning knob (see
-                            paper_2605_27147_gb300/autotune.py): 1 = three shared-
-                            memory stages of 384 consumer threads, 2 = two stages of
-                            512, 0 = chosen per call by size; others: PS_EINVAL      */
-    uint32_t reserved[2];
+    uint32_t reserved[3];
 } ps_config;
 
 /* ps_config.flags */

@@ -41,8 +41,7 @@ class ps_config(ctypes.Structure):
         ("tile_log2", ctypes.c_uint32),
         ("pool_pages", ctypes.c_uint32),
         ("flags", ctypes.c_uint32),
-        ("merge_shape", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint32 * 2),
+        ("reserved", ctypes.c_uint32 * 3),
     ]
 
 
@@ -201,7 +200,7 @@ class Context:
 
     def __init__(self, max_n: int, *, mode: int = PS_MODE_PINGPONG, want_perm: bool = True,
                  max_total: int = 0, max_count: int = 0, tile_log2: int = 0, page_log2: int = 0,
-                 pool_pages: int = 0, flags: int = 0, merge_shape: int = 0, device: int = 0,
+                 pool_pages: int = 0, flags: int = 0, device: int = 0,
                  stream=None):
         import torch
 
@@ -209,7 +208,7 @@ class Context:
         self.stream = stream if stream is not None else torch.cuda.current_stream(device)
         cfg = ps_config(mode=mode, want_perm=1 if want_perm else 0, max_n=max_n, max_total=max_total,
                         max_count=max_count, page_log2=page_log2, tile_log2=tile_log2,
-                        pool_pages=pool_pages, flags=flags, merge_shape=merge_shape)
+                        pool_pages=pool_pages, flags=flags)
         h = ctypes.c_void_p()
         _check(lib().ps_create(ctypes.byref(cfg), device, ctypes.c_void_p(self.stream.cuda_stream),
                                ctypes.byref(h)), "ps_create")

@@ -14,9 +14,7 @@ struct ps_ctx {
     cudaStream_t stream;
     int num_sms;
     int grid_runs, grid_plan, grid_tiles, grid_vm;
-    int grid_merge[3];              // HBM merge kernel grid per shape (1, 2)
-    int merge_shape;                // 1 or 2 when fixed by the config, 0: chosen per call
-    int cur_shape;                  // the shape of the call being enqueued
+    int grid_merge;
     unsigned long long max_total;
     uint32_t max_count;
     ps::Job base;               // device buffers; per-call fields filled by each run
@@ -104,8 +102,7 @@ ps_status enqueue(ps_ctx* c, const ps::Job& J)
     if (J.vm) {
         if (ps::launch_vm(J, c->grid_vm, s) != cudaSuccess || !mark(5)) return PS_ECUDA;
     } else {
-        if (ps::launch_merge_rounds(J, c->grid_merge[c->cur_shape], c->cur_shape, s) != cudaSuccess || !mark(5))
-            return PS_ECUDA;
+        if (ps::launch_merge_rounds(J, c->grid_merge, s) != cudaSuccess || !mark(5)) return PS_ECUDA;
     }
     if (ps::launch_finish(J, s) != cudaSuccess || !mark(6)) return PS_ECUDA;
     if (cudaMemcpyAsync(c->h_ctr, J.ctr, sizeof(ps::Ctr), cudaMemcpyDeviceToHost, s) != cudaSuccess)
@@ -157,11 +154,6 @@ ps_status run_common(ps_ctx* c, uint32_t* d_keys, uint32_t* d_perm, const uint64
     J.offsets = reinterpret_cast<const unsigned long long*>(d_offsets);
     J.single_n = single_n;
     J.count = count;
-    // the HBM merge kernel's shape: measured on GB300, three stages of 384
-    // consumer threads win up to about 2^26 elements, two stages of 512 above
-    const unsigned long long size = d_offsets ? J.max_total : single_n;
-    c->cur_shape = c->merge_shape ? c->merge_shape : (size >= (1ull << 26) ? 2 : 1);
-    J.merge_e = ps::merge_chunk(c->cur_shape);
     c->last_valid = 0;
     ps_status st = enqueue(c, J);
     if (st != PS_OK) {
@@ -247,19 +239,14 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
     c->grid_runs = std::min(c->num_sms * ps::RUN_GRID_PER_SM, ps::RUN_RANGES_MAX);
     c->grid_plan = c->num_sms * 8;
     c->grid_tiles = ps::tiles_max_grid(c->num_sms);
-    if (cfg->merge_shape > 2) {
-        delete c;
-        return PS_EINVAL;
-    }
-    c->merge_shape = (int)cfg->merge_shape;
-    c->grid_merge[0] = 0;
-    for (int sh = 1; sh <= 2; ++sh) c->grid_merge[sh] = ps::merge_rounds_max_grid(c->num_sms, sh);
+    c->grid_merge = ps::merge_rounds_max_grid(c->num_sms);
     c->grid_vm = ps::vm_rounds_max_grid(c->num_sms);
     if (c->grid_vm > 1024) c->grid_vm = 1024;
 
     ps::Job& J = c->base;
     std::memset(&J, 0, sizeof(J));
     J.tile_cap = 1u << tile_log2;
+    J.merge_e = ps::merge_chunk();
     J.max_n = cfg->max_n;
     J.max_total = max_total;
     const unsigned long long slot_cap = max_total / 32 + 2ull * c->max_count + 2;
@@ -267,7 +254,7 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
     const unsigned long long entry_cap = slot_cap;
     // chunks summed over all rounds: at most 32 rounds of max_total outputs
     const unsigned long long chunk_node_cap =
-        (unsigned long long)(ps::NPOW - 1) * (max_total / ps::MERGE_E_MIN) + entry_cap + 2;
+        (unsigned long long)(ps::NPOW - 1) * (max_total / ps::merge_chunk()) + entry_cap + 2;
     if (chunk_cap > 0xffffffffull || entry_cap > 0xffffffffull ||
         chunk_node_cap > 0xffffffffull) {
         delete c;

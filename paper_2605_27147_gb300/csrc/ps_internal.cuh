@@ -41,7 +41,6 @@ constexpr uint32_t RANGE_COUNT_MASK = 0x7fffffffu;
 constexpr int RUN_GRID_PER_SM = 4;            // run-detection CTAs (chunk ranges) per SM
 constexpr int RUN_RANGES_MAX = 1024;
 
-constexpr uint32_t MERGE_E_MIN = 384 * 9;   // smallest HBM merge chunk of the kernel's shapes
 
 constexpr int TILE_BLOCK = 256;
 constexpr int TILE_MAX_LOG2 = 12;  // tile capacity bound of the shared-memory layout
@@ -145,7 +144,7 @@ struct Job {
     uint32_t count;
     uint32_t want_perm;
     uint32_t tile_cap;          // T: largest merge-tree node merged on chip
-    uint32_t merge_e;           // outputs per HBM merge chunk (the merge kernel's shape)
+    uint32_t merge_e;           // outputs per HBM merge chunk (set from the merge kernel's shape)
     unsigned long long max_n;   // limits the offsets table is checked against
     unsigned long long max_total;
     Inst* inst;
@@ -335,15 +334,15 @@ __device__ __forceinline__ uint32_t find_inst(uint32_t count, unsigned long long
 // ---------------------------------------------------------------- launchers
 cudaError_t launch_setup(const Job& J, cudaStream_t s);
 cudaError_t launch_runs(const Job& J, int grid, cudaStream_t s);
-uint32_t merge_chunk(int shape);
+uint32_t merge_chunk();
 cudaError_t launch_plan(const Job& J, int grid, cudaStream_t s);
 cudaError_t launch_tiles(const Job& J, int grid, cudaStream_t s);
-cudaError_t launch_merge_rounds(const Job& J, int grid, int shape, cudaStream_t s);
+cudaError_t launch_merge_rounds(const Job& J, int grid, cudaStream_t s);
 cudaError_t launch_finish(const Job& J, cudaStream_t s);
 cudaError_t launch_vm(const Job& J, int grid, cudaStream_t s);
 int vm_rounds_max_grid(int num_sms);
 uint32_t vm_groups_per_cta(uint32_t plog2);
-int merge_rounds_max_grid(int num_sms, int shape);
+int merge_rounds_max_grid(int num_sms);
 int tiles_max_grid(int num_sms);
 
 }  // namespace ps

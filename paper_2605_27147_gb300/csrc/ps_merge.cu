@@ -714,37 +714,30 @@ __global__ void __launch_bounds__(Shape<NST, BLOCK>::MTHREADS, merge_min_ctas<NS
     else consumer_warps<NST, BLOCK>(J, sm, C);
 }
 
-// The two shapes: 1 = three stages of 384 consumer threads (measured best up
-// to about 2^26 elements), 2 = two stages of 512 consumer threads (larger).
-template <int NST, int BLOCK>
-int max_grid(int num_sms)
+// The shape used: two shared-memory stages of 512 consumer threads (two CTAs
+// per SM).  Measured on GB300 against 256-448 consumer threads and 2-4 stages,
+// it was the fastest from 10^5 elements to 2^28 and for batches.
+using MergeShape = Shape<2, 512>;
+
+int merge_rounds_max_grid(int num_sms)
 {
     int per_sm = 0;
-    const int bytes = (int)sizeof(MergeSmem<NST, BLOCK>);
-    cudaFuncSetAttribute(k_merge_rounds<NST, BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_merge_rounds<NST, BLOCK>, Shape<NST, BLOCK>::MTHREADS,
-                                                  bytes);
+    const int bytes = (int)sizeof(MergeSmem<2, 512>);
+    cudaFuncSetAttribute(k_merge_rounds<2, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_merge_rounds<2, 512>, MergeShape::MTHREADS, bytes);
     return num_sms * (per_sm > 0 ? per_sm : 1);
 }
 
-int merge_rounds_max_grid(int num_sms, int shape)
+uint32_t merge_chunk()
 {
-    return shape == 2 ? max_grid<2, 512>(num_sms) : max_grid<3, 384>(num_sms);
+    return (uint32_t)MergeShape::E;
 }
 
-uint32_t merge_chunk(int shape)
-{
-    return shape == 2 ? (uint32_t)Shape<2, 512>::E : (uint32_t)Shape<3, 384>::E;
-}
-
-cudaError_t launch_merge_rounds(const Job& J, int grid, int shape, cudaStream_t s)
+cudaError_t launch_merge_rounds(const Job& J, int grid, cudaStream_t s)
 {
     void* args[] = {(void*)&J};
-    if (shape == 2)
-        return cudaLaunchCooperativeKernel((const void*)k_merge_rounds<2, 512>, dim3(grid),
-                                           dim3(Shape<2, 512>::MTHREADS), args, sizeof(MergeSmem<2, 512>), s);
-    return cudaLaunchCooperativeKernel((const void*)k_merge_rounds<3, 384>, dim3(grid),
-                                       dim3(Shape<3, 384>::MTHREADS), args, sizeof(MergeSmem<3, 384>), s);
+    return cudaLaunchCooperativeKernel((const void*)k_merge_rounds<2, 512>, dim3(grid), dim3(MergeShape::MTHREADS),
+                                       args, sizeof(MergeSmem<2, 512>), s);
 }
 
 }  // namespace ps

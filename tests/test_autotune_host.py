@@ -18,7 +18,7 @@ def test_cache_file_round_trip(tmp_path, monkeypatch):
     path = tmp_path / "sub" / "autotune.json"
     monkeypatch.setenv("PS_AUTOTUNE_CACHE", str(path))
     assert autotune._load_file() == {}                 # no file yet
-    entry = {"tile_log2": 12, "merge_shape": 2, "ms": 38.6, "trials": [], "shape": "k"}
+    entry = {"tile_log2": 12, "ms": 38.6, "trials": [], "shape": "k"}
     autotune._store_file({"k": entry})
     assert json.loads(path.read_text()) == {"k": entry}
     assert autotune._load_file() == {"k": entry}
@@ -26,6 +26,5 @@ def test_cache_file_round_trip(tmp_path, monkeypatch):
     assert autotune._load_file() == {}
 
 
-def test_candidates_cover_both_merge_kernel_shapes():
+def test_candidates_cover_every_tile_size():
     assert set(autotune.TILE_LOG2) == {10, 11, 12}
-    assert set(autotune.MERGE_SHAPES) == {1, 2}

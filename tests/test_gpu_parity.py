@@ -100,14 +100,14 @@ def test_result_is_stable_sort_large(oracle_mod):
         assert st["n"] == n
 
 
-@pytest.mark.parametrize("ctas", [1, 2])
-def test_merge_kernel_shapes(oracle_mod, ctas):
-    # 1: three shared-memory stages of 384 consumer threads; 2: two stages of 512
+@pytest.mark.parametrize("tile_log2", [10, 11])
+def test_smaller_tiles(oracle_mod, tile_log2):
+    # smaller on-chip tiles leave more of the tree to the HBM merge kernel
     from paper_2605_27147_gb300 import binding
 
-    with binding.Context(1 << 22, want_perm=True, merge_shape=ctas) as c:
+    with binding.Context(1 << 22, want_perm=True, tile_log2=tile_log2) as c:
         for dist, n in (("uniform", 3000017), ("runs", (1 << 22) - 5), ("few", 1234567)):
-            keys = inputs.make(dist, n, 17 + ctas)
+            keys = inputs.make(dist, n, 17 + tile_log2)
             ref = oracle_mod.powersort(keys)
             k, p, st = gpu_sort(c, keys)
             assert_matches_oracle(c, keys, ref, k, p, st)
