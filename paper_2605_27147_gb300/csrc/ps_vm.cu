@@ -80,11 +80,6 @@ __device__ __forceinline__ uint32_t vkey(const Job& J, uint32_t v)
     return phys_k(J, J.pt[v >> J.vm_plog2])[v & ((1u << J.vm_plog2) - 1)];
 }
 
-__device__ __forceinline__ uint32_t vperm(const Job& J, uint32_t v)
-{
-    return phys_p(J, J.pt[v >> J.vm_plog2])[v & ((1u << J.vm_plog2) - 1)];
-}
-
 __device__ __forceinline__ uint32_t page_size(const Job& J, uint32_t u, uint32_t n)
 {
     const uint32_t P = 1u << J.vm_plog2;
