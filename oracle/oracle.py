@@ -12,6 +12,10 @@ all arithmetic is in the C source, which follows the paper:
 * :func:`stable_sort`  -- the plain definition of the result (stable order)
 * :func:`powersort`    -- Algorithm 1 with Pingpong storage (Sec. 3)
 * :func:`powersort_vm` -- Algorithm 1 with virtual-memory storage (Sec. 4)
+
+``descending_runs=True`` selects the run-detection variant named in Sec. 5
+("Algorithm variants"): strictly decreasing runs are accepted too and
+reversed in place.
 """
 from __future__ import annotations
 
@@ -49,7 +53,12 @@ class _Stats(ctypes.Structure):
         ("max_stack", ctypes.c_uint32),
         ("max_power", ctypes.c_uint32),
         ("page_size", ctypes.c_uint32),
+        ("reversed_runs", ctypes.c_uint64),
+        ("reverse_moves", ctypes.c_uint64),
     ]
+
+
+DESCENDING_RUNS = 1   # ORACLE_DESCENDING_RUNS
 
 
 def compile_source(src: str, so: str) -> str:
@@ -100,6 +109,12 @@ def _declare(lib):
     lib.oracle_powersort_vm.restype = ctypes.c_int
     lib.oracle_powersort_vm.argtypes = [u32p, u32p, ctypes.c_uint64, ctypes.c_uint64,
                                         u32p, u8p, u32p, ctypes.POINTER(_Stats)]
+    lib.oracle_powersort_ex.restype = ctypes.c_int
+    lib.oracle_powersort_ex.argtypes = [u32p, u32p, ctypes.c_uint64, u32p, u8p, u32p,
+                                        ctypes.c_uint32, ctypes.POINTER(_Stats)]
+    lib.oracle_powersort_vm_ex.restype = ctypes.c_int
+    lib.oracle_powersort_vm_ex.argtypes = [u32p, u32p, ctypes.c_uint64, ctypes.c_uint64,
+                                           u32p, u8p, u32p, ctypes.c_uint32, ctypes.POINTER(_Stats)]
 
 
 def _ptr(a: np.ndarray, ctype):
@@ -139,7 +154,7 @@ class OracleResult:
     stats: dict = field(default_factory=dict)
 
 
-def _run(fn_name: str, keys: np.ndarray, page_size: int | None, lib=None):
+def _run(fn_name: str, keys: np.ndarray, page_size: int | None, lib=None, options: int | None = None):
     lib = lib or _load()
     key = np.array(keys, dtype=np.uint32, copy=True)
     n = key.size
@@ -151,8 +166,10 @@ def _run(fn_name: str, keys: np.ndarray, page_size: int | None, lib=None):
     args = [_ptr(key, ctypes.c_uint32), _ptr(perm, ctypes.c_uint32), n]
     if page_size is not None:
         args.append(page_size)
-    args += [_ptr(runs, ctypes.c_uint32), _ptr(pw, ctypes.c_uint8), _ptr(mg, ctypes.c_uint32),
-             ctypes.byref(st)]
+    args += [_ptr(runs, ctypes.c_uint32), _ptr(pw, ctypes.c_uint8), _ptr(mg, ctypes.c_uint32)]
+    if options is not None:
+        args.append(options)
+    args.append(ctypes.byref(st))
     rc = getattr(lib, fn_name)(*args)
     if rc:
         raise MemoryError(fn_name)
@@ -168,11 +185,15 @@ def _run(fn_name: str, keys: np.ndarray, page_size: int | None, lib=None):
     )
 
 
-def powersort(keys: np.ndarray, lib=None) -> OracleResult:
+def powersort(keys: np.ndarray, lib=None, descending_runs: bool = False) -> OracleResult:
     """Algorithm 1 with Pingpong storage, executed literally on one core."""
+    if descending_runs:
+        return _run("oracle_powersort_ex", keys, None, lib, DESCENDING_RUNS)
     return _run("oracle_powersort", keys, None, lib)
 
 
-def powersort_vm(keys: np.ndarray, page_size: int, lib=None) -> OracleResult:
+def powersort_vm(keys: np.ndarray, page_size: int, lib=None, descending_runs: bool = False) -> OracleResult:
     """Algorithm 1 with virtual-memory (paged) storage, on one core."""
+    if descending_runs:
+        return _run("oracle_powersort_vm_ex", keys, int(page_size), lib, DESCENDING_RUNS)
     return _run("oracle_powersort_vm", keys, int(page_size), lib)

@@ -21,13 +21,22 @@
  *                        runs as page lists, a free list, PageMerge
  *                        (Algorithm 2, left) and the final page-permuting Copy;
  *                        it reports the peak number of pages in use.
+ *   oracle_powersort_ex, oracle_powersort_vm_ex
+ *                        the same with options; ORACLE_DESCENDING_RUNS takes
+ *                        the variant of Sec. 5 "Algorithm variants" that also
+ *                        accepts decreasing runs (reversed in place).
  *
  * Readings taken where the paper is silent (all listed in the design doc):
  *   - indices are 0-based and half open: a = [i, j), b = [j, k);
  *   - the final loop of Algorithm 1 pops the stack after every merge;
  *   - minrun for n < 64 is n (the halving loop never runs);
  *   - a forced run ends at min(s + minrun, n) and is not re-scanned after the
- *     insertion sort; a natural run at least minrun long is kept whole.
+ *     insertion sort; a natural run at least minrun long is kept whole;
+ *   - decreasing runs (variant): a run whose first two elements are in
+ *     strictly decreasing order continues while the order stays strictly
+ *     decreasing and is then reversed (strictness keeps equal elements in
+ *     input order, so the sort stays stable); a shorter one than minrun is
+ *     extended and insertion-sorted like any other forced run.
  * Parity is pinned for every function here (no "parity unpinned" entries).
  */
 #include <stdint.h>
@@ -51,7 +60,12 @@ typedef struct {
     uint32_t max_stack;          /* largest stack height seen                 */
     uint32_t max_power;          /* largest boundary power                    */
     uint32_t page_size;          /* VM storage: P (else 0)                    */
+    uint64_t reversed_runs;      /* decreasing runs found and reversed        */
+    uint64_t reverse_moves;      /* element moves made by the reversals       */
 } oracle_stats;
+
+/* options of oracle_powersort_ex / oracle_powersort_vm_ex */
+#define ORACLE_DESCENDING_RUNS 1u
 
 /* Sec. 5, "Algorithm variants": start from l = n and halve (rounding up)
  * until l < 64.  When n < 64 the loop body never runs and minrun = n. */
@@ -115,13 +129,36 @@ int oracle_stable_sort(const uint32_t* keys, uint64_t n, uint32_t* keys_out, uin
  * Sec. 5: a run shorter than minrun is extended to min(s + minrun, n)
  * elements and sorted by (stable) insertion sort.  Returns the run end. */
 static uint64_t extract_run(uint32_t* key, uint32_t* perm, uint64_t s, uint64_t n,
-                            uint32_t minrun, oracle_stats* st)
+                            uint32_t minrun, uint32_t options, oracle_stats* st)
 {
     uint64_t e = s + 1;
-    while (e < n) {
+    int down = 0;
+    if ((options & ORACLE_DESCENDING_RUNS) && e < n) {
         st->scan_comparisons++;
-        if (key[e - 1] > key[e]) break;   /* first descent: run ends here */
+        down = key[s] > key[e];
+    }
+    if (down) {
+        /* strictly decreasing run: extend while a[e-1] > a[e], then reverse */
         ++e;
+        while (e < n) {
+            st->scan_comparisons++;
+            if (!(key[e - 1] > key[e])) break;
+            ++e;
+        }
+        for (uint64_t x = s, y = e - 1; x < y; ++x, --y) {
+            uint32_t tk = key[x], tp = perm[x];
+            key[x] = key[y]; perm[x] = perm[y];
+            key[y] = tk; perm[y] = tp;
+            st->reverse_moves += 2;
+        }
+        st->reversed_runs++;
+    } else {
+        if (e < n && (options & ORACLE_DESCENDING_RUNS)) ++e;   /* pair (s, s+1) already compared */
+        while (e < n) {
+            st->scan_comparisons++;
+            if (key[e - 1] > key[e]) break;   /* first descent: run ends here */
+            ++e;
+        }
     }
     if (e - s < minrun) {
         uint64_t end = s + minrun < n ? s + minrun : n;
@@ -190,9 +227,10 @@ static void pingpong_merge_to_stack(const uint32_t* key, const uint32_t* perm, u
  *   run_starts: receives the start of every run plus n (runs + 1 entries).
  *   powers:     powers[t] = Power of the boundary between run t and run t+1.
  *   merges:     (lo, mid, hi) triples in execution order.
+ *   options:    ORACLE_DESCENDING_RUNS or 0.
  * Any output pointer may be NULL.  Returns 0, or -1 on allocation failure. */
-int oracle_powersort(uint32_t* key, uint32_t* perm, uint64_t n, uint32_t* run_starts,
-                     uint8_t* powers, uint32_t* merges, oracle_stats* st)
+int oracle_powersort_ex(uint32_t* key, uint32_t* perm, uint64_t n, uint32_t* run_starts,
+                        uint8_t* powers, uint32_t* merges, uint32_t options, oracle_stats* st)
 {
     memset(st, 0, sizeof(*st));
     st->n = n;
@@ -209,11 +247,11 @@ int oracle_powersort(uint32_t* key, uint32_t* perm, uint64_t n, uint32_t* run_st
     uint32_t stk_p[80];
     int top = 0;
 
-    uint64_t ci = 0, cj = extract_run(key, perm, 0, n, st->minrun, st); /* curr */
+    uint64_t ci = 0, cj = extract_run(key, perm, 0, n, st->minrun, options, st); /* curr */
     if (run_starts) run_starts[0] = 0;
     st->runs = 1;
     while (cj < n) {                                   /* work not empty */
-        uint64_t nj = cj, nk = extract_run(key, perm, cj, n, st->minrun, st); /* next */
+        uint64_t nj = cj, nk = extract_run(key, perm, cj, n, st->minrun, options, st); /* next */
         if (run_starts) run_starts[st->runs] = (uint32_t)nj;
         uint32_t p = oracle_power(n, ci, cj, nk);
         if (powers) powers[st->runs - 1] = (uint8_t)p;
@@ -269,6 +307,12 @@ int oracle_powersort(uint32_t* key, uint32_t* perm, uint64_t n, uint32_t* run_st
     free(bkey);
     free(bperm);
     return 0;
+}
+
+int oracle_powersort(uint32_t* key, uint32_t* perm, uint64_t n, uint32_t* run_starts,
+                     uint8_t* powers, uint32_t* merges, oracle_stats* st)
+{
+    return oracle_powersort_ex(key, perm, n, run_starts, powers, merges, 0u, st);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -402,16 +446,35 @@ static void vm_note_peak(vm_mem* m)
 }
 
 /* ExtractRun on the VM work buffer: find the run in place (as in the
- * Pingpong form), sort a forced run by insertion sort in place, then move it
- * element by element into a fresh buffer. */
-static int vm_extract_run(vm_mem* m, vm_buf* work, vm_buf* out, uint32_t minrun)
+ * Pingpong form; with ORACLE_DESCENDING_RUNS a strictly decreasing run is
+ * reversed in place), sort a forced run by insertion sort in place, then move
+ * it element by element into a fresh buffer. */
+static int vm_extract_run(vm_mem* m, vm_buf* work, vm_buf* out, uint32_t minrun, uint32_t options)
 {
     oracle_stats* st = m->st;
     uint64_t avail = work->len, e = 1;
+    int down = 0;
+    if ((options & ORACLE_DESCENDING_RUNS) && e < avail) {
+        st->scan_comparisons++;
+        down = *vm_kslot(m, work, 0) > *vm_kslot(m, work, 1);
+        ++e;
+    }
     while (e < avail) {
         st->scan_comparisons++;
-        if (*vm_kslot(m, work, e - 1) > *vm_kslot(m, work, e)) break;
+        const int desc = *vm_kslot(m, work, e - 1) > *vm_kslot(m, work, e);
+        if (desc != down) break;   /* ascending: first descent; decreasing: first non-descent */
         ++e;
+    }
+    if (down) {
+        for (uint64_t x = 0, y = e - 1; x < y; ++x, --y) {
+            uint32_t tk = *vm_kslot(m, work, x), tp = *vm_pslot(m, work, x);
+            *vm_kslot(m, work, x) = *vm_kslot(m, work, y);
+            *vm_pslot(m, work, x) = *vm_pslot(m, work, y);
+            *vm_kslot(m, work, y) = tk;
+            *vm_pslot(m, work, y) = tp;
+            st->reverse_moves += 2;
+        }
+        st->reversed_runs++;
     }
     if (e < minrun) {
         uint64_t end = minrun < avail ? minrun : avail;
@@ -512,10 +575,11 @@ static int vm_copy_back(vm_mem* m, vm_buf* c)
 /* Algorithm 1 with virtual-memory buffers.  Same outputs as oracle_powersort
  * plus st->peak_pages (pages in use at the busiest moment, input pages
  * included) and st->pool_pages (pages allocated beyond the input).
- * page_size must be >= 1.  Returns 0, or -1 on allocation failure. */
-int oracle_powersort_vm(uint32_t* key, uint32_t* perm, uint64_t n, uint64_t page_size,
-                        uint32_t* run_starts, uint8_t* powers, uint32_t* merges,
-                        oracle_stats* st)
+ * page_size must be >= 1; options as for oracle_powersort_ex.  Returns 0,
+ * or -1 on allocation failure. */
+int oracle_powersort_vm_ex(uint32_t* key, uint32_t* perm, uint64_t n, uint64_t page_size,
+                           uint32_t* run_starts, uint8_t* powers, uint32_t* merges,
+                           uint32_t options, oracle_stats* st)
 {
     memset(st, 0, sizeof(*st));
     st->n = n;
@@ -551,13 +615,13 @@ int oracle_powersort_vm(uint32_t* key, uint32_t* perm, uint64_t n, uint64_t page
     vm_note_peak(&m);
 
     uint64_t ci = 0;
-    if (vm_extract_run(&m, &work, &curr, st->minrun)) goto done;
+    if (vm_extract_run(&m, &work, &curr, st->minrun, options)) goto done;
     uint64_t cj = curr.len;
     if (run_starts) run_starts[0] = 0;
     st->runs = 1;
     while (work.len) {
         uint64_t nj = cj;
-        if (vm_extract_run(&m, &work, &next, st->minrun)) goto done;
+        if (vm_extract_run(&m, &work, &next, st->minrun, options)) goto done;
         uint64_t nk = nj + next.len;
         if (run_starts) run_starts[st->runs] = (uint32_t)nj;
         uint32_t p = oracle_power(n, ci, cj, nk);
@@ -609,4 +673,11 @@ done:
     if (m.pkey) for (uint64_t q = m.in_pages; q < m.npages; ++q) { free(m.pkey[q]); free(m.pperm[q]); }
     free(m.pkey); free(m.pperm); free(m.free_stack); free(m.in_free);
     return rc;
+}
+
+int oracle_powersort_vm(uint32_t* key, uint32_t* perm, uint64_t n, uint64_t page_size,
+                        uint32_t* run_starts, uint8_t* powers, uint32_t* merges,
+                        oracle_stats* st)
+{
+    return oracle_powersort_vm_ex(key, perm, n, page_size, run_starts, powers, merges, 0u, st);
 }

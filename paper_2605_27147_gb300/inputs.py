@@ -17,6 +17,8 @@ Distributions (shapes of the paper's workloads, Sec. 5):
               the paper's presortedness construction with S = mean_run.
 ``paper``     the paper's own recipe: values uniform in [100, 10**9], then the
               Geometric presort with parameter 1/S.
+``updown``    like ``runs``, but a fair coin sorts each segment ascending or
+              descending (inputs for the decreasing-run variant of Sec. 5).
 ``sorted`` / ``reversed`` / ``equal`` / ``few``   degenerate cases.
 """
 from __future__ import annotations
@@ -105,6 +107,16 @@ def runs(n: int, seed: int, mean_run: float = 1024.0) -> np.ndarray:
     return presort_segments_fast(keys, lens)
 
 
+def updown(n: int, seed: int, mean_run: float = 1024.0) -> np.ndarray:
+    """Geometric segments as in :func:`runs`, each sorted ascending or (coin) descending."""
+    keys = mt_raw(seed, n)
+    lens = geometric_lengths(n, seed + 7919, mean_run)
+    down = (mt_raw(seed + 104729, lens.size) & np.uint32(1)).astype(bool)
+    seg = np.repeat(np.arange(lens.size, dtype=np.int64), lens)
+    sk = np.where(np.repeat(down, lens), ~keys, keys)
+    return keys[np.lexsort((sk, seg))]
+
+
 def paper(n: int, seed: int, S: float = 2.0) -> np.ndarray:
     """Sec. 5 recipe: values uniform in [100, 10**9], presorted with parameter S."""
     raw = mt_raw(seed, n).astype(np.uint64)
@@ -125,6 +137,8 @@ def make(dist: str, n: int, seed: int) -> np.ndarray:
         return runs(n, seed)
     if dist == "paper":
         return paper(n, seed)
+    if dist == "updown":
+        return updown(n, seed)
     if dist == "sorted":
         return np.sort(uniform(n, seed))
     if dist == "reversed":

@@ -6,6 +6,8 @@
 * :func:`cartesian_nodes` -- the merge tree as the Cartesian tree of the
   boundary powers, found by brute force (nearest smaller power on each side).
 * :func:`run_entropy` -- H of Sec. 2 from the run lengths.
+* :func:`runs_by_rule_descending` -- run starts of the decreasing-run variant
+  (Sec. 5) by a plain scan.
 """
 from __future__ import annotations
 
@@ -74,3 +76,28 @@ def naive_stable_insertion_sort(keys):
             y -= 1
         a[y] = v
     return np.array([k for k, _ in a], np.uint32), np.array([i for _, i in a], np.uint32)
+
+
+def runs_by_rule_descending(keys, m):
+    """Run starts by a plain scan of the decreasing-run variant's rule: a run
+    whose first pair is strictly decreasing continues while strictly
+    decreasing and is reversed; otherwise it continues while non-decreasing;
+    a run shorter than m is extended to m elements (or the end) and sorted."""
+    a = [int(x) for x in keys]
+    n = len(a)
+    starts, s = [0], 0
+    while s < n:
+        e = s + 1
+        if e < n and a[s] > a[e]:
+            while e < n and a[e - 1] > a[e]:
+                e += 1
+            a[s:e] = a[s:e][::-1]
+        else:
+            while e < n and a[e - 1] <= a[e]:
+                e += 1
+        if e - s < m:
+            e = min(s + m, n)
+            a[s:e] = sorted(a[s:e])
+        s = e
+        starts.append(s)
+    return starts

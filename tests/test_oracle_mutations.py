@@ -14,7 +14,7 @@ import pytest
 
 import oracle
 from oracle import oracle as ocore
-from checks import cartesian_nodes, check_stable_sort
+from checks import cartesian_nodes, check_stable_sort, runs_by_rule_descending
 from conftest import golden_rows
 from paper_2605_27147_gb300 import inputs
 
@@ -34,6 +34,15 @@ MUTATIONS = {
                                  "if (key[e - 1] >= key[e]) break;   /* first descent: run ends here */"),
     "forced run one short": ("uint64_t end = s + minrun < n ? s + minrun : n;",
                              "uint64_t end = s + minrun - 1 < n ? s + minrun - 1 : n;"),
+    "decreasing runs take equal keys": ("if (!(key[e - 1] > key[e])) break;",
+                                        "if (!(key[e - 1] >= key[e])) break;"),
+    "decreasing run starts on a tie": ("down = key[s] > key[e];", "down = key[s] >= key[e];"),
+    "reversal leaves the permutation": ("key[x] = key[y]; perm[x] = perm[y];", "key[x] = key[y];"),
+    "paged decreasing runs take equal keys": (
+        "const int desc = *vm_kslot(m, work, e - 1) > *vm_kslot(m, work, e);",
+        "const int desc = *vm_kslot(m, work, e - 1) >= *vm_kslot(m, work, e);"),
+    "paged reversal off by one": ("for (uint64_t x = 0, y = e - 1; x < y; ++x, --y) {",
+                                  "for (uint64_t x = 0, y = e - 2; x < y; ++x, --y) {"),
 }
 
 
@@ -69,6 +78,22 @@ def run_pins(lib):
         nodes = cartesian_nodes(r.run_starts, r.powers)
         assert got == nodes
         assert r.stats["merge_cost"] == sum(h - l for l, h in nodes.values())
+    # the decreasing-run variant (Sec. 5), both storages: a strictly
+    # decreasing array is one reversed run; results and runs by the rule
+    dec = np.arange(3000, 0, -1, dtype=np.uint32)
+    d = oracle.powersort(dec, lib=lib, descending_runs=True)
+    assert d.stats["runs"] == 1 and np.array_equal(d.perm, np.arange(2999, -1, -1))
+    for dist, n in [("updown", 20000), ("few", 3000), ("reversed", 1000)]:
+        keys = inputs.make(dist, n, n)
+        starts = runs_by_rule_descending(keys, oracle.minrun(n, lib=lib))
+        for vm in (False, True):
+            if vm:
+                r = oracle.powersort_vm(keys, 32, lib=lib, descending_runs=True)
+            else:
+                r = oracle.powersort(keys, lib=lib, descending_runs=True)
+            assert np.array_equal(r.perm, np.argsort(keys, kind="stable"))
+            assert np.array_equal(r.keys, keys[r.perm])
+            assert r.run_starts.tolist() == starts
 
 
 def test_shipped_oracle_passes_pins(oracle_mod):
