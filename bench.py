@@ -10,6 +10,11 @@ permutation is produced):
                uniform, Zipf(1.1) over 2^20 values, presorted Geometric(mean
                2^10) runs (seed 1)
   hbm_2^28     one step = one single-instance sort of n = 2^28 uniform (seed 2)
+  updown_2^24  one step = one sort of n = 2^24 Geometric(mean 2^10) segments,
+               each sorted ascending or descending by a coin (seed 1), with
+               the decreasing-run variant of Sec. 5 (PS_FLAG_DESCENDING_RUNS);
+               the line also carries the rate of the plain rule on the same
+               input
   serving      a Poisson stream of 2000 requests/s for 10 s (sizes log-uniform
                in [2^10, 2^24], seed 4) through the continuous-batching server
                under a 64 GB device-memory budget; reports sustained elements/s
@@ -50,9 +55,11 @@ UNIT = "elements/s"
 WORKLOADS = {
     "plain_2^24": [("uniform", 1 << 24, 1), ("zipf", 1 << 24, 1), ("runs", 1 << 24, 1)],
     "hbm_2^28": [("uniform", 1 << 28, 2)],
+    "updown_2^24": [("updown", 1 << 24, 1)],
     "batched_4096": None,
     "serving": None,
 }
+DESCENDING_WORKLOADS = {"updown_2^24"}   # sorted with the decreasing-run variant
 FLUSH_BYTES = 512 << 20
 BYTES_PER_MERGED_ELEM = 16   # key + perm entry read, key + perm entry written
 LAUNCHES_PER_BATCH = 13      # one batched Pingpong call: setup, 2 run detection, 7 planning, tiles, merges, finish
@@ -171,7 +178,7 @@ def traffic_from_profile(workload):
         return None
 
 
-def cpu_oracle_rate(data, budget_s):
+def cpu_oracle_rate(data, budget_s, descending_runs=False):
     """Single-threaded oracle throughput on a bounded sample (elements/s)."""
     import oracle
 
@@ -181,7 +188,7 @@ def cpu_oracle_rate(data, budget_s):
         if spent > budget_s and done:
             break
         t0 = time.perf_counter()
-        oracle.powersort(keys)
+        oracle.powersort(keys, descending_runs=descending_runs)
         dt = time.perf_counter() - t0
         spent += dt
         done += n
@@ -210,12 +217,13 @@ def run_reference(args):
     import oracle
 
     oracle.build()
+    desc = args.workload in DESCENDING_WORKLOADS
     times, elems = [], 0
     for i in range(args.warmup + args.steps):
         d, n, s, keys = data[i % len(data)]
         t0 = time.perf_counter()
         for k in (keys if isinstance(keys, list) else [keys]):
-            oracle.powersort(k)
+            oracle.powersort(k, descending_runs=desc)
         dt = time.perf_counter() - t0
         if i >= args.warmup:
             times.append(dt)
@@ -539,8 +547,10 @@ def main():
     perm = torch.empty(max_n, dtype=torch.int32, device=dev)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     mode = binding.PS_MODE_VM if args.storage == "vm" else binding.PS_MODE_PINGPONG
-    ctx = binding.Context(max_n, mode=mode, want_perm=True, flags=binding.PS_FLAG_TIMING, device=local,
-                          stream=stream)
+    desc = args.workload in DESCENDING_WORKLOADS
+    variant = binding.PS_FLAG_DESCENDING_RUNS if desc else 0
+    ctx = binding.Context(max_n, mode=mode, want_perm=True, flags=binding.PS_FLAG_TIMING | variant,
+                          device=local, stream=stream)
 
     def one_sort(i, timed):
         n = data[i][1]
@@ -600,11 +610,36 @@ def main():
     total_ms_max = replicas.max_over_ranks(total_ms, dist, dev)
     value = replicas.job_rate(elems, world, total_ms_max)
 
+    plain_rule = None
+    if desc:
+        # the same inputs and timing without the variant: the plain rule's rate
+        pctx = binding.Context(max_n, mode=mode, want_perm=True, device=local, stream=stream)
+        pms, pel = 0.0, 0
+        for step in range(args.warmup + args.steps):
+            for i in range(len(data)):
+                n = data[i][1]
+                work[:n].copy_(pristine[i])
+                flush.fill_(i)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                pctx.run(work[:n], perm[:n], stats=False)
+                e1.record(stream)
+                e1.synchronize()
+                if step >= args.warmup:
+                    pms += e0.elapsed_time(e1)
+                    pel += n
+        work[:data[0][1]].copy_(pristine[0])
+        pst = pctx.run(work[:data[0][1]], perm[:data[0][1]], stats=True)
+        pctx.close()
+        plain_rule = {"value": pel / (pms / 1000.0), "unit": UNIT, "runs": pst["runs"],
+                      "merge_cost": pst["merge_cost"], "note": "same input and timing, ascending runs only"}
+
     # end to end through ps_run_host with pinned host arrays
     e2e = None
     if not args.no_e2e:
-        hctx = binding.Context(max_n, mode=mode, want_perm=True, flags=binding.PS_FLAG_HOST_IO, device=local,
-                               stream=stream)
+        hctx = binding.Context(max_n, mode=mode, want_perm=True, flags=binding.PS_FLAG_HOST_IO | variant,
+                               device=local, stream=stream)
         hk = torch.empty(max_n, dtype=torch.int32, pin_memory=True)
         hp = torch.empty(max_n, dtype=torch.int32, pin_memory=True)
         src = [torch.from_numpy(k.view(np.int32)) for _, _, _, k in data]
@@ -636,7 +671,7 @@ def main():
     if rank == 0 and not args.no_cpu:
         sample = data if args.workload == "plain_2^24" else [(d, 1 << 24, s, k[: 1 << 24].copy())
                                                            for d, n, s, k in data]
-        rate, spent, used = cpu_oracle_rate(sample, args.cpu_sample_seconds)
+        rate, spent, used = cpu_oracle_rate(sample, args.cpu_sample_seconds, desc)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{used} ({spent:.1f} s of one host core)"}
 
@@ -653,6 +688,7 @@ def main():
             "instances": [f"{d} n=2^{int(np.log2(n))} seed {s}" for d, n, s, _ in data],
             "outputs": "sorted keys + stable permutation (uint32)",
             "storage": args.storage,
+            "runs": "ascending and strictly decreasing (Sec. 5 variant)" if desc else "ascending (Sec. 5 rule)",
             "scratch_bytes": hbm[0]["scratch_bytes"],
             "peak_pool_pages": hbm[0]["peak_pages"],
             "l2": "flushed before every timed sort (512 MiB write)",
@@ -678,6 +714,7 @@ def main():
                                                       "hbm_merge_elems", "max_power", "scratch_bytes",
                                                       "peak_pages")} for i in hbm},
         "round_timeline_us": rounds,
+        "plain_rule": plain_rule,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clk.summary(),

@@ -81,6 +81,13 @@ typedef struct ps_config {
 /* ps_config.flags */
 #define PS_FLAG_TIMING 1u  /* record CUDA events around every phase (ps_get_phase_times) */
 #define PS_FLAG_HOST_IO 2u /* allocate device arrays for ps_run_host (max_total keys + perm) */
+/* Run detection also takes strictly decreasing runs and reverses them in
+ * place (the variant Sec. 5 "Algorithm variants" names).  A run whose first
+ * two elements are strictly decreasing continues while the order stays
+ * strictly decreasing; equal neighbours end it, so the sort stays stable.
+ * The result is the same stable sort; the runs, powers and merge tree are
+ * those of the variant. */
+#define PS_FLAG_DESCENDING_RUNS 4u
 
 /* Per-call statistics (sums over instances for batched calls).  The paper's
  * merge cost M is the sum of the lengths of all merge inputs (Sec. 2

@@ -26,7 +26,7 @@ EXPORTS = (
     "ps_server_wait", "ps_server_get_stats", "ps_server_destroy",
 )
 PS_NOALLOC_MAX_N = 262144
-PS_FLAG_TIMING, PS_FLAG_HOST_IO = 1, 2
+PS_FLAG_TIMING, PS_FLAG_HOST_IO, PS_FLAG_DESCENDING_RUNS = 1, 2, 4
 PHASES = ("setup", "runs", "plan", "tiles", "merge_rounds", "finish")
 
 

@@ -322,6 +322,7 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
         st = dev_alloc(c, &c->io_keys, max_total);
         if (st == PS_OK && cfg->want_perm) st = dev_alloc(c, &c->io_perm, max_total);
     }
+    J.desc_runs = (cfg->flags & PS_FLAG_DESCENDING_RUNS) ? 1u : 0u;
     if (st == PS_OK && (cfg->flags & PS_FLAG_TIMING)) {
         c->timing = true;
         for (cudaEvent_t& e : c->ev)

@@ -143,6 +143,7 @@ struct Job {
     unsigned long long single_n;        // instance size when offsets == nullptr
     uint32_t count;
     uint32_t want_perm;
+    uint32_t desc_runs;         // nonzero: strictly decreasing runs are taken and reversed
     uint32_t tile_cap;          // T: largest merge-tree node merged on chip
     uint32_t merge_e;           // outputs per HBM merge chunk (set from the merge kernel's shape)
     unsigned long long max_n;   // limits the offsets table is checked against

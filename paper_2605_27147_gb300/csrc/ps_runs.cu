@@ -22,6 +22,15 @@
 // chunk is entered at state 0 whatever came before: its map is constant, and
 // it restarts the run count.
 //
+// Decreasing runs (the variant Sec. 5 "Algorithm variants" names, taken when
+// Job::desc_runs is set): a run whose first pair descends strictly ends at the
+// first non-descent instead (or at n), and is reversed later by the tile
+// kernel.  A run that spans the chunk start B is then either ascending (no
+// descent at B) or strictly decreasing (a descent at B), so the natural state
+// becomes X0 = the first position after B whose descent bit differs from B's;
+// when B's own bit decides (a run ends at B) the state is B + 0.  The entry
+// states stay at most minrun + 1.
+//
 // The maps are composed by a reduce-then-scan.  k_runs: every CTA owns a
 // contiguous range of chunks, computes their maps and folds them into one
 // 64-entry map for the range; the last CTA to finish walks the ranges' maps
@@ -219,6 +228,26 @@ __device__ __forceinline__ int next_desc(const uint32_t* bits, int k0, int kmax)
     return (w << 5) + __ffs(word) - 1;
 }
 
+// First clear bit at index >= k0 in bits[0, kmax), kmax a multiple of 32;
+// kmax when there is none.
+__device__ __forceinline__ int next_clear(const uint32_t* bits, int k0, int kmax)
+{
+    if (k0 >= kmax) return kmax;
+    int w = k0 >> 5;
+    uint32_t word = ~bits[w] & (FULL << (k0 & 31));
+    const int wmax = kmax >> 5;
+    while (word == 0) {
+        if (++w >= wmax) return kmax;
+        word = ~bits[w];
+    }
+    return (w << 5) + __ffs(word) - 1;
+}
+
+__device__ __forceinline__ bool desc_bit(const uint32_t* bits, int k)
+{
+    return ((bits[k >> 5] >> (k & 31)) & 1u) != 0;
+}
+
 constexpr int KMAX = RUN_WORDS * 32;
 constexpr int WIN = 32;                      // maps staged in shared memory per batch
 
@@ -328,24 +357,31 @@ __device__ __forceinline__ void bits_from_keys(const ChunkView& v, const KeyWind
     }
 }
 
-// Can any step from inside the chunk be natural?  Only if some descent e
-// (or position 0) inside the chunk is followed by minrun - 1 >= 31 positions
-// without a descent.  Each thread looks for a run of 31 clear bits starting
-// in its word (a 64-bit window over it and the next word); finding none
-// proves every chain forced all the way, with a closed form.  Finding one
-// only selects the exact chain walk.
-__device__ __forceinline__ bool chunk_may_natural(const ChunkView& v, const uint32_t* bits)
+// Bit p of the result: bits p .. p + 30 of x are all set.
+__device__ __forceinline__ unsigned long long ones31(unsigned long long x)
+{
+    unsigned long long r = x & (x >> 1);   // runs of 2
+    r &= r >> 2;                           // 4
+    r &= r >> 4;                           // 8
+    r &= r >> 8;                           // 16
+    return r & (r >> 15);                  // 31
+}
+
+// Can any step from inside the chunk be natural?  Only if a run start s in
+// the chunk is followed by minrun - 1 >= 31 positions without a descent (or,
+// with decreasing runs, 31 positions with one).  Each thread looks for 31
+// clear (or set) bits starting in its word (a 64-bit window over it and the
+// next word); finding none proves every chain forced all the way, with a
+// closed form.  Finding one only selects the exact chain walk.
+__device__ __forceinline__ bool chunk_may_natural(const ChunkView& v, const uint32_t* bits, bool desc)
 {
     const int tid = threadIdx.x;
     bool may = false;
     for (int w = tid; w < RUN_WORDS && w * 32 <= (int)v.span; w += RUN_BLOCK) {
         const unsigned long long hi = w + 1 < RUN_WORDS ? bits[w + 1] : 0u;
-        const unsigned long long z = ~((unsigned long long)bits[w] | (hi << 32));
-        unsigned long long r = z & (z >> 1);   // runs of 2 clear bits
-        r &= r >> 2;                           // 4
-        r &= r >> 4;                           // 8
-        r &= r >> 8;                           // 16
-        r &= r >> 15;                          // 31: bit p set <=> bits p .. p + 30 clear
+        const unsigned long long x = (unsigned long long)bits[w] | (hi << 32);
+        unsigned long long r = ones31(~x);     // bit p set <=> bits p .. p + 30 clear
+        if (desc) r |= ones31(x);              // ... or all set
         // run starts p = e + 1 with 1 <= p <= span (e = 0: the chunk's first position)
         uint32_t starts = (uint32_t)r;
         if (w == 0) starts &= ~1u;
@@ -356,31 +392,55 @@ __device__ __forceinline__ bool chunk_may_natural(const ChunkView& v, const uint
     return __syncthreads_or(may) != 0;
 }
 
+// Natural end (chunk offset) of the run that starts at offset k < span, or
+// KMAX when it lies past the halo.  An ascending run ends at the first descent
+// (the end n carries a descent bit).  With decreasing runs, a run whose first
+// pair descends ends at the first non-descent; n's bit is set, so the search
+// is capped at n instead.
+__device__ __forceinline__ int natural_end(const ChunkView& v, const uint32_t* bits, int k, bool desc)
+{
+    if (desc && (uint32_t)k + 1u < v.rem && desc_bit(bits, k + 1)) {
+        const int e = next_clear(bits, k + 2, KMAX);
+        return (uint32_t)e > v.rem ? (int)v.rem : e;
+    }
+    return next_desc(bits, k + 1, KMAX);
+}
+
+// Offset of entry state m: D0, the first descent at or after the chunk start;
+// with decreasing runs X0, the first offset > 0 whose descent bit differs from
+// offset 0's (capped at n).  KMAX (or beyond span) when outside the chunk.
+__device__ __forceinline__ int natural_state_offset(const ChunkView& v, const uint32_t* bits, bool desc)
+{
+    if (!desc) return next_desc(bits, 0, KMAX);
+    const int x = desc_bit(bits, 0) ? next_clear(bits, 1, KMAX) : next_desc(bits, 1, KMAX);
+    return (uint32_t)x > v.rem ? (int)v.rem : x;
+}
+
 // Exit state of a chain that stopped at chunk offset k (or ran past the halo).
 __device__ __forceinline__ uint32_t exit_state(const ChunkView& v, int k, bool symbolic)
 {
     // the last chunk's chains all end at n; elsewhere the exit is an entry state
     // of the next chunk (a position past the next chunk's first minrun positions
-    // can only be its D0, even when it is n)
+    // can only be its D0 -- X0 with decreasing runs -- even when it is n)
     if (v.E == v.n) return STATE_END;
     if (symbolic) return v.m;
     const uint32_t x = (uint32_t)k - v.span;
     return x < v.m ? x : v.m;
 }
 
-// Start offset of the chain entered in state s (s < m: offset s; s = m: the
-// first descent), or -1 when no run starts in the chunk from there.
-__device__ __forceinline__ int entry_offset(const ChunkView& v, const uint32_t* bits, uint32_t s)
+// Start offset of the chain entered in state s (s < m: offset s; s = m: D0,
+// or X0 with decreasing runs), or -1 when no run starts in the chunk from there.
+__device__ __forceinline__ int entry_offset(const ChunkView& v, const uint32_t* bits, uint32_t s, bool desc)
 {
     if (s < v.m) return (int)s;
-    const int d0 = next_desc(bits, 0, KMAX);
+    const int d0 = natural_state_offset(v, bits, desc);
     return (d0 >= KMAX || (uint32_t)d0 >= v.span) ? -1 : d0;
 }
 
 // Map entry of state s: (runs started in the chunk << 8) | exit state.
-__device__ uint32_t chain_map(const ChunkView& v, const uint32_t* bits, uint32_t s, bool walk)
+__device__ uint32_t chain_map(const ChunkView& v, const uint32_t* bits, uint32_t s, bool walk, bool desc)
 {
-    const int k0 = entry_offset(v, bits, s);
+    const int k0 = entry_offset(v, bits, s, desc);
     if (k0 < 0) return v.E == v.n ? STATE_END : v.m;
     if (!walk) {
         // forced steps only: starts k0, k0 + m, k0 + 2m, ... below span
@@ -393,8 +453,8 @@ __device__ uint32_t chain_map(const ChunkView& v, const uint32_t* bits, uint32_t
     bool symbolic = false;
     while ((uint32_t)k < v.span) {
         ++cnt;
-        const int d = next_desc(bits, k + 1, KMAX);
-        if (d >= KMAX) { symbolic = true; break; }   // f = d = next chunk's D0
+        const int d = natural_end(v, bits, k, desc);
+        if (d >= KMAX) { symbolic = true; break; }   // f = d = next chunk's D0 (X0)
         k = max(d, (int)min((uint32_t)k + v.m, v.rem));
     }
     return (cnt << 8) | exit_state(v, k, symbolic);
@@ -455,8 +515,9 @@ __global__ void __launch_bounds__(RUN_BLOCK) k_runs(Job J)
         __syncthreads();
         bits_from_keys(v, w, keys[buf], bits);
         __syncthreads();
-        const bool walk = chunk_may_natural(v, bits);
-        if (tid <= (int)v.m) mapv[tid] = chain_map(v, bits, (uint32_t)tid, walk);
+        const bool desc = J.desc_runs != 0;
+        const bool walk = chunk_may_natural(v, bits, desc);
+        if (tid <= (int)v.m) mapv[tid] = chain_map(v, bits, (uint32_t)tid, walk, desc);
         __syncthreads();
         // an instance's first chunk is entered at state 0 whatever came before:
         // its map is constant; states above m never occur and copy state m
@@ -464,7 +525,7 @@ __global__ void __launch_bounds__(RUN_BLOCK) k_runs(Job J)
         uint32_t f = 0;
         if (tid < MAP_STATES) f = first ? mapv[0] : mapv[min((uint32_t)tid, v.m)];
         if (tid == 0) {
-            const int d0 = next_desc(bits, 0, KMAX);
+            const int d0 = natural_state_offset(v, bits, desc);
             J.chunk_info[g] = (walk ? 0u : CHUNK_FORCED) | (first ? CHUNK_FIRST : 0u) | (uint32_t)min(d0, 0xffff);
             if (first) s_reset = RANGE_RESET;
         }
@@ -596,7 +657,7 @@ __global__ void __launch_bounds__(RUN_BLOCK) k_runs_emit(Job J)
             if (st > v.m || prefix + cnt + 1 > cap || cnt > (uint32_t)RUN_REC) {
                 if (lane == 0) set_error(C, DERR_INTERNAL, 13);
             } else if (info & CHUNK_FORCED) {
-                // forced steps only: starts k0, k0 + m, ... (k0: the entry offset or D0)
+                // forced steps only: starts k0, k0 + m, ... (k0: the entry offset or D0 / X0)
                 const uint32_t d0 = info & 0xffffu;
                 const uint32_t k0 = st < v.m ? st : d0;
                 for (uint32_t x = lane; x < cnt; x += 32) rs[x] = v.B + k0 + x * v.m;
@@ -607,11 +668,12 @@ __global__ void __launch_bounds__(RUN_BLOCK) k_runs_emit(Job J)
                 __syncwarp();
                 if (lane == 0) {
                     uint32_t c2 = 0;
-                    int k = entry_offset(v, bits[warp], st);
+                    const bool desc = J.desc_runs != 0;
+                    int k = entry_offset(v, bits[warp], st, desc);
                     if (k >= 0) {
                         while ((uint32_t)k < v.span && c2 < cnt) {
                             rs[c2++] = v.B + (uint32_t)k;
-                            const int d = next_desc(bits[warp], k + 1, KMAX);
+                            const int d = natural_end(v, bits[warp], k, desc);
                             if (d >= KMAX) break;
                             k = max(d, (int)min((uint32_t)k + v.m, v.rem));
                         }

@@ -15,8 +15,14 @@
 //
 // The finished tile goes to buffer depth & 1 (0 = caller's arrays, 1 = the
 // scratch arrays) with its stable permutation, ready for the HBM rounds.
-// A single run longer than T (always a natural, sorted run) is streamed:
-// keys copied when its buffer is the scratch one, perm written.
+// A single run longer than T (always a natural run) is streamed: keys copied
+// when its buffer is the scratch one, perm written.
+//
+// With decreasing runs on (Job::desc_runs), a natural run -- longer than
+// minrun, or a single streamed run -- whose first pair descends is strictly
+// decreasing and is reversed here, keys and positions together (its elements
+// are distinct, so the reversal is the stable order).  Runs of at most 64
+// elements need nothing extra: the forced-run sort orders them anyway.
 //
 // Whatever order its merges run in, a subtree's result is the stable sort of
 // its range: the elements ordered by (key, input position).  A tile made of
@@ -167,10 +173,32 @@ __global__ void __launch_bounds__(TILE_BLOCK) k_tiles(Job J)
         const uint32_t* ksrc = J.keysA + I.off + lo;
 
         if (size > (uint32_t)TILE_MAX) {
-            // only a single natural run (hence sorted) can exceed the tile size
-            for (uint32_t x = tid; x < size; x += TILE_BLOCK) {
-                if (to_scratch) kdst[x] = ksrc[x];
-                if (pdst) pdst[x] = lo + x;
+            // only a single natural run can exceed the tile size: sorted, or
+            // strictly decreasing (reversed pairwise: x and size-1-x by one
+            // thread, so in place is safe)
+            // every thread reads the first pair before any thread writes
+            const bool down = __syncthreads_or(J.desc_runs && ksrc[0] > ksrc[1]) != 0;
+            if (down) {
+                for (uint32_t x = tid; x < size - 1 - x; x += TILE_BLOCK) {
+                    const uint32_t y = size - 1 - x;
+                    const uint32_t a = ksrc[x], b = ksrc[y];
+                    kdst[x] = b;
+                    kdst[y] = a;
+                    if (pdst) {
+                        pdst[x] = lo + y;
+                        pdst[y] = lo + x;
+                    }
+                }
+                if ((size & 1u) && tid == 0) {
+                    const uint32_t x = size >> 1;
+                    kdst[x] = ksrc[x];
+                    if (pdst) pdst[x] = lo + x;
+                }
+            } else {
+                for (uint32_t x = tid; x < size; x += TILE_BLOCK) {
+                    if (to_scratch) kdst[x] = ksrc[x];
+                    if (pdst) pdst[x] = lo + x;
+                }
             }
             if (to_scratch && tid == 0) atomicAdd(&J.ctr->leaf_moves, (unsigned long long)size);
             __syncthreads();
@@ -214,7 +242,25 @@ __global__ void __launch_bounds__(TILE_BLOCK) k_tiles(Job J)
         // the result is the stable order an insertion sort gives
         for (uint32_t r = warp; r < nr; r += TILE_BLOCK / 32) {
             const uint32_t rlo = rs_s[r], len = rs_s[r + 1] - rlo;
-            if (len > 64 || len < 2) continue;
+            if (len > 64) {
+                // a natural run; reversed when strictly decreasing
+                // every lane reads the first pair before any lane writes
+                const bool down = J.desc_runs && sm.key[0][rlo] > sm.key[0][rlo + 1];
+                if (__any_sync(FULL, down)) {
+                    for (uint32_t x = lane; x < len - 1 - x; x += 32) {
+                        const uint32_t y = rlo + len - 1 - x;
+                        const uint32_t a = sm.key[0][rlo + x], b = sm.key[0][y];
+                        const uint16_t ia = sm.idx[0][rlo + x], ib = sm.idx[0][y];
+                        sm.key[0][rlo + x] = b;
+                        sm.key[0][y] = a;
+                        sm.idx[0][rlo + x] = ib;
+                        sm.idx[0][y] = ia;
+                    }
+                    __syncwarp();
+                }
+                continue;
+            }
+            if (len < 2) continue;
             const bool ok0 = lane < (int)len, ok1 = lane + 32 < (int)len;
             uint32_t k0 = ok0 ? sm.key[0][rlo + lane] : FULL;
             uint32_t k1 = ok1 ? sm.key[0][rlo + lane + 32] : FULL;
