@@ -283,7 +283,9 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
         // a wave: one output page for every page group of every CTA
         J.vm_wave_max = (uint32_t)c->grid_vm * ps::vm_groups_per_cta(plog2);
         J.vm_pool = cfg->pool_pages ? cfg->pool_pages : J.vm_wave_max + 64;
-        if (J.vm_pool < 8) J.vm_pool = 8;
+        if (J.vm_pool < 16) J.vm_pool = 16;
+        // the free-page ring: the pool's pages plus at most one push per page per round
+        J.vm_ring_cap = J.vm_pool + (uint32_t)ps::NPOW * J.vm_na_cap;
         const size_t P = (size_t)1 << plog2;
         if (st == PS_OK) st = dev_alloc(c, &J.pool_keys, (size_t)J.vm_pool * P);
         if (st == PS_OK && cfg->want_perm) st = dev_alloc(c, &J.pool_perm, (size_t)J.vm_pool * P);
@@ -293,7 +295,8 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
         if (st == PS_OK) st = dev_alloc(c, &J.page_nodes, 2ull * J.vm_na_cap);
         if (st == PS_OK) st = dev_alloc(c, &J.consumed, J.vm_na_cap);
         if (st == PS_OK) st = dev_alloc(c, &J.touched, J.vm_na_cap);
-        if (st == PS_OK) st = dev_alloc(c, &J.free_stack, (size_t)J.vm_na_cap + J.vm_pool);
+        if (st == PS_OK) st = dev_alloc(c, &J.free_stack, (size_t)J.vm_ring_cap);
+        if (st == PS_OK) st = dev_alloc(c, &J.vm_rec, (size_t)J.vm_na_cap * ps::VM_REC_WORDS);
         if (st == PS_OK) st = dev_alloc(c, &J.holder, (size_t)J.vm_na_cap + J.vm_pool);
         if (st == PS_OK) st = dev_alloc(c, &J.vm_split_at, (size_t)J.vm_na_cap + 1);
     } else {
@@ -337,7 +340,7 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
     if (st == PS_OK && ((!vm && !J.keysB) || !J.inst || !J.chunk_map || !J.chunk_info || !J.chunk_bits || !J.range_agg || !J.range_entry ||
                         !J.run_start || !J.kappa || !J.power || !J.na || !J.nb || !J.tiles || !J.gnodes ||
                         !J.gsorted || !J.dep || !J.chunk_node || !J.ctr ||
-                        (!vm && cfg->want_perm && !J.permB) || (vm && (!J.pool_keys || !J.pt || !J.vm_split_at))))
+                        (!vm && cfg->want_perm && !J.permB) || (vm && (!J.pool_keys || !J.pt || !J.vm_split_at || !J.vm_rec || !J.free_stack))))
         st = PS_EINTERNAL;
     if (st != PS_OK) {
         cudaGetLastError();

@@ -48,6 +48,7 @@ constexpr int TILE_MAX_LOG2 = 12;  // tile capacity bound of the shared-memory l
 constexpr int PLAN_BLOCK = 256;
 constexpr int NPOW = 33;           // powers are 1..32 for n < 2^32
 constexpr uint32_t NONE = 0xffffffffu;
+constexpr uint32_t VM_REC_WORDS = 16;   // page record: segment count + 3 x (s0, s1, lo, mid, hi)
 
 // device error codes (mirrors ps_status)
 constexpr uint32_t DERR_INVAL = 1;
@@ -110,10 +111,13 @@ struct Ctr {
     // virtual-memory storage
     uint32_t vm_free_top;              // entries on the free-page stack
     uint32_t vm_touched;               // pages written by the current round
-    uint32_t vm_wave;                  // pages in the current wave
+    uint32_t vm_wave;                  // final Copy: free pages handed out in the batch
     uint32_t vm_in_use_peak;           // most physical pages holding data at once
-    uint32_t vm_waves;                 // waves run by the call
+    uint32_t vm_waves;                 // VM rounds run by the call
     uint32_t vm_copy_moves;            // page copies made by the final Copy
+    uint32_t vm_ring_head;             // tickets handed out: the ring slot each output page pops
+    uint32_t vm_ring_tail;             // free pages pushed onto the ring so far
+    uint32_t vm_round_base;            // ring_head at the start of the current round
     uint32_t max_power;
     unsigned long long leaf_moves;
     unsigned long long M_total;
@@ -177,7 +181,8 @@ struct Job {
     uint32_t vm_na;             // virtual pages of the instance: ceil(n / P) (set per call)
     uint32_t vm_na_cap;         // capacity of the page tables
     uint32_t vm_pool;           // pool pages (physical pages vm_na_cap .. vm_na_cap + pool)
-    uint32_t vm_wave_max;       // output pages per wave
+    uint32_t vm_wave_max;       // output pages in flight at once (one per page group)
+    uint32_t vm_ring_cap;       // slots of the free-page ring (never wraps within a call)
     uint32_t* pool_keys;        // pool pages, P keys each
     uint32_t* pool_perm;
     uint32_t* pt;               // virtual page -> physical page
@@ -186,7 +191,8 @@ struct Job {
     uint32_t* page_nodes;       // 2 per page: those merges (GSorted index)
     uint32_t* consumed;         // elements of the page consumed by the current round
     uint32_t* touched;          // the round's written pages, in order
-    uint32_t* free_stack;       // free physical pages
+    uint32_t* free_stack;       // free physical pages: a FIFO ring in the rounds, a stack in Copy
+    uint32_t* vm_rec;           // per touched page: its merge segments and gaps (VM_REC_WORDS)
     uint32_t* holder;           // physical page -> virtual page it holds (final Copy)
     uint32_t* vm_split_at;      // per page start inside a merge of the round: its merge-path split
 };
@@ -313,6 +319,29 @@ __device__ __forceinline__ void fence_proxy_async_smem()
 __device__ __forceinline__ void fence_proxy_async_global()
 {
     asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// Asynchronous global -> shared copies (cp.async): no registers held while
+// they fly; commit groups, then wait for all but the newest N.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(smem)), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(smem)), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 // Upper bound of spin waits in cycles (about two seconds at 2 GHz); a wait

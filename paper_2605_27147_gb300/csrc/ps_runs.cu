@@ -184,17 +184,19 @@ __global__ void __launch_bounds__(1024) k_setup(Job J)
         __syncthreads();
     }
     if (J.vm) {
-        // virtual-memory storage: every virtual page starts as its own array page,
-        // the free stack holds the pool pages
+        // virtual-memory storage: every virtual page starts as its own array page;
+        // the free-page ring (filled by the rounds kernel) starts with the pool pages
         const uint32_t na = J.single_n ? (uint32_t)((J.single_n + (1ull << J.vm_plog2) - 1) >> J.vm_plog2) : 0u;
         for (uint32_t u = threadIdx.x; u < J.vm_na_cap; u += blockDim.x) {
             J.pt[u] = u;
             J.page_cnt[u] = 0;
             J.consumed[u] = 0;
         }
-        for (uint32_t i = threadIdx.x; i < J.vm_pool; i += blockDim.x) J.free_stack[i] = J.vm_na_cap + i;
         if (threadIdx.x == 0) {
-            C->vm_free_top = J.vm_pool;
+            C->vm_free_top = 0;
+            C->vm_ring_head = 0;
+            C->vm_ring_tail = J.vm_pool;
+            C->vm_round_base = 0;
             C->vm_touched = 0;
             C->vm_wave = 0;
             C->vm_in_use_peak = 0;
@@ -302,26 +304,6 @@ __device__ __forceinline__ KeyWindow window_of(const ChunkView& v)
     return w;
 }
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(smem)), "l"(gmem) : "memory");
-}
-
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(smem)), "l"(gmem) : "memory");
-}
-
-__device__ __forceinline__ void cp_async_commit()
-{
-    asm volatile("cp.async.commit_group;" ::: "memory");
-}
-
-template <int N>
-__device__ __forceinline__ void cp_async_wait()
-{
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
 
 // Start staging the window (one commit group per call).
 __device__ __forceinline__ void stage_keys(const ChunkView& v, const KeyWindow& w, uint32_t* keys)

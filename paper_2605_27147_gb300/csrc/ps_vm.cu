@@ -10,14 +10,15 @@
 // (elements of a touched page that no merge of the round covers are carried
 // over unchanged); an input page goes back to the stack once all of its
 // elements have been consumed (the paper's PopFront freeing an emptied page).
-// Rounds run in waves of at most vm_wave_max output pages, in page order, each
-// wave taking its pages from the stack: a merge consumes exactly as many
-// input elements as it writes, so the pages freed by one wave cover the next
-// one, and the pool needs only about one wave of pages plus a few partly
-// consumed pages -- not n elements.  Every merge-path split a page needs (at
-// page boundaries inside a merge) is searched at the start of the round, all
-// pages in parallel, while every input page still holds its data; the waves
-// then only stream.  Finally Copy (Sec. 4) moves every virtual page to its own
+// Inside a round the output pages form a dataflow in page order: each takes
+// the next free page from a FIFO ring and pushes the input pages it was the
+// last to consume: a merge consumes exactly as many input elements as it
+// writes, so the freed pages keep pace with the taken ones, and the pool needs
+// about one page per page group in flight plus a few partly consumed pages --
+// not n elements.  Every merge-path split a page needs (at page boundaries
+// inside a merge) is searched at the start of the round, all pages in
+// parallel, while every input page still holds its data; the pages then only
+// stream.  Finally Copy (Sec. 4) moves every virtual page to its own
 // array page: a page still holding data that is needed later is first moved
 // to a free page, exactly as the paper describes.
 #include <algorithm>
@@ -141,77 +142,74 @@ __device__ uint32_t vm_split(const Job& J, const GSorted& g, uint32_t d)
     return l;
 }
 
-// Count `cnt` consumed elements of virtual range [v0, v0 + cnt); a page whose
-// every element is consumed goes back to the free stack.
-__device__ void consume(const Job& J, uint32_t v0, uint32_t cnt, uint32_t n)
+// Push a free physical page onto the ring.
+__device__ __forceinline__ void ring_push(const Job& J, uint32_t page)
 {
-    const uint32_t L = J.vm_plog2;
-    while (cnt) {
-        const uint32_t u = v0 >> L;
-        const uint32_t take = min(cnt, ((u + 1) << L) - v0);
-        const uint32_t before = atomicAdd(&J.consumed[u], take);
-        if (before + take == page_size(J, u, n)) {
-            // the caller's last array page may be partial: like the paper's partial
-            // input page it is never declared free (it could not hold a full page)
-            const uint32_t old = J.pt[u];
-            const bool partial_tail = old + 1 == J.vm_na && (n & ((1u << J.vm_plog2) - 1)) != 0;
-            if (!partial_tail) {
-                const uint32_t at = atomicAdd(&J.ctr->vm_free_top, 1u);
-                J.free_stack[at] = old;
-            }
-        }
-        v0 += take;
-        cnt -= take;
+    const uint32_t at = atomicAdd(&J.ctr->vm_ring_tail, 1u);
+    if (at < J.vm_ring_cap) st_release_u32(&J.free_stack[at], page);
+    else set_error(J.ctr, DERR_INTERNAL, 66);
+}
+
+// Count `take` consumed elements of virtual page u; the page goes back to the
+// free ring once every element is consumed.
+__device__ void consume_page(const Job& J, uint32_t u, uint32_t take, uint32_t n)
+{
+    const uint32_t before = atomicAdd(&J.consumed[u], take);
+    if (before + take == page_size(J, u, n)) {
+        // the caller's last array page may be partial: like the paper's partial
+        // input page it is never declared free (it could not hold a full page)
+        const uint32_t old = J.pt[u];
+        const bool partial_tail = old + 1 == J.vm_na && (n & ((1u << J.vm_plog2) - 1)) != 0;
+        if (!partial_tail) ring_push(J, old);
     }
+}
+
+// Thread q < 4 of a group counts its share of the consumed virtual ranges
+// [v0, v0 + c0) and [v1, v1 + c1), each at most one page long (two pages touched).
+__device__ __forceinline__ void consume_ranges(const Job& J, uint32_t q, uint32_t v0, uint32_t c0, uint32_t v1,
+                                               uint32_t c1, uint32_t n)
+{
+    if (q >= 4) return;
+    const uint32_t L = J.vm_plog2;
+    const uint32_t v = q < 2 ? v0 : v1, c = q < 2 ? c0 : c1;
+    if (!c) return;
+    const uint32_t first = min(c, (((v >> L) + 1) << L) - v);   // elements in v's page
+    if ((q & 1u) == 0) consume_page(J, v >> L, first, n);
+    else if (c > first) consume_page(J, (v >> L) + 1, c - first, n);
 }
 
 struct VmSmem {
     uint32_t k[VM_SLOTS];
     uint32_t p[VM_SLOTS];
-    uint32_t seg_lo[VM_WARPS][6], seg_hi[VM_WARPS][6], seg_node[VM_WARPS][6];
-    uint32_t nseg[VM_WARPS];
-    uint32_t a[VM_WARPS][2];
+    uint16_t src[VM_SLOTS];                     // the merge's choice per output: slot in k / p
+    uint32_t rec[VM_WARPS][VM_REC_WORDS + 2];   // the page's record, then the splits at its two ends
+    uint32_t ph[VM_WARPS][4];                   // physical pages of the input slices (two each)
+    uint32_t claim[VM_WARPS][2];                // (virtual page, output page) of the group's current page
 };
 
-// One output page of the current wave, by one group: its merge segments and
-// copy gaps.
-__device__ void vm_page(const Job& J, VmSmem& sm, const VmGroup& G, uint32_t u, uint32_t n, bool perm)
+// One output page by one group: its merge segments and copy gaps, from the
+// record the round's step 2 wrote, into the fresh physical page `out`.
+__device__ void vm_page(const Job& J, VmSmem& sm, const VmGroup& G, uint32_t u, uint32_t out, uint32_t n,
+                        bool perm)
 {
     const uint32_t tid = G.tid, gi = G.g;
     uint32_t* sk = sm.k + gi * (G.cap + 8);
     uint32_t* sp = sm.p + gi * (G.cap + 8);
+    uint32_t* rec = sm.rec[gi];
     const uint32_t L = J.vm_plog2;
-    const uint32_t ps0 = u << L, pe = min(ps0 + (1u << L), n);
-    uint32_t* dk = phys_k(J, J.pt_new[u]);
-    uint32_t* dp = perm ? phys_p(J, J.pt_new[u]) : nullptr;
-    if (tid == 0) {
-        // up to two merges touch the page; order them, fill the gaps with copies
-        uint32_t e[2] = {NONE, NONE};
-        const uint32_t c = min(J.page_cnt[u], 2u);
-        for (uint32_t i = 0; i < c; ++i) e[i] = J.page_nodes[2 * u + i];
-        if (c == 2 && J.gsorted[e[0]].goff > J.gsorted[e[1]].goff) {
-            const uint32_t t = e[0];
-            e[0] = e[1];
-            e[1] = t;
-        }
-        uint32_t cur = ps0, ns = 0;
-        for (uint32_t i = 0; i < c; ++i) {
-            const GSorted g = J.gsorted[e[i]];
-            const uint32_t lo = (uint32_t)g.goff, hi = lo + g.la + g.lb;
-            const uint32_t s0 = max(lo, ps0), s1 = min(hi, pe);
-            if (s0 >= s1) continue;
-            if (s0 > cur) { sm.seg_lo[gi][ns] = cur; sm.seg_hi[gi][ns] = s0; sm.seg_node[gi][ns] = NONE; ++ns; }
-            sm.seg_lo[gi][ns] = s0; sm.seg_hi[gi][ns] = s1; sm.seg_node[gi][ns] = e[i]; ++ns;
-            cur = s1;
-        }
-        if (cur < pe) { sm.seg_lo[gi][ns] = cur; sm.seg_hi[gi][ns] = pe; sm.seg_node[gi][ns] = NONE; ++ns; }
-        sm.nseg[gi] = ns;
-    }
+    const uint32_t ps0 = u << L;
+    uint32_t* dk = phys_k(J, out);
+    uint32_t* dp = perm ? phys_p(J, out) : nullptr;
+    // the record and the splits at the page's two ends, in one round trip
+    if (tid < VM_REC_WORDS) rec[tid] = J.vm_rec[(size_t)u * VM_REC_WORDS + tid];
+    else if (tid == VM_REC_WORDS) rec[tid] = J.vm_split_at[u];
+    else if (tid == VM_REC_WORDS + 1) rec[tid] = u + 1 < J.vm_na ? J.vm_split_at[u + 1] : 0u;
     group_sync(G);
-    const uint32_t nseg = sm.nseg[gi];
+    const uint32_t nseg = min(rec[0], 3u);
     for (uint32_t sg = 0; sg < nseg; ++sg) {
-        const uint32_t s0 = sm.seg_lo[gi][sg], s1 = sm.seg_hi[gi][sg], e = sm.seg_node[gi][sg];
-        if (e == NONE) {                         // carried over unchanged (a gap)
+        const uint32_t* R = rec + 1 + 5 * sg;
+        const uint32_t s0 = R[0], s1 = R[1], lo = R[2];
+        if (lo == NONE) {                        // carried over unchanged (a gap)
 #pragma unroll 8
             for (uint32_t v = s0 + tid; v < s1; v += G.nthr) {
                 const uint32_t ph = J.pt[v >> L], off = v & ((1u << L) - 1u);
@@ -219,75 +217,103 @@ __device__ void vm_page(const Job& J, VmSmem& sm, const VmGroup& G, uint32_t u, 
                 if (dp) dp[v - ps0] = phys_p(J, ph)[off];
             }
             group_sync(G);
-            if (tid == 0) consume(J, s0, s1 - s0, n);
+            consume_ranges(J, tid, s0, s1 - s0, 0u, 0u, n);
             continue;
         }
-        const GSorted g = J.gsorted[e];
-        const uint32_t lo = (uint32_t)g.goff, mid = lo + g.la;
-        for (uint32_t x0 = s0; x0 < s1; x0 += G.cap) {
-            const uint32_t x1 = min(x0 + G.cap, s1);
-            const uint32_t d0 = x0 - lo, d1 = x1 - lo;
-            if (tid < 2) {
-                // the splits at the merge's ends are 0 and la; at a page start
-                // inside the merge the round's search left it in vm_split_at
-                // (a sub-chunk always holds a whole page, so no other boundary
-                // occurs)
-                const uint32_t x = tid == 0 ? x0 : x1, d = x - lo;
-                uint32_t a;
-                if (d == 0) a = 0;
-                else if (d == g.la + g.lb) a = g.la;
-                else if ((x & ((1u << L) - 1u)) == 0) a = J.vm_split_at[x >> L];
-                else { a = 0; set_error(J.ctr, DERR_INTERNAL, 65); }   // a sub-chunk holds a whole page
-                sm.a[gi][tid] = a;
+        const uint32_t mid = R[3], hi = R[4], la = mid - lo;
+        // the splits: 0 / la at the merge's ends; at a page end inside the
+        // merge the round's search left them in vm_split_at
+        const uint32_t a0 = s0 == lo ? 0u : rec[VM_REC_WORDS];
+        const uint32_t a1 = s1 == hi ? la : rec[VM_REC_WORDS + 1];
+        const uint32_t b0 = (s0 - lo) - a0, b1 = (s1 - lo) - a1;
+        const uint32_t na = a1 - a0, nb = b1 - b0, cnt = na + nb;
+        if (cnt > G.cap) {   // a segment never exceeds a page, and a page fits a group
+            if (tid == 0) set_error(J.ctr, DERR_INTERNAL, 65);
+            return;
+        }
+        // the slices' keys (and permutation): each slice is at most a page, so
+        // it spans at most two physical pages; their ids first, then every
+        // element by an asynchronous copy (all in flight at once)
+        const uint32_t va = lo + a0, vb = mid + b0;
+        if (tid < 4) {
+            const uint32_t v = tid < 2 ? va : vb, c = tid < 2 ? na : nb;
+            const uint32_t vp = (v >> L) + (tid & 1u);
+            const bool used = c && ((tid & 1u) == 0 || ((v + c - 1) >> L) != (v >> L));
+            sm.ph[gi][tid] = used ? J.pt[vp] : 0u;
+        }
+        group_sync(G);
+        for (uint32_t i = tid; i < cnt; i += G.nthr) {
+            const bool left = i < na;
+            const uint32_t v = left ? va + i : vb + (i - na);
+            const uint32_t ph = sm.ph[gi][(left ? 0u : 2u) + ((v >> L) != ((left ? va : vb) >> L))];
+            const uint32_t off = v & ((1u << L) - 1u);
+            cp_async4(&sk[i], phys_k(J, ph) + off);
+            if (perm) cp_async4(&sp[i], phys_p(J, ph) + off);
+        }
+        cp_async_commit();
+        cp_async_wait<0>();
+        group_sync(G);
+        // every input element is read: the consumed counts can go out while
+        // the merge runs (a freed page is not read again this round)
+        consume_ranges(J, tid, lo + a0, na, mid + b0, nb, n);
+        // each thread merges VM_K consecutive outputs, recording for each the
+        // staging slot it comes from; then the group writes the page out in
+        // order, consecutive threads on consecutive words
+        uint16_t* ssrc = sm.src + gi * (G.cap + 8);
+        const uint32_t t0 = tid * VM_K;
+        if (t0 < cnt) {
+            uint32_t l = t0 > nb ? t0 - nb : 0u, h = min(t0, na);
+            while (l < h) {
+                const uint32_t m = (l + h) >> 1;
+                if (sk[m] <= sk[na + t0 - 1 - m]) l = m + 1; else h = m;
             }
-            group_sync(G);
-            const uint32_t a0 = sm.a[gi][0], a1 = sm.a[gi][1], b0 = d0 - a0, b1 = d1 - a1;
-            const uint32_t na = a1 - a0, nb = b1 - b0, cnt = na + nb;
-            // the slices' keys (and permutation) through the page table; eight
-            // iterations per thread in flight at once
-#pragma unroll 8
-            for (uint32_t i = tid; i < cnt; i += G.nthr) {
-                const uint32_t v = i < na ? lo + a0 + i : mid + b0 + (i - na);
-                const uint32_t ph = J.pt[v >> L], off = v & ((1u << L) - 1u);
-                sk[i] = phys_k(J, ph)[off];
-                if (perm) sp[i] = phys_p(J, ph)[off];
-            }
-            group_sync(G);
-            // each thread merges VM_K consecutive outputs straight into the
-            // fresh output page (a pool page nobody else reads this wave)
-            const uint32_t t0 = tid * VM_K;
-            if (t0 < cnt) {
-                uint32_t l = t0 > nb ? t0 - nb : 0u, h = min(t0, na);
-                while (l < h) {
-                    const uint32_t m = (l + h) >> 1;
-                    if (sk[m] <= sk[na + t0 - 1 - m]) l = m + 1; else h = m;
-                }
-                uint32_t ia = l, ib = na + (t0 - l);
-                uint32_t* ok = dk + (x0 - ps0) + t0;
-                uint32_t* op = dp ? dp + (x0 - ps0) + t0 : nullptr;
+            uint32_t ia = l, ib = na + (t0 - l);
 #pragma unroll 4
-                for (int j = 0; j < VM_K; ++j) {
-                    if (t0 + j < cnt) {
-                        const bool ta = ia < na && (ib >= cnt || sk[ia] <= sk[ib]);
-                        const uint32_t src = ta ? ia : ib;
-                        ok[j] = sk[src];
-                        if (op) op[j] = sp[src];
-                        ia += ta;
-                        ib += !ta;
-                    }
+            for (int j = 0; j < VM_K; ++j) {
+                if (t0 + j < cnt) {
+                    const bool ta = ia < na && (ib >= cnt || sk[ia] <= sk[ib]);
+                    ssrc[t0 + j] = (uint16_t)(ta ? ia : ib);
+                    ia += ta;
+                    ib += !ta;
                 }
-            }
-            group_sync(G);
-            if (tid == 0) {
-                consume(J, lo + a0, na, n);
-                consume(J, mid + b0, nb, n);
             }
         }
+        group_sync(G);
+        uint32_t* ok = dk + (s0 - ps0);
+        uint32_t* op = dp ? dp + (s0 - ps0) : nullptr;
+#pragma unroll 4
+        for (uint32_t i = tid; i < cnt; i += G.nthr) {
+            const uint32_t from = ssrc[i];
+            ok[i] = sk[from];
+            if (op) op[i] = sp[from];
+        }
+        group_sync(G);
     }
 }
 
 }  // namespace
 
+// The HBM merge rounds with virtual-memory storage.  Per round:
+//   1. every merge marks the pages it touches (a warp per merge);
+//   2. one thread per touched page writes the page's record (its merge
+//      segments and gaps, in order) and, for a page start inside a merge, the
+//      merge-path split there -- all before any page of the round is recycled;
+//   3. CTA 0 lists the touched pages in page order;
+//   4. the pages, as a dataflow: every page group takes tickets from one
+//      counter (the next one while it merges the current page); ticket t
+//      names the touched page t - base and the ring slot t its output page is
+//      popped from.  Pages therefore take free pages in
+//      page order, and a group holding a page never waits: it reads its
+//      inputs, merges into the fresh page and pushes every input page it
+//      consumed last.  When every group waits for a free page, all pages
+//      before the first waiting ticket are done: every segment left of it has
+//      returned all its input pages, and the merge in progress has taken at
+//      most five pages more than it returned (two partly consumed pages per
+//      run and the page it shares with its left neighbour), so a pool of 16
+//      pages always has one to give (a bounded wait records PS_ETIMEOUT
+//      should that ever fail);
+//   5. the written pages become current.
+// Grid barriers separate the steps; there are none between pages.
 __global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_rounds(Job J)
 {
     __shared__ VmSmem sm;
@@ -299,6 +325,12 @@ __global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_rounds(Job J)
     const uint32_t L = J.vm_plog2, NA = J.vm_na;
     const uint32_t nwarps_grid = gridDim.x * (VM_BLOCK / 32);
     const uint32_t gwarp = blockIdx.x * (VM_BLOCK / 32) + warp;
+    const uint32_t gtid = blockIdx.x * VM_BLOCK + tid, gstride = gridDim.x * VM_BLOCK;
+
+    // the ring: the pool's pages, then empty slots
+    for (uint32_t i = gtid; i < J.vm_ring_cap; i += gstride)
+        J.free_stack[i] = i < J.vm_pool ? J.vm_na_cap + i : NONE;
+    if (!vm_barrier(C)) return;
 
     for (int r = 0; r < NPOW; ++r) {
         if (*(volatile uint32_t*)&C->error) return;
@@ -321,18 +353,50 @@ __global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_rounds(Job J)
             }
         }
         if (!vm_barrier(C)) return;
-        // 1b. the merge-path split at every page start that lies inside a merge,
-        //     one thread per page, before any input page can be recycled
-        for (uint32_t u = blockIdx.x * VM_BLOCK + tid; u < NA; u += gridDim.x * VM_BLOCK) {
-            const uint32_t c = min(J.page_cnt[u], 2u), ps0 = u << L;
-            for (uint32_t i = 0; i < c; ++i) {
-                const GSorted g = J.gsorted[J.page_nodes[2 * u + i]];
-                const uint32_t lo = (uint32_t)g.goff;
-                if (lo < ps0 && ps0 < lo + g.la + g.lb) J.vm_split_at[u] = vm_split(J, g, ps0 - lo);
+        // 2. per touched page (a thread each): its record -- up to two merges,
+        //    ordered, with the gaps between them filled by copies -- and the
+        //    merge-path split at its start when that lies inside a merge,
+        //    searched while every input page still holds its data
+        for (uint32_t u = gtid; u < NA; u += gstride) {
+            const uint32_t c = min(J.page_cnt[u], 2u);
+            if (c == 0) continue;
+            const uint32_t ps0 = u << L, pe = min(ps0 + (1u << L), n);
+            GSorted g[2];
+            g[0] = J.gsorted[J.page_nodes[2 * u]];
+            if (c == 2) {
+                g[1] = J.gsorted[J.page_nodes[2 * u + 1]];
+                if (g[0].goff > g[1].goff) {
+                    const GSorted t = g[0];
+                    g[0] = g[1];
+                    g[1] = t;
+                }
             }
+            uint32_t w[VM_REC_WORDS];
+            uint32_t ns = 0, cur = ps0;
+            for (uint32_t i = 0; i < c; ++i) {
+                const uint32_t lo = (uint32_t)g[i].goff, mid = lo + g[i].la, hi = mid + g[i].lb;
+                const uint32_t s0 = max(lo, ps0), s1 = min(hi, pe);
+                if (s0 >= s1) continue;
+                if (s0 > cur) {
+                    w[1 + 5 * ns] = cur; w[2 + 5 * ns] = s0; w[3 + 5 * ns] = NONE; w[4 + 5 * ns] = 0; w[5 + 5 * ns] = 0;
+                    ++ns;
+                }
+                w[1 + 5 * ns] = s0; w[2 + 5 * ns] = s1; w[3 + 5 * ns] = lo; w[4 + 5 * ns] = mid; w[5 + 5 * ns] = hi;
+                ++ns;
+                cur = s1;
+                if (lo < ps0 && ps0 < hi) J.vm_split_at[u] = vm_split(J, g[i], ps0 - lo);
+            }
+            if (cur < pe) {
+                w[1 + 5 * ns] = cur; w[2 + 5 * ns] = pe; w[3 + 5 * ns] = NONE; w[4 + 5 * ns] = 0; w[5 + 5 * ns] = 0;
+                ++ns;
+            }
+            w[0] = ns;
+            for (uint32_t i = 1 + 5 * ns; i < VM_REC_WORDS; ++i) w[i] = 0;
+            uint4* dst = reinterpret_cast<uint4*>(J.vm_rec + (size_t)u * VM_REC_WORDS);
+#pragma unroll
+            for (int q = 0; q < (int)VM_REC_WORDS / 4; ++q) dst[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
         }
-        if (!vm_barrier(C)) return;
-        // 2. the touched pages, in page order (CTA 0; each thread takes
+        // 3. the touched pages, in page order (CTA 0; each thread takes
         //    TOUCH_PER consecutive pages per pass)
         if (blockIdx.x == 0) {
             constexpr uint32_t TOUCH_PER = 8;
@@ -362,46 +426,76 @@ __global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_rounds(Job J)
                 carry += tot;
                 __syncthreads();
             }
-            if (tid == 0) C->vm_touched = carry;
+            if (tid == 0) {
+                C->vm_touched = carry;
+                C->vm_round_base = C->vm_ring_head;
+                C->vm_waves += 1;
+            }
         }
         if (!vm_barrier(C)) return;
-        // 3. waves of output pages
-        const uint32_t ntouched = C->vm_touched;
-        for (uint32_t pos = 0; pos < ntouched;) {
-            if (blockIdx.x == 0) {
-                // the wave's output pages come off the top of the free stack
-                __shared__ uint32_t s_top, s_k;
-                if (tid == 0) {
-                    const uint32_t top = C->vm_free_top;
-                    const uint32_t k = min(min(J.vm_wave_max, top), ntouched - pos);
-                    if (k == 0) set_error(C, DERR_INTERNAL, 62);      // no free page: cannot progress
-                    C->vm_free_top = top - k;
-                    C->vm_wave = k;
-                    C->vm_waves += 1;
-                    const uint32_t extra = J.vm_pool > top - k ? J.vm_pool - (top - k) : 0u;   // pages beyond n/P
-                    if (extra > C->vm_in_use_peak) C->vm_in_use_peak = extra;
-                    s_top = top;
-                    s_k = k;
-                }
-                __syncthreads();
-                for (uint32_t j = tid; j < s_k; j += VM_BLOCK) J.pt_new[J.touched[pos + j]] = J.free_stack[s_top - 1 - j];
-            }
-            if (!vm_barrier(C)) return;
-            if (*(volatile uint32_t*)&C->error) return;
-            const uint32_t k = C->vm_wave;
+        // 4. the pages, as a dataflow over tickets
+        {
+            const uint32_t ntouched = C->vm_touched, base = C->vm_round_base;
             const VmGroup G = vm_group(L);
-            for (uint32_t j = blockIdx.x * G.groups + G.g; j < k; j += gridDim.x * G.groups)
-                vm_page(J, sm, G, J.touched[pos + j], n, perm);
-            if (!vm_barrier(C)) return;
-            pos += k;
+            // the group's next ticket is drawn while its current page is merged
+            uint32_t t_next = G.tid == 0 ? atomicAdd(&C->vm_ring_head, 1u) : 0u;
+            for (;;) {
+                if (G.tid == 0) {
+                    uint32_t u = NONE, out = NONE;
+                    const uint32_t t = t_next;
+                    if (t - base < ntouched && !*(volatile uint32_t*)&C->error) {
+                        u = J.touched[t - base];
+                        if (t >= J.vm_ring_cap) {
+                            set_error(C, DERR_INTERNAL, 67);
+                        } else {
+                            // pop slot t: wait (bounded) until a free page is pushed there
+                            const long long c0 = clock64();
+                            uint32_t nap = 32;
+                            for (;;) {
+                                const uint32_t v = ld_acquire_u32(&J.free_stack[t]);
+                                if (v != NONE) {
+                                    out = v;
+                                    break;
+                                }
+                                if (*(volatile uint32_t*)&C->error) break;
+                                if (clock64() - c0 > SPIN_LIMIT_CYCLES) {
+                                    set_error(C, DERR_TIMEOUT, 68);
+                                    break;
+                                }
+                                __nanosleep(nap);
+                                nap = nap < 512 ? nap * 2 : 512;
+                            }
+                            if (out != NONE) {
+                                J.pt_new[u] = out;
+                                // pages beyond the array's n / P in use after this pop
+                                const uint32_t tail = ld_relaxed_u32(&C->vm_ring_tail);
+                                const uint32_t free_after = tail > t + 1 ? tail - (t + 1) : 0u;
+                                if (J.vm_pool > free_after) atomicMax(&C->vm_in_use_peak, J.vm_pool - free_after);
+                            }
+                        }
+                    }
+                    sm.claim[G.g][0] = u;
+                    sm.claim[G.g][1] = out;
+                    if (out != NONE) t_next = atomicAdd(&C->vm_ring_head, 1u);
+                }
+                group_sync(G);
+                const uint32_t u = sm.claim[G.g][0], out = sm.claim[G.g][1];
+                group_sync(G);
+                if (u == NONE || out == NONE) break;
+                vm_page(J, sm, G, u, out, n, perm);
+            }
         }
-        // 4. the written pages become current; reset the per-round tables
-        for (uint32_t j = blockIdx.x * VM_BLOCK + tid; j < ntouched; j += gridDim.x * VM_BLOCK) {
+        if (!vm_barrier(C)) return;
+        // 5. the written pages become current; reset the per-round tables; the
+        //    over-drawn tickets are returned
+        const uint32_t ntouched = C->vm_touched;
+        for (uint32_t j = gtid; j < ntouched; j += gstride) {
             const uint32_t u = J.touched[j];
             J.pt[u] = J.pt_new[u];
             J.page_cnt[u] = 0;
             J.consumed[u] = 0;
         }
+        if (gtid == 0) C->vm_ring_head = C->vm_round_base + ntouched;
         if (!vm_barrier(C)) return;
     }
 }
