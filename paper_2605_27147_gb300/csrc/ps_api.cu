@@ -298,7 +298,7 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
         if (st == PS_OK) st = dev_alloc(c, &J.free_stack, (size_t)J.vm_ring_cap);
         if (st == PS_OK) st = dev_alloc(c, &J.vm_rec, (size_t)J.vm_na_cap * ps::VM_REC_WORDS);
         if (st == PS_OK) st = dev_alloc(c, &J.holder, (size_t)J.vm_na_cap + J.vm_pool);
-        if (st == PS_OK) st = dev_alloc(c, &J.vm_split_at, (size_t)J.vm_na_cap + 1);
+        if (st == PS_OK) st = dev_alloc(c, &J.vm_split_at, ((size_t)J.vm_na_cap + 1) * ps::VM_SPLIT_WORDS);
     } else {
         if (st == PS_OK) st = dev_alloc(c, &J.keysB, max_total);
         if (st == PS_OK && cfg->want_perm) st = dev_alloc(c, &J.permB, max_total);

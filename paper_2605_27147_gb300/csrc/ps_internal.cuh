@@ -48,7 +48,14 @@ constexpr int TILE_MAX_LOG2 = 12;  // tile capacity bound of the shared-memory l
 constexpr int PLAN_BLOCK = 256;
 constexpr int NPOW = 33;           // powers are 1..32 for n < 2^32
 constexpr uint32_t NONE = 0xffffffffu;
-constexpr uint32_t VM_REC_WORDS = 16;   // page record: segment count + 3 x (s0, s1, lo, mid, hi)
+// VM page record: segment count, then up to 3 segments of (s0, s1, lo, mid,
+// hi, four physical pages: the left slice's first page and the next, the
+// right slice's first page and the next); a gap has lo = NONE and its page first
+constexpr uint32_t VM_REC_WORDS = 32;
+constexpr uint32_t VM_SEG_WORDS = 9;
+// per page start inside a merge: the split, then the four physical pages of
+// the slices that start there
+constexpr uint32_t VM_SPLIT_WORDS = 8;
 
 // device error codes (mirrors ps_status)
 constexpr uint32_t DERR_INVAL = 1;
@@ -195,6 +202,7 @@ struct Job {
     uint32_t* vm_rec;           // per touched page: its merge segments and gaps (VM_REC_WORDS)
     uint32_t* holder;           // physical page -> virtual page it holds (final Copy)
     uint32_t* vm_split_at;      // per page start inside a merge of the round: its merge-path split
+                                // and the slices' pages (VM_SPLIT_WORDS)
 };
 
 // ---------------------------------------------------------------- helpers

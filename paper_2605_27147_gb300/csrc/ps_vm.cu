@@ -142,6 +142,38 @@ __device__ uint32_t vm_split(const Job& J, const GSorted& g, uint32_t d)
     return l;
 }
 
+// The same split by a team of eight lanes (lane & ~7 .. lane | 7, converged):
+// an 8-ary search, seven probes per step.  The predicate L[m] <= R[d-1-m] is
+// true below the split and false from it on, so the trues among increasing
+// probes form a prefix.
+__device__ uint32_t vm_split_team(const Job& J, const GSorted& g, uint32_t d, uint32_t lane)
+{
+    const uint32_t tl = lane & 7u, shift = lane & 24u;
+    const uint32_t tmask = 0xffu << shift;
+    const uint32_t lo = (uint32_t)g.goff, mid = lo + g.la;
+    uint32_t l = d > g.lb ? d - g.lb : 0u;
+    uint32_t h = min(d, g.la);
+    while (l < h) {
+        const uint32_t span = h - l;
+        // probes: l + 1 .. l + span when span <= 7, else seven evenly spaced
+        const uint32_t k = span <= 7u ? span : 7u;
+        const uint32_t m = span <= 7u ? l + tl : l + (uint32_t)(((unsigned long long)(tl + 1) * span) >> 3);
+        bool t = false;
+        if (tl < k) t = vkey(J, lo + m) <= vkey(J, mid + d - 1 - m);
+        const uint32_t bits = (__ballot_sync(tmask, t) >> shift) & 0x7fu;
+        const uint32_t trues = __popc(bits);   // a prefix of the probes
+        if (span <= 7u) {
+            l += trues;
+            break;
+        }
+        const uint32_t m_lo = trues ? l + (uint32_t)(((unsigned long long)trues * span) >> 3) : 0u;
+        const uint32_t m_hi = trues < 7u ? l + (uint32_t)(((unsigned long long)(trues + 1) * span) >> 3) : h;
+        if (trues) l = m_lo + 1;
+        h = m_hi;
+    }
+    return l;
+}
+
 // Push a free physical page onto the ring.
 __device__ __forceinline__ void ring_push(const Job& J, uint32_t page)
 {
@@ -150,40 +182,52 @@ __device__ __forceinline__ void ring_push(const Job& J, uint32_t page)
     else set_error(J.ctr, DERR_INTERNAL, 66);
 }
 
-// Count `take` consumed elements of virtual page u; the page goes back to the
-// free ring once every element is consumed.
-__device__ void consume_page(const Job& J, uint32_t u, uint32_t take, uint32_t n)
-{
-    const uint32_t before = atomicAdd(&J.consumed[u], take);
-    if (before + take == page_size(J, u, n)) {
-        // the caller's last array page may be partial: like the paper's partial
-        // input page it is never declared free (it could not hold a full page)
-        const uint32_t old = J.pt[u];
-        const bool partial_tail = old + 1 == J.vm_na && (n & ((1u << J.vm_plog2) - 1)) != 0;
-        if (!partial_tail) ring_push(J, old);
-    }
-}
+// Consumed-element counting, split in two so that the atomic's latency
+// overlaps the merge: consume_start counts thread q's share (q < 4) of the
+// consumed virtual ranges [v0, v0 + c0) and [v1, v1 + c1) -- each at most a
+// page long, so two pages each -- and consume_finish pushes the page onto the
+// free ring if this count completed it.  The caller's last array page may be
+// partial: like the paper's partial input page it is never declared free.
+struct Consumed {
+    uint32_t u, take, before;
+};
 
-// Thread q < 4 of a group counts its share of the consumed virtual ranges
-// [v0, v0 + c0) and [v1, v1 + c1), each at most one page long (two pages touched).
-__device__ __forceinline__ void consume_ranges(const Job& J, uint32_t q, uint32_t v0, uint32_t c0, uint32_t v1,
-                                               uint32_t c1, uint32_t n)
+__device__ __forceinline__ Consumed consume_start(const Job& J, uint32_t q, uint32_t v0, uint32_t c0, uint32_t v1,
+                                                  uint32_t c1)
 {
-    if (q >= 4) return;
+    Consumed r = {NONE, 0u, 0u};
+    if (q >= 4) return r;
     const uint32_t L = J.vm_plog2;
     const uint32_t v = q < 2 ? v0 : v1, c = q < 2 ? c0 : c1;
-    if (!c) return;
+    if (!c) return r;
     const uint32_t first = min(c, (((v >> L) + 1) << L) - v);   // elements in v's page
-    if ((q & 1u) == 0) consume_page(J, v >> L, first, n);
-    else if (c > first) consume_page(J, (v >> L) + 1, c - first, n);
+    if ((q & 1u) == 0) {
+        r.u = v >> L;
+        r.take = first;
+    } else if (c > first) {
+        r.u = (v >> L) + 1;
+        r.take = c - first;
+    } else {
+        return r;
+    }
+    r.before = atomicAdd(&J.consumed[r.u], r.take);
+    return r;
+}
+
+__device__ __forceinline__ void consume_finish(const Job& J, const Consumed& r, uint32_t n)
+{
+    if (r.u == NONE || r.before + r.take != page_size(J, r.u, n)) return;
+    const uint32_t old = J.pt[r.u];
+    const bool partial_tail = old + 1 == J.vm_na && (n & ((1u << J.vm_plog2) - 1)) != 0;
+    if (!partial_tail) ring_push(J, old);
 }
 
 struct VmSmem {
     uint32_t k[VM_SLOTS];
     uint32_t p[VM_SLOTS];
     uint16_t src[VM_SLOTS];                     // the merge's choice per output: slot in k / p
-    uint32_t rec[VM_WARPS][VM_REC_WORDS + 2];   // the page's record, then the splits at its two ends
-    uint32_t ph[VM_WARPS][4];                   // physical pages of the input slices (two each)
+    // the page's record, the split block of its start, the split at its end
+    uint32_t rec[VM_WARPS][VM_REC_WORDS + 6];
     uint32_t claim[VM_WARPS][2];                // (virtual page, output page) of the group's current page
 };
 
@@ -200,31 +244,40 @@ __device__ void vm_page(const Job& J, VmSmem& sm, const VmGroup& G, uint32_t u, 
     const uint32_t ps0 = u << L;
     uint32_t* dk = phys_k(J, out);
     uint32_t* dp = perm ? phys_p(J, out) : nullptr;
-    // the record and the splits at the page's two ends, in one round trip
-    if (tid < VM_REC_WORDS) rec[tid] = J.vm_rec[(size_t)u * VM_REC_WORDS + tid];
-    else if (tid == VM_REC_WORDS) rec[tid] = J.vm_split_at[u];
-    else if (tid == VM_REC_WORDS + 1) rec[tid] = u + 1 < J.vm_na ? J.vm_split_at[u + 1] : 0u;
+    // the record, the split block of the page's start and the split at its
+    // end, in one round trip
+    for (uint32_t i = tid; i < VM_REC_WORDS + 6; i += G.nthr) {
+        uint32_t x;
+        if (i < VM_REC_WORDS) x = J.vm_rec[(size_t)u * VM_REC_WORDS + i];
+        else if (i < VM_REC_WORDS + 5) x = J.vm_split_at[(size_t)u * VM_SPLIT_WORDS + (i - VM_REC_WORDS)];
+        else x = u + 1 < J.vm_na ? J.vm_split_at[(size_t)(u + 1) * VM_SPLIT_WORDS] : 0u;
+        rec[i] = x;
+    }
     group_sync(G);
     const uint32_t nseg = min(rec[0], 3u);
     for (uint32_t sg = 0; sg < nseg; ++sg) {
-        const uint32_t* R = rec + 1 + 5 * sg;
+        const uint32_t* R = rec + 1 + VM_SEG_WORDS * sg;
         const uint32_t s0 = R[0], s1 = R[1], lo = R[2];
         if (lo == NONE) {                        // carried over unchanged (a gap)
+            const uint32_t ph = R[5];
 #pragma unroll 8
             for (uint32_t v = s0 + tid; v < s1; v += G.nthr) {
-                const uint32_t ph = J.pt[v >> L], off = v & ((1u << L) - 1u);
+                const uint32_t off = v & ((1u << L) - 1u);
                 dk[v - ps0] = phys_k(J, ph)[off];
                 if (dp) dp[v - ps0] = phys_p(J, ph)[off];
             }
             group_sync(G);
-            consume_ranges(J, tid, s0, s1 - s0, 0u, 0u, n);
+            consume_finish(J, consume_start(J, tid, s0, s1 - s0, 0u, 0u), n);
             continue;
         }
         const uint32_t mid = R[3], hi = R[4], la = mid - lo;
         // the splits: 0 / la at the merge's ends; at a page end inside the
-        // merge the round's search left them in vm_split_at
-        const uint32_t a0 = s0 == lo ? 0u : rec[VM_REC_WORDS];
-        const uint32_t a1 = s1 == hi ? la : rec[VM_REC_WORDS + 1];
+        // merge the round's search left them in vm_split_at (with the pages
+        // of the slices starting there)
+        const bool inside = s0 != lo;
+        const uint32_t a0 = inside ? rec[VM_REC_WORDS] : 0u;
+        const uint32_t a1 = s1 == hi ? la : rec[VM_REC_WORDS + 5];
+        const uint32_t* sph = inside ? rec + VM_REC_WORDS + 1 : R + 5;
         const uint32_t b0 = (s0 - lo) - a0, b1 = (s1 - lo) - a1;
         const uint32_t na = a1 - a0, nb = b1 - b0, cnt = na + nb;
         if (cnt > G.cap) {   // a segment never exceeds a page, and a page fits a group
@@ -232,20 +285,13 @@ __device__ void vm_page(const Job& J, VmSmem& sm, const VmGroup& G, uint32_t u, 
             return;
         }
         // the slices' keys (and permutation): each slice is at most a page, so
-        // it spans at most two physical pages; their ids first, then every
-        // element by an asynchronous copy (all in flight at once)
+        // it spans at most two physical pages, named in the record; every
+        // element comes by an asynchronous copy (all in flight at once)
         const uint32_t va = lo + a0, vb = mid + b0;
-        if (tid < 4) {
-            const uint32_t v = tid < 2 ? va : vb, c = tid < 2 ? na : nb;
-            const uint32_t vp = (v >> L) + (tid & 1u);
-            const bool used = c && ((tid & 1u) == 0 || ((v + c - 1) >> L) != (v >> L));
-            sm.ph[gi][tid] = used ? J.pt[vp] : 0u;
-        }
-        group_sync(G);
         for (uint32_t i = tid; i < cnt; i += G.nthr) {
             const bool left = i < na;
             const uint32_t v = left ? va + i : vb + (i - na);
-            const uint32_t ph = sm.ph[gi][(left ? 0u : 2u) + ((v >> L) != ((left ? va : vb) >> L))];
+            const uint32_t ph = sph[(left ? 0u : 2u) + ((v >> L) != ((left ? va : vb) >> L))];
             const uint32_t off = v & ((1u << L) - 1u);
             cp_async4(&sk[i], phys_k(J, ph) + off);
             if (perm) cp_async4(&sp[i], phys_p(J, ph) + off);
@@ -253,9 +299,9 @@ __device__ void vm_page(const Job& J, VmSmem& sm, const VmGroup& G, uint32_t u, 
         cp_async_commit();
         cp_async_wait<0>();
         group_sync(G);
-        // every input element is read: the consumed counts can go out while
-        // the merge runs (a freed page is not read again this round)
-        consume_ranges(J, tid, lo + a0, na, mid + b0, nb, n);
+        // every input element is read: the consumed counts go out now and are
+        // looked at after the merge (a freed page is not read again this round)
+        const Consumed cons = consume_start(J, tid, lo + a0, na, mid + b0, nb);
         // each thread merges VM_K consecutive outputs, recording for each the
         // staging slot it comes from; then the group writes the page out in
         // order, consecutive threads on consecutive words
@@ -287,6 +333,7 @@ __device__ void vm_page(const Job& J, VmSmem& sm, const VmGroup& G, uint32_t u, 
             ok[i] = sk[from];
             if (op) op[i] = sp[from];
         }
+        consume_finish(J, cons, n);
         group_sync(G);
     }
 }
@@ -354,8 +401,8 @@ __global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_rounds(Job J)
         }
         if (!vm_barrier(C)) return;
         // 2. per touched page (a thread each): its record -- up to two merges,
-        //    ordered, with the gaps between them filled by copies -- and the
-        //    merge-path split at its start when that lies inside a merge,
+        //    ordered, with the gaps between them filled by copies; and per page
+        //    start inside a merge (eight lanes each) the merge-path split there,
         //    searched while every input page still holds its data
         for (uint32_t u = gtid; u < NA; u += gstride) {
             const uint32_t c = min(J.page_cnt[u], 2u);
@@ -372,29 +419,59 @@ __global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_rounds(Job J)
                 }
             }
             uint32_t w[VM_REC_WORDS];
+            for (uint32_t i = 0; i < VM_REC_WORDS; ++i) w[i] = 0;
             uint32_t ns = 0, cur = ps0;
+            const uint32_t own = J.pt[u];
             for (uint32_t i = 0; i < c; ++i) {
                 const uint32_t lo = (uint32_t)g[i].goff, mid = lo + g[i].la, hi = mid + g[i].lb;
                 const uint32_t s0 = max(lo, ps0), s1 = min(hi, pe);
                 if (s0 >= s1) continue;
+                uint32_t* W = w + 1 + VM_SEG_WORDS * ns;
                 if (s0 > cur) {
-                    w[1 + 5 * ns] = cur; w[2 + 5 * ns] = s0; w[3 + 5 * ns] = NONE; w[4 + 5 * ns] = 0; w[5 + 5 * ns] = 0;
+                    W[0] = cur; W[1] = s0; W[2] = NONE; W[5] = own;
                     ++ns;
+                    W += VM_SEG_WORDS;
                 }
-                w[1 + 5 * ns] = s0; w[2 + 5 * ns] = s1; w[3 + 5 * ns] = lo; w[4 + 5 * ns] = mid; w[5 + 5 * ns] = hi;
+                W[0] = s0; W[1] = s1; W[2] = lo; W[3] = mid; W[4] = hi;
+                if (s0 == lo) {
+                    // the slices start at the runs' starts: their pages are known now
+                    // (a page start inside the merge gets them from the split search)
+                    W[5] = J.pt[lo >> L];
+                    W[6] = (lo >> L) + 1 < NA ? J.pt[(lo >> L) + 1] : 0u;
+                    W[7] = (mid >> L) < NA ? J.pt[mid >> L] : 0u;
+                    W[8] = (mid >> L) + 1 < NA ? J.pt[(mid >> L) + 1] : 0u;
+                }
                 ++ns;
                 cur = s1;
-                if (lo < ps0 && ps0 < hi) J.vm_split_at[u] = vm_split(J, g[i], ps0 - lo);
             }
             if (cur < pe) {
-                w[1 + 5 * ns] = cur; w[2 + 5 * ns] = pe; w[3 + 5 * ns] = NONE; w[4 + 5 * ns] = 0; w[5 + 5 * ns] = 0;
+                uint32_t* W = w + 1 + VM_SEG_WORDS * ns;
+                W[0] = cur; W[1] = pe; W[2] = NONE; W[5] = own;
                 ++ns;
             }
             w[0] = ns;
-            for (uint32_t i = 1 + 5 * ns; i < VM_REC_WORDS; ++i) w[i] = 0;
             uint4* dst = reinterpret_cast<uint4*>(J.vm_rec + (size_t)u * VM_REC_WORDS);
 #pragma unroll
             for (int q = 0; q < (int)VM_REC_WORDS / 4; ++q) dst[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+        }
+        for (uint32_t u = gtid >> 3; u < NA; u += gstride >> 3) {
+            const uint32_t c = min(J.page_cnt[u], 2u), ps0 = u << L;
+            for (uint32_t i = 0; i < c; ++i) {
+                const GSorted g = J.gsorted[J.page_nodes[2 * u + i]];
+                const uint32_t lo = (uint32_t)g.goff;
+                if (lo < ps0 && ps0 < lo + g.la + g.lb) {
+                    const uint32_t a = vm_split_team(J, g, ps0 - lo, lane);
+                    // the split, and the pages of the two slices that start here
+                    const uint32_t tl = lane & 7u;
+                    uint32_t x = a;
+                    if (tl >= 1 && tl <= 4) {
+                        const uint32_t v = tl <= 2 ? lo + a : lo + g.la + (ps0 - lo - a);
+                        const uint32_t vp = (v >> L) + ((tl - 1) & 1u);
+                        x = vp < NA ? J.pt[vp] : 0u;
+                    }
+                    if (tl <= 4) J.vm_split_at[(size_t)u * VM_SPLIT_WORDS + tl] = x;
+                }
+            }
         }
         // 3. the touched pages, in page order (CTA 0; each thread takes
         //    TOUCH_PER consecutive pages per pass)
@@ -500,6 +577,24 @@ __global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_rounds(Job J)
     }
 }
 
+// One page copied by one warp: 16-byte vectors when the caller's arrays are
+// 16-byte aligned (pool pages always are, and a page is a multiple of 16
+// bytes), else word by word; the partial last page's tail word by word.
+__device__ void vm_copy_page(const Job& J, uint32_t dst, uint32_t src, uint32_t cnt, bool perm, uint32_t lane)
+{
+    const bool vec = ((reinterpret_cast<uintptr_t>(J.keysA) | reinterpret_cast<uintptr_t>(J.permA)) & 15u) == 0;
+    const uint32_t nv = vec ? cnt >> 2 : 0u;
+    for (int pass = 0; pass < (perm ? 2 : 1); ++pass) {
+        const uint32_t* s = pass ? phys_p(J, src) : phys_k(J, src);
+        uint32_t* d = pass ? phys_p(J, dst) : phys_k(J, dst);
+        const uint4* s4 = reinterpret_cast<const uint4*>(s);
+        uint4* d4 = reinterpret_cast<uint4*>(d);
+#pragma unroll 8
+        for (uint32_t i = lane; i < nv; i += 32) d4[i] = s4[i];
+        for (uint32_t i = (nv << 2) + lane; i < cnt; i += 32) d[i] = s[i];
+    }
+}
+
 // Copy (Sec. 4), in batches of target pages.  The paper walks the virtual
 // pages in order: a target array page that still holds data needed later is
 // first moved out to a free page, then the page's own data is copied in.
@@ -510,28 +605,16 @@ __global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_rounds(Job J)
 // step 2 never overwrite a source; each copy frees its source, so the number
 // of free pages is the same after every batch.  Counting pages shows that
 // with at most pool - 1 targets per batch the free pages cover every move out.
-__device__ void vm_copy_page(const Job& J, uint32_t dst, uint32_t src, uint32_t cnt, bool perm)
-{
-    uint32_t* dk = phys_k(J, dst);
-    const uint32_t* sk = phys_k(J, src);
-    for (uint32_t i = threadIdx.x; i < cnt; i += VM_BLOCK) dk[i] = sk[i];
-    if (perm) {
-        uint32_t* dp = phys_p(J, dst);
-        const uint32_t* sp = phys_p(J, src);
-        for (uint32_t i = threadIdx.x; i < cnt; i += VM_BLOCK) dp[i] = sp[i];
-    }
-}
-
 __global__ void __launch_bounds__(VM_BLOCK) k_vm_copy(Job J)
 {
-    __shared__ uint32_t s_src;
     Ctr* C = J.ctr;
     if (*(volatile uint32_t*)&C->error) return;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
     const bool perm = J.want_perm != 0;
     const uint32_t n = J.inst[0].n;
     const uint32_t NA = J.vm_na, NP = J.vm_na_cap + J.vm_pool;
     const uint32_t gtid = blockIdx.x * VM_BLOCK + tid, gstride = gridDim.x * VM_BLOCK;
+    const uint32_t gwarp = gtid >> 5, nwarps = gstride >> 5;
     const bool tail_partial = (n & ((1u << J.vm_plog2) - 1)) != 0;
     // holder[p]: the virtual page whose data physical page p holds (NONE: none)
     for (uint32_t p = gtid; p < NP; p += gstride) J.holder[p] = NONE;
@@ -558,45 +641,41 @@ __global__ void __launch_bounds__(VM_BLOCK) k_vm_copy(Job J)
             if (J.holder[p] == NONE) J.free_stack[atomicAdd(&C->vm_free_top, 1u)] = p;
         }
         if (!vm_barrier(C)) return;
-        // step 1: move needed data out of the batch's targets
-        for (uint32_t q = q0 + blockIdx.x; q < q1; q += gridDim.x) {
+        // step 1: move needed data out of the batch's targets (a warp per target)
+        for (uint32_t q = q0 + gwarp; q < q1; q += nwarps) {
             const uint32_t r = J.holder[q];
             if (r == NONE || r == q) continue;
-            if (tid == 0) {
+            uint32_t f = NONE;
+            if (lane == 0) {
                 const uint32_t at = atomicAdd(&C->vm_wave, 1u);
-                s_src = at < C->vm_free_top ? J.free_stack[at] : NONE;
-                if (s_src == NONE) set_error(C, DERR_INTERNAL, 65);
+                f = at < C->vm_free_top ? J.free_stack[at] : NONE;
+                if (f == NONE) set_error(C, DERR_INTERNAL, 65);
             }
-            __syncthreads();
-            const uint32_t f = s_src;
-            if (f != NONE) {
-                vm_copy_page(J, f, q, page_size(J, r, n), perm);
-                __syncthreads();
-                if (tid == 0) {
-                    J.pt[r] = f;
-                    J.holder[f] = r;
-                    J.holder[q] = NONE;
-                    atomicAdd(&C->vm_copy_moves, 1u);
-                }
+            f = __shfl_sync(0xffffffffu, f, 0);
+            if (f == NONE) continue;
+            vm_copy_page(J, f, q, page_size(J, r, n), perm, lane);
+            __syncwarp();
+            if (lane == 0) {
+                J.pt[r] = f;
+                J.holder[f] = r;
+                J.holder[q] = NONE;
+                atomicAdd(&C->vm_copy_moves, 1u);
             }
-            __syncthreads();
         }
         if (!vm_barrier(C)) return;
         if (*(volatile uint32_t*)&C->error) return;
-        // step 2: every target receives its own data
-        for (uint32_t q = q0 + blockIdx.x; q < q1; q += gridDim.x) {
+        // step 2: every target receives its own data (a warp per target)
+        for (uint32_t q = q0 + gwarp; q < q1; q += nwarps) {
             const uint32_t src = J.pt[q];
-            if (src != q) {
-                vm_copy_page(J, q, src, page_size(J, q, n), perm);
-                __syncthreads();
-                if (tid == 0) {
-                    J.holder[src] = NONE;
-                    J.pt[q] = q;
-                    J.holder[q] = q;
-                    atomicAdd(&C->vm_copy_moves, 1u);
-                }
+            if (src == q) continue;
+            vm_copy_page(J, q, src, page_size(J, q, n), perm, lane);
+            __syncwarp();
+            if (lane == 0) {
+                J.holder[src] = NONE;
+                J.pt[q] = q;
+                J.holder[q] = q;
+                atomicAdd(&C->vm_copy_moves, 1u);
             }
-            __syncthreads();
         }
         if (!vm_barrier(C)) return;
         q0 = q1;

@@ -111,3 +111,19 @@ def test_smaller_tiles(oracle_mod, tile_log2):
             ref = oracle_mod.powersort(keys)
             k, p, st = gpu_sort(c, keys)
             assert_matches_oracle(c, keys, ref, k, p, st)
+
+
+def test_unaligned_caller_arrays(ctx, oracle_mod):
+    # arrays starting 4, 8 and 12 bytes past a 16-byte boundary
+    for shift in (1, 2, 3):
+        n = 300007 + shift
+        keys = inputs.make("runs", n, 40 + shift)
+        ref = oracle_mod.powersort(keys)
+        kbuf = torch.empty(n + 4, dtype=torch.int32, device="cuda")
+        pbuf = torch.empty(n + 4, dtype=torch.int32, device="cuda")
+        dk, dp = kbuf[shift:shift + n], pbuf[shift:shift + n]
+        dk.copy_(torch.from_numpy(keys.view(np.int32)))
+        st = ctx.run(dk, dp, stats=True)
+        assert np.array_equal(to_host(dk), ref.keys)
+        assert np.array_equal(to_host(dp), ref.perm)
+        assert st["merge_cost"] == ref.stats["merge_cost"]

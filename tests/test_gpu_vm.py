@@ -65,3 +65,20 @@ def test_vm_keys_only(oracle_mod):
             k, p, st = gpu_sort(ctx, keys, want_perm=False)
             assert np.array_equal(k, ref.keys)
             assert st["merge_cost"] == ref.stats["merge_cost"]
+
+
+def test_vm_unaligned_caller_arrays(oracle_mod):
+    # the caller's arrays start 4 bytes past a 16-byte boundary: the page
+    # copies must not assume vector alignment
+    with _vm(1 << 20, page_log2=8) as ctx:
+        for n in (70001, (1 << 20) - 3):
+            keys = inputs.make("uniform", n, 12)
+            ref = oracle_mod.powersort(keys)
+            kbuf = torch.empty(n + 1, dtype=torch.int32, device="cuda")
+            pbuf = torch.empty(n + 1, dtype=torch.int32, device="cuda")
+            dk, dp = kbuf[1:], pbuf[1:]
+            dk.copy_(torch.from_numpy(keys.view(np.int32)))
+            st = ctx.run(dk, dp, stats=True)
+            assert np.array_equal(dk.cpu().numpy().view(np.uint32), ref.keys)
+            assert np.array_equal(dp.cpu().numpy().view(np.uint32), ref.perm)
+            assert st["merge_cost"] == ref.stats["merge_cost"]
