@@ -15,6 +15,9 @@ permutation is produced):
                the decreasing-run variant of Sec. 5 (PS_FLAG_DESCENDING_RUNS);
                the line also carries the rate of the plain rule on the same
                input
+  bands_2^24   one step = one sort of n = 2^24: sorted blocks of 2^13 keys in
+               descending value bands; with --storage vm the merges splice
+               whole pages through the page table (stats: pages_spliced)
   serving      a Poisson stream of 2000 requests/s for 10 s (sizes log-uniform
                in [2^10, 2^24], seed 4) through the continuous-batching server
                under a 64 GB device-memory budget; reports sustained elements/s
@@ -56,6 +59,7 @@ WORKLOADS = {
     "plain_2^24": [("uniform", 1 << 24, 1), ("zipf", 1 << 24, 1), ("runs", 1 << 24, 1)],
     "hbm_2^28": [("uniform", 1 << 28, 2)],
     "updown_2^24": [("updown", 1 << 24, 1)],
+    "bands_2^24": [("bands", 1 << 24, 1)],
     "batched_4096": None,
     "serving": None,
 }
@@ -712,7 +716,7 @@ def main():
         },
         "stats": {data[i][0]: {k: hbm[i][k] for k in ("runs", "merge_cost", "tiles", "global_nodes", "rounds",
                                                       "hbm_merge_elems", "max_power", "scratch_bytes",
-                                                      "peak_pages")} for i in hbm},
+                                                      "peak_pages", "pages_spliced")} for i in hbm},
         "round_timeline_us": rounds,
         "plain_rule": plain_rule,
         "cpu_baseline": cpu,

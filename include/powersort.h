@@ -107,7 +107,8 @@ typedef struct ps_stats {
     uint32_t instances;
     uint64_t hbm_merge_elems; /* sum of the sizes of the merges done through HBM  */
     uint32_t launches;      /* kernels the call launched                          */
-    uint32_t pad;
+    uint32_t pages_spliced; /* VM mode: output pages that took over a whole input
+                               page through the page table, moving no element */
 } ps_stats;
 
 typedef struct ps_ctx ps_ctx;

@@ -61,7 +61,7 @@ class ps_stats(ctypes.Structure):
         ("instances", ctypes.c_uint32),
         ("hbm_merge_elems", ctypes.c_uint64),
         ("launches", ctypes.c_uint32),
-        ("pad", ctypes.c_uint32),
+        ("pages_spliced", ctypes.c_uint32),
     ]
 
     def as_dict(self):

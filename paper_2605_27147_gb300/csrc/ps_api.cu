@@ -136,6 +136,7 @@ void fill_stats(const ps_ctx* c, ps_stats* st, uint32_t count)
     st->instances = count;
     st->hbm_merge_elems = h->hbm_elems;
     st->launches = LAUNCHES_PER_CALL + (c->base.vm ? 1u : 0u);   // VM: rounds + the final Copy
+    st->pages_spliced = c->base.vm ? h->vm_spliced : 0u;
 }
 
 ps_status run_common(ps_ctx* c, uint32_t* d_keys, uint32_t* d_perm, const uint64_t* d_offsets,

@@ -122,6 +122,7 @@ struct Ctr {
     uint32_t vm_in_use_peak;           // most physical pages holding data at once
     uint32_t vm_waves;                 // VM rounds run by the call
     uint32_t vm_copy_moves;            // page copies made by the final Copy
+    uint32_t vm_spliced;               // output pages that took over a whole input page
     uint32_t vm_ring_head;             // tickets handed out: the ring slot each output page pops
     uint32_t vm_ring_tail;             // free pages pushed onto the ring so far
     uint32_t vm_round_base;            // ring_head at the start of the current round

@@ -202,6 +202,7 @@ __global__ void __launch_bounds__(1024) k_setup(Job J)
             C->vm_in_use_peak = 0;
             C->vm_waves = 0;
             C->vm_copy_moves = 0;
+            C->vm_spliced = 0;
             if (na > J.vm_na_cap) set_error(C, DERR_INTERNAL, 3);
         }
     }

@@ -284,6 +284,20 @@ __device__ void vm_page(const Job& J, VmSmem& sm, const VmGroup& G, uint32_t u, 
             if (tid == 0) set_error(J.ctr, DERR_INTERNAL, 65);
             return;
         }
+        // page splicing: when the whole output page is one whole input page
+        // (a page-aligned slice of a single run), the output page takes over
+        // that physical page through the page table and no element moves; the
+        // input page is consumed by this page alone, so it is not freed, and
+        // the fresh page goes back to the ring
+        if (cnt == (1u << L) && s0 == ps0 && ((na == cnt && ((lo + a0) & (cnt - 1u)) == 0) ||
+                                              (nb == cnt && ((mid + b0) & (cnt - 1u)) == 0))) {
+            if (tid == 0) {
+                J.pt_new[u] = na == cnt ? sph[0] : sph[2];
+                ring_push(J, out);
+                atomicAdd(&J.ctr->vm_spliced, 1u);
+            }
+            return;
+        }
         // the slices' keys (and permutation): each slice is at most a page, so
         // it spans at most two physical pages, named in the record; every
         // element comes by an asynchronous copy (all in flight at once)

@@ -19,6 +19,10 @@ Distributions (shapes of the paper's workloads, Sec. 5):
               Geometric presort with parameter 1/S.
 ``updown``    like ``runs``, but a fair coin sorts each segment ascending or
               descending (inputs for the decreasing-run variant of Sec. 5).
+``bands``     sorted blocks of 2**13 uniform keys, each block drawn from a
+              value band below the previous block's (data appended in
+              reverse order of a partitioning key): every merge puts one run
+              wholly before the other.
 ``sorted`` / ``reversed`` / ``equal`` / ``few``   degenerate cases.
 """
 from __future__ import annotations
@@ -117,6 +121,16 @@ def updown(n: int, seed: int, mean_run: float = 1024.0) -> np.ndarray:
     return keys[np.lexsort((sk, seg))]
 
 
+def bands(n: int, seed: int, block: int = 1 << 13) -> np.ndarray:
+    """Sorted blocks of ``block`` keys in descending value bands (see module doc)."""
+    nb = max(1, -(-n // block))
+    width = (1 << 32) // nb
+    raw = mt_raw(seed, n).astype(np.uint64)
+    b = np.arange(n, dtype=np.int64) // block
+    keys = ((nb - 1 - b).astype(np.uint64) * np.uint64(width) + raw % np.uint64(width)).astype(np.uint32)
+    return presort_segments_fast(keys, np.diff(np.append(np.arange(0, n, block), n)))
+
+
 def paper(n: int, seed: int, S: float = 2.0) -> np.ndarray:
     """Sec. 5 recipe: values uniform in [100, 10**9], presorted with parameter S."""
     raw = mt_raw(seed, n).astype(np.uint64)
@@ -139,6 +153,8 @@ def make(dist: str, n: int, seed: int) -> np.ndarray:
         return paper(n, seed)
     if dist == "updown":
         return updown(n, seed)
+    if dist == "bands":
+        return bands(n, seed)
     if dist == "sorted":
         return np.sort(uniform(n, seed))
     if dist == "reversed":

@@ -32,7 +32,7 @@ def test_config_1_uniform_2_16(ctx, oracle_mod):
 
 EDGE = [0, 1, 2, 3, 31, 32, 33, 63, 64, 65, 127, 128, 129, 1000, 4095, 4096, 4097, 8191, 8193,
         12345, 65535, 65537, 100003, 262147]
-DISTS = ["uniform", "zipf", "runs", "paper", "sorted", "reversed", "equal", "few"]
+DISTS = ["uniform", "zipf", "runs", "paper", "sorted", "reversed", "equal", "few", "bands"]
 
 
 @pytest.mark.parametrize("dist", DISTS)

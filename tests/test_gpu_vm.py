@@ -20,7 +20,7 @@ def _vm(max_n, **kw):
     return binding.Context(max_n, mode=binding.PS_MODE_VM, want_perm=True, **kw)
 
 
-@pytest.mark.parametrize("dist", ["uniform", "zipf", "runs", "paper", "few", "sorted", "reversed", "equal"])
+@pytest.mark.parametrize("dist", ["uniform", "zipf", "runs", "paper", "few", "sorted", "reversed", "equal", "bands"])
 def test_vm_matches_oracle(oracle_mod, dist):
     with _vm(1 << 20, page_log2=8) as ctx:          # small pages: many pages, many waves
         for n in (1, 63, 64, 1000, 4097, 8193, 65537, 300007, 1 << 20):
@@ -82,3 +82,31 @@ def test_vm_unaligned_caller_arrays(oracle_mod):
             assert np.array_equal(dk.cpu().numpy().view(np.uint32), ref.keys)
             assert np.array_equal(dp.cpu().numpy().view(np.uint32), ref.perm)
             assert st["merge_cost"] == ref.stats["merge_cost"]
+
+
+def test_vm_page_splicing(oracle_mod):
+    # ascending blocks of 8192 keys with every block below the one before it:
+    # each merge outputs its right run and then its left run unchanged, every
+    # slice is a whole page-aligned input page, so every output page takes
+    # over an input page and no element moves in the merges: the spliced
+    # pages are exactly M / P
+    with _vm(1 << 20, page_log2=8) as ctx:
+        L, K = 8192, 64
+        blocks = [np.arange(L, dtype=np.uint32) + np.uint32((K - 1 - b) * L) for b in range(K)]
+        keys = np.concatenate(blocks)
+        ref = oracle_mod.powersort(keys)
+        k, p, st = gpu_sort(ctx, keys)
+        assert_matches_oracle(ctx, keys, ref, k, p, st)
+        assert st["merge_cost"] == keys.size * 6
+        assert st["pages_spliced"] == st["merge_cost"] // 256
+        # blocks shifted off the page grid: fewer splices, the same result
+        keys2 = np.concatenate([np.arange(100, dtype=np.uint32) + np.uint32(K * L), keys])
+        ref2 = oracle_mod.powersort(keys2)
+        k2, p2, st2 = gpu_sort(ctx, keys2)
+        assert_matches_oracle(ctx, keys2, ref2, k2, p2, st2)
+        assert st2["pages_spliced"] < st["pages_spliced"]
+        # unsorted data interleaves every page: nothing to splice
+        keys3 = inputs.make("uniform", 1 << 20, 4)
+        k3, p3, st3 = gpu_sort(ctx, keys3)
+        assert np.array_equal(k3, oracle_mod.powersort(keys3).keys)
+        assert st3["pages_spliced"] == 0
