@@ -15,7 +15,9 @@ all arithmetic is in the C source, which follows the paper:
 
 ``descending_runs=True`` selects the run-detection variant named in Sec. 5
 ("Algorithm variants"): strictly decreasing runs are accepted too and
-reversed in place.
+reversed in place.  ``key_type`` ("u32", "i32" or "f32") says how the 32-bit
+keys are ordered: unsigned, two's complement, or IEEE 754 totalOrder; keys
+are always passed as their 32-bit patterns (``arr.view(np.uint32)``).
 """
 from __future__ import annotations
 
@@ -59,6 +61,7 @@ class _Stats(ctypes.Structure):
 
 
 DESCENDING_RUNS = 1   # ORACLE_DESCENDING_RUNS
+KEY_ORDER = {"u32": 0, "i32": 2, "f32": 4}   # ORACLE_KEY_I32, ORACLE_KEY_F32
 
 
 def compile_source(src: str, so: str) -> str:
@@ -103,6 +106,8 @@ def _declare(lib):
     lib.oracle_power.argtypes = [ctypes.c_uint64] * 4
     lib.oracle_stable_sort.restype = ctypes.c_int
     lib.oracle_stable_sort.argtypes = [u32p, ctypes.c_uint64, u32p, u32p]
+    lib.oracle_stable_sort_ex.restype = ctypes.c_int
+    lib.oracle_stable_sort_ex.argtypes = [u32p, ctypes.c_uint64, ctypes.c_uint32, u32p, u32p]
     lib.oracle_powersort.restype = ctypes.c_int
     lib.oracle_powersort.argtypes = [u32p, u32p, ctypes.c_uint64, u32p, u8p, u32p,
                                      ctypes.POINTER(_Stats)]
@@ -130,15 +135,15 @@ def power(n: int, i: int, j: int, k: int, lib=None) -> int:
     return int((lib or _load()).oracle_power(n, i, j, k))
 
 
-def stable_sort(keys: np.ndarray):
+def stable_sort(keys: np.ndarray, key_type: str = "u32"):
     """The definition of the result: (sorted keys, stable permutation)."""
     keys = np.ascontiguousarray(keys, dtype=np.uint32)
     n = keys.size
     ko = np.empty(n, np.uint32)
     po = np.empty(n, np.uint32)
     if n:
-        rc = _load().oracle_stable_sort(_ptr(keys, ctypes.c_uint32), n,
-                                        _ptr(ko, ctypes.c_uint32), _ptr(po, ctypes.c_uint32))
+        rc = _load().oracle_stable_sort_ex(_ptr(keys, ctypes.c_uint32), n, KEY_ORDER[key_type],
+                                           _ptr(ko, ctypes.c_uint32), _ptr(po, ctypes.c_uint32))
         if rc:
             raise MemoryError("oracle_stable_sort")
     return ko, po
@@ -185,15 +190,22 @@ def _run(fn_name: str, keys: np.ndarray, page_size: int | None, lib=None, option
     )
 
 
-def powersort(keys: np.ndarray, lib=None, descending_runs: bool = False) -> OracleResult:
+def _options(descending_runs: bool, key_type: str) -> int:
+    return (DESCENDING_RUNS if descending_runs else 0) | KEY_ORDER[key_type]
+
+
+def powersort(keys: np.ndarray, lib=None, descending_runs: bool = False, key_type: str = "u32") -> OracleResult:
     """Algorithm 1 with Pingpong storage, executed literally on one core."""
-    if descending_runs:
-        return _run("oracle_powersort_ex", keys, None, lib, DESCENDING_RUNS)
+    opt = _options(descending_runs, key_type)
+    if opt:
+        return _run("oracle_powersort_ex", keys, None, lib, opt)
     return _run("oracle_powersort", keys, None, lib)
 
 
-def powersort_vm(keys: np.ndarray, page_size: int, lib=None, descending_runs: bool = False) -> OracleResult:
+def powersort_vm(keys: np.ndarray, page_size: int, lib=None, descending_runs: bool = False,
+                 key_type: str = "u32") -> OracleResult:
     """Algorithm 1 with virtual-memory (paged) storage, on one core."""
-    if descending_runs:
-        return _run("oracle_powersort_vm_ex", keys, int(page_size), lib, DESCENDING_RUNS)
+    opt = _options(descending_runs, key_type)
+    if opt:
+        return _run("oracle_powersort_vm_ex", keys, int(page_size), lib, opt)
     return _run("oracle_powersort_vm", keys, int(page_size), lib)

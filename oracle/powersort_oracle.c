@@ -24,7 +24,11 @@
  *   oracle_powersort_ex, oracle_powersort_vm_ex
  *                        the same with options; ORACLE_DESCENDING_RUNS takes
  *                        the variant of Sec. 5 "Algorithm variants" that also
- *                        accepts decreasing runs (reversed in place).
+ *                        accepts decreasing runs (reversed in place);
+ *                        ORACLE_KEY_I32 / ORACLE_KEY_F32 read the 32-bit keys
+ *                        as two's-complement integers / IEEE-754 binary32
+ *                        values ordered by the standard's totalOrder
+ *   oracle_stable_sort_ex the stable-sort definition under those key orders
  *
  * Readings taken where the paper is silent (all listed in the design doc):
  *   - indices are 0-based and half open: a = [i, j), b = [j, k);
@@ -64,8 +68,34 @@ typedef struct {
     uint64_t reverse_moves;      /* element moves made by the reversals       */
 } oracle_stats;
 
-/* options of oracle_powersort_ex / oracle_powersort_vm_ex */
+/* options of oracle_powersort_ex / oracle_powersort_vm_ex / oracle_stable_sort_ex */
 #define ORACLE_DESCENDING_RUNS 1u
+#define ORACLE_KEY_I32 2u
+#define ORACLE_KEY_F32 4u
+
+/* The key order of the running call (the oracle is single-threaded). */
+static uint32_t g_key_order;
+
+/* key_gt(a, b): key a sorts strictly after key b.
+ *   default        unsigned 32-bit integers;
+ *   ORACLE_KEY_I32 two's-complement 32-bit integers;
+ *   ORACLE_KEY_F32 IEEE 754 binary32 totalOrder (IEEE 754-2008 Sec. 5.10):
+ *                  negative values (sign bit set) precede positive ones;
+ *                  among positives a larger bit pattern (exponent, then
+ *                  fraction, then NaN payload) is larger; among negatives the
+ *                  order of the magnitudes is reversed.  So -NaN < -inf <
+ *                  ... < -0 < +0 < ... < +inf < +NaN. */
+static int key_gt(uint32_t a, uint32_t b)
+{
+    if (g_key_order & ORACLE_KEY_I32) return (int32_t)a > (int32_t)b;
+    if (g_key_order & ORACLE_KEY_F32) {
+        const int na = (int)(a >> 31), nb = (int)(b >> 31);
+        if (na != nb) return nb;                        /* a positive, b negative */
+        const uint32_t ma = a & 0x7fffffffu, mb = b & 0x7fffffffu;
+        return na ? ma < mb : ma > mb;
+    }
+    return a > b;
+}
 
 /* Sec. 5, "Algorithm variants": start from l = n and halve (rounding up)
  * until l < 64.  When n < 64 the loop body never runs and minrun = n. */
@@ -103,13 +133,15 @@ static int cmp_pair(const void* x, const void* y)
 {
     const kv_pair* a = (const kv_pair*)x;
     const kv_pair* b = (const kv_pair*)y;
-    if (a->key != b->key) return a->key < b->key ? -1 : 1;
+    if (a->key != b->key) return key_gt(b->key, a->key) ? -1 : 1;
     if (a->idx != b->idx) return a->idx < b->idx ? -1 : 1;
     return 0;
 }
 
-int oracle_stable_sort(const uint32_t* keys, uint64_t n, uint32_t* keys_out, uint32_t* perm_out)
+int oracle_stable_sort_ex(const uint32_t* keys, uint64_t n, uint32_t options, uint32_t* keys_out,
+                          uint32_t* perm_out)
 {
+    g_key_order = options & (ORACLE_KEY_I32 | ORACLE_KEY_F32);
     if (n == 0) return 0;
     kv_pair* v = (kv_pair*)malloc(n * sizeof(kv_pair));
     if (!v) return -1;
@@ -121,6 +153,11 @@ int oracle_stable_sort(const uint32_t* keys, uint64_t n, uint32_t* keys_out, uin
     }
     free(v);
     return 0;
+}
+
+int oracle_stable_sort(const uint32_t* keys, uint64_t n, uint32_t* keys_out, uint32_t* perm_out)
+{
+    return oracle_stable_sort_ex(keys, n, 0u, keys_out, perm_out);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -135,14 +172,14 @@ static uint64_t extract_run(uint32_t* key, uint32_t* perm, uint64_t s, uint64_t 
     int down = 0;
     if ((options & ORACLE_DESCENDING_RUNS) && e < n) {
         st->scan_comparisons++;
-        down = key[s] > key[e];
+        down = key_gt(key[s], key[e]);
     }
     if (down) {
         /* strictly decreasing run: extend while a[e-1] > a[e], then reverse */
         ++e;
         while (e < n) {
             st->scan_comparisons++;
-            if (!(key[e - 1] > key[e])) break;
+            if (!key_gt(key[e - 1], key[e])) break;
             ++e;
         }
         for (uint64_t x = s, y = e - 1; x < y; ++x, --y) {
@@ -156,7 +193,7 @@ static uint64_t extract_run(uint32_t* key, uint32_t* perm, uint64_t s, uint64_t 
         if (e < n && (options & ORACLE_DESCENDING_RUNS)) ++e;   /* pair (s, s+1) already compared */
         while (e < n) {
             st->scan_comparisons++;
-            if (key[e - 1] > key[e]) break;   /* first descent: run ends here */
+            if (key_gt(key[e - 1], key[e])) break;   /* first descent: run ends here */
             ++e;
         }
     }
@@ -168,7 +205,7 @@ static uint64_t extract_run(uint32_t* key, uint32_t* perm, uint64_t s, uint64_t 
             uint64_t y = x;
             while (y > s) {
                 st->insert_comparisons++;
-                if (!(key[y - 1] > v)) break; /* strict: equal keys stay put */
+                if (!key_gt(key[y - 1], v)) break; /* strict: equal keys stay put */
                 key[y] = key[y - 1];
                 perm[y] = perm[y - 1];
                 st->insert_moves++;
@@ -192,7 +229,7 @@ static void pingpong_merge(uint32_t* key, uint32_t* perm, const uint32_t* bkey,
     uint64_t xa = i, xb = j, xr = i;
     while (xa < j && xb < k) {
         st->merge_comparisons++;
-        if (bkey[xa] <= key[xb]) { key[xr] = bkey[xa]; perm[xr] = bperm[xa]; ++xa; }
+        if (!key_gt(bkey[xa], key[xb])) { key[xr] = bkey[xa]; perm[xr] = bperm[xa]; ++xa; }
         else                     { key[xr] = key[xb];  perm[xr] = perm[xb];  ++xb; }
         ++xr;
         st->moves++;
@@ -214,7 +251,7 @@ static void pingpong_merge_to_stack(const uint32_t* key, const uint32_t* perm, u
     while (xa > i && xb > j) {
         st->merge_comparisons++;
         --xr;
-        if (bkey[xa - 1] > key[xb - 1]) { bkey[xr] = bkey[xa - 1]; bperm[xr] = bperm[xa - 1]; --xa; }
+        if (key_gt(bkey[xa - 1], key[xb - 1])) { bkey[xr] = bkey[xa - 1]; bperm[xr] = bperm[xa - 1]; --xa; }
         else                            { bkey[xr] = key[xb - 1];  bperm[xr] = perm[xb - 1];  --xb; }
         st->moves++;
     }
@@ -233,6 +270,7 @@ int oracle_powersort_ex(uint32_t* key, uint32_t* perm, uint64_t n, uint32_t* run
                         uint8_t* powers, uint32_t* merges, uint32_t options, oracle_stats* st)
 {
     memset(st, 0, sizeof(*st));
+    g_key_order = options & (ORACLE_KEY_I32 | ORACLE_KEY_F32);
     st->n = n;
     st->minrun = oracle_minrun(n);
     for (uint64_t x = 0; x < n; ++x) perm[x] = (uint32_t)x;
@@ -456,12 +494,12 @@ static int vm_extract_run(vm_mem* m, vm_buf* work, vm_buf* out, uint32_t minrun,
     int down = 0;
     if ((options & ORACLE_DESCENDING_RUNS) && e < avail) {
         st->scan_comparisons++;
-        down = *vm_kslot(m, work, 0) > *vm_kslot(m, work, 1);
+        down = key_gt(*vm_kslot(m, work, 0), *vm_kslot(m, work, 1));
         ++e;
     }
     while (e < avail) {
         st->scan_comparisons++;
-        const int desc = *vm_kslot(m, work, e - 1) > *vm_kslot(m, work, e);
+        const int desc = key_gt(*vm_kslot(m, work, e - 1), *vm_kslot(m, work, e));
         if (desc != down) break;   /* ascending: first descent; decreasing: first non-descent */
         ++e;
     }
@@ -483,7 +521,7 @@ static int vm_extract_run(vm_mem* m, vm_buf* work, vm_buf* out, uint32_t minrun,
             uint64_t y = x;
             while (y > 0) {
                 st->insert_comparisons++;
-                if (!(*vm_kslot(m, work, y - 1) > v)) break;
+                if (!key_gt(*vm_kslot(m, work, y - 1), v)) break;
                 *vm_kslot(m, work, y) = *vm_kslot(m, work, y - 1);
                 *vm_pslot(m, work, y) = *vm_pslot(m, work, y - 1);
                 st->insert_moves++;
@@ -509,7 +547,7 @@ static int vm_merge(vm_mem* m, vm_buf* a, vm_buf* b, vm_buf* out)
     vm_buf_init(out);
     while (a->len && b->len) {
         m->st->merge_comparisons++;
-        vm_buf* src = (*vm_kslot(m, a, 0) <= *vm_kslot(m, b, 0)) ? a : b;
+        vm_buf* src = !key_gt(*vm_kslot(m, a, 0), *vm_kslot(m, b, 0)) ? a : b;
         uint32_t k = *vm_kslot(m, src, 0), p = *vm_pslot(m, src, 0);
         vm_pop_front(m, src);
         if (vm_push_back(m, out, k, p)) return -1;
@@ -582,6 +620,7 @@ int oracle_powersort_vm_ex(uint32_t* key, uint32_t* perm, uint64_t n, uint64_t p
                            uint32_t options, oracle_stats* st)
 {
     memset(st, 0, sizeof(*st));
+    g_key_order = options & (ORACLE_KEY_I32 | ORACLE_KEY_F32);
     st->n = n;
     st->minrun = oracle_minrun(n);
     st->page_size = (uint32_t)page_size;

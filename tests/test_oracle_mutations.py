@@ -21,28 +21,33 @@ from paper_2605_27147_gb300 import inputs
 SRC = os.path.join(os.path.dirname(ocore.__file__), "powersort_oracle.c")
 
 MUTATIONS = {
-    "merge ties take the right run": ("if (bkey[xa] <= key[xb])", "if (bkey[xa] < key[xb])"),
-    "right-to-left merge ties take the left run": ("if (bkey[xa - 1] > key[xb - 1])", "if (bkey[xa - 1] >= key[xb - 1])"),
-    "insertion sort unstable": ("if (!(key[y - 1] > v)) break;", "if (!(key[y - 1] >= v)) break;"),
+    "merge ties take the right run": ("if (!key_gt(bkey[xa], key[xb]))", "if (key_gt(key[xb], bkey[xa]))"),
+    "right-to-left merge ties take the left run": ("if (key_gt(bkey[xa - 1], key[xb - 1]))",
+                                                   "if (!key_gt(key[xb - 1], bkey[xa - 1]))"),
+    "insertion sort unstable": ("if (!key_gt(key[y - 1], v)) break;", "if (key_gt(v, key[y - 1])) break;"),
     "power off by one": ("if (hi > lo) return p;", "if (hi > lo) return p + 1;"),
     "power uses wrong index": ("(((unsigned __int128)(i + j)) << p)", "(((unsigned __int128)(i + k)) << p)"),
     "minrun loop bound": ("while (l >= 64) l = (l + 1) / 2;", "while (l > 64) l = (l + 1) / 2;"),
     "minrun rounds down": ("while (l >= 64) l = (l + 1) / 2;", "while (l >= 64) l = l / 2;"),
     "merge cost drops the left input": ("st->merge_cost += cj - ti;\n            ci = ti;\n            --top;                                     /* Pop */",
                                         "st->merge_cost += cj - ci;\n            ci = ti;\n            --top;                                     /* Pop */"),
-    "runs strictly increasing": ("if (key[e - 1] > key[e]) break;   /* first descent: run ends here */",
-                                 "if (key[e - 1] >= key[e]) break;   /* first descent: run ends here */"),
+    "runs strictly increasing": ("if (key_gt(key[e - 1], key[e])) break;   /* first descent: run ends here */",
+                                 "if (!key_gt(key[e], key[e - 1])) break;   /* first descent: run ends here */"),
     "forced run one short": ("uint64_t end = s + minrun < n ? s + minrun : n;",
                              "uint64_t end = s + minrun - 1 < n ? s + minrun - 1 : n;"),
-    "decreasing runs take equal keys": ("if (!(key[e - 1] > key[e])) break;",
-                                        "if (!(key[e - 1] >= key[e])) break;"),
-    "decreasing run starts on a tie": ("down = key[s] > key[e];", "down = key[s] >= key[e];"),
+    "decreasing runs take equal keys": ("if (!key_gt(key[e - 1], key[e])) break;",
+                                        "if (key_gt(key[e], key[e - 1])) break;"),
+    "decreasing run starts on a tie": ("down = key_gt(key[s], key[e]);", "down = !key_gt(key[e], key[s]);"),
     "reversal leaves the permutation": ("key[x] = key[y]; perm[x] = perm[y];", "key[x] = key[y];"),
     "paged decreasing runs take equal keys": (
-        "const int desc = *vm_kslot(m, work, e - 1) > *vm_kslot(m, work, e);",
-        "const int desc = *vm_kslot(m, work, e - 1) >= *vm_kslot(m, work, e);"),
+        "const int desc = key_gt(*vm_kslot(m, work, e - 1), *vm_kslot(m, work, e));",
+        "const int desc = !key_gt(*vm_kslot(m, work, e), *vm_kslot(m, work, e - 1));"),
     "paged reversal off by one": ("for (uint64_t x = 0, y = e - 1; x < y; ++x, --y) {",
                                   "for (uint64_t x = 0, y = e - 2; x < y; ++x, --y) {"),
+    "signed keys compared unsigned": ("if (g_key_order & ORACLE_KEY_I32) return (int32_t)a > (int32_t)b;",
+                                      "if (g_key_order & ORACLE_KEY_I32) return a > b;"),
+    "negative floats not reversed": ("return na ? ma < mb : ma > mb;", "return ma > mb;"),
+    "float signs in the wrong order": ("if (na != nb) return nb;", "if (na != nb) return na;"),
 }
 
 
@@ -94,6 +99,20 @@ def run_pins(lib):
             assert np.array_equal(r.perm, np.argsort(keys, kind="stable"))
             assert np.array_equal(r.keys, keys[r.perm])
             assert r.run_starts.tolist() == starts
+    # typed key orders: numpy's stable argsort on int32 / float32 views, and
+    # the hand-worked totalOrder fixture
+    ik = (inputs.make("runs", 20000, 3).astype(np.int64) - (1 << 31)).astype(np.int32)
+    r = oracle.powersort(ik.view(np.uint32), lib=lib, key_type="i32")
+    assert np.array_equal(r.perm, np.argsort(ik, kind="stable"))
+    fk = (ik.astype(np.float32) * np.float32(1e-3))
+    r = oracle.powersort(fk.view(np.uint32), lib=lib, key_type="f32")
+    assert np.array_equal(r.perm, np.argsort(fk, kind="stable"))
+    rows = golden_rows("f32_total_order.txt")
+    bits = np.zeros(len(rows), np.uint32)
+    for rank, idx, b in rows:
+        bits[int(idx)] = int(b, 16)
+    r = oracle.powersort(bits, lib=lib, key_type="f32")
+    assert r.perm.tolist() == [int(idx) for rank, idx, b in rows]
 
 
 def test_shipped_oracle_passes_pins(oracle_mod):
