@@ -64,6 +64,16 @@ typedef enum ps_mode {
     PS_MODE_VM = 1        /* Sec. 4: page pool of O(sqrt(n log n)) elements + tables */
 } ps_mode;
 
+/* How the 32-bit keys are ordered (the key-value generalisation: the keys
+ * are sorted as these values; their bit patterns travel unchanged). */
+typedef enum ps_key_type {
+    PS_KEY_U32 = 0, /* unsigned integers (the default)                            */
+    PS_KEY_I32 = 1, /* two's-complement signed integers                           */
+    PS_KEY_F32 = 2  /* IEEE 754 binary32 under totalOrder (IEEE 754-2008 Sec. 5.10):
+                       -NaN < -inf < ... < -0 < +0 < ... < +inf < +NaN; NaNs of one
+                       sign ordered by their bit patterns                         */
+} ps_key_type;
+
 typedef struct ps_config {
     uint32_t mode;       /* ps_mode                                                  */
     uint32_t want_perm;  /* nonzero: calls may produce the stable permutation        */
@@ -75,7 +85,8 @@ typedef struct ps_config {
     uint32_t tile_log2;  /* on-chip tile capacity 2^tile_log2 in 10..12 (0: 12)      */
     uint32_t pool_pages; /* VM page-pool size in pages (0: chosen by the library)    */
     uint32_t flags;      /* PS_FLAG_* below                                          */
-    uint32_t reserved[3];
+    uint32_t key_type;   /* ps_key_type of the keys this context sorts               */
+    uint32_t reserved[2];
 } ps_config;
 
 /* ps_config.flags */
@@ -140,6 +151,18 @@ PS_API ps_status ps_run(ps_ctx* ctx, uint32_t* d_keys, uint32_t* d_perm, uint64_
  * it can be captured into a CUDA graph (see ps_graph_create_batched). */
 PS_API ps_status ps_run_batched(ps_ctx* ctx, uint32_t* d_keys, uint32_t* d_perm,
                                 const uint64_t* d_offsets, uint32_t count, ps_stats* stats);
+
+/* Payloads of any width follow the keys through the stable permutation:
+ * d_dst row r = d_src row perm[r], rows of row_bytes bytes (>= 1).  With
+ * d_offsets NULL there is one instance of n rows; otherwise `count`
+ * instances laid out as in ps_run_batched (n is ignored; perm values are
+ * local to each instance, rows of instance q start at row off[q] of both
+ * arrays).  d_src and d_dst must not overlap.  Asynchronous on the
+ * context's stream; a permutation entry outside its instance (or a bad
+ * offsets table) copies nothing for that row and makes the next
+ * synchronising call return PS_EINVAL. */
+PS_API ps_status ps_gather_rows(ps_ctx* ctx, const uint32_t* d_perm, const uint64_t* d_offsets, uint32_t count,
+                                uint64_t n, const void* d_src, void* d_dst, uint32_t row_bytes);
 
 /* A batched sort captured once into a CUDA graph and replayed with one
  * launch (its arrays are fixed at capture time; refill them between

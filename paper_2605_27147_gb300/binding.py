@@ -23,10 +23,11 @@ EXPORTS = (
     "ps_get_phase_times", "ps_get_runs", "ps_get_powers", "ps_get_nodes", "ps_get_instance_stats",
     "ps_destroy", "ps_run_noalloc", "ps_get_round_times", "ps_graph_create_batched",
     "ps_graph_launch", "ps_graph_destroy", "ps_server_create", "ps_server_submit", "ps_server_poll",
-    "ps_server_wait", "ps_server_get_stats", "ps_server_destroy",
+    "ps_server_wait", "ps_server_get_stats", "ps_server_destroy", "ps_gather_rows",
 )
 PS_NOALLOC_MAX_N = 262144
 PS_FLAG_TIMING, PS_FLAG_HOST_IO, PS_FLAG_DESCENDING_RUNS = 1, 2, 4
+PS_KEY_U32, PS_KEY_I32, PS_KEY_F32 = 0, 1, 2
 PHASES = ("setup", "runs", "plan", "tiles", "merge_rounds", "finish")
 
 
@@ -41,7 +42,8 @@ class ps_config(ctypes.Structure):
         ("tile_log2", ctypes.c_uint32),
         ("pool_pages", ctypes.c_uint32),
         ("flags", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint32 * 3),
+        ("key_type", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32 * 2),
     ]
 
 
@@ -144,6 +146,8 @@ def lib(build_if_missing: bool = True):
                                          ctypes.POINTER(ctypes.c_uint32)]
         L.ps_sync.restype = ctypes.c_int
         L.ps_sync.argtypes = [vp]
+        L.ps_gather_rows.restype = ctypes.c_int
+        L.ps_gather_rows.argtypes = [vp, vp, vp, ctypes.c_uint32, ctypes.c_uint64, vp, vp, ctypes.c_uint32]
         L.ps_graph_create_batched.restype = ctypes.c_int
         L.ps_graph_create_batched.argtypes = [vp, vp, vp, vp, ctypes.c_uint32, ctypes.POINTER(vp)]
         L.ps_graph_launch.restype = ctypes.c_int
@@ -200,7 +204,7 @@ class Context:
 
     def __init__(self, max_n: int, *, mode: int = PS_MODE_PINGPONG, want_perm: bool = True,
                  max_total: int = 0, max_count: int = 0, tile_log2: int = 0, page_log2: int = 0,
-                 pool_pages: int = 0, flags: int = 0, device: int = 0,
+                 pool_pages: int = 0, flags: int = 0, key_type: int = PS_KEY_U32, device: int = 0,
                  stream=None):
         import torch
 
@@ -208,7 +212,7 @@ class Context:
         self.stream = stream if stream is not None else torch.cuda.current_stream(device)
         cfg = ps_config(mode=mode, want_perm=1 if want_perm else 0, max_n=max_n, max_total=max_total,
                         max_count=max_count, page_log2=page_log2, tile_log2=tile_log2,
-                        pool_pages=pool_pages, flags=flags)
+                        pool_pages=pool_pages, flags=flags, key_type=key_type)
         h = ctypes.c_void_p()
         _check(lib().ps_create(ctypes.byref(cfg), device, ctypes.c_void_p(self.stream.cuda_stream),
                                ctypes.byref(h)), "ps_create")
@@ -249,6 +253,15 @@ class Context:
         _check(lib().ps_run_batched(self._h, _ptr(keys), _ptr(perm), _ptr(offsets), offsets.numel() - 1,
                                     ctypes.byref(st) if st is not None else None), "ps_run_batched")
         return st.as_dict() if st is not None else None
+
+    def gather_rows(self, perm, src, dst, *, offsets=None):
+        """ps_gather_rows: dst row r = src row perm[r] (rows of src's trailing
+        dimensions, any width; per instance when ``offsets`` is given)."""
+        rows = src.shape[0] if src.dim() else 0
+        row_bytes = (src.numel() // max(rows, 1)) * src.element_size()
+        count = offsets.numel() - 1 if offsets is not None else 0
+        _check(lib().ps_gather_rows(self._h, _ptr(perm), _ptr(offsets), count, rows, _ptr(src), _ptr(dst),
+                                    row_bytes), "ps_gather_rows")
 
     def graph_batched(self, keys, offsets, perm=None) -> "Graph":
         """Capture ps_run_batched on these arrays into a replayable CUDA graph."""

@@ -95,7 +95,10 @@ ps_status enqueue(ps_ctx* c, const ps::Job& J)
         return !c->timing || c->capturing || cudaEventRecord(c->ev[i], s) == cudaSuccess;
     };
     if (!mark(0)) return PS_ECUDA;
-    if (ps::launch_setup(J, s) != cudaSuccess || !mark(1)) return PS_ECUDA;
+    if (ps::launch_setup(J, s) != cudaSuccess) return PS_ECUDA;
+    // typed keys: to order-preserving unsigned words before run detection
+    if (J.key_type != PS_KEY_U32 && ps::launch_key_map(J, true, c->grid_runs, s) != cudaSuccess) return PS_ECUDA;
+    if (!mark(1)) return PS_ECUDA;
     if (ps::launch_runs(J, c->grid_runs, s) != cudaSuccess || !mark(2)) return PS_ECUDA;
     if (ps::launch_plan(J, c->grid_plan, s) != cudaSuccess || !mark(3)) return PS_ECUDA;
     if (ps::launch_tiles(J, c->grid_tiles, s) != cudaSuccess || !mark(4)) return PS_ECUDA;
@@ -104,7 +107,9 @@ ps_status enqueue(ps_ctx* c, const ps::Job& J)
     } else {
         if (ps::launch_merge_rounds(J, c->grid_merge, s) != cudaSuccess || !mark(5)) return PS_ECUDA;
     }
-    if (ps::launch_finish(J, s) != cudaSuccess || !mark(6)) return PS_ECUDA;
+    if (ps::launch_finish(J, s) != cudaSuccess) return PS_ECUDA;
+    if (J.key_type != PS_KEY_U32 && ps::launch_key_map(J, false, c->grid_runs, s) != cudaSuccess) return PS_ECUDA;
+    if (!mark(6)) return PS_ECUDA;
     if (cudaMemcpyAsync(c->h_ctr, J.ctr, sizeof(ps::Ctr), cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return PS_ECUDA;
     return PS_OK;
@@ -135,7 +140,8 @@ void fill_stats(const ps_ctx* c, ps_stats* st, uint32_t count)
     st->rounds = h->rounds;
     st->instances = count;
     st->hbm_merge_elems = h->hbm_elems;
-    st->launches = LAUNCHES_PER_CALL + (c->base.vm ? 1u : 0u);   // VM: rounds + the final Copy
+    // VM: rounds + the final Copy; typed keys: the two maps
+    st->launches = LAUNCHES_PER_CALL + (c->base.vm ? 1u : 0u) + (c->base.key_type != PS_KEY_U32 ? 2u : 0u);
     st->pages_spliced = c->base.vm ? h->vm_spliced : 0u;
 }
 
@@ -208,6 +214,7 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
     *out = nullptr;
     if (!cfg) return PS_EINVAL;
     if (cfg->mode != PS_MODE_PINGPONG && cfg->mode != PS_MODE_VM) return PS_EINVAL;
+    if (cfg->key_type > PS_KEY_F32) return PS_EINVAL;
     if (cfg->mode == PS_MODE_VM && cfg->max_count > 1) return PS_EINVAL;   // VM storage: one instance per call
     if (cfg->max_n == 0 || cfg->max_n > LIMIT_N) return PS_EINVAL;
     const unsigned long long max_total = cfg->max_total ? cfg->max_total : cfg->max_n;
@@ -327,6 +334,7 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
         if (st == PS_OK && cfg->want_perm) st = dev_alloc(c, &c->io_perm, max_total);
     }
     J.desc_runs = (cfg->flags & PS_FLAG_DESCENDING_RUNS) ? 1u : 0u;
+    J.key_type = cfg->key_type;
     if (st == PS_OK && (cfg->flags & PS_FLAG_TIMING)) {
         c->timing = true;
         for (cudaEvent_t& e : c->ev)
@@ -509,6 +517,25 @@ PS_API void ps_graph_destroy(ps_graph* g)
     cudaGraphExecDestroy(g->exec);
     cudaGraphDestroy(g->graph);
     delete g;
+}
+
+PS_API ps_status ps_gather_rows(ps_ctx* ctx, const uint32_t* d_perm, const uint64_t* d_offsets, uint32_t count,
+                                uint64_t n, const void* d_src, void* d_dst, uint32_t row_bytes)
+{
+    if (!ctx || row_bytes == 0) return PS_EINVAL;
+    if (d_offsets ? count == 0 : n > ctx->max_total) return PS_EINVAL;
+    if (!d_offsets && n == 0) return PS_OK;
+    if (!d_perm || !d_src || !d_dst) return PS_EINVAL;
+    DeviceGuard g(ctx->device);
+    const int grid = ctx->num_sms * 8;
+    if (ps::launch_gather_rows(d_perm, reinterpret_cast<const unsigned long long*>(d_offsets), count, n,
+                               ctx->max_total, d_src, d_dst, row_bytes, ctx->base.ctr, grid, ctx->stream) != cudaSuccess)
+        return PS_ECUDA;
+    // a bad row surfaces at the next synchronising call, as a sort's would
+    if (cudaMemcpyAsync(&ctx->h_ctr->error, &ctx->base.ctr->error, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                        ctx->stream) != cudaSuccess)
+        return PS_ECUDA;
+    return PS_OK;
 }
 
 PS_API ps_status ps_sync(ps_ctx* ctx)
