@@ -9,6 +9,8 @@ from .oracle import (  # noqa: F401
     power,
     stable_sort,
     powersort,
+    powersort_records,
+    stable_sort_records,
     powersort_vm,
     OracleResult,
 )

@@ -12,6 +12,9 @@ all arithmetic is in the C source, which follows the paper:
 * :func:`stable_sort`  -- the plain definition of the result (stable order)
 * :func:`powersort`    -- Algorithm 1 with Pingpong storage (Sec. 3)
 * :func:`powersort_vm` -- Algorithm 1 with virtual-memory storage (Sec. 4)
+* :func:`powersort_records`, :func:`stable_sort_records` -- the same for
+  records of several 32-bit words ordered lexicographically (the paper's blob
+  types, Sec. 5 "Input data types")
 
 ``descending_runs=True`` selects the run-detection variant named in Sec. 5
 ("Algorithm variants"): strictly decreasing runs are accepted too and
@@ -106,6 +109,11 @@ def _declare(lib):
     lib.oracle_power.argtypes = [ctypes.c_uint64] * 4
     lib.oracle_stable_sort.restype = ctypes.c_int
     lib.oracle_stable_sort.argtypes = [u32p, ctypes.c_uint64, u32p, u32p]
+    lib.oracle_powersort_records.restype = ctypes.c_int
+    lib.oracle_powersort_records.argtypes = [u32p, ctypes.c_uint32, ctypes.c_uint64, u32p, u32p, u8p, u32p,
+                                             ctypes.c_uint32, ctypes.POINTER(_Stats)]
+    lib.oracle_stable_sort_records.restype = ctypes.c_int
+    lib.oracle_stable_sort_records.argtypes = [u32p, ctypes.c_uint32, ctypes.c_uint64, u32p]
     lib.oracle_stable_sort_ex.restype = ctypes.c_int
     lib.oracle_stable_sort_ex.argtypes = [u32p, ctypes.c_uint64, ctypes.c_uint32, u32p, u32p]
     lib.oracle_powersort.restype = ctypes.c_int
@@ -209,3 +217,44 @@ def powersort_vm(keys: np.ndarray, page_size: int, lib=None, descending_runs: bo
     if opt:
         return _run("oracle_powersort_vm_ex", keys, int(page_size), lib, opt)
     return _run("oracle_powersort_vm", keys, int(page_size), lib)
+
+
+def powersort_records(rec: np.ndarray, lib=None, descending_runs: bool = False) -> OracleResult:
+    """Algorithm 1 on records (rows of ``rec``, uint32 words, lexicographic
+    order).  ``keys`` and ``perm`` of the result are both the stable order of
+    the record indices."""
+    lib = lib or _load()
+    rec = np.ascontiguousarray(rec, dtype=np.uint32)
+    n, words = rec.shape
+    perm = np.empty(n, np.uint32)
+    runs = np.empty(n + 2, np.uint32)
+    pw = np.zeros(max(n, 1), np.uint8)
+    mg = np.empty((max(n, 1), 3), np.uint32)
+    st = _Stats()
+    rc = lib.oracle_powersort_records(_ptr(rec, ctypes.c_uint32), words, n, _ptr(perm, ctypes.c_uint32),
+                                      _ptr(runs, ctypes.c_uint32), _ptr(pw, ctypes.c_uint8),
+                                      _ptr(mg, ctypes.c_uint32), DESCENDING_RUNS if descending_runs else 0,
+                                      ctypes.byref(st))
+    if rc:
+        raise MemoryError("oracle_powersort_records")
+    stats = {name: int(getattr(st, name)) for name, _ in _Stats._fields_}
+    r = stats["runs"]
+    return OracleResult(
+        keys=perm.copy(),
+        perm=perm,
+        run_starts=runs[: r + 1].copy() if n else np.zeros(1, np.uint32),
+        powers=pw[: max(r - 1, 0)].copy(),
+        merges=mg[: stats["merges"]].copy(),
+        stats=stats,
+    )
+
+
+def stable_sort_records(rec: np.ndarray, lib=None) -> np.ndarray:
+    """The definition for records: indices ordered by (row, index)."""
+    lib = lib or _load()
+    rec = np.ascontiguousarray(rec, dtype=np.uint32)
+    n, words = rec.shape
+    perm = np.empty(n, np.uint32)
+    if n and lib.oracle_stable_sort_records(_ptr(rec, ctypes.c_uint32), words, n, _ptr(perm, ctypes.c_uint32)):
+        raise MemoryError("oracle_stable_sort_records")
+    return perm

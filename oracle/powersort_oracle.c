@@ -29,6 +29,11 @@
  *                        as two's-complement integers / IEEE-754 binary32
  *                        values ordered by the standard's totalOrder
  *   oracle_stable_sort_ex the stable-sort definition under those key orders
+ *   oracle_powersort_records, oracle_stable_sort_records
+ *                        the same for records of `words` 32-bit words ordered
+ *                        lexicographically (the paper's blob types, Sec. 5
+ *                        "Input data types"): the keys are record indices
+ *                        compared through the rows
  *
  * Readings taken where the paper is silent (all listed in the design doc):
  *   - indices are 0-based and half open: a = [i, j), b = [j, k);
@@ -72,6 +77,12 @@ typedef struct {
 #define ORACLE_DESCENDING_RUNS 1u
 #define ORACLE_KEY_I32 2u
 #define ORACLE_KEY_F32 4u
+#define ORACLE_RECORDS 8u
+
+/* The records of the running call (ORACLE_RECORDS): row i is
+ * g_rec[i * g_rec_words .. (i + 1) * g_rec_words). */
+static const uint32_t* g_rec;
+static uint32_t g_rec_words;
 
 /* The key order of the running call (the oracle is single-threaded). */
 static uint32_t g_key_order;
@@ -87,6 +98,14 @@ static uint32_t g_key_order;
  *                  ... < -0 < +0 < ... < +inf < +NaN. */
 static int key_gt(uint32_t a, uint32_t b)
 {
+    if (g_key_order & ORACLE_RECORDS) {
+        /* lexicographic: the first differing word (as unsigned) decides */
+        const uint32_t* ra = g_rec + (uint64_t)a * g_rec_words;
+        const uint32_t* rb = g_rec + (uint64_t)b * g_rec_words;
+        for (uint32_t w = 0; w < g_rec_words; ++w)
+            if (ra[w] != rb[w]) return ra[w] > rb[w];
+        return 0;
+    }
     if (g_key_order & ORACLE_KEY_I32) return (int32_t)a > (int32_t)b;
     if (g_key_order & ORACLE_KEY_F32) {
         const int na = (int)(a >> 31), nb = (int)(b >> 31);
@@ -133,7 +152,8 @@ static int cmp_pair(const void* x, const void* y)
 {
     const kv_pair* a = (const kv_pair*)x;
     const kv_pair* b = (const kv_pair*)y;
-    if (a->key != b->key) return key_gt(b->key, a->key) ? -1 : 1;
+    if (key_gt(a->key, b->key)) return 1;
+    if (key_gt(b->key, a->key)) return -1;
     if (a->idx != b->idx) return a->idx < b->idx ? -1 : 1;
     return 0;
 }
@@ -141,7 +161,7 @@ static int cmp_pair(const void* x, const void* y)
 int oracle_stable_sort_ex(const uint32_t* keys, uint64_t n, uint32_t options, uint32_t* keys_out,
                           uint32_t* perm_out)
 {
-    g_key_order = options & (ORACLE_KEY_I32 | ORACLE_KEY_F32);
+    g_key_order = options & (ORACLE_KEY_I32 | ORACLE_KEY_F32 | ORACLE_RECORDS);
     if (n == 0) return 0;
     kv_pair* v = (kv_pair*)malloc(n * sizeof(kv_pair));
     if (!v) return -1;
@@ -270,7 +290,7 @@ int oracle_powersort_ex(uint32_t* key, uint32_t* perm, uint64_t n, uint32_t* run
                         uint8_t* powers, uint32_t* merges, uint32_t options, oracle_stats* st)
 {
     memset(st, 0, sizeof(*st));
-    g_key_order = options & (ORACLE_KEY_I32 | ORACLE_KEY_F32);
+    g_key_order = options & (ORACLE_KEY_I32 | ORACLE_KEY_F32 | ORACLE_RECORDS);
     st->n = n;
     st->minrun = oracle_minrun(n);
     for (uint64_t x = 0; x < n; ++x) perm[x] = (uint32_t)x;
@@ -620,7 +640,7 @@ int oracle_powersort_vm_ex(uint32_t* key, uint32_t* perm, uint64_t n, uint64_t p
                            uint32_t options, oracle_stats* st)
 {
     memset(st, 0, sizeof(*st));
-    g_key_order = options & (ORACLE_KEY_I32 | ORACLE_KEY_F32);
+    g_key_order = options & (ORACLE_KEY_I32 | ORACLE_KEY_F32 | ORACLE_RECORDS);
     st->n = n;
     st->minrun = oracle_minrun(n);
     st->page_size = (uint32_t)page_size;
@@ -719,4 +739,35 @@ int oracle_powersort_vm(uint32_t* key, uint32_t* perm, uint64_t n, uint64_t page
                         oracle_stats* st)
 {
     return oracle_powersort_vm_ex(key, perm, n, page_size, run_starts, powers, merges, 0u, st);
+}
+
+/* Records (ORACLE_RECORDS): Algorithm 1 on the record indices 0..n-1, every
+ * comparison made on the rows.  perm receives the stable order (perm[r] =
+ * index of the r-th record); run_starts, powers, merges and st as for
+ * oracle_powersort_ex (options may add ORACLE_DESCENDING_RUNS). */
+int oracle_powersort_records(const uint32_t* rec, uint32_t words, uint64_t n, uint32_t* perm,
+                             uint32_t* run_starts, uint8_t* powers, uint32_t* merges, uint32_t options,
+                             oracle_stats* st)
+{
+    uint32_t* idx = (uint32_t*)malloc((n ? n : 1) * sizeof(uint32_t));
+    if (!idx) return -1;
+    for (uint64_t i = 0; i < n; ++i) idx[i] = (uint32_t)i;
+    g_rec = rec;
+    g_rec_words = words;
+    int rc = oracle_powersort_ex(idx, perm, n, run_starts, powers, merges, options | ORACLE_RECORDS, st);
+    free(idx);
+    return rc;
+}
+
+/* The definition for records: indices ordered by (row, index). */
+int oracle_stable_sort_records(const uint32_t* rec, uint32_t words, uint64_t n, uint32_t* perm_out)
+{
+    uint32_t* idx = (uint32_t*)malloc((n ? n : 1) * sizeof(uint32_t));
+    if (!idx) return -1;
+    for (uint64_t i = 0; i < n; ++i) idx[i] = (uint32_t)i;
+    g_rec = rec;
+    g_rec_words = words;
+    int rc = oracle_stable_sort_ex(idx, n, ORACLE_RECORDS, NULL, perm_out);
+    free(idx);
+    return rc;
 }

@@ -166,6 +166,36 @@ def make(dist: str, n: int, seed: int) -> np.ndarray:
     raise ValueError(f"unknown distribution {dist!r}")
 
 
+def records(kind: str, n: int, seed: int, words: int = 30, S: float = 0.0) -> np.ndarray:
+    """Records of ``words`` 32-bit words (rows of an (n, words) array), the
+    paper's data types (Sec. 5 "Input data types"), values uniform in
+    [100, 10**9]:
+
+    ``random``  every word random (``randomBlob30``: most comparisons end at
+                the first word);
+    ``zero``    every word but the last is 0 (``zeroBlob30``, and the rows the
+                ``ptr`` type points to: every comparison reads all words);
+    ``few``     every word drawn from {100, 101, 102}: long common prefixes.
+
+    With S > 1, consecutive segments of Geometric(1/S) length are sorted
+    (lexicographically), the paper's presort."""
+    raw = mt_raw(seed, n * words).astype(np.uint64).reshape(n, words) if n else np.zeros((0, words), np.uint64)
+    if kind == "few":
+        rec = (np.uint64(100) + raw % np.uint64(3)).astype(np.uint32)
+    else:
+        rec = (np.uint64(100) + raw % np.uint64(10 ** 9 - 100 + 1)).astype(np.uint32)
+        if kind == "zero":
+            rec[:, :-1] = 0
+        elif kind != "random":
+            raise ValueError(f"unknown record kind {kind!r}")
+    if S > 1 and n:
+        lens = geometric_lengths(n, seed + 7919, S)
+        seg = np.repeat(np.arange(lens.size, dtype=np.int64), lens)
+        order = np.lexsort(tuple(rec[:, w] for w in range(words - 1, -1, -1)) + (seg,))
+        rec = rec[order]
+    return np.ascontiguousarray(rec)
+
+
 def batch_lengths(count: int, seed: int, lo_log2: float = 8.0, hi_log2: float = 20.0) -> np.ndarray:
     """Instance lengths floor(2**(lo + (hi-lo) u)), u uniform (log-uniform sizes)."""
     u = _unit_doubles(seed, count)

@@ -48,6 +48,10 @@ MUTATIONS = {
                                       "if (g_key_order & ORACLE_KEY_I32) return a > b;"),
     "negative floats not reversed": ("return na ? ma < mb : ma > mb;", "return ma > mb;"),
     "float signs in the wrong order": ("if (na != nb) return nb;", "if (na != nb) return na;"),
+    "records skip their first word": ("for (uint32_t w = 0; w < g_rec_words; ++w)",
+                                      "for (uint32_t w = 1; w < g_rec_words; ++w)"),
+    "records compare the wrong way": ("if (ra[w] != rb[w]) return ra[w] > rb[w];",
+                                      "if (ra[w] != rb[w]) return ra[w] < rb[w];"),
 }
 
 
@@ -113,6 +117,10 @@ def run_pins(lib):
         bits[int(idx)] = int(b, 16)
     r = oracle.powersort(bits, lib=lib, key_type="f32")
     assert r.perm.tolist() == [int(idx) for rank, idx, b in rows]
+    # records: numpy's stable lexsort
+    rec = inputs.records("few", 3000, 2, words=5)
+    r = oracle.powersort_records(rec, lib=lib)
+    assert np.array_equal(r.perm, np.lexsort(tuple(rec[:, w] for w in range(4, -1, -1))))
 
 
 def test_shipped_oracle_passes_pins(oracle_mod):
