@@ -99,6 +99,10 @@ typedef struct ps_config {
  * The result is the same stable sort; the runs, powers and merge tree are
  * those of the variant. */
 #define PS_FLAG_DESCENDING_RUNS 4u
+/* Allocate the arrays ps_sort_records needs (about 13 bytes per element of
+ * max_n: window keys, descent mask, group list, merge scratch). */
+#define PS_FLAG_RECORDS 8u
+#define PS_RECORD_MAX_WORDS 1024u
 
 /* Per-call statistics (sums over instances for batched calls).  The paper's
  * merge cost M is the sum of the lengths of all merge inputs (Sec. 2
@@ -163,6 +167,19 @@ PS_API ps_status ps_run_batched(ps_ctx* ctx, uint32_t* d_keys, uint32_t* d_perm,
  * synchronising call return PS_EINVAL. */
 PS_API ps_status ps_gather_rows(ps_ctx* ctx, const uint32_t* d_perm, const uint64_t* d_offsets, uint32_t count,
                                 uint64_t n, const void* d_src, void* d_dst, uint32_t row_bytes);
+
+/* Records: rows of `words` 32-bit words (row i = d_rec[i * words, (i + 1) *
+ * words)), ordered lexicographically with the words as unsigned integers
+ * (the paper's blob types, Sec. 5 "Input data types").  d_perm receives the
+ * stable order (n entries); d_rec_out, if not NULL, the rows in that order
+ * (n * words words; it must not overlap d_rec, which is read only).  The runs,
+ * powers, merge tree and merge cost (ps_get_*) are those of Algorithm 1 on
+ * the records; the rows move once, at the end.  Needs a context made with
+ * PS_FLAG_RECORDS and want_perm, keys of type PS_KEY_U32 and no
+ * PS_FLAG_DESCENDING_RUNS; 1 <= words <= PS_RECORD_MAX_WORDS, n <= max_n.
+ * Asynchronous unless stats is given. */
+PS_API ps_status ps_sort_records(ps_ctx* ctx, const uint32_t* d_rec, uint32_t words, uint64_t n,
+                                 uint32_t* d_perm, uint32_t* d_rec_out, ps_stats* stats);
 
 /* A batched sort captured once into a CUDA graph and replayed with one
  * launch (its arrays are fixed at capture time; refill them between

@@ -23,10 +23,10 @@ EXPORTS = (
     "ps_get_phase_times", "ps_get_runs", "ps_get_powers", "ps_get_nodes", "ps_get_instance_stats",
     "ps_destroy", "ps_run_noalloc", "ps_get_round_times", "ps_graph_create_batched",
     "ps_graph_launch", "ps_graph_destroy", "ps_server_create", "ps_server_submit", "ps_server_poll",
-    "ps_server_wait", "ps_server_get_stats", "ps_server_destroy", "ps_gather_rows",
+    "ps_server_wait", "ps_server_get_stats", "ps_server_destroy", "ps_gather_rows", "ps_sort_records",
 )
 PS_NOALLOC_MAX_N = 262144
-PS_FLAG_TIMING, PS_FLAG_HOST_IO, PS_FLAG_DESCENDING_RUNS = 1, 2, 4
+PS_FLAG_TIMING, PS_FLAG_HOST_IO, PS_FLAG_DESCENDING_RUNS, PS_FLAG_RECORDS = 1, 2, 4, 8
 PS_KEY_U32, PS_KEY_I32, PS_KEY_F32 = 0, 1, 2
 PHASES = ("setup", "runs", "plan", "tiles", "merge_rounds", "finish")
 
@@ -146,6 +146,8 @@ def lib(build_if_missing: bool = True):
                                          ctypes.POINTER(ctypes.c_uint32)]
         L.ps_sync.restype = ctypes.c_int
         L.ps_sync.argtypes = [vp]
+        L.ps_sort_records.restype = ctypes.c_int
+        L.ps_sort_records.argtypes = [vp, vp, ctypes.c_uint32, ctypes.c_uint64, vp, vp, ctypes.POINTER(ps_stats)]
         L.ps_gather_rows.restype = ctypes.c_int
         L.ps_gather_rows.argtypes = [vp, vp, vp, ctypes.c_uint32, ctypes.c_uint64, vp, vp, ctypes.c_uint32]
         L.ps_graph_create_batched.restype = ctypes.c_int
@@ -252,6 +254,15 @@ class Context:
         st = ps_stats() if stats else None
         _check(lib().ps_run_batched(self._h, _ptr(keys), _ptr(perm), _ptr(offsets), offsets.numel() - 1,
                                     ctypes.byref(st) if st is not None else None), "ps_run_batched")
+        return st.as_dict() if st is not None else None
+
+    def sort_records(self, rec, perm, out=None, *, stats: bool = False):
+        """ps_sort_records: ``rec`` is an (n, words) 32-bit tensor; ``perm``
+        receives the stable lexicographic order, ``out`` (optional) the rows."""
+        st = ps_stats() if stats else None
+        n, words = (rec.shape[0], rec.shape[1]) if rec.dim() == 2 else (rec.shape[0], 1)
+        _check(lib().ps_sort_records(self._h, _ptr(rec), words, n, _ptr(perm), _ptr(out),
+                                     ctypes.byref(st) if st is not None else None), "ps_sort_records")
         return st.as_dict() if st is not None else None
 
     def gather_rows(self, perm, src, dst, *, offsets=None):

@@ -29,6 +29,11 @@ struct ps_ctx {
     cudaEvent_t ev[7];          // phase boundaries of the last call (PS_FLAG_TIMING)
     uint32_t* io_keys;          // device arrays of ps_run_host (PS_FLAG_HOST_IO)
     uint32_t* io_perm;
+    uint32_t* rec_keys;         // ps_sort_records (PS_FLAG_RECORDS): window keys,
+    uint32_t* rec_mask;         //   descent mask,
+    uint32_t* rec_tmp;          //   merge scratch of the tie fix-up,
+    uint32_t* rec_groups;       //   groups of equal windows (start, end)
+    uint32_t rec_group_cap;
 };
 
 namespace {
@@ -329,6 +334,13 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
     J.gidx = J.kappa;
     if (st == PS_OK) st = dev_alloc(c, &J.chunk_node, chunk_node_cap);
     if (st == PS_OK) st = dev_alloc(c, &J.ctr, 1);
+    if (st == PS_OK && (cfg->flags & PS_FLAG_RECORDS)) {
+        c->rec_group_cap = (uint32_t)(cfg->max_n / 2 + 1);
+        st = dev_alloc(c, &c->rec_keys, cfg->max_n);
+        if (st == PS_OK) st = dev_alloc(c, &c->rec_mask, cfg->max_n / 32 + 2);
+        if (st == PS_OK) st = dev_alloc(c, &c->rec_tmp, cfg->max_n);
+        if (st == PS_OK) st = dev_alloc(c, &c->rec_groups, 2ull * c->rec_group_cap);
+    }
     if (st == PS_OK && (cfg->flags & PS_FLAG_HOST_IO)) {
         st = dev_alloc(c, &c->io_keys, max_total);
         if (st == PS_OK && cfg->want_perm) st = dev_alloc(c, &c->io_perm, max_total);
@@ -517,6 +529,52 @@ PS_API void ps_graph_destroy(ps_graph* g)
     cudaGraphExecDestroy(g->exec);
     cudaGraphDestroy(g->graph);
     delete g;
+}
+
+PS_API ps_status ps_sort_records(ps_ctx* ctx, const uint32_t* d_rec, uint32_t words, uint64_t n,
+                                 uint32_t* d_perm, uint32_t* d_rec_out, ps_stats* stats)
+{
+    if (!ctx || !ctx->rec_keys || !ctx->cfg.want_perm) return PS_EINVAL;
+    if (ctx->base.desc_runs || ctx->base.key_type != PS_KEY_U32) return PS_EINVAL;
+    if (words == 0 || words > PS_RECORD_MAX_WORDS || n > ctx->cfg.max_n) return PS_EINVAL;
+    if (n > 0 && (!d_rec || !d_perm)) return PS_EINVAL;
+    if (n == 0) {
+        if (stats) std::memset(stats, 0, sizeof(*stats));
+        return PS_OK;
+    }
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = ctx->stream;
+    ps::Ctr* C = ctx->base.ctr;
+    const int grid = ctx->num_sms * 8;
+    // the shared prefix starts at "every word", the group list empty
+    if (cudaMemsetAsync(&C->rec_lcp, 0xff, sizeof(uint32_t), s) != cudaSuccess ||
+        cudaMemsetAsync(&C->rec_groups, 0, sizeof(uint32_t), s) != cudaSuccess)
+        return PS_ECUDA;
+    if (ps::launch_records_prepare(d_rec, words, n, ctx->rec_mask, ctx->rec_keys, C, grid, s) != cudaSuccess)
+        return PS_ECUDA;
+    // the 32-bit pipeline on the window keys, runs from the descent mask
+    ctx->base.desc_mask = ctx->rec_mask;
+    ps_status st = run_common(ctx, ctx->rec_keys, d_perm, nullptr, n, 1, nullptr);
+    ctx->base.desc_mask = nullptr;
+    if (st != PS_OK) return st;
+    if (ps::launch_records_fix(d_rec, words, n, ctx->rec_keys, d_perm, ctx->rec_tmp, ctx->rec_groups,
+                               ctx->rec_group_cap, C, grid, s) != cudaSuccess)
+        return PS_ECUDA;
+    if (d_rec_out && ps::launch_gather_rows(d_perm, nullptr, 0, n, ctx->max_total, d_rec, d_rec_out, words * 4u, C,
+                                            grid, s) != cudaSuccess)
+        return PS_ECUDA;
+    if (cudaMemcpyAsync(&ctx->h_ctr->error, &C->error, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return PS_ECUDA;
+    if (stats) {
+        st = sync_and_check(ctx);
+        if (st != PS_OK) return st;
+        fill_stats(ctx, stats, 1);
+        if (cudaMemcpy(ctx->h_inst, ctx->base.inst, sizeof(ps::Inst), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return PS_ECUDA;
+        stats->minrun = ctx->h_inst->minrun;
+        stats->launches += 4u + (d_rec_out ? 1u : 0u);
+    }
+    return PS_OK;
 }
 
 PS_API ps_status ps_gather_rows(ps_ctx* ctx, const uint32_t* d_perm, const uint64_t* d_offsets, uint32_t count,

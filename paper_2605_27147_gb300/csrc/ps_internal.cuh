@@ -124,6 +124,8 @@ struct Ctr {
     uint32_t vm_copy_moves;            // page copies made by the final Copy
     uint32_t vm_spliced;               // output pages that took over a whole input page
     uint32_t keys_mapped;              // typed keys: the forward map ran (the inverse must too)
+    uint32_t rec_lcp;                  // records: words every row shares (NONE: all rows equal)
+    uint32_t rec_groups;               // records: groups of equal window keys listed for the fix-up
     uint32_t vm_ring_head;             // tickets handed out: the ring slot each output page pops
     uint32_t vm_ring_tail;             // free pages pushed onto the ring so far
     uint32_t vm_round_base;            // ring_head at the start of the current round
@@ -158,6 +160,7 @@ struct Job {
     uint32_t want_perm;
     uint32_t desc_runs;         // nonzero: strictly decreasing runs are taken and reversed
     uint32_t key_type;          // ps_key_type: keys are mapped to order-preserving u32 and back
+    const uint32_t* desc_mask;  // records: descent bit per position (run detection reads it, not keys)
     uint32_t tile_cap;          // T: largest merge-tree node merged on chip
     uint32_t merge_e;           // outputs per HBM merge chunk (set from the merge kernel's shape)
     unsigned long long max_n;   // limits the offsets table is checked against
@@ -383,6 +386,11 @@ cudaError_t launch_finish(const Job& J, cudaStream_t s);
 cudaError_t launch_vm(const Job& J, int grid, cudaStream_t s);
 int vm_rounds_max_grid(int num_sms);
 cudaError_t launch_key_map(const Job& J, bool forward, int grid, cudaStream_t s);
+cudaError_t launch_records_prepare(const uint32_t* rec, uint32_t W, unsigned long long n, uint32_t* mask,
+                                   uint32_t* keys, Ctr* C, int grid, cudaStream_t s);
+cudaError_t launch_records_fix(const uint32_t* rec, uint32_t W, unsigned long long n, const uint32_t* keys,
+                               uint32_t* perm, uint32_t* tmp, uint32_t* groups, uint32_t cap, Ctr* C, int grid,
+                               cudaStream_t s);
 cudaError_t launch_gather_rows(const uint32_t* perm, const unsigned long long* offsets, uint32_t count,
                                unsigned long long n, unsigned long long max_total, const void* src, void* dst,
                                uint32_t row_bytes, Ctr* ctr, int grid, cudaStream_t s);

@@ -1,0 +1,203 @@
+// Records: rows of W 32-bit words ordered lexicographically (the paper's
+// blob types, Sec. 5 "Input data types": randomBlob30, zeroBlob30, and the
+// rows ptr points to).
+//
+// The merge tree of Algorithm 1 depends only on where the runs are, and the
+// runs only on which neighbours descend.  So:
+//   1. k_rec_scan compares every row with its predecessor (the first word
+//      that differs decides) and writes the exact descent mask, and finds L,
+//      the length of the prefix all rows share (the smallest first
+//      difference over all neighbours);
+//   2. k_rec_key extracts the window key, word L of every row: the first
+//      word in which rows differ at all, and an order-preserving image of
+//      the row (a smaller row never has a larger window);
+//   3. the 32-bit pipeline sorts the window keys with the permutation, its
+//      run detection reading the descent mask, so runs, powers, merge tree
+//      and merge cost are those of the records;
+//   4. rows whose windows are equal may still differ later: every group of
+//      equal windows comes out of the merges in input order (every merge is
+//      stable), and k_rec_fix sorts each group by the rest of the row, ties
+//      by input index -- one CTA per group: a bitonic sort in shared memory
+//      up to REC_SMEM entries, a merge sort through a scratch array above;
+//   5. the rows move once, through the permutation (ps_gather_rows' kernel),
+//      instead of at every merge.
+#include "ps_internal.cuh"
+
+namespace ps {
+
+namespace {
+
+constexpr int REC_BLOCK = 256;
+constexpr uint32_t REC_SMEM = 2048;   // group entries sorted in shared memory
+
+// Row a sorts strictly before row b, comparing words w0 .. W-1; equal rows by index.
+__device__ __forceinline__ bool rec_less(const uint32_t* rec, uint32_t W, uint32_t w0, uint32_t a, uint32_t b)
+{
+    const uint32_t* ra = rec + (size_t)a * W;
+    const uint32_t* rb = rec + (size_t)b * W;
+    for (uint32_t w = w0; w < W; ++w) {
+        const uint32_t x = __ldg(ra + w), y = __ldg(rb + w);
+        if (x != y) return x < y;
+    }
+    return a < b;
+}
+
+}  // namespace
+
+// Descent mask (bit i: row i-1 > row i; bit 0 clear) and the shared prefix.
+__global__ void __launch_bounds__(REC_BLOCK) k_rec_scan(const uint32_t* rec, uint32_t W, unsigned long long n,
+                                                        uint32_t* mask, Ctr* C)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    const unsigned long long warps = ((unsigned long long)gridDim.x * REC_BLOCK) >> 5;
+    uint32_t lcp = W;
+    for (unsigned long long w = (((unsigned long long)blockIdx.x * REC_BLOCK) >> 5) + (threadIdx.x >> 5);
+         w * 32 < n; w += warps) {
+        const unsigned long long i = w * 32 + lane;
+        bool desc = false;
+        if (i > 0 && i < n) {
+            const uint32_t* ra = rec + (size_t)(i - 1) * W;
+            const uint32_t* rb = rec + (size_t)i * W;
+            uint32_t f = W;
+            for (uint32_t k = 0; k < W; ++k) {
+                const uint32_t x = __ldg(ra + k), y = __ldg(rb + k);
+                if (x != y) {
+                    f = k;
+                    desc = x > y;
+                    break;
+                }
+            }
+            lcp = min(lcp, f);
+        }
+        const uint32_t word = __ballot_sync(0xffffffffu, desc);
+        if (lane == 0) mask[w] = word;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lcp = min(lcp, __shfl_xor_sync(0xffffffffu, lcp, o));
+    if (lane == 0 && lcp < W) atomicMin(&C->rec_lcp, lcp);
+}
+
+// The window key of every row: word L (0 when every row is equal).
+__global__ void __launch_bounds__(REC_BLOCK) k_rec_key(const uint32_t* rec, uint32_t W, unsigned long long n,
+                                                       uint32_t* keys, const Ctr* C)
+{
+    const uint32_t L = *(volatile const uint32_t*)&C->rec_lcp;
+    const unsigned long long stride = (unsigned long long)gridDim.x * REC_BLOCK;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * REC_BLOCK + threadIdx.x; i < n; i += stride)
+        keys[i] = L < W ? __ldg(rec + (size_t)i * W + L) : 0u;
+}
+
+// Groups of equal windows (two or more rows): a thread per group start lists
+// it (start, end) -- only when the rows can still differ after word L.
+__global__ void __launch_bounds__(REC_BLOCK) k_rec_groups(const uint32_t* keys, uint32_t W, unsigned long long n,
+                                                          uint32_t* groups, uint32_t cap, Ctr* C)
+{
+    const uint32_t L = *(volatile const uint32_t*)&C->rec_lcp;
+    if (L >= W - 1 || *(volatile uint32_t*)&C->error) return;   // NONE: all rows equal
+    const unsigned long long stride = (unsigned long long)gridDim.x * REC_BLOCK;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * REC_BLOCK + threadIdx.x; i + 1 < n; i += stride) {
+        const uint32_t k = keys[i];
+        if (keys[i + 1] != k || (i > 0 && keys[i - 1] == k)) continue;
+        unsigned long long e = i + 2;
+        while (e < n && keys[e] == k) ++e;
+        const uint32_t at = atomicAdd(&C->rec_groups, 1u);
+        if (at < cap) {
+            groups[2 * at] = (uint32_t)i;
+            groups[2 * at + 1] = (uint32_t)e;
+        } else {
+            set_error(C, DERR_INTERNAL, 80);
+        }
+    }
+}
+
+// Sort one group's permutation entries by (row from word L + 1, index).
+__global__ void __launch_bounds__(REC_BLOCK) k_rec_fix(const uint32_t* rec, uint32_t W, uint32_t* perm,
+                                                       uint32_t* tmp, const uint32_t* groups, uint32_t cap, Ctr* C)
+{
+    __shared__ uint32_t s[REC_SMEM];
+    const uint32_t L = *(volatile const uint32_t*)&C->rec_lcp;
+    if (L >= W - 1 || *(volatile uint32_t*)&C->error) return;   // NONE: all rows equal
+    const uint32_t w0 = L + 1;
+    const uint32_t ng = min(*(volatile const uint32_t*)&C->rec_groups, cap);
+    const uint32_t tid = threadIdx.x;
+    for (uint32_t gi = blockIdx.x; gi < ng; gi += gridDim.x) {
+        const uint32_t a = groups[2 * gi], g = groups[2 * gi + 1] - a;
+        // blocks of up to REC_SMEM entries: bitonic sort in shared memory
+        for (uint32_t b0 = 0; b0 < g; b0 += REC_SMEM) {
+            const uint32_t m = min(REC_SMEM, g - b0);
+            uint32_t P = 2;
+            while (P < m) P <<= 1;
+            for (uint32_t x = tid; x < P; x += REC_BLOCK) s[x] = x < m ? perm[a + b0 + x] : NONE;
+            __syncthreads();
+            for (uint32_t k = 2; k <= P; k <<= 1) {
+                for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                    for (uint32_t x = tid; x < P; x += REC_BLOCK) {
+                        const uint32_t y = x ^ j;
+                        if (y > x) {
+                            const uint32_t u = s[x], v = s[y];
+                            // NONE (padding) sorts last
+                            const bool v_first = u == NONE ? v != NONE : (v != NONE && rec_less(rec, W, w0, v, u));
+                            const bool up = (x & k) == 0;
+                            if (up ? v_first : !v_first && u != v) {
+                                s[x] = v;
+                                s[y] = u;
+                            }
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            for (uint32_t x = tid; x < m; x += REC_BLOCK) perm[a + b0 + x] = s[x];
+            __syncthreads();
+        }
+        // larger groups: merge the sorted blocks pairwise, perm <-> tmp
+        uint32_t* src = perm + a;
+        uint32_t* dst = tmp + a;
+        for (uint32_t w = REC_SMEM; w < g; w <<= 1) {
+            for (uint32_t o0 = tid * 16u; o0 < g; o0 += REC_BLOCK * 16u) {
+                const uint32_t x = o0 - o0 % (2 * w);             // the pair [x, x + w) + [x + w, x + 2w)
+                const uint32_t na = min(w, g - x), nb = g - x > w ? min(w, g - x - w) : 0u;
+                const uint32_t* A = src + x;
+                const uint32_t* B = src + x + na;
+                const uint32_t d = o0 - x;
+                uint32_t lo = d > nb ? d - nb : 0u, hi = min(d, na);
+                while (lo < hi) {                                  // A wins ties: take A while !(B < A)
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (!rec_less(rec, W, w0, B[d - 1 - mid], A[mid])) lo = mid + 1; else hi = mid;
+                }
+                uint32_t ia = lo, ib = d - lo;
+                const uint32_t end = min(o0 + 16u, x + na + nb);
+                for (uint32_t o = o0; o < end; ++o) {
+                    const bool take_a = ia < na && (ib >= nb || !rec_less(rec, W, w0, B[ib], A[ia]));
+                    dst[o] = take_a ? A[ia++] : B[ib++];
+                }
+            }
+            __syncthreads();
+            uint32_t* t = src;
+            src = dst;
+            dst = t;
+        }
+        if (src != perm + a)
+            for (uint32_t x = tid; x < g; x += REC_BLOCK) perm[a + x] = src[x];
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_records_prepare(const uint32_t* rec, uint32_t W, unsigned long long n, uint32_t* mask,
+                                   uint32_t* keys, Ctr* C, int grid, cudaStream_t s)
+{
+    k_rec_scan<<<grid, REC_BLOCK, 0, s>>>(rec, W, n, mask, C);
+    k_rec_key<<<grid, REC_BLOCK, 0, s>>>(rec, W, n, keys, C);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_records_fix(const uint32_t* rec, uint32_t W, unsigned long long n, const uint32_t* keys,
+                               uint32_t* perm, uint32_t* tmp, uint32_t* groups, uint32_t cap, Ctr* C, int grid,
+                               cudaStream_t s)
+{
+    k_rec_groups<<<grid, REC_BLOCK, 0, s>>>(keys, W, n, groups, cap, C);
+    k_rec_fix<<<grid, REC_BLOCK, 0, s>>>(rec, W, perm, tmp, groups, cap, C);
+    return cudaGetLastError();
+}
+
+}  // namespace ps

@@ -350,6 +350,27 @@ __device__ __forceinline__ unsigned long long ones31(unsigned long long x)
     return r & (r >> 15);                  // 31
 }
 
+// The same bitmask from a precomputed descent mask (bit i <-> position i of
+// the instance; records compare whole rows, which the keys cannot): chunks
+// start at multiples of 32, so the chunk's words are whole mask words; the
+// end n counts as a descent, positions past it as none.
+__device__ __forceinline__ void bits_from_mask(const ChunkView& v, const uint32_t* mask, uint32_t* bits)
+{
+    for (int w = threadIdx.x; w < RUN_WORDS; w += RUN_BLOCK) {
+        const unsigned long long P0 = (unsigned long long)v.B + 32u * (unsigned)w;
+        uint32_t word = 0;
+        if (P0 < v.n) word = mask[(P0 >> 5)];
+        // clear positions >= n, then set position n
+        if (P0 + 32 > v.n) {
+            const uint32_t k = P0 < v.n ? (uint32_t)(v.n - P0) : 0u;   // positions of the word below n
+            word &= k ? (0xffffffffu >> (32u - k)) : 0u;
+            if (P0 <= v.n && v.n < P0 + 32) word |= 1u << (uint32_t)(v.n - P0);
+        }
+        if (P0 == 0) word &= ~1u;   // position 0 has no predecessor
+        bits[w] = word;
+    }
+}
+
 // Can any step from inside the chunk be natural?  Only if a run start s in
 // the chunk is followed by minrun - 1 >= 31 positions without a descent (or,
 // with decreasing runs, 31 positions with one).  Each thread looks for 31
@@ -480,7 +501,7 @@ __global__ void __launch_bounds__(RUN_BLOCK) k_runs(Job J)
     if (g0 < g1) {
         vn = chunk_view(J, g0, qi);
         wn = window_of(vn);
-        stage_keys(vn, wn, keys[0]);
+        if (!J.desc_mask) stage_keys(vn, wn, keys[0]);
     }
     for (uint32_t g = g0; g < g1; ++g) {
         const ChunkView v = vn;
@@ -490,13 +511,16 @@ __global__ void __launch_bounds__(RUN_BLOCK) k_runs(Job J)
         if (g + 1 < g1) {
             vn = chunk_view(J, g + 1, qi);
             wn = window_of(vn);
-            stage_keys(vn, wn, keys[buf ^ 1]);
-            cp_async_wait<1>();
+            if (!J.desc_mask) {
+                stage_keys(vn, wn, keys[buf ^ 1]);
+                cp_async_wait<1>();
+            }
         } else {
             cp_async_wait<0>();
         }
         __syncthreads();
-        bits_from_keys(v, w, keys[buf], bits);
+        if (J.desc_mask) bits_from_mask(v, J.desc_mask, bits);
+        else bits_from_keys(v, w, keys[buf], bits);
         __syncthreads();
         const bool desc = J.desc_runs != 0;
         const bool walk = chunk_may_natural(v, bits, desc);
