@@ -15,6 +15,10 @@ permutation is produced):
                the decreasing-run variant of Sec. 5 (PS_FLAG_DESCENDING_RUNS);
                the line also carries the rate of the plain rule on the same
                input
+  records_2^23 one step = two record sorts of n = 2^23 rows of 30 words
+               (randomBlob30 and zeroBlob30, the paper's blob types, values in
+               [100, 10^9], seed 1) with the sorted rows written out; rate in
+               records/s
   bands_2^24   one step = one sort of n = 2^24: sorted blocks of 2^13 keys in
                descending value bands; with --storage vm the merges splice
                whole pages through the page table (stats: pages_spliced)
@@ -60,6 +64,7 @@ WORKLOADS = {
     "hbm_2^28": [("uniform", 1 << 28, 2)],
     "updown_2^24": [("updown", 1 << 24, 1)],
     "bands_2^24": [("bands", 1 << 24, 1)],
+    "records_2^23": None,
     "batched_4096": None,
     "serving": None,
 }
@@ -78,6 +83,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="pingpong", choices=["pingpong", "vm"],
                     help="run storage of the plain workloads: Pingpong (n-element scratch) or VM pages")
+    ap.add_argument("--key-type", default="u32", choices=["u32", "i32", "f32"],
+                    help="plain workloads: order the same 32-bit patterns as unsigned, signed or float keys")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample-seconds", type=float, default=20.0)
@@ -182,7 +189,7 @@ def traffic_from_profile(workload):
         return None
 
 
-def cpu_oracle_rate(data, budget_s, descending_runs=False):
+def cpu_oracle_rate(data, budget_s, descending_runs=False, key_type="u32"):
     """Single-threaded oracle throughput on a bounded sample (elements/s)."""
     import oracle
 
@@ -192,7 +199,7 @@ def cpu_oracle_rate(data, budget_s, descending_runs=False):
         if spent > budget_s and done:
             break
         t0 = time.perf_counter()
-        oracle.powersort(keys, descending_runs=descending_runs)
+        oracle.powersort(keys, descending_runs=descending_runs, key_type=key_type)
         dt = time.perf_counter() - t0
         spent += dt
         done += n
@@ -204,6 +211,8 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    if args.workload == "records_2^23":
+        return run_reference_records(args)
     if args.workload == "batched_4096":
         from paper_2605_27147_gb300 import inputs as _inp
 
@@ -227,7 +236,7 @@ def run_reference(args):
         d, n, s, keys = data[i % len(data)]
         t0 = time.perf_counter()
         for k in (keys if isinstance(keys, list) else [keys]):
-            oracle.powersort(k, descending_runs=desc)
+            oracle.powersort(k, descending_runs=desc, key_type=args.key_type)
         dt = time.perf_counter() - t0
         if i >= args.warmup:
             times.append(dt)
@@ -244,6 +253,33 @@ def run_reference(args):
         "config": {"workload": args.workload, "note": "CPU oracle on host cores (bounded sample per step)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_records(args, m=1 << 19, words=30):
+    """The oracle on records: each step sorts the first 2^19 rows of one set."""
+    import oracle
+    from paper_2605_27147_gb300 import inputs
+
+    oracle.build()
+    sets = [inputs.records(k, m, 1, words=words) for k in ("random", "zero")]
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.powersort_records(sets[i % 2])
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    value = m * len(times) / sum(times)
+    line = {
+        "impl": "reference", "metric": "records/s (30-word rows, lexicographic), 1xGB300", "value": value,
+        "unit": "records/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * sum(times) / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "records_2^23", "note": "CPU oracle, first 2^19 rows per step"},
+        "cpu_baseline": {"value": value, "unit": "records/s", "cores": 1, "kind": "oracle",
+                         "sample": "first 2^19 rows of randomBlob30 / zeroBlob30, alternating"},
+        "e2e": {"value": value, "unit": "records/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
@@ -425,6 +461,98 @@ def run_batched(args):
         dist.destroy_process_group()
 
 
+def run_records(args, n=1 << 23, words=30):
+    """Record sorts: rows of 30 words, lexicographic (ps_sort_records)."""
+    import torch
+
+    from paper_2605_27147_gb300 import binding, inputs, replicas
+
+    world, rank, local = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    kinds = ("random", "zero")
+    host = [inputs.records(k, n, 1 + replicas.replica_seed(0, rank), words=words) for k in kinds]
+    recs = [torch.from_numpy(h.view(np.int32)).to(dev) for h in host]
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    out = torch.empty((n, words), dtype=torch.int32, device=dev)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = binding.Context(n, want_perm=True, flags=binding.PS_FLAG_RECORDS | binding.PS_FLAG_TIMING, device=local,
+                          stream=stream)
+    for _ in range(args.warmup):
+        for r in recs:
+            ctx.sort_records(r, perm, out)
+    ctx.sync()
+    times, merge_ms, merge_bytes, phases = [], 0.0, 0, []
+    stats = {}
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            for i, r in enumerate(recs):
+                flush.fill_(i)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx.sort_records(r, perm, out)
+                e1.record(stream)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+                ph = ctx.phase_times()
+                phases.append(ph)
+                merge_ms += ph["merge_rounds"]
+    for i, r in enumerate(recs):
+        st = ctx.sort_records(r, perm, out, stats=True)
+        stats[kinds[i]] = {k: st[k] for k in ("runs", "merge_cost", "rounds", "hbm_merge_elems")}
+        merge_bytes += BYTES_PER_MERGED_ELEM * st["hbm_merge_elems"] * args.steps
+        if i == len(recs) - 1:
+            # the last sort's rows must be in lexicographic order
+            o = out.cpu().numpy().view(np.uint32)
+            d = o[1:] != o[:-1]
+            f = np.argmax(d, axis=1)
+            rows = np.arange(n - 1)
+            assert np.all(~d.any(axis=1) | (o[1:][rows, f] > o[:-1][rows, f]))
+    total_ms = replicas.max_over_ranks(sum(times), dist, dev)
+    value = replicas.job_rate(n * len(times), world, total_ms)
+    peak, peak_kind = peaks()
+    achieved = merge_bytes / (merge_ms / 1000.0) / 1e9
+    row_bytes = 3 * words * 4 * n * len(times)     # rows read by the scan, read and written by the gather
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        import oracle
+
+        oracle.build()
+        m = 1 << 19
+        t0 = time.perf_counter()
+        for h in host:
+            oracle.powersort_records(h[:m])
+        dt = time.perf_counter() - t0
+        cpu = {"value": m * len(host) / dt, "unit": "records/s", "cores": 1, "kind": "oracle",
+               "sample": f"the first 2^19 rows of each record set ({dt:.1f} s of one host core)"}
+    line = {
+        "metric": "records/s (30-word rows, lexicographic), 1xGB300", "value": value, "unit": "records/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "records_2^23", "instances": [f"{k}Blob30 n=2^23 seed 1" for k in kinds],
+                   "outputs": "stable permutation + the rows in order", "l2": "flushed before every timed sort"},
+        "roofline": {"kernel": "k_merge_rounds (window keys)", "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None},
+        "kernels": {"phase_ms_per_step": {k: sum(p[k] for p in phases) / args.steps for k in binding.PHASES},
+                    "row_gbs": row_bytes / (sum(times) / 1000.0) / 1e9},
+        "stats": stats, "cpu_baseline": cpu, "e2e": None, "clocks": clk.summary(),
+        "gpu_launches": None,
+    }
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 def run_serving(args, rate=2000.0, duration=10.0, budget=64 << 30):
     # Elements per batch are capped so that a burst cannot build one long
     # batch (latency grows with the batch; the offered load is far below
@@ -527,6 +655,8 @@ def main():
         return run_batched(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "records_2^23":
+        return run_records(args)
 
     import torch
 
@@ -553,8 +683,9 @@ def main():
     mode = binding.PS_MODE_VM if args.storage == "vm" else binding.PS_MODE_PINGPONG
     desc = args.workload in DESCENDING_WORKLOADS
     variant = binding.PS_FLAG_DESCENDING_RUNS if desc else 0
+    key_type = {"u32": binding.PS_KEY_U32, "i32": binding.PS_KEY_I32, "f32": binding.PS_KEY_F32}[args.key_type]
     ctx = binding.Context(max_n, mode=mode, want_perm=True, flags=binding.PS_FLAG_TIMING | variant,
-                          device=local, stream=stream)
+                          key_type=key_type, device=local, stream=stream)
 
     def one_sort(i, timed):
         n = data[i][1]
@@ -617,7 +748,7 @@ def main():
     plain_rule = None
     if desc:
         # the same inputs and timing without the variant: the plain rule's rate
-        pctx = binding.Context(max_n, mode=mode, want_perm=True, device=local, stream=stream)
+        pctx = binding.Context(max_n, mode=mode, want_perm=True, key_type=key_type, device=local, stream=stream)
         pms, pel = 0.0, 0
         for step in range(args.warmup + args.steps):
             for i in range(len(data)):
@@ -643,7 +774,7 @@ def main():
     e2e = None
     if not args.no_e2e:
         hctx = binding.Context(max_n, mode=mode, want_perm=True, flags=binding.PS_FLAG_HOST_IO | variant,
-                               device=local, stream=stream)
+                               key_type=key_type, device=local, stream=stream)
         hk = torch.empty(max_n, dtype=torch.int32, pin_memory=True)
         hp = torch.empty(max_n, dtype=torch.int32, pin_memory=True)
         src = [torch.from_numpy(k.view(np.int32)) for _, _, _, k in data]
@@ -663,9 +794,16 @@ def main():
                 esum += n
                 bi += 4 * n
                 bo += 8 * n
-        # the result of the last e2e sort must be the sorted keys
+        # the result of the last e2e sort must be the sorted keys (in the key order)
         last_n = data[-1][1]
-        assert np.all(np.diff(hk[:last_n].numpy().view(np.uint32).astype(np.int64)) >= 0)
+        out = hk[:last_n].numpy()
+        if args.key_type == "i32":
+            assert np.all(np.diff(out.view(np.int32).astype(np.int64)) >= 0)
+        elif args.key_type == "u32":
+            assert np.all(np.diff(out.view(np.uint32).astype(np.int64)) >= 0)
+        else:   # totalOrder: as signed integers, negatives by reversed magnitude
+            b = out.view(np.int32).astype(np.int64)
+            assert np.all(np.diff(np.where(b < 0, -(b & 0x7fffffff) - 1, b)) >= 0)
         hctx.close()
         e2e = {"value": esum * world / tsum, "unit": UNIT, "h2d_bytes_per_step": bi // e2e_steps,
                "d2h_bytes_per_step": bo // e2e_steps, "steps": e2e_steps,
@@ -675,7 +813,7 @@ def main():
     if rank == 0 and not args.no_cpu:
         sample = data if args.workload == "plain_2^24" else [(d, 1 << 24, s, k[: 1 << 24].copy())
                                                            for d, n, s, k in data]
-        rate, spent, used = cpu_oracle_rate(sample, args.cpu_sample_seconds, desc)
+        rate, spent, used = cpu_oracle_rate(sample, args.cpu_sample_seconds, desc, args.key_type)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{used} ({spent:.1f} s of one host core)"}
 
@@ -692,6 +830,8 @@ def main():
             "instances": [f"{d} n=2^{int(np.log2(n))} seed {s}" for d, n, s, _ in data],
             "outputs": "sorted keys + stable permutation (uint32)",
             "storage": args.storage,
+            "keys": {"u32": "unsigned 32-bit", "i32": "signed 32-bit (two's complement)",
+                     "f32": "IEEE 754 binary32, totalOrder"}[args.key_type],
             "runs": "ascending and strictly decreasing (Sec. 5 variant)" if desc else "ascending (Sec. 5 rule)",
             "scratch_bytes": hbm[0]["scratch_bytes"],
             "peak_pool_pages": hbm[0]["peak_pages"],
