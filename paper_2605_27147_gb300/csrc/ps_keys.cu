@@ -14,9 +14,13 @@
 // Both maps are elementwise and in place: 8 bytes per element of traffic.
 //
 // Payloads.  The sort's permutation gives every row's source: row r of the
-// output is row perm[r] of the input.  A thread copies a row of up to 16
-// bytes, a warp a wider one, with the widest word (16, 4 or 1 bytes) that
-// both arrays' alignment and the row width allow.
+// output is row perm[r] of the input.  One instance of rows that are whole
+// words goes by tiles: a CTA reads 256 permutation entries,
+// then copies the tile's words (16, 8 or 4 bytes, as alignment allows) in
+// output order, consecutive threads on consecutive words (coalesced
+// stores, every load independent).  Otherwise
+// a thread copies a row of up to 16 bytes, a warp a wider one, with the
+// widest word (16, 4 or 1 bytes) that the alignment and the width allow.
 #include "ps_internal.cuh"
 
 namespace ps {
@@ -117,6 +121,42 @@ __global__ void __launch_bounds__(256) k_gather_rows(const uint32_t* perm, const
     }
 }
 
+template <typename Wd>
+__global__ void __launch_bounds__(256) k_gather_tiled(const uint32_t* perm, unsigned long long n, const Wd* src,
+                                                      Wd* dst, uint32_t wpr, Ctr* C)
+{
+    __shared__ uint32_t sp[256];
+    const uint32_t tid = threadIdx.x;
+    const uint32_t drow = 256u / wpr, dword = 256u % wpr;
+    for (unsigned long long t0 = (unsigned long long)blockIdx.x * 256; t0 < n;
+         t0 += (unsigned long long)gridDim.x * 256) {
+        const uint32_t rows = (uint32_t)min(256ull, n - t0);
+        if (tid < rows) {
+            uint32_t p = perm[t0 + tid];
+            if (p >= n) {
+                set_error(C, DERR_INVAL, 71);
+                p = NONE;
+            }
+            sp[tid] = p;
+        }
+        __syncthreads();
+        const uint32_t total = rows * wpr;
+        uint32_t row = tid / wpr, word = tid % wpr;
+#pragma unroll 8
+        for (uint32_t q = tid; q < total; q += 256) {
+            const uint32_t p = sp[row];
+            if (p != NONE) dst[(t0 + row) * wpr + word] = src[(unsigned long long)p * wpr + word];
+            row += drow;
+            word += dword;
+            if (word >= wpr) {
+                word -= wpr;
+                ++row;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 cudaError_t launch_key_map(const Job& J, bool forward, int grid, cudaStream_t s)
 {
     k_key_map<<<grid, 256, 0, s>>>(J, forward ? 1 : 0);
@@ -127,8 +167,20 @@ cudaError_t launch_gather_rows(const uint32_t* perm, const unsigned long long* o
                                unsigned long long n, unsigned long long max_total, const void* src, void* dst,
                                uint32_t row_bytes, Ctr* ctr, int grid, cudaStream_t s)
 {
-    k_gather_rows<<<grid, 256, 0, s>>>(perm, offsets, count, n, max_total, static_cast<const unsigned char*>(src),
-                                       static_cast<unsigned char*>(dst), row_bytes, ctr);
+    const uintptr_t al = reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst) | row_bytes;
+    if (!offsets && (al & 15u) == 0) {
+        k_gather_tiled<uint4><<<grid, 256, 0, s>>>(perm, n, static_cast<const uint4*>(src), static_cast<uint4*>(dst),
+                                                   row_bytes >> 4, ctr);
+    } else if (!offsets && (al & 7u) == 0) {
+        k_gather_tiled<uint2><<<grid, 256, 0, s>>>(perm, n, static_cast<const uint2*>(src), static_cast<uint2*>(dst),
+                                                   row_bytes >> 3, ctr);
+    } else if (!offsets && (al & 3u) == 0) {
+        k_gather_tiled<uint32_t><<<grid, 256, 0, s>>>(perm, n, static_cast<const uint32_t*>(src),
+                                                      static_cast<uint32_t*>(dst), row_bytes >> 2, ctr);
+    } else {
+        k_gather_rows<<<grid, 256, 0, s>>>(perm, offsets, count, n, max_total, static_cast<const unsigned char*>(src),
+                                           static_cast<unsigned char*>(dst), row_bytes, ctr);
+    }
     return cudaGetLastError();
 }
 

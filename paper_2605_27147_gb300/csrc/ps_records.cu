@@ -29,6 +29,7 @@ namespace {
 
 constexpr int REC_BLOCK = 256;
 constexpr uint32_t REC_SMEM = 2048;   // group entries sorted in shared memory
+constexpr uint32_t REC_TILE_WORDS = 64;   // rows up to this width are scanned through shared memory
 
 // Row a sorts strictly before row b, comparing words w0 .. W-1; equal rows by index.
 __device__ __forceinline__ bool rec_less(const uint32_t* rec, uint32_t W, uint32_t w0, uint32_t a, uint32_t b)
@@ -44,7 +45,52 @@ __device__ __forceinline__ bool rec_less(const uint32_t* rec, uint32_t W, uint32
 
 }  // namespace
 
-// Descent mask (bit i: row i-1 > row i; bit 0 clear) and the shared prefix.
+// Descent mask (bit i: row i-1 > row i; bit 0 clear) and the shared prefix,
+// for rows of at most REC_TILE_WORDS words: a CTA stages a tile of 256 rows
+// and the row before it (contiguous words, coalesced loads), then every
+// thread compares its row with the one before in shared memory.
+__global__ void __launch_bounds__(REC_BLOCK) k_rec_scan_tiled(const uint32_t* rec, uint32_t W, unsigned long long n,
+                                                              uint32_t* mask, Ctr* C)
+{
+    extern __shared__ uint32_t rows[];   // (REC_BLOCK + 1) * W words
+    const uint32_t tid = threadIdx.x, lane = tid & 31u;
+    uint32_t lcp = W;
+    for (unsigned long long t0 = (unsigned long long)blockIdx.x * REC_BLOCK; t0 < n;
+         t0 += (unsigned long long)gridDim.x * REC_BLOCK) {
+        // rows t0 - 1 .. t0 + 255 (those that exist) at slots 0 .. 256
+        const unsigned long long r0 = t0 ? t0 - 1 : 0ull;
+        const unsigned long long r1 = min(t0 + REC_BLOCK, n);
+        const uint32_t slot0 = t0 ? 0u : 1u;
+        const uint32_t nw = (uint32_t)(r1 - r0) * W;
+        const uint32_t* g = rec + (size_t)r0 * W;
+        uint32_t* d = rows + slot0 * W;
+        for (uint32_t x = tid; x < nw; x += REC_BLOCK) d[x] = __ldg(g + x);
+        __syncthreads();
+        const unsigned long long i = t0 + tid;
+        bool desc = false;
+        if (i > 0 && i < n) {
+            const uint32_t* ra = rows + (size_t)tid * W;   // row i - 1 at slot tid
+            const uint32_t* rb = ra + W;                    // row i at slot tid + 1
+            uint32_t f = W;
+            for (uint32_t k = 0; k < W; ++k) {
+                if (ra[k] != rb[k]) {
+                    f = k;
+                    desc = ra[k] > rb[k];
+                    break;
+                }
+            }
+            lcp = min(lcp, f);
+        }
+        const uint32_t word = __ballot_sync(0xffffffffu, desc);
+        if (lane == 0 && i < n) mask[i >> 5] = word;
+        __syncthreads();
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lcp = min(lcp, __shfl_xor_sync(0xffffffffu, lcp, o));
+    if (lane == 0 && lcp < W) atomicMin(&C->rec_lcp, lcp);
+}
+
+// The same for wider rows, straight from global memory (a warp per 32 rows).
 __global__ void __launch_bounds__(REC_BLOCK) k_rec_scan(const uint32_t* rec, uint32_t W, unsigned long long n,
                                                         uint32_t* mask, Ctr* C)
 {
@@ -186,7 +232,14 @@ __global__ void __launch_bounds__(REC_BLOCK) k_rec_fix(const uint32_t* rec, uint
 cudaError_t launch_records_prepare(const uint32_t* rec, uint32_t W, unsigned long long n, uint32_t* mask,
                                    uint32_t* keys, Ctr* C, int grid, cudaStream_t s)
 {
-    k_rec_scan<<<grid, REC_BLOCK, 0, s>>>(rec, W, n, mask, C);
+    if (W <= REC_TILE_WORDS) {
+        const size_t smem = (size_t)(REC_BLOCK + 1) * W * sizeof(uint32_t);
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(k_rec_scan_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_rec_scan_tiled<<<grid, REC_BLOCK, smem, s>>>(rec, W, n, mask, C);
+    } else {
+        k_rec_scan<<<grid, REC_BLOCK, 0, s>>>(rec, W, n, mask, C);
+    }
     k_rec_key<<<grid, REC_BLOCK, 0, s>>>(rec, W, n, keys, C);
     return cudaGetLastError();
 }
