@@ -9,6 +9,7 @@ from .oracle import (  # noqa: F401
     power,
     stable_sort,
     powersort,
+    powersort_keys64,
     powersort_records,
     stable_sort_records,
     powersort_vm,

@@ -12,6 +12,8 @@ all arithmetic is in the C source, which follows the paper:
 * :func:`stable_sort`  -- the plain definition of the result (stable order)
 * :func:`powersort`    -- Algorithm 1 with Pingpong storage (Sec. 3)
 * :func:`powersort_vm` -- Algorithm 1 with virtual-memory storage (Sec. 4)
+* :func:`powersort_keys64` -- Algorithm 1 on 64-bit keys ("u64", "i64" or
+  "f64": unsigned, two's complement, IEEE 754 binary64 totalOrder)
 * :func:`powersort_records`, :func:`stable_sort_records` -- the same for
   records of several 32-bit words ordered lexicographically (the paper's blob
   types, Sec. 5 "Input data types")
@@ -109,6 +111,9 @@ def _declare(lib):
     lib.oracle_power.argtypes = [ctypes.c_uint64] * 4
     lib.oracle_stable_sort.restype = ctypes.c_int
     lib.oracle_stable_sort.argtypes = [u32p, ctypes.c_uint64, u32p, u32p]
+    lib.oracle_powersort_keys64.restype = ctypes.c_int
+    lib.oracle_powersort_keys64.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.c_uint64, u32p, u32p, u8p, u32p,
+                                            ctypes.c_uint32, ctypes.POINTER(_Stats)]
     lib.oracle_powersort_records.restype = ctypes.c_int
     lib.oracle_powersort_records.argtypes = [u32p, ctypes.c_uint32, ctypes.c_uint64, u32p, u32p, u8p, u32p,
                                              ctypes.c_uint32, ctypes.POINTER(_Stats)]
@@ -258,3 +263,31 @@ def stable_sort_records(rec: np.ndarray, lib=None) -> np.ndarray:
     if n and lib.oracle_stable_sort_records(_ptr(rec, ctypes.c_uint32), words, n, _ptr(perm, ctypes.c_uint32)):
         raise MemoryError("oracle_stable_sort_records")
     return perm
+
+
+def powersort_keys64(keys: np.ndarray, key_type: str = "u64", lib=None, descending_runs: bool = False) -> OracleResult:
+    """Algorithm 1 on 64-bit keys given as their bit patterns (uint64)."""
+    lib = lib or _load()
+    keys = np.ascontiguousarray(keys, dtype=np.uint64)
+    n = keys.size
+    perm = np.empty(n, np.uint32)
+    runs = np.empty(n + 2, np.uint32)
+    pw = np.zeros(max(n, 1), np.uint8)
+    mg = np.empty((max(n, 1), 3), np.uint32)
+    st = _Stats()
+    opt = {"u64": 0, "i64": 2, "f64": 4}[key_type] | (DESCENDING_RUNS if descending_runs else 0)
+    rc = lib.oracle_powersort_keys64(keys.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), n,
+                                     _ptr(perm, ctypes.c_uint32), _ptr(runs, ctypes.c_uint32), _ptr(pw, ctypes.c_uint8),
+                                     _ptr(mg, ctypes.c_uint32), opt, ctypes.byref(st))
+    if rc:
+        raise MemoryError("oracle_powersort_keys64")
+    stats = {name: int(getattr(st, name)) for name, _ in _Stats._fields_}
+    r = stats["runs"]
+    return OracleResult(
+        keys=keys[perm],
+        perm=perm,
+        run_starts=runs[: r + 1].copy() if n else np.zeros(1, np.uint32),
+        powers=pw[: max(r - 1, 0)].copy(),
+        merges=mg[: stats["merges"]].copy(),
+        stats=stats,
+    )

@@ -29,6 +29,10 @@
  *                        as two's-complement integers / IEEE-754 binary32
  *                        values ordered by the standard's totalOrder
  *   oracle_stable_sort_ex the stable-sort definition under those key orders
+ *   oracle_powersort_keys64
+ *                        64-bit keys (unsigned, two's complement, or IEEE 754
+ *                        binary64 under totalOrder): Algorithm 1 on indices,
+ *                        comparing the keys by those definitions
  *   oracle_powersort_records, oracle_stable_sort_records
  *                        the same for records of `words` 32-bit words ordered
  *                        lexicographically (the paper's blob types, Sec. 5
@@ -78,6 +82,10 @@ typedef struct {
 #define ORACLE_KEY_I32 2u
 #define ORACLE_KEY_F32 4u
 #define ORACLE_RECORDS 8u
+#define ORACLE_KEYS64 16u   /* with ORACLE_KEY_I32 / ORACLE_KEY_F32: int64 / binary64 */
+
+/* The 64-bit keys of the running call (ORACLE_KEYS64). */
+static const uint64_t* g_keys64;
 
 /* The records of the running call (ORACLE_RECORDS): row i is
  * g_rec[i * g_rec_words .. (i + 1) * g_rec_words). */
@@ -98,6 +106,18 @@ static uint32_t g_key_order;
  *                  ... < -0 < +0 < ... < +inf < +NaN. */
 static int key_gt(uint32_t a, uint32_t b)
 {
+    if (g_key_order & ORACLE_KEYS64) {
+        /* indices of 64-bit keys; the same three orders at 64 bits */
+        const uint64_t x = g_keys64[a], y = g_keys64[b];
+        if (g_key_order & ORACLE_KEY_I32) return (int64_t)x > (int64_t)y;
+        if (g_key_order & ORACLE_KEY_F32) {
+            const int nx = (int)(x >> 63), ny = (int)(y >> 63);
+            if (nx != ny) return ny;
+            const uint64_t mx = x & 0x7fffffffffffffffull, my = y & 0x7fffffffffffffffull;
+            return nx ? mx < my : mx > my;
+        }
+        return x > y;
+    }
     if (g_key_order & ORACLE_RECORDS) {
         /* lexicographic: the first differing word (as unsigned) decides */
         const uint32_t* ra = g_rec + (uint64_t)a * g_rec_words;
@@ -161,7 +181,7 @@ static int cmp_pair(const void* x, const void* y)
 int oracle_stable_sort_ex(const uint32_t* keys, uint64_t n, uint32_t options, uint32_t* keys_out,
                           uint32_t* perm_out)
 {
-    g_key_order = options & (ORACLE_KEY_I32 | ORACLE_KEY_F32 | ORACLE_RECORDS);
+    g_key_order = options & (ORACLE_KEY_I32 | ORACLE_KEY_F32 | ORACLE_RECORDS | ORACLE_KEYS64);
     if (n == 0) return 0;
     kv_pair* v = (kv_pair*)malloc(n * sizeof(kv_pair));
     if (!v) return -1;
@@ -290,7 +310,7 @@ int oracle_powersort_ex(uint32_t* key, uint32_t* perm, uint64_t n, uint32_t* run
                         uint8_t* powers, uint32_t* merges, uint32_t options, oracle_stats* st)
 {
     memset(st, 0, sizeof(*st));
-    g_key_order = options & (ORACLE_KEY_I32 | ORACLE_KEY_F32 | ORACLE_RECORDS);
+    g_key_order = options & (ORACLE_KEY_I32 | ORACLE_KEY_F32 | ORACLE_RECORDS | ORACLE_KEYS64);
     st->n = n;
     st->minrun = oracle_minrun(n);
     for (uint64_t x = 0; x < n; ++x) perm[x] = (uint32_t)x;
@@ -640,7 +660,7 @@ int oracle_powersort_vm_ex(uint32_t* key, uint32_t* perm, uint64_t n, uint64_t p
                            uint32_t options, oracle_stats* st)
 {
     memset(st, 0, sizeof(*st));
-    g_key_order = options & (ORACLE_KEY_I32 | ORACLE_KEY_F32 | ORACLE_RECORDS);
+    g_key_order = options & (ORACLE_KEY_I32 | ORACLE_KEY_F32 | ORACLE_RECORDS | ORACLE_KEYS64);
     st->n = n;
     st->minrun = oracle_minrun(n);
     st->page_size = (uint32_t)page_size;
@@ -768,6 +788,22 @@ int oracle_stable_sort_records(const uint32_t* rec, uint32_t words, uint64_t n, 
     g_rec = rec;
     g_rec_words = words;
     int rc = oracle_stable_sort_ex(idx, n, ORACLE_RECORDS, NULL, perm_out);
+    free(idx);
+    return rc;
+}
+
+/* 64-bit keys: Algorithm 1 on the indices 0..n-1, comparing keys[i] by the
+ * order `options` names (0: unsigned, ORACLE_KEY_I32: int64, ORACLE_KEY_F32:
+ * binary64 totalOrder; ORACLE_DESCENDING_RUNS may be added).  perm receives
+ * the stable order. */
+int oracle_powersort_keys64(const uint64_t* keys, uint64_t n, uint32_t* perm, uint32_t* run_starts,
+                            uint8_t* powers, uint32_t* merges, uint32_t options, oracle_stats* st)
+{
+    uint32_t* idx = (uint32_t*)malloc((n ? n : 1) * sizeof(uint32_t));
+    if (!idx) return -1;
+    for (uint64_t i = 0; i < n; ++i) idx[i] = (uint32_t)i;
+    g_keys64 = keys;
+    int rc = oracle_powersort_ex(idx, perm, n, run_starts, powers, merges, options | ORACLE_KEYS64, st);
     free(idx);
     return rc;
 }

@@ -48,6 +48,9 @@ MUTATIONS = {
                                       "if (g_key_order & ORACLE_KEY_I32) return a > b;"),
     "negative floats not reversed": ("return na ? ma < mb : ma > mb;", "return ma > mb;"),
     "float signs in the wrong order": ("if (na != nb) return nb;", "if (na != nb) return na;"),
+    "int64 keys compared unsigned": ("if (g_key_order & ORACLE_KEY_I32) return (int64_t)x > (int64_t)y;",
+                                     "if (g_key_order & ORACLE_KEY_I32) return x > y;"),
+    "negative doubles not reversed": ("return nx ? mx < my : mx > my;", "return mx > my;"),
     "records skip their first word": ("for (uint32_t w = 0; w < g_rec_words; ++w)",
                                       "for (uint32_t w = 1; w < g_rec_words; ++w)"),
     "records compare the wrong way": ("if (ra[w] != rb[w]) return ra[w] > rb[w];",
@@ -117,6 +120,13 @@ def run_pins(lib):
         bits[int(idx)] = int(b, 16)
     r = oracle.powersort(bits, lib=lib, key_type="f32")
     assert r.perm.tolist() == [int(idx) for rank, idx, b in rows]
+    # 64-bit keys: numpy's stable argsort
+    k64 = (ik.astype(np.int64) << np.int64(20)) - np.int64(12345)
+    r = oracle.powersort_keys64(k64.view(np.uint64), "i64", lib=lib)
+    assert np.array_equal(r.perm, np.argsort(k64, kind="stable"))
+    f64 = k64.astype(np.float64) * 1e-7
+    r = oracle.powersort_keys64(f64.view(np.uint64), "f64", lib=lib)
+    assert np.array_equal(r.perm, np.argsort(f64, kind="stable"))
     # records: numpy's stable lexsort
     rec = inputs.records("few", 3000, 2, words=5)
     r = oracle.powersort_records(rec, lib=lib)
