@@ -99,8 +99,9 @@ typedef struct ps_config {
  * The result is the same stable sort; the runs, powers and merge tree are
  * those of the variant. */
 #define PS_FLAG_DESCENDING_RUNS 4u
-/* Allocate the arrays ps_sort_records needs (about 13 bytes per element of
- * max_n: window keys, descent mask, group list, merge scratch). */
+/* Allocate the arrays ps_sort_records and ps_sort_keys64 need (about 21
+ * bytes per element of max_n: window keys, descent mask, group list, merge
+ * scratch, the sorted 64-bit rows). */
 #define PS_FLAG_RECORDS 8u
 #define PS_RECORD_MAX_WORDS 1024u
 
@@ -180,6 +181,17 @@ PS_API ps_status ps_gather_rows(ps_ctx* ctx, const uint32_t* d_perm, const uint6
  * Asynchronous unless stats is given. */
 PS_API ps_status ps_sort_records(ps_ctx* ctx, const uint32_t* d_rec, uint32_t words, uint64_t n,
                                  uint32_t* d_perm, uint32_t* d_rec_out, ps_stats* stats);
+
+/* 64-bit keys: sort d_keys[0, n) in place, stably, read as key_type's
+ * 64-bit counterpart (PS_KEY_U32: unsigned, PS_KEY_I32: two's complement,
+ * PS_KEY_F32: IEEE 754 binary64 under totalOrder); d_perm receives the
+ * stable permutation.  A 64-bit key is a record of two words (high, low),
+ * so this runs the record sort on an order-preserving image of the keys:
+ * runs, powers, merge tree and merge cost are Algorithm 1's on the 64-bit
+ * keys.  Needs a context made with PS_FLAG_RECORDS and want_perm (and the
+ * context's own key_type PS_KEY_U32).  Asynchronous unless stats is given. */
+PS_API ps_status ps_sort_keys64(ps_ctx* ctx, uint64_t* d_keys, uint64_t n, uint32_t* d_perm, uint32_t key_type,
+                                ps_stats* stats);
 
 /* A batched sort captured once into a CUDA graph and replayed with one
  * launch (its arrays are fixed at capture time; refill them between

@@ -24,6 +24,7 @@ EXPORTS = (
     "ps_destroy", "ps_run_noalloc", "ps_get_round_times", "ps_graph_create_batched",
     "ps_graph_launch", "ps_graph_destroy", "ps_server_create", "ps_server_submit", "ps_server_poll",
     "ps_server_wait", "ps_server_get_stats", "ps_server_destroy", "ps_gather_rows", "ps_sort_records",
+    "ps_sort_keys64",
 )
 PS_NOALLOC_MAX_N = 262144
 PS_FLAG_TIMING, PS_FLAG_HOST_IO, PS_FLAG_DESCENDING_RUNS, PS_FLAG_RECORDS = 1, 2, 4, 8
@@ -146,6 +147,8 @@ def lib(build_if_missing: bool = True):
                                          ctypes.POINTER(ctypes.c_uint32)]
         L.ps_sync.restype = ctypes.c_int
         L.ps_sync.argtypes = [vp]
+        L.ps_sort_keys64.restype = ctypes.c_int
+        L.ps_sort_keys64.argtypes = [vp, vp, ctypes.c_uint64, vp, ctypes.c_uint32, ctypes.POINTER(ps_stats)]
         L.ps_sort_records.restype = ctypes.c_int
         L.ps_sort_records.argtypes = [vp, vp, ctypes.c_uint32, ctypes.c_uint64, vp, vp, ctypes.POINTER(ps_stats)]
         L.ps_gather_rows.restype = ctypes.c_int
@@ -263,6 +266,14 @@ class Context:
         n, words = (rec.shape[0], rec.shape[1]) if rec.dim() == 2 else (rec.shape[0], 1)
         _check(lib().ps_sort_records(self._h, _ptr(rec), words, n, _ptr(perm), _ptr(out),
                                      ctypes.byref(st) if st is not None else None), "ps_sort_records")
+        return st.as_dict() if st is not None else None
+
+    def sort_keys64(self, keys, perm, key_type: int = PS_KEY_U32, *, stats: bool = False):
+        """ps_sort_keys64: ``keys`` is a 64-bit tensor sorted in place (as
+        unsigned, int64 or float64 per ``key_type``: PS_KEY_U32/I32/F32)."""
+        st = ps_stats() if stats else None
+        _check(lib().ps_sort_keys64(self._h, _ptr(keys), keys.numel(), _ptr(perm), key_type,
+                                    ctypes.byref(st) if st is not None else None), "ps_sort_keys64")
         return st.as_dict() if st is not None else None
 
     def gather_rows(self, perm, src, dst, *, offsets=None):

@@ -34,6 +34,10 @@ struct ps_ctx {
     uint32_t* rec_tmp;          //   merge scratch of the tie fix-up,
     uint32_t* rec_groups;       //   groups of equal windows (start, end)
     uint32_t rec_group_cap;
+    uint32_t* rec_rows;         //   ps_sort_keys64: the sorted (high, low) rows
+    uint32_t* rec_big;          //   the groups larger than one CTA's shared memory
+    uint32_t rec_big_cap;
+    int grid_rec_big;           //   cooperative grid of their merge passes
 };
 
 namespace {
@@ -340,6 +344,10 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
         if (st == PS_OK) st = dev_alloc(c, &c->rec_mask, cfg->max_n / 32 + 2);
         if (st == PS_OK) st = dev_alloc(c, &c->rec_tmp, cfg->max_n);
         if (st == PS_OK) st = dev_alloc(c, &c->rec_groups, 2ull * c->rec_group_cap);
+        c->rec_big_cap = (uint32_t)(cfg->max_n / 2048 + 2);
+        if (st == PS_OK) st = dev_alloc(c, &c->rec_big, 2ull * c->rec_big_cap);
+        if (st == PS_OK) st = dev_alloc(c, &c->rec_rows, 2ull * cfg->max_n);
+        c->grid_rec_big = ps::records_fix_big_grid(c->num_sms);
     }
     if (st == PS_OK && (cfg->flags & PS_FLAG_HOST_IO)) {
         st = dev_alloc(c, &c->io_keys, max_total);
@@ -531,24 +539,18 @@ PS_API void ps_graph_destroy(ps_graph* g)
     delete g;
 }
 
-PS_API ps_status ps_sort_records(ps_ctx* ctx, const uint32_t* d_rec, uint32_t words, uint64_t n,
-                                 uint32_t* d_perm, uint32_t* d_rec_out, ps_stats* stats)
+namespace {
+
+// The record sort, enqueued (n >= 1, arguments checked by the caller).
+ps_status records_async(ps_ctx* ctx, const uint32_t* d_rec, uint32_t words, uint64_t n, uint32_t* d_perm,
+                        uint32_t* d_rec_out)
 {
-    if (!ctx || !ctx->rec_keys || !ctx->cfg.want_perm) return PS_EINVAL;
-    if (ctx->base.desc_runs || ctx->base.key_type != PS_KEY_U32) return PS_EINVAL;
-    if (words == 0 || words > PS_RECORD_MAX_WORDS || n > ctx->cfg.max_n) return PS_EINVAL;
-    if (n > 0 && (!d_rec || !d_perm)) return PS_EINVAL;
-    if (n == 0) {
-        if (stats) std::memset(stats, 0, sizeof(*stats));
-        return PS_OK;
-    }
-    DeviceGuard g(ctx->device);
     cudaStream_t s = ctx->stream;
     ps::Ctr* C = ctx->base.ctr;
     const int grid = ctx->num_sms * 8;
     // the shared prefix starts at "every word", the group list empty
     if (cudaMemsetAsync(&C->rec_lcp, 0xff, sizeof(uint32_t), s) != cudaSuccess ||
-        cudaMemsetAsync(&C->rec_groups, 0, sizeof(uint32_t), s) != cudaSuccess)
+        cudaMemsetAsync(&C->rec_groups, 0, 3 * sizeof(uint32_t), s) != cudaSuccess)   // groups, nbig, gmax
         return PS_ECUDA;
     if (ps::launch_records_prepare(d_rec, words, n, ctx->rec_mask, ctx->rec_keys, C, grid, s) != cudaSuccess)
         return PS_ECUDA;
@@ -558,23 +560,74 @@ PS_API ps_status ps_sort_records(ps_ctx* ctx, const uint32_t* d_rec, uint32_t wo
     ctx->base.desc_mask = nullptr;
     if (st != PS_OK) return st;
     if (ps::launch_records_fix(d_rec, words, n, ctx->rec_keys, d_perm, ctx->rec_tmp, ctx->rec_groups,
-                               ctx->rec_group_cap, C, grid, s) != cudaSuccess)
+                               ctx->rec_group_cap, ctx->rec_big, ctx->rec_big_cap, C, grid, ctx->grid_rec_big,
+                               s) != cudaSuccess)
         return PS_ECUDA;
     if (d_rec_out && ps::launch_gather_rows(d_perm, nullptr, 0, n, ctx->max_total, d_rec, d_rec_out, words * 4u, C,
                                             grid, s) != cudaSuccess)
         return PS_ECUDA;
-    if (cudaMemcpyAsync(&ctx->h_ctr->error, &C->error, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
-        return PS_ECUDA;
-    if (stats) {
-        st = sync_and_check(ctx);
-        if (st != PS_OK) return st;
-        fill_stats(ctx, stats, 1);
-        if (cudaMemcpy(ctx->h_inst, ctx->base.inst, sizeof(ps::Inst), cudaMemcpyDeviceToHost) != cudaSuccess)
-            return PS_ECUDA;
-        stats->minrun = ctx->h_inst->minrun;
-        stats->launches += 4u + (d_rec_out ? 1u : 0u);
-    }
     return PS_OK;
+}
+
+// After an enqueued record sort: surface its errors, and the statistics.
+ps_status records_finish(ps_ctx* ctx, ps_stats* stats, uint32_t extra_launches)
+{
+    if (cudaMemcpyAsync(&ctx->h_ctr->error, &ctx->base.ctr->error, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                        ctx->stream) != cudaSuccess)
+        return PS_ECUDA;
+    if (!stats) return PS_OK;
+    ps_status st = sync_and_check(ctx);
+    if (st != PS_OK) return st;
+    fill_stats(ctx, stats, 1);
+    if (cudaMemcpy(ctx->h_inst, ctx->base.inst, sizeof(ps::Inst), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return PS_ECUDA;
+    stats->minrun = ctx->h_inst->minrun;
+    stats->launches += 5u + extra_launches;   // scan, window keys, groups, fix-up, big groups
+    return PS_OK;
+}
+
+bool records_ready(const ps_ctx* ctx)
+{
+    return ctx && ctx->rec_keys && ctx->cfg.want_perm && !ctx->base.desc_runs && ctx->base.key_type == PS_KEY_U32;
+}
+
+}  // namespace
+
+PS_API ps_status ps_sort_records(ps_ctx* ctx, const uint32_t* d_rec, uint32_t words, uint64_t n,
+                                 uint32_t* d_perm, uint32_t* d_rec_out, ps_stats* stats)
+{
+    if (!records_ready(ctx)) return PS_EINVAL;
+    if (words == 0 || words > PS_RECORD_MAX_WORDS || n > ctx->cfg.max_n) return PS_EINVAL;
+    if (n > 0 && (!d_rec || !d_perm)) return PS_EINVAL;
+    if (n == 0) {
+        if (stats) std::memset(stats, 0, sizeof(*stats));
+        return PS_OK;
+    }
+    DeviceGuard g(ctx->device);
+    ps_status st = records_async(ctx, d_rec, words, n, d_perm, d_rec_out);
+    if (st != PS_OK) return st;
+    return records_finish(ctx, stats, d_rec_out ? 1u : 0u);
+}
+
+PS_API ps_status ps_sort_keys64(ps_ctx* ctx, uint64_t* d_keys, uint64_t n, uint32_t* d_perm, uint32_t key_type,
+                                ps_stats* stats)
+{
+    if (!records_ready(ctx) || key_type > PS_KEY_F32 || n > ctx->cfg.max_n) return PS_EINVAL;
+    if (n > 0 && (!d_keys || !d_perm)) return PS_EINVAL;
+    if (n == 0) {
+        if (stats) std::memset(stats, 0, sizeof(*stats));
+        return PS_OK;
+    }
+    DeviceGuard g(ctx->device);
+    const int grid = ctx->num_sms * 8;
+    // keys -> order-preserving (high, low) rows in place; sort the rows into
+    // rec_rows; back to keys in order
+    if (ps::launch_key64(true, nullptr, d_keys, n, key_type, grid, ctx->stream) != cudaSuccess) return PS_ECUDA;
+    ps_status st = records_async(ctx, reinterpret_cast<const uint32_t*>(d_keys), 2, n, d_perm, ctx->rec_rows);
+    if (st != PS_OK) return st;
+    if (ps::launch_key64(false, ctx->rec_rows, d_keys, n, key_type, grid, ctx->stream) != cudaSuccess)
+        return PS_ECUDA;
+    return records_finish(ctx, stats, 3u);   // the row gather and the two maps
 }
 
 PS_API ps_status ps_gather_rows(ps_ctx* ctx, const uint32_t* d_perm, const uint64_t* d_offsets, uint32_t count,

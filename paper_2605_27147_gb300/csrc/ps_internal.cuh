@@ -126,6 +126,8 @@ struct Ctr {
     uint32_t keys_mapped;              // typed keys: the forward map ran (the inverse must too)
     uint32_t rec_lcp;                  // records: words every row shares (NONE: all rows equal)
     uint32_t rec_groups;               // records: groups of equal window keys listed for the fix-up
+    uint32_t rec_nbig;                 // records: groups too large for one CTA's shared memory
+    uint32_t rec_gmax;                 // records: the largest group
     uint32_t vm_ring_head;             // tickets handed out: the ring slot each output page pops
     uint32_t vm_ring_tail;             // free pages pushed onto the ring so far
     uint32_t vm_round_base;            // ring_head at the start of the current round
@@ -362,6 +364,51 @@ __device__ __forceinline__ void cp_async_wait()
 // that exceeds it records DERR_TIMEOUT and gives up.
 constexpr long long SPIN_LIMIT_CYCLES = 4000000000ll;
 
+// Grid-wide barrier of a cooperative launch (all CTAs resident, at most
+// 1024): arrivals are counted per group of 32 CTAs, the last group's last
+// arrival bumps a generation that the others wait for -- at most
+// SPIN_LIMIT_CYCLES, after which DERR_TIMEOUT is recorded and false returned.
+__device__ __forceinline__ bool grid_barrier(Ctr* C)
+{
+    __syncthreads();
+    __shared__ uint32_t s_ok;
+    if (threadIdx.x == 0) {
+        uint32_t ok = 1;
+        const uint32_t gen = ld_acquire_u32(&C->bar_gen);
+        __threadfence();
+        const uint32_t grp = blockIdx.x >> 5;
+        const uint32_t ngroups = (gridDim.x + 31) >> 5;
+        const uint32_t gsize = min(32u, gridDim.x - (grp << 5));
+        bool last = false;
+        if (atomicAdd(&C->bar_group[grp], 1u) == gsize - 1) {
+            atomicExch(&C->bar_group[grp], 0u);
+            last = atomicAdd(&C->bar_count, 1u) == ngroups - 1;
+        }
+        if (last) {
+            atomicExch(&C->bar_count, 0u);
+            __threadfence();
+            st_release_u32(&C->bar_gen, gen + 1);
+        } else {
+            const long long t0 = clock64();
+            uint32_t nap = 64;
+            while (ld_relaxed_u32(&C->bar_gen) == gen) {
+                __nanosleep(nap);
+                nap = nap < 1024 ? nap * 2 : 1024;
+                if (clock64() - t0 > SPIN_LIMIT_CYCLES) {
+                    set_error(C, DERR_TIMEOUT, 60);
+                    ok = 0;
+                    break;
+                }
+            }
+            fence_acquire_gpu();
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
 // Index of the instance whose [base, base + size) range holds x, for a
 // non-decreasing array of bases (binary search; the last of equal bases).
 template <typename F>
@@ -389,8 +436,11 @@ cudaError_t launch_key_map(const Job& J, bool forward, int grid, cudaStream_t s)
 cudaError_t launch_records_prepare(const uint32_t* rec, uint32_t W, unsigned long long n, uint32_t* mask,
                                    uint32_t* keys, Ctr* C, int grid, cudaStream_t s);
 cudaError_t launch_records_fix(const uint32_t* rec, uint32_t W, unsigned long long n, const uint32_t* keys,
-                               uint32_t* perm, uint32_t* tmp, uint32_t* groups, uint32_t cap, Ctr* C, int grid,
-                               cudaStream_t s);
+                               uint32_t* perm, uint32_t* tmp, uint32_t* groups, uint32_t cap, uint32_t* big,
+                               uint32_t big_cap, Ctr* C, int grid, int coop_grid, cudaStream_t s);
+int records_fix_big_grid(int num_sms);
+cudaError_t launch_key64(bool in, const void* rows, void* keys, unsigned long long n, uint32_t type, int grid,
+                         cudaStream_t s);
 cudaError_t launch_gather_rows(const uint32_t* perm, const unsigned long long* offsets, uint32_t count,
                                unsigned long long n, unsigned long long max_total, const void* src, void* dst,
                                uint32_t row_bytes, Ctr* ctr, int grid, cudaStream_t s);

@@ -157,6 +157,50 @@ __global__ void __launch_bounds__(256) k_gather_tiled(const uint32_t* perm, unsi
     }
 }
 
+// 64-bit keys as two-word records: the same order-preserving maps at 64
+// bits, and the halves swapped so that the high word comes first in memory.
+__device__ __forceinline__ unsigned long long key64_to_order(unsigned long long x, uint32_t type)
+{
+    if (type == PS_KEY_I32) return x ^ 0x8000000000000000ull;
+    if (type == PS_KEY_F32) return x ^ ((unsigned long long)((long long)x >> 63) | 0x8000000000000000ull);
+    return x;
+}
+
+__device__ __forceinline__ unsigned long long key64_from_order(unsigned long long y, uint32_t type)
+{
+    if (type == PS_KEY_I32) return y ^ 0x8000000000000000ull;
+    if (type == PS_KEY_F32) return y ^ (((y >> 63) - 1ull) | 0x8000000000000000ull);
+    return y;
+}
+
+__global__ void __launch_bounds__(256) k_key64_in(unsigned long long* keys, unsigned long long n, uint32_t type)
+{
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const unsigned long long y = key64_to_order(keys[i], type);
+        keys[i] = (y << 32) | (y >> 32);   // words (high, low)
+    }
+}
+
+__global__ void __launch_bounds__(256) k_key64_out(const unsigned long long* rows, unsigned long long* keys,
+                                                   unsigned long long n, uint32_t type)
+{
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const unsigned long long r = rows[i];
+        keys[i] = key64_from_order((r << 32) | (r >> 32), type);
+    }
+}
+
+cudaError_t launch_key64(bool in, const void* rows, void* keys, unsigned long long n, uint32_t type, int grid,
+                         cudaStream_t s)
+{
+    if (in) k_key64_in<<<grid, 256, 0, s>>>(static_cast<unsigned long long*>(keys), n, type);
+    else k_key64_out<<<grid, 256, 0, s>>>(static_cast<const unsigned long long*>(rows),
+                                           static_cast<unsigned long long*>(keys), n, type);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_key_map(const Job& J, bool forward, int grid, cudaStream_t s)
 {
     k_key_map<<<grid, 256, 0, s>>>(J, forward ? 1 : 0);

@@ -16,9 +16,11 @@
 //      and merge cost are those of the records;
 //   4. rows whose windows are equal may still differ later: every group of
 //      equal windows comes out of the merges in input order (every merge is
-//      stable), and k_rec_fix sorts each group by the rest of the row, ties
-//      by input index -- one CTA per group: a bitonic sort in shared memory
-//      up to REC_SMEM entries, a merge sort through a scratch array above;
+//      stable), and the fix-up sorts each group by the rest of the row, ties
+//      by input index: k_rec_fix sorts blocks of up to REC_SMEM entries in
+//      shared memory (bitonic, one CTA per group), and for larger groups the
+//      cooperative k_rec_fix_big merges the blocks pass by pass, every pass
+//      spread over the whole grid (a grid barrier between passes);
 //   5. the rows move once, through the permutation (ps_gather_rows' kernel),
 //      instead of at every merge.
 #include "ps_internal.cuh"
@@ -41,6 +43,38 @@ __device__ __forceinline__ bool rec_less(const uint32_t* rec, uint32_t W, uint32
         if (x != y) return x < y;
     }
     return a < b;
+}
+
+// Outputs [o0, o0 + 16) of one merge pass of width w over a group of g
+// entries: the pair [x, x + w) + [x + w, x + 2w) holding o0 is merged from
+// src to dst, the first run winning ties.
+__device__ void merge_chunk16(const uint32_t* rec, uint32_t W, uint32_t w0, const uint32_t* src, uint32_t* dst,
+                              uint32_t g, uint32_t w, uint32_t o0)
+{
+    const uint32_t x = o0 - o0 % (2 * w);
+    const uint32_t na = min(w, g - x), nb = g - x > w ? min(w, g - x - w) : 0u;
+    const uint32_t* A = src + x;
+    const uint32_t* B = src + x + na;
+    const uint32_t d = o0 - x;
+    uint32_t lo = d > nb ? d - nb : 0u, hi = min(d, na);
+    while (lo < hi) {                                  // A wins ties: take A while !(B < A)
+        const uint32_t mid = (lo + hi) >> 1;
+        if (!rec_less(rec, W, w0, B[d - 1 - mid], A[mid])) lo = mid + 1; else hi = mid;
+    }
+    uint32_t ia = lo, ib = d - lo;
+    const uint32_t end = min(o0 + 16u, x + na + nb);
+    for (uint32_t o = o0; o < end; ++o) {
+        const bool take_a = ia < na && (ib >= nb || !rec_less(rec, W, w0, B[ib], A[ia]));
+        dst[o] = take_a ? A[ia++] : B[ib++];
+    }
+}
+
+// Merge passes a group of g > REC_SMEM entries needs (blocks of REC_SMEM).
+__device__ __forceinline__ uint32_t merge_passes(uint32_t g)
+{
+    uint32_t p = 0;
+    for (unsigned long long w = REC_SMEM; w < g; w <<= 1) ++p;
+    return p;
 }
 
 }  // namespace
@@ -136,7 +170,8 @@ __global__ void __launch_bounds__(REC_BLOCK) k_rec_key(const uint32_t* rec, uint
 // Groups of equal windows (two or more rows): a thread per group start lists
 // it (start, end) -- only when the rows can still differ after word L.
 __global__ void __launch_bounds__(REC_BLOCK) k_rec_groups(const uint32_t* keys, uint32_t W, unsigned long long n,
-                                                          uint32_t* groups, uint32_t cap, Ctr* C)
+                                                          uint32_t* groups, uint32_t cap, uint32_t* big,
+                                                          uint32_t big_cap, Ctr* C)
 {
     const uint32_t L = *(volatile const uint32_t*)&C->rec_lcp;
     if (L >= W - 1 || *(volatile uint32_t*)&C->error) return;   // NONE: all rows equal
@@ -153,12 +188,23 @@ __global__ void __launch_bounds__(REC_BLOCK) k_rec_groups(const uint32_t* keys, 
         } else {
             set_error(C, DERR_INTERNAL, 80);
         }
+        if (e - i > REC_SMEM) {   // its merge passes run in k_rec_fix_big
+            const uint32_t b = atomicAdd(&C->rec_nbig, 1u);
+            atomicMax(&C->rec_gmax, (uint32_t)(e - i));
+            if (b < big_cap) {
+                big[2 * b] = (uint32_t)i;
+                big[2 * b + 1] = (uint32_t)e;
+            } else {
+                set_error(C, DERR_INTERNAL, 81);
+            }
+        }
     }
 }
 
-// Sort one group's permutation entries by (row from word L + 1, index).
+// Sort every group's permutation entries by (row from word L + 1, index) in
+// blocks of up to REC_SMEM entries (the whole group when it fits).
 __global__ void __launch_bounds__(REC_BLOCK) k_rec_fix(const uint32_t* rec, uint32_t W, uint32_t* perm,
-                                                       uint32_t* tmp, const uint32_t* groups, uint32_t cap, Ctr* C)
+                                                       const uint32_t* groups, uint32_t cap, Ctr* C)
 {
     __shared__ uint32_t s[REC_SMEM];
     const uint32_t L = *(volatile const uint32_t*)&C->rec_lcp;
@@ -196,36 +242,43 @@ __global__ void __launch_bounds__(REC_BLOCK) k_rec_fix(const uint32_t* rec, uint
             for (uint32_t x = tid; x < m; x += REC_BLOCK) perm[a + b0 + x] = s[x];
             __syncthreads();
         }
-        // larger groups: merge the sorted blocks pairwise, perm <-> tmp
-        uint32_t* src = perm + a;
-        uint32_t* dst = tmp + a;
-        for (uint32_t w = REC_SMEM; w < g; w <<= 1) {
-            for (uint32_t o0 = tid * 16u; o0 < g; o0 += REC_BLOCK * 16u) {
-                const uint32_t x = o0 - o0 % (2 * w);             // the pair [x, x + w) + [x + w, x + 2w)
-                const uint32_t na = min(w, g - x), nb = g - x > w ? min(w, g - x - w) : 0u;
-                const uint32_t* A = src + x;
-                const uint32_t* B = src + x + na;
-                const uint32_t d = o0 - x;
-                uint32_t lo = d > nb ? d - nb : 0u, hi = min(d, na);
-                while (lo < hi) {                                  // A wins ties: take A while !(B < A)
-                    const uint32_t mid = (lo + hi) >> 1;
-                    if (!rec_less(rec, W, w0, B[d - 1 - mid], A[mid])) lo = mid + 1; else hi = mid;
-                }
-                uint32_t ia = lo, ib = d - lo;
-                const uint32_t end = min(o0 + 16u, x + na + nb);
-                for (uint32_t o = o0; o < end; ++o) {
-                    const bool take_a = ia < na && (ib >= nb || !rec_less(rec, W, w0, B[ib], A[ia]));
-                    dst[o] = take_a ? A[ia++] : B[ib++];
-                }
-            }
-            __syncthreads();
-            uint32_t* t = src;
-            src = dst;
-            dst = t;
+    }
+}
+
+// The merge passes of every group larger than REC_SMEM (its blocks already
+// sorted by k_rec_fix): pass p merges pairs of width REC_SMEM << p from perm
+// to tmp (even p) or back (odd p), for every group that still has pairs;
+// chunks of 16 outputs of all such groups are spread over the grid, and a
+// grid barrier separates the passes.  A group whose last pass wrote tmp is
+// copied back at the end.
+__global__ void __launch_bounds__(REC_BLOCK) k_rec_fix_big(const uint32_t* rec, uint32_t W, uint32_t* perm,
+                                                           uint32_t* tmp, const uint32_t* big, uint32_t big_cap,
+                                                           Ctr* C)
+{
+    const uint32_t L = *(volatile const uint32_t*)&C->rec_lcp;
+    if (L >= W - 1 || *(volatile uint32_t*)&C->error) return;
+    const uint32_t gmax = *(volatile const uint32_t*)&C->rec_gmax;
+    if (gmax <= REC_SMEM) return;                     // the same answer in every CTA
+    const uint32_t w0 = L + 1;
+    const uint32_t nbig = min(*(volatile const uint32_t*)&C->rec_nbig, big_cap);
+    const uint32_t gt = blockIdx.x * REC_BLOCK + threadIdx.x, gs = gridDim.x * REC_BLOCK;
+    const uint32_t passes = merge_passes(gmax);
+    for (uint32_t p = 0; p < passes; ++p) {
+        const uint32_t w = REC_SMEM << p;
+        const uint32_t* from = (p & 1u) ? tmp : perm;
+        uint32_t* to = (p & 1u) ? perm : tmp;
+        for (uint32_t b = 0; b < nbig; ++b) {
+            const uint32_t a = big[2 * b], g = big[2 * b + 1] - a;
+            if (g <= w) continue;
+            const uint32_t chunks = (g + 15u) >> 4;
+            for (uint32_t c = gt; c < chunks; c += gs) merge_chunk16(rec, W, w0, from + a, to + a, g, w, c * 16u);
         }
-        if (src != perm + a)
-            for (uint32_t x = tid; x < g; x += REC_BLOCK) perm[a + x] = src[x];
-        __syncthreads();
+        if (!grid_barrier(C)) return;
+    }
+    for (uint32_t b = 0; b < nbig; ++b) {
+        const uint32_t a = big[2 * b], g = big[2 * b + 1] - a;
+        if (merge_passes(g) & 1u)
+            for (uint32_t x = gt; x < g; x += gs) perm[a + x] = tmp[a + x];
     }
 }
 
@@ -245,12 +298,21 @@ cudaError_t launch_records_prepare(const uint32_t* rec, uint32_t W, unsigned lon
 }
 
 cudaError_t launch_records_fix(const uint32_t* rec, uint32_t W, unsigned long long n, const uint32_t* keys,
-                               uint32_t* perm, uint32_t* tmp, uint32_t* groups, uint32_t cap, Ctr* C, int grid,
-                               cudaStream_t s)
+                               uint32_t* perm, uint32_t* tmp, uint32_t* groups, uint32_t cap, uint32_t* big,
+                               uint32_t big_cap, Ctr* C, int grid, int coop_grid, cudaStream_t s)
 {
-    k_rec_groups<<<grid, REC_BLOCK, 0, s>>>(keys, W, n, groups, cap, C);
-    k_rec_fix<<<grid, REC_BLOCK, 0, s>>>(rec, W, perm, tmp, groups, cap, C);
-    return cudaGetLastError();
+    k_rec_groups<<<grid, REC_BLOCK, 0, s>>>(keys, W, n, groups, cap, big, big_cap, C);
+    k_rec_fix<<<grid, REC_BLOCK, 0, s>>>(rec, W, perm, groups, cap, C);
+    void* args[] = {(void*)&rec, (void*)&W, (void*)&perm, (void*)&tmp, (void*)&big, (void*)&big_cap, (void*)&C};
+    return cudaLaunchCooperativeKernel((const void*)k_rec_fix_big, dim3(coop_grid), dim3(REC_BLOCK), args, 0, s);
+}
+
+int records_fix_big_grid(int num_sms)
+{
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rec_fix_big, REC_BLOCK, 0);
+    const int g = num_sms * (per_sm > 0 ? per_sm : 1);
+    return g < 1024 ? g : 1024;   // the grid barrier counts at most 1024 CTAs
 }
 
 }  // namespace ps

@@ -87,47 +87,6 @@ __device__ __forceinline__ uint32_t page_size(const Job& J, uint32_t u, uint32_t
     return (u + 1 == J.vm_na) ? n - u * P : P;
 }
 
-__device__ bool vm_barrier(Ctr* C)
-{
-    __syncthreads();
-    __shared__ uint32_t s_ok;
-    if (threadIdx.x == 0) {
-        uint32_t ok = 1;
-        const uint32_t gen = ld_acquire_u32(&C->bar_gen);
-        __threadfence();
-        const uint32_t grp = blockIdx.x >> 5;
-        const uint32_t ngroups = (gridDim.x + 31) >> 5;
-        const uint32_t gsize = min(32u, gridDim.x - (grp << 5));
-        bool last = false;
-        if (atomicAdd(&C->bar_group[grp], 1u) == gsize - 1) {
-            atomicExch(&C->bar_group[grp], 0u);
-            last = atomicAdd(&C->bar_count, 1u) == ngroups - 1;
-        }
-        if (last) {
-            atomicExch(&C->bar_count, 0u);
-            __threadfence();
-            st_release_u32(&C->bar_gen, gen + 1);
-        } else {
-            const long long t0 = clock64();
-            uint32_t nap = 64;
-            while (ld_relaxed_u32(&C->bar_gen) == gen) {
-                __nanosleep(nap);
-                nap = nap < 1024 ? nap * 2 : 1024;
-                if (clock64() - t0 > SPIN_LIMIT_CYCLES) {
-                    set_error(C, DERR_TIMEOUT, 60);
-                    ok = 0;
-                    break;
-                }
-            }
-            fence_acquire_gpu();
-        }
-        __threadfence();
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
-
 // Left-child elements among the first d outputs of merge g (merge path over
 // the page-table-translated keys).
 __device__ uint32_t vm_split(const Job& J, const GSorted& g, uint32_t d)
@@ -391,7 +350,7 @@ __global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_rounds(Job J)
     // the ring: the pool's pages, then empty slots
     for (uint32_t i = gtid; i < J.vm_ring_cap; i += gstride)
         J.free_stack[i] = i < J.vm_pool ? J.vm_na_cap + i : NONE;
-    if (!vm_barrier(C)) return;
+    if (!grid_barrier(C)) return;
 
     for (int r = 0; r < NPOW; ++r) {
         if (*(volatile uint32_t*)&C->error) return;
@@ -413,7 +372,7 @@ __global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_rounds(Job J)
                 }
             }
         }
-        if (!vm_barrier(C)) return;
+        if (!grid_barrier(C)) return;
         // 2. per touched page (a thread each): its record -- up to two merges,
         //    ordered, with the gaps between them filled by copies; and per page
         //    start inside a merge (eight lanes each) the merge-path split there,
@@ -523,7 +482,7 @@ __global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_rounds(Job J)
                 C->vm_waves += 1;
             }
         }
-        if (!vm_barrier(C)) return;
+        if (!grid_barrier(C)) return;
         // 4. the pages, as a dataflow over tickets
         {
             const uint32_t ntouched = C->vm_touched, base = C->vm_round_base;
@@ -576,7 +535,7 @@ __global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_rounds(Job J)
                 vm_page(J, sm, G, u, out, n, perm);
             }
         }
-        if (!vm_barrier(C)) return;
+        if (!grid_barrier(C)) return;
         // 5. the written pages become current; reset the per-round tables; the
         //    over-drawn tickets are returned
         const uint32_t ntouched = C->vm_touched;
@@ -587,7 +546,7 @@ __global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_rounds(Job J)
             J.consumed[u] = 0;
         }
         if (gtid == 0) C->vm_ring_head = C->vm_round_base + ntouched;
-        if (!vm_barrier(C)) return;
+        if (!grid_barrier(C)) return;
     }
 }
 
@@ -632,9 +591,9 @@ __global__ void __launch_bounds__(VM_BLOCK) k_vm_copy(Job J)
     const bool tail_partial = (n & ((1u << J.vm_plog2) - 1)) != 0;
     // holder[p]: the virtual page whose data physical page p holds (NONE: none)
     for (uint32_t p = gtid; p < NP; p += gstride) J.holder[p] = NONE;
-    if (!vm_barrier(C)) return;
+    if (!grid_barrier(C)) return;
     for (uint32_t u = gtid; u < NA; u += gstride) J.holder[J.pt[u]] = u;
-    if (!vm_barrier(C)) return;
+    if (!grid_barrier(C)) return;
     for (uint32_t q0 = 0; q0 < NA;) {
         // at most pool - 1 targets: then the free pages always cover the moves out
         // (one page of slack for the partial last array page, which is never free)
@@ -646,7 +605,7 @@ __global__ void __launch_bounds__(VM_BLOCK) k_vm_copy(Job J)
             C->vm_free_top = 0;
             C->vm_wave = 0;
         }
-        if (!vm_barrier(C)) return;
+        if (!grid_barrier(C)) return;
         for (uint32_t p = gtid; p < NP; p += gstride) {
             if (p >= J.vm_na_cap && p - J.vm_na_cap >= J.vm_pool) continue;
             const bool is_array = p < J.vm_na_cap;
@@ -654,7 +613,7 @@ __global__ void __launch_bounds__(VM_BLOCK) k_vm_copy(Job J)
             if (is_array && tail_partial && p + 1 == NA) continue;
             if (J.holder[p] == NONE) J.free_stack[atomicAdd(&C->vm_free_top, 1u)] = p;
         }
-        if (!vm_barrier(C)) return;
+        if (!grid_barrier(C)) return;
         // step 1: move needed data out of the batch's targets (a warp per target)
         for (uint32_t q = q0 + gwarp; q < q1; q += nwarps) {
             const uint32_t r = J.holder[q];
@@ -676,7 +635,7 @@ __global__ void __launch_bounds__(VM_BLOCK) k_vm_copy(Job J)
                 atomicAdd(&C->vm_copy_moves, 1u);
             }
         }
-        if (!vm_barrier(C)) return;
+        if (!grid_barrier(C)) return;
         if (*(volatile uint32_t*)&C->error) return;
         // step 2: every target receives its own data (a warp per target)
         for (uint32_t q = q0 + gwarp; q < q1; q += nwarps) {
@@ -691,7 +650,7 @@ __global__ void __launch_bounds__(VM_BLOCK) k_vm_copy(Job J)
                 atomicAdd(&C->vm_copy_moves, 1u);
             }
         }
-        if (!vm_barrier(C)) return;
+        if (!grid_barrier(C)) return;
         q0 = q1;
     }
 }
