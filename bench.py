@@ -19,6 +19,9 @@ permutation is produced):
                (randomBlob30 and zeroBlob30, the paper's blob types, values in
                [100, 10^9], seed 1) with the sorted rows written out; rate in
                records/s
+  keys64_2^24  one step = three 64-bit key sorts of n = 2^24 (ps_sort_keys64):
+               uniform unsigned, int64 within +-2^31 (two tie groups of n/2 on
+               the high word), uniform float64 bit patterns (seed 1)
   bands_2^24   one step = one sort of n = 2^24: sorted blocks of 2^13 keys in
                descending value bands; with --storage vm the merges splice
                whole pages through the page table (stats: pages_spliced)
@@ -65,6 +68,7 @@ WORKLOADS = {
     "updown_2^24": [("updown", 1 << 24, 1)],
     "bands_2^24": [("bands", 1 << 24, 1)],
     "records_2^23": None,
+    "keys64_2^24": None,
     "batched_4096": None,
     "serving": None,
 }
@@ -213,6 +217,10 @@ def run_reference(args):
         return
     if args.workload == "records_2^23":
         return run_reference_records(args)
+    if args.workload == "keys64_2^24":
+        print(json.dumps({"impl": "reference", "unavailable": "keys64_2^24 has no CPU reference arm; "
+                          "tests/test_gpu_keys64.py checks it against the oracle"}), flush=True)
+        return
     if args.workload == "batched_4096":
         from paper_2605_27147_gb300 import inputs as _inp
 
@@ -553,6 +561,81 @@ def run_records(args, n=1 << 23, words=30):
         dist.destroy_process_group()
 
 
+def run_keys64(args, n=1 << 24):
+    """64-bit key sorts through ps_sort_keys64."""
+    import torch
+
+    from paper_2605_27147_gb300 import binding, inputs, replicas
+
+    world, rank, local = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    seed = 1 + replicas.replica_seed(0, rank)
+    hi = inputs.uniform(n, seed).astype(np.uint64)
+    lo = inputs.uniform(n, seed + 1).astype(np.uint64)
+    sets = [("u64", binding.PS_KEY_U32, (hi << np.uint64(32)) | lo),
+            ("i64", binding.PS_KEY_I32, (lo.astype(np.int64) - (1 << 31)).view(np.uint64)),
+            ("f64", binding.PS_KEY_F32, (lo << np.uint64(32)) | hi)]
+    pristine = [torch.from_numpy(b.view(np.int64)).to(dev) for _, _, b in sets]
+    work = torch.empty(n, dtype=torch.int64, device=dev)
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = binding.Context(n, want_perm=True, flags=binding.PS_FLAG_RECORDS, device=local, stream=stream)
+    for _ in range(args.warmup):
+        for i, (_, kt, _) in enumerate(sets):
+            work.copy_(pristine[i])
+            ctx.sort_keys64(work, perm, kt)
+    ctx.sync()
+    per_set = {name: 0.0 for name, _, _ in sets}
+    times = []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            for i, (name, kt, _) in enumerate(sets):
+                work.copy_(pristine[i])
+                flush.fill_(i)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx.sort_keys64(work, perm, kt)
+                e1.record(stream)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+                per_set[name] += times[-1]
+    stats = {}
+    for i, (name, kt, b) in enumerate(sets):
+        work.copy_(pristine[i])
+        st = ctx.sort_keys64(work, perm, kt, stats=True)
+        stats[name] = {k: st[k] for k in ("runs", "merge_cost", "rounds")}
+    out = work.cpu().numpy().view(np.uint64)          # the f64 set, last: non-decreasing in totalOrder
+    sgn = (out >> np.uint64(63)).astype(bool)
+    img = np.where(sgn, ~out, out | np.uint64(1 << 63))
+    assert np.all(img[1:] >= img[:-1])
+    total_ms = replicas.max_over_ranks(sum(times), dist, dev)
+    value = replicas.job_rate(n * len(times), world, total_ms)
+    line = {
+        "metric": "64-bit keys/s (sort + stable permutation), 1xGB300", "value": value, "unit": "elements/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "keys64_2^24", "instances": [f"{name} n=2^24" for name, _, _ in sets],
+                   "l2": "flushed before every timed sort"},
+        "per_set_elements_per_s": {k: n * args.steps / (v / 1000.0) for k, v in per_set.items()},
+        "stats": stats, "clocks": clk.summary(), "cpu_baseline": None, "e2e": None, "roofline": None,
+        "gpu_launches": None,
+    }
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 def run_serving(args, rate=2000.0, duration=10.0, budget=64 << 30):
     # Elements per batch are capped so that a burst cannot build one long
     # batch (latency grows with the batch; the offered load is far below
@@ -657,6 +740,8 @@ def main():
         return run_serving(args)
     if args.workload == "records_2^23":
         return run_records(args)
+    if args.workload == "keys64_2^24":
+        return run_keys64(args)
 
     import torch
 

@@ -99,7 +99,7 @@ typedef struct ps_config {
  * The result is the same stable sort; the runs, powers and merge tree are
  * those of the variant. */
 #define PS_FLAG_DESCENDING_RUNS 4u
-/* Allocate the arrays ps_sort_records and ps_sort_keys64 need (about 21
+/* Allocate the arrays ps_sort_records and ps_sort_keys64 need (about 25
  * bytes per element of max_n: window keys, descent mask, group list, merge
  * scratch, the sorted 64-bit rows). */
 #define PS_FLAG_RECORDS 8u

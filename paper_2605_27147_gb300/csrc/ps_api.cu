@@ -342,7 +342,7 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
         c->rec_group_cap = (uint32_t)(cfg->max_n / 2 + 1);
         st = dev_alloc(c, &c->rec_keys, cfg->max_n);
         if (st == PS_OK) st = dev_alloc(c, &c->rec_mask, cfg->max_n / 32 + 2);
-        if (st == PS_OK) st = dev_alloc(c, &c->rec_tmp, cfg->max_n);
+        if (st == PS_OK) st = dev_alloc(c, &c->rec_tmp, 2ull * cfg->max_n);   // u32 scratch, or packed u64 words
         if (st == PS_OK) st = dev_alloc(c, &c->rec_groups, 2ull * c->rec_group_cap);
         c->rec_big_cap = (uint32_t)(cfg->max_n / 2048 + 2);
         if (st == PS_OK) st = dev_alloc(c, &c->rec_big, 2ull * c->rec_big_cap);
@@ -559,7 +559,10 @@ ps_status records_async(ps_ctx* ctx, const uint32_t* d_rec, uint32_t words, uint
     ps_status st = run_common(ctx, ctx->rec_keys, d_perm, nullptr, n, 1, nullptr);
     ctx->base.desc_mask = nullptr;
     if (st != PS_OK) return st;
-    if (ps::launch_records_fix(d_rec, words, n, ctx->rec_keys, d_perm, ctx->rec_tmp, ctx->rec_groups,
+    // packed fix-up words: rec_tmp and rec_rows (free until the row gather)
+    if (ps::launch_records_fix(d_rec, words, n, ctx->rec_keys, d_perm, ctx->rec_tmp,
+                               reinterpret_cast<unsigned long long*>(ctx->rec_tmp),
+                               reinterpret_cast<unsigned long long*>(ctx->rec_rows), ctx->rec_groups,
                                ctx->rec_group_cap, ctx->rec_big, ctx->rec_big_cap, C, grid, ctx->grid_rec_big,
                                s) != cudaSuccess)
         return PS_ECUDA;

@@ -436,8 +436,9 @@ cudaError_t launch_key_map(const Job& J, bool forward, int grid, cudaStream_t s)
 cudaError_t launch_records_prepare(const uint32_t* rec, uint32_t W, unsigned long long n, uint32_t* mask,
                                    uint32_t* keys, Ctr* C, int grid, cudaStream_t s);
 cudaError_t launch_records_fix(const uint32_t* rec, uint32_t W, unsigned long long n, const uint32_t* keys,
-                               uint32_t* perm, uint32_t* tmp, uint32_t* groups, uint32_t cap, uint32_t* big,
-                               uint32_t big_cap, Ctr* C, int grid, int coop_grid, cudaStream_t s);
+                               uint32_t* perm, uint32_t* tmp, unsigned long long* comp, unsigned long long* comp2,
+                               uint32_t* groups, uint32_t cap, uint32_t* big, uint32_t big_cap, Ctr* C, int grid,
+                               int coop_grid, cudaStream_t s);
 int records_fix_big_grid(int num_sms);
 cudaError_t launch_key64(bool in, const void* rows, void* keys, unsigned long long n, uint32_t type, int grid,
                          cudaStream_t s);

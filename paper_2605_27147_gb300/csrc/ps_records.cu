@@ -18,9 +18,12 @@
 //      equal windows comes out of the merges in input order (every merge is
 //      stable), and the fix-up sorts each group by the rest of the row, ties
 //      by input index: k_rec_fix sorts blocks of up to REC_SMEM entries in
-//      shared memory (bitonic, one CTA per group), and for larger groups the
-//      cooperative k_rec_fix_big merges the blocks pass by pass, every pass
-//      spread over the whole grid (a grid barrier between passes);
+//      shared memory (bitonic; a small group whole by one CTA, the blocks of
+//      larger groups spread over all CTAs), and the cooperative
+//      k_rec_fix_big merges those blocks pass by pass, every pass spread over
+//      the whole grid (a grid barrier between passes).  With one word left
+//      to compare (64-bit keys: the low word) entries are packed as (word <<
+//      32 | index) and compared directly, without reading rows;
 //   5. the rows move once, through the permutation (ps_gather_rows' kernel),
 //      instead of at every merge.
 #include "ps_internal.cuh"
@@ -167,8 +170,9 @@ __global__ void __launch_bounds__(REC_BLOCK) k_rec_key(const uint32_t* rec, uint
         keys[i] = L < W ? __ldg(rec + (size_t)i * W + L) : 0u;
 }
 
-// Groups of equal windows (two or more rows): a thread per group start lists
-// it (start, end) -- only when the rows can still differ after word L.
+// Groups of equal windows (two or more rows) in the sorted window keys: a
+// thread per group start lists it (start, end) -- only when the rows can
+// still differ after word L.
 __global__ void __launch_bounds__(REC_BLOCK) k_rec_groups(const uint32_t* keys, uint32_t W, unsigned long long n,
                                                           uint32_t* groups, uint32_t cap, uint32_t* big,
                                                           uint32_t big_cap, Ctr* C)
@@ -179,8 +183,19 @@ __global__ void __launch_bounds__(REC_BLOCK) k_rec_groups(const uint32_t* keys, 
     for (unsigned long long i = (unsigned long long)blockIdx.x * REC_BLOCK + threadIdx.x; i + 1 < n; i += stride) {
         const uint32_t k = keys[i];
         if (keys[i + 1] != k || (i > 0 && keys[i - 1] == k)) continue;
-        unsigned long long e = i + 2;
-        while (e < n && keys[e] == k) ++e;
+        // the keys are sorted: the group ends at the first key above k,
+        // found by galloping then bisection (O(log size) loads)
+        unsigned long long lo = i + 1, step = 1;   // keys[lo] == k
+        while (lo + step < n && keys[lo + step] == k) {
+            lo += step;
+            step <<= 1;
+        }
+        unsigned long long hi = min(lo + step, n);  // keys[hi] != k or hi == n
+        while (hi - lo > 1) {
+            const unsigned long long mid = (lo + hi) >> 1;
+            if (keys[mid] == k) lo = mid; else hi = mid;
+        }
+        const unsigned long long e = hi;
         const uint32_t at = atomicAdd(&C->rec_groups, 1u);
         if (at < cap) {
             groups[2 * at] = (uint32_t)i;
@@ -201,84 +216,157 @@ __global__ void __launch_bounds__(REC_BLOCK) k_rec_groups(const uint32_t* keys, 
     }
 }
 
-// Sort every group's permutation entries by (row from word L + 1, index) in
-// blocks of up to REC_SMEM entries (the whole group when it fits).
+// One block of up to REC_SMEM entries of a group, sorted by (row from word
+// w0, index) in shared memory (bitonic).  With one word left to compare
+// (w0 = W - 1) every entry becomes one 64-bit word (that word << 32 |
+// index) and the network compares words; otherwise entries compare their
+// rows.  The sorted entries go back to perm, or (packed words of a group
+// that still needs merge passes) to comp.
+__device__ void fix_block(const uint32_t* rec, uint32_t W, uint32_t w0, uint32_t* perm,
+                          unsigned long long* comp, uint32_t base, uint32_t m, uint32_t* s,
+                          unsigned long long* s64)
+{
+    const uint32_t tid = threadIdx.x;
+    const bool packed = w0 + 1 == W;
+    uint32_t P = 2;
+    while (P < m) P <<= 1;
+    for (uint32_t x = tid; x < P; x += REC_BLOCK) {
+        const uint32_t p = x < m ? perm[base + x] : NONE;
+        if (packed) s64[x] = x < m ? ((unsigned long long)__ldg(rec + (size_t)p * W + w0) << 32) | p : ~0ull;
+        else s[x] = p;
+    }
+    __syncthreads();
+    for (uint32_t k = 2; k <= P; k <<= 1) {
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            for (uint32_t x = tid; x < P; x += REC_BLOCK) {
+                const uint32_t y = x ^ j;
+                if (y <= x) continue;
+                const bool up = (x & k) == 0;
+                if (packed) {
+                    const unsigned long long u = s64[x], v = s64[y];
+                    if (up ? v < u : u < v) {
+                        s64[x] = v;
+                        s64[y] = u;
+                    }
+                } else {
+                    const uint32_t u = s[x], v = s[y];
+                    // NONE (padding) sorts last
+                    const bool v_first = u == NONE ? v != NONE : (v != NONE && rec_less(rec, W, w0, v, u));
+                    if (up ? v_first : !v_first && u != v) {
+                        s[x] = v;
+                        s[y] = u;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (uint32_t x = tid; x < m; x += REC_BLOCK) {
+        if (!packed) perm[base + x] = s[x];
+        else if (comp) comp[base + x] = s64[x];
+        else perm[base + x] = (uint32_t)s64[x];
+    }
+    __syncthreads();
+}
+
+// Sort every group by (row from word L + 1, index): a group of up to
+// REC_SMEM entries whole, by one CTA; the blocks of larger groups spread
+// over all CTAs (their merge passes follow in k_rec_fix_big).
 __global__ void __launch_bounds__(REC_BLOCK) k_rec_fix(const uint32_t* rec, uint32_t W, uint32_t* perm,
-                                                       const uint32_t* groups, uint32_t cap, Ctr* C)
+                                                       unsigned long long* comp, const uint32_t* groups,
+                                                       uint32_t cap, const uint32_t* big, uint32_t big_cap, Ctr* C)
 {
     __shared__ uint32_t s[REC_SMEM];
+    __shared__ unsigned long long s64[REC_SMEM];
     const uint32_t L = *(volatile const uint32_t*)&C->rec_lcp;
     if (L >= W - 1 || *(volatile uint32_t*)&C->error) return;   // NONE: all rows equal
     const uint32_t w0 = L + 1;
     const uint32_t ng = min(*(volatile const uint32_t*)&C->rec_groups, cap);
-    const uint32_t tid = threadIdx.x;
     for (uint32_t gi = blockIdx.x; gi < ng; gi += gridDim.x) {
         const uint32_t a = groups[2 * gi], g = groups[2 * gi + 1] - a;
-        // blocks of up to REC_SMEM entries: bitonic sort in shared memory
-        for (uint32_t b0 = 0; b0 < g; b0 += REC_SMEM) {
-            const uint32_t m = min(REC_SMEM, g - b0);
-            uint32_t P = 2;
-            while (P < m) P <<= 1;
-            for (uint32_t x = tid; x < P; x += REC_BLOCK) s[x] = x < m ? perm[a + b0 + x] : NONE;
-            __syncthreads();
-            for (uint32_t k = 2; k <= P; k <<= 1) {
-                for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-                    for (uint32_t x = tid; x < P; x += REC_BLOCK) {
-                        const uint32_t y = x ^ j;
-                        if (y > x) {
-                            const uint32_t u = s[x], v = s[y];
-                            // NONE (padding) sorts last
-                            const bool v_first = u == NONE ? v != NONE : (v != NONE && rec_less(rec, W, w0, v, u));
-                            const bool up = (x & k) == 0;
-                            if (up ? v_first : !v_first && u != v) {
-                                s[x] = v;
-                                s[y] = u;
-                            }
-                        }
-                    }
-                    __syncthreads();
-                }
-            }
-            for (uint32_t x = tid; x < m; x += REC_BLOCK) perm[a + b0 + x] = s[x];
-            __syncthreads();
-        }
+        if (g <= REC_SMEM) fix_block(rec, W, w0, perm, nullptr, a, g, s, s64);
+    }
+    const uint32_t nbig = min(*(volatile const uint32_t*)&C->rec_nbig, big_cap);
+    for (uint32_t b = 0; b < nbig; ++b) {
+        const uint32_t a = big[2 * b], g = big[2 * b + 1] - a;
+        const uint32_t nblk = (g + REC_SMEM - 1) / REC_SMEM;
+        for (uint32_t k = blockIdx.x; k < nblk; k += gridDim.x)
+            fix_block(rec, W, w0, perm, comp, a + k * REC_SMEM, min(REC_SMEM, g - k * REC_SMEM), s, s64);
+    }
+}
+
+// Outputs [o0, o0 + 16) of one merge pass over packed words (distinct, so
+// no tie rule is needed).
+__device__ void merge_chunk16_packed(const unsigned long long* src, unsigned long long* dst, uint32_t g, uint32_t w,
+                                     uint32_t o0)
+{
+    const uint32_t x = o0 - o0 % (2 * w);
+    const uint32_t na = min(w, g - x), nb = g - x > w ? min(w, g - x - w) : 0u;
+    const unsigned long long* A = src + x;
+    const unsigned long long* B = src + x + na;
+    const uint32_t d = o0 - x;
+    uint32_t lo = d > nb ? d - nb : 0u, hi = min(d, na);
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (A[mid] < B[d - 1 - mid]) lo = mid + 1; else hi = mid;
+    }
+    uint32_t ia = lo, ib = d - lo;
+    const uint32_t end = min(o0 + 16u, x + na + nb);
+    for (uint32_t o = o0; o < end; ++o) {
+        const bool take_a = ia < na && (ib >= nb || A[ia] < B[ib]);
+        dst[o] = take_a ? A[ia++] : B[ib++];
     }
 }
 
 // The merge passes of every group larger than REC_SMEM (its blocks already
-// sorted by k_rec_fix): pass p merges pairs of width REC_SMEM << p from perm
-// to tmp (even p) or back (odd p), for every group that still has pairs;
-// chunks of 16 outputs of all such groups are spread over the grid, and a
-// grid barrier separates the passes.  A group whose last pass wrote tmp is
-// copied back at the end.
+// sorted by k_rec_fix): pass p merges pairs of width REC_SMEM << p, for
+// every group that still has pairs; chunks of 16 outputs of all such groups
+// are spread over the grid, and a grid barrier separates the passes.  Rows
+// compared through perm <-> tmp, or packed words through comp <-> comp2;
+// at the end every group's entries are back in perm.
 __global__ void __launch_bounds__(REC_BLOCK) k_rec_fix_big(const uint32_t* rec, uint32_t W, uint32_t* perm,
-                                                           uint32_t* tmp, const uint32_t* big, uint32_t big_cap,
-                                                           Ctr* C)
+                                                           uint32_t* tmp, unsigned long long* comp,
+                                                           unsigned long long* comp2, const uint32_t* big,
+                                                           uint32_t big_cap, Ctr* C)
 {
     const uint32_t L = *(volatile const uint32_t*)&C->rec_lcp;
     if (L >= W - 1 || *(volatile uint32_t*)&C->error) return;
     const uint32_t gmax = *(volatile const uint32_t*)&C->rec_gmax;
     if (gmax <= REC_SMEM) return;                     // the same answer in every CTA
     const uint32_t w0 = L + 1;
+    const bool packed = w0 + 1 == W;
     const uint32_t nbig = min(*(volatile const uint32_t*)&C->rec_nbig, big_cap);
     const uint32_t gt = blockIdx.x * REC_BLOCK + threadIdx.x, gs = gridDim.x * REC_BLOCK;
     const uint32_t passes = merge_passes(gmax);
     for (uint32_t p = 0; p < passes; ++p) {
         const uint32_t w = REC_SMEM << p;
-        const uint32_t* from = (p & 1u) ? tmp : perm;
-        uint32_t* to = (p & 1u) ? perm : tmp;
         for (uint32_t b = 0; b < nbig; ++b) {
             const uint32_t a = big[2 * b], g = big[2 * b + 1] - a;
             if (g <= w) continue;
             const uint32_t chunks = (g + 15u) >> 4;
-            for (uint32_t c = gt; c < chunks; c += gs) merge_chunk16(rec, W, w0, from + a, to + a, g, w, c * 16u);
+            for (uint32_t c = gt; c < chunks; c += gs) {
+                if (packed) {
+                    const unsigned long long* from = (p & 1u) ? comp2 : comp;
+                    unsigned long long* to = (p & 1u) ? comp : comp2;
+                    merge_chunk16_packed(from + a, to + a, g, w, c * 16u);
+                } else {
+                    const uint32_t* from = (p & 1u) ? tmp : perm;
+                    uint32_t* to = (p & 1u) ? perm : tmp;
+                    merge_chunk16(rec, W, w0, from + a, to + a, g, w, c * 16u);
+                }
+            }
         }
         if (!grid_barrier(C)) return;
     }
     for (uint32_t b = 0; b < nbig; ++b) {
         const uint32_t a = big[2 * b], g = big[2 * b + 1] - a;
-        if (merge_passes(g) & 1u)
+        const bool odd = (merge_passes(g) & 1u) != 0;   // the last pass wrote the second buffer
+        if (packed) {
+            const unsigned long long* fin = odd ? comp2 : comp;
+            for (uint32_t x = gt; x < g; x += gs) perm[a + x] = (uint32_t)fin[a + x];
+        } else if (odd) {
             for (uint32_t x = gt; x < g; x += gs) perm[a + x] = tmp[a + x];
+        }
     }
 }
 
@@ -298,12 +386,14 @@ cudaError_t launch_records_prepare(const uint32_t* rec, uint32_t W, unsigned lon
 }
 
 cudaError_t launch_records_fix(const uint32_t* rec, uint32_t W, unsigned long long n, const uint32_t* keys,
-                               uint32_t* perm, uint32_t* tmp, uint32_t* groups, uint32_t cap, uint32_t* big,
-                               uint32_t big_cap, Ctr* C, int grid, int coop_grid, cudaStream_t s)
+                               uint32_t* perm, uint32_t* tmp, unsigned long long* comp, unsigned long long* comp2,
+                               uint32_t* groups, uint32_t cap, uint32_t* big, uint32_t big_cap, Ctr* C, int grid,
+                               int coop_grid, cudaStream_t s)
 {
     k_rec_groups<<<grid, REC_BLOCK, 0, s>>>(keys, W, n, groups, cap, big, big_cap, C);
-    k_rec_fix<<<grid, REC_BLOCK, 0, s>>>(rec, W, perm, groups, cap, C);
-    void* args[] = {(void*)&rec, (void*)&W, (void*)&perm, (void*)&tmp, (void*)&big, (void*)&big_cap, (void*)&C};
+    k_rec_fix<<<grid, REC_BLOCK, 0, s>>>(rec, W, perm, comp, groups, cap, big, big_cap, C);
+    void* args[] = {(void*)&rec, (void*)&W,   (void*)&perm,    (void*)&tmp, (void*)&comp,
+                    (void*)&comp2, (void*)&big, (void*)&big_cap, (void*)&C};
     return cudaLaunchCooperativeKernel((const void*)k_rec_fix_big, dim3(coop_grid), dim3(REC_BLOCK), args, 0, s);
 }
 
