@@ -83,6 +83,11 @@ def test_argument_errors_need_no_gpu(lib):
     assert lib.ps_run_batched(None, None, None, None, 1, None) == binding.PS_EINVAL
     assert lib.ps_sync(None) == binding.PS_EINVAL
     assert lib.ps_get_runs(None, 0, None, 0, None) == binding.PS_EINVAL
+    assert lib.ps_sort_records(None, None, 30, 10, None, None, None) == binding.PS_EINVAL
+    assert lib.ps_sort_keys64(None, None, 10, None, 0, None) == binding.PS_EINVAL
+    assert lib.ps_gather_rows(None, None, None, 0, 10, None, None, 4) == binding.PS_EINVAL
+    cfg = binding.ps_config(mode=0, want_perm=1, max_n=100, key_type=3)
+    assert lib.ps_create(ctypes.byref(cfg), 0, None, ctypes.byref(h)) == binding.PS_EINVAL
     lib.ps_destroy(None)
 
 
