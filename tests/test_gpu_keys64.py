@@ -85,3 +85,12 @@ def test_f64_special_values(kctx, oracle_mod):
 def test_keys64_2_21(kctx, oracle_mod):
     for kind in ("u64", "f64"):
         check(kctx, oracle_mod, gen(kind, "uniform", 1 << 21, 11), kind)
+
+
+def test_keys64_with_vm_storage(oracle_mod):
+    from paper_2605_27147_gb300 import binding
+
+    with binding.Context(1 << 20, mode=binding.PS_MODE_VM, page_log2=9, want_perm=True,
+                         flags=binding.PS_FLAG_RECORDS) as c:
+        for kind in ("u64", "i64"):
+            check(c, oracle_mod, gen(kind, "few" if kind == "i64" else "runs", 500009, 3), kind)

@@ -106,3 +106,12 @@ def test_records_need_the_flag():
     with _ctx(1 << 10) as c:
         with pytest.raises(binding.PowersortError):
             c.sort_records(torch.zeros((10, 0), dtype=torch.int32, device="cuda"), perm)
+
+
+def test_records_with_vm_storage(oracle_mod):
+    # the window keys go through the paged merge rounds instead of Pingpong
+    from paper_2605_27147_gb300 import binding
+
+    with _ctx(1 << 20, mode=binding.PS_MODE_VM, page_log2=8) as c:
+        for kind, n in (("random", 300007), ("few", 100003)):
+            check(c, oracle_mod, inputs.records(kind, n, 8, words=30 if kind == "random" else 6))
