@@ -277,7 +277,9 @@ typedef struct ps_server_config {
     uint32_t lanes;          /* batches in flight at once (0: 4)                   */
     uint32_t want_perm;      /* nonzero: requests may ask for the permutation      */
     uint32_t device;
-    uint32_t reserved[4];
+    uint32_t key_type;       /* ps_key_type of every request's keys                */
+    uint32_t flags;          /* PS_FLAG_DESCENDING_RUNS or 0                      */
+    uint32_t reserved[2];
 } ps_server_config;
 
 typedef struct ps_server_stats {

@@ -253,6 +253,8 @@ PS_API ps_status ps_server_create(const ps_server_config* cfg, ps_server** out)
         std::memset(&c, 0, sizeof(c));
         c.mode = PS_MODE_PINGPONG;
         c.want_perm = S->cfg.want_perm;
+        c.key_type = S->cfg.key_type;
+        c.flags = S->cfg.flags & PS_FLAG_DESCENDING_RUNS;
         c.max_n = S->cfg.max_n;
         c.max_total = lane_total;
         c.max_count = S->lane_count;

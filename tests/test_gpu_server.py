@@ -77,3 +77,26 @@ def test_server_budget_too_small():
     with pytest.raises(binding.PowersortError) as e:
         binding.Server(1 << 20, 1 << 20, lanes=2, lane_max_total=1 << 20)
     assert e.value.status == binding.PS_ENOMEM
+
+
+def test_typed_keys_and_decreasing_runs(oracle_mod):
+    # every lane sorts float keys (totalOrder) with the decreasing-run variant
+    from paper_2605_27147_gb300 import binding
+
+    rng = np.random.RandomState(9)
+    reqs = []
+    for i, n in enumerate([0, 1, 100, 5000, 70001, 300007]):
+        f = (inputs.updown(n, 40 + i, mean_run=float(rng.choice([20, 900]))).astype(np.float64) - 2.0 ** 31)
+        keys = f.astype(np.float32).view(np.uint32)
+        reqs.append((keys, _pinned(keys), torch.empty(max(n, 1), dtype=torch.int32).pin_memory(),
+                     torch.empty(max(n, 1), dtype=torch.int32).pin_memory()))
+    with binding.Server(1 << 30, 1 << 20, lanes=2, lane_max_total=1 << 20, lane_max_count=4,
+                        key_type=binding.PS_KEY_F32, flags=binding.PS_FLAG_DESCENDING_RUNS) as srv:
+        tickets = [srv.submit(hin.data_ptr(), hk.data_ptr(), hp.data_ptr(), keys.size) for keys, hin, hk, hp in reqs]
+        for t in tickets:
+            srv.wait(t, 120.0)
+    for keys, hin, hk, hp in reqs:
+        n = keys.size
+        ref = oracle_mod.powersort(keys, key_type="f32", descending_runs=True)
+        assert np.array_equal(hk.numpy().view(np.uint32)[:n], ref.keys)
+        assert np.array_equal(hp.numpy().view(np.uint32)[:n], ref.perm)
