@@ -87,7 +87,7 @@ __device__ __forceinline__ uint32_t merge_passes(uint32_t g)
 // and the row before it (contiguous words, coalesced loads), then every
 // thread compares its row with the one before in shared memory.
 __global__ void __launch_bounds__(REC_BLOCK) k_rec_scan_tiled(const uint32_t* rec, uint32_t W, unsigned long long n,
-                                                              uint32_t* mask, Ctr* C)
+                                                              uint32_t* mask, uint32_t* keys, Ctr* C)
 {
     extern __shared__ uint32_t rows[];   // (REC_BLOCK + 1) * W words
     const uint32_t tid = threadIdx.x, lane = tid & 31u;
@@ -104,6 +104,9 @@ __global__ void __launch_bounds__(REC_BLOCK) k_rec_scan_tiled(const uint32_t* re
         for (uint32_t x = tid; x < nw; x += REC_BLOCK) d[x] = __ldg(g + x);
         __syncthreads();
         const unsigned long long i = t0 + tid;
+        // word 0 is the window whenever any two neighbours differ there (the
+        // usual case): written now, k_rec_key then has nothing to do
+        if (i < n) keys[i] = rows[(size_t)(tid + 1) * W];
         bool desc = false;
         if (i > 0 && i < n) {
             const uint32_t* ra = rows + (size_t)tid * W;   // row i - 1 at slot tid
@@ -160,11 +163,14 @@ __global__ void __launch_bounds__(REC_BLOCK) k_rec_scan(const uint32_t* rec, uin
     if (lane == 0 && lcp < W) atomicMin(&C->rec_lcp, lcp);
 }
 
-// The window key of every row: word L (0 when every row is equal).
+// The window key of every row: word L (0 when every row is equal).  When
+// skip0 is set the tiled scan has already written word 0, which is the
+// window when L = 0.
 __global__ void __launch_bounds__(REC_BLOCK) k_rec_key(const uint32_t* rec, uint32_t W, unsigned long long n,
-                                                       uint32_t* keys, const Ctr* C)
+                                                       uint32_t* keys, const Ctr* C, int skip0)
 {
     const uint32_t L = *(volatile const uint32_t*)&C->rec_lcp;
+    if (skip0 && L == 0) return;
     const unsigned long long stride = (unsigned long long)gridDim.x * REC_BLOCK;
     for (unsigned long long i = (unsigned long long)blockIdx.x * REC_BLOCK + threadIdx.x; i < n; i += stride)
         keys[i] = L < W ? __ldg(rec + (size_t)i * W + L) : 0u;
@@ -377,11 +383,12 @@ cudaError_t launch_records_prepare(const uint32_t* rec, uint32_t W, unsigned lon
         const size_t smem = (size_t)(REC_BLOCK + 1) * W * sizeof(uint32_t);
         if (smem > 48 * 1024)
             cudaFuncSetAttribute(k_rec_scan_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_rec_scan_tiled<<<grid, REC_BLOCK, smem, s>>>(rec, W, n, mask, C);
+        k_rec_scan_tiled<<<grid, REC_BLOCK, smem, s>>>(rec, W, n, mask, keys, C);
+        k_rec_key<<<grid, REC_BLOCK, 0, s>>>(rec, W, n, keys, C, 1);
     } else {
         k_rec_scan<<<grid, REC_BLOCK, 0, s>>>(rec, W, n, mask, C);
+        k_rec_key<<<grid, REC_BLOCK, 0, s>>>(rec, W, n, keys, C, 0);
     }
-    k_rec_key<<<grid, REC_BLOCK, 0, s>>>(rec, W, n, keys, C);
     return cudaGetLastError();
 }
 
