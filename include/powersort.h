@@ -55,7 +55,8 @@ typedef enum ps_status {
     PS_ENOMEM = 2,
     PS_ECUDA = 3,
     PS_ETIMEOUT = 4,
-    PS_EINTERNAL = 5
+    PS_EINTERNAL = 5,
+    PS_ECANCELED = 6    /* a server request cancelled before it ran             */
 } ps_status;
 
 /* Run storage (Sec. 1 "Pingpong Powersort" and "Virtual-Memory Powersort"). */
@@ -236,6 +237,20 @@ PS_API ps_status ps_get_round_times(ps_ctx* ctx, float* h_us, uint32_t cap, uint
  * after enqueueing, so this is where such errors surface). */
 PS_API ps_status ps_sync(ps_ctx* ctx);
 
+/* Failure detection, exercised on purpose: a cooperative launch of two CTAs
+ * in which one never arrives at the grid barrier the other waits at (the
+ * same barrier and spin limit every persistent kernel of the library uses).
+ * The waiting CTA gives up after the limit (about two seconds), records the
+ * timeout and returns; the call returns PS_ETIMEOUT and the context stays
+ * usable (the next sort resets the device status).  No GPU fault, trap or
+ * hang is involved. */
+PS_API ps_status ps_selftest_wait_timeout(ps_ctx* ctx);
+
+/* Canary words after every device buffer the context owns: PS_OK while they
+ * hold their pattern, PS_EINTERNAL if a kernel wrote past a buffer's end
+ * (synchronises). */
+PS_API ps_status ps_check_guards(ps_ctx* ctx);
+
 /* Introspection of the last call, for parity checks (synchronises).
  *   ps_get_runs:   run starts of instance q plus its end (runs + 1 entries),
  *                  instance-local (ExtractRun, Sec. 2 / Sec. 5).
@@ -289,6 +304,11 @@ typedef struct ps_server_stats {
     uint32_t lanes;
     uint32_t max_busy_lanes; /* most lanes seen busy at once (overlap evidence)    */
 } ps_server_stats;
+
+/* Cancel a queued request: PS_OK when it had not left the queue (its wait /
+ * poll then return PS_ECANCELED and it counts as failed), PS_EINVAL when the
+ * ticket is unknown or the request is already on the GPU or done. */
+PS_API ps_status ps_server_cancel(ps_server* srv, uint64_t ticket);
 
 /* Start a server (allocates every lane up front; PS_ENOMEM if the lanes do not
  * fit the budget). */

@@ -14,7 +14,7 @@ import numpy as np
 
 from . import build as _build
 
-PS_OK, PS_EINVAL, PS_ENOMEM, PS_ECUDA, PS_ETIMEOUT, PS_EINTERNAL = range(6)
+PS_OK, PS_EINVAL, PS_ENOMEM, PS_ECUDA, PS_ETIMEOUT, PS_EINTERNAL, PS_ECANCELED = range(7)
 PS_MODE_PINGPONG, PS_MODE_VM = 0, 1
 
 # every symbol include/powersort.h declares
@@ -24,7 +24,7 @@ EXPORTS = (
     "ps_destroy", "ps_run_noalloc", "ps_get_round_times", "ps_graph_create_batched",
     "ps_graph_launch", "ps_graph_destroy", "ps_server_create", "ps_server_submit", "ps_server_poll",
     "ps_server_wait", "ps_server_get_stats", "ps_server_destroy", "ps_gather_rows", "ps_sort_records",
-    "ps_sort_keys64",
+    "ps_sort_keys64", "ps_selftest_wait_timeout", "ps_check_guards", "ps_server_cancel",
 )
 PS_NOALLOC_MAX_N = 262144
 PS_FLAG_TIMING, PS_FLAG_HOST_IO, PS_FLAG_DESCENDING_RUNS, PS_FLAG_RECORDS = 1, 2, 4, 8
@@ -149,6 +149,12 @@ def lib(build_if_missing: bool = True):
                                          ctypes.POINTER(ctypes.c_uint32)]
         L.ps_sync.restype = ctypes.c_int
         L.ps_sync.argtypes = [vp]
+        L.ps_selftest_wait_timeout.restype = ctypes.c_int
+        L.ps_selftest_wait_timeout.argtypes = [vp]
+        L.ps_check_guards.restype = ctypes.c_int
+        L.ps_check_guards.argtypes = [vp]
+        L.ps_server_cancel.restype = ctypes.c_int
+        L.ps_server_cancel.argtypes = [vp, ctypes.c_uint64]
         L.ps_sort_keys64.restype = ctypes.c_int
         L.ps_sort_keys64.argtypes = [vp, vp, ctypes.c_uint64, vp, ctypes.c_uint32, ctypes.POINTER(ps_stats)]
         L.ps_sort_records.restype = ctypes.c_int
@@ -269,6 +275,14 @@ class Context:
         _check(lib().ps_sort_records(self._h, _ptr(rec), words, n, _ptr(perm), _ptr(out),
                                      ctypes.byref(st) if st is not None else None), "ps_sort_records")
         return st.as_dict() if st is not None else None
+
+    def check_guards(self):
+        """ps_check_guards: raises if a canary word after a device buffer changed."""
+        _check(lib().ps_check_guards(self._h), "ps_check_guards")
+
+    def selftest_wait_timeout(self) -> int:
+        """ps_selftest_wait_timeout: the status it returns (PS_ETIMEOUT expected)."""
+        return int(lib().ps_selftest_wait_timeout(self._h))
 
     def sort_keys64(self, keys, perm, key_type: int = PS_KEY_U32, *, stats: bool = False):
         """ps_sort_keys64: ``keys`` is a 64-bit tensor sorted in place (as
@@ -392,6 +406,13 @@ class Server:
         _check(lib().ps_server_submit(self._h, in_ptr, keys_out_ptr, perm_out_ptr, n, ctypes.byref(t)),
                "ps_server_submit")
         return t.value
+
+    def cancel(self, ticket: int) -> bool:
+        """ps_server_cancel: True if the request was still queued and is now cancelled."""
+        st = lib().ps_server_cancel(self._h, ticket)
+        if st not in (PS_OK, PS_EINVAL):
+            _check(st, "ps_server_cancel")
+        return st == PS_OK
 
     def poll(self, ticket: int):
         done, lat = ctypes.c_int(), ctypes.c_double()

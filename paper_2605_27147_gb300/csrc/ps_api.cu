@@ -24,6 +24,7 @@ struct ps_ctx {
     int last_valid;
     size_t scratch_bytes;
     std::vector<void*> allocs;
+    std::vector<unsigned char*> guards;   // canary words after every allocation
     bool timing;
     bool capturing;             // inside ps_graph_create_batched: no events, no syncs
     cudaEvent_t ev[7];          // phase boundaries of the last call (PS_FLAG_TIMING)
@@ -59,17 +60,29 @@ struct DeviceGuard {
     }
 };
 
+constexpr size_t GUARD_BYTES = 64;
+constexpr unsigned char GUARD_BYTE = 0xa5;
+
+// Device allocation owned by the context, followed by GUARD_BYTES of canary
+// (ps_check_guards reads them back).
 template <typename T>
 ps_status dev_alloc(ps_ctx* c, T** p, size_t count)
 {
     *p = nullptr;
     if (count == 0) return PS_OK;
     void* q = nullptr;
-    if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) {
+    const size_t bytes = (count * sizeof(T) + 15) & ~(size_t)15;
+    if (cudaMalloc(&q, bytes + GUARD_BYTES) != cudaSuccess) {
         cudaGetLastError();
         return PS_ENOMEM;
     }
     c->allocs.push_back(q);
+    unsigned char* g = static_cast<unsigned char*>(q) + bytes;
+    if (cudaMemset(g, GUARD_BYTE, GUARD_BYTES) != cudaSuccess) {
+        cudaGetLastError();
+        return PS_ECUDA;
+    }
+    c->guards.push_back(g);
     c->scratch_bytes += count * sizeof(T);
     *p = static_cast<T*>(q);
     return PS_OK;
@@ -83,6 +96,7 @@ void free_all(ps_ctx* c)
     c->timing = false;
     for (void* p : c->allocs) cudaFree(p);
     c->allocs.clear();
+    c->guards.clear();
     if (c->h_ctr) cudaFreeHost(c->h_ctr);
     if (c->h_inst) cudaFreeHost(c->h_inst);
     c->h_ctr = nullptr;
@@ -213,6 +227,7 @@ PS_API const char* ps_status_str(ps_status s)
     case PS_ECUDA: return "PS_ECUDA: CUDA call failed";
     case PS_ETIMEOUT: return "PS_ETIMEOUT: device-side wait exceeded its limit";
     case PS_EINTERNAL: return "PS_EINTERNAL: device-side consistency check failed";
+    case PS_ECANCELED: return "PS_ECANCELED: request cancelled before it ran";
     }
     return "unknown ps_status";
 }
@@ -650,6 +665,41 @@ PS_API ps_status ps_gather_rows(ps_ctx* ctx, const uint32_t* d_perm, const uint6
                         ctx->stream) != cudaSuccess)
         return PS_ECUDA;
     return PS_OK;
+}
+
+PS_API ps_status ps_check_guards(ps_ctx* ctx)
+{
+    if (!ctx) return PS_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return PS_ECUDA;
+    }
+    unsigned char h[GUARD_BYTES];
+    for (unsigned char* d : ctx->guards) {
+        if (cudaMemcpy(h, d, GUARD_BYTES, cudaMemcpyDeviceToHost) != cudaSuccess) return PS_ECUDA;
+        for (size_t i = 0; i < GUARD_BYTES; ++i)
+            if (h[i] != GUARD_BYTE) return PS_EINTERNAL;
+    }
+    return PS_OK;
+}
+
+PS_API ps_status ps_selftest_wait_timeout(ps_ctx* ctx)
+{
+    if (!ctx) return PS_EINVAL;
+    DeviceGuard g(ctx->device);
+    ps::Ctr* C = ctx->base.ctr;
+    cudaStream_t s = ctx->stream;
+    // a clean status and barrier, the probe, then the barrier counters reset
+    // (a CTA that never arrived leaves its group's count behind)
+    if (cudaMemsetAsync(&C->error, 0, 2 * sizeof(uint32_t), s) != cudaSuccess) return PS_ECUDA;   // error, err_where
+    if (ps::launch_wait_probe(C, s) != cudaSuccess) return PS_ECUDA;
+    if (cudaMemcpyAsync(&ctx->h_ctr->error, &C->error, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return PS_ECUDA;
+    if (cudaMemsetAsync(&C->bar_count, 0, sizeof(uint32_t), s) != cudaSuccess ||
+        cudaMemsetAsync(C->bar_group, 0, sizeof(C->bar_group), s) != cudaSuccess)
+        return PS_ECUDA;
+    return sync_and_check(ctx);
 }
 
 PS_API ps_status ps_sync(ps_ctx* ctx)

@@ -442,6 +442,7 @@ cudaError_t launch_records_fix(const uint32_t* rec, uint32_t W, unsigned long lo
 int records_fix_big_grid(int num_sms);
 cudaError_t launch_key64(bool in, const void* rows, void* keys, unsigned long long n, uint32_t type, int grid,
                          cudaStream_t s);
+cudaError_t launch_wait_probe(Ctr* C, cudaStream_t s);
 cudaError_t launch_gather_rows(const uint32_t* perm, const unsigned long long* offsets, uint32_t count,
                                unsigned long long n, unsigned long long max_total, const void* src, void* dst,
                                uint32_t row_bytes, Ctr* ctr, int grid, cudaStream_t s);

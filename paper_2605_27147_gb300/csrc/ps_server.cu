@@ -304,6 +304,26 @@ PS_API ps_status ps_server_submit(ps_server* S, const uint32_t* h_in, uint32_t* 
     return PS_OK;
 }
 
+PS_API ps_status ps_server_cancel(ps_server* S, uint64_t ticket)
+{
+    if (!S) return PS_EINVAL;
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (ticket >= S->reqs.size() || S->reqs[ticket].state != QUEUED) return PS_EINVAL;
+    for (auto it = S->queue.begin(); it != S->queue.end(); ++it) {
+        if (*it == ticket) {
+            S->queue.erase(it);
+            break;
+        }
+    }
+    Req& r = S->reqs[ticket];
+    r.state = FAILED;
+    r.status = PS_ECANCELED;
+    r.latency_s = std::chrono::duration<double>(Clock::now() - r.t_submit).count();
+    ++S->failed;
+    S->cv_done.notify_all();
+    return PS_OK;
+}
+
 PS_API ps_status ps_server_poll(ps_server* S, uint64_t ticket, int* done, double* latency_s)
 {
     if (!S || !done) return PS_EINVAL;

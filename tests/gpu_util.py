@@ -43,6 +43,7 @@ def assert_matches_oracle(ctx, keys: np.ndarray, ref, got_keys, got_perm, stats,
     assert ist["minrun"] == ref.stats["minrun"]
     if stats is not None and q == 0 and stats.get("instances", 1) == 1:
         assert stats["merge_cost"] == ref.stats["merge_cost"]
+    ctx.check_guards()   # no kernel wrote past the end of a buffer the context owns
 
 
 def _first_diff(name, a, b):

@@ -60,7 +60,7 @@ def test_only_declared_symbols_are_exported(lib):
 
 
 def test_status_strings(lib):
-    for code in range(6):
+    for code in range(7):
         assert lib.ps_status_str(code).startswith(b"PS_")
 
 
@@ -86,6 +86,9 @@ def test_argument_errors_need_no_gpu(lib):
     assert lib.ps_sort_records(None, None, 30, 10, None, None, None) == binding.PS_EINVAL
     assert lib.ps_sort_keys64(None, None, 10, None, 0, None) == binding.PS_EINVAL
     assert lib.ps_gather_rows(None, None, None, 0, 10, None, None, 4) == binding.PS_EINVAL
+    assert lib.ps_selftest_wait_timeout(None) == binding.PS_EINVAL
+    assert lib.ps_check_guards(None) == binding.PS_EINVAL
+    assert lib.ps_server_cancel(None, 0) == binding.PS_EINVAL
     cfg = binding.ps_config(mode=0, want_perm=1, max_n=100, key_type=3)
     assert lib.ps_create(ctypes.byref(cfg), 0, None, ctypes.byref(h)) == binding.PS_EINVAL
     lib.ps_destroy(None)

@@ -100,3 +100,30 @@ def test_typed_keys_and_decreasing_runs(oracle_mod):
         ref = oracle_mod.powersort(keys, key_type="f32", descending_runs=True)
         assert np.array_equal(hk.numpy().view(np.uint32)[:n], ref.keys)
         assert np.array_equal(hp.numpy().view(np.uint32)[:n], ref.perm)
+
+
+def test_cancel_queued_requests(oracle_mod):
+    # one lane, one request per batch: while a large request holds the lane,
+    # the small ones behind it are still queued and can be cancelled
+    from paper_2605_27147_gb300 import binding
+
+    big = inputs.make("uniform", 1 << 22, 1)
+    small = [inputs.make("uniform", 5000, 2 + i) for i in range(6)]
+    bufs = [(k, _pinned(k), torch.empty(k.size, dtype=torch.int32).pin_memory(),
+             torch.empty(k.size, dtype=torch.int32).pin_memory()) for k in [big] + small]
+    with binding.Server(1 << 30, 1 << 22, lanes=1, lane_max_total=1 << 22, lane_max_count=1) as srv:
+        tickets = [srv.submit(hin.data_ptr(), hk.data_ptr(), hp.data_ptr(), k.size) for k, hin, hk, hp in bufs]
+        cancelled = [srv.cancel(t) for t in tickets[1:4]]
+        assert any(cancelled)
+        for i, t in enumerate(tickets):
+            k, hin, hk, hp = bufs[i]
+            if 1 <= i <= 3 and cancelled[i - 1]:
+                with pytest.raises(binding.PowersortError) as e:
+                    srv.wait(t, 120.0)
+                assert e.value.status == binding.PS_ECANCELED
+                assert not srv.cancel(t)             # only once
+            else:
+                srv.wait(t, 120.0)
+                assert np.array_equal(hk.numpy().view(np.uint32), oracle_mod.stable_sort(k)[0])
+        st = srv.stats()
+        assert st["failed"] == sum(cancelled) and st["completed"] == len(tickets) - sum(cancelled)
