@@ -127,3 +127,23 @@ def test_unaligned_caller_arrays(ctx, oracle_mod):
         assert np.array_equal(to_host(dk), ref.keys)
         assert np.array_equal(to_host(dp), ref.perm)
         assert st["merge_cost"] == ref.stats["merge_cost"]
+
+
+def test_host_arrays(oracle_mod):
+    # ps_run_host: pinned host arrays in and out, copies inside the call
+    from paper_2605_27147_gb300 import binding
+
+    with binding.Context(1 << 20, want_perm=True, flags=binding.PS_FLAG_HOST_IO) as c:
+        for n in (1, 2, 3, 4097, 300007, 1 << 20):
+            keys = inputs.make("runs", n, 70 + n)
+            ref = oracle_mod.powersort(keys)
+            hk = torch.from_numpy(keys.view(np.int32).copy()).pin_memory()
+            hp = torch.empty(n, dtype=torch.int32).pin_memory()
+            st = c.run_host(hk.data_ptr(), n, hp.data_ptr(), stats=True)
+            assert np.array_equal(hk.numpy().view(np.uint32), ref.keys)
+            assert np.array_equal(hp.numpy().view(np.uint32), ref.perm)
+            assert st["merge_cost"] == ref.stats["merge_cost"]
+            hk2 = torch.from_numpy(keys.view(np.int32).copy()).pin_memory()
+            c.run_host(hk2.data_ptr(), n, None)              # keys only
+            assert np.array_equal(hk2.numpy().view(np.uint32), ref.keys)
+        c.check_guards()
