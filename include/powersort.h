@@ -84,7 +84,7 @@ typedef struct ps_config {
     uint32_t page_log2;  /* VM page size P = 2^page_log2 (0: chosen from max_n as
                             sqrt(n / log2 n) rounded to a power of two, Sec. 4)      */
     uint32_t tile_log2;  /* on-chip tile capacity 2^tile_log2 in 10..12 (0: 12)      */
-    uint32_t pool_pages; /* VM page-pool size in pages (0: chosen by the library)    */
+    uint32_t pool_pages; /* VM page-pool size in pages (0: chosen by the library; >= 16) */
     uint32_t flags;      /* PS_FLAG_* below                                          */
     uint32_t key_type;   /* ps_key_type of the keys this context sorts               */
     uint32_t reserved[2];

@@ -312,7 +312,8 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
         J.vm = 1;
         J.vm_plog2 = plog2;
         J.vm_na_cap = (uint32_t)((cfg->max_n + (1ull << plog2) - 1) >> plog2);
-        // a wave: one output page for every page group of every CTA
+        // pages in flight: one output page per page group of every CTA; the
+        // pool holds them plus slack for partly consumed pages
         J.vm_wave_max = (uint32_t)c->grid_vm * ps::vm_groups_per_cta(plog2);
         J.vm_pool = cfg->pool_pages ? cfg->pool_pages : J.vm_wave_max + 64;
         if (J.vm_pool < 16) J.vm_pool = 16;
