@@ -218,9 +218,7 @@ def run_reference(args):
     if args.workload == "records_2^23":
         return run_reference_records(args)
     if args.workload == "keys64_2^24":
-        print(json.dumps({"impl": "reference", "unavailable": "keys64_2^24 has no CPU reference arm; "
-                          "tests/test_gpu_keys64.py checks it against the oracle"}), flush=True)
-        return
+        return run_reference_keys64(args)
     if args.workload == "batched_4096":
         from paper_2605_27147_gb300 import inputs as _inp
 
@@ -288,6 +286,37 @@ def run_reference_records(args, m=1 << 19, words=30):
         "cpu_baseline": {"value": value, "unit": "records/s", "cores": 1, "kind": "oracle",
                          "sample": "first 2^19 rows of randomBlob30 / zeroBlob30, alternating"},
         "e2e": {"value": value, "unit": "records/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_keys64(args, m=1 << 21):
+    """The oracle on 64-bit keys: each step sorts the first 2^21 keys of one set."""
+    import oracle
+    from paper_2605_27147_gb300 import inputs
+
+    oracle.build()
+    hi = inputs.uniform(m, 1).astype(np.uint64)
+    lo = inputs.uniform(m, 2).astype(np.uint64)
+    sets = [((hi << np.uint64(32)) | lo, "u64"), ((lo.astype(np.int64) - (1 << 31)).view(np.uint64), "i64"),
+            ((lo << np.uint64(32)) | hi, "f64")]
+    times = []
+    for i in range(args.warmup + args.steps):
+        keys, kind = sets[i % 3]
+        t0 = time.perf_counter()
+        oracle.powersort_keys64(keys, kind)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    value = m * len(times) / sum(times)
+    line = {
+        "impl": "reference", "metric": "64-bit keys/s (sort + stable permutation), 1xGB300", "value": value,
+        "unit": "elements/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * sum(times) / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "keys64_2^24", "note": "CPU oracle, first 2^21 keys of one set per step"},
+        "cpu_baseline": {"value": value, "unit": "elements/s", "cores": 1, "kind": "oracle",
+                         "sample": "first 2^21 keys of the u64 / i64 / f64 sets, in turn"},
+        "e2e": {"value": value, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
