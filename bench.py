@@ -219,6 +219,8 @@ def run_reference(args):
         return run_reference_records(args)
     if args.workload == "keys64_2^24":
         return run_reference_keys64(args)
+    if args.workload == "serving":
+        return run_reference_serving(args)
     if args.workload == "batched_4096":
         from paper_2605_27147_gb300 import inputs as _inp
 
@@ -286,6 +288,38 @@ def run_reference_records(args, m=1 << 19, words=30):
         "cpu_baseline": {"value": value, "unit": "records/s", "cores": 1, "kind": "oracle",
                          "sample": "first 2^19 rows of randomBlob30 / zeroBlob30, alternating"},
         "e2e": {"value": value, "unit": "records/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_serving(args, budget_s=10.0):
+    """The oracle on the serving stream's requests, in arrival order, one at a
+    time, for about budget_s seconds of one core (each step one request)."""
+    import oracle
+    from paper_2605_27147_gb300 import inputs
+
+    oracle.build()
+    _, sizes = inputs.poisson_requests(2000.0, 10.0, 4)
+    elems, spent, done = 0, 0.0, 0
+    for i, n in enumerate(sizes.tolist()):
+        keys = inputs.uniform(int(n), 100 + i)
+        t0 = time.perf_counter()
+        oracle.powersort(keys)
+        spent += time.perf_counter() - t0
+        elems += int(n)
+        done += 1
+        if spent > budget_s and done >= args.steps:
+            break
+    value = elems / spent
+    line = {
+        "impl": "reference", "metric": "hot-path elements/s & % HBM roofline, 1xGB300; batched vs plain; p50/p99 ms",
+        "value": value, "unit": "elements/s", "n_gpus": args.gpus, "steps": done, "warmup": 0,
+        "ms_per_step": 1000 * spent / done, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "serving", "note": f"CPU oracle on the first {done} requests of the stream, one core"},
+        "cpu_baseline": {"value": value, "unit": "elements/s", "cores": 1, "kind": "oracle",
+                         "sample": f"the first {done} requests (sizes log-uniform in [2^10, 2^24], seed 4)"},
+        "e2e": {"value": value, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
