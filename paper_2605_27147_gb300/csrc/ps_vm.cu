@@ -88,21 +88,8 @@ __device__ __forceinline__ uint32_t page_size(const Job& J, uint32_t u, uint32_t
 }
 
 // Left-child elements among the first d outputs of merge g (merge path over
-// the page-table-translated keys).
-__device__ uint32_t vm_split(const Job& J, const GSorted& g, uint32_t d)
-{
-    const uint32_t lo = (uint32_t)g.goff, mid = lo + g.la;
-    uint32_t l = d > g.lb ? d - g.lb : 0u;
-    uint32_t h = min(d, g.la);
-    while (l < h) {
-        const uint32_t m = (l + h) >> 1;
-        if (vkey(J, lo + m) <= vkey(J, mid + d - 1 - m)) l = m + 1; else h = m;
-    }
-    return l;
-}
-
-// The same split by a team of eight lanes (lane & ~7 .. lane | 7, converged):
-// an 8-ary search, seven probes per step.  The predicate L[m] <= R[d-1-m] is
+// the page-table-translated keys), by a team of eight lanes (lane & ~7 ..
+// lane | 7, converged): an 8-ary search, seven probes per step.  The predicate L[m] <= R[d-1-m] is
 // true below the split and false from it on, so the trues among increasing
 // probes form a prefix.
 __device__ uint32_t vm_split_team(const Job& J, const GSorted& g, uint32_t d, uint32_t lane)
