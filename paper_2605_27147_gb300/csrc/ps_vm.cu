@@ -89,9 +89,9 @@ __device__ __forceinline__ uint32_t page_size(const Job& J, uint32_t u, uint32_t
 
 // Left-child elements among the first d outputs of merge g (merge path over
 // the page-table-translated keys), by a team of eight lanes (lane & ~7 ..
-// lane | 7, converged): an 8-ary search, seven probes per step.  The predicate L[m] <= R[d-1-m] is
-// true below the split and false from it on, so the trues among increasing
-// probes form a prefix.
+// lane | 7, converged): an 8-ary search, seven probes per step.  The
+// predicate L[m] <= R[d-1-m] is true below the split and false from it on,
+// so the trues among increasing probes form a prefix.
 __device__ uint32_t vm_split_team(const Job& J, const GSorted& g, uint32_t d, uint32_t lane)
 {
     const uint32_t tl = lane & 7u, shift = lane & 24u;
