@@ -8,6 +8,7 @@ from .oracle import (  # noqa: F401
     minrun,
     power,
     stable_sort,
+    stable_rank,
     powersort,
     powersort_keys64,
     powersort_records,

@@ -10,6 +10,7 @@ all arithmetic is in the C source, which follows the paper:
 * :func:`minrun`       -- Sec. 5, "Algorithm variants" (minimum run length)
 * :func:`power`        -- Sec. 2 Theorem (definition of Power)
 * :func:`stable_sort`  -- the plain definition of the result (stable order)
+* :func:`stable_rank`  -- one output of it: the stable position of one element
 * :func:`powersort`    -- Algorithm 1 with Pingpong storage (Sec. 3)
 * :func:`powersort_vm` -- Algorithm 1 with virtual-memory storage (Sec. 4)
 * :func:`powersort_keys64` -- Algorithm 1 on 64-bit keys ("u64", "i64" or
@@ -120,6 +121,8 @@ def _declare(lib):
     lib.oracle_stable_sort_records.restype = ctypes.c_int
     lib.oracle_stable_sort_records.argtypes = [u32p, ctypes.c_uint32, ctypes.c_uint64, u32p]
     lib.oracle_stable_sort_ex.restype = ctypes.c_int
+    lib.oracle_stable_rank_ex.restype = ctypes.c_uint64
+    lib.oracle_stable_rank_ex.argtypes = [u32p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64]
     lib.oracle_stable_sort_ex.argtypes = [u32p, ctypes.c_uint64, ctypes.c_uint32, u32p, u32p]
     lib.oracle_powersort.restype = ctypes.c_int
     lib.oracle_powersort.argtypes = [u32p, u32p, ctypes.c_uint64, u32p, u8p, u32p,
@@ -160,6 +163,15 @@ def stable_sort(keys: np.ndarray, key_type: str = "u32"):
         if rc:
             raise MemoryError("oracle_stable_sort")
     return ko, po
+
+
+def stable_rank(keys: np.ndarray, i: int, key_type: str = "u32") -> int:
+    """One output of the definition: the position of element i in the stable
+    order (elements with a smaller key, plus equal keys before it)."""
+    keys = np.ascontiguousarray(keys, dtype=np.uint32)
+    if not 0 <= i < keys.size:
+        raise IndexError(i)
+    return int(_load().oracle_stable_rank_ex(_ptr(keys, ctypes.c_uint32), keys.size, KEY_ORDER[key_type], i))
 
 
 @dataclass

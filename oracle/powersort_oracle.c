@@ -29,6 +29,8 @@
  *                        as two's-complement integers / IEEE-754 binary32
  *                        values ordered by the standard's totalOrder
  *   oracle_stable_sort_ex the stable-sort definition under those key orders
+ *   oracle_stable_rank_ex one output of that definition: the stable position
+ *                        of a single element
  *   oracle_powersort_keys64
  *                        64-bit keys (unsigned, two's complement, or IEEE 754
  *                        binary64 under totalOrder): Algorithm 1 on indices,
@@ -198,6 +200,19 @@ int oracle_stable_sort_ex(const uint32_t* keys, uint64_t n, uint32_t options, ui
 int oracle_stable_sort(const uint32_t* keys, uint64_t n, uint32_t* keys_out, uint32_t* perm_out)
 {
     return oracle_stable_sort_ex(keys, n, 0u, keys_out, perm_out);
+}
+
+/* One output of the same definition: the position that element i takes in
+ * the stable order, i.e. the number of elements j that come before it (a
+ * smaller key, or an equal key and j < i).  Lets a check of a very large sort
+ * sample its outputs one by one in O(n) each. */
+uint64_t oracle_stable_rank_ex(const uint32_t* keys, uint64_t n, uint32_t options, uint64_t i)
+{
+    g_key_order = options & (ORACLE_KEY_I32 | ORACLE_KEY_F32);
+    uint64_t r = 0;
+    for (uint64_t j = 0; j < n; ++j)
+        r += key_gt(keys[i], keys[j]) || (j < i && !key_gt(keys[j], keys[i]));
+    return r;
 }
 
 /* ------------------------------------------------------------------------- */

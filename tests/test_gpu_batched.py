@@ -112,6 +112,55 @@ def test_graph_replays_match(bctx, oracle_mod):
     g.close()
 
 
+def test_config_4_full_4096(oracle_mod):
+    """4096 instances of log-uniform length in [2^8, 2^20] (seed 3, about
+    5.2 x 10^8 elements), sorted as the benchmark sorts them: the autotuned
+    tile size and one replay of the captured batched graph.  Every instance
+    by the stable-sort characterisation (vectorised over the batch), and 48
+    sampled instances element by element against the oracle's Algorithm 1
+    (keys, permutation, runs, powers, merge cost)."""
+    from paper_2605_27147_gb300 import autotune, binding
+
+    keys, off = inputs.batch(4096, 3)
+    sizes = np.diff(off.astype(np.int64))
+    total, count, max_n = int(keys.size), int(sizes.size), int(sizes.max())
+    stream = torch.cuda.Stream()
+    dk = to_dev(keys)
+    dp = torch.empty(total, dtype=torch.int32, device="cuda")
+    doff = _dev_offsets(off)
+    tuned = autotune.tune(dk, doff, dp, max_n, stream=stream)
+    with binding.Context(max_n, want_perm=True, max_total=total, max_count=count, tile_log2=tuned["tile_log2"],
+                         stream=stream) as c:
+        g = c.graph_batched(dk, doff, dp)
+        torch.cuda.synchronize()
+        g.launch()
+        c.sync()
+        gk, gp = to_host(dk), to_host(dp)
+        rng = np.random.RandomState(12)
+        for q in sorted(rng.choice(count, size=48, replace=False).tolist()):
+            a, b = int(off[q]), int(off[q + 1])
+            ref = oracle_mod.powersort(keys[a:b])
+            assert np.array_equal(gk[a:b], ref.keys) and np.array_equal(gp[a:b], ref.perm), q
+            assert np.array_equal(c.runs(q), ref.run_starts) and np.array_equal(c.powers(q), ref.powers), q
+            assert c.instance_stats(q)["merge_cost"] == ref.stats["merge_cost"], q
+        g.close()
+    del dk, dp, doff
+    # every instance: a permutation of its own slice, keys non-decreasing,
+    # equal keys in input order
+    inst = np.repeat(np.arange(count, dtype=np.int32), sizes)
+    assert np.all(gp < sizes[inst]), "a permutation entry outside its instance"
+    src = off[:-1].astype(np.uint32)[inst] + gp
+    seen = np.zeros(total, np.int8)
+    seen[src] = 1
+    assert seen.all(), "not a permutation within each instance"
+    del seen
+    assert np.array_equal(keys[src], gk)
+    same = inst[1:] == inst[:-1]
+    assert np.all(gk[1:][same] >= gk[:-1][same]), "keys not non-decreasing"
+    eq = same & (gk[1:] == gk[:-1])
+    assert np.all(gp[1:][eq] > gp[:-1][eq]), "equal keys out of input order"
+
+
 def test_batched_many_small_instances(oracle_mod):
     from paper_2605_27147_gb300 import binding
 

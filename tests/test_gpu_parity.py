@@ -100,6 +100,38 @@ def test_result_is_stable_sort_large(oracle_mod):
         assert st["n"] == n
 
 
+@pytest.mark.parametrize("storage", ["pingpong", "vm"])
+def test_config_3_full_2_28(oracle_mod, storage):
+    """n = 2^28 uniform (seed 2), one call with keys and permutation as the
+    benchmark makes it: every output by the O(n) stable-sort
+    characterisation; the run starts, powers and merge cost by their closed
+    forms (2^23 forced runs of minrun = 32 make a perfectly balanced tree:
+    p_t = 23 - v2(t), M = 23 n); sampled outputs ranked one by one by the
+    oracle's definition."""
+    from paper_2605_27147_gb300 import binding
+
+    n = 1 << 28
+    keys = inputs.make("uniform", n, 2)
+    kw = {"mode": binding.PS_MODE_VM} if storage == "vm" else {}
+    with binding.Context(n, want_perm=True, **kw) as c:
+        dk = to_dev(keys)
+        dp = torch.empty(n, dtype=torch.int32, device="cuda")
+        st = c.run(dk, dp, stats=True)
+        runs, pw = c.runs(), c.powers()
+        gk, gp = to_host(dk), to_host(dp)
+        del dk, dp
+    # no natural run of these keys reaches 32 elements: every run is forced
+    assert st["runs"] == n // 32
+    assert np.array_equal(runs.astype(np.int64), np.arange(0, n + 1, 32, dtype=np.int64))
+    t = np.arange(1, n // 32, dtype=np.int64)
+    assert np.array_equal(pw.astype(np.int64), 23 - np.log2(t & -t).astype(np.int64))
+    assert st["merge_cost"] == 23 * n
+    check_stable_sort(keys, gk, gp)
+    rng = np.random.RandomState(6)
+    for r in rng.randint(0, n, size=6).tolist() + [0, n - 1]:
+        assert oracle_mod.stable_rank(keys, int(gp[r])) == r
+
+
 @pytest.mark.parametrize("tile_log2", [10, 11])
 def test_smaller_tiles(oracle_mod, tile_log2):
     # smaller on-chip tiles leave more of the tree to the HBM merge kernel

@@ -146,6 +146,32 @@ def test_stable_sort_vs_textbook_insertion(oracle_mod):
         assert np.array_equal(ko, nk) and np.array_equal(po, np_)
 
 
+@pytest.mark.parametrize("kt", ["u32", "i32", "f32"])
+def test_stable_rank_is_the_inverse_permutation(oracle_mod, kt):
+    # every element's stable position, one by one, against numpy's stable
+    # argsort of the same order (inverse permutation), on ties and extremes
+    rng = np.random.RandomState(3)
+    for n, hi in ((1, 2 ** 32), (7, 2), (300, 5), (1000, 2 ** 32)):
+        keys = rng.randint(0, hi, size=n, dtype=np.uint64).astype(np.uint32)
+        keys[: min(n, 3)] = [0, 0xffffffff, 0x80000000][: min(n, 3)]
+        if kt == "u32":
+            order = np.argsort(keys, kind="stable")
+        elif kt == "i32":
+            order = np.argsort(keys.view(np.int32), kind="stable")
+        else:
+            # totalOrder on the bit patterns: flip all bits of negatives, the
+            # sign bit of the rest, then compare unsigned
+            b = keys.astype(np.uint64)
+            order = np.argsort(np.where(b >> 31, b ^ 0xffffffff, b | 0x80000000), kind="stable")
+        want = np.empty(n, np.int64)
+        want[order] = np.arange(n)
+        got = [oracle_mod.stable_rank(keys, i, key_type=kt) for i in range(n)]
+        assert got == want.tolist()
+    # a hand example: equal keys keep their input order
+    k = np.array([5, 3, 5, 1, 3], np.uint32)
+    assert [oracle_mod.stable_rank(k, i) for i in range(5)] == [3, 1, 4, 0, 2]
+
+
 @pytest.mark.parametrize("dist", DISTS)
 def test_powersort_result_is_stable_sort(oracle_mod, dist):
     for n in EDGE_SIZES + [1 << 12, (1 << 15) + 123]:
