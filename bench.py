@@ -53,6 +53,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -122,7 +123,10 @@ class ClockSampler:
     def __init__(self, device: int):
         self.device = device
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # the raw samples go to $PS_CLOCKS_DIR (default: a temporary folder);
+        # the JSON line carries their summary
+        out = os.environ.get("PS_CLOCKS_DIR") or os.path.join(tempfile.gettempdir(), "ps_clocks")
+        self.path = os.path.join(out, f"clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:

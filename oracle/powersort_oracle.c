@@ -41,7 +41,7 @@
  *                        "Input data types"): the keys are record indices
  *                        compared through the rows
  *
- * Readings taken where the paper is silent (all listed in the design doc):
+ * Readings taken where the paper is silent:
  *   - indices are 0-based and half open: a = [i, j), b = [j, k);
  *   - the final loop of Algorithm 1 pops the stack after every merge;
  *   - minrun for n < 64 is n (the halving loop never runs);
