@@ -39,9 +39,11 @@ timed sort the input is restored from a pristine copy and L2 is flushed by
 writing a 512 MiB buffer (both untimed); each sort is bracketed by CUDA
 events on the library's stream, and the per-phase kernel times come from
 events the library records between its launches.  ``e2e`` repeats the
-workload through ps_run_host (pinned host arrays; host->device copy of the
-keys, sort, device->host copy of keys and permutation inside the timed
-region).  ``cpu_baseline`` / ``--impl reference`` time the single-threaded CPU
+workload from pinned host arrays, with the host->device copy of the keys and
+the device->host copy of keys and permutation inside the timed region: with
+Pingpong storage as a stream of requests through the server (two lanes, so
+one sort's copies overlap another's kernels), the one-call ps_run_host
+figure beside it; with VM storage through ps_run_host.  ``cpu_baseline`` / ``--impl reference`` time the single-threaded CPU
 oracle on a bounded sample of the same workload.
 """
 from __future__ import annotations
@@ -960,6 +962,38 @@ def main():
         e2e = {"value": esum * world / tsum, "unit": UNIT, "h2d_bytes_per_step": bi // e2e_steps,
                "d2h_bytes_per_step": bo // e2e_steps, "steps": e2e_steps,
                "api": "ps_run_host (pinned host arrays)"}
+        if mode == binding.PS_MODE_PINGPONG:
+            # the same sorts as a stream of host requests through the server:
+            # two lanes, so one sort's copies overlap the other's kernels
+            single = dict(e2e)
+            ins = [torch.from_numpy(k.view(np.int32)).pin_memory() for _, _, _, k in data]
+            kos = [torch.empty(t.numel(), dtype=torch.int32, pin_memory=True) for t in ins]
+            pos = [torch.empty(t.numel(), dtype=torch.int32, pin_memory=True) for t in ins]
+            srv = binding.Server(2 * max_n * 24, max_n, lanes=2, lane_max_total=max_n, lane_max_count=1,
+                                 device=local, key_type=key_type, flags=variant)
+
+            def stream_step():
+                tickets = [srv.submit(ins[i].data_ptr(), kos[i].data_ptr(), pos[i].data_ptr(), ins[i].numel())
+                           for i in range(len(ins))]
+                for t in tickets:
+                    srv.wait(t)
+
+            stream_step()                      # warm-up
+            t0 = time.perf_counter()
+            for _ in range(e2e_steps):
+                stream_step()
+            tstream = time.perf_counter() - t0
+            srv.close()
+            for i, (_, n, _, k) in enumerate(data):
+                # every result is its input gathered through the permutation
+                got = kos[i].numpy().view(np.uint32)
+                assert np.array_equal(k.view(np.uint32)[pos[i].numpy().view(np.uint32)], got)
+                if args.key_type == "u32":
+                    assert np.all(got[1:] >= got[:-1])
+            e2e = {"value": esum * world / tstream, "unit": UNIT, "h2d_bytes_per_step": bi // e2e_steps,
+                   "d2h_bytes_per_step": bo // e2e_steps, "steps": e2e_steps,
+                   "api": "ps_server_submit / ps_server_wait (pinned host arrays, 2 lanes)",
+                   "single_call": {"value": single["value"], "api": single["api"]}}
 
     cpu = None
     if rank == 0 and not args.no_cpu:
