@@ -165,13 +165,13 @@ def stable_sort(keys: np.ndarray, key_type: str = "u32"):
     return ko, po
 
 
-def stable_rank(keys: np.ndarray, i: int, key_type: str = "u32") -> int:
+def stable_rank(keys: np.ndarray, i: int, key_type: str = "u32", lib=None) -> int:
     """One output of the definition: the position of element i in the stable
     order (elements with a smaller key, plus equal keys before it)."""
     keys = np.ascontiguousarray(keys, dtype=np.uint32)
     if not 0 <= i < keys.size:
         raise IndexError(i)
-    return int(_load().oracle_stable_rank_ex(_ptr(keys, ctypes.c_uint32), keys.size, KEY_ORDER[key_type], i))
+    return int((lib or _load()).oracle_stable_rank_ex(_ptr(keys, ctypes.c_uint32), keys.size, KEY_ORDER[key_type], i))
 
 
 @dataclass

@@ -55,6 +55,11 @@ MUTATIONS = {
                                       "for (uint32_t w = 1; w < g_rec_words; ++w)"),
     "records compare the wrong way": ("if (ra[w] != rb[w]) return ra[w] > rb[w];",
                                       "if (ra[w] != rb[w]) return ra[w] < rb[w];"),
+    "stable rank counts the element itself": ("(j < i && !key_gt(keys[j], keys[i]))",
+                                              "(j <= i && !key_gt(keys[j], keys[i]))"),
+    "stable rank drops the equal keys before it": (
+        "r += key_gt(keys[i], keys[j]) || (j < i && !key_gt(keys[j], keys[i]));",
+        "r += key_gt(keys[i], keys[j]);"),
 }
 
 
@@ -127,6 +132,12 @@ def run_pins(lib):
     f64 = k64.astype(np.float64) * 1e-7
     r = oracle.powersort_keys64(f64.view(np.uint64), "f64", lib=lib)
     assert np.array_equal(r.perm, np.argsort(f64, kind="stable"))
+    # one output at a time: stable positions are the inverse of numpy's
+    # stable argsort
+    sk = inputs.make("few", 300, 7)
+    inv = np.empty(sk.size, np.int64)
+    inv[np.argsort(sk, kind="stable")] = np.arange(sk.size)
+    assert [oracle.stable_rank(sk, i, lib=lib) for i in range(sk.size)] == inv.tolist()
     # records: numpy's stable lexsort
     rec = inputs.records("few", 3000, 2, words=5)
     r = oracle.powersort_records(rec, lib=lib)
