@@ -32,7 +32,7 @@
 //     and permutation) and loads the elements outside the slices'
 //     16-byte-aligned interiors (at most three at each end) with ordinary
 //     loads; the stage's "full" mbarrier completes when both have landed.
-//   Eight consumer warps: merge a full stage straight into the output
+//   Consumer warps (BLOCK / 32 of them): merge a full stage into the output
 //     staging arrays (each thread MERGE_K consecutive outputs: merge-path
 //     split inside shared memory, then a branch-free serial merge), release
 //     it, and write the chunk back: the aligned interior by a bulk store, the
