@@ -37,6 +37,9 @@ namespace {
 
 constexpr uint32_t FULL = 0xffffffffu;
 
+constexpr int NODE_HALO = 768;                          // k_nodes: staged slots on each side
+constexpr int NODE_WIN = PLAN_BLOCK + 2 * NODE_HALO;
+
 __device__ __forceinline__ uint32_t inst_of_slot(const Job& J, unsigned long long slot)
 {
     return find_inst(J.count, slot, [&](uint32_t i) { return J.inst[i].run_base; });
@@ -117,10 +120,24 @@ __global__ void __launch_bounds__(PLAN_BLOCK) k_kappa(Job J)
 // Power and node range [na, nb) (run indices) of every boundary; merge cost.
 __global__ void __launch_bounds__(PLAN_BLOCK) k_nodes(Job J)
 {
-    if (*(volatile uint32_t*)&J.ctr->error) return;
+    // kappa of the block's slots and NODE_HALO slots on each side, staged in
+    // shared memory: the probes of every node no wider than the halo stay on
+    // chip, and only wide nodes (small powers, few of them) go to L2
+    __shared__ uint32_t kw[NODE_WIN];
+    __shared__ uint32_t s_err;
+    if (threadIdx.x == 0) s_err = *(volatile uint32_t*)&J.ctr->error;
+    __syncthreads();
+    if (s_err) return;                                       // the whole block leaves together
     const unsigned long long total = J.ctr->total_slots;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < total; base += stride) {
+        const long long w0 = (long long)base - NODE_HALO;   // global slot of kw[0]
+        __syncthreads();                                     // the previous pass's probes are done
+        for (int i = threadIdx.x; i < NODE_WIN; i += PLAN_BLOCK) {
+            const long long g = w0 + i;
+            if (g >= 0 && g < (long long)total) kw[i] = J.kappa[g];
+        }
+        __syncthreads();
         const unsigned long long slot = base + threadIdx.x;
         unsigned long long cost = 0;
         uint32_t q = NONE, p = 0;
@@ -131,9 +148,16 @@ __global__ void __launch_bounds__(PLAN_BLOCK) k_nodes(Job J)
             const uint32_t R = I.runs;
             if (t64 >= 1 && t64 + 1 <= R) {
                 const uint32_t t = (uint32_t)t64;
-                const uint32_t* kap = J.kappa + I.run_base;
+                const uint32_t* kap_g = J.kappa + I.run_base;
+                const long long off = (long long)I.run_base - w0;
+                // kappa of run x of this instance (0 <= x < R: a staged slot
+                // when it falls in the window, else a load)
+                auto kap = [&](long long x) -> uint32_t {
+                    const long long w = off + x;
+                    return (w >= 0 && w < NODE_WIN) ? kw[w] : kap_g[x];
+                };
                 const uint32_t* rs = J.run_start + I.run_base;
-                const uint32_t X = kap[t - 1], Y = kap[t];
+                const uint32_t X = kap(t - 1), Y = kap(t);
                 p = __clz(X ^ Y) + 1;                      // 1..32
                 const uint32_t c = Y >> (32 - p);          // odd: the dyadic point is c / 2^p
                 const unsigned long long XL = (unsigned long long)(c - 1) << (32 - p);
@@ -143,14 +167,14 @@ __global__ void __launch_bounds__(PLAN_BLOCK) k_nodes(Job J)
                 for (;;) {
                     const long long qq = j - step;
                     if (qq < 0) { bad = -1; break; }
-                    if (kap[qq] < XL) { bad = qq; break; }
+                    if (kap(qq) < XL) { bad = qq; break; }
                     j = qq;
                     step <<= 1;
                 }
                 long long lo = bad + 1, hi = j;
                 while (lo < hi) {
                     const long long mid = (lo + hi) >> 1;
-                    if (kap[mid] >= XL) hi = mid; else lo = mid + 1;
+                    if (kap(mid) >= XL) hi = mid; else lo = mid + 1;
                 }
                 const uint32_t a = (uint32_t)lo;
                 // first run with kappa >= XR after t (run t does not qualify), or R
@@ -160,7 +184,7 @@ __global__ void __launch_bounds__(PLAN_BLOCK) k_nodes(Job J)
                 for (;;) {
                     const long long qq = j + step;
                     if (qq > (long long)R - 1) { good = R; break; }
-                    if (kap[qq] >= XR) { good = qq; break; }
+                    if (kap(qq) >= XR) { good = qq; break; }
                     j = qq;
                     step <<= 1;
                 }
@@ -168,7 +192,7 @@ __global__ void __launch_bounds__(PLAN_BLOCK) k_nodes(Job J)
                 hi = good;
                 while (lo < hi) {
                     const long long mid = (lo + hi) >> 1;
-                    if (kap[mid] >= XR) hi = mid; else lo = mid + 1;
+                    if (kap(mid) >= XR) hi = mid; else lo = mid + 1;
                 }
                 const uint32_t b = (uint32_t)lo;
                 J.power[slot] = (uint8_t)p;
