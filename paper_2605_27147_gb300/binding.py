@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import threading
 
 import numpy as np
 
@@ -111,6 +112,7 @@ class PowersortError(RuntimeError):
 
 
 _lib = None
+_lib_lock = threading.Lock()
 
 
 def library_path() -> str:
@@ -118,82 +120,89 @@ def library_path() -> str:
 
 
 def lib(build_if_missing: bool = True):
-    """The loaded ``libpowersort.so`` (built in tree when missing)."""
+    """The loaded ``libpowersort.so``.  With ``build_if_missing`` the in-tree
+    build runs first (a no-op when the library matches the sources), so a
+    stale library is never loaded."""
     global _lib
-    if _lib is None:
-        path = _build.SO
-        if not os.path.exists(path):
-            if not build_if_missing:
-                raise FileNotFoundError(f"{path} is missing: run __graft_entry__.build()")
-            _build.build()
-        L = ctypes.CDLL(path)
-        vp = ctypes.c_void_p
-        u32p = ctypes.POINTER(ctypes.c_uint32)
-        u8p = ctypes.POINTER(ctypes.c_uint8)
-        u64p = ctypes.POINTER(ctypes.c_uint64)
-        L.ps_status_str.restype = ctypes.c_char_p
-        L.ps_status_str.argtypes = [ctypes.c_int]
-        L.ps_create.restype = ctypes.c_int
-        L.ps_create.argtypes = [ctypes.POINTER(ps_config), ctypes.c_int, vp, ctypes.POINTER(vp)]
-        L.ps_run.restype = ctypes.c_int
-        L.ps_run.argtypes = [vp, vp, vp, ctypes.c_uint64, ctypes.POINTER(ps_stats)]
-        L.ps_run_batched.restype = ctypes.c_int
-        L.ps_run_batched.argtypes = [vp, vp, vp, vp, ctypes.c_uint32, ctypes.POINTER(ps_stats)]
-        L.ps_run_host.restype = ctypes.c_int
-        L.ps_run_host.argtypes = [vp, vp, vp, ctypes.c_uint64, ctypes.POINTER(ps_stats)]
-        L.ps_get_phase_times.restype = ctypes.c_int
-        L.ps_get_phase_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_uint32,
-                                         ctypes.POINTER(ctypes.c_uint32)]
-        L.ps_get_round_times.restype = ctypes.c_int
-        L.ps_get_round_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_uint32,
-                                         ctypes.POINTER(ctypes.c_uint32)]
-        L.ps_sync.restype = ctypes.c_int
-        L.ps_sync.argtypes = [vp]
-        L.ps_selftest_wait_timeout.restype = ctypes.c_int
-        L.ps_selftest_wait_timeout.argtypes = [vp]
-        L.ps_check_guards.restype = ctypes.c_int
-        L.ps_check_guards.argtypes = [vp]
-        L.ps_server_cancel.restype = ctypes.c_int
-        L.ps_server_cancel.argtypes = [vp, ctypes.c_uint64]
-        L.ps_sort_keys64.restype = ctypes.c_int
-        L.ps_sort_keys64.argtypes = [vp, vp, ctypes.c_uint64, vp, ctypes.c_uint32, ctypes.POINTER(ps_stats)]
-        L.ps_sort_records.restype = ctypes.c_int
-        L.ps_sort_records.argtypes = [vp, vp, ctypes.c_uint32, ctypes.c_uint64, vp, vp, ctypes.POINTER(ps_stats)]
-        L.ps_gather_rows.restype = ctypes.c_int
-        L.ps_gather_rows.argtypes = [vp, vp, vp, ctypes.c_uint32, ctypes.c_uint64, vp, vp, ctypes.c_uint32]
-        L.ps_graph_create_batched.restype = ctypes.c_int
-        L.ps_graph_create_batched.argtypes = [vp, vp, vp, vp, ctypes.c_uint32, ctypes.POINTER(vp)]
-        L.ps_graph_launch.restype = ctypes.c_int
-        L.ps_graph_launch.argtypes = [vp]
-        L.ps_graph_destroy.restype = None
-        L.ps_graph_destroy.argtypes = [vp]
-        dp = ctypes.POINTER(ctypes.c_double)
-        L.ps_server_create.restype = ctypes.c_int
-        L.ps_server_create.argtypes = [ctypes.POINTER(ps_server_config), ctypes.POINTER(vp)]
-        L.ps_server_submit.restype = ctypes.c_int
-        L.ps_server_submit.argtypes = [vp, vp, vp, vp, ctypes.c_uint64, u64p]
-        L.ps_server_poll.restype = ctypes.c_int
-        L.ps_server_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), dp]
-        L.ps_server_wait.restype = ctypes.c_int
-        L.ps_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_double, dp]
-        L.ps_server_get_stats.restype = ctypes.c_int
-        L.ps_server_get_stats.argtypes = [vp, ctypes.POINTER(ps_server_stats)]
-        L.ps_server_destroy.restype = None
-        L.ps_server_destroy.argtypes = [vp]
-        L.ps_get_runs.restype = ctypes.c_int
-        L.ps_get_runs.argtypes = [vp, ctypes.c_uint32, u32p, ctypes.c_uint64, u64p]
-        L.ps_get_powers.restype = ctypes.c_int
-        L.ps_get_powers.argtypes = [vp, ctypes.c_uint32, u8p, ctypes.c_uint64, u64p]
-        L.ps_get_nodes.restype = ctypes.c_int
-        L.ps_get_nodes.argtypes = [vp, ctypes.c_uint32, u32p, ctypes.c_uint64, u64p]
-        L.ps_get_instance_stats.restype = ctypes.c_int
-        L.ps_get_instance_stats.argtypes = [vp, ctypes.c_uint32, ctypes.POINTER(ps_stats)]
-        L.ps_destroy.restype = None
-        L.ps_destroy.argtypes = [vp]
-        L.ps_run_noalloc.restype = ctypes.c_int
-        L.ps_run_noalloc.argtypes = [vp, vp, ctypes.c_uint64, ctypes.c_int, vp]
-        _lib = L
+    with _lib_lock:
+        if _lib is None:
+            _lib = _load(build_if_missing)
     return _lib
+
+
+def _load(build_if_missing: bool):
+    path = _build.SO
+    if build_if_missing:
+        _build.build()
+    elif not os.path.exists(path):
+        raise FileNotFoundError(f"{path} is missing: run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    vp = ctypes.c_void_p
+    u32p = ctypes.POINTER(ctypes.c_uint32)
+    u8p = ctypes.POINTER(ctypes.c_uint8)
+    u64p = ctypes.POINTER(ctypes.c_uint64)
+    L.ps_status_str.restype = ctypes.c_char_p
+    L.ps_status_str.argtypes = [ctypes.c_int]
+    L.ps_create.restype = ctypes.c_int
+    L.ps_create.argtypes = [ctypes.POINTER(ps_config), ctypes.c_int, vp, ctypes.POINTER(vp)]
+    L.ps_run.restype = ctypes.c_int
+    L.ps_run.argtypes = [vp, vp, vp, ctypes.c_uint64, ctypes.POINTER(ps_stats)]
+    L.ps_run_batched.restype = ctypes.c_int
+    L.ps_run_batched.argtypes = [vp, vp, vp, vp, ctypes.c_uint32, ctypes.POINTER(ps_stats)]
+    L.ps_run_host.restype = ctypes.c_int
+    L.ps_run_host.argtypes = [vp, vp, vp, ctypes.c_uint64, ctypes.POINTER(ps_stats)]
+    L.ps_get_phase_times.restype = ctypes.c_int
+    L.ps_get_phase_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_uint32,
+                                     ctypes.POINTER(ctypes.c_uint32)]
+    L.ps_get_round_times.restype = ctypes.c_int
+    L.ps_get_round_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_uint32,
+                                     ctypes.POINTER(ctypes.c_uint32)]
+    L.ps_sync.restype = ctypes.c_int
+    L.ps_sync.argtypes = [vp]
+    L.ps_selftest_wait_timeout.restype = ctypes.c_int
+    L.ps_selftest_wait_timeout.argtypes = [vp]
+    L.ps_check_guards.restype = ctypes.c_int
+    L.ps_check_guards.argtypes = [vp]
+    L.ps_server_cancel.restype = ctypes.c_int
+    L.ps_server_cancel.argtypes = [vp, ctypes.c_uint64]
+    L.ps_sort_keys64.restype = ctypes.c_int
+    L.ps_sort_keys64.argtypes = [vp, vp, ctypes.c_uint64, vp, ctypes.c_uint32, ctypes.POINTER(ps_stats)]
+    L.ps_sort_records.restype = ctypes.c_int
+    L.ps_sort_records.argtypes = [vp, vp, ctypes.c_uint32, ctypes.c_uint64, vp, vp, ctypes.POINTER(ps_stats)]
+    L.ps_gather_rows.restype = ctypes.c_int
+    L.ps_gather_rows.argtypes = [vp, vp, vp, ctypes.c_uint32, ctypes.c_uint64, vp, vp, ctypes.c_uint32]
+    L.ps_graph_create_batched.restype = ctypes.c_int
+    L.ps_graph_create_batched.argtypes = [vp, vp, vp, vp, ctypes.c_uint32, ctypes.POINTER(vp)]
+    L.ps_graph_launch.restype = ctypes.c_int
+    L.ps_graph_launch.argtypes = [vp]
+    L.ps_graph_destroy.restype = None
+    L.ps_graph_destroy.argtypes = [vp]
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.ps_server_create.restype = ctypes.c_int
+    L.ps_server_create.argtypes = [ctypes.POINTER(ps_server_config), ctypes.POINTER(vp)]
+    L.ps_server_submit.restype = ctypes.c_int
+    L.ps_server_submit.argtypes = [vp, vp, vp, vp, ctypes.c_uint64, u64p]
+    L.ps_server_poll.restype = ctypes.c_int
+    L.ps_server_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), dp]
+    L.ps_server_wait.restype = ctypes.c_int
+    L.ps_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_double, dp]
+    L.ps_server_get_stats.restype = ctypes.c_int
+    L.ps_server_get_stats.argtypes = [vp, ctypes.POINTER(ps_server_stats)]
+    L.ps_server_destroy.restype = None
+    L.ps_server_destroy.argtypes = [vp]
+    L.ps_get_runs.restype = ctypes.c_int
+    L.ps_get_runs.argtypes = [vp, ctypes.c_uint32, u32p, ctypes.c_uint64, u64p]
+    L.ps_get_powers.restype = ctypes.c_int
+    L.ps_get_powers.argtypes = [vp, ctypes.c_uint32, u8p, ctypes.c_uint64, u64p]
+    L.ps_get_nodes.restype = ctypes.c_int
+    L.ps_get_nodes.argtypes = [vp, ctypes.c_uint32, u32p, ctypes.c_uint64, u64p]
+    L.ps_get_instance_stats.restype = ctypes.c_int
+    L.ps_get_instance_stats.argtypes = [vp, ctypes.c_uint32, ctypes.POINTER(ps_stats)]
+    L.ps_destroy.restype = None
+    L.ps_destroy.argtypes = [vp]
+    L.ps_run_noalloc.restype = ctypes.c_int
+    L.ps_run_noalloc.argtypes = [vp, vp, ctypes.c_uint64, ctypes.c_int, vp]
+    return L
 
 
 def _check(st: int, what: str):
