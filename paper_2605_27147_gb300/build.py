@@ -61,9 +61,14 @@ def _digest() -> str:
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None) -> str:
-    """Compile and link; skipped when the sources have not changed."""
+    """Compile and link; skipped when the sources and flags have not changed.
+
+    Extra nvcc flags come from ``extra_flags`` and from the environment
+    variable ``PS_NVCC_FLAGS`` (space-separated, e.g. ``-DPS_MERGE_NSEARCH=10``
+    for a variant build that every later load of the library keeps)."""
     os.makedirs(BUILD, exist_ok=True)
     stamp = os.path.join(BUILD, "stamp")
+    extra_flags = os.environ.get("PS_NVCC_FLAGS", "").split() + list(extra_flags or [])
     dig = _digest() + (" ".join(extra_flags) if extra_flags else "")
     if not force and os.path.exists(SO) and os.path.exists(stamp) and open(stamp).read() == dig:
         return SO
