@@ -47,6 +47,36 @@ def test_power_exhaustive_small(oracle_mod):
                     assert oracle_mod.power(n, i, j, k) == power_by_enumeration(n, i, j, k), (n, i, j, k)
 
 
+def bit_length(x: np.ndarray) -> np.ndarray:
+    """Bits of every (non-negative, < 2^64) integer, by halving."""
+    x = x.astype(np.uint64)
+    bl = np.zeros(x.shape, np.int64)
+    for sh in (32, 16, 8, 4, 2, 1):
+        big = x >= np.uint64(1 << sh)
+        bl += np.where(big, sh, 0)
+        x = np.where(big, x >> np.uint64(sh), x)
+    return bl + (x > 0)
+
+
+def test_power_fixed_point_exhaustive_128(oracle_mod):
+    # every i < j < k <= n for n <= 128 (11.4 M cases) against the 32-bit
+    # fixed-point form of the same definition: with ka, kb the midpoints
+    # (i+j)/2n, (j+k)/2n truncated to 32 binary digits, Power is the position
+    # of their first differing digit, 33 - bit_length(ka ^ kb)
+    lib = oracle_mod.oracle._load()
+    for n in range(2, 129):
+        ijk = np.array([(i, j, k) for i in range(n) for j in range(i + 1, n) for k in range(j + 1, n + 1)],
+                       dtype=np.int64)
+        i, j, k = ijk[:, 0], ijk[:, 1], ijk[:, 2]
+        ka = ((i + j) << 31) // n
+        kb = ((j + k) << 31) // n
+        want = 33 - bit_length(ka ^ kb)
+        f = lib.oracle_power
+        got = np.fromiter((f(n, a, b, c) for a, b, c in ijk.tolist()), dtype=np.int64, count=len(ijk))
+        bad = np.flatnonzero(got != want)
+        assert bad.size == 0, (n, ijk[bad[0]].tolist(), int(got[bad[0]]), int(want[bad[0]]))
+
+
 def test_power_sampled_large(oracle_mod):
     rng = np.random.RandomState(11)
     for _ in range(300):
