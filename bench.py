@@ -51,6 +51,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -245,26 +246,38 @@ def run_reference(args):
 
     oracle.build()
     desc = args.workload in DESCENDING_WORKLOADS
+    vm = args.storage == "vm" and args.workload != "batched_4096"
+
+    def page_size(n):
+        # the library's default page: 2^round(log2 sqrt(n / log2 n)), within [2^8, 2^12]
+        nn = max(float(n), 4.0)
+        return 1 << min(12, max(8, math.floor(math.log2(math.sqrt(nn / math.log2(nn))) + 0.5)))
+
     times, elems = [], 0
     for i in range(args.warmup + args.steps):
         d, n, s, keys = data[i % len(data)]
         t0 = time.perf_counter()
         for k in (keys if isinstance(keys, list) else [keys]):
-            oracle.powersort(k, descending_runs=desc, key_type=args.key_type)
+            if vm:
+                oracle.powersort_vm(k, page_size(k.size), descending_runs=desc, key_type=args.key_type)
+            else:
+                oracle.powersort(k, descending_runs=desc, key_type=args.key_type)
         dt = time.perf_counter() - t0
         if i >= args.warmup:
             times.append(dt)
             elems += n
     total = sum(times)
     value = elems / total
-    sample = (f"one oracle run (Algorithm 1, Pingpong storage, one thread) per step, cycling "
+    storage = "VM storage" if vm else "Pingpong storage"
+    sample = (f"one oracle run (Algorithm 1, {storage}, one thread) per step, cycling "
               f"{', '.join(f'{d} n={n}' for d, n, s, k in data)}")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
-        "config": {"workload": args.workload, "note": "CPU oracle on host cores (bounded sample per step)"},
+        "config": {"workload": args.workload, "storage": "vm" if vm else "pingpong",
+                   "note": "CPU oracle on host cores (bounded sample per step)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
