@@ -205,17 +205,18 @@ def cpu_oracle_rate(data, budget_s, descending_runs=False, key_type="u32"):
     import oracle
 
     oracle.build()
-    done, spent, used = 0, 0.0, []
-    for d, n, s, keys in data:
-        if spent > budget_s and done:
-            break
+    # the step's inputs in turn, at least once each, until about budget_s
+    # seconds of one core are spent
+    done, spent, sorts = 0, 0.0, 0
+    while sorts < len(data) or spent < budget_s:
+        d, n, s, keys = data[sorts % len(data)]
         t0 = time.perf_counter()
         oracle.powersort(keys, descending_runs=descending_runs, key_type=key_type)
-        dt = time.perf_counter() - t0
-        spent += dt
+        spent += time.perf_counter() - t0
         done += n
-        used.append(f"{d} n={n}")
-    return done / spent, spent, "; ".join(used)
+        sorts += 1
+    used = f"{sorts} sorts cycling " + ", ".join(f"{d} n={n}" for d, n, s, k in data)
+    return done / spent, spent, used
 
 
 def run_reference(args):
@@ -617,12 +618,15 @@ def run_records(args, n=1 << 23, words=30):
 
         oracle.build()
         m = 1 << 19
-        t0 = time.perf_counter()
-        for h in host:
-            oracle.powersort_records(h[:m])
-        dt = time.perf_counter() - t0
-        cpu = {"value": m * len(host) / dt, "unit": "records/s", "cores": 1, "kind": "oracle",
-               "sample": f"the first 2^19 rows of each record set ({dt:.1f} s of one host core)"}
+        dt, sorts = 0.0, 0
+        while sorts < len(host) or dt < args.cpu_sample_seconds:   # the sets in turn, to the time budget
+            t0 = time.perf_counter()
+            oracle.powersort_records(host[sorts % len(host)][:m])
+            dt += time.perf_counter() - t0
+            sorts += 1
+        cpu = {"value": m * sorts / dt, "unit": "records/s", "cores": 1, "kind": "oracle",
+               "sample": f"{sorts} sorts of the first 2^19 rows of the record sets in turn "
+                         f"({dt:.1f} s of one host core)"}
     line = {
         "metric": "records/s (30-word rows, lexicographic), 1xGB300", "value": value, "unit": "records/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -690,17 +694,33 @@ def run_keys64(args, n=1 << 24):
                 e1.synchronize()
                 times.append(e0.elapsed_time(e1))
                 per_set[name] += times[-1]
-    stats = {}
+    stats, launches = {}, 0
     for i, (name, kt, b) in enumerate(sets):
         work.copy_(pristine[i])
         st = ctx.sort_keys64(work, perm, kt, stats=True)
-        stats[name] = {k: st[k] for k in ("runs", "merge_cost", "rounds")}
+        stats[name] = {k: st[k] for k in ("runs", "merge_cost", "rounds", "launches")}
+        launches += int(st["launches"]) * args.steps
     out = work.cpu().numpy().view(np.uint64)          # the f64 set, last: non-decreasing in totalOrder
     sgn = (out >> np.uint64(63)).astype(bool)
     img = np.where(sgn, ~out, out | np.uint64(1 << 63))
     assert np.all(img[1:] >= img[:-1])
     total_ms = replicas.max_over_ranks(sum(times), dist, dev)
     value = replicas.job_rate(n * len(times), world, total_ms)
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        import oracle
+
+        oracle.build()
+        m, dt, sorts = 1 << 20, 0.0, 0
+        while sorts < len(sets) or dt < args.cpu_sample_seconds:   # the sets in turn, to the time budget
+            name, _, b = sets[sorts % len(sets)]
+            t0 = time.perf_counter()
+            oracle.powersort_keys64(b[:m], name)
+            dt += time.perf_counter() - t0
+            sorts += 1
+        cpu = {"value": m * sorts / dt, "unit": "elements/s", "cores": 1, "kind": "oracle",
+               "sample": f"{sorts} sorts of the first 2^20 keys of the u64 / i64 / f64 sets in turn "
+                         f"({dt:.1f} s of one host core)"}
     line = {
         "metric": "64-bit keys/s (sort + stable permutation), 1xGB300", "value": value, "unit": "elements/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -708,8 +728,8 @@ def run_keys64(args, n=1 << 24):
         "config": {"workload": "keys64_2^24", "instances": [f"{name} n=2^24" for name, _, _ in sets],
                    "l2": "flushed before every timed sort"},
         "per_set_elements_per_s": {k: n * args.steps / (v / 1000.0) for k, v in per_set.items()},
-        "stats": stats, "clocks": clk.summary(), "cpu_baseline": None, "e2e": None, "roofline": None,
-        "gpu_launches": None,
+        "stats": stats, "clocks": clk.summary(), "cpu_baseline": cpu, "e2e": None, "roofline": None,
+        "gpu_launches": launches,
     }
     ctx.close()
     if rank == 0:
