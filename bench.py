@@ -6,10 +6,18 @@
 Prints ONE JSON line (rank 0).  Workloads (keys are uint32, the stable
 permutation is produced):
 
-  plain_2^24   (default) one step = three single-instance sorts of n = 2^24:
+  hbm_2^28     (default) one step = one single-instance sort of n = 2^28
+               uniform (seed 2), the largest single-instance size.  Unless
+               --no-extras is given, the line also carries the metric's two
+               other parts, each measured in the same run: "batched_vs_plain"
+               (the batched_4096 workload below: one graph replay against a
+               loop of single-instance calls) and "serving" (the serving
+               workload below: p50 / p99 latency and sustained elements/s)
+  plain_2^24   one step = three single-instance sorts of n = 2^24:
                uniform, Zipf(1.1) over 2^20 values, presorted Geometric(mean
                2^10) runs (seed 1)
-  hbm_2^28     one step = one single-instance sort of n = 2^28 uniform (seed 2)
+  uniform_2^26 one step = one sort of n = 2^26 uniform (seed 2): the 2^28
+               workload at a size that ncu captures quickly (profiling only)
   updown_2^24  one step = one sort of n = 2^24 Geometric(mean 2^10) segments,
                each sorted ascending or descending by a coin (seed 1), with
                the decreasing-run variant of Sec. 5 (PS_FLAG_DESCENDING_RUNS);
@@ -69,6 +77,7 @@ UNIT = "elements/s"
 WORKLOADS = {
     "plain_2^24": [("uniform", 1 << 24, 1), ("zipf", 1 << 24, 1), ("runs", 1 << 24, 1)],
     "hbm_2^28": [("uniform", 1 << 28, 2)],
+    "uniform_2^26": [("uniform", 1 << 26, 2)],
     "updown_2^24": [("updown", 1 << 24, 1)],
     "bands_2^24": [("bands", 1 << 24, 1)],
     "records_2^23": None,
@@ -87,7 +96,7 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="plain_2^24", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="hbm_2^28", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="pingpong", choices=["pingpong", "vm"],
                     help="run storage of the plain workloads: Pingpong (n-element scratch) or VM pages")
@@ -95,6 +104,8 @@ def parse():
                     help="plain workloads: order the same 32-bit patterns as unsigned, signed or float keys")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="hbm_2^28: leave out the batched and serving sub-measurements")
     ap.add_argument("--cpu-sample-seconds", type=float, default=20.0)
     ap.add_argument("--lane-total", type=int, default=1 << 25,
                     help="serving: most elements one batch of a lane may hold")
@@ -238,11 +249,14 @@ def run_reference(args):
         for i in range(0, len(parts), 64):      # a step: 64 consecutive instances
             grp = parts[i:i + 64]
             data.append(("batched", sum(p.size for p in grp), 3, grp))
+    elif args.workload == "hbm_2^28":
+        # a bounded sample of the 2^28 workload: its first 2^24 keys per step
+        # (the generator is a stream, so these are the 2^28 input's first keys)
+        from paper_2605_27147_gb300 import inputs as _inp
+
+        data = [(d, 1 << 24, s, _inp.make(d, 1 << 24, s)) for d, n, s in WORKLOADS["hbm_2^28"]]
     else:
         data = make_inputs(args.workload)
-    if args.workload == "hbm_2^28":
-        # a bounded sample of the 2^28 workload: its first 2^24 keys per step
-        data = [(d, 1 << 24, s, k[: 1 << 24].copy()) for d, n, s, k in data]
     import oracle
 
     oracle.build()
@@ -409,8 +423,10 @@ def cpu_oracle_parallel(parts, budget_instances):
                             f"{cores} processes, {cpu_s:.1f} s of CPU, {wall:.1f} s wall"
 
 
-def run_batched(args):
-    """Workload batched_4096: one captured-graph replay per step."""
+def batched_leg(steps, warmup, dev, stream, world=1, dist=None, e2e_steps=3):
+    """Config 4 on one GPU: 4096 instances in one captured-graph replay per
+    step, compared with a loop of single-instance calls on the same data.
+    Returns the measurements as a dict (the caller builds the JSON line)."""
     import torch
 
     from paper_2605_27147_gb300 import autotune, binding, inputs, replicas
@@ -418,30 +434,13 @@ def run_batched(args):
     keys_np, off_np = inputs.batch(4096, 3)
     sizes = np.diff(off_np.astype(np.int64))
     total, count, max_n = int(keys_np.size), int(sizes.size), int(sizes.max())
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    cpu = None
-    if rank == 0 and not args.no_cpu:      # before any CUDA work (the pool is spawned)
-        parts = [keys_np[int(off_np[i]):int(off_np[i + 1])] for i in range(count)]
-        rate, cores, sample = cpu_oracle_parallel(parts, 1024)
-        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    stream = torch.cuda.Stream(dev)
     pristine = torch.from_numpy(keys_np.view(np.int32)).to(dev)
     work = pristine.clone()
     perm = torch.empty(total, dtype=torch.int32, device=dev)
     doff = torch.from_numpy(off_np.astype(np.int64)).to(dev)
     tuned = autotune.tune(work, doff, perm, max_n, stream=stream)
     ctx = binding.Context(max_n, want_perm=True, max_total=total, max_count=count, tile_log2=tuned["tile_log2"],
-                          flags=binding.PS_FLAG_TIMING,
-                          device=local, stream=stream)
+                          flags=binding.PS_FLAG_TIMING, device=dev.index, stream=stream)
     graph = ctx.graph_batched(work, doff, perm)
 
     def replay(timed):
@@ -453,15 +452,15 @@ def run_batched(args):
             e1.record(stream)
         return (e0, e1) if timed else None
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         replay(False)
     ctx.sync()
     if dist:
         dist.barrier()
     torch.cuda.synchronize(dev)
     recs = []
-    with ClockSampler(local) as clk:
-        for _ in range(args.steps):
+    with ClockSampler(dev.index) as clk:
+        for _ in range(steps):
             recs.append(replay(True))
         torch.cuda.synchronize(dev)
     ctx.sync()
@@ -469,7 +468,7 @@ def run_batched(args):
         dist.barrier()
     total_ms = sum(a.elapsed_time(b) for a, b in recs)
     total_ms_max = replicas.max_over_ranks(total_ms, dist, dev)
-    value = replicas.job_rate(args.steps * total, world, total_ms_max)
+    value = replicas.job_rate(steps * total, world, total_ms_max)
     # result check on a few instances (sorted keys, permutation consistent)
     gk = work.cpu().numpy().view(np.uint32)
     gp = perm.cpu().numpy().view(np.uint32)
@@ -483,7 +482,7 @@ def run_batched(args):
     st = ctx.run_batched(work, doff, perm, stats=True)
     ph = ctx.phase_times()
     # the per-instance loop of the plain entry point on the same data
-    plain = binding.Context(max_n, want_perm=True, device=local, stream=stream)
+    plain = binding.Context(max_n, want_perm=True, device=dev.index, stream=stream)
     offs = [int(x) for x in off_np]
     with torch.cuda.stream(stream):
         work.copy_(pristine)
@@ -500,52 +499,89 @@ def run_batched(args):
     loop_rate = total / (loop_ms / 1000.0)
     plain.close()
     # end to end: pinned host keys in, graph replay, keys + permutation out
-    hk = torch.from_numpy(keys_np.view(np.int32)).pin_memory()
-    hko = torch.empty(total, dtype=torch.int32, pin_memory=True)
-    hpo = torch.empty(total, dtype=torch.int32, pin_memory=True)
-    e2e_steps = max(1, min(args.steps, 3))
-    tsum = 0.0
-    for _ in range(e2e_steps):
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        with torch.cuda.stream(stream):
-            work.copy_(hk, non_blocking=True)
-            graph.launch()
-            hko.copy_(work, non_blocking=True)
-            hpo.copy_(perm, non_blocking=True)
-        stream.synchronize()
-        tsum += time.perf_counter() - t0
-    ctx.sync()
-    e2e = {"value": e2e_steps * total * world / tsum, "unit": UNIT, "h2d_bytes_per_step": 4 * total,
-           "d2h_bytes_per_step": 8 * total, "steps": e2e_steps,
-           "api": "ps_graph_launch between pinned host<->device copies"}
+    e2e = None
+    if e2e_steps:
+        hk = torch.from_numpy(keys_np.view(np.int32)).pin_memory()
+        hko = torch.empty(total, dtype=torch.int32, pin_memory=True)
+        hpo = torch.empty(total, dtype=torch.int32, pin_memory=True)
+        tsum = 0.0
+        for _ in range(e2e_steps):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            with torch.cuda.stream(stream):
+                work.copy_(hk, non_blocking=True)
+                graph.launch()
+                hko.copy_(work, non_blocking=True)
+                hpo.copy_(perm, non_blocking=True)
+            stream.synchronize()
+            tsum += time.perf_counter() - t0
+        ctx.sync()
+        e2e = {"value": e2e_steps * total * world / tsum, "unit": UNIT, "h2d_bytes_per_step": 4 * total,
+               "d2h_bytes_per_step": 8 * total, "steps": e2e_steps,
+               "api": "ps_graph_launch between pinned host<->device copies"}
     peak, peak_kind = peaks()
     merge_bytes = BYTES_PER_MERGED_ELEM * st["hbm_merge_elems"]
     achieved = merge_bytes / (ph["merge_rounds"] / 1000.0) / 1e9 if ph["merge_rounds"] > 0 else 0.0
+    graph.close()
+    ctx.close()
+    del work, perm, pristine
+    return {
+        "value": value, "ms_per_step": total_ms_max / steps, "steps": steps, "warmup": warmup,
+        "count": count, "total": total, "max_n": max_n, "tuned": tuned,
+        "loop_rate": loop_rate, "loop_ms": loop_ms, "phases": ph, "stats": st,
+        "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "e2e": e2e, "clocks": clk.summary(),
+    }
+
+
+def run_batched(args):
+    """Workload batched_4096: one captured-graph replay per step."""
+    import torch
+
+    from paper_2605_27147_gb300 import inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    cpu = None
+    if rank == 0 and not args.no_cpu:      # before any CUDA work (the pool is spawned)
+        keys_np, off_np = inputs.batch(4096, 3)
+        parts = [keys_np[int(off_np[i]):int(off_np[i + 1])] for i in range(off_np.size - 1)]
+        rate, cores, sample = cpu_oracle_parallel(parts, 1024)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    r = batched_leg(args.steps, args.warmup, dev, stream, world, dist, e2e_steps=0 if args.no_e2e else 3)
+    st, tuned, value = r["stats"], r["tuned"], r["value"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": "batched_4096", "instances": count, "total_elements": total,
-                   "sizes": "log-uniform in [2^8, 2^20), seed 3, uniform keys", "max_instance": max_n,
+        "config": {"workload": "batched_4096", "instances": r["count"], "total_elements": r["total"],
+                   "sizes": "log-uniform in [2^8, 2^20), seed 3, uniform keys", "max_instance": r["max_n"],
                    "outputs": "sorted keys + stable permutation (uint32)", "storage": "pingpong",
                    "launch": "one CUDA-graph replay per step (persistent cooperative merge kernel)",
                    "autotune": {k: tuned[k] for k in ("tile_log2", "ms", "cached")},
                    "l2": "inputs (2 GiB keys) exceed L2; input restored before every replay (untimed)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "batched_vs_plain_loop": {"batched": value / world, "plain_loop": loop_rate,
-                                  "ratio": (value / world) / loop_rate, "plain_loop_ms": loop_ms,
-                                  "plain_loop_calls": count},
-        "roofline": {"kernel": "k_merge_rounds (HBM merge rounds)", "bound": "hbm", "achieved": achieved,
-                     "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+        "batched_vs_plain_loop": {"batched": value / world, "plain_loop": r["loop_rate"],
+                                  "ratio": (value / world) / r["loop_rate"], "plain_loop_ms": r["loop_ms"],
+                                  "plain_loop_calls": r["count"]},
+        "roofline": {"kernel": "k_merge_rounds (HBM merge rounds)", "bound": "hbm", "achieved": r["achieved"],
+                     "peak": r["peak"], "peak_kind": r["peak_kind"], "unit": "GB/s",
+                     "frac": r["achieved"] / r["peak"], "traffic": None,
                      "algorithmic_bytes": "16 B per element per HBM merge"},
-        "kernels": {"phase_ms_one_call": ph, "stats": {k: st[k] for k in ("runs", "merge_cost", "tiles",
-                                                                           "global_nodes", "rounds",
-                                                                           "hbm_merge_elems")}},
-        "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(), "gpu_launches": int(st["launches"]) * args.steps,
+        "kernels": {"phase_ms_one_call": r["phases"], "stats": {k: st[k] for k in ("runs", "merge_cost", "tiles",
+                                                                                    "global_nodes", "rounds",
+                                                                                    "hbm_merge_elems")}},
+        "cpu_baseline": cpu, "e2e": r["e2e"], "clocks": r["clocks"],
+        "gpu_launches": int(st["launches"]) * args.steps,
     }
-    graph.close()
-    ctx.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -738,18 +774,13 @@ def run_keys64(args, n=1 << 24):
         dist.destroy_process_group()
 
 
-def run_serving(args, rate=2000.0, duration=10.0, budget=64 << 30):
-    # Elements per batch are capped so that a burst cannot build one long
-    # batch (latency grows with the batch; the offered load is far below
-    # capacity, so smaller batches cost no throughput).
-    """Workload serving: Poisson arrivals replayed in real time through ps_server."""
+def serving_leg(local, lane_total, rate=2000.0, duration=10.0, budget=64 << 30, lanes=4):
+    """Config 5: Poisson arrivals replayed in real time through ps_server.
+    Returns the latencies and the server's statistics as a dict."""
     import torch
 
     from paper_2605_27147_gb300 import binding, inputs
 
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
     arrivals, sizes = inputs.poisson_requests(rate, duration, 4)
     sizes = sizes.astype(np.int64)
     max_n = 1 << 24
@@ -762,14 +793,17 @@ def run_serving(args, rate=2000.0, duration=10.0, budget=64 << 30):
     ring_k = torch.empty(ring_n, dtype=torch.int32, pin_memory=True)
     ring_p = torch.empty(ring_n, dtype=torch.int32, pin_memory=True)
     pk, pp, pin = ring_k.data_ptr(), ring_p.data_ptr(), pool.data_ptr()
-    lane_total = args.lane_total
-    srv = binding.Server(budget, max_n, lanes=4, lane_max_total=lane_total, lane_max_count=256, device=local)
+    srv = binding.Server(budget, max_n, lanes=lanes, lane_max_total=lane_total, lane_max_count=256, device=local)
     # warm-up: a few requests (module loading, first launches)
     for i in range(8):
         srv.wait(srv.submit(pin, pk, pp, 1 << 20), 60.0)
+    # the largest request's time alone (the floor of any latency bound)
+    solo = []
+    for _ in range(3):
+        solo.append(srv.wait(srv.submit(pin, pk, pp, int(sizes.max())), 60.0))
     head, tail = 0, 0                   # ring positions (elements, monotone)
     live = []                           # (ticket, ring start, n) in submission order
-    tickets, slots = [], []
+    tickets = []
     t0 = time.perf_counter()
     with ClockSampler(local) as clk:
         for i in range(sizes.size):
@@ -808,24 +842,46 @@ def run_serving(args, rate=2000.0, duration=10.0, budget=64 << 30):
     lat_ms = np.array(lat) * 1000.0
     elems = int(sizes.sum())
     wall = t_end - t0
-    value = elems / wall
+    return {
+        "value": elems / wall, "wall_s": wall, "requests": int(sizes.size), "elements": elems,
+        "offered": elems / duration, "rate": rate, "duration": duration, "budget": budget,
+        "mean_n": float(sizes.mean()), "max_n": int(sizes.max()),
+        "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
+                       "mean": float(lat_ms.mean()), "max": float(lat_ms.max())},
+        "largest_request_solo_ms": 1000.0 * float(min(solo)),
+        "server": st, "clocks": clk.summary(),
+    }
+
+
+def run_serving(args):
+    # Elements per batch are capped so that a burst cannot build one long
+    # batch (latency grows with the batch; the offered load is far below
+    # capacity, so smaller batches cost no throughput).
+    """Workload serving: Poisson arrivals replayed in real time through ps_server."""
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    r = serving_leg(local, args.lane_total)
+    st = r["server"]
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": int(sizes.size), "warmup": 8,
-        "ms_per_step": 1000.0 * wall / sizes.size, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": r["requests"], "warmup": 8,
+        "ms_per_step": 1000.0 * r["wall_s"] / r["requests"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": "serving", "arrivals": f"Poisson {rate:.0f}/s for {duration:.0f} s, seed 4",
-                   "sizes": "log-uniform in [2^10, 2^24]", "requests": int(sizes.size),
-                   "offered_elements_per_s": elems / duration, "budget_bytes": budget,
+        "config": {"workload": "serving", "arrivals": f"Poisson {r['rate']:.0f}/s for {r['duration']:.0f} s, seed 4",
+                   "sizes": "log-uniform in [2^10, 2^24]", "requests": r["requests"],
+                   "offered_elements_per_s": r["offered"], "budget_bytes": r["budget"],
                    "lanes": st["lanes"], "lane_max_total": st["lane_max_total"],
                    "device_bytes": st["device_bytes"], "outputs": "sorted keys + stable permutation",
                    "io": "pinned host arrays in, pinned host arrays out (copies inside every latency)"},
-        "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
-                       "mean": float(lat_ms.mean()), "max": float(lat_ms.max())},
+        "latency_ms": r["latency_ms"],
+        "largest_request_solo_ms": r["largest_request_solo_ms"],
         "server": st,
-        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": int(4 * sizes.mean()),
-                "d2h_bytes_per_step": int(8 * sizes.mean()),
+        "e2e": {"value": r["value"], "unit": UNIT, "h2d_bytes_per_step": int(4 * r["mean_n"]),
+                "d2h_bytes_per_step": int(8 * r["mean_n"]),
                 "api": "ps_server_submit / ps_server_wait on pinned host arrays"},
-        "roofline": None, "cpu_baseline": None, "clocks": clk.summary(),
+        "roofline": None, "cpu_baseline": None, "clocks": r["clocks"],
         "gpu_launches": LAUNCHES_PER_BATCH * int(st["batches"]),
     }
     if rank == 0:
@@ -1029,12 +1085,13 @@ def main():
                    "single_call": {"value": single["value"], "api": single["api"]}}
 
     cpu = None
-    if rank == 0 and not args.no_cpu:
-        sample = data if args.workload == "plain_2^24" else [(d, 1 << 24, s, k[: 1 << 24].copy())
-                                                           for d, n, s, k in data]
+    if rank == 0 and world == 1 and not args.no_cpu:
+        big = any(n > (1 << 24) for _, n, _, _ in data)
+        sample = [(d, 1 << 24, s, k[: 1 << 24].copy()) for d, n, s, k in data] if big else data
         rate, spent, used = cpu_oracle_rate(sample, args.cpu_sample_seconds, desc, args.key_type)
+        what = f"the first 2^24 keys of each n = 2^{int(np.log2(max_n))} input: " if big else ""
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{used} ({spent:.1f} s of one host core)"}
+               "sample": f"{what}{used} ({spent:.1f} s of one host core)"}
 
     peak, peak_kind = peaks()
     achieved = merge_bytes / (merge_ms / 1000.0) / 1e9
@@ -1084,10 +1141,50 @@ def main():
         "gpu_launches": launches_per_sort * len(recs),
     }
     ctx.close()
+    if args.workload == "hbm_2^28" and not args.no_extras and world == 1:
+        # the metric's other two parts, measured in the same run on the same GPU
+        del work, perm, pristine, flush
+        torch.cuda.empty_cache()
+        line["batched_vs_plain"] = batched_summary(batched_leg(max(3, min(args.steps, 10)), 3, dev,
+                                                               torch.cuda.Stream(dev), e2e_steps=0))
+        torch.cuda.empty_cache()
+        line["serving"] = serving_summary(serving_leg(local, args.lane_total))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def batched_summary(r):
+    """The batched_vs_plain sub-object of the headline line (config 4)."""
+    return {
+        "workload": "batched_4096", "instances": r["count"], "total_elements": r["total"],
+        "sizes": "log-uniform in [2^8, 2^20), seed 3, uniform keys",
+        "batched": r["value"], "plain_loop": r["loop_rate"], "ratio": r["value"] / r["loop_rate"],
+        "unit": UNIT, "batched_ms_per_replay": r["ms_per_step"], "replays": r["steps"],
+        "plain_loop_ms": r["loop_ms"], "plain_loop_calls": r["count"],
+        "launch": "one CUDA-graph replay (persistent cooperative merge kernel) vs one ps_run per instance",
+        "autotune": {k: r["tuned"][k] for k in ("tile_log2", "ms", "cached")},
+        "merge_rounds_frac": r["achieved"] / r["peak"],
+        "clocks": r["clocks"],
+    }
+
+
+def serving_summary(r):
+    """The serving sub-object of the headline line (config 5)."""
+    st = r["server"]
+    return {
+        "workload": "serving", "arrivals": f"Poisson {r['rate']:.0f}/s for {r['duration']:.0f} s, seed 4",
+        "sizes": "log-uniform in [2^10, 2^24]", "requests": r["requests"],
+        "p50_ms": r["latency_ms"]["p50"], "p99_ms": r["latency_ms"]["p99"],
+        "mean_ms": r["latency_ms"]["mean"], "max_ms": r["latency_ms"]["max"],
+        "largest_request_solo_ms": r["largest_request_solo_ms"],
+        "sustained": r["value"], "offered": r["offered"], "unit": UNIT,
+        "budget_bytes": r["budget"], "device_bytes": st["device_bytes"], "lanes": st["lanes"],
+        "lane_max_total": st["lane_max_total"], "batches": st["batches"], "max_busy_lanes": st["max_busy_lanes"],
+        "io": "pinned host arrays in and out, copies inside every latency",
+        "clocks": r["clocks"],
+    }
 
 
 if __name__ == "__main__":

@@ -28,7 +28,7 @@ def test_reference_arm_prints_one_json_line():
     for k, t in KEYS.items():
         assert isinstance(d[k], t), (k, d.get(k))
     assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 1 and d["warmup"] == 3
-    assert d["config"]["workload"] == "plain_2^24" and d["vs_baseline"] is None
+    assert d["config"]["workload"] == "hbm_2^28" and d["vs_baseline"] is None
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["cpu_baseline"]["value"] == d["value"]
     e = d["e2e"]
