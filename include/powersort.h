@@ -270,6 +270,12 @@ PS_API ps_status ps_get_nodes(ps_ctx* ctx, uint32_t q, uint32_t* h_out, uint64_t
 /* Statistics of one instance of the last call (synchronises). */
 PS_API ps_status ps_get_instance_stats(ps_ctx* ctx, uint32_t q, ps_stats* stats);
 
+/* Device memory the context owns, in bytes: every buffer ps_create allocated
+ * (the figure ps_stats.scratch_bytes reports after a call).  No kernel runs
+ * and nothing synchronises, so it can be asked right after ps_create (the
+ * server charges its lanes with it against the budget). */
+PS_API ps_status ps_get_scratch_bytes(const ps_ctx* ctx, uint64_t* bytes);
+
 /* Release every device buffer of the context.  NULL is a no-op. */
 PS_API void ps_destroy(ps_ctx* ctx);
 
@@ -282,7 +288,9 @@ PS_API void ps_destroy(ps_ctx* ctx);
  * requests) and enqueues their host->device copies, one batched sort and the
  * device->host copies of the results; lanes run concurrently, so requests
  * arriving while others are on the GPU are admitted as lanes free up.
- * Results are the same stable sort that ps_run computes. */
+ * Results are the same stable sort that ps_run computes.  The memory charged
+ * against budget_bytes is what the lanes really hold: each lane's input and
+ * output arrays and offsets table plus its context's ps_get_scratch_bytes. */
 typedef struct ps_server ps_server;
 typedef struct ps_server_config {
     uint64_t budget_bytes;   /* device memory the server may hold                  */
@@ -299,7 +307,7 @@ typedef struct ps_server_config {
 
 typedef struct ps_server_stats {
     uint64_t submitted, completed, failed, elements, batches, queued;
-    uint64_t device_bytes;   /* device memory held by the lanes                    */
+    uint64_t device_bytes;   /* device memory held by the lanes (<= budget_bytes)  */
     uint64_t lane_max_total;
     uint32_t lanes;
     uint32_t max_busy_lanes; /* most lanes seen busy at once (overlap evidence)    */

@@ -26,6 +26,7 @@ EXPORTS = (
     "ps_graph_launch", "ps_graph_destroy", "ps_server_create", "ps_server_submit", "ps_server_poll",
     "ps_server_wait", "ps_server_get_stats", "ps_server_destroy", "ps_gather_rows", "ps_sort_records",
     "ps_sort_keys64", "ps_selftest_wait_timeout", "ps_check_guards", "ps_server_cancel",
+    "ps_get_scratch_bytes",
 )
 PS_NOALLOC_MAX_N = 262144
 PS_FLAG_TIMING, PS_FLAG_HOST_IO, PS_FLAG_DESCENDING_RUNS, PS_FLAG_RECORDS = 1, 2, 4, 8
@@ -200,6 +201,8 @@ def _load(build_if_missing: bool):
     L.ps_get_instance_stats.argtypes = [vp, ctypes.c_uint32, ctypes.POINTER(ps_stats)]
     L.ps_destroy.restype = None
     L.ps_destroy.argtypes = [vp]
+    L.ps_get_scratch_bytes.restype = ctypes.c_int
+    L.ps_get_scratch_bytes.argtypes = [vp, u64p]
     L.ps_run_noalloc.restype = ctypes.c_int
     L.ps_run_noalloc.argtypes = [vp, vp, ctypes.c_uint64, ctypes.c_int, vp]
     return L
@@ -367,6 +370,11 @@ class Context:
             _check(lib().ps_get_nodes(self._h, q, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
                                       out.size, None), "ps_get_nodes")
         return out.reshape(-1, 2)
+
+    def scratch_bytes(self) -> int:
+        out = ctypes.c_uint64(0)
+        _check(lib().ps_get_scratch_bytes(self._h, ctypes.byref(out)), "ps_get_scratch_bytes")
+        return int(out.value)
 
     def instance_stats(self, q: int = 0) -> dict:
         st = ps_stats()

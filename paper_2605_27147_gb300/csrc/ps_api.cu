@@ -781,6 +781,13 @@ PS_API ps_status ps_get_instance_stats(ps_ctx* ctx, uint32_t q, ps_stats* stats)
     return PS_OK;
 }
 
+PS_API ps_status ps_get_scratch_bytes(const ps_ctx* ctx, uint64_t* bytes)
+{
+    if (!ctx || !bytes) return PS_EINVAL;
+    *bytes = ctx->scratch_bytes;
+    return PS_OK;
+}
+
 PS_API void ps_destroy(ps_ctx* ctx)
 {
     if (!ctx) return;

@@ -14,7 +14,7 @@
 //   k_bucket       HBM nodes placed by round, chunk numbers
 //   k_chunk_nodes  chunk -> merge table; parent links and dependency counts
 //   k_tiles        runs sorted and merged inside shared memory
-//   k_merge_rounds persistent cooperative kernel: every HBM merge, scheduled
+//   k_merge_rounds persistent kernel: every HBM merge, scheduled
 //                  as a dataflow over the merge tree
 #pragma once
 

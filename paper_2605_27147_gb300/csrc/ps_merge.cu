@@ -7,7 +7,7 @@
 // threads x MERGE_K).  Chunks are numbered
 // round by round (rounds go from the largest power to the smallest), so a
 // merge's children always carry smaller chunk numbers than the merge itself.
-// One persistent cooperative launch processes every chunk as a dataflow,
+// One persistent launch processes every chunk as a dataflow,
 // without grid-wide barriers: a merge starts as soon as both of its children
 // are complete, while other merges of the previous round may still run.
 //
@@ -43,8 +43,12 @@
 // Progress: chunks are claimed in increasing order and wait only for smaller
 // chunk numbers, so the smallest unfinished chunk always has its inputs
 // complete; every written chunk is announced (at the latest when its CTA goes
-// idle); cooperative launch keeps every CTA resident.  Every wait is bounded
-// and records DERR_TIMEOUT instead of hanging.
+// idle).  A CTA claims chunks only while it runs and leaves only when it
+// holds none, so every chunk a running CTA waits for is held by a running CTA:
+// progress needs no co-residency, and the kernel is an ordinary launch.  CTAs
+// that cannot start yet (the SMs busy with another stream's kernels, as in
+// the server) start later or find no chunk left; nothing waits for them.
+// Every wait is bounded and records DERR_TIMEOUT instead of hanging.
 #include "ps_internal.cuh"
 
 namespace ps {
@@ -735,9 +739,8 @@ uint32_t merge_chunk()
 
 cudaError_t launch_merge_rounds(const Job& J, int grid, cudaStream_t s)
 {
-    void* args[] = {(void*)&J};
-    return cudaLaunchCooperativeKernel((const void*)k_merge_rounds<2, 512>, dim3(grid), dim3(MergeShape::MTHREADS),
-                                       args, sizeof(MergeSmem<2, 512>), s);
+    k_merge_rounds<2, 512><<<grid, MergeShape::MTHREADS, sizeof(MergeSmem<2, 512>), s>>>(J);
+    return cudaGetLastError();
 }
 
 }  // namespace ps

@@ -52,7 +52,10 @@ struct Lane {
     bool busy = false;
 };
 
-constexpr double BYTES_PER_ELEM_ESTIMATE = 18.0;   // caller arrays + scratch + tables, per element
+// Only for choosing a lane size when the caller gives none: lane arrays
+// (keys + permutation) plus a Pingpong context's scratch and tables, per
+// element.  What the lanes are charged is measured (lane_bytes below).
+constexpr double BYTES_PER_ELEM_ESTIMATE = 18.0;
 
 }  // namespace
 
@@ -223,8 +226,10 @@ PS_API ps_status ps_server_create(const ps_server_config* cfg, ps_server** out)
     }
     if (lane_total < S->cfg.max_n) lane_total = S->cfg.max_n;
     S->lane_total = lane_total;
-    if ((double)lane_total * BYTES_PER_ELEM_ESTIMATE * S->cfg.lanes > (double)S->cfg.budget_bytes) {
-        delete S;                               // the lanes cannot fit: allocate nothing
+    // the lane arrays alone must fit before anything is allocated
+    const double arrays = (double)lane_total * 4.0 * (S->cfg.want_perm ? 2.0 : 1.0) * S->cfg.lanes;
+    if (arrays > (double)S->cfg.budget_bytes) {
+        delete S;
         return PS_ENOMEM;
     }
     int prev = -1;
@@ -260,10 +265,15 @@ PS_API ps_status ps_server_create(const ps_server_config* cfg, ps_server** out)
         c.max_count = S->lane_count;
         st = ps_create(&c, (int)S->cfg.device, L.stream, &L.ctx);
         if (st != PS_OK) break;
-        S->bytes += lane_total * 4 * (S->cfg.want_perm ? 2 : 1) + (S->lane_count + 1) * sizeof(uint64_t);
-        // the context reports its own device memory through the stats of a call;
-        // an empty sort would need a kernel, so use the allocation estimate here
-        S->bytes += (uint64_t)(lane_total * (BYTES_PER_ELEM_ESTIMATE - 8.0));
+        uint64_t scratch = 0;
+        st = ps_get_scratch_bytes(L.ctx, &scratch);
+        if (st != PS_OK) break;
+        // what this lane holds: its arrays, its offsets table and its context
+        S->bytes += lane_total * 4 * (S->cfg.want_perm ? 2 : 1) + (S->lane_count + 1) * sizeof(uint64_t) + scratch;
+        if (S->bytes > S->cfg.budget_bytes) {   // stop as soon as the lanes overrun the budget
+            st = PS_ENOMEM;
+            break;
+        }
     }
     if (st == PS_OK && S->bytes > S->cfg.budget_bytes) st = PS_ENOMEM;
     if (st != PS_OK) {

@@ -89,6 +89,8 @@ def test_argument_errors_need_no_gpu(lib):
     assert lib.ps_selftest_wait_timeout(None) == binding.PS_EINVAL
     assert lib.ps_check_guards(None) == binding.PS_EINVAL
     assert lib.ps_server_cancel(None, 0) == binding.PS_EINVAL
+    out = ctypes.c_uint64(0)
+    assert lib.ps_get_scratch_bytes(None, ctypes.byref(out)) == binding.PS_EINVAL
     cfg = binding.ps_config(mode=0, want_perm=1, max_n=100, key_type=3)
     assert lib.ps_create(ctypes.byref(cfg), 0, None, ctypes.byref(h)) == binding.PS_EINVAL
     lib.ps_destroy(None)

@@ -42,6 +42,7 @@ def test_results_same_alone_and_in_the_mix(oracle_mod):
         lat = [srv.wait(t, 120.0) for _, t in tickets]
         st = srv.stats()
     assert st["completed"] == len(reqs) and st["failed"] == 0
+    assert 0 < st["device_bytes"] <= 2 << 30, st    # what the lanes hold stays within the budget
     assert st["batches"] > 3
     assert st["max_busy_lanes"] >= 2, st            # batches were on the GPU together
     assert all(x >= 0 for x in lat)
@@ -127,3 +128,22 @@ def test_cancel_queued_requests(oracle_mod):
                 assert np.array_equal(hk.numpy().view(np.uint32), oracle_mod.stable_sort(k)[0])
         st = srv.stats()
         assert st["failed"] == sum(cancelled) and st["completed"] == len(tickets) - sum(cancelled)
+
+
+def test_server_charges_what_the_lanes_hold():
+    """The budget is checked against each lane's real allocation: its arrays,
+    its offsets table and its context's scratch (ps_get_scratch_bytes)."""
+    from paper_2605_27147_gb300 import binding
+
+    lane_total, lanes, count = 1 << 20, 2, 64
+    with binding.Context(1 << 20, want_perm=True, max_total=lane_total, max_count=count) as c:
+        scratch = c.scratch_bytes()
+    assert scratch > 8 * lane_total                 # the Pingpong scratch arrays and the tables
+    need = lanes * (8 * lane_total + 8 * (count + 1) + scratch)
+    with binding.Server(need, 1 << 20, lanes=lanes, lane_max_total=lane_total, lane_max_count=count) as srv:
+        st = srv.stats()
+    assert st["device_bytes"] == need
+    # the lane arrays alone fit, the contexts' scratch does not
+    with pytest.raises(binding.PowersortError) as e:
+        binding.Server(need - 1, 1 << 20, lanes=lanes, lane_max_total=lane_total, lane_max_count=count)
+    assert e.value.status == binding.PS_ENOMEM
