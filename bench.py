@@ -88,7 +88,7 @@ WORKLOADS = {
 DESCENDING_WORKLOADS = {"updown_2^24"}   # sorted with the decreasing-run variant
 FLUSH_BYTES = 512 << 20
 BYTES_PER_MERGED_ELEM = 16   # key + perm entry read, key + perm entry written
-LAUNCHES_PER_BATCH = 13      # one batched Pingpong call: setup, 2 run detection, 7 planning, tiles, merges, finish
+LAUNCHES_PER_BATCH = 11      # one batched Pingpong call: setup, 2 run detection, 5 planning, tiles, merges, finish
 
 
 def parse():
@@ -1141,6 +1141,23 @@ def main():
         "gpu_launches": launches_per_sort * len(recs),
     }
     ctx.close()
+    if args.storage == "vm":
+        # extra memory of VM storage (Sec. 4 "Pages needed"; the paper's Fig. 5
+        # table) beside the paper's bound and Pingpong's scratch at the same n
+        st0 = hbm[0]
+        pp = binding.Context(max_n, want_perm=True, device=local, stream=stream)
+        pp_bytes = pp.scratch_bytes()
+        pp.close()
+        bound_elems = math.sqrt(max_n * 1 * math.log2(max_n))      # T = 1 word per element
+        line["vm_memory"] = {
+            "extra_bytes": st0["scratch_bytes"], "page_size": st0["page_size"], "pool_pages": st0["pool_pages"],
+            "pool_bytes": st0["pool_pages"] * st0["page_size"] * 8, "peak_pool_pages": st0["peak_pages"],
+            "paper_bound_elements": bound_elems, "paper_bound_bytes": 8 * bound_elems,
+            "pingpong_scratch_bytes": pp_bytes, "input_bytes": 8 * max_n,
+            "note": "extra_bytes = every device buffer the VM context holds: the page pool, the run list "
+                    "(n/32 slots), page tables (n/P pages) and HBM-merge tables (< 4n/T); the paper's "
+                    "sqrt(n T log n) counts the pool of one sequential sort, keys and permutation here",
+        }
     if args.workload == "hbm_2^28" and not args.no_extras and world == 1:
         # the metric's other two parts, measured in the same run on the same GPU
         del work, perm, pristine, flush

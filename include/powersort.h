@@ -126,6 +126,8 @@ typedef struct ps_stats {
     uint32_t launches;      /* kernels the call launched                          */
     uint32_t pages_spliced; /* VM mode: output pages that took over a whole input
                                page through the page table, moving no element */
+    uint32_t page_size;     /* VM mode: P, elements per page (else 0)             */
+    uint32_t pool_pages;    /* VM mode: pages of the pre-allocated pool (else 0)  */
 } ps_stats;
 
 typedef struct ps_ctx ps_ctx;
@@ -258,7 +260,11 @@ PS_API ps_status ps_check_guards(ps_ctx* ctx);
  *                  q, left to right (runs - 1 entries, Sec. 2 Theorem).
  *   ps_get_nodes:  for every boundary, the element range [lo, hi) of the
  *                  merge that joins its two sides in Algorithm 1 (2 entries
- *                  per boundary: lo, hi), i.e. the merge tree.
+ *                  per boundary: lo, hi), i.e. the merge tree.  The sort keeps
+ *                  only its HBM merges, so this call recomputes every range on
+ *                  the device with the planning's own code, in a temporary
+ *                  device buffer of 8 bytes per boundary (PS_ENOMEM if it
+ *                  cannot be had).
  * h_out receives at most `cap` entries; *count (may be NULL) receives the
  * number available.  PS_EINVAL if q is not an instance of the last call. */
 PS_API ps_status ps_get_runs(ps_ctx* ctx, uint32_t q, uint32_t* h_out, uint64_t cap,

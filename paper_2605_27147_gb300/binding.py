@@ -67,6 +67,8 @@ class ps_stats(ctypes.Structure):
         ("hbm_merge_elems", ctypes.c_uint64),
         ("launches", ctypes.c_uint32),
         ("pages_spliced", ctypes.c_uint32),
+        ("page_size", ctypes.c_uint32),
+        ("pool_pages", ctypes.c_uint32),
     ]
 
     def as_dict(self):

@@ -1,5 +1,6 @@
 // C ABI of the library (include/powersort.h): argument checks, the context
 // with every device buffer allocated up front, and the launch sequence.
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -44,7 +45,7 @@ struct ps_ctx {
 namespace {
 
 constexpr unsigned long long LIMIT_N = 0xffffffffull;  // instance sizes and totals < 2^32
-constexpr uint32_t LAUNCHES_PER_CALL = 13;  // setup, 2 run detection, 7 planning, tiles, merges, finish
+constexpr uint32_t LAUNCHES_PER_CALL = 11;  // setup, 2 run detection, 5 planning, tiles, merges, finish
 constexpr uint32_t NPHASES = 6;
 
 struct DeviceGuard {
@@ -166,6 +167,8 @@ void fill_stats(const ps_ctx* c, ps_stats* st, uint32_t count)
     // VM: rounds + the final Copy; typed keys: the two maps
     st->launches = LAUNCHES_PER_CALL + (c->base.vm ? 1u : 0u) + (c->base.key_type != PS_KEY_U32 ? 2u : 0u);
     st->pages_spliced = c->base.vm ? h->vm_spliced : 0u;
+    st->page_size = c->base.vm ? 1u << c->base.vm_plog2 : 0u;
+    st->pool_pages = c->base.vm ? c->base.vm_pool : 0u;
 }
 
 ps_status run_common(ps_ctx* c, uint32_t* d_keys, uint32_t* d_perm, const uint64_t* d_offsets,
@@ -283,18 +286,39 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
     J.max_total = max_total;
     const unsigned long long slot_cap = max_total / 32 + 2ull * c->max_count + 2;
     const unsigned long long chunk_cap = max_total / ps::RUN_CHUNK + c->max_count + 1;
-    const unsigned long long entry_cap = slot_cap;
-    // chunks summed over all rounds: at most 32 rounds of max_total outputs
+    const unsigned long long T = J.tile_cap;
+    // the merge map: ceil(4 n / T) entries per instance of more than T
+    // elements (an HBM merge of Power p has 2^p < 4n / T)
+    const unsigned long long gmap_cap = (4ull * max_total + T - 1) / T + c->max_count + 1;
+    // HBM merges: at most one per merge-map entry; for one instance, at most
+    // min(2^(p-1), n / (T + 1)) of every power p with 2^p < 4n / T (merges of
+    // one power have distinct odd points c < 2^p, are disjoint, and each has
+    // more than T elements)
+    unsigned long long gnode_cap = gmap_cap;
+    unsigned pmax = 0;                 // the largest power an HBM merge can have
+    while (pmax < 34 && ((1ull << (pmax + 1)) * T < 4ull * cfg->max_n)) ++pmax;
+    if (c->max_count == 1) {
+        unsigned long long g = 0;
+        for (unsigned p = 1; p <= pmax; ++p) g += std::min(1ull << (p - 1), (unsigned long long)cfg->max_n / (T + 1));
+        gnode_cap = std::min(gnode_cap, g + 1);
+    }
+    // tiles: the two children of every HBM merge, or the whole instance
+    const unsigned long long tile_items_cap = 2 * gnode_cap + c->max_count + 1;
+    // chunks summed over all rounds: the HBM merges of one power are disjoint,
+    // so every power holds at most max_total outputs, plus one partial chunk
+    // per merge
     const unsigned long long chunk_node_cap =
-        (unsigned long long)(ps::NPOW - 1) * (max_total / ps::merge_chunk()) + entry_cap + 2;
-    if (chunk_cap > 0xffffffffull || entry_cap > 0xffffffffull ||
+        (unsigned long long)pmax * (max_total / ps::merge_chunk()) + gnode_cap + 2;
+    if (chunk_cap > 0xffffffffull || gmap_cap > 0xffffffffull || tile_items_cap > 0xffffffffull ||
         chunk_node_cap > 0xffffffffull) {
         delete c;
         return PS_EINVAL;
     }
     J.slot_cap = slot_cap;
     J.chunk_cap = (uint32_t)chunk_cap;
-    J.entry_cap = (uint32_t)entry_cap;
+    J.gnode_cap = (uint32_t)gnode_cap;
+    J.tile_cap_items = (uint32_t)tile_items_cap;
+    J.gmap_cap = (uint32_t)gmap_cap;
     J.chunk_node_cap = (uint32_t)chunk_node_cap;
 
     ps_status st = PS_OK;
@@ -319,9 +343,6 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
         if (J.vm_pool < 16) J.vm_pool = 16;
         // the free-page ring: the pool's pages plus at most one push per page per round
         J.vm_ring_cap = J.vm_pool + (uint32_t)ps::NPOW * J.vm_na_cap;
-        const size_t P = (size_t)1 << plog2;
-        if (st == PS_OK) st = dev_alloc(c, &J.pool_keys, (size_t)J.vm_pool * P);
-        if (st == PS_OK && cfg->want_perm) st = dev_alloc(c, &J.pool_perm, (size_t)J.vm_pool * P);
         if (st == PS_OK) st = dev_alloc(c, &J.pt, J.vm_na_cap);
         if (st == PS_OK) st = dev_alloc(c, &J.pt_new, J.vm_na_cap);
         if (st == PS_OK) st = dev_alloc(c, &J.page_cnt, J.vm_na_cap);
@@ -335,24 +356,42 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
     } else {
         if (st == PS_OK) st = dev_alloc(c, &J.keysB, max_total);
         if (st == PS_OK && cfg->want_perm) st = dev_alloc(c, &J.permB, max_total);
+        if (st == PS_OK) st = dev_alloc(c, &J.chunk_node, chunk_node_cap);
+    }
+    // One region for three sets of tables whose lifetimes do not overlap (all
+    // on the context's stream): run detection's chunk maps (until the run
+    // starts are written), the merge planning's tiles, HBM merges and merge
+    // map (until the tiles are merged), and VM storage's page pool (the merge
+    // rounds and Copy).
+    {
+        auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+        const size_t b_map = al(chunk_cap * ps::MAP_STATES * 4), b_info = al(chunk_cap * 4);
+        const size_t b_tiles = al(tile_items_cap * sizeof(ps::TileItem)), b_gn = al(gnode_cap * sizeof(ps::GNode));
+        const size_t b_gmap = al(gmap_cap * 4);
+        const size_t b_pool = vm ? al((size_t)J.vm_pool << J.vm_plog2 << 2) : 0;
+        const size_t bytes = std::max(std::max(b_map + b_info, b_tiles + b_gn + b_gmap),
+                                      b_pool * (cfg->want_perm ? 2u : 1u));
+        unsigned char* U = nullptr;
+        if (st == PS_OK) st = dev_alloc(c, &U, bytes);
+        if (U) {
+            J.chunk_map = reinterpret_cast<uint32_t*>(U);
+            J.chunk_info = reinterpret_cast<uint32_t*>(U + b_map);
+            J.tiles = reinterpret_cast<ps::TileItem*>(U);
+            J.gnodes = reinterpret_cast<ps::GNode*>(U + b_tiles);
+            J.gmap = reinterpret_cast<uint32_t*>(U + b_tiles + b_gn);
+            if (vm) {
+                J.pool_keys = reinterpret_cast<uint32_t*>(U);
+                J.pool_perm = cfg->want_perm ? reinterpret_cast<uint32_t*>(U + b_pool) : nullptr;
+            }
+        }
     }
     if (st == PS_OK) st = dev_alloc(c, &J.inst, c->max_count);
-    if (st == PS_OK) st = dev_alloc(c, &J.chunk_map, chunk_cap * ps::MAP_STATES);
-    if (st == PS_OK) st = dev_alloc(c, &J.chunk_info, chunk_cap);
-    if (st == PS_OK) st = dev_alloc(c, &J.chunk_bits, chunk_cap * ps::RUN_WORDS);
     if (st == PS_OK) st = dev_alloc(c, &J.range_agg, (size_t)c->grid_runs * ps::MAP_STATES);
     if (st == PS_OK) st = dev_alloc(c, &J.range_entry, (size_t)c->grid_runs);
     if (st == PS_OK) st = dev_alloc(c, &J.run_start, slot_cap);
-    if (st == PS_OK) st = dev_alloc(c, &J.kappa, slot_cap);
     if (st == PS_OK) st = dev_alloc(c, &J.power, slot_cap);
-    if (st == PS_OK) st = dev_alloc(c, &J.na, slot_cap);
-    if (st == PS_OK) st = dev_alloc(c, &J.nb, slot_cap);
-    if (st == PS_OK) st = dev_alloc(c, &J.tiles, entry_cap);
-    if (st == PS_OK) st = dev_alloc(c, &J.gnodes, entry_cap);
-    if (st == PS_OK) st = dev_alloc(c, &J.gsorted, entry_cap);
-    if (st == PS_OK) st = dev_alloc(c, &J.dep, entry_cap);
-    J.gidx = J.kappa;
-    if (st == PS_OK) st = dev_alloc(c, &J.chunk_node, chunk_node_cap);
+    if (st == PS_OK) st = dev_alloc(c, &J.gsorted, gnode_cap);
+    if (st == PS_OK) st = dev_alloc(c, &J.dep, gnode_cap);
     if (st == PS_OK) st = dev_alloc(c, &J.ctr, 1);
     if (st == PS_OK && (cfg->flags & PS_FLAG_RECORDS)) {
         c->rec_group_cap = (uint32_t)(cfg->max_n / 2 + 1);
@@ -382,10 +421,10 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
         st = PS_ECUDA;
     if (st == PS_OK && cudaDeviceSynchronize() != cudaSuccess) st = PS_ECUDA;
     // every table the kernels write must exist (permB only with want_perm)
-    if (st == PS_OK && ((!vm && !J.keysB) || !J.inst || !J.chunk_map || !J.chunk_info || !J.chunk_bits || !J.range_agg || !J.range_entry ||
-                        !J.run_start || !J.kappa || !J.power || !J.na || !J.nb || !J.tiles || !J.gnodes ||
-                        !J.gsorted || !J.dep || !J.chunk_node || !J.ctr ||
-                        (!vm && cfg->want_perm && !J.permB) || (vm && (!J.pool_keys || !J.pt || !J.vm_split_at || !J.vm_rec || !J.free_stack))))
+    if (st == PS_OK && ((!vm && (!J.keysB || !J.chunk_node)) || !J.inst || !J.chunk_map || !J.chunk_info ||
+                        !J.range_agg || !J.range_entry || !J.run_start || !J.power || !J.tiles || !J.gnodes ||
+                        !J.gmap || !J.gsorted || !J.dep || !J.ctr || (!vm && cfg->want_perm && !J.permB) ||
+                        (vm && (!J.pool_keys || !J.pt || !J.vm_split_at || !J.vm_rec || !J.free_stack))))
         st = PS_EINTERNAL;
     if (st != PS_OK) {
         cudaGetLastError();
@@ -751,16 +790,23 @@ PS_API ps_status ps_get_nodes(ps_ctx* ctx, uint32_t q, uint32_t* h_out, uint64_t
     const uint64_t nbound = I.runs >= 2 ? (uint64_t)I.runs - 1 : 0;
     if (count) *count = 2 * nbound;
     if (!nbound || !cap) return PS_OK;
-    std::vector<uint32_t> rs(I.runs + 1), na(I.runs), nb(I.runs);
-    if (cudaMemcpy(rs.data(), ctx->base.run_start + I.run_base, rs.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
-        cudaMemcpy(na.data(), ctx->base.na + I.run_base, na.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
-        cudaMemcpy(nb.data(), ctx->base.nb + I.run_base, nb.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
-        return PS_ECUDA;
-    for (uint64_t t = 1; t <= nbound && 2 * (t - 1) + 1 < cap; ++t) {
-        h_out[2 * (t - 1)] = rs[na[t]];
-        h_out[2 * (t - 1) + 1] = rs[nb[t]];
+    // the ranges are not kept after the call (the sort needs them only for
+    // its HBM merges): the planning's node_range recomputes them for every
+    // boundary from the run starts, into a buffer of this call
+    uint32_t* d = nullptr;
+    if (cudaMalloc(&d, 2 * nbound * sizeof(uint32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        return PS_ENOMEM;
     }
-    return PS_OK;
+    ps_status rc = PS_OK;
+    if (ps::launch_node_ranges(ctx->base, q, (uint32_t)nbound, d, ctx->stream) != cudaSuccess ||
+        cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+        rc = PS_ECUDA;
+    const uint64_t k = 2 * nbound < cap ? 2 * nbound : cap;
+    if (rc == PS_OK && cudaMemcpy(h_out, d, k * sizeof(uint32_t), cudaMemcpyDeviceToHost) != cudaSuccess) rc = PS_ECUDA;
+    cudaFree(d);
+    if (rc != PS_OK) cudaGetLastError();
+    return rc;
 }
 
 PS_API ps_status ps_get_instance_stats(ps_ctx* ctx, uint32_t q, ps_stats* stats)

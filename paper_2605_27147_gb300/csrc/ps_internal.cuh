@@ -5,13 +5,12 @@
 //   k_runs         run detection with minrun extension (ExtractRun, Sec. 2/5):
 //                  chunk maps of the chain scan, folded per range, scanned
 //   k_runs_emit    run starts of every chunk from its entry state
-//   k_kappa        fixed-point run midpoints (the quantities Power compares)
-//   k_nodes        Power per boundary (Sec. 2 Theorem) and the element range
-//                  of the merge Algorithm 1 performs at that boundary
-//   k_classify     split the merge tree into on-chip tiles and HBM nodes
-//   k_depth        depth of tiles / HBM nodes (Pingpong buffer parity, Sec. 3)
+//   k_nodes        Power per boundary (Sec. 2 Theorem), the element range of
+//                  the merge Algorithm 1 performs there, and the split of the
+//                  merge tree into HBM merges and on-chip tiles
+//   k_depth        depth of the HBM merges (Pingpong buffer parity, Sec. 3)
 //   k_bucket_scan  round starts (prefix sums of per-round merge / chunk counts)
-//   k_bucket       HBM nodes placed by round, chunk numbers
+//   k_bucket       HBM merges placed by round, chunk numbers; tile depths
 //   k_chunk_nodes  chunk -> merge table; parent links and dependency counts
 //   k_tiles        runs sorted and merged inside shared memory
 //   k_merge_rounds persistent kernel: every HBM merge, scheduled
@@ -72,17 +71,31 @@ struct Inst {
     uint32_t nchunks;
     uint32_t runs;                // R, written by run detection
     uint32_t max_power;
+    uint32_t g_base;              // first entry of the instance's merge map (Job::gmap)
+    uint32_t g_span;              // its entries: ceil(4 n / T) when n > T, else 0
 };
 
-// A subtree merged on chip: runs [r0, r1) of an instance; t = its root
-// boundary (NONE for a single run).  depth = depth of the subtree root.
+// Index of the merge with Power p and dyadic point c / 2^p (c odd) in its
+// instance's merge map: merges of one power have distinct points, so
+// (p, c) names a merge uniquely; an HBM merge (more than T elements) has
+// 2^p < 4n / T, so its index 2^(p-1) - 1 + (c - 1) / 2 < 4n / T.
+__host__ __device__ __forceinline__ uint32_t merge_index(uint32_t p, uint32_t c)
+{
+    return (1u << (p - 1)) - 1u + (c >> 1);
+}
+
+// A subtree merged on chip: runs [r0, r1) of an instance; parent = the GNode
+// index of the HBM merge it is a child of (NONE: the whole instance).  depth
+// = depth of the subtree root.
 struct TileItem {
-    uint32_t inst, r0, r1, t, depth, pad;
+    uint32_t inst, r0, r1, parent, depth, pad;
 };
 
-// A merge done through HBM (boundary t of an instance).
+// A merge done through HBM: boundary t of an instance joining runs [a, t)
+// and [t, b); midx / pidx = merge-map indices of itself and of its parent
+// merge (NONE for the instance's root).
 struct GNode {
-    uint32_t inst, t, depth, power;
+    uint32_t inst, t, a, b, power, depth, midx, pidx;
 };
 
 // HBM merge in round order: output [goff, goff + la + lb), left child
@@ -168,27 +181,29 @@ struct Job {
     unsigned long long max_n;   // limits the offsets table is checked against
     unsigned long long max_total;
     Inst* inst;
+    // run detection's tables (chunk_map, chunk_info) live only until the run
+    // starts are written; the merge planning's (tiles, gnodes, gmap) only
+    // until the tiles are merged; VM storage's page pool only after that:
+    // the three share one region of the context
     uint32_t* chunk_map;        // MAP_STATES per chunk: (runs << 8) | exit state, per entry state
     uint32_t* chunk_info;       // per chunk: CHUNK_FORCED | CHUNK_FIRST | first descent offset
-    uint32_t* chunk_bits;       // RUN_WORDS per chunk: descent bitmask of chunks that need the chain walk
     uint32_t* range_agg;        // MAP_STATES per run-detection CTA: its range's map
     unsigned long long* range_entry;   // per run-detection CTA: (runs before << 8) | entry state
-    uint32_t* run_start;
-    uint32_t* kappa;
-    uint8_t* power;
-    uint32_t* na;
-    uint32_t* nb;
+    uint32_t* run_start;        // per run slot: the run's first element (R + 1 per instance)
+    uint8_t* power;             // per boundary slot: its Power
     TileItem* tiles;
     GNode* gnodes;
+    uint32_t* gmap;             // merge map: per (power, point) index, the merge's GNode index,
+                                // then (from k_bucket on) its GSorted index
     GSorted* gsorted;
     uint32_t* dep;              // per GSorted entry: chunks of its HBM children not yet written
-    uint32_t* gidx;             // per boundary slot: GSorted index of its HBM merge (kappa's memory,
-                                // reused once the powers are known)
     uint32_t* chunk_node;       // per chunk (ids global across rounds): its GSorted index
     Ctr* ctr;
     unsigned long long slot_cap;
     uint32_t chunk_cap;
-    uint32_t entry_cap;         // capacity of tiles / gnodes / gsorted
+    uint32_t gnode_cap;         // capacity of gnodes / gsorted / dep
+    uint32_t tile_cap_items;    // capacity of tiles
+    uint32_t gmap_cap;          // entries of the merge map (all instances)
     uint32_t chunk_node_cap;
     // virtual-memory storage (Sec. 4): pages of P = 2^vm_plog2 elements
     uint32_t vm;                // nonzero: VM storage instead of Pingpong
@@ -427,6 +442,7 @@ cudaError_t launch_setup(const Job& J, cudaStream_t s);
 cudaError_t launch_runs(const Job& J, int grid, cudaStream_t s);
 uint32_t merge_chunk();
 cudaError_t launch_plan(const Job& J, int grid, cudaStream_t s);
+cudaError_t launch_node_ranges(const Job& J, uint32_t q, uint32_t nbound, uint32_t* out, cudaStream_t s);
 cudaError_t launch_tiles(const Job& J, int grid, cudaStream_t s);
 cudaError_t launch_merge_rounds(const Job& J, int grid, cudaStream_t s);
 cudaError_t launch_finish(const Job& J, cudaStream_t s);

@@ -9,7 +9,9 @@
 // integer division), floor(x 2^p) = kappa >> (32 - p) for every p <= 32, so
 //     Power = 1 + (number of leading binary digits kappa_left and kappa_right
 //                  share) = clz(kappa_left ^ kappa_right) + 1,
-// exact for n < 2^32 because Power <= ceil(log2 n) <= 32.
+// exact for n < 2^32 because Power <= ceil(log2 n) <= 32.  kappa is computed
+// from the run starts where it is needed; comparisons kappa >= X are made as
+// (start + end) 2^31 >= X n, without a division.
 //
 // The merge tree.  Algorithm 1 merges the stack top while its power is >= the
 // new power, so the merge made at boundary t joins all runs between the
@@ -17,18 +19,26 @@
 // the right with a smaller power (the Cartesian tree of the powers; two equal
 // powers always have a smaller one between them).  In midpoint terms: if the
 // point found for boundary t is c / 2^p (c odd), that merge covers exactly the
-// runs whose midpoints lie in [(c-1)/2^p, (c+1)/2^p).  k_nodes finds the first
-// and last such run by galloping over the sorted kappa values; the total work
-// is linear in the number of runs for balanced trees.
+// runs whose midpoints lie in [(c-1)/2^p, (c+1)/2^p).  node_range finds the
+// first and last such run by galloping over the runs' midpoints; the total
+// work is linear in the number of runs for balanced trees.
+//
+// Sizes.  The midpoints of a merge's first and last run are less than 2n/2^p
+// apart, and the merge's size is at most twice that distance, so a merge of
+// Power p has fewer than 4n/2^p elements.  A merge of more than T elements
+// (an HBM merge) therefore has 2^p < 4n/T: an instance has fewer than 4n/T
+// HBM merges, and (p, c) indexes them densely (merge_index).
 //
 // The schedule.  A node (merge) whose range has at most T elements, and whose
 // parent's range has more, is a tile: its whole subtree is merged in shared
-// memory by one CTA.  Nodes above T are HBM nodes, merged in rounds of equal
-// power (children have larger powers than their parent, and nodes of equal
-// power are disjoint).  Each HBM node writes buffer depth & 1 (0 = the
-// caller's array, 1 = scratch) and reads buffer (depth + 1) & 1, the
-// Pingpong discipline of Sec. 3 arranged so that the root lands in the
-// caller's array without a final copy.
+// memory by one CTA.  Every tile is a child of an HBM merge (or the whole
+// instance), so k_nodes lists the tiles with the HBM merges: the left part
+// [a, t) and the right part [t, b) of an HBM merge at boundary t are its two
+// children.  HBM merges are done in rounds of equal power (children have
+// larger powers than their parent, and merges of equal power are disjoint).
+// Each writes buffer depth & 1 (0 = the caller's array, 1 = scratch) and
+// reads buffer (depth + 1) & 1, the Pingpong discipline of Sec. 3 arranged so
+// that the root lands in the caller's array without a final copy.
 #include "ps_internal.cuh"
 
 namespace ps {
@@ -37,8 +47,8 @@ namespace {
 
 constexpr uint32_t FULL = 0xffffffffu;
 
-constexpr int NODE_HALO = 768;                          // k_nodes: staged slots on each side
-constexpr int NODE_WIN = PLAN_BLOCK + 2 * NODE_HALO;
+constexpr int NODE_HALO = 768;                          // k_nodes: staged run starts on each side
+constexpr int NODE_WIN = PLAN_BLOCK + 2 * NODE_HALO + 2;
 
 __device__ __forceinline__ uint32_t inst_of_slot(const Job& J, unsigned long long slot)
 {
@@ -58,148 +68,181 @@ __device__ __forceinline__ uint32_t warp_append(uint32_t* counter, bool want)
     return want ? base + __popc(mask & ((1u << lane) - 1u)) : NONE;
 }
 
-__device__ __forceinline__ uint32_t node_size(const uint32_t* rs, const uint32_t* na, const uint32_t* nb, uint32_t t)
+// The fixed-point midpoint of the run [s, e) of an instance of n elements.
+__device__ __forceinline__ uint32_t kappa_of(uint32_t s, uint32_t e, uint32_t n)
 {
-    return rs[nb[t]] - rs[na[t]];
+    return (uint32_t)((((unsigned long long)s + e) << 31) / n);
 }
 
-// Parent of boundary t: the nearer-in-tree of its two smaller neighbours,
-// i.e. the one with the larger power (NONE for the root).
-__device__ __forceinline__ uint32_t parent_of(const uint8_t* pw, const uint32_t* na, const uint32_t* nb,
-                                              uint32_t t, uint32_t R)
+// kappa_of(s, e, n) >= X for an integer X <= 2^32, without the division.
+__device__ __forceinline__ bool kappa_ge(uint32_t s, uint32_t e, uint32_t n, unsigned long long X)
 {
-    const uint32_t a = na[t], b = nb[t];
-    const bool va = a >= 1, vb = b <= R - 1;
-    if (va && vb) return pw[a] > pw[b] ? a : b;
-    if (va) return a;
-    if (vb) return b;
-    return NONE;
+    return (((unsigned long long)s + e) << 31) >= X * n;
 }
 
-// Parent boundary of leaf s: whichever of boundaries s and s+1 exists with the
-// larger power (NONE when the instance is a single run).
-__device__ __forceinline__ uint32_t leaf_parent(const uint8_t* pw, uint32_t s, uint32_t R)
+struct NodeRange {
+    uint32_t a, b;   // the merge joins runs [a, t) and [t, b)
+    uint32_t p, c;   // its Power and dyadic point c / 2^p (c odd)
+};
+
+// Power of boundary t (1 <= t < R) and its point.  rs(x) = start of run x
+// (x <= R, rs(R) = n).
+template <typename RS>
+__device__ __forceinline__ void power_of(RS rs, uint32_t n, uint32_t t, uint32_t& p, uint32_t& c)
 {
-    const bool vl = s >= 1, vr = s + 1 <= R - 1;
-    if (vl && vr) return pw[s] > pw[s + 1] ? s : s + 1;
-    if (vl) return s;
-    if (vr) return s + 1;
-    return NONE;
+    const uint32_t X = kappa_of(rs(t - 1), rs(t), n), Y = kappa_of(rs(t), rs(t + 1), n);
+    p = __clz(X ^ Y) + 1;                 // 1..32
+    c = Y >> (32 - p);                    // odd
 }
 
-// Number of ancestors of boundary t: its left records (chain of nearest
-// smaller boundaries to the left) plus its right records.
-__device__ uint32_t depth_of(const uint32_t* na, const uint32_t* nb, uint32_t t, uint32_t R)
+// The merge Algorithm 1 makes at boundary t: the runs whose midpoints lie in
+// [(c-1)/2^p, (c+1)/2^p), found by galloping out from t.
+template <typename RS>
+__device__ NodeRange node_range(RS rs, uint32_t R, uint32_t n, uint32_t t)
 {
-    uint32_t d = 0, u = t;
-    while (na[u] >= 1) { u = na[u]; ++d; }
-    u = t;
-    while (nb[u] <= R - 1) { u = nb[u]; ++d; }
-    return d;
+    NodeRange r;
+    power_of(rs, n, t, r.p, r.c);
+    const unsigned long long XL = (unsigned long long)(r.c - 1) << (32 - r.p);
+    const unsigned long long XR = (unsigned long long)(r.c + 1) << (32 - r.p);
+    auto ge = [&](long long x, unsigned long long X) { return kappa_ge(rs(x), rs(x + 1), n, X); };
+    // first run with midpoint >= XL (run t-1 qualifies): gallop left
+    long long j = (long long)t - 1, bad = -1, step = 1;
+    for (;;) {
+        const long long q = j - step;
+        if (q < 0) { bad = -1; break; }
+        if (!ge(q, XL)) { bad = q; break; }
+        j = q;
+        step <<= 1;
+    }
+    long long lo = bad + 1, hi = j;
+    while (lo < hi) {
+        const long long mid = (lo + hi) >> 1;
+        if (ge(mid, XL)) hi = mid; else lo = mid + 1;
+    }
+    r.a = (uint32_t)lo;
+    // first run after t with midpoint >= XR (run t does not qualify), or R
+    j = t;
+    long long good = R;
+    step = 1;
+    for (;;) {
+        const long long q = j + step;
+        if (q > (long long)R - 1) { good = R; break; }
+        if (ge(q, XR)) { good = q; break; }
+        j = q;
+        step <<= 1;
+    }
+    lo = j + 1;
+    hi = good;
+    while (lo < hi) {
+        const long long mid = (lo + hi) >> 1;
+        if (ge(mid, XR)) hi = mid; else lo = mid + 1;
+    }
+    r.b = (uint32_t)lo;
+    return r;
 }
 
 }  // namespace
 
-// kappa of every run: the run midpoint in 32-digit fixed point.
-__global__ void __launch_bounds__(PLAN_BLOCK) k_kappa(Job J)
-{
-    if (*(volatile uint32_t*)&J.ctr->error) return;
-    const unsigned long long total = J.ctr->total_slots;
-    for (unsigned long long slot = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; slot < total;
-         slot += (unsigned long long)gridDim.x * blockDim.x) {
-        const uint32_t q = inst_of_slot(J, slot);
-        const Inst& I = J.inst[q];
-        const unsigned long long s = slot - I.run_base;
-        if (s >= I.runs) continue;
-        const uint32_t* rs = J.run_start + I.run_base;
-        const unsigned long long twice_mid = (unsigned long long)rs[s] + rs[s + 1];
-        J.kappa[slot] = (uint32_t)((twice_mid << 31) / I.n);
-    }
-}
-
-// Power and node range [na, nb) (run indices) of every boundary; merge cost.
+// Power of every boundary, the merge cost, and the schedule's lists: every
+// HBM merge (more than T elements) with its parent's merge-map index, and
+// every tile (a child of an HBM merge that has at most T elements or is a
+// single run, or the whole instance when it has at most T elements or is a
+// single run).
 __global__ void __launch_bounds__(PLAN_BLOCK) k_nodes(Job J)
 {
-    // kappa of the block's slots and NODE_HALO slots on each side, staged in
-    // shared memory: the probes of every node no wider than the halo stay on
-    // chip, and only wide nodes (small powers, few of them) go to L2
-    __shared__ uint32_t kw[NODE_WIN];
+    // run starts of the block's slots and NODE_HALO slots on each side,
+    // staged in shared memory: the probes of every node no wider than the
+    // halo stay on chip, and only wide nodes (small powers, few of them) go
+    // to L2
+    __shared__ uint32_t rw[NODE_WIN];
     __shared__ uint32_t s_err;
     if (threadIdx.x == 0) s_err = *(volatile uint32_t*)&J.ctr->error;
     __syncthreads();
     if (s_err) return;                                       // the whole block leaves together
     const unsigned long long total = J.ctr->total_slots;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    const uint32_t T = J.tile_cap;
     for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < total; base += stride) {
-        const long long w0 = (long long)base - NODE_HALO;   // global slot of kw[0]
+        const long long w0 = (long long)base - NODE_HALO;   // global slot of rw[0]
         __syncthreads();                                     // the previous pass's probes are done
         for (int i = threadIdx.x; i < NODE_WIN; i += PLAN_BLOCK) {
             const long long g = w0 + i;
-            if (g >= 0 && g < (long long)total) kw[i] = J.kappa[g];
+            if (g >= 0 && g < (long long)total) rw[i] = J.run_start[g];
         }
         __syncthreads();
         const unsigned long long slot = base + threadIdx.x;
         unsigned long long cost = 0;
         uint32_t q = NONE, p = 0;
+        bool want_g = false, want_l = false, want_r = false, want_root = false;
+        GNode gn = {};
         if (slot < total) {
             q = inst_of_slot(J, slot);
             const Inst& I = J.inst[q];
             const unsigned long long t64 = slot - I.run_base;
-            const uint32_t R = I.runs;
+            const uint32_t R = I.runs, n = I.n;
+            const uint32_t* rs_g = J.run_start + I.run_base;
+            const long long off = (long long)I.run_base - w0;
+            // start of run x of this instance (0 <= x <= R: a staged slot when
+            // it falls in the window, else a load)
+            auto rs = [&](long long x) -> uint32_t {
+                const long long w = off + x;
+                return (w >= 0 && w < NODE_WIN) ? rw[w] : rs_g[x];
+            };
             if (t64 >= 1 && t64 + 1 <= R) {
                 const uint32_t t = (uint32_t)t64;
-                const uint32_t* kap_g = J.kappa + I.run_base;
-                const long long off = (long long)I.run_base - w0;
-                // kappa of run x of this instance (0 <= x < R: a staged slot
-                // when it falls in the window, else a load)
-                auto kap = [&](long long x) -> uint32_t {
-                    const long long w = off + x;
-                    return (w >= 0 && w < NODE_WIN) ? kw[w] : kap_g[x];
-                };
-                const uint32_t* rs = J.run_start + I.run_base;
-                const uint32_t X = kap(t - 1), Y = kap(t);
-                p = __clz(X ^ Y) + 1;                      // 1..32
-                const uint32_t c = Y >> (32 - p);          // odd: the dyadic point is c / 2^p
-                const unsigned long long XL = (unsigned long long)(c - 1) << (32 - p);
-                const unsigned long long XR = (unsigned long long)(c + 1) << (32 - p);
-                // first run with kappa >= XL (run t-1 qualifies): gallop left
-                long long j = (long long)t - 1, bad = -1, step = 1;
-                for (;;) {
-                    const long long qq = j - step;
-                    if (qq < 0) { bad = -1; break; }
-                    if (kap(qq) < XL) { bad = qq; break; }
-                    j = qq;
-                    step <<= 1;
-                }
-                long long lo = bad + 1, hi = j;
-                while (lo < hi) {
-                    const long long mid = (lo + hi) >> 1;
-                    if (kap(mid) >= XL) hi = mid; else lo = mid + 1;
-                }
-                const uint32_t a = (uint32_t)lo;
-                // first run with kappa >= XR after t (run t does not qualify), or R
-                j = t;
-                long long good = R;
-                step = 1;
-                for (;;) {
-                    const long long qq = j + step;
-                    if (qq > (long long)R - 1) { good = R; break; }
-                    if (kap(qq) >= XR) { good = qq; break; }
-                    j = qq;
-                    step <<= 1;
-                }
-                lo = j + 1;
-                hi = good;
-                while (lo < hi) {
-                    const long long mid = (lo + hi) >> 1;
-                    if (kap(mid) >= XR) hi = mid; else lo = mid + 1;
-                }
-                const uint32_t b = (uint32_t)lo;
+                const NodeRange nr = node_range(rs, R, n, t);
+                p = nr.p;
                 J.power[slot] = (uint8_t)p;
-                J.na[slot] = a;
-                J.nb[slot] = b;
-                cost = (unsigned long long)(rs[b] - rs[a]);
+                const uint32_t lo = rs(nr.a), mid = rs(t), hi = rs(nr.b);
+                cost = (unsigned long long)(hi - lo);
+                if (hi - lo > T) {
+                    // an HBM merge; its parent is the one of the two boundaries
+                    // around it with the larger power (both have smaller powers)
+                    want_g = true;
+                    // a child is a tile when it has at most T elements or is a
+                    // single run (a leaf, whatever its length); otherwise it is
+                    // an HBM merge, listed by its own boundary
+                    want_l = mid - lo <= T || t - nr.a == 1;
+                    want_r = hi - mid <= T || nr.b - t == 1;
+                    uint32_t pa = 0, pb = 0, ca = 0, cb = 0;
+                    if (nr.a >= 1) power_of(rs, n, nr.a, pa, ca);
+                    if (nr.b + 1 <= R) power_of(rs, n, nr.b, pb, cb);
+                    uint32_t pidx = NONE;
+                    if (pa || pb) pidx = pa > pb ? merge_index(pa, ca) : merge_index(pb, cb);
+                    const uint32_t midx = merge_index(p, nr.c);
+                    if (midx >= I.g_span || (pidx != NONE && pidx >= I.g_span)) {
+                        set_error(J.ctr, DERR_INTERNAL, 23);   // a merge larger than its power allows
+                        want_g = want_l = want_r = false;
+                    }
+                    gn = GNode{q, t, nr.a, nr.b, p, 0u, midx, pidx};
+                }
+            } else if (t64 == 0 && R >= 1 && (R == 1 || n <= T)) {
+                want_root = true;                      // the whole instance is one tile
             }
+        }
+        const uint32_t g = warp_append(&J.ctr->n_gnodes, want_g);
+        if (want_g) {
+            if (g < J.gnode_cap) {
+                J.gnodes[g] = gn;
+                J.gmap[J.inst[q].g_base + gn.midx] = g;
+            } else {
+                set_error(J.ctr, DERR_INTERNAL, 22);
+            }
+        }
+        uint32_t at = warp_append(&J.ctr->n_tiles, want_l);
+        if (want_l) {
+            if (at < J.tile_cap_items) J.tiles[at] = TileItem{q, gn.a, gn.t, g, 0u, 0u};
+            else set_error(J.ctr, DERR_INTERNAL, 20);
+        }
+        at = warp_append(&J.ctr->n_tiles, want_r);
+        if (want_r) {
+            if (at < J.tile_cap_items) J.tiles[at] = TileItem{q, gn.t, gn.b, g, 0u, 0u};
+            else set_error(J.ctr, DERR_INTERNAL, 21);
+        }
+        at = warp_append(&J.ctr->n_tiles, want_root);
+        if (want_root) {
+            if (at < J.tile_cap_items) J.tiles[at] = TileItem{q, 0u, J.inst[q].runs, NONE, 0u, 0u};
+            else set_error(J.ctr, DERR_INTERNAL, 24);
         }
         // merge cost and largest power, per instance (warp-aggregated when
         // the whole warp works on one instance)
@@ -223,98 +266,33 @@ __global__ void __launch_bounds__(PLAN_BLOCK) k_nodes(Job J)
     }
 }
 
-// Tiles (subtrees of at most T elements whose parent is larger, and runs whose
-// parent is larger) and HBM nodes (merges of more than T elements).
-__global__ void __launch_bounds__(PLAN_BLOCK) k_classify(Job J)
-{
-    if (*(volatile uint32_t*)&J.ctr->error) return;
-    const unsigned long long total = J.ctr->total_slots;
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    const uint32_t T = J.tile_cap;
-    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < total; base += stride) {
-        const unsigned long long slot = base + threadIdx.x;
-        bool want_node_tile = false, want_leaf_tile = false, want_g = false;
-        uint32_t q = 0, s = 0, r0 = 0, r1 = 0;
-        if (slot < total) {
-            q = inst_of_slot(J, slot);
-            const Inst& I = J.inst[q];
-            const unsigned long long s64 = slot - I.run_base;
-            const uint32_t R = I.runs;
-            if (s64 < R) {
-                s = (uint32_t)s64;
-                const uint32_t* rs = J.run_start + I.run_base;
-                const uint8_t* pw = J.power + I.run_base;
-                const uint32_t* na = J.na + I.run_base;
-                const uint32_t* nb = J.nb + I.run_base;
-                if (s >= 1) {                         // boundary s
-                    const uint32_t size = node_size(rs, na, nb, s);
-                    if (size > T) {
-                        want_g = true;
-                    } else {
-                        const uint32_t par = parent_of(pw, na, nb, s, R);
-                        if (par == NONE || node_size(rs, na, nb, par) > T) {
-                            want_node_tile = true;
-                            r0 = na[s];
-                            r1 = nb[s];
-                        }
-                    }
-                }
-                const uint32_t lp = leaf_parent(pw, s, R);   // leaf s
-                if (lp == NONE || node_size(rs, na, nb, lp) > T) want_leaf_tile = true;
-            }
-        }
-        uint32_t at = warp_append(&J.ctr->n_tiles, want_node_tile);
-        if (want_node_tile) {
-            if (at < J.entry_cap) J.tiles[at] = TileItem{q, r0, r1, s, 0u, 0u};
-            else set_error(J.ctr, DERR_INTERNAL, 20);
-        }
-        at = warp_append(&J.ctr->n_tiles, want_leaf_tile);
-        if (want_leaf_tile) {
-            if (at < J.entry_cap) J.tiles[at] = TileItem{q, s, s + 1, NONE, 0u, 0u};
-            else set_error(J.ctr, DERR_INTERNAL, 21);
-        }
-        at = warp_append(&J.ctr->n_gnodes, want_g);
-        if (want_g) {
-            if (at < J.entry_cap) J.gnodes[at] = GNode{q, s, 0u, J.power[slot]};
-            else set_error(J.ctr, DERR_INTERNAL, 22);
-        }
-    }
-}
-
-// Depth (number of ancestors) of every tile root and HBM node; HBM nodes are
-// counted per round (round r holds power 32 - r, so larger powers go first).
+// Depth (number of ancestors) of every HBM merge, by walking the parent
+// links through the merge map (an HBM merge's parent is an HBM merge);
+// merges are counted per round (round r holds power 32 - r, so larger powers
+// go first).
 __global__ void __launch_bounds__(PLAN_BLOCK) k_depth(Job J)
 {
     if (*(volatile uint32_t*)&J.ctr->error) return;
-    const uint32_t nt = min(J.ctr->n_tiles, J.entry_cap);
-    const uint32_t ng = min(J.ctr->n_gnodes, J.entry_cap);
-    const uint32_t total = nt + ng;
-    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
-        if (e < nt) {
-            TileItem it = J.tiles[e];
-            const Inst& I = J.inst[it.inst];
-            const uint32_t R = I.runs;
-            const uint32_t* na = J.na + I.run_base;
-            const uint32_t* nb = J.nb + I.run_base;
-            uint32_t d;
-            if (it.t != NONE) {
-                d = depth_of(na, nb, it.t, R);
-            } else {
-                const uint32_t lp = leaf_parent(J.power + I.run_base, it.r0, R);
-                d = lp == NONE ? 0u : depth_of(na, nb, lp, R) + 1u;
+    const uint32_t ng = min(J.ctr->n_gnodes, J.gnode_cap);
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+        const GNode gn = J.gnodes[g];
+        const Inst& I = J.inst[gn.inst];
+        const uint32_t* gm = J.gmap + I.g_base;
+        uint32_t d = 0, up = gn.pidx;
+        while (up != NONE) {
+            const uint32_t h = gm[up];
+            if (h >= ng || d > NPOW) {
+                set_error(J.ctr, DERR_INTERNAL, 25);
+                break;
             }
-            J.tiles[e].depth = d;
-        } else {
-            const uint32_t g = e - nt;
-            GNode gn = J.gnodes[g];
-            const Inst& I = J.inst[gn.inst];
-            const uint32_t* na = J.na + I.run_base;
-            const uint32_t* nb = J.nb + I.run_base;
-            J.gnodes[g].depth = depth_of(na, nb, gn.t, I.runs);
-            const uint32_t size = node_size(J.run_start + I.run_base, na, nb, gn.t);
-            atomicAdd(&J.ctr->bucket_count[32 - gn.power], 1u);
-            atomicAdd(&J.ctr->bucket_nchunk[32 - gn.power], (size + J.merge_e - 1) / J.merge_e);
+            ++d;
+            up = J.gnodes[h].pidx;
         }
+        J.gnodes[g].depth = d;
+        const uint32_t* rs = J.run_start + I.run_base;
+        const uint32_t size = rs[gn.b] - rs[gn.a];
+        atomicAdd(&J.ctr->bucket_count[32 - gn.power], 1u);
+        atomicAdd(&J.ctr->bucket_nchunk[32 - gn.power], (size + J.merge_e - 1) / J.merge_e);
     }
 }
 
@@ -336,18 +314,19 @@ __global__ void __launch_bounds__(32) k_bucket_scan(Job J)
     C->bucket_start[NPOW] = acc;
     C->bucket_chunk[NPOW] = chunks;
     C->rounds = rounds;
-    if (chunks > J.chunk_node_cap) set_error(C, DERR_INTERNAL, 31);
+    if (!J.vm && chunks > J.chunk_node_cap) set_error(C, DERR_INTERNAL, 31);
 }
 
 // Every HBM merge takes the next place of its round with one 64-bit atomic
 // that advances the round's merge count and chunk count together, so within
 // a round the chunk bases grow with the merge order (the chunk -> merge
-// table below relies on it).
+// table below relies on it); its merge-map entry becomes its GSorted index.
+// Every tile takes the depth below its parent merge.
 __global__ void __launch_bounds__(PLAN_BLOCK) k_bucket(Job J)
 {
     Ctr* C = J.ctr;
     if (*(volatile uint32_t*)&C->error) return;
-    const uint32_t ng = min(C->n_gnodes, J.entry_cap);
+    const uint32_t ng = min(C->n_gnodes, J.gnode_cap);
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t base = blockIdx.x * blockDim.x; base < ng; base += stride) {
         const uint32_t e = base + threadIdx.x;
@@ -356,9 +335,7 @@ __global__ void __launch_bounds__(PLAN_BLOCK) k_bucket(Job J)
             const GNode gn = J.gnodes[e];
             const Inst& I = J.inst[gn.inst];
             const uint32_t* rs = J.run_start + I.run_base;
-            const uint32_t lo = rs[J.na[I.run_base + gn.t]];
-            const uint32_t mid = rs[gn.t];
-            const uint32_t hi = rs[J.nb[I.run_base + gn.t]];
+            const uint32_t lo = rs[gn.a], mid = rs[gn.t], hi = rs[gn.b];
             const uint32_t r = 32 - gn.power;
             const uint32_t nch = (hi - lo + J.merge_e - 1) / J.merge_e;
             const unsigned long long old = atomicAdd(&C->bucket_cursor[r], (1ull << 40) | nch);
@@ -374,7 +351,7 @@ __global__ void __launch_bounds__(PLAN_BLOCK) k_bucket(Job J)
             if (at < C->bucket_start[r + 1]) {
                 J.gsorted[at] = o;
                 J.dep[at] = 0;
-                J.gidx[I.run_base + gn.t] = at;
+                J.gmap[I.g_base + gn.midx] = at;
             } else {
                 set_error(C, DERR_INTERNAL, 32);
             }
@@ -384,26 +361,30 @@ __global__ void __launch_bounds__(PLAN_BLOCK) k_bucket(Job J)
         for (int o = 16; o > 0; o >>= 1) size += __shfl_xor_sync(FULL, size, o);
         if ((threadIdx.x & 31) == 0 && size) atomicAdd(&C->hbm_elems, size);
     }
+    const uint32_t nt = min(C->n_tiles, J.tile_cap_items);
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < nt; e += stride) {
+        const uint32_t par = J.tiles[e].parent;
+        J.tiles[e].depth = par == NONE ? 0u : (par < ng ? J.gnodes[par].depth + 1u : 0u);
+    }
 }
 
 // Chunk -> merge table for every round (chunk ids are global across rounds):
 // each thread covers 32 consecutive chunks with one binary search and a walk.
-// Then every HBM merge is linked to its parent merge (which is larger, hence
-// an HBM merge too) and adds its chunk count to the parent's dependencies.
+// Then every HBM merge is linked to its parent merge and adds its chunk
+// count to the parent's dependencies.  (VM storage runs its rounds with grid
+// barriers and needs neither.)
 __global__ void __launch_bounds__(PLAN_BLOCK) k_chunk_nodes(Job J)
 {
-    if (*(volatile uint32_t*)&J.ctr->error) return;
+    if (J.vm || *(volatile uint32_t*)&J.ctr->error) return;
     const Ctr* C = J.ctr;
-    const uint32_t ng = min(C->n_gnodes, J.entry_cap);
+    const uint32_t ng = min(C->n_gnodes, J.gnode_cap);
     const uint32_t total = C->bucket_chunk[NPOW];
     if (ng == 0 || total > J.chunk_node_cap) return;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < ng; i += gridDim.x * blockDim.x) {
         const GNode gn = J.gnodes[i];
-        const Inst& I = J.inst[gn.inst];
-        const uint32_t me = J.gidx[I.run_base + gn.t];
-        const uint32_t p = parent_of(J.power + I.run_base, J.na + I.run_base, J.nb + I.run_base, gn.t, I.runs);
-        if (p == NONE) continue;                 // the instance's root
-        const uint32_t par = J.gidx[I.run_base + p];
+        if (gn.pidx == NONE) continue;           // the instance's root
+        const uint32_t* gm = J.gmap + J.inst[gn.inst].g_base;
+        const uint32_t me = gm[gn.midx], par = gm[gn.pidx];
         if (me >= ng || par >= ng) {
             set_error(J.ctr, DERR_INTERNAL, 33);
             continue;
@@ -429,6 +410,21 @@ __global__ void __launch_bounds__(PLAN_BLOCK) k_chunk_nodes(Job J)
             }
             J.chunk_node[c] = e;
         }
+    }
+}
+
+// Introspection: the element range [lo, hi) of the merge at every boundary of
+// instance q (the same node_range as k_nodes), two words per boundary.
+__global__ void __launch_bounds__(PLAN_BLOCK) k_node_ranges(Job J, uint32_t q, uint32_t* out)
+{
+    const Inst& I = J.inst[q];
+    const uint32_t R = I.runs, n = I.n;
+    const uint32_t* rs_g = J.run_start + I.run_base;
+    auto rs = [&](long long x) -> uint32_t { return rs_g[x]; };
+    for (uint32_t t = 1 + blockIdx.x * blockDim.x + threadIdx.x; t < R; t += gridDim.x * blockDim.x) {
+        const NodeRange nr = node_range(rs, R, n, t);
+        out[2 * (t - 1)] = rs_g[nr.a];
+        out[2 * (t - 1) + 1] = rs_g[nr.b];
     }
 }
 
@@ -469,13 +465,18 @@ cudaError_t launch_finish(const Job& J, cudaStream_t s)
 
 cudaError_t launch_plan(const Job& J, int grid, cudaStream_t s)
 {
-    k_kappa<<<grid, PLAN_BLOCK, 0, s>>>(J);
     k_nodes<<<grid, PLAN_BLOCK, 0, s>>>(J);
-    k_classify<<<grid, PLAN_BLOCK, 0, s>>>(J);
     k_depth<<<grid, PLAN_BLOCK, 0, s>>>(J);
     k_bucket_scan<<<1, 32, 0, s>>>(J);
     k_bucket<<<grid, PLAN_BLOCK, 0, s>>>(J);
     k_chunk_nodes<<<grid, PLAN_BLOCK, 0, s>>>(J);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_node_ranges(const Job& J, uint32_t q, uint32_t nbound, uint32_t* out, cudaStream_t s)
+{
+    const int grid = (int)((nbound + PLAN_BLOCK - 1) / PLAN_BLOCK);
+    if (grid > 0) k_node_ranges<<<grid < 4096 ? grid : 4096, PLAN_BLOCK, 0, s>>>(J, q, out);
     return cudaGetLastError();
 }
 

@@ -95,12 +95,13 @@ __global__ void __launch_bounds__(1024) k_setup(Job J)
     __shared__ unsigned long long ws64[32];
     __shared__ uint32_t ws32[32];
     __shared__ unsigned long long carry_slots;
-    __shared__ uint32_t carry_chunks;
+    __shared__ uint32_t carry_chunks, carry_gmap;
     Ctr* C = J.ctr;
     __shared__ uint32_t s_bad;
     if (threadIdx.x == 0) {
         carry_slots = 0;
         carry_chunks = 0;
+        carry_gmap = 0;
         s_bad = 0;
         C->error = 0;
         C->err_where = 0;
@@ -155,10 +156,14 @@ __global__ void __launch_bounds__(1024) k_setup(Job J)
         const uint32_t n = (uint32_t)n64;
         const uint32_t nchunks = (valid && n >= 64) ? (n + RUN_CHUNK - 1) / RUN_CHUNK : 0u;
         const unsigned long long cap = valid ? (unsigned long long)(n / 32) + 2ull : 0ull;
-        uint32_t tot_c;
+        // merge-map entries: an HBM merge (more than T elements) has an index
+        // below 4n / T (merge_index)
+        const uint32_t gspan = (valid && n > J.tile_cap) ? (uint32_t)((4ull * n + J.tile_cap - 1) / J.tile_cap) : 0u;
+        uint32_t tot_c, tot_g;
         unsigned long long tot_s;
         const uint32_t cb = block_exclusive_scan<uint32_t>(nchunks, ws32, tot_c);
         const unsigned long long sb = block_exclusive_scan<unsigned long long>(cap, ws64, tot_s);
+        const uint32_t gb = block_exclusive_scan<uint32_t>(gspan, ws32, tot_g);
         if (valid) {
             Inst I;
             I.off = off;
@@ -169,6 +174,8 @@ __global__ void __launch_bounds__(1024) k_setup(Job J)
             I.chunk_base = carry_chunks + cb;
             I.nchunks = nchunks;
             I.max_power = 0;
+            I.g_base = carry_gmap + gb;
+            I.g_span = gspan;
             I.runs = n == 0 ? 0u : (n < 64 ? 1u : 0u);
             J.inst[i] = I;
             if (n < 64 && I.run_base + 1 < J.slot_cap) {   // one run [0, n) (or none)
@@ -180,6 +187,7 @@ __global__ void __launch_bounds__(1024) k_setup(Job J)
         if (threadIdx.x == 0) {
             carry_chunks += tot_c;
             carry_slots += tot_s;
+            carry_gmap += tot_g;
         }
         __syncthreads();
     }
@@ -210,7 +218,8 @@ __global__ void __launch_bounds__(1024) k_setup(Job J)
         C->total_chunks = carry_chunks;
         C->total_slots = carry_slots;
         if (s_bad) set_error(C, DERR_INVAL, 2);
-        else if (carry_chunks > J.chunk_cap || carry_slots > J.slot_cap) set_error(C, DERR_INTERNAL, 1);
+        else if (carry_chunks > J.chunk_cap || carry_slots > J.slot_cap || carry_gmap > J.gmap_cap)
+            set_error(C, DERR_INTERNAL, 1);
     }
 }
 
@@ -536,8 +545,6 @@ __global__ void __launch_bounds__(RUN_BLOCK) k_runs(Job J)
             J.chunk_info[g] = (walk ? 0u : CHUNK_FORCED) | (first ? CHUNK_FIRST : 0u) | (uint32_t)min(d0, 0xffff);
             if (first) s_reset = RANGE_RESET;
         }
-        if (walk)   // k_runs_emit walks one chain of this chunk over the same bitmask
-            for (int x = tid; x < RUN_WORDS; x += RUN_BLOCK) J.chunk_bits[(size_t)g * RUN_WORDS + x] = bits[x];
         __syncthreads();
         if (tid < MAP_STATES) {
             mapv[tid] = f;
@@ -618,11 +625,17 @@ __global__ void __launch_bounds__(RUN_BLOCK) k_runs(Job J)
 }
 
 // Pass 2: every CTA walks its range's chunk maps from the range entry and
-// writes the run starts of each chunk.
+// writes the run starts of each chunk: a warp per chunk in closed form when
+// every step in it is forced; otherwise the whole CTA rebuilds the chunk's
+// descent bitmask (from the keys, as pass 1 did, or from the record mask)
+// and one thread walks the one chain the chunk takes.  Rebuilding reads the
+// chunk's keys a second time instead of keeping every bitmask between the
+// passes (RUN_WORDS words per chunk, an eighth of the keys' size).
 __global__ void __launch_bounds__(RUN_BLOCK) k_runs_emit(Job J)
 {
     constexpr int NW = RUN_BLOCK / 32;
-    __shared__ uint32_t bits[NW][RUN_WORDS];     // one descent bitmask per warp
+    __shared__ __align__(16) uint32_t keys[WIN_SLOTS];   // one chunk's key window
+    __shared__ uint32_t bits[RUN_WORDS];
     __shared__ uint32_t win[WIN][MAP_STATES];
     __shared__ unsigned long long entry[WIN];    // runs before the chunk << 8 | its entry state
 
@@ -633,7 +646,25 @@ __global__ void __launch_bounds__(RUN_BLOCK) k_runs_emit(Job J)
     const uint32_t K = (T + G - 1) / G;
     const uint32_t g0 = min(blockIdx.x * K, T), g1 = min(g0 + K, T);
     unsigned long long at = J.range_entry[blockIdx.x];
+    const bool desc = J.desc_runs != 0;
 
+    // the run starts of chunk g, from its map entry: count checks, and the
+    // instance's end after its last chunk
+    auto finish_chunk = [&](const ChunkView& v, uint32_t me, unsigned long long prefix, uint32_t cnt) {
+        const Inst& I = J.inst[v.qi];
+        const unsigned long long cap = (unsigned long long)(v.n / 32) + 2;
+        if (v.c + 1 == I.nchunks) {
+            const unsigned long long R = prefix + cnt;
+            if ((me & 0xffu) != STATE_END || R + 1 > cap) {
+                set_error(C, DERR_INTERNAL, 12);
+            } else {
+                J.run_start[I.run_base + R] = v.n;
+                J.inst[v.qi].runs = (uint32_t)R;
+            }
+        }
+    };
+
+    uint32_t qb = NONE;                          // the block's instance cursor (walked chunks)
     for (uint32_t b0 = g0; b0 < g1; b0 += WIN) {
         const uint32_t nb = min((uint32_t)WIN, g1 - b0);
         for (uint32_t i = tid; i < nb * MAP_STATES; i += RUN_BLOCK)
@@ -648,13 +679,14 @@ __global__ void __launch_bounds__(RUN_BLOCK) k_runs_emit(Job J)
             }
         }
         __syncthreads();
-        // one warp per chunk
+        // forced-only chunks: one warp per chunk, in closed form
         uint32_t qi = NONE;
         for (uint32_t i = warp; i < nb; i += NW) {
             const uint32_t g = b0 + i;
+            const uint32_t info = J.chunk_info[g];
+            if (!(info & CHUNK_FORCED)) continue;
             const ChunkView v = chunk_view(J, g, qi);
             const Inst& I = J.inst[v.qi];
-            const uint32_t info = J.chunk_info[g];
             const uint32_t st = (uint32_t)(entry[i] & 0xffu);
             const unsigned long long prefix = entry[i] >> 8;
             const uint32_t me = win[i][st < (uint32_t)MAP_STATES ? st : 0u];
@@ -663,41 +695,55 @@ __global__ void __launch_bounds__(RUN_BLOCK) k_runs_emit(Job J)
             const unsigned long long cap = (unsigned long long)(v.n / 32) + 2;
             if (st > v.m || prefix + cnt + 1 > cap || cnt > (uint32_t)RUN_REC) {
                 if (lane == 0) set_error(C, DERR_INTERNAL, 13);
-            } else if (info & CHUNK_FORCED) {
-                // forced steps only: starts k0, k0 + m, ... (k0: the entry offset or D0 / X0)
-                const uint32_t d0 = info & 0xffffu;
-                const uint32_t k0 = st < v.m ? st : d0;
-                for (uint32_t x = lane; x < cnt; x += 32) rs[x] = v.B + k0 + x * v.m;
+                continue;
+            }
+            // starts k0, k0 + m, ... (k0: the entry offset or D0 / X0)
+            const uint32_t d0 = info & 0xffffu;
+            const uint32_t k0 = st < v.m ? st : d0;
+            for (uint32_t x = lane; x < cnt; x += 32) rs[x] = v.B + k0 + x * v.m;
+            if (lane == 0) finish_chunk(v, me, prefix, cnt);
+        }
+        // chunks with a natural step: the whole block, one chunk at a time
+        for (uint32_t i = 0; i < nb; ++i) {
+            const uint32_t g = b0 + i;
+            if (J.chunk_info[g] & CHUNK_FORCED) continue;   // the same for every thread
+            const ChunkView v = chunk_view(J, g, qb);
+            if (J.desc_mask) {
+                bits_from_mask(v, J.desc_mask, bits);
             } else {
-                // the one chain this chunk takes, over the bitmask pass 1 kept
-                const uint32_t* gb = J.chunk_bits + (size_t)g * RUN_WORDS;
-                for (int x = lane; x < RUN_WORDS; x += 32) bits[warp][x] = gb[x];
-                __syncwarp();
-                if (lane == 0) {
+                const KeyWindow w = window_of(v);
+                stage_keys(v, w, keys);
+                cp_async_wait<0>();
+                __syncthreads();
+                bits_from_keys(v, w, keys, bits);
+            }
+            __syncthreads();
+            if (tid == 0) {
+                const Inst& I = J.inst[v.qi];
+                const uint32_t st = (uint32_t)(entry[i] & 0xffu);
+                const unsigned long long prefix = entry[i] >> 8;
+                const uint32_t me = win[i][st < (uint32_t)MAP_STATES ? st : 0u];
+                const uint32_t cnt = (me & RANGE_COUNT_MASK) >> 8;
+                uint32_t* rs = J.run_start + I.run_base + prefix;
+                const unsigned long long cap = (unsigned long long)(v.n / 32) + 2;
+                if (st > v.m || prefix + cnt + 1 > cap || cnt > (uint32_t)RUN_REC) {
+                    set_error(C, DERR_INTERNAL, 13);
+                } else {
                     uint32_t c2 = 0;
-                    const bool desc = J.desc_runs != 0;
-                    int k = entry_offset(v, bits[warp], st, desc);
+                    int k = entry_offset(v, bits, st, desc);
                     if (k >= 0) {
                         while ((uint32_t)k < v.span && c2 < cnt) {
                             rs[c2++] = v.B + (uint32_t)k;
-                            const int d = natural_end(v, bits[warp], k, desc);
+                            const int d = natural_end(v, bits, k, desc);
                             if (d >= KMAX) break;
                             k = max(d, (int)min((uint32_t)k + v.m, v.rem));
                         }
                     }
                     if (c2 != cnt) set_error(C, DERR_INTERNAL, 14);
-                }
-                __syncwarp();
-            }
-            if (v.c + 1 == I.nchunks && lane == 0) {
-                const unsigned long long R = prefix + cnt;
-                if ((me & 0xffu) != STATE_END || R + 1 > cap) {
-                    set_error(C, DERR_INTERNAL, 12);
-                } else {
-                    J.run_start[I.run_base + R] = v.n;
-                    J.inst[v.qi].runs = (uint32_t)R;
+                    finish_chunk(v, me, prefix, cnt);
                 }
             }
+            __syncthreads();                     // the window and bitmask are free again
         }
         __syncthreads();
     }

@@ -9,7 +9,13 @@
 // ps_run_batched over the batch and the device->host copies of the sorted
 // keys and permutations, and records an event.  Lanes run concurrently, so a
 // request arriving while other batches are on the GPU is admitted as soon as
-// a lane frees up, and its work overlaps theirs.  A ticket completes when its
+// a lane frees up, and its work overlaps theirs: one batch's host->device
+// copies and another's device->host copies run on the copy engines while a
+// third batch computes.  The batches' kernels themselves run one batch after
+// the other, in dispatch order (each batch's sort waits for the previous
+// batch's sort): a batch's kernels fill the GPU, and a small batch whose
+// dependent kernels interleaved with a large batch's would wait behind one
+// of its long kernels at almost every step.  A ticket completes when its
 // lane's event has fired; its latency is measured from submission.
 #include <chrono>
 #include <condition_variable>
@@ -47,6 +53,7 @@ struct Lane {
     uint64_t* doff = nullptr;
     uint64_t* hoff = nullptr;       // pinned
     cudaEvent_t done = nullptr;
+    cudaEvent_t computed = nullptr; // the batch's sort has finished (its copies out may still run)
     std::vector<uint64_t> batch;    // tickets in flight
     std::vector<Req> jobs;          // their arrays, copied under the lock
     bool busy = false;
@@ -73,6 +80,7 @@ struct ps_server {
     uint64_t bytes = 0;
     uint64_t completed = 0, elements = 0, batches = 0, failed = 0;
     uint32_t max_in_flight_lanes = 0;
+    cudaEvent_t last_computed = nullptr;   // the sort of the batch dispatched last (dispatcher only)
 };
 
 namespace {
@@ -85,6 +93,7 @@ void lane_free(Lane& L)
     if (L.doff) cudaFree(L.doff);
     if (L.hoff) cudaFreeHost(L.hoff);
     if (L.done) cudaEventDestroy(L.done);
+    if (L.computed) cudaEventDestroy(L.computed);
     if (L.stream) cudaStreamDestroy(L.stream);
     L = Lane{};
 }
@@ -106,8 +115,12 @@ ps_status launch_batch(ps_server* S, Lane& L)
         if (r.n && cudaMemcpyAsync(L.dkeys + L.hoff[i], r.in, r.n * 4, cudaMemcpyHostToDevice, L.stream) != cudaSuccess)
             return PS_ECUDA;
     }
+    // the sort starts after the previous batch's sort (copies in are not held back)
+    if (S->last_computed && cudaStreamWaitEvent(L.stream, S->last_computed, 0) != cudaSuccess) return PS_ECUDA;
     const ps_status st = ps_run_batched(L.ctx, L.dkeys, S->cfg.want_perm ? L.dperm : nullptr, L.doff, (uint32_t)k, nullptr);
     if (st != PS_OK) return st;
+    if (cudaEventRecord(L.computed, L.stream) != cudaSuccess) return PS_ECUDA;
+    S->last_computed = L.computed;
     for (size_t i = 0; i < k; ++i) {
         const Req& r = L.jobs[i];
         if (!r.n) continue;
@@ -243,7 +256,8 @@ PS_API ps_status ps_server_create(const ps_server_config* cfg, ps_server** out)
     S->lanes.resize(S->cfg.lanes);
     for (Lane& L : S->lanes) {
         if (cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) != cudaSuccess) {
+            cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&L.computed, cudaEventDisableTiming) != cudaSuccess) {
             st = PS_ECUDA;
             break;
         }

@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(TILE_BLOCK) k_tiles(Job J)
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (*(volatile uint32_t*)&J.ctr->error) return;
-    const uint32_t ntiles = min(J.ctr->n_tiles, J.entry_cap);
+    const uint32_t ntiles = min(J.ctr->n_tiles, J.tile_cap_items);
 
     for (uint32_t e = blockIdx.x; e < ntiles; e += gridDim.x) {
         const TileItem it = J.tiles[e];

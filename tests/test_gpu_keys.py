@@ -80,7 +80,7 @@ def test_typed_full_2_24(oracle_mod, kt):
     with _ctx(1 << 24, kt) as ctx:
         gk, gp, st = gpu_sort(ctx, k)
         assert_matches_oracle(ctx, k, ref, gk, gp, st)
-        assert st["launches"] == 15
+        assert st["launches"] == 13
 
 
 def test_typed_vm_and_descending(oracle_mod):

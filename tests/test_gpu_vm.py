@@ -57,6 +57,38 @@ def test_vm_uses_far_less_memory_than_pingpong(oracle_mod):
     assert sv["peak_pages"] > 0
 
 
+def vm_extra_bound(n, page_size, pool_pages, tile=4096):
+    """Device memory a VM context may hold for one instance of n keys with
+    their permutation: the page pool (keys + permutation) + the run list
+    (start and power per run slot, n/32 + 4 slots) + the page tables (about
+    330 bytes per virtual page: page table, round records and splits, the
+    free-page ring) + the merge tables (fewer than 4n/T HBM merges, about
+    120 bytes each) + 1 MB of fixed-size tables and guards."""
+    pages = -(-n // page_size)
+    return (pool_pages * page_size * 8 + 5 * (n // 32 + 4) + 330 * pages + 120 * (4 * n // tile + 8)
+            + (1 << 20))
+
+
+def test_vm_extra_memory_bound(oracle_mod):
+    """VM storage's extra memory (Sec. 4 "Pages needed") is the page pool plus
+    tables of n/32 run slots, n/P pages and 4n/T HBM merges: at n = 2^24 it is
+    within the stated bound and under a quarter of Pingpong's scratch."""
+    from paper_2605_27147_gb300 import binding
+
+    n = 1 << 24
+    keys = inputs.make("uniform", n, 6)
+    with _vm(n) as vm, binding.Context(n, want_perm=True) as pp:
+        kv, pv, sv = gpu_sort(vm, keys)
+        pp_bytes = pp.scratch_bytes()
+        assert vm.scratch_bytes() == sv["scratch_bytes"]
+    ref_k, ref_p = oracle_mod.stable_sort(keys)
+    assert np.array_equal(pv, ref_p) and np.array_equal(kv, ref_k)
+    assert sv["page_size"] > 0 and sv["pool_pages"] >= 16
+    assert 0 < sv["peak_pages"] <= sv["pool_pages"]
+    assert sv["scratch_bytes"] <= vm_extra_bound(n, sv["page_size"], sv["pool_pages"]), sv
+    assert 4 * sv["scratch_bytes"] < pp_bytes, (sv["scratch_bytes"], pp_bytes)
+
+
 def test_vm_keys_only(oracle_mod):
     with _vm(1 << 20, page_log2=9) as ctx:
         for n in (5000, 654321):
