@@ -793,7 +793,16 @@ def serving_leg(local, lane_total, rate=2000.0, duration=10.0, budget=64 << 30, 
     ring_k = torch.empty(ring_n, dtype=torch.int32, pin_memory=True)
     ring_p = torch.empty(ring_n, dtype=torch.int32, pin_memory=True)
     pk, pp, pin = ring_k.data_ptr(), ring_p.data_ptr(), pool.data_ptr()
-    srv = binding.Server(budget, max_n, lanes=lanes, lane_max_total=lane_total, lane_max_count=256, device=local)
+    # the server's per-batch trace (host and device times of every batch's
+    # copies in, wait for the previous sort, sort and copies out) explains
+    # the tail: where a slow request's time went
+    trace_path = os.path.join(tempfile.mkdtemp(prefix="ps_trace_"), "batches.csv")
+    os.environ["PS_SERVER_TRACE"] = trace_path
+    try:
+        srv = binding.Server(budget, max_n, lanes=lanes, lane_max_total=lane_total, lane_max_count=256,
+                             device=local)
+    finally:
+        del os.environ["PS_SERVER_TRACE"]
     # warm-up: a few requests (module loading, first launches)
     for i in range(8):
         srv.wait(srv.submit(pin, pk, pp, 1 << 20), 60.0)
@@ -804,12 +813,21 @@ def serving_leg(local, lane_total, rate=2000.0, duration=10.0, budget=64 << 30, 
     head, tail = 0, 0                   # ring positions (elements, monotone)
     live = []                           # (ticket, ring start, n) in submission order
     tickets = []
+    import gc
+
+    gc.disable()                        # no collector pause inside the stream
     t0 = time.perf_counter()
     with ClockSampler(local) as clk:
         for i in range(sizes.size):
             n = int(sizes[i])
-            while time.perf_counter() - t0 < arrivals[i]:
-                pass
+            # sleep until just before the arrival, then spin the last 200 us
+            # (a core spinning for the whole stream competes with the server)
+            while True:
+                dt = arrivals[i] - (time.perf_counter() - t0)
+                if dt <= 0:
+                    break
+                if dt > 4e-4:
+                    time.sleep(dt - 2e-4)
             # free completed slots at the ring's tail; wait if the ring is full
             while live and (head - tail + n > ring_n):
                 tk, st0, nn = live[0]
@@ -837,8 +855,10 @@ def serving_leg(local, lane_total, rate=2000.0, duration=10.0, budget=64 << 30, 
             tickets.append(t)
         lat = [srv.wait(t, 120.0) for t in tickets]
         t_end = time.perf_counter()
+    gc.enable()
     st = srv.stats()
-    srv.close()
+    srv.close()                         # writes the trace
+    phases = batch_phases(trace_path)
     lat_ms = np.array(lat) * 1000.0
     elems = int(sizes.sum())
     wall = t_end - t0
@@ -849,8 +869,43 @@ def serving_leg(local, lane_total, rate=2000.0, duration=10.0, budget=64 << 30, 
         "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
                        "mean": float(lat_ms.mean()), "max": float(lat_ms.max())},
         "largest_request_solo_ms": 1000.0 * float(min(solo)),
+        "batch_phases_ms": phases,
         "server": st, "clocks": clk.summary(),
+        "raw": {"arrival_s": arrivals, "n": sizes, "latency_ms": lat_ms},   # not printed
     }
+
+
+def batch_phases(path):
+    """p50 / p99 / max per phase of the server's batches, from its trace (ms):
+    enqueue (host), copies in, wait for the previous batch's sort, sort,
+    copies out; and the batches whose copies in ran below 10 GB/s."""
+    import csv
+
+    try:
+        rows = list(csv.DictReader(open(path)))
+    except OSError:
+        return None
+    if not rows:
+        return None
+    col = lambda k: np.array([float(r[k]) for r in rows])
+    el = col("elements")
+    parts = {
+        "enqueue": 1000.0 * (col("host_enqueue_end_s") - col("host_enqueue_begin_s")),
+        "copies_in": col("gpu_copies_in_done_ms") - col("gpu_first_copy_in_ms"),
+        "wait_previous_sort": col("gpu_sort_start_ms") - col("gpu_copies_in_done_ms"),
+        "sort": col("gpu_sort_end_ms") - col("gpu_sort_start_ms"),
+        "copies_out": col("gpu_copies_out_done_ms") - col("gpu_sort_end_ms"),
+    }
+    out = {k: {"p50": float(np.percentile(v, 50)), "p99": float(np.percentile(v, 99)), "max": float(v.max())}
+           for k, v in parts.items()}
+    cin = parts["copies_in"]
+    slow = (el >= (1 << 20)) & (4.0 * el / np.maximum(cin, 1e-6) / 1e6 < 10.0)
+    out["batches"] = len(rows)
+    out["slow_copies_in"] = {"batches": int(slow.sum()),
+                             "host_times_s": [round(float(x), 3) for x in col("host_enqueue_begin_s")[slow][:8]],
+                             "note": "batches of >= 2^20 elements whose host->device copies (pinned "
+                                     "sources) ran below 10 GB/s"}
+    return out
 
 
 def run_serving(args):
@@ -877,6 +932,7 @@ def run_serving(args):
                    "io": "pinned host arrays in, pinned host arrays out (copies inside every latency)"},
         "latency_ms": r["latency_ms"],
         "largest_request_solo_ms": r["largest_request_solo_ms"],
+        "batch_phases_ms": r["batch_phases_ms"],
         "server": st,
         "e2e": {"value": r["value"], "unit": UNIT, "h2d_bytes_per_step": int(4 * r["mean_n"]),
                 "d2h_bytes_per_step": int(8 * r["mean_n"]),
@@ -1196,6 +1252,7 @@ def serving_summary(r):
         "p50_ms": r["latency_ms"]["p50"], "p99_ms": r["latency_ms"]["p99"],
         "mean_ms": r["latency_ms"]["mean"], "max_ms": r["latency_ms"]["max"],
         "largest_request_solo_ms": r["largest_request_solo_ms"],
+        "batch_phases_ms": r["batch_phases_ms"],
         "sustained": r["value"], "offered": r["offered"], "unit": UNIT,
         "budget_bytes": r["budget"], "device_bytes": st["device_bytes"], "lanes": st["lanes"],
         "lane_max_total": st["lane_max_total"], "batches": st["batches"], "max_busy_lanes": st["max_busy_lanes"],

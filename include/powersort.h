@@ -325,7 +325,11 @@ typedef struct ps_server_stats {
 PS_API ps_status ps_server_cancel(ps_server* srv, uint64_t ticket);
 
 /* Start a server (allocates every lane up front; PS_ENOMEM if the lanes do not
- * fit the budget). */
+ * fit the budget).  Tracing: when the environment variable PS_SERVER_TRACE
+ * names a file, the server records every batch (lane, requests, elements, the
+ * host times it was enqueued and seen complete, and device event times of its
+ * first copy in, copies in done, sort start, sort end and copies out done)
+ * and writes them there as CSV when it is destroyed. */
 PS_API ps_status ps_server_create(const ps_server_config* cfg, ps_server** out);
 /* Queue one sort: h_in[0, n) is read (not modified); the sorted keys go to
  * h_keys_out and, if h_perm_out is not NULL, the stable permutation to

@@ -19,7 +19,10 @@
 // lane's event has fired; its latency is measured from submission.
 #include <chrono>
 #include <condition_variable>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <string>
 #include <deque>
 #include <mutex>
 #include <new>
@@ -57,6 +60,22 @@ struct Lane {
     std::vector<uint64_t> batch;    // tickets in flight
     std::vector<Req> jobs;          // their arrays, copied under the lock
     bool busy = false;
+    bool signalled = false;         // the stream reached the batch's end (host callback, under the lock)
+    struct ps_server* owner = nullptr;
+    // tracing (PS_SERVER_TRACE): timing events of the batch in flight -- its
+    // first copy in, copies in done, sort start, sort end, copies out done --
+    // and the host times it was enqueued
+    cudaEvent_t tev[5] = {};
+    double t_enq0 = 0.0, t_enq1 = 0.0;
+};
+
+// One traced batch: host times in seconds and device times in milliseconds,
+// both since the server started.
+struct TraceRow {
+    uint32_t lane, requests;
+    uint64_t elements;
+    double t_enq0, t_enq1, t_seen;
+    float gpu[5];
 };
 
 // Only for choosing a lane size when the caller gives none: lane arrays
@@ -81,9 +100,25 @@ struct ps_server {
     uint64_t completed = 0, elements = 0, batches = 0, failed = 0;
     uint32_t max_in_flight_lanes = 0;
     cudaEvent_t last_computed = nullptr;   // the sort of the batch dispatched last (dispatcher only)
+    // tracing: on when PS_SERVER_TRACE names a file, written at destroy
+    std::string trace_path;
+    cudaEvent_t trace_t0 = nullptr;
+    Clock::time_point t_start;
+    std::vector<TraceRow> trace;
 };
 
 namespace {
+
+// Host function enqueued after a batch's last copy: wakes the dispatcher
+// instead of having it poll the lanes' events.  It calls no CUDA function.
+void CUDART_CB on_batch_end(void* arg)
+{
+    Lane* L = static_cast<Lane*>(arg);
+    ps_server* S = L->owner;
+    std::lock_guard<std::mutex> lk(S->mu);
+    L->signalled = true;
+    S->cv_work.notify_one();
+}
 
 void lane_free(Lane& L)
 {
@@ -94,6 +129,8 @@ void lane_free(Lane& L)
     if (L.hoff) cudaFreeHost(L.hoff);
     if (L.done) cudaEventDestroy(L.done);
     if (L.computed) cudaEventDestroy(L.computed);
+    for (cudaEvent_t& e : L.tev)
+        if (e) cudaEventDestroy(e);
     if (L.stream) cudaStreamDestroy(L.stream);
     L = Lane{};
 }
@@ -102,6 +139,11 @@ void lane_free(Lane& L)
 ps_status launch_batch(ps_server* S, Lane& L)
 {
     const size_t k = L.jobs.size();
+    const bool tr = S->trace_t0 != nullptr;
+    if (tr) {
+        L.t_enq0 = std::chrono::duration<double>(Clock::now() - S->t_start).count();
+        if (cudaEventRecord(L.tev[0], L.stream) != cudaSuccess) return PS_ECUDA;
+    }
     uint64_t acc = 0;
     L.hoff[0] = 0;
     for (size_t i = 0; i < k; ++i) {
@@ -115,11 +157,14 @@ ps_status launch_batch(ps_server* S, Lane& L)
         if (r.n && cudaMemcpyAsync(L.dkeys + L.hoff[i], r.in, r.n * 4, cudaMemcpyHostToDevice, L.stream) != cudaSuccess)
             return PS_ECUDA;
     }
+    if (tr && cudaEventRecord(L.tev[1], L.stream) != cudaSuccess) return PS_ECUDA;
     // the sort starts after the previous batch's sort (copies in are not held back)
     if (S->last_computed && cudaStreamWaitEvent(L.stream, S->last_computed, 0) != cudaSuccess) return PS_ECUDA;
+    if (tr && cudaEventRecord(L.tev[2], L.stream) != cudaSuccess) return PS_ECUDA;
     const ps_status st = ps_run_batched(L.ctx, L.dkeys, S->cfg.want_perm ? L.dperm : nullptr, L.doff, (uint32_t)k, nullptr);
     if (st != PS_OK) return st;
     if (cudaEventRecord(L.computed, L.stream) != cudaSuccess) return PS_ECUDA;
+    if (tr && cudaEventRecord(L.tev[3], L.stream) != cudaSuccess) return PS_ECUDA;
     S->last_computed = L.computed;
     for (size_t i = 0; i < k; ++i) {
         const Req& r = L.jobs[i];
@@ -131,7 +176,40 @@ ps_status launch_batch(ps_server* S, Lane& L)
             return PS_ECUDA;
     }
     if (cudaEventRecord(L.done, L.stream) != cudaSuccess) return PS_ECUDA;
+    if (tr && cudaEventRecord(L.tev[4], L.stream) != cudaSuccess) return PS_ECUDA;
+    if (cudaLaunchHostFunc(L.stream, on_batch_end, &L) != cudaSuccess) return PS_ECUDA;
+    if (tr) L.t_enq1 = std::chrono::duration<double>(Clock::now() - S->t_start).count();
     return PS_OK;
+}
+
+// A completed batch's trace row (dispatcher, lock held; the events are done).
+void trace_batch(ps_server* S, Lane& L, uint32_t lane)
+{
+    TraceRow row;
+    row.lane = lane;
+    row.requests = (uint32_t)L.jobs.size();
+    row.elements = 0;
+    for (const Req& r : L.jobs) row.elements += r.n;
+    row.t_enq0 = L.t_enq0;
+    row.t_enq1 = L.t_enq1;
+    row.t_seen = std::chrono::duration<double>(Clock::now() - S->t_start).count();
+    for (int i = 0; i < 5; ++i)
+        if (cudaEventElapsedTime(&row.gpu[i], S->trace_t0, L.tev[i]) != cudaSuccess) row.gpu[i] = -1.0f;
+    cudaGetLastError();
+    S->trace.push_back(row);
+}
+
+void trace_write(const ps_server* S)
+{
+    FILE* f = std::fopen(S->trace_path.c_str(), "w");
+    if (!f) return;
+    std::fprintf(f, "lane,requests,elements,host_enqueue_begin_s,host_enqueue_end_s,host_seen_s,"
+                    "gpu_first_copy_in_ms,gpu_copies_in_done_ms,gpu_sort_start_ms,gpu_sort_end_ms,gpu_copies_out_done_ms\n");
+    for (const TraceRow& r : S->trace)
+        std::fprintf(f, "%u,%u,%llu,%.6f,%.6f,%.6f,%.4f,%.4f,%.4f,%.4f,%.4f\n", r.lane, r.requests,
+                     (unsigned long long)r.elements, r.t_enq0, r.t_enq1, r.t_seen, r.gpu[0], r.gpu[1], r.gpu[2],
+                     r.gpu[3], r.gpu[4]);
+    std::fclose(f);
 }
 
 void dispatcher(ps_server* S)
@@ -142,7 +220,8 @@ void dispatcher(ps_server* S)
         bool progress = false;
         // completions
         for (Lane& L : S->lanes) {
-            if (!L.busy) continue;
+            if (!L.busy || !L.signalled) continue;
+            L.signalled = false;
             const cudaError_t q = cudaEventQuery(L.done);
             if (q == cudaErrorNotReady) continue;
             ps_status st = q == cudaSuccess ? PS_OK : PS_ECUDA;
@@ -153,6 +232,7 @@ void dispatcher(ps_server* S)
             } else {
                 cudaGetLastError();
             }
+            if (st == PS_OK && S->trace_t0) trace_batch(S, L, (uint32_t)(&L - &S->lanes[0]));
             const auto now = Clock::now();
             for (uint64_t t : L.batch) {
                 Req& r = S->reqs[t];
@@ -212,8 +292,9 @@ void dispatcher(ps_server* S)
         if (busy > S->max_in_flight_lanes) S->max_in_flight_lanes = busy;
         if (S->stop && S->queue.empty() && busy == 0) break;
         if (!progress) {
-            // nothing changed: sleep until a submission, or poll the events again
-            S->cv_work.wait_for(lk, std::chrono::microseconds(busy ? 20 : 2000));
+            // nothing changed: sleep until a submission or a batch's end wakes
+            // the dispatcher (the timeout only bounds a missed wake-up)
+            S->cv_work.wait_for(lk, std::chrono::milliseconds(busy ? 5 : 50));
         }
     }
 }
@@ -255,7 +336,11 @@ PS_API ps_status ps_server_create(const ps_server_config* cfg, ps_server** out)
     ps_status st = PS_OK;
     S->lanes.resize(S->cfg.lanes);
     for (Lane& L : S->lanes) {
-        if (cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking) != cudaSuccess ||
+        L.owner = S;
+        bool ev_ok = true;
+        if (std::getenv("PS_SERVER_TRACE"))
+            for (cudaEvent_t& e : L.tev) ev_ok = ev_ok && cudaEventCreate(&e) == cudaSuccess;
+        if (!ev_ok || cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&L.computed, cudaEventDisableTiming) != cudaSuccess) {
             st = PS_ECUDA;
@@ -298,6 +383,18 @@ PS_API ps_status ps_server_create(const ps_server_config* cfg, ps_server** out)
         return st;
     }
     S->reqs.reserve(1 << 16);
+    S->t_start = Clock::now();
+    if (const char* tp = std::getenv("PS_SERVER_TRACE")) {
+        if (*tp && cudaEventCreate(&S->trace_t0) == cudaSuccess &&
+            cudaEventRecord(S->trace_t0, S->lanes[0].stream) == cudaSuccess) {
+            S->trace_path = tp;
+            S->trace.reserve(1 << 16);
+        } else {
+            cudaGetLastError();
+            if (S->trace_t0) cudaEventDestroy(S->trace_t0);
+            S->trace_t0 = nullptr;
+        }
+    }
     S->th = std::thread(dispatcher, S);
     if (prev >= 0) cudaSetDevice(prev);
     *out = S;
@@ -404,10 +501,13 @@ PS_API void ps_server_destroy(ps_server* S)
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice((int)S->cfg.device);
-    for (Lane& L : S->lanes) {
+    for (Lane& L : S->lanes)
         if (L.stream) cudaStreamSynchronize(L.stream);
-        lane_free(L);
+    if (S->trace_t0) {
+        trace_write(S);
+        cudaEventDestroy(S->trace_t0);
     }
+    for (Lane& L : S->lanes) lane_free(L);
     if (prev >= 0) cudaSetDevice(prev);
     delete S;
 }
