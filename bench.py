@@ -1032,10 +1032,12 @@ def main():
         st = ctx.run(work[:n], perm[:n], stats=True)
         hbm[i] = st
         launches_per_sort = int(st["launches"])
-        if args.storage == "pingpong":
-            rounds[data[i][0]] = [[round(x, 1) for x in rt] for rt in ctx.round_times()]
+        rounds[data[i][0]] = [[round(x, 1) for x in rt] for rt in ctx.round_times()]
     merge_ms = sum(p["merge_rounds"] for p in phases)
-    merge_bytes = sum(BYTES_PER_MERGED_ELEM * hbm[i]["hbm_merge_elems"] for _, _, _, i in recs)
+    # HBM merges move key + permutation entry, read and written: 16 B per
+    # element; VM storage's final Copy moves whole pages the same way
+    merge_bytes = sum(BYTES_PER_MERGED_ELEM * (hbm[i]["hbm_merge_elems"] + hbm[i]["copy_pages"] * hbm[i]["page_size"])
+                      for _, _, _, i in recs)
     tiles_ms = sum(p["tiles"] for p in phases)
     tiles_bytes = sum(12 * data[i][1] for _, _, _, i in recs)   # keys read, keys + perm written
     runs_ms = sum(p["runs"] for p in phases)
@@ -1177,7 +1179,9 @@ def main():
             "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic,
             "algorithmic_bytes": "16 B per element per HBM merge (key + perm read and written), "
-                                 "summed over the merges of the call",
+                                 "summed over the merges of the call"
+                                 + ("; plus 16 B per element of every page the final Copy moves"
+                                    if args.storage == "vm" else ""),
         },
         "kernels": {
             "phase_ms_per_step": {k: v / args.steps for k, v in phase_tot.items()},
@@ -1188,7 +1192,7 @@ def main():
         },
         "stats": {data[i][0]: {k: hbm[i][k] for k in ("runs", "merge_cost", "tiles", "global_nodes", "rounds",
                                                       "hbm_merge_elems", "max_power", "scratch_bytes",
-                                                      "peak_pages", "pages_spliced")} for i in hbm},
+                                                      "peak_pages", "pages_spliced", "copy_pages")} for i in hbm},
         "round_timeline_us": rounds,
         "plain_rule": plain_rule,
         "cpu_baseline": cpu,
@@ -1198,6 +1202,14 @@ def main():
     }
     ctx.close()
     if args.storage == "vm":
+        # where a paged sort's merge time goes: per round, the fixed steps
+        # (page marks, records, splits, the touched list, the page-table
+        # swap) and the page dataflow; from the statistics call's timeline
+        line["vm_rounds"] = {
+            k: {"rounds": len(rt),
+                "fixed_steps_ms": sum((b - a) + (d - c) for a, b, c, d in rt) / 1000.0,
+                "pages_ms": sum(c - b for a, b, c, d in rt) / 1000.0}
+            for k, rt in rounds.items()}
         # extra memory of VM storage (Sec. 4 "Pages needed"; the paper's Fig. 5
         # table) beside the paper's bound and Pingpong's scratch at the same n
         st0 = hbm[0]

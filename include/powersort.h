@@ -128,6 +128,7 @@ typedef struct ps_stats {
                                page through the page table, moving no element */
     uint32_t page_size;     /* VM mode: P, elements per page (else 0)             */
     uint32_t pool_pages;    /* VM mode: pages of the pre-allocated pool (else 0)  */
+    uint64_t copy_pages;    /* VM mode: page moves made by the final Copy (Sec. 4)  */
 } ps_stats;
 
 typedef struct ps_ctx ps_ctx;
@@ -223,14 +224,17 @@ PS_API ps_status ps_run_host(ps_ctx* ctx, uint32_t* h_keys, uint32_t* h_perm, ui
  * launches.  h_ms receives min(cap, 6) values; *count (may be NULL) gets 6. */
 PS_API ps_status ps_get_phase_times(ps_ctx* ctx, float* h_ms, uint32_t cap, uint32_t* count);
 
-/* Timeline of the HBM merges of the last Pingpong call (synchronises).  The
- * merges are grouped in rounds of equal power (children before parents) but
- * run as a dataflow: a merge starts when its two children are complete, so
- * rounds overlap.  For every round that ran, four values in microseconds
- * since the merge kernel started: the first and the last time one of the
- * round's chunks found its inputs complete, and the first and the last time
- * one of its chunks sent its output.  h_us receives min(cap, 4 x rounds)
- * values; *count (may be NULL) gets 4 x rounds (0 for VM storage). */
+/* Timeline of the HBM merges of the last call (synchronises), four values
+ * per round that ran, in microseconds since the merge kernel started.
+ * Pingpong: the merges are grouped in rounds of equal power (children before
+ * parents) but run as a dataflow: a merge starts when its two children are
+ * complete, so rounds overlap; the values are the first and the last time
+ * one of the round's chunks found its inputs complete, and the first and the
+ * last time one of its chunks sent its output.  VM storage: the rounds are
+ * separated by grid barriers; the values are the round's start, the start of
+ * its page dataflow (after the page marks, records, splits and the list of
+ * touched pages), the end of the page dataflow, and the round's end.  h_us
+ * receives min(cap, 4 x rounds) values; *count (may be NULL) gets 4 x rounds. */
 PS_API ps_status ps_get_round_times(ps_ctx* ctx, float* h_us, uint32_t cap, uint32_t* count);
 
 /* Wait for the context's stream and report the device-side status of the

@@ -69,6 +69,7 @@ class ps_stats(ctypes.Structure):
         ("pages_spliced", ctypes.c_uint32),
         ("page_size", ctypes.c_uint32),
         ("pool_pages", ctypes.c_uint32),
+        ("copy_pages", ctypes.c_uint64),
     ]
 
     def as_dict(self):
@@ -336,7 +337,8 @@ class Context:
         return {name: float(buf[i]) for i, name in enumerate(PHASES)}
 
     def round_times(self) -> list:
-        """[(split_us, merge_us, barrier_us, own_search_us)] per HBM merge round of the last call."""
+        """Four times (us since the merge kernel's start) per HBM merge round of
+        the last call, as ps_get_round_times describes for each storage."""
         cnt = ctypes.c_uint32()
         _check(lib().ps_get_round_times(self._h, None, 0, ctypes.byref(cnt)), "ps_get_round_times")
         buf = (ctypes.c_float * max(1, cnt.value))()

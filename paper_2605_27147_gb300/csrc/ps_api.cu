@@ -169,6 +169,7 @@ void fill_stats(const ps_ctx* c, ps_stats* st, uint32_t count)
     st->pages_spliced = c->base.vm ? h->vm_spliced : 0u;
     st->page_size = c->base.vm ? 1u << c->base.vm_plog2 : 0u;
     st->pool_pages = c->base.vm ? c->base.vm_pool : 0u;
+    st->copy_pages = c->base.vm ? h->vm_copy_moves : 0u;
 }
 
 ps_status run_common(ps_ctx* c, uint32_t* d_keys, uint32_t* d_perm, const uint64_t* d_offsets,
@@ -343,6 +344,8 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
         if (J.vm_pool < 16) J.vm_pool = 16;
         // the free-page ring: the pool's pages plus at most one push per page per round
         J.vm_ring_cap = J.vm_pool + (uint32_t)ps::NPOW * J.vm_na_cap;
+        // the final Copy keeps two free-page stacks of up to every physical page
+        if (J.vm_ring_cap < 2 * (J.vm_na_cap + J.vm_pool)) J.vm_ring_cap = 2 * (J.vm_na_cap + J.vm_pool);
         if (st == PS_OK) st = dev_alloc(c, &J.pt, J.vm_na_cap);
         if (st == PS_OK) st = dev_alloc(c, &J.pt_new, J.vm_na_cap);
         if (st == PS_OK) st = dev_alloc(c, &J.page_cnt, J.vm_na_cap);
@@ -353,6 +356,7 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
         if (st == PS_OK) st = dev_alloc(c, &J.vm_rec, (size_t)J.vm_na_cap * ps::VM_REC_WORDS);
         if (st == PS_OK) st = dev_alloc(c, &J.holder, (size_t)J.vm_na_cap + J.vm_pool);
         if (st == PS_OK) st = dev_alloc(c, &J.vm_split_at, ((size_t)J.vm_na_cap + 1) * ps::VM_SPLIT_WORDS);
+        if (st == PS_OK) st = dev_alloc(c, &J.vm_cta_count, (size_t)c->grid_vm);
     } else {
         if (st == PS_OK) st = dev_alloc(c, &J.keysB, max_total);
         if (st == PS_OK && cfg->want_perm) st = dev_alloc(c, &J.permB, max_total);
@@ -424,7 +428,7 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
     if (st == PS_OK && ((!vm && (!J.keysB || !J.chunk_node)) || !J.inst || !J.chunk_map || !J.chunk_info ||
                         !J.range_agg || !J.range_entry || !J.run_start || !J.power || !J.tiles || !J.gnodes ||
                         !J.gmap || !J.gsorted || !J.dep || !J.ctr || (!vm && cfg->want_perm && !J.permB) ||
-                        (vm && (!J.pool_keys || !J.pt || !J.vm_split_at || !J.vm_rec || !J.free_stack))))
+                        (vm && (!J.pool_keys || !J.pt || !J.vm_split_at || !J.vm_rec || !J.free_stack || !J.vm_cta_count))))
         st = PS_EINTERNAL;
     if (st != PS_OK) {
         cudaGetLastError();

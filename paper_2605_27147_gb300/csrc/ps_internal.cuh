@@ -136,6 +136,8 @@ struct Ctr {
     uint32_t vm_waves;                 // VM rounds run by the call
     uint32_t vm_copy_moves;            // page copies made by the final Copy
     uint32_t vm_spliced;               // output pages that took over a whole input page
+    uint32_t vm_copy_top[2];           // final Copy: entries on the two free-page stacks
+    uint32_t vm_copy_taken[2];         // final Copy: entries of each stack handed out
     uint32_t keys_mapped;              // typed keys: the forward map ran (the inverse must too)
     uint32_t rec_lcp;                  // records: words every row shares (NONE: all rows equal)
     uint32_t rec_groups;               // records: groups of equal window keys listed for the fix-up
@@ -226,6 +228,7 @@ struct Job {
     uint32_t* holder;           // physical page -> virtual page it holds (final Copy)
     uint32_t* vm_split_at;      // per page start inside a merge of the round: its merge-path split
                                 // and the slices' pages (VM_SPLIT_WORDS)
+    uint32_t* vm_cta_count;     // per CTA of the rounds kernel: touched pages of its block of pages
 };
 
 // ---------------------------------------------------------------- helpers

@@ -168,6 +168,38 @@ __device__ __forceinline__ void consume_finish(const Job& J, const Consumed& r, 
     if (!partial_tail) ring_push(J, old);
 }
 
+// Sum of v over the CTA (every thread gets it); ws: one word per warp.
+__device__ __forceinline__ uint32_t block_sum(uint32_t v, uint32_t* ws)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) ws[warp] = v;
+    __syncthreads();
+    uint32_t t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+    return t;
+}
+
+// Number of threads below this one (in thread order) whose flag is set, and
+// the CTA's total; ws: one word per warp.
+__device__ __forceinline__ uint32_t block_rank(bool flag, uint32_t* ws, uint32_t& total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t m = __ballot_sync(0xffffffffu, flag);
+    __syncthreads();
+    if (lane == 0) ws[warp] = __popc(m);
+    __syncthreads();
+    uint32_t before = __popc(m & ((1u << lane) - 1u)), t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        if (w < warp) before += ws[w];
+        t += ws[w];
+    }
+    total = t;
+    return before;
+}
+
 struct VmSmem {
     uint32_t k[VM_SLOTS];
     uint32_t p[VM_SLOTS];
@@ -339,10 +371,14 @@ __global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_rounds(Job J)
         J.free_stack[i] = i < J.vm_pool ? J.vm_na_cap + i : NONE;
     if (!grid_barrier(C)) return;
 
+    // pages per CTA block of step 3
+    const uint32_t BK = (NA + gridDim.x - 1) / gridDim.x;
+    if (blockIdx.x == 0 && tid == 0) C->merge_t0 = globaltimer_ns();
     for (int r = 0; r < NPOW; ++r) {
         if (*(volatile uint32_t*)&C->error) return;
         const uint32_t e0 = C->bucket_start[r], e1 = C->bucket_start[r + 1];
         if (e0 == e1) continue;
+        if (blockIdx.x == 0 && tid == 0) C->round_ns[r][0] = globaltimer_ns();
         // 1. the pages each merge of the round touches (a warp per merge)
         for (uint32_t e = e0 + gwarp; e < e1; e += nwarps_grid) {
             const GSorted g = J.gsorted[e];
@@ -360,6 +396,14 @@ __global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_rounds(Job J)
             }
         }
         if (!grid_barrier(C)) return;
+        // the touched pages of this CTA's block of pages (listed in step 3)
+        {
+            const uint32_t b0 = min(blockIdx.x * BK, NA), b1 = min(b0 + BK, NA);
+            uint32_t c = 0;
+            for (uint32_t u = b0 + tid; u < b1; u += VM_BLOCK) c += J.page_cnt[u] > 0 ? 1u : 0u;
+            c = block_sum(c, warp_sums);
+            if (tid == 0) J.vm_cta_count[blockIdx.x] = c;
+        }
         // 2. per touched page (a thread each): its record -- up to two merges,
         //    ordered, with the gaps between them filled by copies; and per page
         //    start inside a merge (eight lanes each) the merge-path split there,
@@ -433,43 +477,35 @@ __global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_rounds(Job J)
                 }
             }
         }
-        // 3. the touched pages, in page order (CTA 0; each thread takes
-        //    TOUCH_PER consecutive pages per pass)
-        if (blockIdx.x == 0) {
-            constexpr uint32_t TOUCH_PER = 8;
-            uint32_t carry = 0;
-            for (uint32_t base = 0; base < NA; base += VM_BLOCK * TOUCH_PER) {
-                const uint32_t u0 = base + tid * TOUCH_PER;
-                uint32_t flags = 0;
-#pragma unroll
-                for (uint32_t i = 0; i < TOUCH_PER; ++i)
-                    if (u0 + i < NA && J.page_cnt[u0 + i] > 0) flags |= 1u << i;
-                const uint32_t c = __popc(flags);
-                uint32_t x = c;                       // inclusive warp scan of the counts
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-                    if (lane >= o) x += y;
-                }
-                if (lane == 31) warp_sums[warp] = x;
-                __syncthreads();
-                uint32_t before = carry + x - c, tot = 0;
-                for (int w = 0; w < VM_BLOCK / 32; ++w) {
-                    if (w < warp) before += warp_sums[w];
-                    tot += warp_sums[w];
-                }
-                for (uint32_t i = 0; i < TOUCH_PER; ++i)
-                    if (flags & (1u << i)) J.touched[before++] = u0 + i;
+        // 3. the touched pages, in page order: every CTA lists the pages of
+        //    its own contiguous block of BK pages, after the touched pages of
+        //    the blocks before it (counted at the start of step 2)
+        if (!grid_barrier(C)) return;
+        {
+            __shared__ uint32_t s_before;
+            uint32_t before = 0;                      // touched pages in the blocks before this one
+            for (uint32_t j = tid; j < blockIdx.x; j += VM_BLOCK) before += __ldcg(J.vm_cta_count + j);
+            before = block_sum(before, warp_sums);
+            if (tid == 0) s_before = before;
+            __syncthreads();
+            uint32_t carry = s_before;
+            const uint32_t b0 = min(blockIdx.x * BK, NA), b1 = min(b0 + BK, NA);
+            for (uint32_t u0 = b0; u0 < b1; u0 += VM_BLOCK) {
+                const uint32_t u = u0 + tid;
+                const bool t = u < b1 && J.page_cnt[u] > 0;
+                uint32_t tot;
+                const uint32_t at = carry + block_rank(t, warp_sums, tot);
+                if (t) J.touched[at] = u;
                 carry += tot;
-                __syncthreads();
             }
-            if (tid == 0) {
-                C->vm_touched = carry;
+            if (blockIdx.x == gridDim.x - 1 && tid == 0) {
+                C->vm_touched = carry;                // the last block's end: every touched page
                 C->vm_round_base = C->vm_ring_head;
                 C->vm_waves += 1;
             }
         }
         if (!grid_barrier(C)) return;
+        if (blockIdx.x == 0 && tid == 0) C->round_ns[r][1] = globaltimer_ns();
         // 4. the pages, as a dataflow over tickets
         {
             const uint32_t ntouched = C->vm_touched, base = C->vm_round_base;
@@ -523,6 +559,7 @@ __global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_rounds(Job J)
             }
         }
         if (!grid_barrier(C)) return;
+        if (blockIdx.x == 0 && tid == 0) C->round_ns[r][2] = globaltimer_ns();
         // 5. the written pages become current; reset the per-round tables; the
         //    over-drawn tickets are returned
         const uint32_t ntouched = C->vm_touched;
@@ -534,13 +571,15 @@ __global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_rounds(Job J)
         }
         if (gtid == 0) C->vm_ring_head = C->vm_round_base + ntouched;
         if (!grid_barrier(C)) return;
+        if (blockIdx.x == 0 && tid == 0) C->round_ns[r][3] = globaltimer_ns();
     }
 }
 
-// One page copied by one warp: 16-byte vectors when the caller's arrays are
-// 16-byte aligned (pool pages always are, and a page is a multiple of 16
+// One page copied by the whole CTA: 16-byte vectors when the caller's arrays
+// are 16-byte aligned (pool pages always are, and a page is a multiple of 16
 // bytes), else word by word; the partial last page's tail word by word.
-__device__ void vm_copy_page(const Job& J, uint32_t dst, uint32_t src, uint32_t cnt, bool perm, uint32_t lane)
+// Sources are read at L2 (other CTAs wrote them in earlier steps).
+__device__ void vm_copy_page(const Job& J, uint32_t dst, uint32_t src, uint32_t cnt, bool perm)
 {
     const bool vec = ((reinterpret_cast<uintptr_t>(J.keysA) | reinterpret_cast<uintptr_t>(J.permA)) & 15u) == 0;
     const uint32_t nv = vec ? cnt >> 2 : 0u;
@@ -549,73 +588,84 @@ __device__ void vm_copy_page(const Job& J, uint32_t dst, uint32_t src, uint32_t 
         uint32_t* d = pass ? phys_p(J, dst) : phys_k(J, dst);
         const uint4* s4 = reinterpret_cast<const uint4*>(s);
         uint4* d4 = reinterpret_cast<uint4*>(d);
-#pragma unroll 8
-        for (uint32_t i = lane; i < nv; i += 32) d4[i] = s4[i];
-        for (uint32_t i = (nv << 2) + lane; i < cnt; i += 32) d[i] = s[i];
+#pragma unroll 4
+        for (uint32_t i = threadIdx.x; i < nv; i += VM_BLOCK) d4[i] = __ldcg(s4 + i);
+        for (uint32_t i = (nv << 2) + threadIdx.x; i < cnt; i += VM_BLOCK) d[i] = __ldcg(s + i);
     }
 }
 
 // Copy (Sec. 4), in batches of target pages.  The paper walks the virtual
 // pages in order: a target array page that still holds data needed later is
 // first moved out to a free page, then the page's own data is copied in.
-// Here a batch of up to `pool` consecutive targets does the same in two
-// parallel steps: (1) every target of the batch that holds another page's
-// data moves it out to a free page; (2) every target receives its own data.
-// After step 1 no target of the batch holds needed data, so the copies of
-// step 2 never overwrite a source; each copy frees its source, so the number
-// of free pages is the same after every batch.  Counting pages shows that
-// with at most pool - 1 targets per batch the free pages cover every move out.
+// Here a batch of up to pool - 1 consecutive targets does the same in two
+// parallel steps, a CTA per page: (1) every target of the batch that holds
+// another page's data moves it out to a free page; (2) every target receives
+// its own data.  After step 1 no target of the batch holds needed data, so
+// the copies of step 2 never overwrite a source; each copy frees its source,
+// so the number of free pages is the same after every batch, and counting
+// pages shows that with at most pool - 1 targets per batch the free pages
+// cover every move out.  A free page is one that holds nothing, is not a
+// target of this or an earlier batch, and is not the caller's partial last
+// page (never freed, as in the paper).  The free pages of the next batch are
+// gathered during step 2 -- this batch's unused ones and the sources step 2
+// frees, without the next batch's targets -- into the other of two stacks,
+// so a batch needs two grid barriers.
 __global__ void __launch_bounds__(VM_BLOCK) k_vm_copy(Job J)
 {
     Ctr* C = J.ctr;
     if (*(volatile uint32_t*)&C->error) return;
-    const int tid = threadIdx.x, lane = tid & 31;
+    __shared__ uint32_t s_f;
+    const int tid = threadIdx.x;
     const bool perm = J.want_perm != 0;
     const uint32_t n = J.inst[0].n;
     const uint32_t NA = J.vm_na, NP = J.vm_na_cap + J.vm_pool;
     const uint32_t gtid = blockIdx.x * VM_BLOCK + tid, gstride = gridDim.x * VM_BLOCK;
-    const uint32_t gwarp = gtid >> 5, nwarps = gstride >> 5;
     const bool tail_partial = (n & ((1u << J.vm_plog2) - 1)) != 0;
+    const uint32_t BMAX = J.vm_pool - 1;
+    uint32_t* stack[2] = {J.free_stack, J.free_stack + NP};
+    // a page that may serve as a free page for batches ending before qend
+    auto usable = [&](uint32_t p, uint32_t qend) {
+        if (p >= J.vm_na_cap) return true;                    // a pool page
+        return p < NA && p >= qend && !(tail_partial && p + 1 == NA);
+    };
     // holder[p]: the virtual page whose data physical page p holds (NONE: none)
     for (uint32_t p = gtid; p < NP; p += gstride) J.holder[p] = NONE;
+    if (gtid == 0) {
+        C->vm_copy_top[0] = C->vm_copy_top[1] = 0;
+        C->vm_copy_taken[0] = C->vm_copy_taken[1] = 0;
+    }
     if (!grid_barrier(C)) return;
     for (uint32_t u = gtid; u < NA; u += gstride) J.holder[J.pt[u]] = u;
     if (!grid_barrier(C)) return;
-    for (uint32_t q0 = 0; q0 < NA;) {
-        // at most pool - 1 targets: then the free pages always cover the moves out
-        // (one page of slack for the partial last array page, which is never free)
-        const uint32_t B = min(J.vm_pool - 1, NA - q0);
-        const uint32_t q1 = q0 + B;
-        // free pages: hold nothing, are not a target of this or an earlier batch,
-        // and are not the partial last array page
+    // the first batch's free pages
+    {
+        const uint32_t q1 = min(BMAX, NA);
+        for (uint32_t p = gtid; p < NP; p += gstride)
+            if (usable(p, q1) && J.holder[p] == NONE) stack[0][atomicAdd(&C->vm_copy_top[0], 1u)] = p;
+    }
+    if (!grid_barrier(C)) return;
+    for (uint32_t q0 = 0, k = 0; q0 < NA; ++k) {
+        const uint32_t cur = k & 1u, nxt = cur ^ 1u;
+        const uint32_t q1 = q0 + min(BMAX, NA - q0);
+        const uint32_t q2 = q1 + min(BMAX, NA - q1);
+        // step 1: move needed data out of the batch's targets (a CTA per target)
         if (gtid == 0) {
-            C->vm_free_top = 0;
-            C->vm_wave = 0;
+            C->vm_copy_top[nxt] = 0;          // the next batch's stack fills in step 2
+            C->vm_copy_taken[nxt] = 0;
         }
-        if (!grid_barrier(C)) return;
-        for (uint32_t p = gtid; p < NP; p += gstride) {
-            if (p >= J.vm_na_cap && p - J.vm_na_cap >= J.vm_pool) continue;
-            const bool is_array = p < J.vm_na_cap;
-            if (is_array && (p >= NA || p < q1)) continue;
-            if (is_array && tail_partial && p + 1 == NA) continue;
-            if (J.holder[p] == NONE) J.free_stack[atomicAdd(&C->vm_free_top, 1u)] = p;
-        }
-        if (!grid_barrier(C)) return;
-        // step 1: move needed data out of the batch's targets (a warp per target)
-        for (uint32_t q = q0 + gwarp; q < q1; q += nwarps) {
-            const uint32_t r = J.holder[q];
+        for (uint32_t q = q0 + blockIdx.x; q < q1; q += gridDim.x) {
+            const uint32_t r = __ldcg(J.holder + q);
             if (r == NONE || r == q) continue;
-            uint32_t f = NONE;
-            if (lane == 0) {
-                const uint32_t at = atomicAdd(&C->vm_wave, 1u);
-                f = at < C->vm_free_top ? J.free_stack[at] : NONE;
-                if (f == NONE) set_error(C, DERR_INTERNAL, 65);
+            if (tid == 0) {
+                const uint32_t at = atomicAdd(&C->vm_copy_taken[cur], 1u);
+                s_f = at < __ldcg(&C->vm_copy_top[cur]) ? __ldcg(stack[cur] + at) : NONE;
+                if (s_f == NONE) set_error(C, DERR_INTERNAL, 65);
             }
-            f = __shfl_sync(0xffffffffu, f, 0);
-            if (f == NONE) continue;
-            vm_copy_page(J, f, q, page_size(J, r, n), perm, lane);
-            __syncwarp();
-            if (lane == 0) {
+            __syncthreads();
+            const uint32_t f = s_f;
+            if (f != NONE) vm_copy_page(J, f, q, page_size(J, r, n), perm);
+            __syncthreads();
+            if (tid == 0 && f != NONE) {
                 J.pt[r] = f;
                 J.holder[f] = r;
                 J.holder[q] = NONE;
@@ -624,17 +674,28 @@ __global__ void __launch_bounds__(VM_BLOCK) k_vm_copy(Job J)
         }
         if (!grid_barrier(C)) return;
         if (*(volatile uint32_t*)&C->error) return;
-        // step 2: every target receives its own data (a warp per target)
-        for (uint32_t q = q0 + gwarp; q < q1; q += nwarps) {
-            const uint32_t src = J.pt[q];
+        // step 2: every target receives its own data (a CTA per target); the
+        // freed sources and the unused free pages that the next batch may use
+        // go onto the other stack
+        for (uint32_t q = q0 + blockIdx.x; q < q1; q += gridDim.x) {
+            const uint32_t src = __ldcg(J.pt + q);
             if (src == q) continue;
-            vm_copy_page(J, q, src, page_size(J, q, n), perm, lane);
-            __syncwarp();
-            if (lane == 0) {
+            vm_copy_page(J, q, src, page_size(J, q, n), perm);
+            __syncthreads();
+            if (tid == 0) {
                 J.holder[src] = NONE;
                 J.pt[q] = q;
                 J.holder[q] = q;
                 atomicAdd(&C->vm_copy_moves, 1u);
+                if (usable(src, q2)) stack[nxt][atomicAdd(&C->vm_copy_top[nxt], 1u)] = src;
+            }
+        }
+        {
+            const uint32_t top = __ldcg(&C->vm_copy_top[cur]);
+            const uint32_t taken = min(__ldcg(&C->vm_copy_taken[cur]), top);
+            for (uint32_t i = taken + gtid; i < top; i += gstride) {
+                const uint32_t p = __ldcg(stack[cur] + i);
+                if (usable(p, q2)) stack[nxt][atomicAdd(&C->vm_copy_top[nxt], 1u)] = p;
             }
         }
         if (!grid_barrier(C)) return;
