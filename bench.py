@@ -100,6 +100,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="pingpong", choices=["pingpong", "vm"],
                     help="run storage of the plain workloads: Pingpong (n-element scratch) or VM pages")
+    ap.add_argument("--page-log2", type=int, default=0,
+                    help="VM storage: page size 2^k elements (0: the library's default)")
     ap.add_argument("--key-type", default="u32", choices=["u32", "i32", "f32"],
                     help="plain workloads: order the same 32-bit patterns as unsigned, signed or float keys")
     ap.add_argument("--no-e2e", action="store_true")
@@ -984,7 +986,7 @@ def main():
     variant = binding.PS_FLAG_DESCENDING_RUNS if desc else 0
     key_type = {"u32": binding.PS_KEY_U32, "i32": binding.PS_KEY_I32, "f32": binding.PS_KEY_F32}[args.key_type]
     ctx = binding.Context(max_n, mode=mode, want_perm=True, flags=binding.PS_FLAG_TIMING | variant,
-                          key_type=key_type, device=local, stream=stream)
+                          key_type=key_type, page_log2=args.page_log2, device=local, stream=stream)
 
     def one_sort(i, timed):
         n = data[i][1]
