@@ -442,6 +442,7 @@ def batched_leg(steps, warmup, dev, stream, world=1, dist=None, e2e_steps=3):
     doff = torch.from_numpy(off_np.astype(np.int64)).to(dev)
     tuned = autotune.tune(work, doff, perm, max_n, stream=stream)
     ctx = binding.Context(max_n, want_perm=True, max_total=total, max_count=count, tile_log2=tuned["tile_log2"],
+                          merge_lanes=tuned["merge_lanes"],
                           flags=binding.PS_FLAG_TIMING, device=dev.index, stream=stream)
     graph = ctx.graph_batched(work, doff, perm)
 
@@ -568,7 +569,7 @@ def run_batched(args):
                    "sizes": "log-uniform in [2^8, 2^20), seed 3, uniform keys", "max_instance": r["max_n"],
                    "outputs": "sorted keys + stable permutation (uint32)", "storage": "pingpong",
                    "launch": "one CUDA-graph replay per step (persistent cooperative merge kernel)",
-                   "autotune": {k: tuned[k] for k in ("tile_log2", "ms", "cached")},
+                   "autotune": {k: tuned[k] for k in ("tile_log2", "merge_lanes", "ms", "cached")},
                    "l2": "inputs (2 GiB keys) exceed L2; input restored before every replay (untimed)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "batched_vs_plain_loop": {"batched": value / world, "plain_loop": r["loop_rate"],
@@ -1251,7 +1252,7 @@ def batched_summary(r):
         "unit": UNIT, "batched_ms_per_replay": r["ms_per_step"], "replays": r["steps"],
         "plain_loop_ms": r["loop_ms"], "plain_loop_calls": r["count"],
         "launch": "one CUDA-graph replay (persistent cooperative merge kernel) vs one ps_run per instance",
-        "autotune": {k: r["tuned"][k] for k in ("tile_log2", "ms", "cached")},
+        "autotune": {k: r["tuned"][k] for k in ("tile_log2", "merge_lanes", "ms", "cached")},
         "merge_rounds_frac": r["achieved"] / r["peak"],
         "clocks": r["clocks"],
     }

@@ -87,7 +87,9 @@ typedef struct ps_config {
     uint32_t pool_pages; /* VM page-pool size in pages (0: chosen by the library; >= 16) */
     uint32_t flags;      /* PS_FLAG_* below                                          */
     uint32_t key_type;   /* ps_key_type of the keys this context sorts               */
-    uint32_t reserved[2];
+    uint32_t merge_lanes; /* HBM merge kernel: most chunks a CTA prepares ahead
+                             (its search lanes), 1..16 (0: 16); a tuning knob      */
+    uint32_t merge_ctas;  /* HBM merge kernel: CTAs per SM, 1 or 2 (0: 2)          */
 } ps_config;
 
 /* ps_config.flags */

@@ -1,10 +1,13 @@
 """Autotuner for batched sorts.
 
 For a batch shape (instance count, total elements, largest instance) it
-captures the batched sort into a CUDA graph for every candidate of
+captures the batched sort into a CUDA graph for every candidate pair of
 
 * tile_log2          -- on-chip tile capacity 2^10 .. 2^12 (how much of the
                         merge tree is merged in shared memory before the HBM merges)
+* merge_lanes        -- chunks each CTA of the HBM merge kernel prepares ahead
+                        (its search lanes: 4, 8 or 16); few lanes spread a
+                        round's chunks over more CTAs, many hide more latency
 
 times each graph's replays with CUDA events, and keeps the fastest.  Results
 are cached in memory and in a JSON file (``$PS_AUTOTUNE_CACHE``, default
@@ -20,6 +23,7 @@ import os
 import threading
 
 TILE_LOG2 = (10, 11, 12)
+MERGE_LANES = (4, 8, 16)
 _lock = threading.Lock()
 _mem: dict = {}
 
@@ -29,7 +33,7 @@ def _cache_path() -> str:
                           os.path.join(os.path.expanduser("~"), ".cache", "paper_2605_27147_gb300", "autotune.json"))
 
 
-CACHE_VERSION = 3   # entries of other versions (other tuning knobs) are not reused
+CACHE_VERSION = 4   # entries of other versions (other tuning knobs) are not reused
 
 
 def shape_key(gpu: str, count: int, total: int, max_n: int) -> str:
@@ -59,7 +63,7 @@ def _store_file(d: dict) -> None:
 
 def tune(keys, offsets, perm, max_n: int, *, reps: int = 3, stream=None, use_cache: bool = True,
          candidates=None) -> dict:
-    """Best tile_log2 for sorting this batch, with timings.
+    """Best (tile_log2, merge_lanes) for sorting this batch, with timings.
 
     keys / perm: CUDA int32 tensors (keys are restored after tuning);
     offsets: CUDA int64 tensor of count + 1 entries."""
@@ -81,11 +85,11 @@ def tune(keys, offsets, perm, max_n: int, *, reps: int = 3, stream=None, use_cac
                 return dict(disk[key], cached=True)
     stream = stream or torch.cuda.Stream(keys.device)
     pristine = keys.clone()
-    cands = candidates or list(TILE_LOG2)
+    cands = candidates or [(t, l) for t in TILE_LOG2 for l in MERGE_LANES]
     results = []
-    for tile_log2 in cands:
+    for tile_log2, merge_lanes in cands:
         with binding.Context(max_n, want_perm=perm is not None, max_total=total, max_count=count,
-                             tile_log2=tile_log2, stream=stream) as ctx:
+                             tile_log2=tile_log2, merge_lanes=merge_lanes, stream=stream) as ctx:
             g = ctx.graph_batched(keys, offsets, perm)
             times = []
             with torch.cuda.stream(stream):
@@ -99,11 +103,11 @@ def tune(keys, offsets, perm, max_n: int, *, reps: int = 3, stream=None, use_cac
                     if i:
                         times.append(e0.elapsed_time(e1))
             g.close()
-        results.append({"tile_log2": tile_log2, "ms": min(times)})
+        results.append({"tile_log2": tile_log2, "merge_lanes": merge_lanes, "ms": min(times)})
     keys.copy_(pristine)
     torch.cuda.synchronize(keys.device)
     best = min(results, key=lambda r: r["ms"])
-    out = {"tile_log2": best["tile_log2"], "ms": best["ms"],
+    out = {"tile_log2": best["tile_log2"], "merge_lanes": best["merge_lanes"], "ms": best["ms"],
            "trials": results, "shape": key}
     with _lock:
         _mem[key] = out

@@ -46,7 +46,8 @@ class ps_config(ctypes.Structure):
         ("pool_pages", ctypes.c_uint32),
         ("flags", ctypes.c_uint32),
         ("key_type", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint32 * 2),
+        ("merge_lanes", ctypes.c_uint32),
+        ("merge_ctas", ctypes.c_uint32),
     ]
 
 
@@ -233,14 +234,15 @@ class Context:
     def __init__(self, max_n: int, *, mode: int = PS_MODE_PINGPONG, want_perm: bool = True,
                  max_total: int = 0, max_count: int = 0, tile_log2: int = 0, page_log2: int = 0,
                  pool_pages: int = 0, flags: int = 0, key_type: int = PS_KEY_U32, device: int = 0,
-                 stream=None):
+                 stream=None, merge_lanes: int = 0, merge_ctas: int = 0):
         import torch
 
         self.device = device
         self.stream = stream if stream is not None else torch.cuda.current_stream(device)
         cfg = ps_config(mode=mode, want_perm=1 if want_perm else 0, max_n=max_n, max_total=max_total,
                         max_count=max_count, page_log2=page_log2, tile_log2=tile_log2,
-                        pool_pages=pool_pages, flags=flags, key_type=key_type)
+                        pool_pages=pool_pages, flags=flags, key_type=key_type, merge_lanes=merge_lanes,
+                        merge_ctas=merge_ctas)
         h = ctypes.c_void_p()
         _check(lib().ps_create(ctypes.byref(cfg), device, ctypes.c_void_p(self.stream.cuda_stream),
                                ctypes.byref(h)), "ps_create")

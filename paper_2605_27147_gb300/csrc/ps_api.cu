@@ -250,6 +250,7 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
     const uint32_t tile_log2 = cfg->tile_log2 ? cfg->tile_log2 : (uint32_t)ps::TILE_MAX_LOG2;
     if (tile_log2 < 10 || tile_log2 > (uint32_t)ps::TILE_MAX_LOG2) return PS_EINVAL;
     if (device < 0) return PS_EINVAL;
+    if (cfg->merge_lanes > 16 || cfg->merge_ctas > 2) return PS_EINVAL;
 
     ps_ctx* c = new (std::nothrow) ps_ctx();
     if (!c) return PS_ENOMEM;
@@ -276,6 +277,8 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
     c->grid_plan = c->num_sms * 8;
     c->grid_tiles = ps::tiles_max_grid(c->num_sms);
     c->grid_merge = ps::merge_rounds_max_grid(c->num_sms);
+    if (cfg->merge_ctas && c->grid_merge > c->num_sms * (int)cfg->merge_ctas)
+        c->grid_merge = c->num_sms * (int)cfg->merge_ctas;
     c->grid_vm = ps::vm_rounds_max_grid(c->num_sms);
     if (c->grid_vm > 1024) c->grid_vm = 1024;
 
@@ -283,6 +286,7 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
     std::memset(&J, 0, sizeof(J));
     J.tile_cap = 1u << tile_log2;
     J.merge_e = ps::merge_chunk();
+    J.merge_lanes = cfg->merge_lanes;
     J.max_n = cfg->max_n;
     J.max_total = max_total;
     const unsigned long long slot_cap = max_total / 32 + 2ull * c->max_count + 2;

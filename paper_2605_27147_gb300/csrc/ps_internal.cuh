@@ -73,6 +73,7 @@ struct Inst {
     uint32_t max_power;
     uint32_t g_base;              // first entry of the instance's merge map (Job::gmap)
     uint32_t g_span;              // its entries: ceil(4 n / T) when n > T, else 0
+    unsigned long long recip;     // floor((2^64 - 1) / n): divisions by n as a multiply (0 when n = 0)
 };
 
 // Index of the merge with Power p and dyadic point c / 2^p (c odd) in its
@@ -180,6 +181,7 @@ struct Job {
     const uint32_t* desc_mask;  // records: descent bit per position (run detection reads it, not keys)
     uint32_t tile_cap;          // T: largest merge-tree node merged on chip
     uint32_t merge_e;           // outputs per HBM merge chunk (set from the merge kernel's shape)
+    uint32_t merge_lanes;       // search lanes per CTA of the merge kernel (at most its ring size)
     unsigned long long max_n;   // limits the offsets table is checked against
     unsigned long long max_total;
     Inst* inst;

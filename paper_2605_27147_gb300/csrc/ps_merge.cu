@@ -386,7 +386,8 @@ __device__ __noinline__ void search_warp(const Job& J, MergeSmem<NST, BLOCK>& sm
     uint32_t rounds = 0;
     for (int r = 0; r < NPOW; ++r) rounds += sm.round_chunk[r + 1] > sm.round_chunk[r] ? 1u : 0u;
     const uint32_t share = rounds ? (total_chunks + rounds * gridDim.x - 1) / (rounds * gridDim.x) : 0u;
-    const int lanes = (int)min((uint32_t)NSEARCH, max(2u, share));
+    const uint32_t cap = J.merge_lanes ? min(J.merge_lanes, (uint32_t)NSEARCH) : (uint32_t)NSEARCH;
+    const int lanes = (int)min(cap, max(min(2u, cap), share));
     uint32_t state = lane < lanes ? S_CLAIM : S_DONE;
     if (lane >= lanes && lane < NSEARCH) st_vol(&sm.ring_state[lane], RS_END);
     uint32_t c = 0, e = 0, d0 = 0, d1 = 0, round = 0;

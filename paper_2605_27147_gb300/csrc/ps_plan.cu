@@ -68,10 +68,19 @@ __device__ __forceinline__ uint32_t warp_append(uint32_t* counter, bool want)
     return want ? base + __popc(mask & ((1u << lane) - 1u)) : NONE;
 }
 
-// The fixed-point midpoint of the run [s, e) of an instance of n elements.
-__device__ __forceinline__ uint32_t kappa_of(uint32_t s, uint32_t e, uint32_t n)
+// The fixed-point midpoint of the run [s, e) of an instance of n elements:
+// floor(x / n) for x = (s + e) 2^31 < 2^64, without a division.  With
+// recip = floor((2^64 - 1) / n) > (2^64 - 1) / n - 1, the high half of
+// x * recip is at most x / n and more than x / n - 2, so the quotient is it
+// or one of the next two integers, found by comparing the remainder with n.
+__device__ __forceinline__ uint32_t kappa_of(uint32_t s, uint32_t e, uint32_t n, unsigned long long recip)
 {
-    return (uint32_t)((((unsigned long long)s + e) << 31) / n);
+    const unsigned long long x = ((unsigned long long)s + e) << 31;
+    unsigned long long q = __umul64hi(x, recip);
+    unsigned long long r = x - q * n;
+    if (r >= n) { ++q; r -= n; }
+    if (r >= n) ++q;
+    return (uint32_t)q;
 }
 
 // kappa_of(s, e, n) >= X for an integer X <= 2^32, without the division.
@@ -88,9 +97,10 @@ struct NodeRange {
 // Power of boundary t (1 <= t < R) and its point.  rs(x) = start of run x
 // (x <= R, rs(R) = n).
 template <typename RS>
-__device__ __forceinline__ void power_of(RS rs, uint32_t n, uint32_t t, uint32_t& p, uint32_t& c)
+__device__ __forceinline__ void power_of(RS rs, uint32_t n, unsigned long long recip, uint32_t t, uint32_t& p,
+                                         uint32_t& c)
 {
-    const uint32_t X = kappa_of(rs(t - 1), rs(t), n), Y = kappa_of(rs(t), rs(t + 1), n);
+    const uint32_t X = kappa_of(rs(t - 1), rs(t), n, recip), Y = kappa_of(rs(t), rs(t + 1), n, recip);
     p = __clz(X ^ Y) + 1;                 // 1..32
     c = Y >> (32 - p);                    // odd
 }
@@ -98,10 +108,10 @@ __device__ __forceinline__ void power_of(RS rs, uint32_t n, uint32_t t, uint32_t
 // The merge Algorithm 1 makes at boundary t: the runs whose midpoints lie in
 // [(c-1)/2^p, (c+1)/2^p), found by galloping out from t.
 template <typename RS>
-__device__ NodeRange node_range(RS rs, uint32_t R, uint32_t n, uint32_t t)
+__device__ NodeRange node_range(RS rs, uint32_t R, uint32_t n, unsigned long long recip, uint32_t t)
 {
     NodeRange r;
-    power_of(rs, n, t, r.p, r.c);
+    power_of(rs, n, recip, t, r.p, r.c);
     const unsigned long long XL = (unsigned long long)(r.c - 1) << (32 - r.p);
     const unsigned long long XR = (unsigned long long)(r.c + 1) << (32 - r.p);
     auto ge = [&](long long x, unsigned long long X) { return kappa_ge(rs(x), rs(x + 1), n, X); };
@@ -190,7 +200,7 @@ __global__ void __launch_bounds__(PLAN_BLOCK) k_nodes(Job J)
             };
             if (t64 >= 1 && t64 + 1 <= R) {
                 const uint32_t t = (uint32_t)t64;
-                const NodeRange nr = node_range(rs, R, n, t);
+                const NodeRange nr = node_range(rs, R, n, I.recip, t);
                 p = nr.p;
                 J.power[slot] = (uint8_t)p;
                 const uint32_t lo = rs(nr.a), mid = rs(t), hi = rs(nr.b);
@@ -205,8 +215,8 @@ __global__ void __launch_bounds__(PLAN_BLOCK) k_nodes(Job J)
                     want_l = mid - lo <= T || t - nr.a == 1;
                     want_r = hi - mid <= T || nr.b - t == 1;
                     uint32_t pa = 0, pb = 0, ca = 0, cb = 0;
-                    if (nr.a >= 1) power_of(rs, n, nr.a, pa, ca);
-                    if (nr.b + 1 <= R) power_of(rs, n, nr.b, pb, cb);
+                    if (nr.a >= 1) power_of(rs, n, I.recip, nr.a, pa, ca);
+                    if (nr.b + 1 <= R) power_of(rs, n, I.recip, nr.b, pb, cb);
                     uint32_t pidx = NONE;
                     if (pa || pb) pidx = pa > pb ? merge_index(pa, ca) : merge_index(pb, cb);
                     const uint32_t midx = merge_index(p, nr.c);
@@ -422,7 +432,7 @@ __global__ void __launch_bounds__(PLAN_BLOCK) k_node_ranges(Job J, uint32_t q, u
     const uint32_t* rs_g = J.run_start + I.run_base;
     auto rs = [&](long long x) -> uint32_t { return rs_g[x]; };
     for (uint32_t t = 1 + blockIdx.x * blockDim.x + threadIdx.x; t < R; t += gridDim.x * blockDim.x) {
-        const NodeRange nr = node_range(rs, R, n, t);
+        const NodeRange nr = node_range(rs, R, n, I.recip, t);
         out[2 * (t - 1)] = rs_g[nr.a];
         out[2 * (t - 1) + 1] = rs_g[nr.b];
     }

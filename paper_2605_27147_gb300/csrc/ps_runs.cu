@@ -171,6 +171,7 @@ __global__ void __launch_bounds__(1024) k_setup(Job J)
             I.M = 0;
             I.n = n;
             I.minrun = minrun_of(n);
+            I.recip = n ? 0xffffffffffffffffull / n : 0ull;
             I.chunk_base = carry_chunks + cb;
             I.nchunks = nchunks;
             I.max_power = 0;

@@ -28,3 +28,4 @@ def test_cache_file_round_trip(tmp_path, monkeypatch):
 
 def test_candidates_cover_every_tile_size():
     assert set(autotune.TILE_LOG2) == {10, 11, 12}
+    assert set(autotune.MERGE_LANES) == {4, 8, 16}

@@ -130,7 +130,7 @@ def test_config_4_full_4096(oracle_mod):
     doff = _dev_offsets(off)
     tuned = autotune.tune(dk, doff, dp, max_n, stream=stream)
     with binding.Context(max_n, want_perm=True, max_total=total, max_count=count, tile_log2=tuned["tile_log2"],
-                         stream=stream) as c:
+                         merge_lanes=tuned["merge_lanes"], stream=stream) as c:
         g = c.graph_batched(dk, doff, dp)
         torch.cuda.synchronize()
         g.launch()
@@ -175,3 +175,28 @@ def test_batched_many_small_instances(oracle_mod):
             ref = oracle_mod.powersort(parts[q])
             assert np.array_equal(gk[a:b], ref.keys) and np.array_equal(gp[a:b], ref.perm)
         assert st["instances"] == 4096
+
+
+@pytest.mark.parametrize("lanes,ctas", [(1, 1), (4, 2), (16, 1), (2, 0)])
+def test_merge_kernel_knobs_keep_the_result(oracle_mod, lanes, ctas):
+    """The merge kernel's tuning knobs (search lanes per CTA, CTAs per SM)
+    change its schedule only: every instance still equals the oracle."""
+    from paper_2605_27147_gb300 import binding
+
+    rng = np.random.RandomState(21)
+    sizes = [int(x) for x in np.floor(2.0 ** (8 + 11 * rng.rand(120)))]
+    parts = [inputs.make(("uniform", "zipf", "runs", "few")[i % 4], n, 300 + i) for i, n in enumerate(sizes)]
+    keys = np.concatenate(parts)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    dk, doff = to_dev(keys), _dev_offsets(off)
+    dp = torch.empty(keys.size, dtype=torch.int32, device="cuda")
+    with binding.Context(max(sizes), want_perm=True, max_total=keys.size, max_count=len(sizes),
+                         merge_lanes=lanes, merge_ctas=ctas) as c:
+        st = c.run_batched(dk, doff, dp, stats=True)
+        gk, gp = to_host(dk), to_host(dp)
+        for q, part in enumerate(parts):
+            a, b = int(off[q]), int(off[q + 1])
+            ref = oracle_mod.powersort(part)
+            assert np.array_equal(gk[a:b], ref.keys) and np.array_equal(gp[a:b], ref.perm), q
+        assert st["global_nodes"] > 0
+        c.check_guards()
