@@ -595,17 +595,25 @@ __device__ __noinline__ void consumer_warps(const Job& J, MergeSmem<NST, BLOCK>&
         const uint32_t* Bk = &sm.in_k[s][S.sk[1]];
         const uint32_t* Ap = &sm.in_p[s][S.sp[0]];
         const uint32_t* Bp = &sm.in_p[s][S.sp[1]];
-        if (tid == 0) bulk_wait_read_all();         // the previous output has left the staging arrays
-        consumers_sync<BLOCK>();
+        // the split of this thread's outputs reads only the stage, so it runs
+        // while the previous chunk's store may still be reading the output
+        // staging arrays
         const uint32_t x0 = tid * MERGE_K;
+        uint32_t ia = 0, ib = 0, va = 0, vb = 0;
         if (x0 < cnt) {
             uint32_t lo = x0 > nb ? x0 - nb : 0u, hi = min(x0, na);
             while (lo < hi) {
                 const uint32_t mid = (lo + hi) >> 1;
                 if (Ak[mid] <= Bk[x0 - 1 - mid]) lo = mid + 1; else hi = mid;
             }
-            uint32_t ia = lo, ib = x0 - lo;
-            uint32_t va = ia < na ? Ak[ia] : 0xffffffffu, vb = ib < nb ? Bk[ib] : 0xffffffffu;
+            ia = lo;
+            ib = x0 - lo;
+            va = ia < na ? Ak[ia] : 0xffffffffu;
+            vb = ib < nb ? Bk[ib] : 0xffffffffu;
+        }
+        if (tid == 0) bulk_wait_read_all();         // the previous output has left the staging arrays
+        consumers_sync<BLOCK>();
+        if (x0 < cnt) {
             uint32_t* outk = &sm.out_k[sok + x0];
             uint32_t* outp = &sm.out_p[sop + x0];
             const uint32_t nout = min(cnt - x0, (uint32_t)MERGE_K);
