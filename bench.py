@@ -194,11 +194,13 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
-def traffic_from_profile(workload):
-    """dram bytes per launch of k_merge_rounds from the committed ncu summary,
+def traffic_from_profile(workload, storage="pingpong"):
+    """DRAM bytes per launch of the merge phase's kernels (k_merge_rounds, or
+    k_vm_rounds + k_vm_copy with VM storage) from the committed ncu summary,
     if it was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", f"merge_rounds_{workload}.txt")
-    src = os.path.join(ROOT, "paper_2605_27147_gb300", "csrc", "ps_merge.cu")
+    name, kernel_src = ("merge_rounds", "ps_merge.cu") if storage == "pingpong" else ("vm_rounds", "ps_vm.cu")
+    path = os.path.join(ROOT, "profiles", f"{name}_{workload}.txt")
+    src = os.path.join(ROOT, "paper_2605_27147_gb300", "csrc", kernel_src)
     try:
         digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         vals = {}
@@ -1168,8 +1170,7 @@ def main():
 
     peak, peak_kind = peaks()
     achieved = merge_bytes / (merge_ms / 1000.0) / 1e9
-    # the committed ncu summary covers the Pingpong merge kernel only
-    traffic = traffic_from_profile(args.workload) if args.storage == "pingpong" else None
+    traffic = traffic_from_profile(args.workload, args.storage)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,

@@ -172,6 +172,18 @@ __global__ void __launch_bounds__(PLAN_BLOCK) k_nodes(Job J)
     const unsigned long long total = J.ctr->total_slots;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     const uint32_t T = J.tile_cap;
+    // lane 0: the instance whose merge cost and largest power this warp accumulates
+    uint32_t acc_q = NONE, acc_p = 0;
+    unsigned long long acc_m = 0;
+    auto flush = [&]() {
+        if (acc_q != NONE) {
+            if (acc_m) atomicAdd(&J.inst[acc_q].M, acc_m);
+            if (acc_p) atomicMax(&J.inst[acc_q].max_power, acc_p);
+        }
+        acc_q = NONE;
+        acc_m = 0;
+        acc_p = 0;
+    };
     for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < total; base += stride) {
         const long long w0 = (long long)base - NODE_HALO;   // global slot of rw[0]
         __syncthreads();                                     // the previous pass's probes are done
@@ -254,8 +266,11 @@ __global__ void __launch_bounds__(PLAN_BLOCK) k_nodes(Job J)
             if (at < J.tile_cap_items) J.tiles[at] = TileItem{q, 0u, J.inst[q].runs, NONE, 0u, 0u};
             else set_error(J.ctr, DERR_INTERNAL, 24);
         }
-        // merge cost and largest power, per instance (warp-aggregated when
-        // the whole warp works on one instance)
+        // merge cost and largest power, per instance: summed over the warp
+        // when the whole warp works on one instance, and over the warp's
+        // passes while the instance stays the same (one atomic per warp and
+        // instance: every warp updating the same instance at every pass
+        // queued on one cache line)
         const uint32_t q0 = __shfl_sync(FULL, q, 0);
         if (__all_sync(FULL, q == q0) && q0 != NONE) {
             unsigned long long sum = cost;
@@ -266,14 +281,19 @@ __global__ void __launch_bounds__(PLAN_BLOCK) k_nodes(Job J)
                 pm = max(pm, __shfl_xor_sync(FULL, pm, o));
             }
             if ((threadIdx.x & 31) == 0) {
-                if (sum) atomicAdd(&J.inst[q0].M, sum);
-                if (pm) atomicMax(&J.inst[q0].max_power, pm);
+                if (acc_q != q0) {
+                    flush();
+                    acc_q = q0;
+                }
+                acc_m += sum;
+                acc_p = max(acc_p, pm);
             }
         } else if (q != NONE) {
             if (cost) atomicAdd(&J.inst[q].M, cost);
             if (p) atomicMax(&J.inst[q].max_power, p);
         }
     }
+    if ((threadIdx.x & 31) == 0) flush();
 }
 
 // Depth (number of ancestors) of every HBM merge, by walking the parent
