@@ -14,7 +14,7 @@ struct ps_ctx {
     int device;
     cudaStream_t stream;
     int num_sms;
-    int grid_runs, grid_plan, grid_tiles, grid_vm;
+    int grid_runs, grid_plan, grid_nodes, grid_tiles, grid_vm;
     int grid_merge;
     unsigned long long max_total;
     uint32_t max_count;
@@ -124,7 +124,7 @@ ps_status enqueue(ps_ctx* c, const ps::Job& J)
     if (J.key_type != PS_KEY_U32 && ps::launch_key_map(J, true, c->grid_runs, s) != cudaSuccess) return PS_ECUDA;
     if (!mark(1)) return PS_ECUDA;
     if (ps::launch_runs(J, c->grid_runs, s) != cudaSuccess || !mark(2)) return PS_ECUDA;
-    if (ps::launch_plan(J, c->grid_plan, s) != cudaSuccess || !mark(3)) return PS_ECUDA;
+    if (ps::launch_plan(J, c->grid_plan, c->grid_nodes, s) != cudaSuccess || !mark(3)) return PS_ECUDA;
     if (ps::launch_tiles(J, c->grid_tiles, s) != cudaSuccess || !mark(4)) return PS_ECUDA;
     if (J.vm) {
         if (ps::launch_vm(J, c->grid_vm, s) != cudaSuccess || !mark(5)) return PS_ECUDA;
@@ -275,6 +275,7 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
     c->num_sms = prop.multiProcessorCount;
     c->grid_runs = std::min(c->num_sms * ps::RUN_GRID_PER_SM, ps::RUN_RANGES_MAX);
     c->grid_plan = c->num_sms * 8;
+    c->grid_nodes = ps::nodes_max_grid(c->num_sms);
     c->grid_tiles = ps::tiles_max_grid(c->num_sms);
     c->grid_merge = ps::merge_rounds_max_grid(c->num_sms);
     if (cfg->merge_ctas && c->grid_merge > c->num_sms * (int)cfg->merge_ctas)

@@ -446,7 +446,8 @@ __device__ __forceinline__ uint32_t find_inst(uint32_t count, unsigned long long
 cudaError_t launch_setup(const Job& J, cudaStream_t s);
 cudaError_t launch_runs(const Job& J, int grid, cudaStream_t s);
 uint32_t merge_chunk();
-cudaError_t launch_plan(const Job& J, int grid, cudaStream_t s);
+cudaError_t launch_plan(const Job& J, int grid, int nodes_grid, cudaStream_t s);
+int nodes_max_grid(int num_sms);
 cudaError_t launch_node_ranges(const Job& J, uint32_t q, uint32_t nbound, uint32_t* out, cudaStream_t s);
 cudaError_t launch_tiles(const Job& J, int grid, cudaStream_t s);
 cudaError_t launch_merge_rounds(const Job& J, int grid, cudaStream_t s);

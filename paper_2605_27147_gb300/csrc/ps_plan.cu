@@ -49,6 +49,12 @@ constexpr uint32_t FULL = 0xffffffffu;
 
 constexpr int NODE_HALO = 768;                          // k_nodes: staged run starts on each side
 constexpr int NODE_WIN = PLAN_BLOCK + 2 * NODE_HALO + 2;
+// k_nodes buffers the HBM merges and tiles it finds in shared memory and
+// appends them to the global lists in bulk: a pass adds at most PLAN_BLOCK
+// merges and 2 PLAN_BLOCK tiles, so the buffers are flushed whenever another
+// pass could overflow them (for unsorted data about once per block)
+constexpr int NODE_BUF_G = PLAN_BLOCK + 64;
+constexpr int NODE_BUF_T = 2 * PLAN_BLOCK + 128;
 
 __device__ __forceinline__ uint32_t inst_of_slot(const Job& J, unsigned long long slot)
 {
@@ -166,9 +172,49 @@ __global__ void __launch_bounds__(PLAN_BLOCK) k_nodes(Job J)
     // to L2
     __shared__ uint32_t rw[NODE_WIN];
     __shared__ uint32_t s_err;
-    if (threadIdx.x == 0) s_err = *(volatile uint32_t*)&J.ctr->error;
+    // buffered HBM merges (inst, t, a, b, power, midx, pidx) and tiles (inst,
+    // r0, r1, buffered index of the parent merge or NONE), their counts and
+    // the global places of a flush
+    __shared__ uint32_t sg[NODE_BUF_G][7];
+    __shared__ uint32_t st[NODE_BUF_T][4];
+    __shared__ uint32_t s_ng, s_nt, s_bg, s_bt;
+    if (threadIdx.x == 0) {
+        s_err = *(volatile uint32_t*)&J.ctr->error;
+        s_ng = 0;
+        s_nt = 0;
+    }
     __syncthreads();
     if (s_err) return;                                       // the whole block leaves together
+    // the buffered items to the global lists: one atomic per list
+    auto flush_items = [&]() {
+        if (threadIdx.x == 0) {
+            s_bg = s_ng ? atomicAdd(&J.ctr->n_gnodes, s_ng) : 0u;
+            s_bt = s_nt ? atomicAdd(&J.ctr->n_tiles, s_nt) : 0u;
+        }
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < s_ng; i += PLAN_BLOCK) {
+            const uint32_t g = s_bg + i;
+            const uint32_t* b = sg[i];
+            if (g < J.gnode_cap) {
+                J.gnodes[g] = GNode{b[0], b[1], b[2], b[3], b[4], 0u, b[5], b[6]};
+                J.gmap[J.inst[b[0]].g_base + b[5]] = g;
+            } else {
+                set_error(J.ctr, DERR_INTERNAL, 22);
+            }
+        }
+        for (uint32_t j = threadIdx.x; j < s_nt; j += PLAN_BLOCK) {
+            const uint32_t at = s_bt + j;
+            const uint32_t* b = st[j];
+            if (at < J.tile_cap_items) J.tiles[at] = TileItem{b[0], b[1], b[2], b[3] == NONE ? NONE : s_bg + b[3], 0u, 0u};
+            else set_error(J.ctr, DERR_INTERNAL, 20);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_ng = 0;
+            s_nt = 0;
+        }
+        __syncthreads();
+    };
     const unsigned long long total = J.ctr->total_slots;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     const uint32_t T = J.tile_cap;
@@ -242,30 +288,28 @@ __global__ void __launch_bounds__(PLAN_BLOCK) k_nodes(Job J)
                 want_root = true;                      // the whole instance is one tile
             }
         }
-        const uint32_t g = warp_append(&J.ctr->n_gnodes, want_g);
+        // this pass's items into the block's buffers (they have room: see
+        // the flush below)
+        uint32_t lg = NONE;
         if (want_g) {
-            if (g < J.gnode_cap) {
-                J.gnodes[g] = gn;
-                J.gmap[J.inst[q].g_base + gn.midx] = g;
-            } else {
-                set_error(J.ctr, DERR_INTERNAL, 22);
-            }
+            lg = atomicAdd(&s_ng, 1u);
+            uint32_t* b = sg[lg];
+            b[0] = q; b[1] = gn.t; b[2] = gn.a; b[3] = gn.b; b[4] = gn.power; b[5] = gn.midx; b[6] = gn.pidx;
         }
-        uint32_t at = warp_append(&J.ctr->n_tiles, want_l);
         if (want_l) {
-            if (at < J.tile_cap_items) J.tiles[at] = TileItem{q, gn.a, gn.t, g, 0u, 0u};
-            else set_error(J.ctr, DERR_INTERNAL, 20);
+            uint32_t* b = st[atomicAdd(&s_nt, 1u)];
+            b[0] = q; b[1] = gn.a; b[2] = gn.t; b[3] = lg;
         }
-        at = warp_append(&J.ctr->n_tiles, want_r);
         if (want_r) {
-            if (at < J.tile_cap_items) J.tiles[at] = TileItem{q, gn.t, gn.b, g, 0u, 0u};
-            else set_error(J.ctr, DERR_INTERNAL, 21);
+            uint32_t* b = st[atomicAdd(&s_nt, 1u)];
+            b[0] = q; b[1] = gn.t; b[2] = gn.b; b[3] = lg;
         }
-        at = warp_append(&J.ctr->n_tiles, want_root);
         if (want_root) {
-            if (at < J.tile_cap_items) J.tiles[at] = TileItem{q, 0u, J.inst[q].runs, NONE, 0u, 0u};
-            else set_error(J.ctr, DERR_INTERNAL, 24);
+            uint32_t* b = st[atomicAdd(&s_nt, 1u)];
+            b[0] = q; b[1] = 0u; b[2] = J.inst[q].runs; b[3] = NONE;
         }
+        __syncthreads();
+        if (s_ng > (uint32_t)(NODE_BUF_G - PLAN_BLOCK) || s_nt > (uint32_t)(NODE_BUF_T - 2 * PLAN_BLOCK)) flush_items();
         // merge cost and largest power, per instance: summed over the warp
         // when the whole warp works on one instance, and over the warp's
         // passes while the instance stays the same (one atomic per warp and
@@ -294,6 +338,8 @@ __global__ void __launch_bounds__(PLAN_BLOCK) k_nodes(Job J)
         }
     }
     if ((threadIdx.x & 31) == 0) flush();
+    __syncthreads();
+    if (s_ng || s_nt) flush_items();
 }
 
 // Depth (number of ancestors) of every HBM merge, by walking the parent
@@ -493,9 +539,17 @@ cudaError_t launch_finish(const Job& J, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_plan(const Job& J, int grid, cudaStream_t s)
+int nodes_max_grid(int num_sms)
 {
-    k_nodes<<<grid, PLAN_BLOCK, 0, s>>>(J);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_nodes, PLAN_BLOCK, 0);
+    return num_sms * (per_sm > 0 ? per_sm : 1);
+}
+
+cudaError_t launch_plan(const Job& J, int grid, int nodes_grid, cudaStream_t s)
+{
+    // k_nodes: every CTA resident at once (its passes are equal shares)
+    k_nodes<<<nodes_grid, PLAN_BLOCK, 0, s>>>(J);
     k_depth<<<grid, PLAN_BLOCK, 0, s>>>(J);
     k_bucket_scan<<<1, 32, 0, s>>>(J);
     k_bucket<<<grid, PLAN_BLOCK, 0, s>>>(J);
