@@ -40,6 +40,8 @@ struct ps_ctx {
     uint32_t* rec_big;          //   the groups larger than one CTA's shared memory
     uint32_t rec_big_cap;
     int grid_rec_big;           //   cooperative grid of their merge passes
+    unsigned long long* rec_off; //  two-word rows: the big groups as instances of
+    ps_ctx* rec_inner;          //   a batched 32-bit sort in this inner context
 };
 
 namespace {
@@ -91,6 +93,8 @@ ps_status dev_alloc(ps_ctx* c, T** p, size_t count)
 
 void free_all(ps_ctx* c)
 {
+    if (c->rec_inner) ::ps_destroy(c->rec_inner);
+    c->rec_inner = nullptr;
     if (c->timing)
         for (cudaEvent_t& e : c->ev)
             if (e) cudaEventDestroy(e);
@@ -412,6 +416,21 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
         if (st == PS_OK) st = dev_alloc(c, &c->rec_big, 2ull * c->rec_big_cap);
         if (st == PS_OK) st = dev_alloc(c, &c->rec_rows, 2ull * cfg->max_n);
         c->grid_rec_big = ps::records_fix_big_grid(c->num_sms);
+        if (st == PS_OK && cfg->mode == PS_MODE_PINGPONG) {
+            // two-word rows (64-bit keys): the big tie groups' last words are
+            // sorted as one batch of 32-bit instances
+            st = dev_alloc(c, &c->rec_off, (size_t)c->rec_big_cap + 1);
+            ps_config ic{};
+            ic.mode = PS_MODE_PINGPONG;
+            ic.want_perm = 1;
+            ic.max_n = cfg->max_n;
+            ic.max_total = cfg->max_n;
+            ic.max_count = c->rec_big_cap;
+            ic.merge_lanes = cfg->merge_lanes;
+            ic.merge_ctas = cfg->merge_ctas;
+            if (st == PS_OK) st = ps_create(&ic, device, cuda_stream, &c->rec_inner);
+            if (st == PS_OK) c->scratch_bytes += c->rec_inner->scratch_bytes;
+        }
     }
     if (st == PS_OK && (cfg->flags & PS_FLAG_HOST_IO)) {
         st = dev_alloc(c, &c->io_keys, max_total);
@@ -624,12 +643,28 @@ ps_status records_async(ps_ctx* ctx, const uint32_t* d_rec, uint32_t words, uint
     ctx->base.desc_mask = nullptr;
     if (st != PS_OK) return st;
     // packed fix-up words: rec_tmp and rec_rows (free until the row gather)
+    const bool nested = words == 2 && ctx->rec_inner;
     if (ps::launch_records_fix(d_rec, words, n, ctx->rec_keys, d_perm, ctx->rec_tmp,
                                reinterpret_cast<unsigned long long*>(ctx->rec_tmp),
                                reinterpret_cast<unsigned long long*>(ctx->rec_rows), ctx->rec_groups,
                                ctx->rec_group_cap, ctx->rec_big, ctx->rec_big_cap, C, grid, ctx->grid_rec_big,
-                               s) != cudaSuccess)
+                               nested, s) != cudaSuccess)
         return PS_ECUDA;
+    if (nested) {
+        // the big groups' last words (rec_tmp[0, n)) sorted with their local
+        // permutation (rec_tmp[n, 2n)); their entries kept in rec_rows
+        uint32_t* keys2 = ctx->rec_tmp;
+        uint32_t* perm2 = ctx->rec_tmp + ctx->cfg.max_n;
+        if (ps::launch_records_nested_prep(d_rec, words, d_perm, ctx->rec_big, ctx->rec_big_cap, ctx->rec_off, keys2,
+                                           ctx->rec_rows, C, grid, s) != cudaSuccess)
+            return PS_ECUDA;
+        st = ps_run_batched(ctx->rec_inner, keys2, perm2, reinterpret_cast<const uint64_t*>(ctx->rec_off),
+                            ctx->rec_big_cap, nullptr);
+        if (st != PS_OK) return st;
+        if (ps::launch_records_nested_apply(words, d_perm, ctx->rec_big, ctx->rec_big_cap, ctx->rec_off, perm2,
+                                            ctx->rec_rows, C, ctx->rec_inner->base.ctr, grid, s) != cudaSuccess)
+            return PS_ECUDA;
+    }
     if (d_rec_out && ps::launch_gather_rows(d_perm, nullptr, 0, n, ctx->max_total, d_rec, d_rec_out, words * 4u, C,
                                             grid, s) != cudaSuccess)
         return PS_ECUDA;
@@ -637,7 +672,7 @@ ps_status records_async(ps_ctx* ctx, const uint32_t* d_rec, uint32_t words, uint
 }
 
 // After an enqueued record sort: surface its errors, and the statistics.
-ps_status records_finish(ps_ctx* ctx, ps_stats* stats, uint32_t extra_launches)
+ps_status records_finish(ps_ctx* ctx, ps_stats* stats, uint32_t extra_launches, bool nested)
 {
     if (cudaMemcpyAsync(&ctx->h_ctr->error, &ctx->base.ctr->error, sizeof(uint32_t), cudaMemcpyDeviceToHost,
                         ctx->stream) != cudaSuccess)
@@ -649,7 +684,10 @@ ps_status records_finish(ps_ctx* ctx, ps_stats* stats, uint32_t extra_launches)
     if (cudaMemcpy(ctx->h_inst, ctx->base.inst, sizeof(ps::Inst), cudaMemcpyDeviceToHost) != cudaSuccess)
         return PS_ECUDA;
     stats->minrun = ctx->h_inst->minrun;
-    stats->launches += 5u + extra_launches;   // scan, window keys, groups, fix-up, big groups
+    // scan, window keys, groups, fix-up, and the big groups' merge passes
+    // -- or, for two-word rows, their nested sort (offsets, gather, the
+    // batched sort, apply)
+    stats->launches += 4u + (nested ? 3u + LAUNCHES_PER_CALL : 1u) + extra_launches;
     return PS_OK;
 }
 
@@ -673,7 +711,7 @@ PS_API ps_status ps_sort_records(ps_ctx* ctx, const uint32_t* d_rec, uint32_t wo
     DeviceGuard g(ctx->device);
     ps_status st = records_async(ctx, d_rec, words, n, d_perm, d_rec_out);
     if (st != PS_OK) return st;
-    return records_finish(ctx, stats, d_rec_out ? 1u : 0u);
+    return records_finish(ctx, stats, d_rec_out ? 1u : 0u, words == 2 && ctx->rec_inner);
 }
 
 PS_API ps_status ps_sort_keys64(ps_ctx* ctx, uint64_t* d_keys, uint64_t n, uint32_t* d_perm, uint32_t key_type,
@@ -694,7 +732,7 @@ PS_API ps_status ps_sort_keys64(ps_ctx* ctx, uint64_t* d_keys, uint64_t n, uint3
     if (st != PS_OK) return st;
     if (ps::launch_key64(false, ctx->rec_rows, d_keys, n, key_type, grid, ctx->stream) != cudaSuccess)
         return PS_ECUDA;
-    return records_finish(ctx, stats, 3u);   // the row gather and the two maps
+    return records_finish(ctx, stats, 3u, ctx->rec_inner != nullptr);   // the row gather and the two maps
 }
 
 PS_API ps_status ps_gather_rows(ps_ctx* ctx, const uint32_t* d_perm, const uint64_t* d_offsets, uint32_t count,

@@ -460,8 +460,14 @@ cudaError_t launch_records_prepare(const uint32_t* rec, uint32_t W, unsigned lon
 cudaError_t launch_records_fix(const uint32_t* rec, uint32_t W, unsigned long long n, const uint32_t* keys,
                                uint32_t* perm, uint32_t* tmp, unsigned long long* comp, unsigned long long* comp2,
                                uint32_t* groups, uint32_t cap, uint32_t* big, uint32_t big_cap, Ctr* C, int grid,
-                               int coop_grid, cudaStream_t s);
+                               int coop_grid, bool nested, cudaStream_t s);
 int records_fix_big_grid(int num_sms);
+cudaError_t launch_records_nested_prep(const uint32_t* rec, uint32_t W, const uint32_t* perm, const uint32_t* big,
+                                       uint32_t big_cap, unsigned long long* off, uint32_t* keys2, uint32_t* save,
+                                       Ctr* C, int grid, cudaStream_t s);
+cudaError_t launch_records_nested_apply(uint32_t W, uint32_t* perm, const uint32_t* big, uint32_t big_cap,
+                                        const unsigned long long* off, const uint32_t* perm2, const uint32_t* save,
+                                        Ctr* C, const Ctr* C2, int grid, cudaStream_t s);
 cudaError_t launch_key64(bool in, const void* rows, void* keys, unsigned long long n, uint32_t type, int grid,
                          cudaStream_t s);
 cudaError_t launch_wait_probe(Ctr* C, cudaStream_t s);

@@ -24,6 +24,11 @@
 //      the whole grid (a grid barrier between passes).  With one word left
 //      to compare (64-bit keys: the low word) entries are packed as (word <<
 //      32 | index) and compared directly, without reading rows;
+//      With two-word rows whose first words tie in groups larger than
+//      REC_SMEM (64-bit keys of a small range: the window is the high word,
+//      one word is left), the merge passes are replaced: the library's own
+//      batched 32-bit sort (a second, internal context) orders every such
+//      group's last words, stably, in one call (k_rec_nested_*);
 //   5. the rows move once, through the permutation (ps_gather_rows' kernel),
 //      instead of at every merge.
 #include "ps_internal.cuh"
@@ -280,7 +285,8 @@ __device__ void fix_block(const uint32_t* rec, uint32_t W, uint32_t w0, uint32_t
 // over all CTAs (their merge passes follow in k_rec_fix_big).
 __global__ void __launch_bounds__(REC_BLOCK) k_rec_fix(const uint32_t* rec, uint32_t W, uint32_t* perm,
                                                        unsigned long long* comp, const uint32_t* groups,
-                                                       uint32_t cap, const uint32_t* big, uint32_t big_cap, Ctr* C)
+                                                       uint32_t cap, const uint32_t* big, uint32_t big_cap, Ctr* C,
+                                                       uint32_t nested)
 {
     __shared__ uint32_t s[REC_SMEM];
     __shared__ unsigned long long s64[REC_SMEM];
@@ -292,7 +298,9 @@ __global__ void __launch_bounds__(REC_BLOCK) k_rec_fix(const uint32_t* rec, uint
         const uint32_t a = groups[2 * gi], g = groups[2 * gi + 1] - a;
         if (g <= REC_SMEM) fix_block(rec, W, w0, perm, nullptr, a, g, s, s64);
     }
-    const uint32_t nbig = min(*(volatile const uint32_t*)&C->rec_nbig, big_cap);
+    // big groups: blocks for the merge passes, unless the nested sort
+    // orders them (one word left to compare)
+    const uint32_t nbig = (nested && w0 + 1 == W) ? 0u : min(*(volatile const uint32_t*)&C->rec_nbig, big_cap);
     for (uint32_t b = 0; b < nbig; ++b) {
         const uint32_t a = big[2 * b], g = big[2 * b + 1] - a;
         const uint32_t nblk = (g + REC_SMEM - 1) / REC_SMEM;
@@ -376,6 +384,127 @@ __global__ void __launch_bounds__(REC_BLOCK) k_rec_fix_big(const uint32_t* rec, 
     }
 }
 
+// The nested sort of the big groups (one word left, w0 = W - 1): the number
+// of groups it orders (0 when there is nothing to fix up).
+__device__ __forceinline__ uint32_t nested_groups(uint32_t W, uint32_t big_cap, Ctr* C)
+{
+    const uint32_t L = *(volatile const uint32_t*)&C->rec_lcp;
+    if (L >= W || L + 2 != W || *(volatile uint32_t*)&C->error) return 0u;
+    return min(*(volatile const uint32_t*)&C->rec_nbig, big_cap);
+}
+
+// One CTA: the nested sort's instance offsets -- the big groups in list
+// order, then empty instances up to big_cap.
+__global__ void __launch_bounds__(1024) k_rec_nested_offsets(uint32_t W, const uint32_t* big, uint32_t big_cap,
+                                                              unsigned long long* off, Ctr* C)
+{
+    __shared__ unsigned long long ws[32];
+    __shared__ unsigned long long carry;
+    const uint32_t nbig = nested_groups(W, big_cap, C);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (uint32_t b0 = 0; b0 < big_cap; b0 += 1024) {
+        const uint32_t b = b0 + threadIdx.x;
+        const unsigned long long v = b < nbig ? (unsigned long long)(big[2 * b + 1] - big[2 * b]) : 0ull;
+        unsigned long long x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) ws[warp] = x;
+        __syncthreads();
+        unsigned long long before = carry, tot = 0;
+        for (int w = 0; w < 32; ++w) {
+            if (w < warp) before += ws[w];
+            tot += ws[w];
+        }
+        if (b < big_cap) off[b] = before + x - v;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) off[big_cap] = carry;
+}
+
+// The big group holding entry j of the nested sort (its offsets
+// non-decreasing): the last b < nbig with off[b] <= j.
+__device__ __forceinline__ uint32_t nested_group_of(const unsigned long long* off, uint32_t nbig, unsigned long long j)
+{
+    uint32_t lo = 0, hi = nbig;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (off[mid] <= j) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// The nested sort's keys: the last word of every big group's rows in the
+// group's current (input) order; and the entries themselves, kept.
+__global__ void __launch_bounds__(REC_BLOCK) k_rec_nested_gather(const uint32_t* rec, uint32_t W, const uint32_t* perm,
+                                                                 const uint32_t* big, uint32_t big_cap,
+                                                                 const unsigned long long* off, uint32_t* keys2,
+                                                                 uint32_t* save, Ctr* C)
+{
+    const uint32_t nbig = nested_groups(W, big_cap, C);
+    if (!nbig) return;
+    const unsigned long long total = off[nbig];
+    for (unsigned long long j = (unsigned long long)blockIdx.x * REC_BLOCK + threadIdx.x; j < total;
+         j += (unsigned long long)gridDim.x * REC_BLOCK) {
+        const uint32_t b = nested_group_of(off, nbig, j);
+        const uint32_t p = perm[big[2 * b] + (uint32_t)(j - off[b])];
+        keys2[j] = __ldg(rec + (size_t)p * W + (W - 1));
+        save[j] = p;
+    }
+}
+
+// Every big group's entries in the nested sort's order (its permutation is
+// local to the group).  An error of the nested sort (its own counters, C2)
+// becomes this sort's error and leaves perm as the window sort left it.
+__global__ void __launch_bounds__(REC_BLOCK) k_rec_nested_apply(uint32_t W, uint32_t* perm, const uint32_t* big,
+                                                                uint32_t big_cap, const unsigned long long* off,
+                                                                const uint32_t* perm2, const uint32_t* save, Ctr* C,
+                                                                const Ctr* C2)
+{
+    const uint32_t nbig = nested_groups(W, big_cap, C);
+    if (!nbig) return;
+    const uint32_t e2 = *(volatile const uint32_t*)&C2->error;
+    if (e2) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_error(C, e2, 83);
+        return;
+    }
+    const unsigned long long total = off[nbig];
+    for (unsigned long long j = (unsigned long long)blockIdx.x * REC_BLOCK + threadIdx.x; j < total;
+         j += (unsigned long long)gridDim.x * REC_BLOCK) {
+        const uint32_t b = nested_group_of(off, nbig, j);
+        const uint32_t g = big[2 * b + 1] - big[2 * b];
+        const uint32_t local = perm2[j];
+        if (local >= g) {
+            set_error(C, DERR_INTERNAL, 82);
+            continue;
+        }
+        perm[big[2 * b] + (uint32_t)(j - off[b])] = save[off[b] + local];
+    }
+}
+
+cudaError_t launch_records_nested_prep(const uint32_t* rec, uint32_t W, const uint32_t* perm, const uint32_t* big,
+                                       uint32_t big_cap, unsigned long long* off, uint32_t* keys2, uint32_t* save,
+                                       Ctr* C, int grid, cudaStream_t s)
+{
+    k_rec_nested_offsets<<<1, 1024, 0, s>>>(W, big, big_cap, off, C);
+    k_rec_nested_gather<<<grid, REC_BLOCK, 0, s>>>(rec, W, perm, big, big_cap, off, keys2, save, C);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_records_nested_apply(uint32_t W, uint32_t* perm, const uint32_t* big, uint32_t big_cap,
+                                        const unsigned long long* off, const uint32_t* perm2, const uint32_t* save,
+                                        Ctr* C, const Ctr* C2, int grid, cudaStream_t s)
+{
+    k_rec_nested_apply<<<grid, REC_BLOCK, 0, s>>>(W, perm, big, big_cap, off, perm2, save, C, C2);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_records_prepare(const uint32_t* rec, uint32_t W, unsigned long long n, uint32_t* mask,
                                    uint32_t* keys, Ctr* C, int grid, cudaStream_t s)
 {
@@ -395,10 +524,11 @@ cudaError_t launch_records_prepare(const uint32_t* rec, uint32_t W, unsigned lon
 cudaError_t launch_records_fix(const uint32_t* rec, uint32_t W, unsigned long long n, const uint32_t* keys,
                                uint32_t* perm, uint32_t* tmp, unsigned long long* comp, unsigned long long* comp2,
                                uint32_t* groups, uint32_t cap, uint32_t* big, uint32_t big_cap, Ctr* C, int grid,
-                               int coop_grid, cudaStream_t s)
+                               int coop_grid, bool nested, cudaStream_t s)
 {
     k_rec_groups<<<grid, REC_BLOCK, 0, s>>>(keys, W, n, groups, cap, big, big_cap, C);
-    k_rec_fix<<<grid, REC_BLOCK, 0, s>>>(rec, W, perm, comp, groups, cap, big, big_cap, C);
+    k_rec_fix<<<grid, REC_BLOCK, 0, s>>>(rec, W, perm, comp, groups, cap, big, big_cap, C, nested ? 1u : 0u);
+    if (nested) return cudaGetLastError();       // the big groups go to the nested sort
     void* args[] = {(void*)&rec, (void*)&W,   (void*)&perm,    (void*)&tmp, (void*)&comp,
                     (void*)&comp2, (void*)&big, (void*)&big_cap, (void*)&C};
     return cudaLaunchCooperativeKernel((const void*)k_rec_fix_big, dim3(coop_grid), dim3(REC_BLOCK), args, 0, s);

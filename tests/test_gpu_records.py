@@ -79,6 +79,23 @@ def test_records_large_tie_groups(rctx, oracle_mod):
     check(rctx, oracle_mod, rec)
 
 
+def test_records_two_words_many_big_groups(rctx, oracle_mod):
+    # two-word rows: the first word leaves 40 groups of 2049 .. 9000 rows (the
+    # nested batched sort of their last words) between groups of a few rows
+    # (the shared-memory fix-up); the last word takes 5 values, so ties inside
+    # a group show the nested sort's stability in the permutation
+    u = inputs.uniform(300000, 17)
+    sizes = [2049 + int(x) % 6952 for x in u[:40]] + [1 + int(x) % 40 for x in u[40:1040]]
+    word0 = np.repeat(np.arange(len(sizes), dtype=np.uint32) * 7, sizes)
+    n = word0.size
+    order = np.argsort(inputs.uniform(n, 18), kind="stable")
+    rec = np.stack([word0[order], inputs.uniform(n, 19) % 5], axis=1).astype(np.uint32)
+    for _ in range(2):   # twice on one context: the group tables start over
+        check(rctx, oracle_mod, rec)
+    # then a call with no big group at all
+    check(rctx, oracle_mod, inputs.records("random", 70001, 3, words=2))
+
+
 def test_records_all_equal_and_sorted(rctx, oracle_mod):
     rec = np.full((5000, 4), 9, np.uint32)
     st = check(rctx, oracle_mod, rec)
