@@ -578,18 +578,42 @@ __global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_rounds(Job J)
 // One page copied by the whole CTA: 16-byte vectors when the caller's arrays
 // are 16-byte aligned (pool pages always are, and a page is a multiple of 16
 // bytes), else word by word; the partial last page's tail word by word.
-// Sources are read at L2 (other CTAs wrote them in earlier steps).
-__device__ void vm_copy_page(const Job& J, uint32_t dst, uint32_t src, uint32_t cnt, bool perm)
+// Every thread issues its loads of both arrays (keys, then permutation) for
+// up to VM_COPY_U vectors each before it stores, so a page of up to
+// VM_BLOCK * VM_COPY_U * 4 elements takes one memory round trip.  Sources
+// are read at L2 (other CTAs wrote them in earlier steps).
+constexpr uint32_t VM_COPY_U = 4;
+
+__device__ __noinline__ void vm_copy_page(const Job& J, uint32_t dst, uint32_t src, uint32_t cnt, bool perm)
 {
     const bool vec = ((reinterpret_cast<uintptr_t>(J.keysA) | reinterpret_cast<uintptr_t>(J.permA)) & 15u) == 0;
     const uint32_t nv = vec ? cnt >> 2 : 0u;
+    const uint4* sk = reinterpret_cast<const uint4*>(phys_k(J, src));
+    uint4* dk = reinterpret_cast<uint4*>(phys_k(J, dst));
+    const uint4* sp = perm ? reinterpret_cast<const uint4*>(phys_p(J, src)) : nullptr;
+    uint4* dp = perm ? reinterpret_cast<uint4*>(phys_p(J, dst)) : nullptr;
+    for (uint32_t i0 = threadIdx.x; i0 < nv; i0 += VM_BLOCK * VM_COPY_U) {
+        uint4 a[VM_COPY_U], b[VM_COPY_U];
+#pragma unroll
+        for (uint32_t u = 0; u < VM_COPY_U; ++u) {
+            const uint32_t i = i0 + u * VM_BLOCK;
+            if (i < nv) {
+                a[u] = __ldcg(sk + i);
+                if (perm) b[u] = __ldcg(sp + i);
+            }
+        }
+#pragma unroll
+        for (uint32_t u = 0; u < VM_COPY_U; ++u) {
+            const uint32_t i = i0 + u * VM_BLOCK;
+            if (i < nv) {
+                dk[i] = a[u];
+                if (perm) dp[i] = b[u];
+            }
+        }
+    }
     for (int pass = 0; pass < (perm ? 2 : 1); ++pass) {
         const uint32_t* s = pass ? phys_p(J, src) : phys_k(J, src);
         uint32_t* d = pass ? phys_p(J, dst) : phys_k(J, dst);
-        const uint4* s4 = reinterpret_cast<const uint4*>(s);
-        uint4* d4 = reinterpret_cast<uint4*>(d);
-#pragma unroll 4
-        for (uint32_t i = threadIdx.x; i < nv; i += VM_BLOCK) d4[i] = __ldcg(s4 + i);
         for (uint32_t i = (nv << 2) + threadIdx.x; i < cnt; i += VM_BLOCK) d[i] = __ldcg(s + i);
     }
 }
@@ -597,7 +621,9 @@ __device__ void vm_copy_page(const Job& J, uint32_t dst, uint32_t src, uint32_t 
 // Copy (Sec. 4), in batches of target pages.  The paper walks the virtual
 // pages in order: a target array page that still holds data needed later is
 // first moved out to a free page, then the page's own data is copied in.
-// Here a batch of up to pool - 1 consecutive targets does the same in two
+// Here a batch of up to pool - 1 consecutive targets (a multiple of the
+// CTAs when there are more, so that every CTA copies as many pages as the
+// others in one step) does the same in two
 // parallel steps, a CTA per page: (1) every target of the batch that holds
 // another page's data moves it out to a free page; (2) every target receives
 // its own data.  After step 1 no target of the batch holds needed data, so
@@ -610,7 +636,7 @@ __device__ void vm_copy_page(const Job& J, uint32_t dst, uint32_t src, uint32_t 
 // gathered during step 2 -- this batch's unused ones and the sources step 2
 // frees, without the next batch's targets -- into the other of two stacks,
 // so a batch needs two grid barriers.
-__global__ void __launch_bounds__(VM_BLOCK) k_vm_copy(Job J)
+__global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_copy(Job J)
 {
     Ctr* C = J.ctr;
     if (*(volatile uint32_t*)&C->error) return;
@@ -621,7 +647,10 @@ __global__ void __launch_bounds__(VM_BLOCK) k_vm_copy(Job J)
     const uint32_t NA = J.vm_na, NP = J.vm_na_cap + J.vm_pool;
     const uint32_t gtid = blockIdx.x * VM_BLOCK + tid, gstride = gridDim.x * VM_BLOCK;
     const bool tail_partial = (n & ((1u << J.vm_plog2) - 1)) != 0;
-    const uint32_t BMAX = J.vm_pool - 1;
+    // targets per batch: pool - 1, rounded down to a multiple of the grid
+    // when that leaves at least one per CTA (every CTA then copies as many
+    // pages as the others in each step)
+    const uint32_t BMAX = J.vm_pool - 1 >= gridDim.x ? (J.vm_pool - 1) / gridDim.x * gridDim.x : J.vm_pool - 1;
     uint32_t* stack[2] = {J.free_stack, J.free_stack + NP};
     // a page that may serve as a free page for batches ending before qend
     auto usable = [&](uint32_t p, uint32_t qend) {
@@ -705,8 +734,11 @@ __global__ void __launch_bounds__(VM_BLOCK) k_vm_copy(Job J)
 
 int vm_rounds_max_grid(int num_sms)
 {
-    int per_sm = 0;
+    // both cooperative kernels run on this grid: the smaller residency
+    int per_sm = 0, copy_per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_vm_rounds, VM_BLOCK, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&copy_per_sm, k_vm_copy, VM_BLOCK, 0);
+    if (copy_per_sm < per_sm) per_sm = copy_per_sm;
     if (per_sm > 6) per_sm = 6;
     return num_sms * (per_sm > 0 ? per_sm : 1);
 }
