@@ -333,7 +333,7 @@ __device__ void vm_page(const Job& J, VmSmem& sm, const VmGroup& G, uint32_t u, 
 }  // namespace
 
 // The HBM merge rounds with virtual-memory storage.  Per round:
-//   1. every merge marks the pages it touches (a warp per merge);
+//   1. every merge marks the pages it touches (a team of warps per merge);
 //   2. one thread per touched page writes the page's record (its merge
 //      segments and gaps, in order) and, for a page start inside a merge, the
 //      merge-path split there -- all before any page of the round is recycled;
@@ -379,12 +379,16 @@ __global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_rounds(Job J)
         const uint32_t e0 = C->bucket_start[r], e1 = C->bucket_start[r + 1];
         if (e0 == e1) continue;
         if (blockIdx.x == 0 && tid == 0) C->round_ns[r][0] = globaltimer_ns();
-        // 1. the pages each merge of the round touches (a warp per merge)
-        for (uint32_t e = e0 + gwarp; e < e1; e += nwarps_grid) {
+        // 1. the pages each merge of the round touches: a team of W warps per
+        //    merge, W = the grid's warps / the round's merges (at least 1), so
+        //    that a round of few large merges still spreads over the grid
+        const uint32_t W = e1 - e0 >= nwarps_grid ? 1u : nwarps_grid / (e1 - e0);
+        const uint32_t teams = nwarps_grid / W, team = gwarp / W, tw = gwarp % W;
+        for (uint32_t e = e0 + team; team < teams && e < e1; e += teams) {
             const GSorted g = J.gsorted[e];
             const uint32_t lo = (uint32_t)g.goff, hi = lo + g.la + g.lb;
             const uint32_t first = lo >> L, last = (hi - 1) >> L;
-            for (uint32_t u = first + lane; u <= last; u += 32) {
+            for (uint32_t u = first + tw * 32u + lane; u <= last; u += W * 32u) {
                 if (u == first || u == last) {
                     const uint32_t slot = atomicAdd(&J.page_cnt[u], 1u);
                     if (slot < 2) J.page_nodes[2 * u + slot] = e;
