@@ -622,32 +622,59 @@ __device__ __noinline__ void vm_copy_page(const Job& J, uint32_t dst, uint32_t s
     }
 }
 
-// Copy (Sec. 4), in batches of target pages.  The paper walks the virtual
-// pages in order: a target array page that still holds data needed later is
-// first moved out to a free page, then the page's own data is copied in.
-// Here a batch of up to pool - 1 consecutive targets (a multiple of the
-// CTAs when there are more, so that every CTA copies as many pages as the
-// others in one step) does the same in two
-// parallel steps, a CTA per page: (1) every target of the batch that holds
-// another page's data moves it out to a free page; (2) every target receives
-// its own data.  After step 1 no target of the batch holds needed data, so
-// the copies of step 2 never overwrite a source; each copy frees its source,
-// so the number of free pages is the same after every batch, and counting
-// pages shows that with at most pool - 1 targets per batch the free pages
-// cover every move out.  A free page is one that holds nothing, is not a
-// target of this or an earlier batch, and is not the caller's partial last
-// page (never freed, as in the paper).  The free pages of the next batch are
-// gathered during step 2 -- this batch's unused ones and the sources step 2
-// frees, without the next batch's targets -- into the other of two stacks,
-// so a batch needs two grid barriers.
-__global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_copy(Job J)
+// Copy (Sec. 4): every virtual page u moves from its physical page pt[u] to
+// the caller's array page u.  The paper walks the virtual pages in order: a
+// target array page that still holds data needed later is first moved out
+// to a free page, then the page's own data is copied in.  The moves form
+// chains: array page u receives virtual page u's data from pt[u]; when
+// pt[u] = v is itself a target, v can receive its own data only after that,
+// and so on, until pt[.] is a pool page.  A chain starts at a target that
+// holds nothing, and a cycle of targets has no start.  So Copy walks every
+// chain from its start, one page move per target (the paper's walk in the
+// order that needs no evictions), with the chains in parallel:
+//   1. holder[p], the virtual page physical page p holds;
+//   2. the rank of every target along its chain, by pointer jumping over
+//      the predecessor links (holder) -- a target on a cycle never reaches a
+//      start; its cycle's smallest target becomes its start, whose data is
+//      saved to a free pool page first, and the ranks are taken again;
+//   3. long chains are cut into segments of S moves at the ranks divisible
+//      by S: the data of every segment start but a chain's first is saved
+//      to a free pool page, so the segment before it reads the saved copy
+//      while the segment itself overwrites the page.  S is the smallest
+//      power of two (and at least the moves per CTA) for which the free pool
+//      pages cover every save;
+//   4. a CTA per segment walks it, page by page.
+// When no S of at most COPY_SEG_MAX moves fits the free pages, the batched
+// order below runs instead: batches of up to pool - 1 consecutive targets (a
+// multiple of the CTAs when there are more) in two parallel steps, a CTA per
+// page: (1) every target of the batch that holds another page's data moves
+// it out to a free page; (2) every target receives its own data.  After
+// step 1 no target of the batch holds needed data, so the copies of step 2
+// never overwrite a source; each copy frees its source, so the number of
+// free pages is the same after every batch, and counting pages shows that
+// with at most pool - 1 targets per batch the free pages cover every move
+// out.  A free page is one that holds nothing, is not a target of this or an
+// earlier batch, and is not the caller's partial last page (never freed, as
+// in the paper).  The free pages of the next batch are gathered during step
+// 2 -- this batch's unused ones and the sources step 2 frees, without the
+// next batch's targets -- into the other of two stacks, so a batch needs two
+// grid barriers.
+constexpr uint32_t COPY_SEG_MAX = 1024;   // longest segment the chain walk accepts
+constexpr uint32_t COPY_KMAX = 17;        // segment lengths 2^0 .. 2^16 counted
+
+// scratch of the chain walk in the page-record table (free during Copy):
+// arrays of vm_na_cap words
+enum : uint32_t { CW_ANC0, CW_DIST0, CW_MIN0, CW_ANC1, CW_DIST1, CW_MIN1, CW_FLAGS, CW_TEMP, CW_COUNTERS };
+constexpr uint32_t CF_DONE = 1u, CF_CYCLE = 2u, CF_SAVED = 4u;
+// counters after the arrays: [0, COPY_KMAX) saves needed per segment length,
+// then cycles, moves to make, and a flag "a cycle exists"
+enum : uint32_t { CC_CYCLES = COPY_KMAX, CC_MOVES, CC_ANY_CYCLE, CC_WORDS };
+static_assert(CW_COUNTERS + 1 <= VM_REC_WORDS, "the chain walk's scratch fits the page records");
+
+__device__ bool copy_in_batches(const Job& J, Ctr* C, uint32_t n, bool perm)
 {
-    Ctr* C = J.ctr;
-    if (*(volatile uint32_t*)&C->error) return;
     __shared__ uint32_t s_f;
     const int tid = threadIdx.x;
-    const bool perm = J.want_perm != 0;
-    const uint32_t n = J.inst[0].n;
     const uint32_t NA = J.vm_na, NP = J.vm_na_cap + J.vm_pool;
     const uint32_t gtid = blockIdx.x * VM_BLOCK + tid, gstride = gridDim.x * VM_BLOCK;
     const bool tail_partial = (n & ((1u << J.vm_plog2) - 1)) != 0;
@@ -661,22 +688,13 @@ __global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_copy(Job J)
         if (p >= J.vm_na_cap) return true;                    // a pool page
         return p < NA && p >= qend && !(tail_partial && p + 1 == NA);
     };
-    // holder[p]: the virtual page whose data physical page p holds (NONE: none)
-    for (uint32_t p = gtid; p < NP; p += gstride) J.holder[p] = NONE;
-    if (gtid == 0) {
-        C->vm_copy_top[0] = C->vm_copy_top[1] = 0;
-        C->vm_copy_taken[0] = C->vm_copy_taken[1] = 0;
-    }
-    if (!grid_barrier(C)) return;
-    for (uint32_t u = gtid; u < NA; u += gstride) J.holder[J.pt[u]] = u;
-    if (!grid_barrier(C)) return;
     // the first batch's free pages
     {
         const uint32_t q1 = min(BMAX, NA);
         for (uint32_t p = gtid; p < NP; p += gstride)
             if (usable(p, q1) && J.holder[p] == NONE) stack[0][atomicAdd(&C->vm_copy_top[0], 1u)] = p;
     }
-    if (!grid_barrier(C)) return;
+    if (!grid_barrier(C)) return false;
     for (uint32_t q0 = 0, k = 0; q0 < NA; ++k) {
         const uint32_t cur = k & 1u, nxt = cur ^ 1u;
         const uint32_t q1 = q0 + min(BMAX, NA - q0);
@@ -705,8 +723,8 @@ __global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_copy(Job J)
                 atomicAdd(&C->vm_copy_moves, 1u);
             }
         }
-        if (!grid_barrier(C)) return;
-        if (*(volatile uint32_t*)&C->error) return;
+        if (!grid_barrier(C)) return false;
+        if (*(volatile uint32_t*)&C->error) return false;
         // step 2: every target receives its own data (a CTA per target); the
         // freed sources and the unused free pages that the next batch may use
         // go onto the other stack
@@ -731,9 +749,210 @@ __global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_copy(Job J)
                 if (usable(p, q2)) stack[nxt][atomicAdd(&C->vm_copy_top[nxt], 1u)] = p;
             }
         }
-        if (!grid_barrier(C)) return;
+        if (!grid_barrier(C)) return false;
         q0 = q1;
     }
+    return true;
+}
+
+// Pointer jumping over the predecessor links: after the rounds, a target on
+// a chain has anc = NONE and dist = its rank (moves before it on its chain);
+// a target on a cycle keeps anc != NONE, and min is the smallest target on
+// its cycle (the jumps have covered it).  Returns the buffer the result is in.
+__device__ int copy_rank(const Job& J, Ctr* C, uint32_t* W, uint32_t NAC, uint32_t NA, int rounds, bool& ok)
+{
+    const uint32_t gtid = blockIdx.x * VM_BLOCK + threadIdx.x, gstride = gridDim.x * VM_BLOCK;
+    int cur = 0;
+    for (int r = 0; r < rounds; ++r) {
+        const uint32_t* anc = W + (cur ? CW_ANC1 : CW_ANC0) * NAC;
+        const uint32_t* dist = W + (cur ? CW_DIST1 : CW_DIST0) * NAC;
+        const uint32_t* mn = W + (cur ? CW_MIN1 : CW_MIN0) * NAC;
+        uint32_t* anc2 = W + (cur ? CW_ANC0 : CW_ANC1) * NAC;
+        uint32_t* dist2 = W + (cur ? CW_DIST0 : CW_DIST1) * NAC;
+        uint32_t* mn2 = W + (cur ? CW_MIN0 : CW_MIN1) * NAC;
+        for (uint32_t u = gtid; u < NA; u += gstride) {
+            const uint32_t a = __ldcg(anc + u);
+            uint32_t d = __ldcg(dist + u), m = __ldcg(mn + u), a2 = NONE;
+            if (a != NONE && a < NA) {
+                a2 = __ldcg(anc + a);
+                d += __ldcg(dist + a);
+                m = min(m, __ldcg(mn + a));
+            }
+            anc2[u] = a2;
+            dist2[u] = d;
+            mn2[u] = m;
+        }
+        cur ^= 1;
+        if (!grid_barrier(C)) {
+            ok = false;
+            return cur;
+        }
+    }
+    ok = true;
+    return cur;
+}
+
+__global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_copy(Job J)
+{
+    Ctr* C = J.ctr;
+    if (*(volatile uint32_t*)&C->error) return;
+    __shared__ uint32_t s_cnt[CC_WORDS];
+    const int tid = threadIdx.x;
+    const bool perm = J.want_perm != 0;
+    const uint32_t n = J.inst[0].n;
+    const uint32_t NA = J.vm_na, NAC = J.vm_na_cap, NP = J.vm_na_cap + J.vm_pool;
+    const uint32_t gtid = blockIdx.x * VM_BLOCK + tid, gstride = gridDim.x * VM_BLOCK;
+    uint32_t* W = J.vm_rec;                         // the chain walk's scratch
+    uint32_t* cnt = W + CW_COUNTERS * NAC;         // its counters
+    uint32_t* free_pool = J.free_stack;            // free pool pages
+    uint32_t* seg = J.free_stack + NP;             // segment starts
+    // 1. holder[p]: the virtual page whose data physical page p holds
+    for (uint32_t p = gtid; p < NP; p += gstride) J.holder[p] = NONE;
+    if (gtid < CC_WORDS) cnt[gtid] = 0;
+    if (gtid == 0) {
+        C->vm_copy_top[0] = C->vm_copy_top[1] = 0;
+        C->vm_copy_taken[0] = C->vm_copy_taken[1] = 0;
+    }
+    if (!grid_barrier(C)) return;
+    for (uint32_t u = gtid; u < NA; u += gstride) J.holder[J.pt[u]] = u;
+    if (!grid_barrier(C)) return;
+    // the free pool pages; every target's predecessor link (the target whose
+    // data it holds) and rank 1, or none and rank 0 at a chain's start
+    for (uint32_t p = NAC + gtid; p < NP; p += gstride)
+        if (J.holder[p] == NONE) free_pool[atomicAdd(&C->vm_copy_top[0], 1u)] = p;
+    for (uint32_t u = gtid; u < NA; u += gstride) {
+        const uint32_t pu = J.pt[u];
+        const uint32_t h = J.holder[u];
+        const bool done = pu == u;
+        W[CW_FLAGS * NAC + u] = done ? CF_DONE : 0u;
+        W[CW_ANC0 * NAC + u] = (done || h == NONE) ? NONE : h;
+        W[CW_DIST0 * NAC + u] = (done || h == NONE) ? 0u : 1u;
+        W[CW_MIN0 * NAC + u] = u;
+    }
+    if (!grid_barrier(C)) return;
+    // 2. ranks by pointer jumping (2^rounds > NA covers every chain and cycle)
+    const int rounds = 33 - __clz(max(NA, 1u));
+    bool ok = true;
+    int fin = copy_rank(J, C, W, NAC, NA, rounds, ok);
+    if (!ok) return;
+    // targets on cycles: the smallest of each is its start; rank again with
+    // the starts' links cut (the chains' ranks stay)
+    for (uint32_t u = gtid; u < NA; u += gstride) {
+        const uint32_t f = W[CW_FLAGS * NAC + u];
+        if (f & CF_DONE) continue;
+        if (W[(fin ? CW_ANC1 : CW_ANC0) * NAC + u] != NONE) {
+            W[CW_FLAGS * NAC + u] = f | CF_CYCLE;
+            if (W[(fin ? CW_MIN1 : CW_MIN0) * NAC + u] == u) atomicAdd(&cnt[CC_CYCLES], 1u);
+            cnt[CC_ANY_CYCLE] = 1u;
+        }
+    }
+    if (!grid_barrier(C)) return;
+    if (__ldcg(&cnt[CC_ANY_CYCLE])) {
+        for (uint32_t u = gtid; u < NA; u += gstride) {
+            const uint32_t f = W[CW_FLAGS * NAC + u];
+            uint32_t a = NONE, d = 0;
+            if (f & CF_CYCLE) {
+                const bool start = W[(fin ? CW_MIN1 : CW_MIN0) * NAC + u] == u;
+                a = start ? NONE : J.holder[u];
+                d = start ? 0u : 1u;
+            } else if (!(f & CF_DONE)) {
+                d = W[(fin ? CW_DIST1 : CW_DIST0) * NAC + u];
+            }
+            W[CW_ANC0 * NAC + u] = a;
+            W[CW_DIST0 * NAC + u] = d;
+            W[CW_MIN0 * NAC + u] = u;
+        }
+        if (!grid_barrier(C)) return;
+        fin = copy_rank(J, C, W, NAC, NA, rounds, ok);
+        if (!ok) return;
+    }
+    const uint32_t* rank = W + (fin ? CW_DIST1 : CW_DIST0) * NAC;
+    // 3. saves needed for every segment length 2^k: the targets of rank > 0
+    //    divisible by 2^k, plus one per cycle; and the moves to make
+    for (int i = tid; i < CC_WORDS; i += VM_BLOCK) s_cnt[i] = 0;
+    __syncthreads();
+    for (uint32_t u = gtid; u < NA; u += gstride) {
+        if (W[CW_FLAGS * NAC + u] & CF_DONE) continue;
+        const uint32_t rk = __ldcg(rank + u);
+        atomicAdd(&s_cnt[CC_MOVES], 1u);
+        if (rk == 0) continue;
+        for (uint32_t k = 0; k < COPY_KMAX; ++k)
+            if ((rk & ((1u << k) - 1u)) == 0) atomicAdd(&s_cnt[k], 1u);
+    }
+    __syncthreads();
+    for (int i = tid; i < (int)CC_CYCLES; i += VM_BLOCK)
+        if (s_cnt[i]) atomicAdd(&cnt[i], s_cnt[i]);
+    if (tid == 0 && s_cnt[CC_MOVES]) atomicAdd(&cnt[CC_MOVES], s_cnt[CC_MOVES]);
+    if (!grid_barrier(C)) return;
+    // every thread takes the same S
+    const uint32_t nfree = __ldcg(&C->vm_copy_top[0]), ncyc = __ldcg(&cnt[CC_CYCLES]);
+    const uint32_t moves = __ldcg(&cnt[CC_MOVES]);
+    uint32_t k = 0;
+    while (k + 1 < COPY_KMAX && (1u << k) * 2u * gridDim.x < moves) ++k;   // at least the moves per CTA / 2
+    while (k < COPY_KMAX && __ldcg(&cnt[k]) + ncyc > nfree) ++k;
+    if (k >= COPY_KMAX || (1u << k) > COPY_SEG_MAX) {
+        // the chains do not split into short enough segments: batches
+        if (gtid == 0) C->vm_copy_top[0] = 0;
+        if (!grid_barrier(C)) return;
+        copy_in_batches(J, C, n, perm);
+        return;
+    }
+    const uint32_t S = 1u << k;
+    // the segment starts, and a free pool page for the data of every one
+    // that holds data (a cycle's start, or rank > 0 divisible by S)
+    for (uint32_t u = gtid; u < NA; u += gstride) {
+        const uint32_t f = W[CW_FLAGS * NAC + u];
+        if (f & CF_DONE) continue;
+        const uint32_t rk = __ldcg(rank + u);
+        if ((rk & (S - 1u)) != 0) continue;
+        if (rk > 0 || (f & CF_CYCLE)) {
+            const uint32_t at = atomicAdd(&C->vm_copy_taken[0], 1u);
+            if (at >= nfree) {
+                set_error(C, DERR_INTERNAL, 69);
+                continue;
+            }
+            W[CW_TEMP * NAC + u] = __ldcg(free_pool + at);
+            W[CW_FLAGS * NAC + u] = f | CF_SAVED;
+        }
+        seg[atomicAdd(&C->vm_copy_top[1], 1u)] = u;
+    }
+    if (!grid_barrier(C)) return;
+    if (*(volatile uint32_t*)&C->error) return;
+    const uint32_t nseg = __ldcg(&C->vm_copy_top[1]);
+    // the saves (a CTA per page): the data a segment start holds is its
+    // predecessor's
+    uint32_t made = 0;
+    for (uint32_t i = blockIdx.x; i < nseg; i += gridDim.x) {
+        const uint32_t u = __ldcg(seg + i);
+        if (!(__ldcg(W + CW_FLAGS * NAC + u) & CF_SAVED)) continue;
+        vm_copy_page(J, __ldcg(W + CW_TEMP * NAC + u), u, page_size(J, J.holder[u], n), perm);
+        ++made;
+    }
+    if (!grid_barrier(C)) return;
+    // 4. the walks (a CTA per segment): u receives its data from pt[u] -- or
+    //    from the saved copy when pt[u] starts the next segment, which ends
+    //    this one; a pool page ends the chain
+    for (uint32_t i = blockIdx.x; i < nseg; i += gridDim.x) {
+        uint32_t u = __ldcg(seg + i);
+        for (uint32_t step = 0;; ++step) {
+            if (step > S) {                         // never expected: a segment has at most S moves
+                if (tid == 0) set_error(C, DERR_INTERNAL, 70);
+                break;
+            }
+            const uint32_t p = __ldcg(J.pt + u);
+            const bool target = p < NA;
+            const uint32_t fv = target ? __ldcg(W + CW_FLAGS * NAC + p) : 0u;
+            const bool saved = target && (fv & CF_SAVED);
+            vm_copy_page(J, u, saved ? __ldcg(W + CW_TEMP * NAC + p) : p, page_size(J, u, n), perm);
+            ++made;
+            __syncthreads();                       // u's loads of p are complete before p is written
+            if (!target || saved) break;
+            u = p;
+        }
+    }
+    if (tid == 0 && made) atomicAdd(&C->vm_copy_moves, made);
+    if (!grid_barrier(C)) return;
+    for (uint32_t u = gtid; u < NA; u += gstride) J.pt[u] = u;
 }
 
 int vm_rounds_max_grid(int num_sms)
