@@ -588,14 +588,15 @@ __global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_rounds(Job J)
 // are read at L2 (other CTAs wrote them in earlier steps).
 constexpr uint32_t VM_COPY_U = 4;
 
-__device__ __noinline__ void vm_copy_page(const Job& J, uint32_t dst, uint32_t src, uint32_t cnt, bool perm)
+__device__ __noinline__ void vm_copy_keys_perm(const Job& J, uint32_t* dkw, uint32_t* dpw, const uint32_t* skw,
+                                               const uint32_t* spw, uint32_t cnt, bool perm)
 {
     const bool vec = ((reinterpret_cast<uintptr_t>(J.keysA) | reinterpret_cast<uintptr_t>(J.permA)) & 15u) == 0;
     const uint32_t nv = vec ? cnt >> 2 : 0u;
-    const uint4* sk = reinterpret_cast<const uint4*>(phys_k(J, src));
-    uint4* dk = reinterpret_cast<uint4*>(phys_k(J, dst));
-    const uint4* sp = perm ? reinterpret_cast<const uint4*>(phys_p(J, src)) : nullptr;
-    uint4* dp = perm ? reinterpret_cast<uint4*>(phys_p(J, dst)) : nullptr;
+    const uint4* sk = reinterpret_cast<const uint4*>(skw);
+    uint4* dk = reinterpret_cast<uint4*>(dkw);
+    const uint4* sp = perm ? reinterpret_cast<const uint4*>(spw) : nullptr;
+    uint4* dp = perm ? reinterpret_cast<uint4*>(dpw) : nullptr;
     for (uint32_t i0 = threadIdx.x; i0 < nv; i0 += VM_BLOCK * VM_COPY_U) {
         uint4 a[VM_COPY_U], b[VM_COPY_U];
 #pragma unroll
@@ -616,10 +617,16 @@ __device__ __noinline__ void vm_copy_page(const Job& J, uint32_t dst, uint32_t s
         }
     }
     for (int pass = 0; pass < (perm ? 2 : 1); ++pass) {
-        const uint32_t* s = pass ? phys_p(J, src) : phys_k(J, src);
-        uint32_t* d = pass ? phys_p(J, dst) : phys_k(J, dst);
+        const uint32_t* s = pass ? spw : skw;
+        uint32_t* d = pass ? dpw : dkw;
         for (uint32_t i = (nv << 2) + threadIdx.x; i < cnt; i += VM_BLOCK) d[i] = __ldcg(s + i);
     }
+}
+
+__device__ __forceinline__ void vm_copy_page(const Job& J, uint32_t dst, uint32_t src, uint32_t cnt, bool perm)
+{
+    vm_copy_keys_perm(J, phys_k(J, dst), perm ? phys_p(J, dst) : nullptr, phys_k(J, src), perm ? phys_p(J, src) : nullptr,
+                      cnt, perm);
 }
 
 // Copy (Sec. 4): every virtual page u moves from its physical page pt[u] to
@@ -639,10 +646,12 @@ __device__ __noinline__ void vm_copy_page(const Job& J, uint32_t dst, uint32_t s
 //      saved to a free pool page first, and the ranks are taken again;
 //   3. long chains are cut into segments of S moves at the ranks divisible
 //      by S: the data of every segment start but a chain's first is saved
-//      to a free pool page, so the segment before it reads the saved copy
-//      while the segment itself overwrites the page.  S is the smallest
-//      power of two (and at least the moves per CTA) for which the free pool
-//      pages cover every save;
+//      to a temporary page, so the segment before it reads the saved copy
+//      while the segment itself overwrites the page.  The temporaries are
+//      the free pool pages and page-sized slots of the page-record and split
+//      tables (rewritten by every round, unused during Copy).  S is the
+//      smallest power of two (and at least the moves per CTA) for which the
+//      temporaries cover every save;
 //   4. a CTA per segment walks it, page by page.
 // When no S of at most COPY_SEG_MAX moves fits the free pages, the batched
 // order below runs instead: batches of up to pool - 1 consecutive targets (a
@@ -792,11 +801,49 @@ __device__ int copy_rank(const Job& J, Ctr* C, uint32_t* W, uint32_t NAC, uint32
     return cur;
 }
 
+// Temporary pages of the chain walk beyond the pool: page-sized slots (keys,
+// then permutation) in the page-record table past the walk's own scratch,
+// then in the split table.  Slot ids follow the physical page ids.
+struct CopySlots {
+    uint32_t* a;      // first region and its slots
+    uint32_t na;
+    uint32_t* b;      // second region and its slots
+    uint32_t nb;
+};
+
+__device__ __forceinline__ CopySlots copy_slots(const Job& J)
+{
+    const size_t P = (size_t)1 << J.vm_plog2, NAC = J.vm_na_cap;
+    const size_t a0 = ((CW_COUNTERS * NAC + CC_WORDS) + 3) & ~(size_t)3;     // 16-byte aligned
+    const size_t a_words = (size_t)VM_REC_WORDS * NAC, b_words = (NAC + 1) * VM_SPLIT_WORDS;
+    CopySlots c;
+    c.a = J.vm_rec + a0;
+    c.na = a_words > a0 ? (uint32_t)((a_words - a0) / (2 * P)) : 0u;
+    c.b = J.vm_split_at;
+    c.nb = (uint32_t)(b_words / (2 * P));
+    return c;
+}
+
+__device__ __forceinline__ uint32_t* temp_k(const Job& J, const CopySlots& cs, uint32_t NP, uint32_t id)
+{
+    if (id < NP) return phys_k(J, id);
+    const size_t P = (size_t)1 << J.vm_plog2;
+    const uint32_t i = id - NP;
+    return i < cs.na ? cs.a + 2 * P * i : cs.b + 2 * P * (i - cs.na);
+}
+
+__device__ __forceinline__ uint32_t* temp_p(const Job& J, const CopySlots& cs, uint32_t NP, uint32_t id)
+{
+    if (id < NP) return phys_p(J, id);
+    return temp_k(J, cs, NP, id) + ((size_t)1 << J.vm_plog2);
+}
+
 __global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_copy(Job J)
 {
     Ctr* C = J.ctr;
     if (*(volatile uint32_t*)&C->error) return;
     __shared__ uint32_t s_cnt[CC_WORDS];
+    const CopySlots cs = copy_slots(J);
     const int tid = threadIdx.x;
     const bool perm = J.want_perm != 0;
     const uint32_t n = J.inst[0].n;
@@ -820,6 +867,7 @@ __global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_copy(Job J)
     // data it holds) and rank 1, or none and rank 0 at a chain's start
     for (uint32_t p = NAC + gtid; p < NP; p += gstride)
         if (J.holder[p] == NONE) free_pool[atomicAdd(&C->vm_copy_top[0], 1u)] = p;
+    for (uint32_t i = gtid; i < cs.na + cs.nb; i += gstride) free_pool[atomicAdd(&C->vm_copy_top[0], 1u)] = NP + i;
     for (uint32_t u = gtid; u < NA; u += gstride) {
         const uint32_t pu = J.pt[u];
         const uint32_t h = J.holder[u];
@@ -925,7 +973,9 @@ __global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_copy(Job J)
     for (uint32_t i = blockIdx.x; i < nseg; i += gridDim.x) {
         const uint32_t u = __ldcg(seg + i);
         if (!(__ldcg(W + CW_FLAGS * NAC + u) & CF_SAVED)) continue;
-        vm_copy_page(J, __ldcg(W + CW_TEMP * NAC + u), u, page_size(J, J.holder[u], n), perm);
+        const uint32_t t = __ldcg(W + CW_TEMP * NAC + u);
+        vm_copy_keys_perm(J, temp_k(J, cs, NP, t), temp_p(J, cs, NP, t), phys_k(J, u), phys_p(J, u),
+                          page_size(J, J.holder[u], n), perm);
         ++made;
     }
     if (!grid_barrier(C)) return;
@@ -943,7 +993,9 @@ __global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_copy(Job J)
             const bool target = p < NA;
             const uint32_t fv = target ? __ldcg(W + CW_FLAGS * NAC + p) : 0u;
             const bool saved = target && (fv & CF_SAVED);
-            vm_copy_page(J, u, saved ? __ldcg(W + CW_TEMP * NAC + p) : p, page_size(J, u, n), perm);
+            const uint32_t src = saved ? __ldcg(W + CW_TEMP * NAC + p) : p;
+            vm_copy_keys_perm(J, phys_k(J, u), phys_p(J, u), temp_k(J, cs, NP, src), temp_p(J, cs, NP, src),
+                              page_size(J, u, n), perm);
             ++made;
             __syncthreads();                       // u's loads of p are complete before p is written
             if (!target || saved) break;
