@@ -31,13 +31,17 @@ namespace {
 
 constexpr int VM_BLOCK = 256;
 constexpr int VM_WARPS = VM_BLOCK / 32;
-constexpr int VM_K = 16;                  // outputs per thread of a merge sub-chunk
+// outputs per thread of a merge sub-chunk: odd, so that the threads of a
+// warp search and merge at positions spread over the shared-memory banks
+// (with 16 the split positions of a warp fell on a few banks), and at least
+// 16, so that a group's sub-chunk holds a page
+constexpr int VM_K = 17;
 constexpr int VM_SLOTS = VM_BLOCK * VM_K + 8 * VM_WARPS;   // staging words per CTA
 
 // A CTA works on several output pages at once: groups of W warps, W = P / 512
-// clamped to 1..8, each group merging sub-chunks of 512 W = 16 x its threads
-// outputs (at least one page) in its own slice of shared memory, with its own
-// named barrier.
+// clamped to 1..8, each group merging sub-chunks of 544 W = VM_K x its
+// threads outputs (at least one page) in its own slice of shared memory, with
+// its own named barrier.
 struct VmGroup {
     uint32_t g;        // group index inside the CTA
     uint32_t groups;   // groups per CTA
@@ -653,6 +657,9 @@ __device__ __forceinline__ void vm_copy_page(const Job& J, uint32_t dst, uint32_
 //      smallest power of two (and at least the moves per CTA) for which the
 //      temporaries cover every save;
 //   4. a CTA per segment walks it, page by page.
+// Two targets that hold each other's data (a cycle of two, as a reversal of
+// the page order makes) trade it directly, one CTA per pair, and need no
+// temporary.
 // When no S of at most COPY_SEG_MAX moves fits the free pages, the batched
 // order below runs instead: batches of up to pool - 1 consecutive targets (a
 // multiple of the CTAs when there are more) in two parallel steps, a CTA per
@@ -674,7 +681,7 @@ constexpr uint32_t COPY_KMAX = 17;        // segment lengths 2^0 .. 2^16 counted
 // scratch of the chain walk in the page-record table (free during Copy):
 // arrays of vm_na_cap words
 enum : uint32_t { CW_ANC0, CW_DIST0, CW_MIN0, CW_ANC1, CW_DIST1, CW_MIN1, CW_FLAGS, CW_TEMP, CW_COUNTERS };
-constexpr uint32_t CF_DONE = 1u, CF_CYCLE = 2u, CF_SAVED = 4u;
+constexpr uint32_t CF_DONE = 1u, CF_CYCLE = 2u, CF_SAVED = 4u, CF_SWAP = 8u;
 // counters after the arrays: [0, COPY_KMAX) saves needed per segment length,
 // then cycles, moves to make, and a flag "a cycle exists"
 enum : uint32_t { CC_CYCLES = COPY_KMAX, CC_MOVES, CC_ANY_CYCLE, CC_WORDS };
@@ -801,6 +808,34 @@ __device__ int copy_rank(const Job& J, Ctr* C, uint32_t* W, uint32_t NAC, uint32
     return cur;
 }
 
+// Two array pages that hold each other's data (a cycle of two) trade it by
+// one CTA, every thread loading both of its words before storing either:
+// page u receives cu elements from v, page v receives cv from u.
+__device__ __noinline__ void vm_swap_pages(const Job& J, uint32_t u, uint32_t v, uint32_t cu, uint32_t cv, bool perm)
+{
+    const bool vec = ((reinterpret_cast<uintptr_t>(J.keysA) | reinterpret_cast<uintptr_t>(J.permA)) & 15u) == 0;
+    for (int pass = 0; pass < (perm ? 2 : 1); ++pass) {
+        uint32_t* a = pass ? phys_p(J, u) : phys_k(J, u);
+        uint32_t* b = pass ? phys_p(J, v) : phys_k(J, v);
+        const uint32_t na = vec ? cu >> 2 : 0u, nb = vec ? cv >> 2 : 0u, nv = max(na, nb);
+        uint4* a4 = reinterpret_cast<uint4*>(a);
+        uint4* b4 = reinterpret_cast<uint4*>(b);
+        for (uint32_t i = threadIdx.x; i < nv; i += VM_BLOCK) {
+            uint4 x = make_uint4(0u, 0u, 0u, 0u), y = x;
+            if (i < na) x = __ldcg(b4 + i);
+            if (i < nb) y = __ldcg(a4 + i);
+            if (i < na) a4[i] = x;
+            if (i < nb) b4[i] = y;
+        }
+        for (uint32_t i = threadIdx.x; i < max(cu, cv); i += VM_BLOCK) {
+            const bool ia = i >= (na << 2) && i < cu, ib = i >= (nb << 2) && i < cv;
+            const uint32_t x = ia ? __ldcg(b + i) : 0u, y = ib ? __ldcg(a + i) : 0u;
+            if (ia) a[i] = x;
+            if (ib) b[i] = y;
+        }
+    }
+}
+
 // Temporary pages of the chain walk beyond the pool: page-sized slots (keys,
 // then permutation) in the page-record table past the walk's own scratch,
 // then in the split table.  Slot ids follow the physical page ids.
@@ -871,8 +906,10 @@ __global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_copy(Job J)
     for (uint32_t u = gtid; u < NA; u += gstride) {
         const uint32_t pu = J.pt[u];
         const uint32_t h = J.holder[u];
-        const bool done = pu == u;
-        W[CW_FLAGS * NAC + u] = done ? CF_DONE : 0u;
+        // a cycle of two trades its pages directly and stays out of the ranks
+        const bool swap = pu != u && pu < NA && h == pu;
+        const bool done = pu == u || swap;
+        W[CW_FLAGS * NAC + u] = (done ? CF_DONE : 0u) | (swap ? CF_SWAP : 0u);
         W[CW_ANC0 * NAC + u] = (done || h == NONE) ? NONE : h;
         W[CW_DIST0 * NAC + u] = (done || h == NONE) ? 0u : 1u;
         W[CW_MIN0 * NAC + u] = u;
@@ -895,6 +932,13 @@ __global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_copy(Job J)
         }
     }
     if (!grid_barrier(C)) return;
+    if (__ldcg(&cnt[CC_CYCLES]) > __ldcg(&C->vm_copy_top[0])) {
+        // more cycles than temporaries: batches (before ranking again)
+        if (gtid == 0) C->vm_copy_top[0] = 0;
+        if (!grid_barrier(C)) return;
+        copy_in_batches(J, C, n, perm);
+        return;
+    }
     if (__ldcg(&cnt[CC_ANY_CYCLE])) {
         for (uint32_t u = gtid; u < NA; u += gstride) {
             const uint32_t f = W[CW_FLAGS * NAC + u];
@@ -950,6 +994,7 @@ __global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_copy(Job J)
     // that holds data (a cycle's start, or rank > 0 divisible by S)
     for (uint32_t u = gtid; u < NA; u += gstride) {
         const uint32_t f = W[CW_FLAGS * NAC + u];
+        if ((f & CF_SWAP) && u < J.pt[u]) seg[atomicAdd(&C->vm_copy_top[1], 1u)] = u;   // a pair, once
         if (f & CF_DONE) continue;
         const uint32_t rk = __ldcg(rank + u);
         if ((rk & (S - 1u)) != 0) continue;
@@ -984,6 +1029,12 @@ __global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_copy(Job J)
     //    this one; a pool page ends the chain
     for (uint32_t i = blockIdx.x; i < nseg; i += gridDim.x) {
         uint32_t u = __ldcg(seg + i);
+        if (__ldcg(W + CW_FLAGS * NAC + u) & CF_SWAP) {
+            const uint32_t v = __ldcg(J.pt + u);
+            vm_swap_pages(J, u, v, page_size(J, u, n), page_size(J, v, n), perm);
+            made += 2;
+            continue;
+        }
         for (uint32_t step = 0;; ++step) {
             if (step > S) {                         // never expected: a segment has at most S moves
                 if (tid == 0) set_error(C, DERR_INTERNAL, 70);
