@@ -36,7 +36,8 @@ constexpr int VM_WARPS = VM_BLOCK / 32;
 // (with 16 the split positions of a warp fell on a few banks), and at least
 // 16, so that a group's sub-chunk holds a page
 constexpr int VM_K = 17;
-constexpr int VM_SLOTS = VM_BLOCK * VM_K + 8 * VM_WARPS;   // staging words per CTA
+constexpr int VM_GROUP_PAD = 16;          // staging words per group beyond its sub-chunk (slice phases)
+constexpr int VM_SLOTS = VM_BLOCK * VM_K + VM_GROUP_PAD * VM_WARPS;   // staging words per CTA
 
 // A CTA works on several output pages at once: groups of W warps, W = P / 512
 // clamped to 1..8, each group merging sub-chunks of 544 W = VM_K x its
@@ -204,7 +205,7 @@ __device__ __forceinline__ uint32_t block_rank(bool flag, uint32_t* ws, uint32_t
     return before;
 }
 
-struct VmSmem {
+struct __align__(16) VmSmem {
     uint32_t k[VM_SLOTS];
     uint32_t p[VM_SLOTS];
     uint16_t src[VM_SLOTS];                     // the merge's choice per output: slot in k / p
@@ -219,8 +220,8 @@ __device__ void vm_page(const Job& J, VmSmem& sm, const VmGroup& G, uint32_t u, 
                         bool perm)
 {
     const uint32_t tid = G.tid, gi = G.g;
-    uint32_t* sk = sm.k + gi * (G.cap + 8);
-    uint32_t* sp = sm.p + gi * (G.cap + 8);
+    uint32_t* sk = sm.k + gi * (G.cap + VM_GROUP_PAD);   // 16-byte aligned: cap is a multiple of 4
+    uint32_t* sp = sm.p + gi * (G.cap + VM_GROUP_PAD);
     uint32_t* rec = sm.rec[gi];
     const uint32_t L = J.vm_plog2;
     const uint32_t ps0 = u << L;
@@ -281,16 +282,41 @@ __device__ void vm_page(const Job& J, VmSmem& sm, const VmGroup& G, uint32_t u, 
             return;
         }
         // the slices' keys (and permutation): each slice is at most a page, so
-        // it spans at most two physical pages, named in the record; every
-        // element comes by an asynchronous copy (all in flight at once)
+        // it spans at most two physical pages, named in the record.  A slice
+        // is staged at the 16-byte phase of its first element (the left one
+        // from slot sa, the right one from sb), so the 16-byte blocks of a
+        // page land on 16-byte blocks of the staging arrays and move by
+        // 16-byte asynchronous copies; the up to three elements before and
+        // after the blocks of each page move one by one (everything in flight
+        // at once; one by one throughout when a page's base is not 16-byte
+        // aligned, as a caller's array may not be)
         const uint32_t va = lo + a0, vb = mid + b0;
-        for (uint32_t i = tid; i < cnt; i += G.nthr) {
-            const bool left = i < na;
-            const uint32_t v = left ? va + i : vb + (i - na);
-            const uint32_t ph = sph[(left ? 0u : 2u) + ((v >> L) != ((left ? va : vb) >> L))];
-            const uint32_t off = v & ((1u << L) - 1u);
-            cp_async4(&sk[i], phys_k(J, ph) + off);
-            if (perm) cp_async4(&sp[i], phys_p(J, ph) + off);
+        const uint32_t sa = va & 3u, sb = ((sa + na + 3u) & ~3u) + (vb & 3u);
+        for (uint32_t side = 0; side < 2; ++side) {
+            const uint32_t v0 = side ? vb : va, len = side ? nb : na, d0 = side ? sb : sa;
+            for (uint32_t part = 0, done = 0; part < 2 && done < len; ++part) {
+                const uint32_t off = (v0 + done) & ((1u << L) - 1u);
+                const uint32_t run = min(len - done, (1u << L) - off);
+                const uint32_t ph = sph[2u * side + part];
+                const uint32_t* gk = phys_k(J, ph) + off;
+                const uint32_t* gp = perm ? phys_p(J, ph) + off : nullptr;
+                const uint32_t d = d0 + done;           // staging slot of the run's first element
+                const uint32_t phase = (d & 3u) << 2;   // its byte offset in a 16-byte block
+                const bool al = (reinterpret_cast<uintptr_t>(gk) & 15u) == phase &&
+                                (!perm || (reinterpret_cast<uintptr_t>(gp) & 15u) == phase);
+                const uint32_t head = al ? min(run, (4u - (d & 3u)) & 3u) : run;
+                const uint32_t body = al ? ((run - head) & ~3u) : 0u;
+                for (uint32_t q = tid; q < body / 4u; q += G.nthr) {
+                    cp_async16(&sk[d + head + 4u * q], gk + head + 4u * q);
+                    if (perm) cp_async16(&sp[d + head + 4u * q], gp + head + 4u * q);
+                }
+                for (uint32_t j = tid; j < run - body; j += G.nthr) {
+                    const uint32_t x = j < head ? j : j + body;
+                    cp_async4(&sk[d + x], gk + x);
+                    if (perm) cp_async4(&sp[d + x], gp + x);
+                }
+                done += run;
+            }
         }
         cp_async_commit();
         cp_async_wait<0>();
@@ -301,20 +327,22 @@ __device__ void vm_page(const Job& J, VmSmem& sm, const VmGroup& G, uint32_t u, 
         // each thread merges VM_K consecutive outputs, recording for each the
         // staging slot it comes from; then the group writes the page out in
         // order, consecutive threads on consecutive words
-        uint16_t* ssrc = sm.src + gi * (G.cap + 8);
+        uint16_t* ssrc = sm.src + gi * (G.cap + VM_GROUP_PAD);
+        const uint32_t* A = sk + sa;
+        const uint32_t* B = sk + sb;
         const uint32_t t0 = tid * VM_K;
         if (t0 < cnt) {
             uint32_t l = t0 > nb ? t0 - nb : 0u, h = min(t0, na);
             while (l < h) {
                 const uint32_t m = (l + h) >> 1;
-                if (sk[m] <= sk[na + t0 - 1 - m]) l = m + 1; else h = m;
+                if (A[m] <= B[t0 - 1 - m]) l = m + 1; else h = m;
             }
-            uint32_t ia = l, ib = na + (t0 - l);
+            uint32_t ia = l, ib = t0 - l;
 #pragma unroll 4
             for (int j = 0; j < VM_K; ++j) {
                 if (t0 + j < cnt) {
-                    const bool ta = ia < na && (ib >= cnt || sk[ia] <= sk[ib]);
-                    ssrc[t0 + j] = (uint16_t)(ta ? ia : ib);
+                    const bool ta = ia < na && (ib >= nb || A[ia] <= B[ib]);
+                    ssrc[t0 + j] = (uint16_t)(ta ? sa + ia : sb + ib);
                     ia += ta;
                     ib += !ta;
                 }
