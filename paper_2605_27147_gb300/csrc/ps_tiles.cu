@@ -29,9 +29,10 @@
 // many short runs (the usual case for unsorted data: forced runs of minrun
 // elements) therefore takes a faster road to the same result: each element
 // becomes one 64-bit word (key << 32 | position), every thread sorts 16
-// consecutive words in registers with a bitonic network, and the sorted
+// consecutive words in registers with a sorting network, and the sorted
 // blocks are merged pairwise in shared memory (merge path, 16 outputs per
-// thread) up to the whole tile.  The words are distinct, so no tie rule is
+// thread, comparing keys with ties to the left block) up to the whole
+// tile.  The words are distinct, so no tie rule is
 // needed and the order is exactly the stable one.  Tiles of few runs follow
 // the tree level by level as described above.
 #include "ps_internal.cuh"
@@ -65,26 +66,38 @@ __device__ __forceinline__ uint32_t net_slot(uint32_t x)
     return x + (x >> 4);
 }
 
-// Bitonic sorting network over N words held in registers (ascending).
+// Batcher's odd-even merge sorting network over N words held in registers
+// (ascending): 63 comparators for N = 16, where the bitonic network takes 80.
+// Merges sorted runs of p words pairwise, for p = 1, 2, 4, ...; comparator
+// (a, a + k) acts only within one run of 2p words.
 template <int N>
 __device__ __forceinline__ void sort_registers(unsigned long long (&v)[N])
 {
 #pragma unroll
-    for (int k = 2; k <= N; k <<= 1) {
+    for (int p = 1; p < N; p <<= 1) {
 #pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int k = p; k >= 1; k >>= 1) {
 #pragma unroll
-            for (int i = 0; i < N; ++i) {
-                const int l = i ^ j;
-                if (l > i) {
-                    const unsigned long long a = v[i], b = v[l];
-                    const bool swap = ((i & k) == 0) ? (b < a) : (a < b);
-                    v[i] = swap ? b : a;
-                    v[l] = swap ? a : b;
+            for (int j = k % p; j + k < N; j += 2 * k) {
+#pragma unroll
+                for (int i = 0; i < k && i + j + k < N; ++i) {
+                    const int a = i + j, b = a + k;
+                    if (a / (2 * p) == b / (2 * p)) {
+                        const unsigned long long x = v[a], y = v[b];
+                        const bool swap = y < x;
+                        v[a] = swap ? y : x;
+                        v[b] = swap ? x : y;
+                    }
                 }
             }
         }
     }
+}
+
+// Key of the word at slot s of a word array: its high half.
+__device__ __forceinline__ uint32_t net_key(const unsigned long long* w, uint32_t s)
+{
+    return reinterpret_cast<const uint32_t*>(w)[2 * s + 1];
 }
 
 // The network road for one tile of `size` elements: sorted (key, position)
@@ -114,10 +127,14 @@ __device__ int tile_network(NetSmem& sm, const uint32_t* ksrc, uint32_t size)
         if (x0 < P) {
             const uint32_t blk = x0 & ~(2 * w - 1), d = x0 - blk;
             const uint32_t A = blk, B = blk + w;
+            // keys only: the blocks are stably sorted and A's positions come
+            // before B's, so ties to A keep the (key, position) order (a block
+            // holding padding is followed only by padding)
             uint32_t lo = d > w ? d - w : 0u, hi = min(d, w);
             while (lo < hi) {
                 const uint32_t mid = (lo + hi) >> 1;
-                if (src[net_slot(A + mid)] <= src[net_slot(B + d - 1 - mid)]) lo = mid + 1; else hi = mid;
+                if (net_key(src, net_slot(A + mid)) <= net_key(src, net_slot(B + d - 1 - mid))) lo = mid + 1;
+                else hi = mid;
             }
             uint32_t ia = lo, ib = d - lo;
             unsigned long long va = ia < w ? src[net_slot(A + ia)] : 0ull;
@@ -127,7 +144,7 @@ __device__ int tile_network(NetSmem& sm, const uint32_t* ksrc, uint32_t size)
             // slot (a valid address whose value is never used)
 #pragma unroll
             for (int j = 0; j < NET_PER; ++j) {
-                const bool take_a = ia < w && (ib >= w || va <= vb);
+                const bool take_a = ia < w && (ib >= w || (uint32_t)(va >> 32) <= (uint32_t)(vb >> 32));
                 out[j] = take_a ? va : vb;
                 ia += take_a;
                 ib += !take_a;
