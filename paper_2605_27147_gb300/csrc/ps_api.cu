@@ -41,7 +41,10 @@ struct ps_ctx {
     uint32_t rec_big_cap;
     int grid_rec_big;           //   cooperative grid of their merge passes
     unsigned long long* rec_off; //  two-word rows: the big groups as instances of
-    ps_ctx* rec_inner;          //   a batched 32-bit sort in this inner context
+    ps_ctx* rec_inner;          //   a batched 32-bit sort in this inner context,
+    cudaStream_t rec_cap_stream; //  captured on this stream into the body of a
+    cudaGraph_t rec_graph;      //   graph's conditional node (run only when a
+    cudaGraphExec_t rec_exec;   //   big group exists)
 };
 
 namespace {
@@ -93,8 +96,14 @@ ps_status dev_alloc(ps_ctx* c, T** p, size_t count)
 
 void free_all(ps_ctx* c)
 {
+    if (c->rec_exec) cudaGraphExecDestroy(c->rec_exec);
+    if (c->rec_graph) cudaGraphDestroy(c->rec_graph);
+    c->rec_exec = nullptr;
+    c->rec_graph = nullptr;
     if (c->rec_inner) ::ps_destroy(c->rec_inner);
     c->rec_inner = nullptr;
+    if (c->rec_cap_stream) cudaStreamDestroy(c->rec_cap_stream);
+    c->rec_cap_stream = nullptr;
     if (c->timing)
         for (cudaEvent_t& e : c->ev)
             if (e) cudaEventDestroy(e);
@@ -239,6 +248,70 @@ PS_API const char* ps_status_str(ps_status s)
     }
     return "unknown ps_status";
 }
+
+namespace {
+
+// The nested sort of two-word rows' big tie groups as a graph: a kernel sets
+// the condition from the device-side count of big groups, and the
+// conditional node's body is the inner context's batched sort of the fixed
+// buffers (captured once).  On failure the graph is left out.
+void build_nested_graph(ps_ctx* c)
+{
+    ps_ctx* in = c->rec_inner;
+    cudaGraph_t g = nullptr;
+    cudaGraphConditionalHandle h;
+    bool ok = cudaGraphCreate(&g, 0) == cudaSuccess &&
+              cudaGraphConditionalHandleCreate(&h, g, 0u, cudaGraphCondAssignDefault) == cudaSuccess;
+    cudaGraphNode_t kn = nullptr, cn = nullptr;
+    uint32_t W = 2, cap = c->rec_big_cap;
+    ps::Ctr* C = c->base.ctr;
+    void* args[] = {&h, &W, &cap, &C};
+    if (ok) {
+        cudaGraphNodeParams kp = {};
+        kp.type = cudaGraphNodeTypeKernel;
+        kp.kernel.func = const_cast<void*>(ps::records_nested_cond_kernel());
+        kp.kernel.gridDim = dim3(1);
+        kp.kernel.blockDim = dim3(32);
+        kp.kernel.kernelParams = args;
+        ok = cudaGraphAddNode(&kn, g, nullptr, nullptr, 0, &kp) == cudaSuccess;
+    }
+    cudaGraph_t body = nullptr;
+    if (ok) {
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeIf;
+        cp.conditional.size = 1;
+        ok = cudaGraphAddNode(&cn, g, &kn, nullptr, 1, &cp) == cudaSuccess;
+        if (ok) body = cp.conditional.phGraph_out[0];
+    }
+    if (ok) {
+        ok = cudaStreamBeginCaptureToGraph(c->rec_cap_stream, body, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            in->capturing = true;
+            const ps_status st = run_common(in, c->rec_tmp, c->rec_tmp + c->cfg.max_n,
+                                            reinterpret_cast<const uint64_t*>(c->rec_off), 0, c->rec_big_cap, nullptr);
+            in->capturing = false;
+            cudaGraph_t captured = nullptr;
+            const cudaError_t e = cudaStreamEndCapture(c->rec_cap_stream, &captured);
+            ok = st == PS_OK && e == cudaSuccess;
+            in->last_valid = 0;
+        }
+    }
+    cudaGraphExec_t ex = nullptr;
+    if (ok) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        if (ex) cudaGraphExecDestroy(ex);
+        if (g) cudaGraphDestroy(g);
+        return;
+    }
+    c->rec_graph = g;
+    c->rec_exec = ex;
+}
+
+}  // namespace
 
 PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, ps_ctx** out)
 {
@@ -432,8 +505,13 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
             ic.max_count = c->rec_big_cap;
             ic.merge_lanes = cfg->merge_lanes;
             ic.merge_ctas = cfg->merge_ctas;
-            if (st == PS_OK) st = ps_create(&ic, device, cuda_stream, &c->rec_inner);
+            // the inner context enqueues on a private stream, so that its sort
+            // can be captured (the caller's stream may be the legacy one)
+            if (st == PS_OK && cudaStreamCreateWithFlags(&c->rec_cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+                st = PS_ECUDA;
+            if (st == PS_OK) st = ps_create(&ic, device, c->rec_cap_stream, &c->rec_inner);
             if (st == PS_OK) c->scratch_bytes += c->rec_inner->scratch_bytes;
+            if (st == PS_OK) build_nested_graph(c);   // without it the sort is enqueued directly
         }
     }
     if (st == PS_OK && (cfg->flags & PS_FLAG_HOST_IO)) {
@@ -662,9 +740,15 @@ ps_status records_async(ps_ctx* ctx, const uint32_t* d_rec, uint32_t words, uint
         if (ps::launch_records_nested_prep(d_rec, words, d_perm, ctx->rec_big, ctx->rec_big_cap, ctx->rec_off, keys2,
                                            ctx->rec_rows, C, grid, s) != cudaSuccess)
             return PS_ECUDA;
-        st = ps_run_batched(ctx->rec_inner, keys2, perm2, reinterpret_cast<const uint64_t*>(ctx->rec_off),
-                            ctx->rec_big_cap, nullptr);
-        if (st != PS_OK) return st;
+        if (ctx->rec_exec) {
+            if (cudaGraphLaunch(ctx->rec_exec, s) != cudaSuccess) return PS_ECUDA;
+        } else {
+            // no graph: the inner sort on the caller's stream, whatever the count
+            ctx->rec_inner->stream = s;
+            st = ps_run_batched(ctx->rec_inner, keys2, perm2, reinterpret_cast<const uint64_t*>(ctx->rec_off),
+                                ctx->rec_big_cap, nullptr);
+            if (st != PS_OK) return st;
+        }
         if (ps::launch_records_nested_apply(words, d_perm, ctx->rec_big, ctx->rec_big_cap, ctx->rec_off, perm2,
                                             ctx->rec_rows, C, ctx->rec_inner->base.ctr, grid, s) != cudaSuccess)
             return PS_ECUDA;
@@ -690,8 +774,15 @@ ps_status records_finish(ps_ctx* ctx, ps_stats* stats, uint32_t extra_launches, 
     stats->minrun = ctx->h_inst->minrun;
     // scan, window keys, groups, fix-up, and the big groups' merge passes
     // -- or, for two-word rows, their nested sort (offsets, gather, the
-    // batched sort, apply)
-    stats->launches += 4u + (nested ? 3u + LAUNCHES_PER_CALL : 1u) + extra_launches;
+    // condition, apply, and the batched sort when a big group exists)
+    uint32_t nested_launches = 0;
+    if (nested) {
+        uint32_t nbig = 0;
+        if (cudaMemcpy(&nbig, &ctx->base.ctr->rec_nbig, sizeof(nbig), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return PS_ECUDA;
+        nested_launches = (ctx->rec_exec ? 4u : 3u) + (nbig || !ctx->rec_exec ? LAUNCHES_PER_CALL : 0u);
+    }
+    stats->launches += 4u + (nested ? nested_launches : 1u) + extra_launches;
     return PS_OK;
 }
 

@@ -462,6 +462,9 @@ cudaError_t launch_records_fix(const uint32_t* rec, uint32_t W, unsigned long lo
                                uint32_t* groups, uint32_t cap, uint32_t* big, uint32_t big_cap, Ctr* C, int grid,
                                int coop_grid, bool nested, cudaStream_t s);
 int records_fix_big_grid(int num_sms);
+// k_rec_nested_cond(cudaGraphConditionalHandle, uint32_t W, uint32_t big_cap, Ctr*): sets
+// a graph's condition to "a big group needs the nested sort"
+const void* records_nested_cond_kernel();
 cudaError_t launch_records_nested_prep(const uint32_t* rec, uint32_t W, const uint32_t* perm, const uint32_t* big,
                                        uint32_t big_cap, unsigned long long* off, uint32_t* keys2, uint32_t* save,
                                        Ctr* C, int grid, cudaStream_t s);

@@ -488,6 +488,18 @@ __global__ void __launch_bounds__(REC_BLOCK) k_rec_nested_apply(uint32_t W, uint
     }
 }
 
+// The nested sort runs (a graph's conditional node) only when there is a
+// big group to order.
+__global__ void k_rec_nested_cond(cudaGraphConditionalHandle h, uint32_t W, uint32_t big_cap, Ctr* C)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, nested_groups(W, big_cap, C) ? 1u : 0u);
+}
+
+const void* records_nested_cond_kernel()
+{
+    return reinterpret_cast<const void*>(k_rec_nested_cond);
+}
+
 cudaError_t launch_records_nested_prep(const uint32_t* rec, uint32_t W, const uint32_t* perm, const uint32_t* big,
                                        uint32_t big_cap, unsigned long long* off, uint32_t* keys2, uint32_t* save,
                                        Ctr* C, int grid, cudaStream_t s)
