@@ -478,6 +478,7 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
     if (st == PS_OK) st = dev_alloc(c, &J.inst, c->max_count);
     if (st == PS_OK) st = dev_alloc(c, &J.range_agg, (size_t)c->grid_runs * ps::MAP_STATES);
     if (st == PS_OK) st = dev_alloc(c, &J.range_entry, (size_t)c->grid_runs);
+    if (st == PS_OK) st = dev_alloc(c, &J.run_grp_agg, (size_t)32 * ps::MAP_STATES);
     if (st == PS_OK) st = dev_alloc(c, &J.run_start, slot_cap);
     if (st == PS_OK) st = dev_alloc(c, &J.power, slot_cap);
     if (st == PS_OK) st = dev_alloc(c, &J.gsorted, gnode_cap);
@@ -532,7 +533,7 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
     if (st == PS_OK && cudaDeviceSynchronize() != cudaSuccess) st = PS_ECUDA;
     // every table the kernels write must exist (permB only with want_perm)
     if (st == PS_OK && ((!vm && (!J.keysB || !J.chunk_node)) || !J.inst || !J.chunk_map || !J.chunk_info ||
-                        !J.range_agg || !J.range_entry || !J.run_start || !J.power || !J.tiles || !J.gnodes ||
+                        !J.range_agg || !J.range_entry || !J.run_grp_agg || !J.run_start || !J.power || !J.tiles || !J.gnodes ||
                         !J.gmap || !J.gsorted || !J.dep || !J.ctr || (!vm && cfg->want_perm && !J.permB) ||
                         (vm && (!J.pool_keys || !J.pt || !J.vm_split_at || !J.vm_rec || !J.free_stack || !J.vm_cta_count))))
         st = PS_EINTERNAL;

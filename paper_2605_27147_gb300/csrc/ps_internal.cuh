@@ -128,6 +128,7 @@ struct Ctr {
     uint32_t bar_count;
     uint32_t bar_gen;
     uint32_t bar_group[32];            // arrivals per group of 32 CTAs (grids of <= 1024 CTAs)
+    uint32_t runs_grp_done[32];        // run detection: finished CTAs per group of 32 ranges
     uint32_t chunk_next[NPOW];         // per round: next chunk to hand out (dynamic scheduling)
     // virtual-memory storage
     uint32_t vm_free_top;              // entries on the free-page stack
@@ -192,7 +193,8 @@ struct Job {
     uint32_t* chunk_map;        // MAP_STATES per chunk: (runs << 8) | exit state, per entry state
     uint32_t* chunk_info;       // per chunk: CHUNK_FORCED | CHUNK_FIRST | first descent offset
     uint32_t* range_agg;        // MAP_STATES per run-detection CTA: its range's map
-    unsigned long long* range_entry;   // per run-detection CTA: (runs before << 8) | entry state
+    unsigned long long* range_entry;   // per group of 32 run-detection CTAs: (runs before << 8) | entry state
+    uint32_t* run_grp_agg;      // MAP_STATES per group of 32 ranges: the group's map
     uint32_t* run_start;        // per run slot: the run's first element (R + 1 per instance)
     uint8_t* power;             // per boundary slot: its Power
     TileItem* tiles;

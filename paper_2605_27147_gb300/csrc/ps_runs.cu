@@ -118,7 +118,10 @@ __global__ void __launch_bounds__(1024) k_setup(Job J)
         C->hbm_elems = 0;
         C->merge_t0 = 0;
     }
-    if (threadIdx.x < 32) C->bar_group[threadIdx.x] = 0;
+    if (threadIdx.x < 32) {
+        C->bar_group[threadIdx.x] = 0;
+        C->runs_grp_done[threadIdx.x] = 0;
+    }
     for (int r = threadIdx.x; r < NPOW + 2; r += blockDim.x) {
         if (r < NPOW) {
             C->round_ns[r][0] = C->round_ns[r][2] = ~0ull;   // minima
@@ -563,65 +566,58 @@ __global__ void __launch_bounds__(RUN_BLOCK) k_runs(Job J)
         __syncthreads();
     }
     if (tid < MAP_STATES) J.range_agg[(size_t)blockIdx.x * MAP_STATES + tid] = agg[tid] | s_reset;
+
+    // The range entries in two levels.  The last CTA of every group of 32
+    // ranges folds the group's range maps into one map (a lane per two entry
+    // states); the last of those walks the group maps in order and writes
+    // each group's entry (runs before it << 8 | state).  Every range's own
+    // entry follows in k_runs_emit from its group's entry and the maps of
+    // the ranges before it in the group.
+    constexpr uint32_t GROUP = 32;
+    static_assert(RUN_RANGES_MAX <= GROUP * 32, "at most 32 groups");
+    static_assert(GROUP * MAP_STATES <= 2 * WIN_SLOTS, "a group's maps fit the key windows");
+    uint32_t (*win)[MAP_STATES] = reinterpret_cast<uint32_t (*)[MAP_STATES]>(&keys[0][0]);
+    const int lane = tid & 31, warp = tid >> 5;
+    const uint32_t grp = blockIdx.x / GROUP, ngroups = (G + GROUP - 1) / GROUP;
+    const uint32_t gsize = min(GROUP, G - grp * GROUP);
     __threadfence();
     __syncthreads();
-    if (tid == 0) s_last = atomicAdd(&C->runs_done, 1u) == G - 1 ? 1u : 0u;
+    if (tid == 0) s_last = atomicAdd(&C->runs_grp_done[grp], 1u) == gsize - 1 ? 1u : 0u;
     __syncthreads();
     if (!s_last) return;
-
-    // The last CTA: the entry (runs before it << 8 | state) of every range,
-    // in order.  Per batch of range maps staged in the (now free) key windows:
-    // every warp folds a group of 32 consecutive ranges into one map (each
-    // lane two entry states), thread 0 walks the group maps, then lane r of
-    // each warp walks its group's ranges from the group's entry.
     __threadfence();
-    constexpr uint32_t GROUP = 32;
-    constexpr uint32_t SCAN_WIN = (2 * WIN_SLOTS / MAP_STATES) / GROUP * GROUP;   // range maps per batch
-    constexpr uint32_t NGROUPS = SCAN_WIN / GROUP;
-    static_assert(NGROUPS <= RUN_BLOCK / 32, "one warp per group");
-    uint32_t (*win)[MAP_STATES] = reinterpret_cast<uint32_t (*)[MAP_STATES]>(&keys[0][0]);
-    __shared__ uint32_t gmap[NGROUPS][MAP_STATES];
-    __shared__ unsigned long long gentry[NGROUPS];
-    const int lane = tid & 31, warp = tid >> 5;
-    unsigned long long at = 0;                   // range 0 begins chunk 0: state 0, no runs before
-    const uint32_t GR = K ? min(G, (T + K - 1) / K) : 0u;   // ranges that hold chunks
-    for (uint32_t r0 = 0; r0 < GR; r0 += SCAN_WIN) {
-        const uint32_t nr = min(SCAN_WIN, GR - r0);
-        for (uint32_t i = tid; i < nr * MAP_STATES; i += RUN_BLOCK)
-            win[i / MAP_STATES][i % MAP_STATES] = __ldcg(J.range_agg + (size_t)r0 * MAP_STATES + i);
-        __syncthreads();
-        const uint32_t ng = (nr + GROUP - 1) / GROUP;
-        if ((uint32_t)warp < ng) {
-            const uint32_t q0 = warp * GROUP, q1 = min(q0 + GROUP, nr);
-            bool reset = false;
-            for (int h = 0; h < 2; ++h) {
-                const uint32_t s0 = (uint32_t)lane + 32u * h;
-                unsigned long long a = s0;
-                for (uint32_t q = q0; q < q1; ++q) {
-                    const bool rq = (win[q][0] & RANGE_RESET) != 0;
-                    a = apply_map(a, win[q], rq);
-                    reset = reset || rq;
-                }
-                gmap[warp][s0] = (uint32_t)(a & 0xffu) | (uint32_t)((a >> 8) << 8) | (reset ? RANGE_RESET : 0u);
+    for (uint32_t i = tid; i < gsize * MAP_STATES; i += RUN_BLOCK)
+        win[i / MAP_STATES][i % MAP_STATES] = __ldcg(J.range_agg + (size_t)grp * GROUP * MAP_STATES + i);
+    __syncthreads();
+    if (warp == 0) {
+        bool reset = false;
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t s0 = (uint32_t)lane + 32u * h;
+            unsigned long long a = s0;
+            for (uint32_t q = 0; q < gsize; ++q) {
+                const bool rq = (win[q][0] & RANGE_RESET) != 0;
+                a = apply_map(a, win[q], rq);
+                reset = reset || rq;
             }
+            J.run_grp_agg[(size_t)grp * MAP_STATES + s0] =
+                (uint32_t)(a & 0xffu) | (uint32_t)((a >> 8) << 8) | (reset ? RANGE_RESET : 0u);
         }
-        __syncthreads();
-        if (tid == 0) {
-            for (uint32_t q = 0; q < ng; ++q) {
-                gentry[q] = at;
-                at = apply_map(at, gmap[q], (gmap[q][0] & RANGE_RESET) != 0);
-            }
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(&C->runs_done, 1u) == ngroups - 1 ? 1u : 0u;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (uint32_t i = tid; i < ngroups * MAP_STATES; i += RUN_BLOCK)
+        win[i / MAP_STATES][i % MAP_STATES] = __ldcg(J.run_grp_agg + i);
+    __syncthreads();
+    if (tid == 0) {
+        unsigned long long at = 0;               // range 0 begins chunk 0: state 0, no runs before
+        for (uint32_t q = 0; q < ngroups; ++q) {
+            J.range_entry[q] = at;
+            at = apply_map(at, win[q], (win[q][0] & RANGE_RESET) != 0);
         }
-        __syncthreads();
-        if ((uint32_t)warp < ng && lane == 0) {
-            unsigned long long a = gentry[warp];
-            const uint32_t q0 = warp * GROUP, q1 = min(q0 + GROUP, nr);
-            for (uint32_t q = q0; q < q1; ++q) {
-                J.range_entry[r0 + q] = a;
-                a = apply_map(a, win[q], (win[q][0] & RANGE_RESET) != 0);
-            }
-        }
-        __syncthreads();
     }
 }
 
@@ -646,7 +642,24 @@ __global__ void __launch_bounds__(RUN_BLOCK) k_runs_emit(Job J)
     const uint32_t T = C->total_chunks, G = gridDim.x;
     const uint32_t K = (T + G - 1) / G;
     const uint32_t g0 = min(blockIdx.x * K, T), g1 = min(g0 + K, T);
-    unsigned long long at = J.range_entry[blockIdx.x];
+    // this range's entry: its group's, through the maps of the ranges before
+    // it in the group (staged in the chunk-map window)
+    __shared__ unsigned long long s_at;
+    {
+        constexpr uint32_t GROUP = 32;
+        static_assert(WIN >= (int)GROUP, "a group's range maps fit the window");
+        const uint32_t q0 = blockIdx.x / GROUP * GROUP, nq = blockIdx.x - q0;
+        for (uint32_t i = tid; i < nq * MAP_STATES; i += RUN_BLOCK)
+            win[i / MAP_STATES][i % MAP_STATES] = __ldcg(J.range_agg + (size_t)q0 * MAP_STATES + i);
+        __syncthreads();
+        if (tid == 0) {
+            unsigned long long a = __ldcg(J.range_entry + blockIdx.x / GROUP);
+            for (uint32_t q = 0; q < nq; ++q) a = apply_map(a, win[q], (win[q][0] & RANGE_RESET) != 0);
+            s_at = a;
+        }
+        __syncthreads();
+    }
+    unsigned long long at = s_at;
     const bool desc = J.desc_runs != 0;
 
     // the run starts of chunk g, from its map entry: count checks, and the
