@@ -779,9 +779,10 @@ def run_keys64(args, n=1 << 24):
         dist.destroy_process_group()
 
 
-def serving_leg(local, lane_total, rate=2000.0, duration=10.0, budget=64 << 30, lanes=4):
-    """Config 5: Poisson arrivals replayed in real time through ps_server.
-    Returns the latencies and the server's statistics as a dict."""
+def serving_leg(local, lane_total, rate=2000.0, duration=10.0, budget=64 << 30, lanes=4, storage="pingpong"):
+    """Config 5: Poisson arrivals replayed in real time through ps_server
+    (lanes of Pingpong or VM storage).  Returns the latencies and the server's
+    statistics as a dict."""
     import torch
 
     from paper_2605_27147_gb300 import binding, inputs
@@ -805,7 +806,8 @@ def serving_leg(local, lane_total, rate=2000.0, duration=10.0, budget=64 << 30, 
     os.environ["PS_SERVER_TRACE"] = trace_path
     try:
         srv = binding.Server(budget, max_n, lanes=lanes, lane_max_total=lane_total, lane_max_count=256,
-                             device=local)
+                             device=local,
+                             storage=binding.PS_MODE_VM if storage == "vm" else binding.PS_MODE_PINGPONG)
     finally:
         del os.environ["PS_SERVER_TRACE"]
     # warm-up: a few requests (module loading, first launches)
@@ -923,7 +925,7 @@ def run_serving(args):
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    r = serving_leg(local, args.lane_total)
+    r = serving_leg(local, args.lane_total, storage=args.storage)
     st = r["server"]
     line = {
         "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": r["requests"], "warmup": 8,
@@ -932,7 +934,7 @@ def run_serving(args):
         "config": {"workload": "serving", "arrivals": f"Poisson {r['rate']:.0f}/s for {r['duration']:.0f} s, seed 4",
                    "sizes": "log-uniform in [2^10, 2^24]", "requests": r["requests"],
                    "offered_elements_per_s": r["offered"], "budget_bytes": r["budget"],
-                   "lanes": st["lanes"], "lane_max_total": st["lane_max_total"],
+                   "lanes": st["lanes"], "lane_max_total": st["lane_max_total"], "storage": args.storage,
                    "device_bytes": st["device_bytes"], "outputs": "sorted keys + stable permutation",
                    "io": "pinned host arrays in, pinned host arrays out (copies inside every latency)"},
         "latency_ms": r["latency_ms"],
@@ -943,7 +945,9 @@ def run_serving(args):
                 "d2h_bytes_per_step": int(8 * r["mean_n"]),
                 "api": "ps_server_submit / ps_server_wait on pinned host arrays"},
         "roofline": None, "cpu_baseline": None, "clocks": r["clocks"],
-        "gpu_launches": LAUNCHES_PER_BATCH * int(st["batches"]),
+        # a VM lane sorts each request by itself (one call, plus the Copy launch)
+        "gpu_launches": ((LAUNCHES_PER_BATCH + 1) * int(r["requests"]) if args.storage == "vm"
+                         else LAUNCHES_PER_BATCH * int(st["batches"])),
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -314,7 +314,16 @@ typedef struct ps_server_config {
     uint32_t device;
     uint32_t key_type;       /* ps_key_type of every request's keys                */
     uint32_t flags;          /* PS_FLAG_DESCENDING_RUNS or 0                      */
-    uint32_t reserved[2];
+    uint32_t storage;        /* ps_mode of the lanes' contexts (0: Pingpong).  With
+                                PS_MODE_VM a lane holds a page pool and tables
+                                instead of Pingpong's n-element scratch (about 8
+                                bytes per element), so a budget admits about twice
+                                the elements per lane.  A request of more than 2^20
+                                elements is then a batch by itself, sorted with paged
+                                storage (Sec. 4: one instance per call); smaller
+                                ones are batched (at most 2^22 elements) in a small
+                                Pingpong context the lane also holds              */
+    uint32_t reserved;
 } ps_server_config;
 
 typedef struct ps_server_stats {

@@ -88,7 +88,8 @@ class ps_server_config(ctypes.Structure):
         ("device", ctypes.c_uint32),
         ("key_type", ctypes.c_uint32),
         ("flags", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint32 * 2),
+        ("storage", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32),
     ]
 
 
@@ -415,10 +416,10 @@ class Server:
 
     def __init__(self, budget_bytes: int, max_n: int, *, lanes: int = 0, lane_max_total: int = 0,
                  lane_max_count: int = 0, want_perm: bool = True, device: int = 0, key_type: int = PS_KEY_U32,
-                 flags: int = 0):
+                 flags: int = 0, storage: int = PS_MODE_PINGPONG):
         cfg = ps_server_config(budget_bytes=budget_bytes, max_n=max_n, lane_max_total=lane_max_total,
                                lane_max_count=lane_max_count, lanes=lanes, want_perm=1 if want_perm else 0,
-                               device=device, key_type=key_type, flags=flags)
+                               device=device, key_type=key_type, flags=flags, storage=storage)
         h = ctypes.c_void_p()
         _check(lib().ps_server_create(ctypes.byref(cfg), ctypes.byref(h)), "ps_server_create")
         self._h = h

@@ -3,7 +3,9 @@
 //
 // The server owns `lanes` lanes; a lane is a batched Powersort context with
 // its own CUDA stream, device input/output arrays and offsets table, sized so
-// that all lanes together stay within the budget.  A dispatcher thread keeps
+// that all lanes together stay within the budget.  With VM storage a lane's
+// context is a paged one (a page pool and tables instead of an n-element
+// scratch buffer) and the lane sorts its batch's requests one after another.  A dispatcher thread keeps
 // every idle lane busy: it takes queued requests in arrival order while they
 // fit the lane (elements and count), enqueues their host->device copies, one
 // ps_run_batched over the batch and the device->host copies of the sorted
@@ -17,6 +19,7 @@
 // dependent kernels interleaved with a large batch's would wait behind one
 // of its long kernels at almost every step.  A ticket completes when its
 // lane's event has fired; its latency is measured from submission.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstdio>
@@ -50,6 +53,7 @@ struct Req {
 
 struct Lane {
     ps_ctx* ctx = nullptr;
+    ps_ctx* ctx_small = nullptr;    // VM storage: batches of small requests (Pingpong)
     cudaStream_t stream = nullptr;
     uint32_t* dkeys = nullptr;
     uint32_t* dperm = nullptr;
@@ -59,6 +63,7 @@ struct Lane {
     cudaEvent_t computed = nullptr; // the batch's sort has finished (its copies out may still run)
     std::vector<uint64_t> batch;    // tickets in flight
     std::vector<Req> jobs;          // their arrays, copied under the lock
+    uint64_t small_max = 0, small_total = 0;   // VM storage: the small context's limits
     bool busy = false;
     bool signalled = false;         // the stream reached the batch's end (host callback, under the lock)
     struct ps_server* owner = nullptr;
@@ -82,6 +87,11 @@ struct TraceRow {
 // (keys + permutation) plus a Pingpong context's scratch and tables, per
 // element.  What the lanes are charged is measured (lane_bytes below).
 constexpr double BYTES_PER_ELEM_ESTIMATE = 18.0;
+constexpr double BYTES_PER_ELEM_ESTIMATE_VM = 9.0;   // arrays + a page pool and tables
+// VM storage: a request of at most SMALL_MAX elements joins a batch of small
+// requests (at most SMALL_TOTAL elements) sorted by the lane's small Pingpong
+// context; a larger one is a batch by itself, sorted with paged storage.
+constexpr uint64_t SMALL_MAX = 1ull << 20, SMALL_TOTAL = 1ull << 22;
 
 }  // namespace
 
@@ -123,6 +133,7 @@ void CUDART_CB on_batch_end(void* arg)
 void lane_free(Lane& L)
 {
     if (L.ctx) ps_destroy(L.ctx);
+    if (L.ctx_small) ps_destroy(L.ctx_small);
     if (L.dkeys) cudaFree(L.dkeys);
     if (L.dperm) cudaFree(L.dperm);
     if (L.doff) cudaFree(L.doff);
@@ -161,8 +172,20 @@ ps_status launch_batch(ps_server* S, Lane& L)
     // the sort starts after the previous batch's sort (copies in are not held back)
     if (S->last_computed && cudaStreamWaitEvent(L.stream, S->last_computed, 0) != cudaSuccess) return PS_ECUDA;
     if (tr && cudaEventRecord(L.tev[2], L.stream) != cudaSuccess) return PS_ECUDA;
-    const ps_status st = ps_run_batched(L.ctx, L.dkeys, S->cfg.want_perm ? L.dperm : nullptr, L.doff, (uint32_t)k, nullptr);
-    if (st != PS_OK) return st;
+    if (S->cfg.storage == PS_MODE_VM && (k != 1 || L.jobs[0].n <= L.small_max)) {
+        // a batch of small requests: the small Pingpong context
+        const ps_status st =
+            ps_run_batched(L.ctx_small, L.dkeys, S->cfg.want_perm ? L.dperm : nullptr, L.doff, (uint32_t)k, nullptr);
+        if (st != PS_OK) return st;
+    } else if (S->cfg.storage == PS_MODE_VM) {
+        // a large request by itself, with paged storage
+        const ps_status st = ps_run(L.ctx, L.dkeys, S->cfg.want_perm ? L.dperm : nullptr, L.jobs[0].n, nullptr);
+        if (st != PS_OK) return st;
+    } else {
+        const ps_status st =
+            ps_run_batched(L.ctx, L.dkeys, S->cfg.want_perm ? L.dperm : nullptr, L.doff, (uint32_t)k, nullptr);
+        if (st != PS_OK) return st;
+    }
     if (cudaEventRecord(L.computed, L.stream) != cudaSuccess) return PS_ECUDA;
     if (tr && cudaEventRecord(L.tev[3], L.stream) != cudaSuccess) return PS_ECUDA;
     S->last_computed = L.computed;
@@ -256,10 +279,16 @@ void dispatcher(ps_server* S)
         for (Lane& L : S->lanes) {
             if (L.busy || S->queue.empty()) continue;
             uint64_t total = 0;
+            const bool vm = S->cfg.storage == PS_MODE_VM;
             while (!S->queue.empty() && L.batch.size() < S->lane_count) {
                 const uint64_t t = S->queue.front();
                 const uint64_t n = S->reqs[t].n;
                 if (total + n > S->lane_total && !L.batch.empty()) break;
+                // VM storage: small requests batch together (within the small
+                // context's total); a large one goes alone
+                if (vm && !L.batch.empty() &&
+                    (n > L.small_max || S->reqs[L.batch[0]].n > L.small_max || total + n > L.small_total))
+                    break;
                 S->queue.pop_front();
                 S->reqs[t].state = RUNNING;
                 L.batch.push_back(t);
@@ -308,6 +337,7 @@ PS_API ps_status ps_server_create(const ps_server_config* cfg, ps_server** out)
     if (!out) return PS_EINVAL;
     *out = nullptr;
     if (!cfg || cfg->max_n == 0 || cfg->max_n > 0xffffffffull || cfg->budget_bytes == 0) return PS_EINVAL;
+    if (cfg->storage != PS_MODE_PINGPONG && cfg->storage != PS_MODE_VM) return PS_EINVAL;
     ps_server* S = new (std::nothrow) ps_server();
     if (!S) return PS_ENOMEM;
     S->cfg = *cfg;
@@ -315,7 +345,8 @@ PS_API ps_status ps_server_create(const ps_server_config* cfg, ps_server** out)
     S->lane_count = S->cfg.lane_max_count ? S->cfg.lane_max_count : 1024;
     uint64_t lane_total = S->cfg.lane_max_total;
     if (!lane_total) {
-        lane_total = (uint64_t)((double)S->cfg.budget_bytes / S->cfg.lanes / BYTES_PER_ELEM_ESTIMATE);
+        const double per_elem = S->cfg.storage == PS_MODE_VM ? BYTES_PER_ELEM_ESTIMATE_VM : BYTES_PER_ELEM_ESTIMATE;
+        lane_total = (uint64_t)((double)S->cfg.budget_bytes / S->cfg.lanes / per_elem);
         if (lane_total > (1ull << 28)) lane_total = 1ull << 28;
     }
     if (lane_total < S->cfg.max_n) lane_total = S->cfg.max_n;
@@ -355,18 +386,33 @@ PS_API ps_status ps_server_create(const ps_server_config* cfg, ps_server** out)
         }
         ps_config c;
         std::memset(&c, 0, sizeof(c));
-        c.mode = PS_MODE_PINGPONG;
+        c.mode = S->cfg.storage;
         c.want_perm = S->cfg.want_perm;
         c.key_type = S->cfg.key_type;
         c.flags = S->cfg.flags & PS_FLAG_DESCENDING_RUNS;
         c.max_n = S->cfg.max_n;
-        c.max_total = lane_total;
-        c.max_count = S->lane_count;
+        c.max_total = S->cfg.storage == PS_MODE_VM ? S->cfg.max_n : lane_total;   // VM: one request per call
+        c.max_count = S->cfg.storage == PS_MODE_VM ? 1u : S->lane_count;
         st = ps_create(&c, (int)S->cfg.device, L.stream, &L.ctx);
         if (st != PS_OK) break;
         uint64_t scratch = 0;
         st = ps_get_scratch_bytes(L.ctx, &scratch);
         if (st != PS_OK) break;
+        if (S->cfg.storage == PS_MODE_VM) {
+            L.small_max = std::min<uint64_t>(SMALL_MAX, S->cfg.max_n);
+            L.small_total = std::min<uint64_t>(SMALL_TOTAL, lane_total);
+            ps_config cs = c;
+            cs.mode = PS_MODE_PINGPONG;
+            cs.max_n = L.small_max;
+            cs.max_total = L.small_total;
+            cs.max_count = S->lane_count;
+            st = ps_create(&cs, (int)S->cfg.device, L.stream, &L.ctx_small);
+            if (st != PS_OK) break;
+            uint64_t small = 0;
+            st = ps_get_scratch_bytes(L.ctx_small, &small);
+            if (st != PS_OK) break;
+            scratch += small;
+        }
         // what this lane holds: its arrays, its offsets table and its context
         S->bytes += lane_total * 4 * (S->cfg.want_perm ? 2 : 1) + (S->lane_count + 1) * sizeof(uint64_t) + scratch;
         if (S->bytes > S->cfg.budget_bytes) {   // stop as soon as the lanes overrun the budget

@@ -147,3 +147,51 @@ def test_server_charges_what_the_lanes_hold():
     with pytest.raises(binding.PowersortError) as e:
         binding.Server(need - 1, 1 << 20, lanes=lanes, lane_max_total=lane_total, lane_max_count=count)
     assert e.value.status == binding.PS_ENOMEM
+
+
+def test_vm_lanes_same_results_in_less_memory(oracle_mod):
+    """VM-storage lanes (the paged mode for a device-memory budget): a large
+    request is sorted by itself with paged storage, small ones (up to 2^20)
+    are batched in a small Pingpong context.  Every request's result equals
+    the oracle's, the server charges each lane its arrays, offsets table and
+    both contexts' scratch, and at n = 2^24 a VM lane's contexts hold under
+    half of a Pingpong lane's."""
+    from paper_2605_27147_gb300 import binding
+
+    rng = np.random.RandomState(9)
+    dists = ["uniform", "zipf", "runs", "few", "sorted", "reversed"]
+    sizes = [int(x) for x in np.floor(2.0 ** (6 + 14 * rng.rand(30)))] + [0, 1, 64, 65, 1 << 20]
+    reqs = []
+    for i, n in enumerate(sizes):
+        keys = inputs.make(dists[i % len(dists)], n, 2000 + i)
+        reqs.append((keys, _pinned(keys), torch.empty(n, dtype=torch.int32).pin_memory(),
+                     torch.empty(n, dtype=torch.int32).pin_memory()))
+    lane_total, lanes, count = 1 << 21, 2, 16
+    with binding.Context(1 << 20, mode=binding.PS_MODE_VM, want_perm=True) as c:
+        vm_scratch = c.scratch_bytes()
+    # the lane's context for batches of small requests (up to 2^20 each, 2^22 in
+    # all, capped by the requests' and the lane's sizes)
+    with binding.Context(1 << 20, want_perm=True, max_total=lane_total, max_count=count) as c:
+        vm_scratch += c.scratch_bytes()
+    with binding.Server(1 << 30, 1 << 20, storage=binding.PS_MODE_VM, lanes=lanes, lane_max_total=lane_total,
+                        lane_max_count=count) as srv:
+        tickets = [(k, srv.submit(hin.data_ptr(), hk.data_ptr(), hp.data_ptr(), keys.size))
+                   for k, (keys, hin, hk, hp) in enumerate(reqs)]
+        for _, t in tickets:
+            srv.wait(t, 120.0)
+        st = srv.stats()
+    assert st["completed"] == len(reqs) and st["failed"] == 0
+    assert st["device_bytes"] == lanes * (8 * lane_total + 8 * (count + 1) + vm_scratch), st
+    for k, (keys, hin, hk, hp) in enumerate(reqs):
+        n = keys.size
+        ref = oracle_mod.powersort(keys)
+        assert np.array_equal(hk.numpy().view(np.uint32)[:n], ref.keys), k
+        assert np.array_equal(hp.numpy().view(np.uint32)[:n], ref.perm), k
+    # the memory a lane's context holds at n = 2^24: a page pool and tables
+    # against Pingpong's n-element scratch
+    big = 1 << 24
+    held = {}
+    for mode in (binding.PS_MODE_PINGPONG, binding.PS_MODE_VM):
+        with binding.Server(1 << 32, big, storage=mode, lanes=1, lane_max_total=big, lane_max_count=1) as s2:
+            held[mode] = s2.stats()["device_bytes"] - 8 * big - 16
+    assert held[binding.PS_MODE_VM] * 2 < held[binding.PS_MODE_PINGPONG], held
