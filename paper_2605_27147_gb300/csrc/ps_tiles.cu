@@ -101,17 +101,20 @@ __device__ __forceinline__ uint32_t net_key(const unsigned long long* w, uint32_
 }
 
 // The network road for one tile of `size` elements: sorted (key, position)
-// words end in sm.w[result]; returns result.
+// words end in sm.w[result]; returns result.  The tile is padded to N, a
+// multiple of 16 words (padding sorts last); the merge levels pair blocks of
+// w words up to the largest power of two below N, the last pair of a level
+// possibly partial or without a partner, so a tile costs its own size, not
+// the next power of two.
 __device__ int tile_network(NetSmem& sm, const uint32_t* ksrc, uint32_t size)
 {
     const int tid = threadIdx.x;
-    uint32_t P = NET_PER;                       // a power of two >= size
-    while (P < size) P <<= 1;
-    for (uint32_t x = tid; x < P; x += TILE_BLOCK)
+    const uint32_t N = (size + NET_PER - 1) & ~(uint32_t)(NET_PER - 1);
+    for (uint32_t x = tid; x < N; x += TILE_BLOCK)
         sm.w[0][net_slot(x)] = x < size ? ((unsigned long long)__ldg(ksrc + x) << 32) | x : ~0ull;
     __syncthreads();
     const uint32_t x0 = (uint32_t)tid * NET_PER;
-    if (x0 < P) {
+    if (x0 < N) {
         unsigned long long v[NET_PER];
 #pragma unroll
         for (int j = 0; j < NET_PER; ++j) v[j] = sm.w[0][net_slot(x0) + j];
@@ -121,34 +124,36 @@ __device__ int tile_network(NetSmem& sm, const uint32_t* ksrc, uint32_t size)
     }
     __syncthreads();
     int cur = 0;
-    for (uint32_t w = NET_PER; w < P; w <<= 1) {
+    for (uint32_t w = NET_PER; w < N; w <<= 1) {
         const unsigned long long* src = sm.w[cur];
         unsigned long long* dst = sm.w[cur ^ 1];
-        if (x0 < P) {
+        if (x0 < N) {
             const uint32_t blk = x0 & ~(2 * w - 1), d = x0 - blk;
             const uint32_t A = blk, B = blk + w;
+            const uint32_t la = min(w, N - A), lb = B < N ? min(w, N - B) : 0u;
             // keys only: the blocks are stably sorted and A's positions come
             // before B's, so ties to A keep the (key, position) order (a block
-            // holding padding is followed only by padding)
-            uint32_t lo = d > w ? d - w : 0u, hi = min(d, w);
+            // holding padding is followed only by padding); a block without a
+            // partner (lb = 0) is copied
+            uint32_t lo = d > lb ? d - lb : 0u, hi = min(d, la);
             while (lo < hi) {
                 const uint32_t mid = (lo + hi) >> 1;
                 if (net_key(src, net_slot(A + mid)) <= net_key(src, net_slot(B + d - 1 - mid))) lo = mid + 1;
                 else hi = mid;
             }
             uint32_t ia = lo, ib = d - lo;
-            unsigned long long va = ia < w ? src[net_slot(A + ia)] : 0ull;
-            unsigned long long vb = ib < w ? src[net_slot(B + ib)] : 0ull;
+            unsigned long long va = ia < la ? src[net_slot(A + ia)] : 0ull;
+            unsigned long long vb = ib < lb ? src[net_slot(B + ib)] : 0ull;
             unsigned long long* out = dst + net_slot(x0);
-            // branch-free serial merge; an exhausted side is read at its first
-            // slot (a valid address whose value is never used)
+            // branch-free serial merge; an exhausted side is read at the
+            // first slot of A (a valid address whose value is never used)
 #pragma unroll
             for (int j = 0; j < NET_PER; ++j) {
-                const bool take_a = ia < w && (ib >= w || (uint32_t)(va >> 32) <= (uint32_t)(vb >> 32));
+                const bool take_a = ia < la && (ib >= lb || (uint32_t)(va >> 32) <= (uint32_t)(vb >> 32));
                 out[j] = take_a ? va : vb;
                 ia += take_a;
                 ib += !take_a;
-                const unsigned long long nxt = src[net_slot(take_a ? A + (ia < w ? ia : 0u) : B + (ib < w ? ib : 0u))];
+                const unsigned long long nxt = src[net_slot(take_a ? A + (ia < la ? ia : 0u) : (ib < lb ? B + ib : A))];
                 va = take_a ? nxt : va;
                 vb = take_a ? vb : nxt;
             }
