@@ -107,6 +107,13 @@ typedef struct ps_config {
  * scratch, the sorted 64-bit rows). */
 #define PS_FLAG_RECORDS 8u
 #define PS_RECORD_MAX_WORDS 1024u
+/* VM storage: the final Copy (Sec. 4) in batches of consecutive target pages
+ * -- each target's content first moved out to a free page, then every target
+ * filled, the paper's page-by-page order done a batch at a time -- instead of
+ * the default walk along the chains of the page permutation (one move per
+ * page).  The result is the same; the default is faster, and falls back to
+ * this order by itself when the chains do not split into short segments. */
+#define PS_FLAG_VM_BATCHED_COPY 16u
 
 /* Per-call statistics (sums over instances for batched calls).  The paper's
  * merge cost M is the sum of the lengths of all merge inputs (Sec. 2

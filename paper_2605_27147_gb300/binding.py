@@ -30,6 +30,7 @@ EXPORTS = (
 )
 PS_NOALLOC_MAX_N = 262144
 PS_FLAG_TIMING, PS_FLAG_HOST_IO, PS_FLAG_DESCENDING_RUNS, PS_FLAG_RECORDS = 1, 2, 4, 8
+PS_FLAG_VM_BATCHED_COPY = 16
 PS_KEY_U32, PS_KEY_I32, PS_KEY_F32 = 0, 1, 2
 PHASES = ("setup", "runs", "plan", "tiles", "merge_rounds", "finish")
 

@@ -520,6 +520,7 @@ PS_API ps_status ps_create(const ps_config* cfg, int device, void* cuda_stream, 
         if (st == PS_OK && cfg->want_perm) st = dev_alloc(c, &c->io_perm, max_total);
     }
     J.desc_runs = (cfg->flags & PS_FLAG_DESCENDING_RUNS) ? 1u : 0u;
+    J.vm_batched_copy = (cfg->flags & PS_FLAG_VM_BATCHED_COPY) ? 1u : 0u;
     J.key_type = cfg->key_type;
     if (st == PS_OK && (cfg->flags & PS_FLAG_TIMING)) {
         c->timing = true;

@@ -178,6 +178,7 @@ struct Job {
     uint32_t count;
     uint32_t want_perm;
     uint32_t desc_runs;         // nonzero: strictly decreasing runs are taken and reversed
+    uint32_t vm_batched_copy;   // nonzero: VM storage's Copy in batches (PS_FLAG_VM_BATCHED_COPY)
     uint32_t key_type;          // ps_key_type: keys are mapped to order-preserving u32 and back
     const uint32_t* desc_mask;  // records: descent bit per position (run detection reads it, not keys)
     uint32_t tile_cap;          // T: largest merge-tree node merged on chip

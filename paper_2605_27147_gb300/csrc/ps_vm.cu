@@ -926,6 +926,10 @@ __global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_copy(Job J)
     if (!grid_barrier(C)) return;
     for (uint32_t u = gtid; u < NA; u += gstride) J.holder[J.pt[u]] = u;
     if (!grid_barrier(C)) return;
+    if (J.vm_batched_copy) {                       // the batched order, asked for
+        copy_in_batches(J, C, n, perm);
+        return;
+    }
     // the free pool pages; every target's predecessor link (the target whose
     // data it holds) and rank 1, or none and rank 0 at a chain's start
     for (uint32_t p = NAC + gtid; p < NP; p += gstride)
