@@ -681,7 +681,8 @@ __device__ __forceinline__ void vm_copy_page(const Job& J, uint32_t dst, uint32_
 //      to a temporary page, so the segment before it reads the saved copy
 //      while the segment itself overwrites the page.  The temporaries are
 //      the free pool pages and page-sized slots of the page-record and split
-//      tables (rewritten by every round, unused during Copy).  S is the
+//      tables (rewritten by every round, unused during Copy) and of the
+//      free-page ring past the two lists Copy keeps in it.  S is the
 //      smallest power of two (and at least the moves per CTA) for which the
 //      temporaries cover every save;
 //   4. a CTA per segment walks it, page by page.
@@ -872,33 +873,41 @@ struct CopySlots {
     uint32_t na;
     uint32_t* b;      // second region and its slots
     uint32_t nb;
+    uint32_t* c;      // third region (the free-page ring past Copy's two lists) and its slots
+    uint32_t nc;
 };
 
 __device__ __forceinline__ CopySlots copy_slots(const Job& J)
 {
-    const size_t P = (size_t)1 << J.vm_plog2, NAC = J.vm_na_cap;
+    const size_t P = (size_t)1 << J.vm_plog2, NAC = J.vm_na_cap, NP = NAC + J.vm_pool;
     const size_t a0 = ((CW_COUNTERS * NAC + CC_WORDS) + 3) & ~(size_t)3;     // 16-byte aligned
+    const size_t c0 = (2 * NP + 3) & ~(size_t)3;
     const size_t a_words = (size_t)VM_REC_WORDS * NAC, b_words = (NAC + 1) * VM_SPLIT_WORDS;
     CopySlots c;
     c.a = J.vm_rec + a0;
     c.na = a_words > a0 ? (uint32_t)((a_words - a0) / (2 * P)) : 0u;
     c.b = J.vm_split_at;
     c.nb = (uint32_t)(b_words / (2 * P));
+    c.c = J.free_stack + c0;
+    c.nc = J.vm_ring_cap > c0 ? (uint32_t)((J.vm_ring_cap - c0) / (2 * P)) : 0u;
     return c;
 }
 
-__device__ __forceinline__ uint32_t* temp_k(const Job& J, const CopySlots& cs, uint32_t NP, uint32_t id)
+__device__ __noinline__ uint32_t* temp_k(const Job& J, uint32_t NP, uint32_t id)
 {
     if (id < NP) return phys_k(J, id);
+    const CopySlots cs = copy_slots(J);
     const size_t P = (size_t)1 << J.vm_plog2;
     const uint32_t i = id - NP;
-    return i < cs.na ? cs.a + 2 * P * i : cs.b + 2 * P * (i - cs.na);
+    if (i < cs.na) return cs.a + 2 * P * i;
+    if (i < cs.na + cs.nb) return cs.b + 2 * P * (i - cs.na);
+    return cs.c + 2 * P * (i - cs.na - cs.nb);
 }
 
-__device__ __forceinline__ uint32_t* temp_p(const Job& J, const CopySlots& cs, uint32_t NP, uint32_t id)
+__device__ __forceinline__ uint32_t* temp_p(const Job& J, uint32_t NP, uint32_t id)
 {
     if (id < NP) return phys_p(J, id);
-    return temp_k(J, cs, NP, id) + ((size_t)1 << J.vm_plog2);
+    return temp_k(J, NP, id) + ((size_t)1 << J.vm_plog2);
 }
 
 __global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_copy(Job J)
@@ -906,7 +915,6 @@ __global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_copy(Job J)
     Ctr* C = J.ctr;
     if (*(volatile uint32_t*)&C->error) return;
     __shared__ uint32_t s_cnt[CC_WORDS];
-    const CopySlots cs = copy_slots(J);
     const int tid = threadIdx.x;
     const bool perm = J.want_perm != 0;
     const uint32_t n = J.inst[0].n;
@@ -934,7 +942,11 @@ __global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_copy(Job J)
     // data it holds) and rank 1, or none and rank 0 at a chain's start
     for (uint32_t p = NAC + gtid; p < NP; p += gstride)
         if (J.holder[p] == NONE) free_pool[atomicAdd(&C->vm_copy_top[0], 1u)] = p;
-    for (uint32_t i = gtid; i < cs.na + cs.nb; i += gstride) free_pool[atomicAdd(&C->vm_copy_top[0], 1u)] = NP + i;
+    {
+        const CopySlots cs = copy_slots(J);
+        for (uint32_t i = gtid; i < cs.na + cs.nb + cs.nc; i += gstride)
+            free_pool[atomicAdd(&C->vm_copy_top[0], 1u)] = NP + i;
+    }
     for (uint32_t u = gtid; u < NA; u += gstride) {
         const uint32_t pu = J.pt[u];
         const uint32_t h = J.holder[u];
@@ -1051,9 +1063,21 @@ __global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_copy(Job J)
         const uint32_t u = __ldcg(seg + i);
         if (!(__ldcg(W + CW_FLAGS * NAC + u) & CF_SAVED)) continue;
         const uint32_t t = __ldcg(W + CW_TEMP * NAC + u);
-        vm_copy_keys_perm(J, temp_k(J, cs, NP, t), temp_p(J, cs, NP, t), phys_k(J, u), phys_p(J, u),
+        vm_copy_keys_perm(J, temp_k(J, NP, t), temp_p(J, NP, t), phys_k(J, u), phys_p(J, u),
                           page_size(J, J.holder[u], n), perm);
         ++made;
+    }
+    // every target's move, so that a walk reads one step ahead: the page it
+    // receives its data from (the saved copy when pt[u] starts a segment),
+    // and the next target of its segment (NONE: the segment ends here)
+    uint32_t* msrc = W + CW_MIN0 * NAC;
+    uint32_t* mnext = W + CW_MIN1 * NAC;
+    for (uint32_t u = gtid; u < NA; u += gstride) {
+        const uint32_t p = J.pt[u];
+        const bool target = p < NA;
+        const bool saved = target && (W[CW_FLAGS * NAC + p] & CF_SAVED);
+        msrc[u] = saved ? W[CW_TEMP * NAC + p] : p;
+        mnext[u] = (!target || saved) ? NONE : p;
     }
     if (!grid_barrier(C)) return;
     // 4. the walks (a CTA per segment): u receives its data from pt[u] -- or
@@ -1067,22 +1091,23 @@ __global__ void __launch_bounds__(VM_BLOCK, 4) k_vm_copy(Job J)
             made += 2;
             continue;
         }
+        uint32_t src = __ldcg(msrc + u), nxt = __ldcg(mnext + u);
         for (uint32_t step = 0;; ++step) {
             if (step > S) {                         // never expected: a segment has at most S moves
                 if (tid == 0) set_error(C, DERR_INTERNAL, 70);
                 break;
             }
-            const uint32_t p = __ldcg(J.pt + u);
-            const bool target = p < NA;
-            const uint32_t fv = target ? __ldcg(W + CW_FLAGS * NAC + p) : 0u;
-            const bool saved = target && (fv & CF_SAVED);
-            const uint32_t src = saved ? __ldcg(W + CW_TEMP * NAC + p) : p;
-            vm_copy_keys_perm(J, phys_k(J, u), phys_p(J, u), temp_k(J, cs, NP, src), temp_p(J, cs, NP, src),
+            // the next step's move flies with this step's copy
+            const uint32_t src2 = nxt < NA ? __ldcg(msrc + nxt) : 0u;
+            const uint32_t nxt2 = nxt < NA ? __ldcg(mnext + nxt) : NONE;
+            vm_copy_keys_perm(J, phys_k(J, u), phys_p(J, u), temp_k(J, NP, src), temp_p(J, NP, src),
                               page_size(J, u, n), perm);
             ++made;
-            __syncthreads();                       // u's loads of p are complete before p is written
-            if (!target || saved) break;
-            u = p;
+            __syncthreads();                       // u's loads of its source are complete before it is written
+            if (nxt >= NA) break;
+            u = nxt;
+            src = src2;
+            nxt = nxt2;
         }
     }
     if (tid == 0 && made) atomicAdd(&C->vm_copy_moves, made);
