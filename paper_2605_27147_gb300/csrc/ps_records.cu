@@ -28,7 +28,9 @@
 //      REC_SMEM (64-bit keys of a small range: the window is the high word,
 //      one word is left), the merge passes are replaced: the library's own
 //      batched 32-bit sort (a second, internal context) orders every such
-//      group's last words, stably, in one call (k_rec_nested_*);
+//      group's last words, stably, in one call (k_rec_nested_*; the call is
+//      a CUDA graph whose conditional node runs it only when such a group
+//      exists);
 //   5. the rows move once, through the permutation (ps_gather_rows' kernel),
 //      instead of at every merge.
 #include "ps_internal.cuh"

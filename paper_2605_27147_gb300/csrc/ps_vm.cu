@@ -708,7 +708,10 @@ constexpr uint32_t COPY_SEG_MAX = 1024;   // longest segment the chain walk acce
 constexpr uint32_t COPY_KMAX = 17;        // segment lengths 2^0 .. 2^16 counted
 
 // scratch of the chain walk in the page-record table (free during Copy):
-// arrays of vm_na_cap words
+// arrays of vm_na_cap words -- the ranking's ancestor, distance and minimum,
+// double-buffered (the minimum arrays then hold every target's move: its
+// source and the next target of its segment), the flags and the saves'
+// temporaries, then the counters
 enum : uint32_t { CW_ANC0, CW_DIST0, CW_MIN0, CW_ANC1, CW_DIST1, CW_MIN1, CW_FLAGS, CW_TEMP, CW_COUNTERS };
 constexpr uint32_t CF_DONE = 1u, CF_CYCLE = 2u, CF_SAVED = 4u, CF_SWAP = 8u;
 // counters after the arrays: [0, COPY_KMAX) saves needed per segment length,
