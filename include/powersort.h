@@ -261,9 +261,10 @@ PS_API ps_status ps_sync(ps_ctx* ctx);
  * hang is involved. */
 PS_API ps_status ps_selftest_wait_timeout(ps_ctx* ctx);
 
-/* Canary words after every device buffer the context owns: PS_OK while they
- * hold their pattern, PS_EINTERNAL if a kernel wrote past a buffer's end
- * (synchronises). */
+/* Canary words after every device buffer the context owns (with
+ * PS_FLAG_RECORDS, also those of the inner context of its nested sort):
+ * PS_OK while they hold their pattern, PS_EINTERNAL if a kernel wrote past a
+ * buffer's end (synchronises). */
 PS_API ps_status ps_check_guards(ps_ctx* ctx);
 
 /* Introspection of the last call, for parity checks (synchronises).

@@ -865,7 +865,8 @@ PS_API ps_status ps_check_guards(ps_ctx* ctx)
         for (size_t i = 0; i < GUARD_BYTES; ++i)
             if (h[i] != GUARD_BYTE) return PS_EINTERNAL;
     }
-    return PS_OK;
+    // the context a record sort keeps for its nested sort
+    return ctx->rec_inner ? ps_check_guards(ctx->rec_inner) : PS_OK;
 }
 
 PS_API ps_status ps_selftest_wait_timeout(ps_ctx* ctx)
