@@ -61,19 +61,6 @@ __device__ __forceinline__ uint32_t inst_of_slot(const Job& J, unsigned long lon
     return find_inst(J.count, slot, [&](uint32_t i) { return J.inst[i].run_base; });
 }
 
-// Warp-aggregated append to a list: returns the slot for this lane (or NONE).
-__device__ __forceinline__ uint32_t warp_append(uint32_t* counter, bool want)
-{
-    const uint32_t mask = __ballot_sync(FULL, want);
-    if (!mask) return NONE;
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(mask) - 1;
-    uint32_t base = 0;
-    if (lane == leader) base = atomicAdd(counter, (uint32_t)__popc(mask));
-    base = __shfl_sync(FULL, base, leader);
-    return want ? base + __popc(mask & ((1u << lane) - 1u)) : NONE;
-}
-
 // The fixed-point midpoint of the run [s, e) of an instance of n elements:
 // floor(x / n) for x = (s + e) 2^31 < 2^64, without a division.  With
 // recip = floor((2^64 - 1) / n) > (2^64 - 1) / n - 1, the high half of
@@ -548,8 +535,13 @@ int nodes_max_grid(int num_sms)
 
 cudaError_t launch_plan(const Job& J, int grid, int nodes_grid, cudaStream_t s)
 {
-    // k_nodes: every CTA resident at once (its passes are equal shares)
-    k_nodes<<<nodes_grid, PLAN_BLOCK, 0, s>>>(J);
+    // k_nodes: every CTA resident at once (its passes are equal shares), and
+    // an odd number of them: the grid stride is then an odd multiple of
+    // PLAN_BLOCK slots, so the boundaries at multiples of 2^k (the wide
+    // merges of a balanced tree, whose searches leave the staged window) fall
+    // to every CTA in turn instead of to the same CTAs in every pass
+    const int ng = nodes_grid > 1 && (nodes_grid & 1) == 0 ? nodes_grid - 1 : nodes_grid;
+    k_nodes<<<ng, PLAN_BLOCK, 0, s>>>(J);
     k_depth<<<grid, PLAN_BLOCK, 0, s>>>(J);
     k_bucket_scan<<<1, 32, 0, s>>>(J);
     k_bucket<<<grid, PLAN_BLOCK, 0, s>>>(J);
