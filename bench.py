@@ -194,21 +194,30 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+def kernel_code_digest(path):
+    """First 16 hex digits of the sha256 of a source file without its
+    whole-line // comments and trailing spaces: edits of comments leave it
+    unchanged, any edit of code changes it."""
+    with open(path) as f:
+        lines = [line.rstrip() for line in f.read().splitlines() if not line.lstrip().startswith("//")]
+    return hashlib.sha256("\n".join(lines).encode()).hexdigest()[:16]
+
+
 def traffic_from_profile(workload, storage="pingpong"):
     """DRAM bytes per launch of the merge phase's kernels (k_merge_rounds, or
     k_vm_rounds + k_vm_copy with VM storage) from the committed ncu summary,
-    if it was taken on the current kernel source (else None)."""
+    if it was taken on the current kernel code (else None)."""
     name, kernel_src = ("merge_rounds", "ps_merge.cu") if storage == "pingpong" else ("vm_rounds", "ps_vm.cu")
     path = os.path.join(ROOT, "profiles", f"{name}_{workload}.txt")
     src = os.path.join(ROOT, "paper_2605_27147_gb300", "csrc", kernel_src)
     try:
-        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        digest = kernel_code_digest(src)
         vals = {}
         for line in open(path):
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 vals[k.strip()] = v.strip()
-        if vals.get("kernel_source_sha256_16") != digest:
+        if vals.get("kernel_code_sha256_16") != digest:
             return None
         return float(vals["dram_bytes_per_launch_scaled"])
     except Exception:

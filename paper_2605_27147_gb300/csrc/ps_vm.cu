@@ -322,7 +322,7 @@ __device__ void vm_page(const Job& J, VmSmem& sm, const VmGroup& G, uint32_t u, 
         cp_async_wait<0>();
         group_sync(G);
         // every input element is read: the consumed counts go out now and are
-        // looked at after the merge (a freed page is not read again this round)
+        // looked at after the merge (a freed page is not read again in this merge round)
         const Consumed cons = consume_start(J, tid, lo + a0, na, mid + b0, nb);
         // each thread merges VM_K consecutive outputs, recording for each the
         // staging slot it comes from; then the group writes the page out in

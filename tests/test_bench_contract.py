@@ -42,3 +42,24 @@ def test_library_arm_fails_loudly_without_a_gpu():
     r = _bench("--steps", "1", "--warmup", "3", "--no-cpu", "--no-e2e", timeout=300)
     assert r.returncode != 0
     assert not any(ln.startswith("{") for ln in r.stdout.splitlines())
+
+
+def test_profile_counters_follow_the_kernel_code(tmp_path):
+    """roofline.traffic comes from a committed ncu summary only while the
+    kernel's code is the one the summary was taken on: editing a comment keeps
+    the digest, editing code changes it."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    src = tmp_path / "k.cu"
+    src.write_text("// a kernel\n__global__ void k(int* p)\n{\n    // store\n    p[0] = 1;\n}\n")
+    d0 = bench.kernel_code_digest(str(src))
+    src.write_text("// a kernel, reworded\n__global__ void k(int* p)   \n{\n        // the store\n    p[0] = 1;\n}\n")
+    assert bench.kernel_code_digest(str(src)) == d0
+    src.write_text("// a kernel\n__global__ void k(int* p)\n{\n    // store\n    p[0] = 2;\n}\n")
+    assert bench.kernel_code_digest(str(src)) != d0
+    # the committed summaries resolve against the sources they name
+    for workload in ("hbm_2^28", "plain_2^24"):
+        for storage in ("pingpong", "vm"):
+            t = bench.traffic_from_profile(workload, storage)
+            assert t is None or t > 0
