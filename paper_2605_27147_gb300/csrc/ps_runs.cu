@@ -229,34 +229,69 @@ __global__ void __launch_bounds__(1024) k_setup(Job J)
 
 namespace {
 
-// First set bit at index >= k0 in bits[0, kmax), kmax a multiple of 32;
-// kmax when there is none.
+// A chunk's descent bitmask is followed, in the same shared array, by two
+// summaries of its words for the searches below: bit w of the first is set
+// when word w has a set bit, bit w of the second when word w has a clear bit.
+// A search then skips a long run of empty (or full) words in one step instead
+// of a dependent load per word.
+constexpr int SUM_WORDS = (RUN_WORDS + 31) / 32;
+constexpr int BITS_NZ = RUN_WORDS;                  // words with a descent
+constexpr int BITS_NF = RUN_WORDS + SUM_WORDS;      // words with a non-descent
+constexpr int BITS_SLOTS = RUN_WORDS + 2 * SUM_WORDS;
+
+// Warp 0, once the bitmask is complete: its summaries.
+__device__ __forceinline__ void bits_summary(uint32_t* bits)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < SUM_WORDS; ++j) {
+        const int w = j * 32 + lane;
+        const uint32_t b = w < RUN_WORDS ? bits[w] : 0u;
+        const uint32_t nz = __ballot_sync(FULL, w < RUN_WORDS && b != 0u);
+        const uint32_t nf = __ballot_sync(FULL, w < RUN_WORDS && b != FULL);
+        if (lane == 0) {
+            bits[BITS_NZ + j] = nz;
+            bits[BITS_NF + j] = nf;
+        }
+    }
+}
+
+// First word index >= w0 whose bit is set in the summary sum, or wmax.
+__device__ __forceinline__ int next_word(const uint32_t* sum, int w0, int wmax)
+{
+    if (w0 >= wmax) return wmax;
+    int j = w0 >> 5;
+    uint32_t m = sum[j] & (FULL << (w0 & 31));
+    while (m == 0) {
+        if (++j >= SUM_WORDS) return wmax;
+        m = sum[j];
+    }
+    const int w = (j << 5) + __ffs(m) - 1;
+    return w < wmax ? w : wmax;
+}
+
+// First set bit at index >= k0 in bits[0, kmax), kmax a multiple of 32 and at
+// most KMAX; kmax when there is none.
 __device__ __forceinline__ int next_desc(const uint32_t* bits, int k0, int kmax)
 {
     if (k0 >= kmax) return kmax;
-    int w = k0 >> 5;
-    uint32_t word = bits[w] & (FULL << (k0 & 31));
-    const int wmax = kmax >> 5;
-    while (word == 0) {
-        if (++w >= wmax) return kmax;
-        word = bits[w];
-    }
-    return (w << 5) + __ffs(word) - 1;
+    const int w = k0 >> 5, wmax = kmax >> 5;
+    const uint32_t word = bits[w] & (FULL << (k0 & 31));
+    if (word) return (w << 5) + __ffs(word) - 1;
+    const int w2 = next_word(bits + BITS_NZ, w + 1, wmax);
+    return w2 < wmax ? (w2 << 5) + __ffs(bits[w2]) - 1 : kmax;
 }
 
-// First clear bit at index >= k0 in bits[0, kmax), kmax a multiple of 32;
-// kmax when there is none.
+// First clear bit at index >= k0 in bits[0, kmax), kmax a multiple of 32 and
+// at most KMAX; kmax when there is none.
 __device__ __forceinline__ int next_clear(const uint32_t* bits, int k0, int kmax)
 {
     if (k0 >= kmax) return kmax;
-    int w = k0 >> 5;
-    uint32_t word = ~bits[w] & (FULL << (k0 & 31));
-    const int wmax = kmax >> 5;
-    while (word == 0) {
-        if (++w >= wmax) return kmax;
-        word = ~bits[w];
-    }
-    return (w << 5) + __ffs(word) - 1;
+    const int w = k0 >> 5, wmax = kmax >> 5;
+    const uint32_t word = ~bits[w] & (FULL << (k0 & 31));
+    if (word) return (w << 5) + __ffs(word) - 1;
+    const int w2 = next_word(bits + BITS_NF, w + 1, wmax);
+    return w2 < wmax ? (w2 << 5) + __ffs(~bits[w2]) - 1 : kmax;
 }
 
 __device__ __forceinline__ bool desc_bit(const uint32_t* bits, int k)
@@ -493,7 +528,7 @@ __device__ __forceinline__ unsigned long long apply_map(unsigned long long at, c
 __global__ void __launch_bounds__(RUN_BLOCK) k_runs(Job J)
 {
     __shared__ __align__(16) uint32_t keys[2][WIN_SLOTS];   // double-buffered key windows
-    __shared__ uint32_t bits[RUN_WORDS];
+    __shared__ uint32_t bits[BITS_SLOTS];
     __shared__ uint32_t mapv[MAP_STATES];
     __shared__ uint32_t agg[MAP_STATES];     // (runs << 8 | state) after the range so far, per entry state
     __shared__ uint32_t s_last, s_reset;
@@ -536,6 +571,7 @@ __global__ void __launch_bounds__(RUN_BLOCK) k_runs(Job J)
         else bits_from_keys(v, w, keys[buf], bits);
         __syncthreads();
         const bool desc = J.desc_runs != 0;
+        if (tid < 32) bits_summary(bits);        // published by chunk_may_natural's barrier
         const bool walk = chunk_may_natural(v, bits, desc);
         if (tid <= (int)v.m) mapv[tid] = chain_map(v, bits, (uint32_t)tid, walk, desc);
         __syncthreads();
@@ -632,7 +668,7 @@ __global__ void __launch_bounds__(RUN_BLOCK) k_runs_emit(Job J)
 {
     constexpr int NW = RUN_BLOCK / 32;
     __shared__ __align__(16) uint32_t keys[WIN_SLOTS];   // one chunk's key window
-    __shared__ uint32_t bits[RUN_WORDS];
+    __shared__ uint32_t bits[BITS_SLOTS];
     __shared__ uint32_t win[WIN][MAP_STATES];
     __shared__ unsigned long long entry[WIN];    // runs before the chunk << 8 | its entry state
 
@@ -732,6 +768,7 @@ __global__ void __launch_bounds__(RUN_BLOCK) k_runs_emit(Job J)
                 bits_from_keys(v, w, keys, bits);
             }
             __syncthreads();
+            if (tid < 32) bits_summary(bits);    // thread 0, which walks, wrote it
             if (tid == 0) {
                 const Inst& I = J.inst[v.qi];
                 const uint32_t st = (uint32_t)(entry[i] & 0xffu);
