@@ -238,6 +238,7 @@ constexpr int SUM_WORDS = (RUN_WORDS + 31) / 32;
 constexpr int BITS_NZ = RUN_WORDS;                  // words with a descent
 constexpr int BITS_NF = RUN_WORDS + SUM_WORDS;      // words with a non-descent
 constexpr int BITS_SLOTS = RUN_WORDS + 2 * SUM_WORDS;
+static_assert(RUN_WORDS <= RUN_BLOCK - 32, "k_runs' last warp has no bitmask words to check");
 
 // Warp 0, once the bitmask is complete: its summaries.
 __device__ __forceinline__ void bits_summary(uint32_t* bits)
@@ -571,7 +572,10 @@ __global__ void __launch_bounds__(RUN_BLOCK) k_runs(Job J)
         else bits_from_keys(v, w, keys[buf], bits);
         __syncthreads();
         const bool desc = J.desc_runs != 0;
-        if (tid < 32) bits_summary(bits);        // published by chunk_may_natural's barrier
+        // the summaries by the last warp, which has no words to check in
+        // chunk_may_natural (so they cost that barrier no time); published
+        // by its barrier
+        if (tid >= RUN_BLOCK - 32) bits_summary(bits);
         const bool walk = chunk_may_natural(v, bits, desc);
         if (tid <= (int)v.m) mapv[tid] = chain_map(v, bits, (uint32_t)tid, walk, desc);
         __syncthreads();
